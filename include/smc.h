@@ -1,0 +1,200 @@
+/*
+ * smc.h -- C ABI of the GB300 swap Monte Carlo library (libsmc.so).
+ *
+ * Canonical, composition-conserving Metropolis swap Monte Carlo on a BCC
+ * alloy lattice, scheduled over non-interacting link cells (SMC-X, Sec. II-A;
+ * SMC-AI, Sec. III-A and Algorithm 1).  Energies come from pair interactions
+ * over neighbour shells or from a small BF16 MLP on per-shell species counts
+ * (MLPNet, Sec. IV-B).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * Lattice.  A box of nx x ny x nz BCC cells (each >= 2), N = 2 nx ny nz < 2^31
+ *   sites.  Site (sub, x, y, z) sits at (x + sub/2, y + sub/2, z + sub/2) a.
+ *   Occupancy is an int8 array of N species indices in [0, nspecies) in the
+ *   canonical order s = ((sub*nz + z)*ny + y)*nx + x.  nspecies <= 8
+ *   (MLP models: <= 5).
+ * Shells.  1: 8 neighbours at sqrt(3)a/2, ordered lexicographically in
+ *   (+-1/2)^3 with - before +; 2: 6 at a; 3: 12 at sqrt(2)a.
+ * Link cells and mini-steps (Sec. II-A; Algorithm 1 lines 1-2).  The link-cell
+ *   edge along an axis of n cells is 4 if n >= 8 and n % 4 == 0, else n.
+ *   A sweep is n_A = 2 Lx Ly Lz mini-steps; mini-step k visits the offset
+ *   (sub, dx, dy, dz) with k = ((sub*Lz + dz)*Ly + dy)*Lx + dx, and every link
+ *   cell tries to swap its site at that offset with a random first-shell
+ *   neighbour.  One sweep = one trial per site (the paper's MC step, Sec. V-A).
+ * Random numbers.  Philox4x32-10 with key (seed lo, seed hi) and counter
+ *   (s >> 2, replica, sweep lo, sweep hi); site s uses output word s & 3:
+ *   partner = shell-1 vector [word >> 29], r = word & (2^29 - 1).  Results do
+ *   not depend on the launch configuration.  Sweep indices 2^64-2 and 2^64-1
+ *   are reserved for the initial configuration.
+ * Metropolis (Algorithm 1 line 9).  Integer models: accept iff dE <= 0 or
+ *   r < floor(2^29 exp(-dE unit_ev / kT)) (table built on the host in FP64).
+ *   Floating-point models: accept iff dE <= 0 or (r + 1/2) 2^-29 <
+ *   exp(-dE / kT) evaluated in FP32.  A swap of two equal species is an
+ *   accepted no-op.
+ * Energies.  Pair: E = sum_i 1/2 sum_m sum_{v in shell m} V_m(s_i, s_{i+v}).
+ *   MLP: E = sum_i f(x_i), x_i = [onehot(s_i) | shell-1 counts | shell-2
+ *   counts | shell-3 counts] (5 entries each), f = W3 silu(W2 silu(W1 x + b1)
+ *   + b2) + b3 with BF16 weights, FP32 biases and FP32 accumulation.
+ *
+ * Memory and streams.  Pointers marked "device" are caller-owned device
+ * memory (for example torch tensors); "host" pointers are read during the
+ * call only.  All work is enqueued on `stream` and is complete when the
+ * stream is synchronised.  The library owns a per-device workspace (link-cell
+ * progress flags, partial sums, acceptance tables) that it grows with
+ * cudaMalloc when needed and never frees before process exit; calls that use
+ * it must not run concurrently on different streams of one device.
+ *
+ * Errors.  Argument errors return synchronously and leave every buffer
+ * untouched.  Device-side failures (a progress wait that exceeded its time
+ * limit) are latched in a device status word; smc_check(stream) synchronises
+ * the stream and returns and clears it.  smc_last_error() gives the message of
+ * the last failing call on the calling thread.  No call aborts the process.
+ */
+#ifndef SMC_H
+#define SMC_H
+
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    SMC_OK = 0,
+    SMC_ERR_ARG = -1,          /* invalid argument */
+    SMC_ERR_UNSUPPORTED = -2,  /* valid but not supported by this build */
+    SMC_ERR_CUDA = -3,         /* a CUDA runtime call failed */
+    SMC_ERR_TIMEOUT = -4,      /* a device-side progress wait timed out */
+    SMC_ERR_STATE = -5         /* inconsistent library state */
+} smc_status;
+
+typedef struct {
+    int32_t nx, ny, nz;  /* cells per axis, each >= 2 */
+    int32_t nspecies;    /* 1..8 */
+} smc_lattice;
+
+enum {
+    SMC_PAIR_I32 = 0,          /* integer pair coefficients (exact path) */
+    SMC_PAIR_F32 = 1,          /* FP32 pair coefficients, eV */
+    SMC_MLP_BF16 = 2,          /* BF16 MLP site energies */
+    SMC_PAIR_F32_MLP_BF16 = 3  /* sum of the two */
+};
+
+/* Energy model (all pointers host memory, read during the call).
+ * Pair coefficients V_m(p, q) (Sec. IV-B, effective pair interactions) are
+ * [nshells][S][S], symmetric in p, q.  MLP weights are BF16 bit patterns in
+ * row-major [out][in] order: w1 [64][20], w2 [64][64], w3 [64]. */
+typedef struct {
+    int32_t kind;            /* SMC_PAIR_I32 .. SMC_PAIR_F32_MLP_BF16 */
+    int32_t nshells;         /* pair shells 1..3 (ignored for SMC_MLP_BF16) */
+    const int32_t *v_i32;    /* SMC_PAIR_I32: units of unit_ev, |V| <= 2^24 */
+    const float *v_f32;      /* SMC_PAIR_F32*: eV */
+    double unit_ev;          /* SMC_PAIR_I32: eV per integer unit (> 0) */
+    const uint16_t *mlp_w1, *mlp_w2, *mlp_w3;
+    const float *mlp_b1, *mlp_b2;
+    float mlp_b3;
+} smc_model;
+
+/* Composition-conserving random initial configuration (the starting state
+ * of Algorithm 1).  Sites are ordered by the 64-bit key
+ * (w(seed; s>>2, replica, 2^64-2)[s&3] << 32) | w(seed; s>>2, replica,
+ * 2^64-1)[s&3] with ties broken by s; the first counts[0] sites in that order
+ * get species 0, the next counts[1] species 1, and so on.
+ *   counts  host [nspecies], non-negative, summing to N.
+ *   occ     device [N] int8, written.
+ * Errors: SMC_ERR_ARG for bad dimensions or counts. */
+smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint64_t seed,
+                            uint32_t replica, int8_t *occ, cudaStream_t stream);
+
+/* nsweeps sweeps of Algorithm 1 on occ, sweeps sweep0 .. sweep0+nsweeps-1.
+ *   occ     device [N] int8, updated in place.
+ *   kT      host [nsweeps], temperature of each sweep in eV (> 0, may be +inf
+ *           for floating-point models).
+ *   e_acc   device double, nullable: += sum of dE of accepted trials (eV),
+ *           summed in a fixed order (bit-reproducible).
+ *   n_acc   device int64, nullable: += number of accepted trials.
+ * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP models
+ * in this entry point when unavailable), SMC_ERR_CUDA. */
+smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                     uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT,
+                     double *e_acc, int64_t *n_acc, cudaStream_t stream);
+
+/* Independent replicas of possibly different sizes (each its own lattice and
+ * occupancy, shared model), advanced together in one persistent launch per
+ * chunk of sweeps.  Replica r uses RNG replica index replica0 + r, so it
+ * reproduces smc_sweep(..., replica0 + r, ...) bit for bit.
+ *   lats    host [R];  occ  host [R] array of device pointers.
+ *   kT      host [R][nsweeps] (eV).
+ *   e_acc, n_acc  device [R], nullable. */
+smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model *model,
+                             int8_t *const *occ, uint64_t seed, uint32_t replica0,
+                             uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
+                             int64_t *n_acc, cudaStream_t stream);
+
+/* Ordered pair counts n_m^{pq} = #{(i, v in shell m): s_i = p, s_{i+v} = q}
+ * (the pair numbers of Eq. 2) and Warren-Cowley SRO
+ * alpha_m^{pq} = 1 - n_m^{pq} / (N c_p z_m c_q) (NaN where c_p or c_q is 0).
+ *   nshells  1..3.   occ  device [N].
+ *   counts   device [nshells][S][S] int64, nullable.
+ *   alpha    device [nshells][S][S] double, nullable. */
+smc_status smc_sro(const smc_lattice *lat, int32_t nshells, const int8_t *occ, int64_t *counts,
+                   double *alpha, cudaStream_t stream);
+
+/* Total energy of occ.
+ *   e      device double (eV), nullable.
+ *   e_int  device int64, nullable; integer models only: E in units of unit_ev
+ *          (exact). */
+smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
+                      double *e, int64_t *e_int, cudaStream_t stream);
+
+/* dE/dtheta of the total energy at configuration occ.
+ * Layout: pair part [nshells][S(S+1)/2] with (p, q), p <= q, row-major over
+ * p then q (one parameter per unordered pair: dE/dV_m^{pq} = n_m^{pq} for
+ * p != q, n_m^{pp}/2 for p = q), then for MLP models the 5569 MLP parameters
+ * W1, b1, W2, b2, W3, b3.
+ *   grad   device float [smc_grad_size(lat, model)]. */
+int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model);
+smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
+                           float *grad, cudaStream_t stream);
+
+/* Lock-step trace of one mini-step: applies mini-step k of sweep `sweep`
+ * (as smc_sweep would) and records, per trial in link-cell order
+ * c = (cz*NLy + cy)*NLx + cx, the dE it computed (eV) and its decision.
+ *   dE   device float [N/n_A], nullable;  acc  device uint8 [N/n_A], nullable. */
+smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ,
+                              uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,
+                              double kT, float *dE, uint8_t *acc, cudaStream_t stream);
+
+/* Philox4x32-10 block function on the device, for tests: out[4i..4i+3] =
+ * Philox(ctr[4i..4i+3], key[2i..2i+1]).  All pointers device memory. */
+smc_status smc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n,
+                             cudaStream_t stream);
+
+/* Synchronises `stream`, returns the latched device status and clears it. */
+smc_status smc_check(cudaStream_t stream);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char *smc_last_error(void);
+
+/* Launch tuning (domain tile shape and CTA size) chosen by the caller's
+ * autotuner; results never depend on it.  tile_y, tile_z: link-cell columns
+ * per tile along y and z (0 = automatic); threads: CTA size, a multiple of 32
+ * in [32, 1024] (0 = automatic); ctas_per_sm: resident CTAs per SM requested
+ * (0 = automatic).  Applies to later sweeps on the calling thread. */
+typedef struct {
+    int32_t tile_y, tile_z, threads, ctas_per_sm;
+} smc_tuning;
+smc_status smc_set_tuning(const smc_tuning *t);
+
+/* Test hooks.  SMC_DBG_TIMEOUT_MS sets the progress-wait limit (default
+ * 2000 ms); SMC_DBG_SKIP_PUBLISH makes the tile with that index never publish
+ * its progress so that its neighbours time out (-1 = off). */
+enum { SMC_DBG_TIMEOUT_MS = 1, SMC_DBG_SKIP_PUBLISH = 2 };
+smc_status smc_debug_set(int32_t what, int64_t value);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,486 @@
+// smc_api.cu -- C ABI entry points of libsmc.so: argument validation,
+// per-device workspace, error reporting and dispatch to the kernels.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "smc_common.cuh"
+
+namespace smc {
+
+static thread_local char g_msg[512] = "";
+static std::mutex g_lock;  // the workspace and parameter blocks are shared
+static thread_local Tuning g_tuning;
+static int64_t g_timeout_ns = 2000LL * 1000 * 1000;
+static int64_t g_skip_tile = -1;
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_msg, sizeof g_msg, fmt, ap);
+    va_end(ap);
+}
+
+smc_status cuda_fail(cudaError_t e, const char *what)
+{
+    set_error("%s: %s", what, cudaGetErrorString(e));
+    return SMC_ERR_CUDA;
+}
+
+Tuning current_tuning() { return g_tuning; }
+int64_t debug_timeout_ns() { return g_timeout_ns; }
+int64_t debug_skip_tile() { return g_skip_tile; }
+
+static Workspace g_ws[64];
+
+Workspace *workspace(smc_status *st)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess || dev < 0 || dev >= 64) {
+        *st = cuda_fail(e == cudaSuccess ? cudaErrorInvalidDevice : e, "cudaGetDevice");
+        return nullptr;
+    }
+    Workspace *ws = &g_ws[dev];
+    if (ws->device < 0) {
+        int sms = 0, optin = 0;
+        e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaDeviceGetAttribute");
+            return nullptr;
+        }
+        const size_t cap = 1 << 20;
+        void *buf = nullptr;
+        e = cudaMalloc(&buf, cap);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaMalloc(workspace)");
+            return nullptr;
+        }
+        e = cudaMemset(buf, 0, 256);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaMemset(workspace)");
+            return nullptr;
+        }
+        ws->buf = buf;
+        ws->cap = cap;
+        ws->status = (int *)buf;
+        ws->num_sms = sms;
+        ws->smem_optin = (size_t)optin;
+        ws->device = dev;
+    }
+    *st = SMC_OK;
+    return ws;
+}
+
+// Scratch starts 256 bytes into the buffer (after the status word).  Growing
+// frees the old buffer only after the device has finished with it.
+void *workspace_scratch(Workspace *ws, size_t bytes, smc_status *st)
+{
+    const size_t need = bytes + 256;
+    if (need > ws->cap) {
+        cudaError_t e = cudaDeviceSynchronize();
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaDeviceSynchronize(workspace growth)");
+            return nullptr;
+        }
+        int status = 0;
+        e = cudaMemcpy(&status, ws->status, sizeof status, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaMemcpy(status)");
+            return nullptr;
+        }
+        size_t cap = ws->cap;
+        while (cap < need) cap *= 2;
+        void *buf = nullptr;
+        e = cudaMalloc(&buf, cap);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaMalloc(workspace)");
+            return nullptr;
+        }
+        e = cudaMemset(buf, 0, 256);
+        if (e == cudaSuccess) e = cudaMemcpy(buf, &status, sizeof status, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            *st = cuda_fail(e, "cudaMemset(workspace)");
+            return nullptr;
+        }
+        cudaFree(ws->buf);
+        ws->buf = buf;
+        ws->cap = cap;
+        ws->status = (int *)buf;
+    }
+    *st = SMC_OK;
+    return (unsigned char *)ws->buf + 256;
+}
+
+bool lattice_valid(const smc_lattice *lat, bool mlp)
+{
+    if (!lat) {
+        set_error("lattice is NULL");
+        return false;
+    }
+    if (lat->nx < 2 || lat->ny < 2 || lat->nz < 2) {
+        set_error("lattice dimensions must be >= 2 (got %d x %d x %d)", lat->nx, lat->ny, lat->nz);
+        return false;
+    }
+    if (lat->nspecies < 1 || lat->nspecies > (mlp ? 5 : kMaxSpecies)) {
+        set_error("nspecies must be in [1, %d] (got %d)", mlp ? 5 : kMaxSpecies, lat->nspecies);
+        return false;
+    }
+    const long long N = 2LL * lat->nx * lat->ny * lat->nz;
+    if (N >= (1LL << 31)) {
+        set_error("lattice too large: N = %lld sites (limit 2^31 - 1)", N);
+        return false;
+    }
+    return true;
+}
+
+static bool is_mlp(const smc_model *m) { return m->kind == SMC_MLP_BF16 || m->kind == SMC_PAIR_F32_MLP_BF16; }
+static bool has_pair(const smc_model *m) { return m->kind != SMC_MLP_BF16; }
+
+bool model_valid(const smc_lattice *lat, const smc_model *m)
+{
+    if (!m) {
+        set_error("model is NULL");
+        return false;
+    }
+    if (m->kind < SMC_PAIR_I32 || m->kind > SMC_PAIR_F32_MLP_BF16) {
+        set_error("unknown model kind %d", m->kind);
+        return false;
+    }
+    const int S = lat->nspecies;
+    if (has_pair(m)) {
+        if (m->nshells < 1 || m->nshells > kMaxShells) {
+            set_error("nshells must be in [1, 3] (got %d)", m->nshells);
+            return false;
+        }
+        if (m->kind == SMC_PAIR_I32) {
+            if (!m->v_i32 || !(m->unit_ev > 0.0) || !std::isfinite(m->unit_ev)) {
+                set_error("integer model needs v_i32 and unit_ev > 0");
+                return false;
+            }
+            for (int i = 0; i < m->nshells * S * S; ++i)
+                if (m->v_i32[i] > (1 << 24) || m->v_i32[i] < -(1 << 24)) {
+                    set_error("|V| must be <= 2^24 (entry %d = %d)", i, m->v_i32[i]);
+                    return false;
+                }
+        } else if (!m->v_f32) {
+            set_error("floating-point pair model needs v_f32");
+            return false;
+        }
+        for (int mm = 0; mm < m->nshells; ++mm)
+            for (int p = 0; p < S; ++p)
+                for (int q = 0; q < p; ++q) {
+                    const int a = (mm * S + p) * S + q, b = (mm * S + q) * S + p;
+                    const bool sym = m->kind == SMC_PAIR_I32 ? m->v_i32[a] == m->v_i32[b] : m->v_f32[a] == m->v_f32[b];
+                    if (!sym) {
+                        set_error("pair coefficients must be symmetric (shell %d, %d-%d)", mm + 1, p, q);
+                        return false;
+                    }
+                }
+    }
+    if (is_mlp(m)) {
+        if (!m->mlp_w1 || !m->mlp_w2 || !m->mlp_w3 || !m->mlp_b1 || !m->mlp_b2) {
+            set_error("MLP model needs w1, w2, w3, b1, b2");
+            return false;
+        }
+        if (S > 5) {
+            set_error("MLP models support at most 5 species");
+            return false;
+        }
+    }
+    return true;
+}
+
+}  // namespace smc
+
+using namespace smc;
+
+#define API_LOCK std::lock_guard<std::mutex> _guard(g_lock)
+
+extern "C" {
+
+const char *smc_last_error(void) { return g_msg; }
+
+smc_status smc_check(cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    cudaError_t e = cudaStreamSynchronize(stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+    int code = 0;
+    e = cudaMemcpy(&code, ws->status, sizeof code, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status)");
+    if (code != 0) {
+        const int zero = 0;
+        e = cudaMemcpy(ws->status, &zero, sizeof zero, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status reset)");
+        if (code == SMC_ERR_TIMEOUT) set_error("a device-side progress wait timed out");
+        return (smc_status)code;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_set_tuning(const smc_tuning *t)
+{
+    if (!t) {
+        g_tuning = Tuning();
+        return SMC_OK;
+    }
+    if (t->tile_y < 0 || t->tile_z < 0 || t->threads < 0 || t->ctas_per_sm < 0 ||
+        (t->threads && (t->threads % 32 || t->threads > 1024))) {
+        set_error("invalid tuning");
+        return SMC_ERR_ARG;
+    }
+    g_tuning.tile_y = t->tile_y;
+    g_tuning.tile_z = t->tile_z;
+    g_tuning.threads = t->threads;
+    g_tuning.ctas_per_sm = t->ctas_per_sm;
+    return SMC_OK;
+}
+
+smc_status smc_debug_set(int32_t what, int64_t value)
+{
+    API_LOCK;
+    if (what == SMC_DBG_TIMEOUT_MS) {
+        if (value <= 0) {
+            set_error("timeout must be positive");
+            return SMC_ERR_ARG;
+        }
+        g_timeout_ns = value * 1000 * 1000;
+        return SMC_OK;
+    }
+    if (what == SMC_DBG_SKIP_PUBLISH) {
+        g_skip_tile = value;
+        return SMC_OK;
+    }
+    set_error("unknown debug key %d", what);
+    return SMC_ERR_ARG;
+}
+
+smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,
+                            int8_t *occ, cudaStream_t stream)
+{
+    API_LOCK;
+    if (!lattice_valid(lat, false)) return SMC_ERR_ARG;
+    if (!counts || !occ) {
+        set_error("counts and occ must be non-NULL");
+        return SMC_ERR_ARG;
+    }
+    const long long N = 2LL * lat->nx * lat->ny * lat->nz;
+    long long tot = 0;
+    for (int p = 0; p < lat->nspecies; ++p) {
+        if (counts[p] < 0) {
+            set_error("negative count for species %d", p);
+            return SMC_ERR_ARG;
+        }
+        tot += counts[p];
+    }
+    if (tot != N) {
+        set_error("counts sum to %lld, lattice has %lld sites", tot, N);
+        return SMC_ERR_ARG;
+    }
+    return launch_init(lat, counts, seed, replica, occ, stream);
+}
+
+static smc_status check_sweep_args(const smc_lattice *lat, const smc_model *model, int8_t *occ, int32_t nsweeps,
+                                   const double *kT, int nkT, uint64_t sweep0)
+{
+    if (!lattice_valid(lat, model && is_mlp(model))) return SMC_ERR_ARG;
+    if (!model_valid(lat, model)) return SMC_ERR_ARG;
+    if (!occ) {
+        set_error("occ is NULL");
+        return SMC_ERR_ARG;
+    }
+    if (nsweeps < 0) {
+        set_error("nsweeps must be >= 0");
+        return SMC_ERR_ARG;
+    }
+    if (nsweeps > 0 && !kT) {
+        set_error("kT is NULL");
+        return SMC_ERR_ARG;
+    }
+    if (sweep0 + (uint64_t)nsweeps > 0xFFFFFFFFFFFFFFFEull || sweep0 + (uint64_t)nsweeps < sweep0) {
+        set_error("sweep indices reach the reserved values 2^64-2, 2^64-1");
+        return SMC_ERR_ARG;
+    }
+    for (int i = 0; i < nkT; ++i) {
+        const double t = kT[i];
+        if (!(t > 0.0) || (model->kind == SMC_PAIR_I32 && !std::isfinite(t))) {
+            set_error("kT[%d] = %g is invalid (must be > 0; finite for integer models)", i, t);
+            return SMC_ERR_ARG;
+        }
+        if (model->kind == SMC_PAIR_I32 && model->unit_ev / t < 29.0 * 0.6931471805599453 / (double)(1 << 24)) {
+            set_error("kT[%d] too high for the integer acceptance table", i);
+            return SMC_ERR_UNSUPPORTED;
+        }
+    }
+    if ((long long)nsweeps * 2 * lc_edge(lat->ny) * lc_edge(lat->nz) >= (1LL << 31)) {
+        set_error("too many sweeps in one call");
+        return SMC_ERR_ARG;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed, uint32_t replica,
+                     uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc, int64_t *n_acc,
+                     cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = check_sweep_args(lat, model, occ, nsweeps, kT, nsweeps, sweep0);
+    if (st != SMC_OK) return st;
+    if (nsweeps == 0) return SMC_OK;
+    if (is_mlp(model)) {
+        set_error("MLP sweeps are not available in this build");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    int8_t *occs[1] = {occ};
+    return launch_pair_sweep(1, lat, model, occs, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+}
+
+smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model *model, int8_t *const *occ,
+                             uint64_t seed, uint32_t replica0, uint64_t sweep0, int32_t nsweeps, const double *kT,
+                             double *e_acc, int64_t *n_acc, cudaStream_t stream)
+{
+    API_LOCK;
+    if (R < 1 || R > kMaxReplicas || !lats || !occ) {
+        set_error("R must be in [1, %d] with lats and occ non-NULL", kMaxReplicas);
+        return SMC_ERR_ARG;
+    }
+    for (int r = 0; r < R; ++r) {
+        smc_status st = check_sweep_args(&lats[r], model, occ[r], nsweeps, kT + (size_t)r * nsweeps, nsweeps, sweep0);
+        if (st != SMC_OK) return st;
+    }
+    if ((uint64_t)replica0 + (uint64_t)R > 0x100000000ull) {
+        set_error("replica indices overflow 32 bits");
+        return SMC_ERR_ARG;
+    }
+    if (nsweeps == 0) return SMC_OK;
+    if (is_mlp(model)) {
+        set_error("MLP sweeps are not available in this build");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    return launch_pair_sweep(R, lats, model, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+}
+
+smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                              uint32_t replica, uint64_t sweep, int32_t k, double kT, float *dE, uint8_t *acc,
+                              cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = check_sweep_args(lat, model, occ, 1, &kT, 1, sweep);
+    if (st != SMC_OK) return st;
+    const int nA = 2 * lc_edge(lat->nx) * lc_edge(lat->ny) * lc_edge(lat->nz);
+    if (k < 0 || k >= nA) {
+        set_error("mini-step %d out of range [0, %d)", k, nA);
+        return SMC_ERR_ARG;
+    }
+    if (is_mlp(model)) {
+        set_error("MLP traces are not available in this build");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
+}
+
+smc_status smc_sro(const smc_lattice *lat, int32_t nshells, const int8_t *occ, int64_t *counts, double *alpha,
+                   cudaStream_t stream)
+{
+    API_LOCK;
+    if (!lattice_valid(lat, false)) return SMC_ERR_ARG;
+    if (nshells < 1 || nshells > kMaxShells || !occ) {
+        set_error("nshells must be in [1, 3] and occ non-NULL");
+        return SMC_ERR_ARG;
+    }
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    unsigned long long *cnt = (unsigned long long *)counts;
+    if (!cnt) {
+        cnt = (unsigned long long *)workspace_scratch(ws, sizeof(unsigned long long) * kMaxShells * 64, &st);
+        if (!cnt) return st;
+    }
+    st = launch_pair_counts(lat, nshells, occ, cnt, stream);
+    if (st != SMC_OK || !alpha) return st;
+    return launch_sro_finish(lat, nshells, cnt, alpha, stream);
+}
+
+smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ, double *e, int64_t *e_int,
+                      cudaStream_t stream)
+{
+    API_LOCK;
+    if (!lattice_valid(lat, model && is_mlp(model)) || !model_valid(lat, model)) return SMC_ERR_ARG;
+    if (!occ) {
+        set_error("occ is NULL");
+        return SMC_ERR_ARG;
+    }
+    if (e_int && model->kind != SMC_PAIR_I32) {
+        set_error("e_int is only defined for integer models");
+        return SMC_ERR_ARG;
+    }
+    if (is_mlp(model)) {
+        set_error("MLP energies are not available in this build");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    unsigned long long *cnt =
+        (unsigned long long *)workspace_scratch(ws, sizeof(unsigned long long) * kMaxShells * 64, &st);
+    if (!cnt) return st;
+    st = launch_pair_counts(lat, model->nshells, occ, cnt, stream);
+    if (st != SMC_OK) return st;
+    return launch_energy_finish(lat, model, cnt, e, e_int, stream);
+}
+
+int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model)
+{
+    if (!lat || !model || lat->nspecies < 1) return -1;
+    const int S = lat->nspecies;
+    int64_t n = 0;
+    if (has_pair(model)) n += (int64_t)model->nshells * S * (S + 1) / 2;
+    if (is_mlp(model)) n += 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1;
+    return n;
+}
+
+smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const int8_t *occ, float *grad,
+                           cudaStream_t stream)
+{
+    API_LOCK;
+    if (!lattice_valid(lat, model && is_mlp(model)) || !model_valid(lat, model)) return SMC_ERR_ARG;
+    if (!occ || !grad) {
+        set_error("occ and grad must be non-NULL");
+        return SMC_ERR_ARG;
+    }
+    if (is_mlp(model)) {
+        set_error("MLP gradients are not available in this build");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    unsigned long long *cnt =
+        (unsigned long long *)workspace_scratch(ws, sizeof(unsigned long long) * kMaxShells * 64, &st);
+    if (!cnt) return st;
+    st = launch_pair_counts(lat, model->nshells, occ, cnt, stream);
+    if (st != SMC_OK) return st;
+    return launch_pair_grad_finish(lat, model, cnt, grad, stream);
+}
+
+smc_status smc_philox4x32_10(const uint32_t *ctr, const uint32_t *key, uint32_t *out, int64_t n, cudaStream_t stream)
+{
+    API_LOCK;
+    if (n < 0 || (n > 0 && (!ctr || !key || !out))) {
+        set_error("invalid philox arguments");
+        return SMC_ERR_ARG;
+    }
+    return launch_philox(ctr, key, out, n, stream);
+}
+
+}  // extern "C"

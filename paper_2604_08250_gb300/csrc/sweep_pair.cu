@@ -1,0 +1,920 @@
+// sweep_pair.cu -- persistent swap-MC sweep kernel for pair models.
+//
+// Algorithm 1 of the paper runs n_A sequential mini-steps per sweep; in each,
+// every link cell (LC) tries to swap its site at the mini-step's offset with
+// a random nearest neighbour, all LCs in parallel (Sec. II-A, III-A).
+//
+// GPU organisation.  With mini-step k = ((sub*Lz + dz)*Ly + dy)*Lx + dx, the
+// Lx consecutive mini-steps that share (sub, dy, dz) form a "group".  Within a
+// group, the trials of one x-row of LCs (a "column", fixed (cy, cz)) read and
+// write only that row's neighbourhood: rows y0-2..y0+2, z0-2..z0+2 of the two
+// sublattices, where y0 = cy*Ly + dy, z0 = cz*Lz + dz.  Distinct columns of a
+// group touch disjoint rows, so a column's Lx mini-steps run inside one CTA
+// in lock-step with only CTA-level barriers, on a copy of those rows in
+// shared memory.  Columns are grouped into rectangular tiles; a tile may start
+// group G only after its 8 neighbouring tiles have finished group G-1
+// (per-tile progress flags in global memory, bounded waits).  Trials in the
+// same mini-step are independent, and a column's dependencies reach only the
+// adjacent columns, so this reproduces the sequential mini-step order exactly.
+//
+// dE of a trial (a -> b) is the pair-model energy change written through the
+// first-neighbour histograms: with D_m[q] = V_m(s_b, q) - V_m(s_a, q),
+//   dE = sum_m [ sum_{j in N_m(a)\b} D_m[s_j] - sum_{j in N_m(b)\a} D_m[s_j] ],
+// which equals the Omega-reduced local-energy difference of Algorithm 1
+// lines 4-8 for pair site energies e_i = 1/2 sum_v V(s_i, s_{i+v}).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <vector>
+
+#include "smc_common.cuh"
+
+namespace smc {
+
+constexpr int kMaxBeta = 1024;
+
+struct RepDesc {
+    int8_t *occ;
+    double *e_acc;
+    long long *n_acc;
+    int nx, ny, nz;
+    int NLx, NLy, NLz;
+    int NTy, NTz;  // tiles along y, z
+    int tile0;     // first global tile of this replica
+    uint32_t rep;  // RNG replica index
+    int vec;       // rows are 16-byte aligned: copy with 16-byte transactions
+};
+
+struct SweepParams {
+    int R, ntiles, G;
+    int Lx, Ly, Lz;
+    int TY, TZ, CB;
+    int nshells, S;
+    int nsweeps;
+    int beta_stride;  // 0: one value per replica; else values per (replica, sweep)
+    int tpc;          // accumulator slots per CTA (>= tiles owned by any CTA)
+    int skip_tile;
+    int pad0;
+    uint64_t seed, sweep0;
+    long long timeout_ns;
+    uint32_t *flags;
+    double *part_e;
+    long long *part_n;
+    unsigned *ticket;
+    int *abort_flag;
+    int *status;
+    const uint32_t *tab;  // integer acceptance tables
+    union {
+        float beta[kMaxBeta];
+        int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
+    } temp;
+    union {
+        int di[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
+        float df[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
+    } D;  // D[m][A][B][q] = V_m(B, q) - V_m(A, q)
+    RepDesc rep[kMaxReplicas];
+};
+static_assert(sizeof(SweepParams) < 32000, "kernel parameter block too large");
+
+constexpr int kDEntries = kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies;
+
+// Slot of row y0 + delta inside a window [lo, lo + W) along an axis of n cells.
+// For n >= W the window rows are distinct and slot = delta - lo; otherwise the
+// window holds the whole axis and slot = (y0 + delta) mod n.
+struct Win {
+    int big;   // n >= W
+    int cnt;   // rows held
+    int base;  // global row of slot 0
+    int lo, y0, n;
+    __device__ __forceinline__ int slot(int delta) const
+    {
+        if (big) return delta - lo;
+        int v = (y0 + delta) % n;
+        return v < 0 ? v + n : v;
+    }
+    __device__ __forceinline__ int row(int k) const
+    {
+        int v = (base + k) % n;
+        return v < 0 ? v + n : v;
+    }
+};
+
+__device__ __forceinline__ Win make_win(int n, int W, int lo, int y0)
+{
+    Win w;
+    w.n = n;
+    w.lo = lo;
+    w.y0 = y0;
+    w.big = n >= W;
+    w.cnt = w.big ? W : n;
+    w.base = w.big ? (y0 + lo) : 0;
+    return w;
+}
+
+// Rows of one column held in shared memory: the trial sublattice ("own",
+// window [-1, 1] per axis) and the partner sublattice ("oth", window
+// [s_off-1, s_off+2], s_off = -1 for sub 0 and 0 for sub 1).
+struct ColView {
+    unsigned char *own, *oth;
+    Win oy, oz, ty, tz;
+    int rowB;
+    __device__ __forceinline__ unsigned char *O(int dy, int dz) const
+    {
+        return own + (oz.slot(dz) * oy.cnt + oy.slot(dy)) * rowB;
+    }
+    __device__ __forceinline__ unsigned char *T(int dy, int dz) const
+    {
+        return oth + (tz.slot(dz) * ty.cnt + ty.slot(dy)) * rowB;
+    }
+};
+
+template <bool IS_INT>
+struct Acc;
+template <>
+struct Acc<true> {
+    using T = int;
+};
+template <>
+struct Acc<false> {
+    using T = float;
+};
+
+// dE of swapping the trial site a (own sublattice, x) with its partner in
+// direction `dir` (bits kx, ky, kz -> vector 2k-1 in half units).
+// Returns the species A, B and the partner's coordinates through pointers.
+template <bool IS_INT, class View>
+__device__ __forceinline__ typename Acc<IS_INT>::T trial_dE(const View &cv, int x, int nx, int s_off,
+                                                            int dir, int nshells, int S, const void *Dtab,
+                                                            int &A, int &B, int &ex, int &ey, int &ez)
+{
+    using T = typename Acc<IS_INT>::T;
+    const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
+    ex = kx + s_off;
+    ey = ky + s_off;
+    ez = kz + s_off;
+    const int xm2 = wrapc(x - 2, nx), xm1 = wrapc(x - 1, nx), xp1 = wrapc(x + 1, nx), xp2 = wrapc(x + 2, nx);
+    auto xo = [&](int d) { return d == -2 ? xm2 : (d == -1 ? xm1 : (d == 0 ? x : (d == 1 ? xp1 : xp2))); };
+    A = cv.O(0, 0)[x] & 7;
+    const int bx = xo(ex);
+    B = cv.T(ey, ez)[bx] & 7;
+    if (A == B) return T(0);
+    const T *D = (const T *)Dtab;
+    const T *D1 = D + ((0 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+    T dE = T(0);
+    // shell 1 of a (partner sublattice), all but b
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (u == dir) continue;
+        const int fx = ((u >> 2) & 1) + s_off, fy = ((u >> 1) & 1) + s_off, fz = (u & 1) + s_off;
+        dE += D1[cv.T(fy, fz)[xo(fx)] & 7];
+    }
+    // shell 1 of b (trial sublattice), all but a
+    const int sb = -1 - s_off;
+    const int nd = 7 - dir;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+        if (u == nd) continue;
+        const int gx = ex + ((u >> 2) & 1) + sb, gy = ey + ((u >> 1) & 1) + sb, gz = ez + (u & 1) + sb;
+        dE -= D1[cv.O(gy, gz)[xo(gx)] & 7];
+    }
+    if (nshells >= 2) {
+        const T *D2 = D + ((1 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+        const unsigned char *o00 = cv.O(0, 0);
+        dE += D2[o00[xm1] & 7] + D2[o00[xp1] & 7] + D2[cv.O(-1, 0)[x] & 7] + D2[cv.O(1, 0)[x] & 7] +
+              D2[cv.O(0, -1)[x] & 7] + D2[cv.O(0, 1)[x] & 7];
+        const unsigned char *tb = cv.T(ey, ez);
+        dE -= D2[tb[xo(ex - 1)] & 7] + D2[tb[xo(ex + 1)] & 7] + D2[cv.T(ey - 1, ez)[bx] & 7] +
+              D2[cv.T(ey + 1, ez)[bx] & 7] + D2[cv.T(ey, ez - 1)[bx] & 7] + D2[cv.T(ey, ez + 1)[bx] & 7];
+    }
+    if (nshells >= 3) {
+        const T *D3 = D + ((2 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+#pragma unroll
+        for (int p = -1; p <= 1; p += 2)
+#pragma unroll
+            for (int q = -1; q <= 1; q += 2) {
+                dE += D3[cv.O(p, q)[x] & 7];           // (0, +-1, +-1)
+                dE += D3[cv.O(p, 0)[xo(q)] & 7];       // (+-1, +-1, 0)
+                dE += D3[cv.O(0, p)[xo(q)] & 7];       // (+-1, 0, +-1)
+                dE -= D3[cv.T(ey + p, ez + q)[bx] & 7];
+                dE -= D3[cv.T(ey + p, ez)[xo(ex + q)] & 7];
+                dE -= D3[cv.T(ey, ez + p)[xo(ex + q)] & 7];
+            }
+    }
+    return dE;
+}
+
+template <bool IS_INT>
+__device__ __forceinline__ bool metropolis(typename Acc<IS_INT>::T dE, uint32_t r, float beta, const uint32_t *tab,
+                                           int2 ti)
+{
+    if (dE <= 0) return true;
+    if constexpr (IS_INT) {
+        return (int)dE < ti.y && r < __ldg(tab + ti.x + (int)dE);
+    } else {
+        const float u = ((float)r + 0.5f) * 1.862645149230957e-09f;  // 2^-29
+        return u < expf(-beta * (float)dE);
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Waits until the 8 neighbouring tiles of (ty, tz) have completed `need`
+// groups.  Bounded: on timeout the status word and the abort flag are set.
+__device__ bool wait_tile(const SweepParams &P, const RepDesc &D, int ty, int tz, uint32_t need, int *s_stop)
+{
+    if (threadIdx.x < 32) {
+        const int k = threadIdx.x;
+        const uint32_t *fp = nullptr;
+        if (k < 9 && k != 4) {
+            int nty = ty + (k % 3) - 1, ntz = tz + (k / 3) - 1;
+            nty = nty < 0 ? nty + D.NTy : (nty >= D.NTy ? nty - D.NTy : nty);
+            ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
+            fp = P.flags + D.tile0 + ntz * D.NTy + nty;
+        }
+        const uint64_t t0 = global_ns();
+        int stop = 0;
+        for (;;) {
+            const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
+            if (__all_sync(0xffffffffu, ok)) break;
+            if (k == 0) {
+                if (ld_volatile_i32(P.abort_flag)) {
+                    stop = 1;
+                } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
+                    atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+                    atomicExch(P.abort_flag, 1);
+                    stop = 1;
+                }
+            }
+            stop = __shfl_sync(0xffffffffu, stop, 0);
+            if (stop) break;
+            __nanosleep(40);
+        }
+        if (k == 0) *s_stop = stop;
+    }
+    __syncthreads();
+    return *s_stop == 0;
+}
+
+template <bool IS_INT>
+__global__ void __launch_bounds__(1024) k_sweep_pair(const __grid_constant__ SweepParams P)
+{
+    using T = typename Acc<IS_INT>::T;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ int s_stop;
+    __shared__ int s_last;
+    const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
+
+    T *Dt = (T *)smem;
+    double *slot_e = (double *)(smem + kDEntries * 4);
+    long long *slot_n = (long long *)(slot_e + P.tpc * nwarp);
+    unsigned char *colbuf = (unsigned char *)(slot_n + P.tpc * nwarp);
+
+    for (int i = tid; i < kDEntries; i += nthr) {
+        if constexpr (IS_INT)
+            Dt[i] = P.D.di[i];
+        else
+            Dt[i] = P.D.df[i];
+    }
+    for (int i = tid; i < P.tpc * nwarp; i += nthr) {
+        slot_e[i] = 0.0;
+        slot_n[i] = 0;
+    }
+    if (tid == 0) s_stop = 0;
+    __syncthreads();
+
+    bool aborted = false;
+    for (int t = 0; t < P.nsweeps && !aborted; ++t) {
+        const uint64_t sweep = P.sweep0 + (uint64_t)t;
+        for (int g = 0; g < P.G && !aborted; ++g) {
+            const uint32_t gstep = (uint32_t)(t * P.G + g);
+            const int dy = g % P.Ly, dz = (g / P.Ly) % P.Lz, sub = g / (P.Ly * P.Lz);
+            const int s_off = sub == 0 ? -1 : 0;
+            int slotk = 0;
+            for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++slotk) {
+                int r = 0;
+                while (r + 1 < P.R && P.rep[r + 1].tile0 <= tile) ++r;
+                const RepDesc &RD = P.rep[r];
+                const int lt = tile - RD.tile0, ty = lt % RD.NTy, tz = lt / RD.NTy;
+                if (!wait_tile(P, RD, ty, tz, gstep, &s_stop)) {
+                    aborted = true;
+                    break;
+                }
+                float beta = 0.f;
+                int2 ti = make_int2(0, 0);
+                if constexpr (IS_INT)
+                    ti = P.temp.tabinfo[P.beta_stride ? r * P.beta_stride + t : r];
+                else
+                    beta = P.temp.beta[P.beta_stride ? r * P.beta_stride + t : r];
+
+                const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
+                const int rowB = (nx + 15) & ~15;
+                const int j0 = ty * P.TY, j1 = min(j0 + P.TY, RD.NLy);
+                const int l0 = tz * P.TZ, l1 = min(l0 + P.TZ, RD.NLz);
+                const int nj = j1 - j0, ncols = nj * (l1 - l0);
+                // window shapes are the same for every column of the tile
+                const Win oy0 = make_win(ny, 3, -1, dy), oz0 = make_win(nz, 3, -1, dz);
+                const Win ty0 = make_win(ny, 4, s_off - 1, dy), tz0 = make_win(nz, 4, s_off - 1, dz);
+                const int rows_own = oy0.cnt * oz0.cnt, rows_oth = ty0.cnt * tz0.cnt;
+                const int rows_col = rows_own + rows_oth;
+                const int col_bytes = rows_col * rowB;
+                T accE = T(0);
+                double accE_d = 0.0;
+                long long accN = 0;
+
+                for (int cb = 0; cb < ncols; cb += P.CB) {
+                    const int nc = min(P.CB, ncols - cb);
+                    // ---- stage the rows of nc columns into shared memory ----
+                    const int chunks_row = rowB >> 4;
+                    const bool vec = RD.vec != 0;
+                    const int total = vec ? nc * rows_col * chunks_row : nc * rows_col * nx;
+                    for (int q = tid; q < total; q += nthr) {
+                        int c, rw, off;
+                        if (vec) {
+                            c = q / (rows_col * chunks_row);
+                            int rem = q - c * rows_col * chunks_row;
+                            rw = rem / chunks_row;
+                            off = (rem - rw * chunks_row) << 4;
+                        } else {
+                            c = q / (rows_col * nx);
+                            int rem = q - c * rows_col * nx;
+                            rw = rem / nx;
+                            off = rem - rw * nx;
+                        }
+                        const int cc = cb + c, j = j0 + cc % nj, l = l0 + cc / nj;
+                        const int y0 = j * P.Ly + dy, z0 = l * P.Lz + dz;
+                        int gsub, gy, gz;
+                        if (rw < rows_own) {
+                            const Win wy = make_win(ny, 3, -1, y0), wz = make_win(nz, 3, -1, z0);
+                            gsub = sub;
+                            gy = wy.row(rw % wy.cnt);
+                            gz = wz.row(rw / wy.cnt);
+                        } else {
+                            const int k2 = rw - rows_own;
+                            const Win wy = make_win(ny, 4, s_off - 1, y0), wz = make_win(nz, 4, s_off - 1, z0);
+                            gsub = 1 - sub;
+                            gy = wy.row(k2 % wy.cnt);
+                            gz = wz.row(k2 / wy.cnt);
+                        }
+                        const int8_t *src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx + off;
+                        unsigned char *dst = colbuf + (size_t)c * col_bytes + rw * rowB + off;
+                        if (vec) {
+                            const unsigned saddr = (unsigned)__cvta_generic_to_shared(dst);
+                            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(src)
+                                         : "memory");
+                        } else {
+                            *dst = (unsigned char)__ldcg(src);
+                        }
+                    }
+                    asm volatile("cp.async.wait_all;" ::: "memory");
+                    __syncthreads();
+
+                    // ---- the Lx mini-steps of this group, in lock-step ----
+                    const int items = nc * NLx;
+                    for (int dx = 0; dx < P.Lx; ++dx) {
+                        for (int it = tid; it < items; it += nthr) {
+                            const int c = it / NLx, i = it - c * NLx;
+                            const int cc = cb + c, j = j0 + cc % nj, l = l0 + cc / nj;
+                            const int y0 = j * P.Ly + dy, z0 = l * P.Lz + dz;
+                            ColView cv;
+                            cv.own = colbuf + (size_t)c * col_bytes;
+                            cv.oth = cv.own + rows_own * rowB;
+                            cv.rowB = rowB;
+                            cv.oy = make_win(ny, 3, -1, y0);
+                            cv.oz = make_win(nz, 3, -1, z0);
+                            cv.ty = make_win(ny, 4, s_off - 1, y0);
+                            cv.tz = make_win(nz, 4, s_off - 1, z0);
+                            const int x = i * P.Lx + dx;
+                            const uint32_t s = (uint32_t)(((sub * nz + z0) * ny + y0) * nx + x);
+                            const uint32_t w = site_word(P.seed, RD.rep, sweep, s);
+                            int A, B, ex, ey, ez;
+                            const T dE = trial_dE<IS_INT, ColView>(cv, x, nx, s_off, (int)(w >> kRBits),
+                                                                   P.nshells, P.S, Dt, A, B, ex, ey, ez);
+                            if (metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti)) {
+                                if (A != B) {
+                                    cv.O(0, 0)[x] = (unsigned char)B;
+                                    cv.T(ey, ez)[wrapc(x + ex, nx)] = (unsigned char)A;
+                                }
+                                if constexpr (IS_INT)
+                                    accE += dE;
+                                else
+                                    accE_d += (double)dE;
+                                accN += 1;
+                            }
+                        }
+                        __syncthreads();
+                    }
+
+                    // ---- write back the rows this group may have changed ----
+                    // trial row (0, 0) and partner rows (s_off .. s_off+1)^2
+                    for (int q = tid; q < nc * 5 * chunks_row * (vec ? 1 : 16); q += nthr) {
+                        int c, wr, off;
+                        if (vec) {
+                            c = q / (5 * chunks_row);
+                            int rem = q - c * 5 * chunks_row;
+                            wr = rem / chunks_row;
+                            off = (rem - wr * chunks_row) << 4;
+                        } else {
+                            c = q / (5 * chunks_row * 16);
+                            int rem = q - c * 5 * chunks_row * 16;
+                            wr = rem / (chunks_row * 16);
+                            off = rem - wr * chunks_row * 16;
+                            if (off >= nx) continue;
+                        }
+                        const int cc = cb + c, j = j0 + cc % nj, l = l0 + cc / nj;
+                        const int y0 = j * P.Ly + dy, z0 = l * P.Lz + dz;
+                        int gsub, gy, gz, srow;
+                        if (wr == 0) {
+                            const Win wy = make_win(ny, 3, -1, y0), wz = make_win(nz, 3, -1, z0);
+                            gsub = sub;
+                            gy = y0;
+                            gz = z0;
+                            srow = wz.slot(0) * wy.cnt + wy.slot(0);
+                        } else {
+                            const int ddy = s_off + ((wr - 1) & 1), ddz = s_off + ((wr - 1) >> 1);
+                            const Win wy = make_win(ny, 4, s_off - 1, y0), wz = make_win(nz, 4, s_off - 1, z0);
+                            gsub = 1 - sub;
+                            gy = wrapc(y0 + ddy, ny);
+                            gz = wrapc(z0 + ddz, nz);
+                            srow = rows_own + wz.slot(ddz) * wy.cnt + wy.slot(ddy);
+                        }
+                        int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx + off;
+                        const unsigned char *srcs = colbuf + (size_t)c * col_bytes + srow * rowB + off;
+                        if (vec)
+                            *(int4 *)dstg = *(const int4 *)srcs;
+                        else
+                            *dstg = (int8_t)*srcs;
+                    }
+                    __syncthreads();
+                }
+
+                // ---- per-tile accumulation (fixed order) and publication ----
+                double e_w;
+                if constexpr (IS_INT)
+                    e_w = (double)warp_sum<long long>((long long)accE);
+                else
+                    e_w = warp_sum<double>(accE_d);
+                const long long n_w = warp_sum<long long>(accN);
+                if (lane == 0) {
+                    slot_e[slotk * nwarp + warp] += e_w;
+                    slot_n[slotk * nwarp + warp] += n_w;
+                }
+                __syncthreads();
+                if (tid == 0 && tile != P.skip_tile) {
+                    __threadfence();
+                    st_release_u32(P.flags + tile, gstep + 1);
+                }
+            }
+        }
+    }
+
+    // ---- per-tile partial sums, then the last CTA reduces them in order ----
+    __syncthreads();
+    if (s_stop) return;
+    {
+        int k = 0;
+        for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++k) {
+            if (tid == 0) {
+                double se = 0.0;
+                long long sn = 0;
+                for (int w = 0; w < nwarp; ++w) {
+                    se += slot_e[k * nwarp + w];
+                    sn += slot_n[k * nwarp + w];
+                }
+                P.part_e[tile] = se;
+                P.part_n[tile] = sn;
+            }
+        }
+    }
+    if (tid == 0) {
+        __threadfence();
+        const unsigned prev = atomicAdd(P.ticket, 1u);
+        s_last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int r = tid; r < P.R; r += nthr) {
+        const RepDesc &RD = P.rep[r];
+        double se = 0.0;
+        long long sn = 0;
+        const int nt = RD.NTy * RD.NTz;
+        for (int k = 0; k < nt; ++k) {
+            se += __ldcg(P.part_e + RD.tile0 + k);
+            sn += __ldcg(P.part_n + RD.tile0 + k);
+        }
+        if (RD.e_acc) *RD.e_acc += se;
+        if (RD.n_acc) *RD.n_acc += sn;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Lock-step trace of one mini-step: one thread per trial, reading rows
+// straight from global memory through the same dE arithmetic.  Phase 1
+// evaluates every trial (read-only), phase 2 applies the accepted swaps.
+// ---------------------------------------------------------------------------
+struct GView {
+    const unsigned char *occ;
+    int nx, ny, nz, sub, y0, z0;
+    __device__ __forceinline__ const unsigned char *O(int dy, int dz) const
+    {
+        return occ + ((size_t)((sub * nz + wrapc(z0 + dz, nz)) * ny + wrapc(y0 + dy, ny))) * nx;
+    }
+    __device__ __forceinline__ const unsigned char *T(int dy, int dz) const
+    {
+        return occ + ((size_t)(((1 - sub) * nz + wrapc(z0 + dz, nz)) * ny + wrapc(y0 + dy, ny))) * nx;
+    }
+};
+
+template <bool IS_INT>
+__global__ void k_ministep_eval(const __grid_constant__ SweepParams P, int k, float *dE_out, uint8_t *acc_out,
+                                int *swap_a, int *swap_b)
+{
+    using T = typename Acc<IS_INT>::T;
+    __shared__ T Dt[kDEntries];
+    for (int i = threadIdx.x; i < kDEntries; i += blockDim.x) {
+        if constexpr (IS_INT)
+            Dt[i] = P.D.di[i];
+        else
+            Dt[i] = P.D.df[i];
+    }
+    __syncthreads();
+    const RepDesc &RD = P.rep[0];
+    const int ntr = RD.NLx * RD.NLy * RD.NLz;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ntr) return;
+    const int dx = k % P.Lx, dy = (k / P.Lx) % P.Ly, dz = (k / (P.Lx * P.Ly)) % P.Lz;
+    const int sub = k / (P.Lx * P.Ly * P.Lz);
+    const int s_off = sub == 0 ? -1 : 0;
+    const int cx = c % RD.NLx, cy = (c / RD.NLx) % RD.NLy, cz = c / (RD.NLx * RD.NLy);
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz;
+    const int x = cx * P.Lx + dx, y0 = cy * P.Ly + dy, z0 = cz * P.Lz + dz;
+    const GView gv{(const unsigned char *)RD.occ, nx, ny, nz, sub, y0, z0};
+    const uint32_t s = (uint32_t)(((sub * nz + z0) * ny + y0) * nx + x);
+    const uint32_t w = site_word(P.seed, RD.rep, P.sweep0, s);
+    int A, B, ex, ey, ez;
+    const T dE = trial_dE<IS_INT, GView>(gv, x, nx, s_off, (int)(w >> kRBits), P.nshells, P.S, Dt, A, B, ex, ey, ez);
+    float beta = 0.f;
+    int2 ti = make_int2(0, 0);
+    if constexpr (IS_INT)
+        ti = P.temp.tabinfo[0];
+    else
+        beta = P.temp.beta[0];
+    const bool acc = metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti);
+    if (dE_out) dE_out[c] = (float)dE;
+    if (acc_out) acc_out[c] = acc ? 1 : 0;
+    const int by = wrapc(y0 + ey, ny), bz = wrapc(z0 + ez, nz), bx = wrapc(x + ex, nx);
+    swap_a[c] = (acc && A != B) ? (int)s : -1;
+    swap_b[c] = ((1 - sub) * nz + bz) * ny * nx + by * nx + bx;
+}
+
+__global__ void k_ministep_apply(int8_t *occ, int ntr, const int *swap_a, const int *swap_b)
+{
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= ntr) return;
+    const int a = swap_a[c];
+    if (a < 0) return;
+    const int b = swap_b[c];
+    const int8_t t = occ[a];
+    occ[a] = occ[b];
+    occ[b] = t;
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct Plan {
+    int Lx, Ly, Lz, G;
+    int threads, CB, TY, TZ, ntiles, grid, tpc;
+    size_t smem;
+};
+
+int col_bytes_of(const smc_lattice &l)
+{
+    const int rowB = (l.nx + 15) & ~15;
+    const int oy = l.ny >= 3 ? 3 : l.ny, oz = l.nz >= 3 ? 3 : l.nz;
+    const int ty = l.ny >= 4 ? 4 : l.ny, tz = l.nz >= 4 ? 4 : l.nz;
+    return (oy * oz + ty * tz) * rowB;
+}
+
+template <bool IS_INT>
+smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
+{
+    const Tuning tu = current_tuning();
+    pl.Lx = lc_edge(lats[0].nx);
+    pl.Ly = lc_edge(lats[0].ny);
+    pl.Lz = lc_edge(lats[0].nz);
+    pl.G = 2 * pl.Ly * pl.Lz;
+    int maxNLx = 1, maxcol = 0;
+    for (int r = 0; r < R; ++r) {
+        maxNLx = std::max(maxNLx, lats[r].nx / pl.Lx);
+        maxcol = std::max(maxcol, col_bytes_of(lats[r]));
+    }
+    pl.threads = tu.threads ? tu.threads : (maxNLx <= 128 ? 128 : 256);
+    if (pl.threads % 32 || pl.threads < 32 || pl.threads > 1024) {
+        set_error("tuning.threads must be a multiple of 32 in [32, 1024]");
+        return SMC_ERR_ARG;
+    }
+    pl.CB = std::max(1, pl.threads / maxNLx);
+    pl.TY = tu.tile_y;
+    pl.TZ = tu.tile_z;
+    if (pl.TY <= 0) pl.TY = pl.CB;
+    if (pl.TZ <= 0) pl.TZ = std::max(1, pl.CB / pl.TY);
+    pl.ntiles = 0;
+    for (int r = 0; r < R; ++r) {
+        const int NLy = lats[r].ny / pl.Ly, NLz = lats[r].nz / pl.Lz;
+        pl.ntiles += ((NLy + pl.TY - 1) / pl.TY) * ((NLz + pl.TZ - 1) / pl.TZ);
+    }
+    pl.CB = std::min(pl.CB, pl.TY * pl.TZ);
+    const int nwarps = pl.threads / 32;
+    const size_t base = (size_t)kDEntries * 4;
+    auto smem_for = [&](int cb, int tpc) { return base + (size_t)tpc * nwarps * 16 + (size_t)cb * maxcol; };
+    while (pl.CB > 1 && smem_for(pl.CB, 64) > ws->smem_optin) pl.CB /= 2;
+    if (smem_for(pl.CB, 1) > ws->smem_optin) {
+        set_error("lattice rows too long for shared memory (nx = %d)", lats[0].nx);
+        return SMC_ERR_UNSUPPORTED;
+    }
+    auto kern = k_sweep_pair<IS_INT>;
+    size_t smem = smem_for(pl.CB, 64);
+    if (smem > ws->smem_optin) smem = ws->smem_optin;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws->smem_optin);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    // resident CTAs with the accumulator slots sized for the worst case
+    int per_sm = 0;
+    for (int tpc_guess = 1;; tpc_guess *= 2) {
+        smem = smem_for(pl.CB, tpc_guess);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, pl.threads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (per_sm < 1) {
+            set_error("sweep kernel does not fit on an SM (threads %d, smem %zu)", pl.threads, smem);
+            return SMC_ERR_UNSUPPORTED;
+        }
+        if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+        pl.grid = std::min(pl.ntiles, per_sm * ws->num_sms);
+        pl.tpc = (pl.ntiles + pl.grid - 1) / pl.grid;
+        if (pl.tpc <= tpc_guess) break;
+        if (tpc_guess > 4096) {
+            set_error("too many tiles per CTA");
+            return SMC_ERR_UNSUPPORTED;
+        }
+    }
+    pl.smem = smem;
+    return SMC_OK;
+}
+
+// Integer acceptance table T[d] = floor(2^29 exp(-d unit / kT)) for d = 0 ..
+// len-1 (T[len] = 0), in FP64 on the host.
+std::vector<uint32_t> int_table(double unit_ev, double kT)
+{
+    std::vector<uint32_t> t;
+    for (int64_t d = 0;; ++d) {
+        const double v = floor(536870912.0 * exp(-(double)d * unit_ev / kT));
+        if (v <= 0.0 || d > (1 << 24)) break;
+        t.push_back((uint32_t)v);
+    }
+    return t;
+}
+
+}  // namespace
+
+template <bool IS_INT>
+static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,
+                             uint32_t replica0, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                             int64_t *n_acc, cudaStream_t stream)
+{
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    Plan pl;
+    st = make_plan<IS_INT>(R, lats, ws, pl);
+    if (st != SMC_OK) return st;
+
+    static SweepParams P;  // large: keep off the stack (host-only, guarded by the API lock)
+    memset(&P, 0, sizeof P);
+    P.R = R;
+    P.G = pl.G;
+    P.Lx = pl.Lx;
+    P.Ly = pl.Ly;
+    P.Lz = pl.Lz;
+    P.TY = pl.TY;
+    P.TZ = pl.TZ;
+    P.CB = pl.CB;
+    P.nshells = m->nshells;
+    P.S = lats[0].nspecies;
+    P.tpc = pl.tpc;
+    P.skip_tile = (int)debug_skip_tile();
+    P.seed = seed;
+    P.timeout_ns = debug_timeout_ns();
+    int tile0 = 0;
+    for (int r = 0; r < R; ++r) {
+        RepDesc &d = P.rep[r];
+        d.occ = occ[r];
+        d.e_acc = e_acc ? e_acc + r : nullptr;
+        d.n_acc = n_acc ? (long long *)n_acc + r : nullptr;
+        d.nx = lats[r].nx;
+        d.ny = lats[r].ny;
+        d.nz = lats[r].nz;
+        d.NLx = d.nx / pl.Lx;
+        d.NLy = d.ny / pl.Ly;
+        d.NLz = d.nz / pl.Lz;
+        d.NTy = (d.NLy + pl.TY - 1) / pl.TY;  // a tile wider than the grid is clipped
+        d.NTz = (d.NLz + pl.TZ - 1) / pl.TZ;
+        d.tile0 = tile0;
+        d.rep = replica0 + (uint32_t)r;
+        d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ[r] % 16 == 0);
+        tile0 += d.NTy * d.NTz;
+    }
+    P.CB = std::min(P.CB, P.TY * P.TZ);
+    P.ntiles = tile0;
+
+    // D[m][A][B][q] = V_m(B, q) - V_m(A, q), padded to 8 species
+    const int S = P.S;
+    for (int mm = 0; mm < m->nshells; ++mm)
+        for (int A = 0; A < S; ++A)
+            for (int B = 0; B < S; ++B)
+                for (int q = 0; q < S; ++q) {
+                    const int idx = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q;
+                    if (IS_INT)
+                        P.D.di[idx] = m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
+                    else
+                        P.D.df[idx] = (float)((double)m->v_f32[(mm * S + B) * S + q] -
+                                              (double)m->v_f32[(mm * S + A) * S + q]);
+                }
+
+    // temperature schedule: constant per replica over the call, or per sweep
+    bool constant = true;
+    for (int r = 0; r < R && constant; ++r)
+        for (int t = 1; t < nsweeps; ++t)
+            if (kT[(size_t)r * nsweeps + t] != kT[(size_t)r * nsweeps]) {
+                constant = false;
+                break;
+            }
+    const int cap = IS_INT ? kMaxBeta / 2 : kMaxBeta;
+    const int chunk = constant ? nsweeps : std::max(1, cap / R);
+    if (!constant && R > cap) {
+        set_error("per-sweep temperatures for more than %d replicas", cap);
+        return SMC_ERR_UNSUPPORTED;
+    }
+
+    // integer path: one acceptance table per distinct kT
+    std::vector<uint32_t> tabs;
+    std::vector<std::pair<double, int2>> tindex;
+    auto table_of = [&](double kt) -> int2 {
+        for (auto &p : tindex)
+            if (p.first == kt) return p.second;
+        std::vector<uint32_t> t = int_table(m->unit_ev, kt);
+        int2 ti = make_int2((int)tabs.size(), (int)t.size());
+        tabs.insert(tabs.end(), t.begin(), t.end());
+        tindex.push_back({kt, ti});
+        return ti;
+    };
+    if (IS_INT) {
+        for (int r = 0; r < R; ++r)
+            for (int t = 0; t < nsweeps; ++t) table_of(kT[(size_t)r * nsweeps + t]);
+    }
+
+    // workspace: [flags | part_e | part_n | ticket, abort | tables]
+    const size_t nt = (size_t)P.ntiles;
+    const size_t off_flags = 0, off_pe = ((nt * 4 + 15) / 16) * 16, off_pn = off_pe + nt * 8;
+    const size_t off_misc = off_pn + nt * 8, off_tab = off_misc + 16;
+    const size_t need = off_tab + tabs.size() * 4;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, need, &st);
+    if (!scr) return st;
+    P.flags = (uint32_t *)(scr + off_flags);
+    P.part_e = (double *)(scr + off_pe);
+    P.part_n = (long long *)(scr + off_pn);
+    P.ticket = (unsigned *)(scr + off_misc);
+    P.abort_flag = (int *)(scr + off_misc + 4);
+    P.status = ws->status;
+    P.tab = (const uint32_t *)(scr + off_tab);
+    cudaError_t e;
+    if (!tabs.empty()) {
+        e = cudaMemcpyAsync(scr + off_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance tables)");
+    }
+
+    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+        const int nc = std::min(chunk, nsweeps - t0);
+        P.sweep0 = sweep0 + (uint64_t)t0;
+        P.nsweeps = nc;
+        P.beta_stride = constant ? 0 : nc;
+        for (int r = 0; r < R; ++r)
+            for (int t = 0; t < (constant ? 1 : nc); ++t) {
+                const double kt = kT[(size_t)r * nsweeps + t0 + t];
+                const int idx = constant ? r : r * nc + t;
+                if (IS_INT)
+                    P.temp.tabinfo[idx] = table_of(kt);
+                else
+                    P.temp.beta[idx] = (float)(1.0 / kt);
+            }
+        e = cudaMemsetAsync(scr, 0, off_tab, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
+        void *args[] = {(void *)&P};
+        e = cudaLaunchCooperativeKernel((const void *)k_sweep_pair<IS_INT>, dim3(pl.grid), dim3(pl.threads), args,
+                                        pl.smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(k_sweep_pair)");
+    }
+    return SMC_OK;
+}
+
+smc_status launch_pair_sweep(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,
+                             uint32_t replica0, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                             int64_t *n_acc, cudaStream_t stream)
+{
+    for (int r = 1; r < R; ++r) {
+        if (lc_edge(lats[r].nx) != lc_edge(lats[0].nx) || lc_edge(lats[r].ny) != lc_edge(lats[0].ny) ||
+            lc_edge(lats[r].nz) != lc_edge(lats[0].nz) || lats[r].nspecies != lats[0].nspecies) {
+            set_error("batched replicas must share link-cell edges and species count (replica %d)", r);
+            return SMC_ERR_UNSUPPORTED;
+        }
+    }
+    if (m->kind == SMC_PAIR_I32)
+        return sweep_impl<true>(R, lats, m, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+    return sweep_impl<false>(R, lats, m, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+}
+
+template <bool IS_INT>
+static smc_status trace_impl(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                             uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,
+                             cudaStream_t stream)
+{
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    static SweepParams P;
+    memset(&P, 0, sizeof P);
+    P.R = 1;
+    P.Lx = lc_edge(lat->nx);
+    P.Ly = lc_edge(lat->ny);
+    P.Lz = lc_edge(lat->nz);
+    P.nshells = m->nshells;
+    P.S = lat->nspecies;
+    P.seed = seed;
+    P.sweep0 = sweep;
+    RepDesc &d = P.rep[0];
+    d.occ = occ;
+    d.nx = lat->nx;
+    d.ny = lat->ny;
+    d.nz = lat->nz;
+    d.NLx = d.nx / P.Lx;
+    d.NLy = d.ny / P.Ly;
+    d.NLz = d.nz / P.Lz;
+    d.rep = replica;
+    const int S = P.S;
+    for (int mm = 0; mm < m->nshells; ++mm)
+        for (int A = 0; A < S; ++A)
+            for (int B = 0; B < S; ++B)
+                for (int q = 0; q < S; ++q) {
+                    const int idx = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q;
+                    if (IS_INT)
+                        P.D.di[idx] = m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
+                    else
+                        P.D.df[idx] = (float)((double)m->v_f32[(mm * S + B) * S + q] -
+                                              (double)m->v_f32[(mm * S + A) * S + q]);
+                }
+    const int ntr = d.NLx * d.NLy * d.NLz;
+    std::vector<uint32_t> tab;
+    if (IS_INT) {
+        tab = int_table(m->unit_ev, kT);
+        P.temp.tabinfo[0] = make_int2(0, (int)tab.size());
+    } else {
+        P.temp.beta[0] = (float)(1.0 / kT);
+    }
+    const size_t off_tab = ((size_t)ntr * 8 + 15) / 16 * 16;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_tab + tab.size() * 4 + 16, &st);
+    if (!scr) return st;
+    int *swap_a = (int *)scr, *swap_b = swap_a + ntr;
+    P.tab = (const uint32_t *)(scr + off_tab);
+    cudaError_t e;
+    if (!tab.empty()) {
+        e = cudaMemcpyAsync(scr + off_tab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance table)");
+    }
+    const int threads = 128, blocks = (ntr + threads - 1) / threads;
+    k_ministep_eval<IS_INT><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_ministep_eval");
+    k_ministep_apply<<<blocks, threads, 0, stream>>>(occ, ntr, swap_a, swap_b);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_ministep_apply");
+    return SMC_OK;
+}
+
+smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                                 uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,
+                                 cudaStream_t stream)
+{
+    if (m->kind == SMC_PAIR_I32)
+        return trace_impl<true>(lat, m, occ, seed, replica, sweep, k, kT, dE, acc, stream);
+    return trace_impl<false>(lat, m, occ, seed, replica, sweep, k, kT, dE, acc, stream);
+}
+
+}  // namespace smc

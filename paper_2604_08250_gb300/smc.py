@@ -1,0 +1,226 @@
+"""Python binding of libsmc.so (ctypes).  Argument marshalling only: every step
+of the Monte Carlo path runs in the library's CUDA kernels.  Device buffers are
+torch tensors; work is enqueued on torch's current CUDA stream.
+
+The library must have been built (``paper_2604_08250_gb300.build.build()``);
+loading fails loudly otherwise -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libsmc.so")
+
+SMC_OK, SMC_ERR_ARG, SMC_ERR_UNSUPPORTED, SMC_ERR_CUDA, SMC_ERR_TIMEOUT, SMC_ERR_STATE = 0, -1, -2, -3, -4, -5
+PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16 = 0, 1, 2, 3
+DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH = 1, 2
+MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
+
+# Every symbol declared in include/smc.h.
+EXPORTS = ("smc_init_lattice", "smc_sweep", "smc_sweep_batched", "smc_sro", "smc_energy", "smc_grad_size",
+           "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check", "smc_last_error",
+           "smc_set_tuning", "smc_debug_set")
+
+
+class SMCError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"smc error {code}: {msg}")
+        self.code = code
+
+
+class _Lat(C.Structure):
+    _fields_ = [("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nspecies", C.c_int32)]
+
+
+class _Model(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nshells", C.c_int32),
+                ("v_i32", C.POINTER(C.c_int32)), ("v_f32", C.POINTER(C.c_float)),
+                ("unit_ev", C.c_double),
+                ("mlp_w1", C.POINTER(C.c_uint16)), ("mlp_w2", C.POINTER(C.c_uint16)),
+                ("mlp_w3", C.POINTER(C.c_uint16)),
+                ("mlp_b1", C.POINTER(C.c_float)), ("mlp_b2", C.POINTER(C.c_float)),
+                ("mlp_b3", C.c_float)]
+
+
+class _Tuning(C.Structure):
+    _fields_ = [("tile_y", C.c_int32), ("tile_z", C.c_int32), ("threads", C.c_int32),
+                ("ctas_per_sm", C.c_int32)]
+
+
+_lib = None
+
+
+def lib():
+    """Loads libsmc.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"libsmc.so not found at {LIB_PATH}: build it with "
+                              "paper_2604_08250_gb300.build.build()")
+        L = C.CDLL(LIB_PATH)
+        P, vp = C.POINTER, C.c_void_p
+        L.smc_last_error.restype = C.c_char_p
+        L.smc_init_lattice.argtypes = [P(_Lat), P(C.c_int64), C.c_uint64, C.c_uint32, vp, vp]
+        L.smc_sweep.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
+                                P(C.c_double), vp, vp, vp]
+        L.smc_sweep_batched.argtypes = [C.c_int32, P(_Lat), P(_Model), P(vp), C.c_uint64, C.c_uint32,
+                                        C.c_uint64, C.c_int32, P(C.c_double), vp, vp, vp]
+        L.smc_sro.argtypes = [P(_Lat), C.c_int32, vp, vp, vp, vp]
+        L.smc_energy.argtypes = [P(_Lat), P(_Model), vp, vp, vp, vp]
+        L.smc_grad_size.argtypes = [P(_Lat), P(_Model)]
+        L.smc_grad_size.restype = C.c_int64
+        L.smc_energy_grad.argtypes = [P(_Lat), P(_Model), vp, vp, vp]
+        L.smc_ministep_trace.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64,
+                                         C.c_int32, C.c_double, vp, vp, vp]
+        L.smc_philox4x32_10.argtypes = [vp, vp, vp, C.c_int64, vp]
+        L.smc_check.argtypes = [vp]
+        L.smc_set_tuning.argtypes = [P(_Tuning)]
+        L.smc_debug_set.argtypes = [C.c_int32, C.c_int64]
+        for name in ("smc_init_lattice", "smc_sweep", "smc_sweep_batched", "smc_sro", "smc_energy",
+                     "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check",
+                     "smc_set_tuning", "smc_debug_set"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _chk(code: int):
+    if code != SMC_OK:
+        raise SMCError(code, lib().smc_last_error().decode())
+
+
+def _stream():
+    import torch
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _dptr(t, dtype=None):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+class Lattice:
+    """nx x ny x nz BCC cells (N = 2 nx ny nz sites), nspecies species."""
+
+    def __init__(self, nx, ny, nz, nspecies):
+        self.nx, self.ny, self.nz, self.nspecies = int(nx), int(ny), int(nz), int(nspecies)
+        self._c = _Lat(self.nx, self.ny, self.nz, self.nspecies)
+
+    @property
+    def nsites(self):
+        return 2 * self.nx * self.ny * self.nz
+
+
+class Model:
+    """Energy model: pair coefficients v [nshells][S][S] (int32 units of unit_ev,
+    or float32 eV) and/or an MLP given as a dict of BF16 bit patterns
+    (w1 [64,20], w2 [64,64], w3 [64], uint16) and FP32 biases (b1, b2, b3)."""
+
+    def __init__(self, kind, nshells=0, v=None, unit_ev=1e-4, mlp=None):
+        self.kind, self.nshells, self.unit_ev = int(kind), int(nshells), float(unit_ev)
+        c = _Model()
+        c.kind, c.nshells, c.unit_ev = self.kind, self.nshells, self.unit_ev
+        if kind == PAIR_I32:
+            self.v = np.ascontiguousarray(v, dtype=np.int32)
+            c.v_i32 = self.v.ctypes.data_as(C.POINTER(C.c_int32))
+        elif kind in (PAIR_F32, PAIR_F32_MLP_BF16):
+            self.v = np.ascontiguousarray(v, dtype=np.float32)
+            c.v_f32 = self.v.ctypes.data_as(C.POINTER(C.c_float))
+        if kind in (MLP_BF16, PAIR_F32_MLP_BF16):
+            self.mlp = {k: np.ascontiguousarray(mlp[k], dtype=np.uint16).reshape(-1) for k in ("w1", "w2", "w3")}
+            for k in ("b1", "b2"):
+                self.mlp[k] = np.ascontiguousarray(mlp[k], dtype=np.float32).reshape(-1)
+            for k in ("w1", "w2", "w3"):
+                setattr(c, "mlp_" + k, self.mlp[k].ctypes.data_as(C.POINTER(C.c_uint16)))
+            for k in ("b1", "b2"):
+                setattr(c, "mlp_" + k, self.mlp[k].ctypes.data_as(C.POINTER(C.c_float)))
+            c.mlp_b3 = float(mlp["b3"])
+        self._c = c
+
+
+def init_lattice(lat, counts, seed, occ, replica=0):
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    _chk(lib().smc_init_lattice(C.byref(lat._c), cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.c_uint64(seed),
+                                C.c_uint32(replica), _dptr(occ), _stream()))
+
+
+def sweep(lat, model, occ, seed, sweep0, nsweeps, kT, replica=0, e_acc=None, n_acc=None):
+    import torch
+    kTa = np.ascontiguousarray(np.broadcast_to(np.asarray(kT, dtype=np.float64), (nsweeps,)))
+    _chk(lib().smc_sweep(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), C.c_uint64(seed),
+                         C.c_uint32(replica), C.c_uint64(sweep0), int(nsweeps),
+                         kTa.ctypes.data_as(C.POINTER(C.c_double)), _dptr(e_acc, torch.float64),
+                         _dptr(n_acc, torch.int64), _stream()))
+
+
+def sweep_batched(lats, model, occs, seed, sweep0, nsweeps, kT, replica0=0, e_acc=None, n_acc=None):
+    import torch
+    R = len(lats)
+    larr = (_Lat * R)(*[l._c for l in lats])
+    parr = (C.c_void_p * R)(*[_dptr(o, torch.int8).value for o in occs])
+    kTa = np.ascontiguousarray(np.broadcast_to(np.asarray(kT, dtype=np.float64).reshape(R, -1), (R, nsweeps)))
+    _chk(lib().smc_sweep_batched(R, larr, C.byref(model._c), parr, C.c_uint64(seed), C.c_uint32(replica0),
+                                 C.c_uint64(sweep0), int(nsweeps), kTa.ctypes.data_as(C.POINTER(C.c_double)),
+                                 _dptr(e_acc, torch.float64), _dptr(n_acc, torch.int64), _stream()))
+
+
+def sro(lat, nshells, occ, counts=None, alpha=None):
+    import torch
+    _chk(lib().smc_sro(C.byref(lat._c), int(nshells), _dptr(occ, torch.int8), _dptr(counts, torch.int64),
+                       _dptr(alpha, torch.float64), _stream()))
+
+
+def energy(lat, model, occ, e=None, e_int=None):
+    import torch
+    _chk(lib().smc_energy(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), _dptr(e, torch.float64),
+                          _dptr(e_int, torch.int64), _stream()))
+
+
+def grad_size(lat, model) -> int:
+    return int(lib().smc_grad_size(C.byref(lat._c), C.byref(model._c)))
+
+
+def energy_grad(lat, model, occ, grad):
+    import torch
+    _chk(lib().smc_energy_grad(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8),
+                               _dptr(grad, torch.float32), _stream()))
+
+
+def ministep_trace(lat, model, occ, seed, sweep_index, k, kT, dE=None, acc=None, replica=0):
+    import torch
+    _chk(lib().smc_ministep_trace(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), C.c_uint64(seed),
+                                  C.c_uint32(replica), C.c_uint64(sweep_index), int(k), float(kT),
+                                  _dptr(dE, torch.float32), _dptr(acc, torch.uint8), _stream()))
+
+
+def philox4x32_10(ctr, key, out):
+    import torch
+    n = ctr.numel() // 4
+    _chk(lib().smc_philox4x32_10(_dptr(ctr, torch.int32), _dptr(key, torch.int32), _dptr(out, torch.int32),
+                                 n, _stream()))
+
+
+def check():
+    """Synchronises the current stream and raises on a latched device error."""
+    _chk(lib().smc_check(_stream()))
+
+
+def set_tuning(tile_y=0, tile_z=0, threads=0, ctas_per_sm=0):
+    t = _Tuning(int(tile_y), int(tile_z), int(threads), int(ctas_per_sm))
+    _chk(lib().smc_set_tuning(C.byref(t)))
+
+
+def debug_set(what, value):
+    _chk(lib().smc_debug_set(int(what), int(value)))

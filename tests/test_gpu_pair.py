@@ -1,0 +1,294 @@
+"""GPU parity of the pair-model path against the CPU oracle (through the C ABI).
+
+Integer models: bit-exact trajectories, energies, counts.  FP32 models: every
+trial's dE within 1e-5 eV of the FP64 oracle and identical decisions, checked
+mini-step by mini-step (lock-step, resynchronising on a decision flip)."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_08250_gb300 import inputs
+from tests import helpers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DE_TOL_EV = 1e-5
+
+
+@pytest.fixture(scope="module")
+def smc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_08250_gb300 import build, smc as s
+    build.build()
+    s.lib()
+    return s
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def gpu_state(smc, dims, S, counts, seed, replica=0):
+    lat = smc.Lattice(*dims, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device=dev())
+    smc.init_lattice(lat, counts, seed, occ, replica=replica)
+    return lat, occ
+
+
+def int_model(S=2, nshells=2, seed=1):
+    V = inputs.pair_int_coeffs(seed, nshells, S)
+    return V
+
+
+def test_philox_known_answers(smc):
+    rows = helpers.read_kat()
+    ctr = torch.tensor(np.array([r[0] for r in rows], dtype=np.uint32).view(np.int32), device=dev())
+    key = torch.tensor(np.array([r[1] for r in rows], dtype=np.uint32).view(np.int32), device=dev())
+    out = torch.zeros_like(ctr)
+    smc.philox4x32_10(ctr.reshape(-1), key.reshape(-1), out.reshape(-1))
+    got = out.cpu().numpy().view(np.uint32)
+    assert np.array_equal(got, np.array([r[2] for r in rows], dtype=np.uint32))
+    # and random counters against the oracle's independent implementation
+    rng = np.random.default_rng(0)
+    c = rng.integers(0, 2 ** 32, size=(256, 4), dtype=np.uint64).astype(np.uint32)
+    k = rng.integers(0, 2 ** 32, size=(256, 2), dtype=np.uint64).astype(np.uint32)
+    o = torch.zeros(256 * 4, dtype=torch.int32, device=dev())
+    smc.philox4x32_10(torch.tensor(c.view(np.int32).reshape(-1), device=dev()),
+                      torch.tensor(k.view(np.int32).reshape(-1), device=dev()), o)
+    got = o.cpu().numpy().view(np.uint32).reshape(256, 4)
+    for i in range(256):
+        assert np.array_equal(got[i], oracle.philox4x32_10(c[i], k[i]))
+
+
+@pytest.mark.parametrize("dims,counts", [((8, 8, 8), None), ((2, 2, 2), [8, 8]), ((6, 10, 4), [100, 0, 380]),
+                                         ((16, 8, 12), None), ((4, 4, 4), [128]), ((8, 4, 6), [0, 0, 192]),
+                                         ((12, 8, 8), [1, 2, 3, 4, 5, 6, 7, 1508])])
+def test_init_matches_oracle(smc, dims, counts):
+    N = 2 * dims[0] * dims[1] * dims[2]
+    if counts is None:
+        counts = inputs.equiatomic_counts(N, 5)
+    S = len(counts)
+    for seed, rep in ((1, 0), (12345678901, 3)):
+        _, occ = gpu_state(smc, dims, S, counts, seed, rep)
+        want = oracle.init_lattice(oracle.Lattice(*dims, S), counts, seed, replica=rep)
+        assert np.array_equal(occ.cpu().numpy(), want)
+
+
+def _run_int(smc, dims, S, nshells, nsweeps, kT, seed=1, vseed=1, chunks=1, sweep0=0):
+    V = int_model(S, nshells, vseed)
+    counts = inputs.equiatomic_counts(2 * dims[0] * dims[1] * dims[2], S)
+    lat, occ = gpu_state(smc, dims, S, counts, seed)
+    model = smc.Model(smc.PAIR_I32, nshells, V, unit_ev=1e-4)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    olat = oracle.Lattice(*dims, S)
+    omodel = oracle.Model(oracle.PAIR_I32, nshells, V, unit_ev=1e-4)
+    ref = oracle.init_lattice(olat, counts, seed)
+    oe = on = 0
+    per = nsweeps // chunks
+    for c in range(chunks):
+        smc.sweep(lat, model, occ, seed, sweep0 + c * per, per, kT, e_acc=e_acc, n_acc=n_acc)
+        e, n = oracle.sweep(olat, omodel, ref, seed, sweep0 + c * per, per, kT)
+        oe += e
+        on += n
+        smc.check()
+        assert np.array_equal(occ.cpu().numpy(), ref), f"occupancy differs after chunk {c}"
+    assert int(n_acc.item()) == on
+    assert float(e_acc.item()) == oe
+    return lat, model, occ, olat, omodel, ref
+
+
+def test_config1_trajectory_bit_exact(smc):
+    """8^3 cells, binary, integer 2-shell coefficients, kT = 25 meV, 100 sweeps:
+    occupancy after every 10 sweeps, accepted count and accumulated dE."""
+    lat, model, occ, olat, omodel, ref = _run_int(smc, (8, 8, 8), 2, 2, 100, 0.025, chunks=10)
+    e_int = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.energy(lat, model, occ, e_int=e_int)
+    assert int(e_int.item()) == oracle.total_energy_i64(olat, omodel, ref)
+
+
+@pytest.mark.parametrize("dims,S,nshells", [((2, 2, 2), 2, 2), ((6, 8, 12), 3, 2), ((8, 12, 16), 3, 3),
+                                            ((16, 8, 8), 4, 1), ((4, 6, 2), 2, 3), ((12, 12, 12), 8, 2),
+                                            ((10, 8, 16), 2, 2)])
+def test_integer_trajectories_other_shapes(smc, dims, S, nshells):
+    _run_int(smc, dims, S, nshells, 6, 0.03, seed=7, vseed=3, chunks=2, sweep0=5)
+
+
+def test_tuning_does_not_change_results(smc):
+    dims, S = (16, 16, 24), 3
+    V = int_model(S, 2, 2)
+    counts = inputs.equiatomic_counts(2 * 16 * 16 * 24, S)
+    model = smc.Model(smc.PAIR_I32, 2, V, unit_ev=1e-4)
+    outs = []
+    for tu in [(0, 0, 0, 0), (1, 1, 32, 0), (2, 3, 64, 1), (4, 6, 128, 2), (3, 1, 96, 0)]:
+        smc.set_tuning(*tu)
+        lat, occ = gpu_state(smc, dims, S, counts, 5)
+        n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+        smc.sweep(lat, model, occ, 5, 0, 3, 0.02, n_acc=n_acc)
+        smc.check()
+        outs.append((occ.cpu().numpy(), int(n_acc.item())))
+    smc.set_tuning()
+    for o, n in outs[1:]:
+        assert np.array_equal(o, outs[0][0]) and n == outs[0][1]
+
+
+def _f32_setup(smc, dims, S=5, seed=3, vseed=2):
+    V = inputs.pair_f32_coeffs(vseed, 2, S)
+    counts = inputs.equiatomic_counts(2 * dims[0] * dims[1] * dims[2], S)
+    lat, occ = gpu_state(smc, dims, S, counts, seed)
+    return V, counts, lat, occ, smc.Model(smc.PAIR_F32, 2, V), oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V)
+
+
+@pytest.mark.parametrize("dims,kT", [((8, 8, 8), 0.06), ((16, 12, 8), 0.03), ((12, 8, 6), 0.2)])
+def test_f32_lockstep_against_oracle(smc, dims, kT):
+    """Every trial of every mini-step of two sweeps: |dE_gpu - dE_oracle| <=
+    1e-5 eV and the same decision (flips resynchronise the oracle)."""
+    V, counts, lat, occ, model, olat, omodel = _f32_setup(smc, dims)
+    ref = occ.cpu().numpy().copy()
+    nA, _ = oracle.schedule(olat)
+    nt = olat.nsites // nA
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    flips = 0
+    worst = 0.0
+    for sw in range(2):
+        for k in range(nA):
+            smc.ministep_trace(lat, model, occ, 9, sw, k, kT, dE=dE, acc=acc)
+            odE, oacc, _, _ = oracle.ministep_trace(olat, omodel, ref, 9, sw, k, kT)
+            g = dE.cpu().numpy().astype(np.float64)
+            worst = max(worst, float(np.abs(g - odE).max()))
+            assert np.all(np.abs(g - odE) <= DE_TOL_EV)
+            ga = acc.cpu().numpy().astype(bool)
+            if not np.array_equal(ga, oacc):
+                flips += int((ga != oacc).sum())
+                ref[:] = occ.cpu().numpy()
+            else:
+                assert np.array_equal(occ.cpu().numpy(), ref)
+    assert flips <= 1, flips
+    assert worst < 1e-6
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 12, 8), (6, 8, 12), (2, 2, 2)])
+def test_f32_sweep_kernel_equals_trace_kernel(smc, dims):
+    """The persistent sweep (shared-memory windows) and the mini-step trace
+    kernel (global reads) share the dE arithmetic: identical trajectories."""
+    V, counts, lat, occ, model, olat, omodel = _f32_setup(smc, dims)
+    occ2 = occ.clone()
+    kT = [0.05, 0.08]
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.sweep(lat, model, occ, 4, 10, 2, kT, e_acc=e_acc)
+    nA, _ = oracle.schedule(olat)
+    for t in range(2):
+        for k in range(nA):
+            smc.ministep_trace(lat, model, occ2, 4, 10 + t, k, kT[t])
+    smc.check()
+    assert torch.equal(occ, occ2)
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, model, occ, e=e)
+    e0 = oracle.total_energy(olat, omodel, oracle.init_lattice(olat, counts, 3))
+    assert float(e.item()) == pytest.approx(e0 + float(e_acc.item()), rel=1e-9, abs=1e-9)
+
+
+def test_counts_sro_energy_grad_match_oracle(smc):
+    for dims, S, nsh in (((8, 8, 8), 5, 3), ((6, 10, 4), 3, 2), ((2, 2, 2), 2, 3), ((16, 16, 16), 8, 3)):
+        N = 2 * dims[0] * dims[1] * dims[2]
+        counts = inputs.equiatomic_counts(N, S)
+        lat, occ = gpu_state(smc, dims, S, counts, 21)
+        olat = oracle.Lattice(*dims, S)
+        ref = oracle.init_lattice(olat, counts, 21)
+        cnt = torch.zeros((nsh, S, S), dtype=torch.int64, device=dev())
+        alpha = torch.zeros((nsh, S, S), dtype=torch.float64, device=dev())
+        smc.sro(lat, nsh, occ, counts=cnt, alpha=alpha)
+        assert np.array_equal(cnt.cpu().numpy(), oracle.pair_counts(olat, nsh, ref))
+        assert np.array_equal(alpha.cpu().numpy(), oracle.sro(olat, nsh, ref))
+        Vf = inputs.pair_f32_coeffs(8, nsh, S)
+        m = smc.Model(smc.PAIR_F32, nsh, Vf)
+        om = oracle.Model(oracle.PAIR_F32, nsh, Vf)
+        e = torch.zeros(1, dtype=torch.float64, device=dev())
+        smc.energy(lat, m, occ, e=e)
+        assert float(e.item()) == pytest.approx(oracle.total_energy(olat, om, ref), rel=1e-12, abs=1e-12)
+        g = torch.zeros(smc.grad_size(lat, m), dtype=torch.float32, device=dev())
+        smc.energy_grad(lat, m, occ, g)
+        assert np.array_equal(g.cpu().numpy().astype(np.float64), oracle.energy_grad(olat, om, ref))
+
+
+def test_batched_replicas_equal_single_runs(smc):
+    edges = [8, 12, 16, 8, 20]
+    S = 5
+    V = inputs.pair_f32_coeffs(3, 2, S)
+    model = smc.Model(smc.PAIR_F32, 2, V)
+    kT = inputs.ladder_kT(len(edges))
+    lats, occs, singles = [], [], []
+    for r, e in enumerate(edges):
+        counts = inputs.equiatomic_counts(2 * e ** 3, S)
+        lat, occ = gpu_state(smc, (e, e, e), S, counts, 11, replica=r)
+        lats.append(lat)
+        occs.append(occ)
+        singles.append(occ.clone())
+    e_acc = torch.zeros(len(edges), dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(len(edges), dtype=torch.int64, device=dev())
+    smc.sweep_batched(lats, model, occs, 11, 0, 3, np.repeat(kT[:, None], 3, 1), e_acc=e_acc, n_acc=n_acc)
+    for r in range(len(edges)):
+        n1 = torch.zeros(1, dtype=torch.int64, device=dev())
+        smc.sweep(lats[r], model, singles[r], 11, 0, 3, kT[r], replica=r, n_acc=n1)
+        smc.check()
+        assert torch.equal(occs[r], singles[r])
+        assert int(n1.item()) == int(n_acc[r].item())
+
+
+def test_timeout_is_reported_and_gpu_stays_usable(smc):
+    dims, S = (16, 16, 16), 2
+    V = int_model(S, 2, 1)
+    counts = inputs.equiatomic_counts(2 * 16 ** 3, S)
+    lat, occ = gpu_state(smc, dims, S, counts, 1)
+    model = smc.Model(smc.PAIR_I32, 2, V, unit_ev=1e-4)
+    smc.set_tuning(1, 1, 32, 0)
+    smc.debug_set(smc.DBG_TIMEOUT_MS, 200)
+    smc.debug_set(smc.DBG_SKIP_PUBLISH, 3)
+    try:
+        smc.sweep(lat, model, occ, 1, 0, 2, 0.025)
+        with pytest.raises(smc.SMCError) as ei:
+            smc.check()
+        assert ei.value.code == smc.SMC_ERR_TIMEOUT
+    finally:
+        smc.debug_set(smc.DBG_SKIP_PUBLISH, -1)
+        smc.debug_set(smc.DBG_TIMEOUT_MS, 2000)
+        smc.set_tuning()
+    # the context is intact: a normal run still matches the oracle
+    _run_int(smc, (8, 8, 8), 2, 2, 3, 0.025)
+
+
+def test_config2_full_size_sampled(smc):
+    """128^3 cells, quinary, FP32 2-shell model: one sweep at 3000 K, then
+    mini-step 0 of the next sweep traced and compared trial by trial on a
+    sample; composition conserved; accumulated dE equals the recomputed E."""
+    c = inputs.CONFIG2
+    dims, S = c["cells"], c["nspecies"]
+    V = inputs.pair_f32_coeffs(c["coeff_seed"], 2, S)
+    counts = inputs.equiatomic_counts(2 * dims[0] * dims[1] * dims[2], S)
+    lat, occ = gpu_state(smc, dims, S, counts, c["mc_seed"])
+    model = smc.Model(smc.PAIR_F32, 2, V)
+    kT = inputs.anneal_kT(c["nsweeps"])
+    e0 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, model, occ, e=e0)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.sweep(lat, model, occ, c["mc_seed"], 0, 2, kT[:2], e_acc=e_acc)
+    e1 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, model, occ, e=e1)
+    smc.check()
+    assert float(e1.item()) == pytest.approx(float(e0.item()) + float(e_acc.item()), rel=1e-9)
+    assert np.array_equal(np.bincount(occ.cpu().numpy(), minlength=S), counts)
+    olat, omodel = oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V)
+    ref = occ.cpu().numpy().copy()
+    nt = olat.nsites // 128
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    smc.ministep_trace(lat, model, occ, c["mc_seed"], 2, 0, kT[2], dE=dE, acc=acc)
+    odE, oacc, _, _ = oracle.ministep_trace(olat, omodel, ref, c["mc_seed"], 2, 0, kT[2])
+    g = dE.cpu().numpy().astype(np.float64)
+    assert np.abs(g - odE).max() <= DE_TOL_EV
+    assert (acc.cpu().numpy().astype(bool) != oacc).sum() <= 1
