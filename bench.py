@@ -1,0 +1,408 @@
+"""Benchmark: Metropolis swap attempts/s on one GB300 (and N independent
+replicas under torchrun).
+
+Workload (one "step" = one full job of the config-2 workload): a BCC box of
+128^3 cells (4,194,304 sites), five species at equal counts, FP32 pair
+coefficients over two shells drawn N(0, 20 meV), annealed linearly from 3000 K
+to 300 K over 1000 sweeps (one trial per site per sweep), followed by the
+total energy and the Warren-Cowley SRO of shells 1-3.  Inputs are synthetic and
+resident in device memory when the timed region starts; L2 is flushed between
+steps.  Extra lines of the JSON object report the 512^3 HBM-resident case,
+the batched replica ladder and the energy gradient against the plain sweep.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2604_08250_gb300 import inputs  # noqa: E402
+
+METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
+BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
+                "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
+                "source": "measured"}
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = float(parts[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def config2_problem():
+    c = inputs.CONFIG2
+    dims, S = c["cells"], c["nspecies"]
+    N = 2 * dims[0] * dims[1] * dims[2]
+    return dict(dims=dims, S=S, N=N, V=inputs.pair_f32_coeffs(c["coeff_seed"], 2, S),
+                counts=inputs.equiatomic_counts(N, S), kT=inputs.anneal_kT(c["nsweeps"], c["t_start"], c["t_end"]),
+                nsweeps=c["nsweeps"], seed=c["mc_seed"])
+
+
+def cpu_baseline(prob, mini_steps: int):
+    """The oracle as it stands, serial, on the first `mini_steps` mini-steps of
+    sweep 0 of the config-2 lattice (32,768 trials each)."""
+    import oracle
+    lat = oracle.Lattice(*prob["dims"], prob["S"])
+    model = oracle.Model(oracle.PAIR_F32, 2, prob["V"])
+    occ = oracle.init_lattice(lat, prob["counts"], prob["seed"])
+    nA, _ = oracle.schedule(lat)
+    t0 = time.perf_counter()
+    ntr = 0
+    for k in range(mini_steps):
+        dE, _, _, _ = oracle.ministep_trace(lat, model, occ, prob["seed"], 0, k, float(prob["kT"][0]))
+        ntr += len(dE)
+    dt = time.perf_counter() - t0
+    return ntr / dt, ntr, dt
+
+
+def run_reference(args, rank):
+    """Reference arm: the serial CPU oracle on the same workload and metric,
+    a bounded sample of the job per step."""
+    if rank != 0:
+        return
+    prob = config2_problem()
+    per_step = 8  # mini-steps of sweep 0 per step (262,144 trials)
+    for _ in range(args.warmup):
+        cpu_baseline(prob, 1)
+    tot_tr, tot_t = 0, 0.0
+    for _ in range(args.steps):
+        rate, ntr, dt = cpu_baseline(prob, per_step)
+        tot_tr += ntr
+        tot_t += dt
+    v = tot_tr / tot_t
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "attempts/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_t / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "bcc128_quinary_f32_pair_anneal", "cells": [128, 128, 128], "sites": prob["N"],
+                       "sample": f"{per_step} mini-steps of sweep 0 per step"},
+            "cpu_baseline": {"value": v, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{per_step} mini-steps (x32768 trials) of sweep 0 per step, serial C"},
+            "e2e": {"value": v, "unit": "attempts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-extras", action="store_true", help="skip the 512^3, batched and gradient lines")
+    ap.add_argument("--cpu-mini-steps", type=int, default=24)
+    ap.add_argument("--profile-sweep", type=int, default=0,
+                    help="profiling driver: one sweep launch on an N^3 quinary FP32 lattice, nothing else")
+    ap.add_argument("--profile-sweeps", type=int, default=1)
+    args = ap.parse_args()
+    if args.profile_sweep:
+        profile_sweep(args.profile_sweep, args.profile_sweeps)
+        return
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    import torch
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    pk = peaks()
+    prob = config2_problem()
+    lat = smc.Lattice(*prob["dims"], prob["S"])
+    model = smc.Model(smc.PAIR_F32, 2, prob["V"])
+    occ0 = torch.empty(prob["N"], dtype=torch.int8, device=dev)
+    smc.init_lattice(lat, prob["counts"], prob["seed"], occ0, replica=rank)
+    occ = torch.empty_like(occ0)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev)
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev)
+    energy = torch.zeros(1, dtype=torch.float64, device=dev)
+    counts = torch.zeros((3, prob["S"], prob["S"]), dtype=torch.int64, device=dev)
+    alpha = torch.zeros((3, prob["S"], prob["S"]), dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
+    stream = torch.cuda.current_stream()
+    nsw = prob["nsweeps"]
+    launches_per_step = 1 + 2 + 2  # sweep kernel; counts + energy finish; counts + SRO finish
+
+    def job(sw_ev=None):
+        if sw_ev:
+            sw_ev[0].record(stream)
+        smc.sweep(lat, model, occ, prob["seed"], 0, nsw, prob["kT"], replica=rank, e_acc=e_acc, n_acc=n_acc)
+        if sw_ev:
+            sw_ev[1].record(stream)
+        smc.energy(lat, model, occ, e=energy)
+        smc.sro(lat, 3, occ, counts=counts, alpha=alpha)
+
+    for _ in range(args.warmup):
+        occ.copy_(occ0)
+        job()
+    smc.check()
+
+    step_ms, sweep_ms = [], []
+    with ClockSampler(local) as clk:
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            occ.copy_(occ0)
+            flush.fill_(1)
+            e0, e1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            s0, s1 = torch.cuda.Event(True), torch.cuda.Event(True)
+            e0.record(stream)
+            job((s0, s1))
+            e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            sweep_ms.append(s0.elapsed_time(s1))
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+    smc.check()
+    total_ms = float(sum(step_ms))
+    if dist:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    attempts_step = prob["N"] * nsw
+    value = world * attempts_step * args.steps / (total_ms * 1e-3)
+    sweep_launch_s = float(np.mean(sweep_ms)) * 1e-3
+    achieved = BYTES_PER_ATTEMPT * attempts_step / sweep_launch_s / 1e9
+
+    # ---- end to end through the C ABI with host buffers ----
+    host_occ = torch.empty(prob["N"], dtype=torch.int8, pin_memory=True)
+    host_occ.copy_(occ0.cpu())
+    host_out = torch.empty(prob["N"], dtype=torch.int8, pin_memory=True)
+    host_obs = torch.empty(1 + 2 * 3 * prob["S"] * prob["S"], dtype=torch.float64, pin_memory=True)
+    e2e_ms = []
+    for it in range(args.warmup + args.steps):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        occ.copy_(host_occ, non_blocking=True)
+        job()
+        host_out.copy_(occ, non_blocking=True)
+        host_obs[0:1].copy_(energy, non_blocking=True)
+        host_obs[1:1 + counts.numel()].copy_(counts.reshape(-1).double(), non_blocking=True)
+        host_obs[1 + counts.numel():].copy_(alpha.reshape(-1), non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_ms.append((time.perf_counter() - t0) * 1e3)
+    e2e_total = float(sum(e2e_ms))
+    if dist:
+        t = torch.tensor([e2e_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_total = float(t.item())
+    e2e_value = world * attempts_step * args.steps / (e2e_total * 1e-3)
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        extras = run_extras(smc, torch, dev, pk)
+    cpu = None
+    if rank == 0:
+        rate, ntr, dt = cpu_baseline(prob, args.cpu_mini_steps)
+        cpu = {"value": rate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+               "sample": f"{args.cpu_mini_steps} mini-steps (x32768 trials) of sweep 0 of the 128^3 job, "
+                         f"serial C oracle, {dt:.1f} s"}
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return
+    traffic = kernel_traffic("k_sweep_fast_bcc128_1000sweeps")
+    line = {
+        "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic (seeded draws; BCC, 5 species, FP32 pair model)",
+        "config": {"workload": "bcc128_quinary_f32_pair_anneal", "cells": [128, 128, 128], "sites": prob["N"],
+                   "sweeps_per_step": nsw, "attempts_per_step": attempts_step, "species": prob["S"], "shells": 2,
+                   "anneal_K": [3000, 300], "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
+                     "kernel": "k_sweep_fast (one launch = 1000 sweeps)",
+                     "bytes_per_attempt": BYTES_PER_ATTEMPT, "peak_source": pk["source"] + " hbm_gbs",
+                     "note": "the 4.2 MB lattice is L2-resident; see extras.hbm_512 for the HBM-resident case"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": prob["N"],
+                "d2h_bytes_per_step": prob["N"] + 8 * (1 + 2 * 3 * prob["S"] * prob["S"])},
+        "gpu_launches": launches_per_step * args.steps,
+        "clocks": clk.summary(),
+        "extras": extras,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def profile_sweep(n: int, nsweeps: int):
+    """Runs exactly one sweep launch (nsweeps sweeps) of the n^3 config-2
+    model after initialisation, for ncu captures (-k regex:k_sweep)."""
+    import torch
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    smc.debug_set(smc.DBG_TIMEOUT_MS, 60000)  # replayed launches run slower under the profiler
+    S = 5
+    lat = smc.Lattice(n, n, n, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device="cuda")
+    smc.init_lattice(lat, inputs.equiatomic_counts(lat.nsites, S), 1, occ)
+    model = smc.Model(smc.PAIR_F32, 2, inputs.pair_f32_coeffs(inputs.CONFIG2["coeff_seed"], 2, S))
+    smc.sweep(lat, model, occ, 1, 0, nsweeps, inputs.anneal_kT(1000)[:nsweeps])
+    smc.check()
+    print(json.dumps({"profile_sweep": n, "sweeps": nsweeps, "ok": True}))
+
+
+def kernel_traffic(name: str):
+    """DRAM bytes per launch from profiles/traffic.json, or None when the
+    kernel source changed after the counters were taken."""
+    import hashlib
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(tp):
+        return None
+    with open(tp) as f:
+        d = json.load(f).get(name)
+    if not d:
+        return None
+    src = os.path.join(ROOT, d["source"])
+    with open(src, "rb") as f:
+        h = hashlib.sha256(f.read()).hexdigest()
+    return d["bytes_per_launch"] if h == d["source_sha256"] else None
+
+
+def run_extras(smc, torch, dev, pk):
+    out = {}
+    stream = torch.cuda.current_stream()
+    S = 5
+    V = inputs.pair_f32_coeffs(inputs.CONFIG2["coeff_seed"], 2, S)
+    model = smc.Model(smc.PAIR_F32, 2, V)
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(True), torch.cuda.Event(True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        b.synchronize()
+        return a.elapsed_time(b) / reps
+
+    # 512^3: lattice (268 MB) larger than L2 -> HBM-resident
+    n = 512
+    lat = smc.Lattice(n, n, n, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device=dev)
+    smc.init_lattice(lat, inputs.equiatomic_counts(lat.nsites, S), 1, occ)
+    kT = inputs.anneal_kT(1000)
+    nsw = 4
+    ms = timed(lambda: smc.sweep(lat, model, occ, 1, 0, nsw, kT[:nsw]), reps=2)
+    att = lat.nsites * nsw / (ms * 1e-3)
+    out["hbm_512"] = {"cells": [n, n, n], "sweeps_per_launch": nsw, "ms_per_sweep": ms / nsw,
+                      "attempts_per_s": att, "achieved_gbs": att * BYTES_PER_ATTEMPT / 1e9,
+                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+    # gradient of E (pair part) at the 512^3 configuration vs one plain sweep of it
+    g = torch.zeros(smc.grad_size(lat, model), dtype=torch.float32, device=dev)
+    gms = timed(lambda: smc.energy_grad(lat, model, occ, g), reps=3)
+    out["grad_512"] = {"ms_per_configuration": gms, "ms_per_plain_sweep": ms / nsw,
+                       "ratio_to_sweep": gms / (ms / nsw), "params": int(g.numel()),
+                       "achieved_gbs": lat.nsites / (gms * 1e-3) / 1e9}
+    del occ
+    # batched: 64 uneven replicas on a temperature ladder, one launch
+    c3 = inputs.CONFIG3
+    edges = inputs.batched_edges(c3["edge_seed"], c3["nrep"])
+    lats = [smc.Lattice(int(e), int(e), int(e), S) for e in edges]
+    occs = []
+    for r, l in enumerate(lats):
+        o = torch.empty(l.nsites, dtype=torch.int8, device=dev)
+        smc.init_lattice(l, inputs.equiatomic_counts(l.nsites, S), 1, o, replica=r)
+        occs.append(o)
+    kTr = inputs.ladder_kT(c3["nrep"], c3["t_min"], c3["t_max"])
+    nb = 20
+    kTb = np.repeat(kTr[:, None], nb, axis=1)
+    bms = timed(lambda: smc.sweep_batched(lats, model, occs, 1, 0, nb, kTb), reps=1)
+    tot = sum(l.nsites for l in lats)
+    batt = tot * nb / (bms * 1e-3)
+    out["batched_64"] = {"replicas": len(lats), "edges_min_max": [int(edges.min()), int(edges.max())],
+                         "total_sites": tot, "sweeps": nb, "attempts_per_s": batt,
+                         "frac_of_measured_hbm": batt * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+    return out
+
+
+if __name__ == "__main__":
+    main()

@@ -181,7 +181,7 @@ const char *smc_last_error(void);
 /* Launch tuning (domain tile shape and CTA size) chosen by the caller's
  * autotuner; results never depend on it.  tile_y, tile_z: link-cell columns
  * per tile along y and z (0 = automatic); threads: CTA size, a multiple of 32
- * in [32, 1024] (0 = automatic); ctas_per_sm: resident CTAs per SM requested
+ * in [32, 512] (0 = automatic; the fast kernel uses at most 256); ctas_per_sm: resident CTAs per SM requested
  * (0 = automatic).  Applies to later sweeps on the calling thread. */
 typedef struct {
     int32_t tile_y, tile_z, threads, ctas_per_sm;

@@ -33,6 +33,7 @@
 namespace smc {
 
 constexpr int kMaxBeta = 1024;
+constexpr int kMaxGroups = 64;
 
 struct RepDesc {
     int8_t *occ;
@@ -65,6 +66,9 @@ struct SweepParams {
     int *abort_flag;
     int *status;
     const uint32_t *tab;  // integer acceptance tables
+    int lag[kMaxGroups];  // group g may start once neighbours completed g+1-lag[g] groups
+    int warp_bytes;       // fast kernel: shared-memory bytes per warp
+    int rowB;             // fast kernel: row stride in shared memory
     union {
         float beta[kMaxBeta];
         int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
@@ -263,7 +267,7 @@ __device__ bool wait_tile(const SweepParams &P, const RepDesc &D, int ty, int tz
 }
 
 template <bool IS_INT>
-__global__ void __launch_bounds__(1024) k_sweep_pair(const __grid_constant__ SweepParams P)
+__global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ SweepParams P)
 {
     using T = typename Acc<IS_INT>::T;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -515,6 +519,448 @@ __global__ void __launch_bounds__(1024) k_sweep_pair(const __grid_constant__ Swe
 }
 
 // ---------------------------------------------------------------------------
+// Fast path: every axis holds >= 2 four-cell link cells (Lx = Ly = Lz = 4).
+// One warp owns a tile of columns and runs it without CTA barriers: it waits
+// for its tile's neighbours, stages the column's rows in its own shared
+// memory, runs the 4 mini-steps of the group (lane i handles link cells
+// i, i+32, ...), writes back the 5 rows the group may change and publishes
+// its progress.  Philox is evaluated once per link cell and group: the four
+// trial sites of a link cell's x-row, x = 4i .. 4i+3, share the counter
+// s >> 2 and use its four output words.
+//
+// Shared-memory rows of a column (stride rb = padded nx + 32): the row body
+// starts 16 bytes in and is framed by a 4-byte periodic halo on each side,
+// so x-2 .. x+2 need no wrap.  Trial-sublattice rows (dy, dz) in [-1, 1]^2
+// are at index (dz+1)*3 + (dy+1); partner-sublattice rows (sy, sz) in
+// [0, 4)^2, i.e. (dy, dz) = (s_off-1+sy, s_off-1+sz), at 9 + sz*4 + sy.
+// Two-shell models never read the four partner corner rows (not loaded).
+// A neighbour of species q adds 1 << (4q) to a histogram of 4-bit counts.
+//
+// dE through the histograms: with c_m[q] = #{j in N_m(a)\b: s_j = q} -
+// #{j in N_m(b)\a: s_j = q} and D_m[q] = V_m(s_b, q) - V_m(s_a, q),
+// dE = sum_m sum_q c_m[q] D_m[q].  For shells 1 and 2, c + 8 lies in [1, 15]
+// and one biased word holds all of c_m; shell 3 keeps the two counts apart.
+// ---------------------------------------------------------------------------
+// Sum over the first S-1 species only: every shell holds the same number of
+// neighbours of a (without b) as of b (without a), so sum_q c[q] = 0 and
+// c[S-1] = -sum_{q<S-1} c[q].  The kernel's table row for (m, A, B) holds
+// D'[q] = D[q] - D[S-1] for q < S-1 and, in entry 7, -8 sum_q D'[q] (the
+// 4-bit fields of shells 1 and 2 carry a bias of 8).
+template <bool IS_INT, int S>
+__device__ __forceinline__ typename Acc<IS_INT>::T dot_biased(uint32_t H, const typename Acc<IS_INT>::T *D)
+{
+    using T = typename Acc<IS_INT>::T;
+    T acc = D[7];
+#pragma unroll
+    for (int q = 0; q < S - 1; ++q) {
+        const int f = (int)((H >> (4 * q)) & 15u);
+        if constexpr (IS_INT)
+            acc += f * D[q];
+        else
+            acc = fmaf((float)f, D[q], acc);
+    }
+    return acc;
+}
+
+template <bool IS_INT, int S>
+__device__ __forceinline__ typename Acc<IS_INT>::T dot_diff(uint32_t Ha, uint32_t Hb, const typename Acc<IS_INT>::T *D)
+{
+    using T = typename Acc<IS_INT>::T;
+    T acc = T(0);
+#pragma unroll
+    for (int q = 0; q < S - 1; ++q) {
+        const int f = (int)((Ha >> (4 * q)) & 15u) - (int)((Hb >> (4 * q)) & 15u);
+        if constexpr (IS_INT)
+            acc += f * D[q];
+        else
+            acc = fmaf((float)f, D[q], acc);
+    }
+    return acc;
+}
+
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+#define SM8(off) ((uint32_t)g_smem[(off)])
+#define NIB(v) (1u << ((v) << 2))
+
+// po: byte offsets (in g_smem) of the 9 trial-sublattice row bodies; pt: of
+// the partner block (row index 0).  Returns dE; A, B and the partner's
+// row offset and x through references.
+template <bool IS_INT, int NSH, int S, int SOFF>
+__device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, uint32_t pt, uint32_t rb, int x,
+                                                           int dir, uint32_t dt, int &A, int &B, uint32_t &brow,
+                                                           int &xb)
+{
+    using T = typename Acc<IS_INT>::T;
+    const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
+    A = (int)(SM8(po[4] + x) & 7u);
+    const uint32_t rbp = pt + (uint32_t)((kz + 1) * 4 + (ky + 1)) * rb;  // partner's row
+    xb = x + SOFF + kx;
+    B = (int)(SM8(rbp + xb) & 7u);
+    brow = rbp;
+    if (A == B) return T(0);
+    // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
+    // trial-sublattice neighbours plus a.  A species >= 8 (invalid input)
+    // shifts the 1 out of the word and is ignored.
+    uint32_t H1 = 0x88888888u - NIB(B) + NIB(A);
+    {
+        const uint32_t xa = pt + x + SOFF;
+        H1 += NIB(SM8(xa + 5 * rb)) + NIB(SM8(xa + 5 * rb + 1)) + NIB(SM8(xa + 6 * rb)) + NIB(SM8(xa + 6 * rb + 1)) +
+              NIB(SM8(xa + 9 * rb)) + NIB(SM8(xa + 9 * rb + 1)) + NIB(SM8(xa + 10 * rb)) + NIB(SM8(xa + 10 * rb + 1));
+        const uint32_t ob = po[0] + (uint32_t)(kz * 3 + ky) * rb + x + kx - 1;
+        H1 -= NIB(SM8(ob)) + NIB(SM8(ob + 1)) + NIB(SM8(ob + rb)) + NIB(SM8(ob + rb + 1)) + NIB(SM8(ob + 3 * rb)) +
+              NIB(SM8(ob + 3 * rb + 1)) + NIB(SM8(ob + 4 * rb)) + NIB(SM8(ob + 4 * rb + 1));
+    }
+    const T *Dt = (const T *)(g_smem + dt);
+    const T *D1 = Dt + (A * kMaxSpecies + B) * kMaxSpecies;
+    T dE = dot_biased<IS_INT, S>(H1, D1);
+    const uint32_t bx = rbp + xb;
+    if (NSH >= 2) {
+        const uint32_t ax = po[4] + x;
+        uint32_t H2 = 0x88888888u;
+        H2 += NIB(SM8(ax - 1)) + NIB(SM8(ax + 1)) + NIB(SM8(po[3] + x)) + NIB(SM8(po[5] + x)) + NIB(SM8(po[1] + x)) +
+              NIB(SM8(po[7] + x));
+        H2 -= NIB(SM8(bx - 1)) + NIB(SM8(bx + 1)) + NIB(SM8(bx - rb)) + NIB(SM8(bx + rb)) + NIB(SM8(bx - 4 * rb)) +
+              NIB(SM8(bx + 4 * rb));
+        dE += dot_biased<IS_INT, S>(H2, D1 + kMaxSpecies * kMaxSpecies * kMaxSpecies);
+    }
+    if (NSH >= 3) {
+        const uint32_t Ha = NIB(SM8(po[0] + x)) + NIB(SM8(po[2] + x)) + NIB(SM8(po[6] + x)) + NIB(SM8(po[8] + x)) +
+                            NIB(SM8(po[3] + x - 1)) + NIB(SM8(po[3] + x + 1)) + NIB(SM8(po[5] + x - 1)) +
+                            NIB(SM8(po[5] + x + 1)) + NIB(SM8(po[1] + x - 1)) + NIB(SM8(po[1] + x + 1)) +
+                            NIB(SM8(po[7] + x - 1)) + NIB(SM8(po[7] + x + 1));
+        const uint32_t Hb = NIB(SM8(bx - 5 * rb)) + NIB(SM8(bx - 3 * rb)) + NIB(SM8(bx + 3 * rb)) +
+                            NIB(SM8(bx + 5 * rb)) + NIB(SM8(bx - rb - 1)) + NIB(SM8(bx - rb + 1)) +
+                            NIB(SM8(bx + rb - 1)) + NIB(SM8(bx + rb + 1)) + NIB(SM8(bx - 4 * rb - 1)) +
+                            NIB(SM8(bx - 4 * rb + 1)) + NIB(SM8(bx + 4 * rb - 1)) + NIB(SM8(bx + 4 * rb + 1));
+        dE += dot_diff<IS_INT, S>(Ha, Hb, D1 + 2 * kMaxSpecies * kMaxSpecies * kMaxSpecies);
+    }
+    return dE;
+}
+#undef NIB
+
+// Stores v at x (in [-1, nx]) of the halo-framed row whose body starts at
+// byte offset `row`, keeping the halo copies of the first and last four
+// cells in step.
+__device__ __forceinline__ void halo_store(uint32_t row, int x, int nx, unsigned char v)
+{
+    const int xr = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    g_smem[row + xr] = v;
+    if (xr < 4) g_smem[row + xr + nx] = v;
+    if (xr >= nx - 4) g_smem[row + xr - nx] = v;
+}
+
+// Bounded wait of one warp for the 8 neighbouring tiles of (ty, tz).
+__device__ bool wait_tile_warp(const SweepParams &P, const RepDesc &D, int ty, int tz, uint32_t need, int lane)
+{
+    const uint32_t *fp = nullptr;
+    if (lane < 9 && lane != 4) {
+        int nty = ty + (lane % 3) - 1, ntz = tz + (lane / 3) - 1;
+        nty = nty < 0 ? nty + D.NTy : (nty >= D.NTy ? nty - D.NTy : nty);
+        ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
+        fp = P.flags + D.tile0 + ntz * D.NTy + nty;
+    }
+    const uint64_t t0 = global_ns();
+    unsigned nap = 32;
+    for (;;) {
+        const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        int stop = 0;
+        if (lane == 0) {
+            if (ld_volatile_i32(P.abort_flag)) {
+                stop = 1;
+            } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
+                atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+                atomicExch(P.abort_flag, 1);
+                stop = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        __nanosleep(nap);
+        nap = nap < 512 ? nap * 2 : 512;
+    }
+}
+
+template <bool IS_INT, int NSH, int S, int SOFF>
+__device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc &RD, uint32_t col, int y0, int z0,
+                                            uint64_t sweep, float beta, int2 ti, uint32_t dt, int lane,
+                                            typename Acc<IS_INT>::T &accE, double &accEd, long long &accN)
+{
+    using T = typename Acc<IS_INT>::T;
+    constexpr int sub = SOFF == -1 ? 0 : 1;
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
+    const uint32_t rb = (uint32_t)P.rowB;
+    const int rows = NSH >= 3 ? 25 : 21;
+    const bool vec = RD.vec != 0;
+    // ---- per-row source (global) and destination (shared) of this column:
+    // lane rr computes row rr once; others read it by shuffle ----
+    const int8_t *my_src = RD.occ;
+    uint32_t my_dst = 0;
+    if (lane < rows) {
+        int slot, gsub, dy, dz;
+        if (lane < 9) {
+            slot = lane;
+            dy = lane % 3 - 1;
+            dz = lane / 3 - 1;
+            gsub = sub;
+        } else {
+            int k = lane - 9;
+            if (NSH < 3) k += (k >= 2) + (k >= 10) + 1;  // skip corner slots 0, 3, 12, 15
+            slot = 9 + k;
+            dy = (k & 3) - 1 + SOFF;
+            dz = (k >> 2) - 1 + SOFF;
+            gsub = 1 - sub;
+        }
+        const int gy = wrapc(y0 + dy, ny), gz = wrapc(z0 + dz, nz);
+        my_src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
+        my_dst = col + (uint32_t)slot * rb + 16;
+    }
+    // ---- stage the rows (L2-only copies: never a stale L1 line) ----
+    {
+        const int cpr = vec ? (nx >> 4) : (nx >> 2);
+        int lr = 0, lc = lane, rstep = 1, cstep = 32;
+        if (cpr < 32) {
+            rstep = 32 / cpr;
+            lr = lane / cpr;
+            lc = lane - lr * cpr;
+            cstep = cpr;
+        }
+        const int iters = (rows + rstep - 1) / rstep;
+        const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+        for (int it = 0; it < iters; ++it) {
+            const int rr = lr + it * rstep;
+            const int rsel = rr < rows ? rr : 0;
+            const int8_t *src = (const int8_t *)__shfl_sync(0xffffffffu, (unsigned long long)my_src, rsel);
+            const uint32_t dst = __shfl_sync(0xffffffffu, my_dst, rsel);
+            if (lr < rstep && rr < rows) {
+                if (vec) {
+                    for (int c = lc; c < cpr; c += cstep)
+                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + dst + 16 * c),
+                                     "l"(src + 16 * c)
+                                     : "memory");
+                } else {
+                    const unsigned *s4 = (const unsigned *)src;
+                    unsigned *d4 = (unsigned *)(g_smem + dst);
+                    for (int c = lc; c < cpr; c += 4 * cstep) {
+                        const int c1 = c + cstep, c2 = c + 2 * cstep, c3 = c + 3 * cstep;
+                        const unsigned v0 = __ldcg(s4 + c);
+                        const unsigned v1 = c1 < cpr ? __ldcg(s4 + c1) : 0u;
+                        const unsigned v2 = c2 < cpr ? __ldcg(s4 + c2) : 0u;
+                        const unsigned v3 = c3 < cpr ? __ldcg(s4 + c3) : 0u;
+                        d4[c] = v0;
+                        if (c1 < cpr) d4[c1] = v1;
+                        if (c2 < cpr) d4[c2] = v2;
+                        if (c3 < cpr) d4[c3] = v3;
+                    }
+                }
+            }
+        }
+        if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncwarp();
+        // periodic halos: 4 bytes before and after each row body
+        if (lane < rows) {
+            *(unsigned *)(g_smem + my_dst - 4) = *(const unsigned *)(g_smem + my_dst + nx - 4);
+            *(unsigned *)(g_smem + my_dst + nx) = *(const unsigned *)(g_smem + my_dst);
+        }
+        __syncwarp();
+    }
+    uint32_t po[9];
+#pragma unroll
+    for (int r = 0; r < 9; ++r) po[r] = col + (uint32_t)r * rb + 16;
+    const uint32_t pt = col + 9 * rb + 16;
+    // ---- Philox words of this lane's link cells, kept in shared memory ----
+    uint32_t *wsm = (uint32_t *)(g_smem + col + 25 * rb);  // [k][dx][lane]
+    const int nk = (NLx + 31) >> 5;
+    const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+#pragma unroll 1
+    for (int k = 0; k < nk; ++k) {
+        const int i = lane + 32 * k;
+        if (i < NLx) {
+            const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
+            wsm[(k * 4 + 0) * 32 + lane] = w.x;
+            wsm[(k * 4 + 1) * 32 + lane] = w.y;
+            wsm[(k * 4 + 2) * 32 + lane] = w.z;
+            wsm[(k * 4 + 3) * 32 + lane] = w.w;
+        }
+    }
+    // ---- the four mini-steps of the group ----
+#pragma unroll 1
+    for (int dx = 0; dx < 4; ++dx) {
+#pragma unroll 1
+        for (int k = 0; k < nk; ++k) {
+            const int i = lane + 32 * k;
+            if (i < NLx) {
+                const int x = 4 * i + dx;
+                const uint32_t w = wsm[(k * 4 + dx) * 32 + lane];
+                int A, B, xb;
+                uint32_t brow;
+                const T dE = fast_dE<IS_INT, NSH, S, SOFF>(po, pt, rb, x, (int)(w >> kRBits), dt, A, B, brow, xb);
+                if (metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti)) {
+                    if (A != B) {
+                        halo_store(po[4], x, nx, (unsigned char)B);
+                        halo_store(brow, xb, nx, (unsigned char)A);
+                    }
+                    if constexpr (IS_INT)
+                        accE += dE;
+                    else
+                        accEd += (double)dE;
+                    accN += 1;
+                }
+            }
+        }
+        __syncwarp();
+    }
+    // ---- write back trial row (0,0) and partner rows (s_off..s_off+1)^2 ----
+    {
+        const int cpr = vec ? (nx >> 4) : (nx >> 2);
+        int lr = 0, lc = lane, rstep = 1, cstep = 32;
+        if (cpr < 32) {
+            rstep = 32 / cpr;
+            lr = lane / cpr;
+            lc = lane - lr * cpr;
+            cstep = cpr;
+        }
+        if (lr < rstep) {
+            for (int wr = lr; wr < 5; wr += rstep) {
+                int slot, gsub, gy, gz;
+                if (wr == 0) {
+                    slot = 4;
+                    gsub = sub;
+                    gy = y0;
+                    gz = z0;
+                } else {
+                    const int sy = 1 + ((wr - 1) & 1), sz = 1 + ((wr - 1) >> 1);
+                    slot = 9 + sz * 4 + sy;
+                    gsub = 1 - sub;
+                    gy = wrapc(y0 + sy - 1 + SOFF, ny);
+                    gz = wrapc(z0 + sz - 1 + SOFF, nz);
+                }
+                int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
+                const unsigned char *srcs = g_smem + col + (uint32_t)slot * rb + 16;
+                if (vec) {
+                    for (int c = lc; c < cpr; c += cstep) *((int4 *)dstg + c) = *((const int4 *)srcs + c);
+                } else {
+                    for (int c = lc; c < cpr; c += cstep) *((unsigned *)dstg + c) = *((const unsigned *)srcs + c);
+                }
+            }
+        }
+    }
+    __syncwarp();
+}
+
+template <bool IS_INT, int NSH, int S>
+__global__ void __launch_bounds__(256, 2) k_sweep_fast(const __grid_constant__ SweepParams P)
+{
+    using T = typename Acc<IS_INT>::T;
+    unsigned char *smem = g_smem;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
+    T *Dt = (T *)smem;
+    for (int i = tid; i < kDEntries; i += blockDim.x) {
+        if constexpr (IS_INT)
+            Dt[i] = P.D.di[i];
+        else
+            Dt[i] = P.D.df[i];
+    }
+    __syncthreads();
+    unsigned char *wbase = smem + kDEntries * 4 + (size_t)warp * P.warp_bytes;
+    double *slot_e = (double *)wbase;
+    long long *slot_n = (long long *)(slot_e + P.tpc);
+    const uint32_t col = (uint32_t)((unsigned char *)(slot_n + P.tpc) - smem);
+    for (int i = lane; i < P.tpc; i += 32) {
+        slot_e[i] = 0.0;
+        slot_n[i] = 0;
+    }
+    __syncwarp();
+
+    bool aborted = false;
+    for (int t = 0; t < P.nsweeps && !aborted; ++t) {
+        const uint64_t sweep = P.sweep0 + (uint64_t)t;
+        for (int g = 0; g < P.G && !aborted; ++g) {
+            const uint32_t gstep = (uint32_t)(t * P.G + g);
+            const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4;
+            const int lagv = P.lag[g];
+            const uint32_t need = gstep + 1 >= (uint32_t)lagv ? gstep + 1 - lagv : 0;
+            int slotk = 0;
+            for (int tile = gw; tile < P.ntiles; tile += NW, ++slotk) {
+                int r = 0;
+                while (r + 1 < P.R && P.rep[r + 1].tile0 <= tile) ++r;
+                const RepDesc &RD = P.rep[r];
+                const int lt = tile - RD.tile0, ty = lt % RD.NTy, tz = lt / RD.NTy;
+                if (!wait_tile_warp(P, RD, ty, tz, need, lane)) {
+                    aborted = true;
+                    break;
+                }
+                float beta = 0.f;
+                int2 ti = make_int2(0, 0);
+                if constexpr (IS_INT)
+                    ti = P.temp.tabinfo[P.beta_stride ? r * P.beta_stride + t : r];
+                else
+                    beta = P.temp.beta[P.beta_stride ? r * P.beta_stride + t : r];
+                T accE = T(0);
+                double accEd = 0.0;
+                long long accN = 0;
+                const int j0 = ty * P.TY, j1 = min(j0 + P.TY, RD.NLy);
+                const int l0 = tz * P.TZ, l1 = min(l0 + P.TZ, RD.NLz);
+                for (int l = l0; l < l1; ++l)
+                    for (int j = j0; j < j1; ++j) {
+                        const int y0 = 4 * j + dy, z0 = 4 * l + dz;
+                        if (sub == 0)
+                            fast_column<IS_INT, NSH, S, -1>(P, RD, col, y0, z0, sweep, beta, ti, 0u, lane, accE,
+                                                            accEd, accN);
+                        else
+                            fast_column<IS_INT, NSH, S, 0>(P, RD, col, y0, z0, sweep, beta, ti, 0u, lane, accE,
+                                                           accEd, accN);
+                    }
+                double e_w;
+                if constexpr (IS_INT)
+                    e_w = (double)warp_sum<long long>((long long)accE);
+                else
+                    e_w = warp_sum<double>(accEd);
+                const long long n_w = warp_sum<long long>(accN);
+                if (lane == 0) {
+                    slot_e[slotk] += e_w;
+                    slot_n[slotk] += n_w;
+                }
+                // every lane's row stores, then one release by lane 0 (the warp
+                // barrier orders the other lanes' stores before it)
+                __syncwarp();
+                if (lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, gstep + 1);
+            }
+        }
+    }
+    // ---- per-tile partial sums; the last warp to finish reduces them in order ----
+    if (aborted) return;
+    if (lane == 0) {
+        int k = 0;
+        for (int tile = gw; tile < P.ntiles; tile += NW, ++k) {
+            P.part_e[tile] = slot_e[k];
+            P.part_n[tile] = slot_n[k];
+        }
+    }
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) last = (atomicAdd(P.ticket, 1u) == (unsigned)NW - 1) ? 1u : 0u;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    for (int r = lane; r < P.R; r += 32) {
+        const RepDesc &RD = P.rep[r];
+        double se = 0.0;
+        long long sn = 0;
+        const int nt = RD.NTy * RD.NTz;
+        for (int k = 0; k < nt; ++k) {
+            se += __ldcg(P.part_e + RD.tile0 + k);
+            sn += __ldcg(P.part_n + RD.tile0 + k);
+        }
+        if (RD.e_acc) *RD.e_acc += se;
+        if (RD.n_acc) *RD.n_acc += sn;
+    }
+}
+
+// ---------------------------------------------------------------------------
 // Lock-step trace of one mini-step: one thread per trial, reading rows
 // straight from global memory through the same dE arithmetic.  Phase 1
 // evaluates every trial (read-only), phase 2 applies the accepted swaps.
@@ -593,8 +1039,9 @@ namespace {
 
 struct Plan {
     int Lx, Ly, Lz, G;
-    int threads, CB, TY, TZ, ntiles, grid, tpc;
+    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0;
     size_t smem;
+    const void *kernel = nullptr;
 };
 
 int col_bytes_of(const smc_lattice &l)
@@ -619,8 +1066,8 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
         maxcol = std::max(maxcol, col_bytes_of(lats[r]));
     }
     pl.threads = tu.threads ? tu.threads : (maxNLx <= 128 ? 128 : 256);
-    if (pl.threads % 32 || pl.threads < 32 || pl.threads > 1024) {
-        set_error("tuning.threads must be a multiple of 32 in [32, 1024]");
+    if (pl.threads % 32 || pl.threads < 32 || pl.threads > 512) {
+        set_error("tuning.threads must be a multiple of 32 in [32, 512]");
         return SMC_ERR_ARG;
     }
     pl.CB = std::max(1, pl.threads / maxNLx);
@@ -643,9 +1090,17 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
         return SMC_ERR_UNSUPPORTED;
     }
     auto kern = k_sweep_pair<IS_INT>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
+    while (pl.CB > 1 && smem_for(pl.CB, 64) > dyn_max) pl.CB /= 2;
+    if (smem_for(pl.CB, 1) > dyn_max) {
+        set_error("lattice rows too long for shared memory (nx = %d)", lats[0].nx);
+        return SMC_ERR_UNSUPPORTED;
+    }
     size_t smem = smem_for(pl.CB, 64);
-    if (smem > ws->smem_optin) smem = ws->smem_optin;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ws->smem_optin);
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     // resident CTAs with the accumulator slots sized for the worst case
     int per_sm = 0;
@@ -661,12 +1116,109 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
         pl.grid = std::min(pl.ntiles, per_sm * ws->num_sms);
         pl.tpc = (pl.ntiles + pl.grid - 1) / pl.grid;
         if (pl.tpc <= tpc_guess) break;
+        if (smem_for(pl.CB, tpc_guess * 2) > dyn_max) {
+            set_error("too many tiles per CTA for shared memory");
+            return SMC_ERR_UNSUPPORTED;
+        }
         if (tpc_guess > 4096) {
             set_error("too many tiles per CTA");
             return SMC_ERR_UNSUPPORTED;
         }
     }
     pl.smem = smem;
+    pl.kernel = (const void *)k_sweep_pair<IS_INT>;
+    return SMC_OK;
+}
+
+template <bool IS_INT, int NSH>
+const void *pick_fast(int S)
+{
+    switch (S) {
+    case 2: return (const void *)k_sweep_fast<IS_INT, NSH, 2>;
+    case 5: return (const void *)k_sweep_fast<IS_INT, NSH, 5>;
+    default: return (const void *)k_sweep_fast<IS_INT, NSH, 8>;
+    }
+}
+
+// Plan of the warp-per-tile kernel: tiles of TY x TZ columns, one warp each
+// (a warp owns ceil(ntiles / warps) tiles), shared memory = D table + per warp
+// (accumulator slots + 25 rows).
+template <bool IS_INT>
+smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
+                          int rowB, int same_nx, Plan &pl)
+{
+    const Tuning tu = current_tuning();
+    pl.Lx = pl.Ly = pl.Lz = 4;
+    pl.G = 32;
+    (void)same_nx;
+    (void)occ;
+    const int S = lats[0].nspecies;
+    pl.kernel = nshells >= 3 ? pick_fast<IS_INT, 3>(S) : pick_fast<IS_INT, 2>(S);
+    pl.threads = tu.threads ? std::min(tu.threads, 256) : 256;  // the kernel's launch bound
+    const int nwarps = pl.threads / 32;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(pl.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    long long ncols = 0;
+    for (int r = 0; r < R; ++r) ncols += (long long)(lats[r].ny / 4) * (lats[r].nz / 4);
+    int nkmax = 1;
+    for (int r = 0; r < R; ++r) nkmax = std::max(nkmax, (lats[r].nx / 4 + 31) / 32);
+    const size_t rows_bytes = (size_t)25 * rowB + (size_t)512 * nkmax;
+    auto smem_for = [&](int tpc) {
+        return (size_t)kDEntries * 4 + (size_t)nwarps * (((size_t)16 * tpc + rows_bytes + 15) / 16 * 16);
+    };
+    // resident warps at one tile slot, to size the default tile
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, pl.threads, smem_for(4));
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1) {
+        set_error("fast sweep kernel does not fit on an SM");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+    const long long warps_res = (long long)per_sm * ws->num_sms * nwarps;
+    pl.TY = tu.tile_y;
+    pl.TZ = tu.tile_z;
+    if (pl.TY <= 0 || pl.TZ <= 0) {
+        int c = 1;
+        while ((long long)(c * 2) * warps_res <= ncols) c *= 2;
+        int ty = 1, tz = 1;
+        while (ty * tz < c) {
+            if (ty <= tz) ty *= 2; else tz *= 2;
+        }
+        if (pl.TY <= 0) pl.TY = ty;
+        if (pl.TZ <= 0) pl.TZ = tz;
+    }
+    pl.ntiles = 0;
+    for (int r = 0; r < R; ++r)
+        pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
+    for (int tpc_guess = 1;; tpc_guess *= 2) {
+        const size_t smem = smem_for(tpc_guess);
+        if (smem > dyn_max) {
+            set_error("fast sweep: shared memory per CTA too large (%zu bytes)", smem);
+            return SMC_ERR_UNSUPPORTED;
+        }
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, pl.threads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (per_sm < 1) {
+            set_error("fast sweep kernel does not fit on an SM (smem %zu)", smem);
+            return SMC_ERR_UNSUPPORTED;
+        }
+        if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+        const int want = (pl.ntiles + nwarps - 1) / nwarps;
+        pl.grid = std::min(want, per_sm * ws->num_sms);
+        pl.tpc = (pl.ntiles + pl.grid * nwarps - 1) / (pl.grid * nwarps);
+        if (pl.tpc <= tpc_guess) {
+            pl.smem = smem;
+            pl.warp_bytes = (int)(((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
+            pl.tpc = tpc_guess;
+            break;
+        }
+    }
+    pl.CB = 1;
     return SMC_OK;
 }
 
@@ -693,9 +1245,26 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
+    // Fast path: 4-cell link cells on every axis, rows of at most 1024 cells,
+    // 4-byte aligned occupancy.
+    bool fast = true;
+    int rowB_fast = 0, same_nx = lats[0].nx;
+    for (int r = 0; r < R; ++r) {
+        const smc_lattice &l = lats[r];
+        fast = fast && lc_edge(l.nx) == 4 && lc_edge(l.ny) == 4 && lc_edge(l.nz) == 4 && l.nx <= 1024 &&
+               ((uintptr_t)occ[r] % 4 == 0);
+        rowB_fast = std::max(rowB_fast, ((l.nx + 15) & ~15) + 32);  // body + 16-byte halo frame each side
+        if (l.nx != same_nx) same_nx = -1;
+    }
+    if (current_tuning().threads && current_tuning().threads % 32) fast = false;
     Plan pl;
-    st = make_plan<IS_INT>(R, lats, ws, pl);
-    if (st != SMC_OK) return st;
+    if (fast) {
+        st = make_fast_plan<IS_INT>(R, lats, occ, ws, m->nshells, rowB_fast, same_nx, pl);
+        if (st != SMC_OK) return st;
+    } else {
+        st = make_plan<IS_INT>(R, lats, ws, pl);
+        if (st != SMC_OK) return st;
+    }
 
     static SweepParams P;  // large: keep off the stack (host-only, guarded by the API lock)
     memset(&P, 0, sizeof P);
@@ -710,6 +1279,15 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     P.nshells = m->nshells;
     P.S = lats[0].nspecies;
     P.tpc = pl.tpc;
+    P.warp_bytes = pl.warp_bytes;
+    P.rowB = rowB_fast;
+    for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
+    if (fast) {
+        // Groups with dy >= 1 conflict with neighbouring columns only two
+        // groups back (pair models with up to three shells), so they may
+        // start once the neighbours have finished the group before last.
+        for (int g = 0; g < pl.G; ++g) P.lag[g] = (g % pl.Ly) == 0 ? 1 : 2;
+    }
     P.skip_tile = (int)debug_skip_tile();
     P.seed = seed;
     P.timeout_ns = debug_timeout_ns();
@@ -735,9 +1313,39 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     P.CB = std::min(P.CB, P.TY * P.TZ);
     P.ntiles = tile0;
 
-    // D[m][A][B][q] = V_m(B, q) - V_m(A, q), padded to 8 species
+    // D[m][A][B][q] = V_m(B, q) - V_m(A, q), padded to 8 species.  The fast
+    // kernel reads D'[q] = D[q] - D[ST-1] for q < ST-1 (ST = its species
+    // template: 2, 5 or 8) and, in entry 7 of shells 1 and 2, -8 sum D'.
     const int S = P.S;
-    for (int mm = 0; mm < m->nshells; ++mm)
+    if (fast) {
+        const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
+        for (int mm = 0; mm < m->nshells; ++mm)
+            for (int A = 0; A < S; ++A)
+                for (int B = 0; B < S; ++B) {
+                    auto Dv = [&](int q) -> double {
+                        if (q >= S) return 0.0;
+                        if (IS_INT) return (double)m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
+                        return (double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q];
+                    };
+                    const int base = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+                    double bias = 0.0;
+                    for (int q = 0; q < ST - 1; ++q) {
+                        const double d = Dv(q) - Dv(ST - 1);
+                        if (IS_INT)
+                            P.D.di[base + q] = (int)d;
+                        else
+                            P.D.df[base + q] = (float)d;
+                        bias += d;
+                    }
+                    if (mm < 2) {
+                        if (IS_INT)
+                            P.D.di[base + 7] = (int)(-8.0 * bias);
+                        else
+                            P.D.df[base + 7] = (float)(-8.0 * bias);
+                    }
+                }
+    }
+    for (int mm = 0; mm < (fast ? 0 : m->nshells); ++mm)
         for (int A = 0; A < S; ++A)
             for (int B = 0; B < S; ++B)
                 for (int q = 0; q < S; ++q) {
@@ -818,9 +1426,8 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
         e = cudaMemsetAsync(scr, 0, off_tab, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
         void *args[] = {(void *)&P};
-        e = cudaLaunchCooperativeKernel((const void *)k_sweep_pair<IS_INT>, dim3(pl.grid), dim3(pl.threads), args,
-                                        pl.smem, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(k_sweep_pair)");
+        e = cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(sweep)");
     }
     return SMC_OK;
 }
