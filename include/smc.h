@@ -121,6 +121,33 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
                      uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT,
                      double *e_acc, int64_t *n_acc, cudaStream_t stream);
 
+/* Allocation-free variant of smc_sweep for callers that cannot call
+ * cudaMalloc: code running while a CUDA graph is being captured (where an
+ * allocation is an error), or applications whose device memory is owned by
+ * their own allocator and must not see a library allocate on its own.  The
+ * paper has no counterpart; it is a deployment convenience.
+ *
+ * It runs the same kernels as smc_sweep for SMC_PAIR_F32 models (same
+ * trajectory and e_acc for the same arguments and tuning), but its scratch
+ * memory (progress flags and partial sums of at most 16384 link-cell tiles)
+ * lives in a fixed 320 KB array inside the library that every GPU which loads
+ * the library keeps until the process exits.  It calls no cudaMalloc,
+ * cudaFree or allocating library routine.
+ *   status  device int32, nullable: set to 0 at the start of the call and to
+ *           SMC_ERR_TIMEOUT if a device-side progress wait timed out.
+ *   other arguments as for smc_sweep.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) while that device is current; make that first call
+ * before any stream capture.  Every call shares the array and rewrites it, so
+ * calls that overlap on the GPU (different streams, or a second process
+ * thread) race; serialise them on one stream.
+ * Errors: SMC_ERR_ARG as smc_sweep; SMC_ERR_UNSUPPORTED for other model
+ * kinds or for lattices needing more than 16384 tiles; SMC_ERR_CUDA. */
+smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int8_t *occ,
+                             uint64_t seed, uint32_t replica, uint64_t sweep0, int32_t nsweeps,
+                             const double *kT, double *e_acc, int64_t *n_acc, int32_t *status,
+                             cudaStream_t stream);
+
 /* Independent replicas of possibly different sizes (each its own lattice and
  * occupancy, shared model), advanced together in one persistent launch per
  * chunk of sweeps.  Replica r uses RNG replica index replica0 + r, so it

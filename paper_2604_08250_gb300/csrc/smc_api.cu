@@ -345,6 +345,39 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
     return launch_pair_sweep(1, lat, model, occs, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
 
+smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                             uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
+                             int64_t *n_acc, int32_t *status, cudaStream_t stream)
+{
+    API_LOCK;
+    if (!lattice_valid(lat, false)) return SMC_ERR_ARG;
+    if (!model_valid(lat, model)) return SMC_ERR_ARG;
+    if (model->kind != SMC_PAIR_F32) {
+        set_error("smc_sweep_noalloc supports SMC_PAIR_F32 models only");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    if (!occ || nsweeps < 0 || (nsweeps > 0 && !kT)) {
+        set_error("occ and kT must be non-NULL and nsweeps >= 0");
+        return SMC_ERR_ARG;
+    }
+    if (sweep0 + (uint64_t)nsweeps > 0xFFFFFFFFFFFFFFFEull || sweep0 + (uint64_t)nsweeps < sweep0) {
+        set_error("sweep indices reach the reserved values 2^64-2, 2^64-1");
+        return SMC_ERR_ARG;
+    }
+    for (int i = 0; i < nsweeps; ++i)
+        if (!(kT[i] > 0.0)) {
+            set_error("kT[%d] = %g is invalid (must be > 0)", i, kT[i]);
+            return SMC_ERR_ARG;
+        }
+    if ((long long)nsweeps * 2 * lc_edge(lat->ny) * lc_edge(lat->nz) >= (1LL << 31)) {
+        set_error("too many sweeps in one call");
+        return SMC_ERR_ARG;
+    }
+    if (nsweeps == 0) return SMC_OK;
+    return launch_pair_sweep_noalloc(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, status,
+                                     stream);
+}
+
 smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model *model, int8_t *const *occ,
                              uint64_t seed, uint32_t replica0, uint64_t sweep0, int32_t nsweeps, const double *kT,
                              double *e_acc, int64_t *n_acc, cudaStream_t stream)

@@ -144,6 +144,9 @@ bool model_valid(const smc_lattice *lat, const smc_model *m);
 smc_status launch_pair_sweep(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ,
                              uint64_t seed, uint32_t replica0, uint64_t sweep0, int nsweeps,
                              const double *kT, double *e_acc, int64_t *n_acc, cudaStream_t stream);
+smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                                     uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT,
+                                     double *e_acc, int64_t *n_acc, int32_t *status, cudaStream_t stream);
 smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                                  uint32_t replica, uint64_t sweep, int k, double kT, float *dE,
                                  uint8_t *acc, cudaStream_t stream);

@@ -1524,4 +1524,166 @@ smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int
     return trace_impl<false>(lat, m, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free sweep (smc_sweep_noalloc).  Some callers cannot call
+// cudaMalloc -- code that runs while a CUDA graph is being captured, or hosts
+// whose memory is owned by their own pool and must not see the library
+// allocate behind its back -- so this entry point keeps its scratch (progress
+// flags, per-tile partial sums, ticket and abort words) in the file-scope
+// array below instead of the library workspace.  Every GPU that loads the
+// library holds the array until the process exits.  Host code must not use
+// the array's name as a device address: its device address is looked up once
+// per device with cudaGetSymbolAddress while that device is current.
+// ---------------------------------------------------------------------------
+constexpr int kNoAllocMaxTiles = 16384;
+constexpr size_t kNoAllocFlagsOff = 256;
+constexpr size_t kNoAllocPartEOff = kNoAllocFlagsOff + (size_t)kNoAllocMaxTiles * 4;
+constexpr size_t kNoAllocPartNOff = kNoAllocPartEOff + (size_t)kNoAllocMaxTiles * 8;
+constexpr size_t kNoAllocBytes = kNoAllocPartNOff + (size_t)kNoAllocMaxTiles * 8;  // 320 KB + 256 B
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+static unsigned char *g_noalloc_ptr[64];  // device address per device, set on first use
+
+smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                                     uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT,
+                                     double *e_acc, int64_t *n_acc, int32_t *status, cudaStream_t stream)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= 64) {
+        set_error("device index %d out of range", dev);
+        return SMC_ERR_UNSUPPORTED;
+    }
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+        g_noalloc_ptr[dev] = (unsigned char *)ptr;
+    }
+    unsigned char *scr = g_noalloc_ptr[dev];
+    // Device attributes the plans need, queried directly (no workspace).
+    Workspace ws;
+    int sms = 0, optin = 0;
+    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
+    ws.device = dev;
+    ws.num_sms = sms;
+    ws.smem_optin = (size_t)optin;
+
+    const int R = 1;
+    const smc_lattice *lats = lat;
+    int8_t *occs[1] = {occ};
+    const bool fast = lc_edge(lat->nx) == 4 && lc_edge(lat->ny) == 4 && lc_edge(lat->nz) == 4 && lat->nx <= 1024 &&
+                      ((uintptr_t)occ % 4 == 0);
+    const int rowB_fast = ((lat->nx + 15) & ~15) + 32;
+    Plan pl;
+    smc_status st = fast ? make_fast_plan<false>(R, lats, occs, &ws, m->nshells, rowB_fast, lat->nx, pl)
+                         : make_plan<false>(R, lats, &ws, pl);
+    if (st != SMC_OK) return st;
+    if (pl.ntiles > kNoAllocMaxTiles) {
+        set_error("smc_sweep_noalloc: %d link-cell tiles exceed the scratch limit of %d (use a larger tile_y/tile_z "
+                  "tuning or smc_sweep)", pl.ntiles, kNoAllocMaxTiles);
+        return SMC_ERR_UNSUPPORTED;
+    }
+
+    static SweepParams P;
+    memset(&P, 0, sizeof P);
+    P.R = 1;
+    P.G = pl.G;
+    P.Lx = pl.Lx;
+    P.Ly = pl.Ly;
+    P.Lz = pl.Lz;
+    P.TY = pl.TY;
+    P.TZ = pl.TZ;
+    P.CB = std::min(pl.CB, pl.TY * pl.TZ);
+    P.nshells = m->nshells;
+    P.S = lat->nspecies;
+    P.tpc = pl.tpc;
+    P.warp_bytes = pl.warp_bytes;
+    P.rowB = rowB_fast;
+    for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
+    if (fast)
+        for (int g = 0; g < pl.G; ++g) P.lag[g] = (g % pl.Ly) == 0 ? 1 : 2;
+    P.skip_tile = -1;
+    P.seed = seed;
+    P.timeout_ns = debug_timeout_ns();
+    RepDesc &d = P.rep[0];
+    d.occ = occ;
+    d.e_acc = e_acc;
+    d.n_acc = (long long *)n_acc;
+    d.nx = lat->nx;
+    d.ny = lat->ny;
+    d.nz = lat->nz;
+    d.NLx = d.nx / pl.Lx;
+    d.NLy = d.ny / pl.Ly;
+    d.NLz = d.nz / pl.Lz;
+    d.NTy = (d.NLy + pl.TY - 1) / pl.TY;
+    d.NTz = (d.NLz + pl.TZ - 1) / pl.TZ;
+    d.tile0 = 0;
+    d.rep = replica;
+    d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ % 16 == 0);
+    P.ntiles = d.NTy * d.NTz;
+    const int S = P.S;
+    if (fast) {
+        const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
+        for (int mm = 0; mm < m->nshells; ++mm)
+            for (int A = 0; A < S; ++A)
+                for (int B = 0; B < S; ++B) {
+                    auto Dv = [&](int q) -> double {
+                        if (q >= S) return 0.0;
+                        return (double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q];
+                    };
+                    const int base = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+                    double bias = 0.0;
+                    for (int q = 0; q < ST - 1; ++q) {
+                        const double dq = Dv(q) - Dv(ST - 1);
+                        P.D.df[base + q] = (float)dq;
+                        bias += dq;
+                    }
+                    if (mm < 2) P.D.df[base + 7] = (float)(-8.0 * bias);
+                }
+    } else {
+        for (int mm = 0; mm < m->nshells; ++mm)
+            for (int A = 0; A < S; ++A)
+                for (int B = 0; B < S; ++B)
+                    for (int q = 0; q < S; ++q)
+                        P.D.df[((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q] =
+                            (float)((double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q]);
+    }
+    bool constant = true;
+    for (int t = 1; t < nsweeps; ++t)
+        if (kT[t] != kT[0]) constant = false;
+    const int chunk = constant ? nsweeps : kMaxBeta;
+    P.flags = (uint32_t *)(scr + kNoAllocFlagsOff);
+    P.part_e = (double *)(scr + kNoAllocPartEOff);
+    P.part_n = (long long *)(scr + kNoAllocPartNOff);
+    P.ticket = (unsigned *)(scr + 0);
+    P.abort_flag = (int *)(scr + 4);
+    P.status = status ? (int *)status : (int *)(scr + 8);
+    P.tab = nullptr;
+    if (status) {
+        e = cudaMemsetAsync(status, 0, sizeof(int32_t), stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
+    }
+    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+        const int nc = std::min(chunk, nsweeps - t0);
+        P.sweep0 = sweep0 + (uint64_t)t0;
+        P.nsweeps = nc;
+        P.beta_stride = constant ? 0 : nc;
+        for (int t = 0; t < (constant ? 1 : nc); ++t) P.temp.beta[t] = (float)(1.0 / kT[t0 + t]);
+        // the array keeps the last call's contents: zero what must start at zero
+        e = cudaMemsetAsync(scr, 0, kNoAllocFlagsOff + (size_t)P.ntiles * 4, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartEOff, 0, (size_t)P.ntiles * 8, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartNOff, 0, (size_t)P.ntiles * 8, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc scratch)");
+        void *args[] = {(void *)&P};
+        e = cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(no-alloc sweep)");
+    }
+    return SMC_OK;
+}
+
 }  // namespace smc

@@ -21,7 +21,7 @@ DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH = 1, 2
 MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 
 # Every symbol declared in include/smc.h.
-EXPORTS = ("smc_init_lattice", "smc_sweep", "smc_sweep_batched", "smc_sro", "smc_energy", "smc_grad_size",
+EXPORTS = ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy", "smc_grad_size",
            "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check", "smc_last_error",
            "smc_set_tuning", "smc_debug_set")
 
@@ -67,6 +67,8 @@ def lib():
         L.smc_init_lattice.argtypes = [P(_Lat), P(C.c_int64), C.c_uint64, C.c_uint32, vp, vp]
         L.smc_sweep.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
                                 P(C.c_double), vp, vp, vp]
+        L.smc_sweep_noalloc.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
+                                         P(C.c_double), vp, vp, vp, vp]
         L.smc_sweep_batched.argtypes = [C.c_int32, P(_Lat), P(_Model), P(vp), C.c_uint64, C.c_uint32,
                                         C.c_uint64, C.c_int32, P(C.c_double), vp, vp, vp]
         L.smc_sro.argtypes = [P(_Lat), C.c_int32, vp, vp, vp, vp]
@@ -80,7 +82,7 @@ def lib():
         L.smc_check.argtypes = [vp]
         L.smc_set_tuning.argtypes = [P(_Tuning)]
         L.smc_debug_set.argtypes = [C.c_int32, C.c_int64]
-        for name in ("smc_init_lattice", "smc_sweep", "smc_sweep_batched", "smc_sro", "smc_energy",
+        for name in ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy",
                      "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check",
                      "smc_set_tuning", "smc_debug_set"):
             getattr(L, name).restype = C.c_int
