@@ -1,0 +1,153 @@
+// sweep_common.cuh -- parameter block and warp-level helpers shared by the
+// pair and MLP sweep kernels.
+#pragma once
+
+#include "smc_common.cuh"
+
+namespace smc {
+
+constexpr int kMaxBeta = 1024;
+constexpr int kMaxGroups = 64;
+
+// MLP weights as the kernels read them (device memory, one copy per call):
+// W1 padded from 20 to 32 inputs, BF16 bit patterns, row = output unit; W2
+// BF16; W3, biases FP32 (W3 widened exactly from BF16).
+struct MlpBlock {
+    uint16_t w1[64 * 32];
+    uint16_t w2[64 * 64];
+    float b1[64], b2[64], w3[64];
+    float b3;
+    float pad[3];
+};
+
+struct RepDesc {
+    int8_t *occ;
+    double *e_acc;
+    long long *n_acc;
+    int nx, ny, nz;
+    int NLx, NLy, NLz;
+    int NTy, NTz;  // tiles along y, z
+    int tile0;     // first global tile of this replica
+    uint32_t rep;  // RNG replica index
+    int vec;       // rows are 16-byte aligned: copy with 16-byte transactions
+};
+
+struct SweepParams {
+    int R, ntiles, G;
+    int Lx, Ly, Lz;
+    int TY, TZ, CB;
+    int nshells, S;
+    int nsweeps;
+    int beta_stride;  // 0: one value per replica; else values per (replica, sweep)
+    int tpc;          // accumulator slots per CTA (>= tiles owned by any CTA)
+    int skip_tile;
+    int pad0;
+    uint64_t seed, sweep0;
+    long long timeout_ns;
+    uint32_t *flags;
+    double *part_e;
+    long long *part_n;
+    unsigned *ticket;
+    int *abort_flag;
+    int *status;
+    const uint32_t *tab;  // integer acceptance tables
+    int lag[kMaxGroups];  // group g may start once neighbours completed g+1-lag[g] groups
+    int warp_bytes;       // fast kernel: shared-memory bytes per warp
+    int nap_cap;          // fast kernel: longest sleep between progress polls (ns)
+    int kind;             // model kind (SMC_PAIR_I32 .. SMC_PAIR_F32_MLP_BF16)
+    const MlpBlock *mlpw; // MLP weights (device), MLP kinds only
+    float *ecache;        // per-site MLP energy f(x_i) (device, N floats), MLP kinds only
+    int rowB;             // fast kernel: row stride in shared memory
+    union {
+        float beta[kMaxBeta];
+        int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
+    } temp;
+    union {
+        int di[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
+        float df[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
+    } D;  // D[m][A][B][q] = V_m(B, q) - V_m(A, q)
+    RepDesc rep[kMaxReplicas];
+};
+static_assert(sizeof(SweepParams) < 32000, "kernel parameter block too large");
+
+constexpr int kDEntries = kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies;
+
+
+template <bool IS_INT>
+struct Acc;
+template <>
+struct Acc<true> {
+    using T = int;
+};
+template <>
+struct Acc<false> {
+    using T = float;
+};
+
+template <bool IS_INT>
+__device__ __forceinline__ bool metropolis(typename Acc<IS_INT>::T dE, uint32_t r, float beta, const uint32_t *tab,
+                                           int2 ti)
+{
+    if constexpr (IS_INT) {
+        if (dE <= 0) return true;
+        return (int)dE < ti.y && r < __ldg(tab + ti.x + (int)dE);
+    } else {
+        const float u = ((float)r + 0.5f) * 1.862645149230957e-09f;  // 2^-29
+        return (dE <= 0.f) | (u < expf(-beta * (float)dE));
+    }
+}
+
+template <typename V>
+__device__ __forceinline__ V warp_sum(V v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+extern __shared__ __align__(16) unsigned char g_smem[];
+
+#define SM8(off) ((uint32_t)g_smem[(off)])
+// Bounded wait of one warp for the 8 neighbouring tiles of (ty, tz).
+static __device__ bool wait_tile_warp(const SweepParams &P, const RepDesc &D, int ty, int tz, uint32_t need, int lane)
+{
+    const uint32_t *fp = nullptr;
+    if (lane < 9 && lane != 4) {
+        int nty = ty + (lane % 3) - 1, ntz = tz + (lane / 3) - 1;
+        nty = nty < 0 ? nty + D.NTy : (nty >= D.NTy ? nty - D.NTy : nty);
+        ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
+        fp = P.flags + D.tile0 + ntz * D.NTy + nty;
+    }
+    const uint64_t t0 = global_ns();
+    unsigned nap = 32;
+    for (;;) {
+        const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        int stop = 0;
+        if (lane == 0) {
+            if (ld_volatile_i32(P.abort_flag)) {
+                stop = 1;
+            } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
+                atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+                atomicExch(P.abort_flag, 1);
+                stop = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        __nanosleep(nap);
+        nap = nap < (unsigned)P.nap_cap ? nap * 2 : (unsigned)P.nap_cap;
+    }
+}
+
+// Stores v at x (in [-1, nx]) of the halo-framed row whose body starts at
+// byte offset `row`, and at the cell's halo copy when it is one of the first
+// or last four cells (elsewhere the second store repeats the first).
+__device__ __forceinline__ void halo_store(uint32_t row, int x, int nx, unsigned char v)
+{
+    const int xr = x < 0 ? x + nx : (x >= nx ? x - nx : x);
+    const int xm = xr < 4 ? xr + nx : (xr >= nx - 4 ? xr - nx : xr);
+    g_smem[row + xr] = v;
+    g_smem[row + xm] = v;
+}
+
+}  // namespace smc

@@ -28,60 +28,9 @@
 #include <cstring>
 #include <vector>
 
-#include "smc_common.cuh"
+#include "sweep_common.cuh"
 
 namespace smc {
-
-constexpr int kMaxBeta = 1024;
-constexpr int kMaxGroups = 64;
-
-struct RepDesc {
-    int8_t *occ;
-    double *e_acc;
-    long long *n_acc;
-    int nx, ny, nz;
-    int NLx, NLy, NLz;
-    int NTy, NTz;  // tiles along y, z
-    int tile0;     // first global tile of this replica
-    uint32_t rep;  // RNG replica index
-    int vec;       // rows are 16-byte aligned: copy with 16-byte transactions
-};
-
-struct SweepParams {
-    int R, ntiles, G;
-    int Lx, Ly, Lz;
-    int TY, TZ, CB;
-    int nshells, S;
-    int nsweeps;
-    int beta_stride;  // 0: one value per replica; else values per (replica, sweep)
-    int tpc;          // accumulator slots per CTA (>= tiles owned by any CTA)
-    int skip_tile;
-    int pad0;
-    uint64_t seed, sweep0;
-    long long timeout_ns;
-    uint32_t *flags;
-    double *part_e;
-    long long *part_n;
-    unsigned *ticket;
-    int *abort_flag;
-    int *status;
-    const uint32_t *tab;  // integer acceptance tables
-    int lag[kMaxGroups];  // group g may start once neighbours completed g+1-lag[g] groups
-    int warp_bytes;       // fast kernel: shared-memory bytes per warp
-    int rowB;             // fast kernel: row stride in shared memory
-    union {
-        float beta[kMaxBeta];
-        int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
-    } temp;
-    union {
-        int di[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
-        float df[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
-    } D;  // D[m][A][B][q] = V_m(B, q) - V_m(A, q)
-    RepDesc rep[kMaxReplicas];
-};
-static_assert(sizeof(SweepParams) < 32000, "kernel parameter block too large");
-
-constexpr int kDEntries = kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies;
 
 // Slot of row y0 + delta inside a window [lo, lo + W) along an axis of n cells.
 // For n >= W the window rows are distinct and slot = delta - lo; otherwise the
@@ -131,17 +80,6 @@ struct ColView {
     {
         return oth + (tz.slot(dz) * ty.cnt + ty.slot(dy)) * rowB;
     }
-};
-
-template <bool IS_INT>
-struct Acc;
-template <>
-struct Acc<true> {
-    using T = int;
-};
-template <>
-struct Acc<false> {
-    using T = float;
 };
 
 // dE of swapping the trial site a (own sublattice, x) with its partner in
@@ -206,27 +144,6 @@ __device__ __forceinline__ typename Acc<IS_INT>::T trial_dE(const View &cv, int 
             }
     }
     return dE;
-}
-
-template <bool IS_INT>
-__device__ __forceinline__ bool metropolis(typename Acc<IS_INT>::T dE, uint32_t r, float beta, const uint32_t *tab,
-                                           int2 ti)
-{
-    if (dE <= 0) return true;
-    if constexpr (IS_INT) {
-        return (int)dE < ti.y && r < __ldg(tab + ti.x + (int)dE);
-    } else {
-        const float u = ((float)r + 0.5f) * 1.862645149230957e-09f;  // 2^-29
-        return u < expf(-beta * (float)dE);
-    }
-}
-
-template <typename V>
-__device__ __forceinline__ V warp_sum(V v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
 }
 
 // Waits until the 8 neighbouring tiles of (ty, tz) have completed `need`
@@ -578,35 +495,48 @@ __device__ __forceinline__ typename Acc<IS_INT>::T dot_diff(uint32_t Ha, uint32_
     return acc;
 }
 
-extern __shared__ __align__(16) unsigned char g_smem[];
-
-#define SM8(off) ((uint32_t)g_smem[(off)])
 #define NIB(v) (1u << ((v) << 2))
 
 // po: byte offsets (in g_smem) of the 9 trial-sublattice row bodies; pt: of
 // the partner block (row index 0).  Returns dE; A, B and the partner's
 // row offset and x through references.
+// Shared-memory row index of partner-sublattice slot (sy, sz).  Two-shell
+// models store the 12 slots they can read (the 4x4 window without its
+// corners) compactly; three-shell models store all 16.
+template <int NSH>
+__host__ __device__ __forceinline__ int pslot(int sy, int sz)
+{
+    if (NSH >= 3) return 9 + sz * 4 + sy;
+    return 9 + (sz == 0 ? sy - 1 : (sz == 1 ? 2 + sy : (sz == 2 ? 6 + sy : 9 + sy)));
+}
+
+// po: byte offsets (in g_smem) of the 9 trial-sublattice row bodies; col0:
+// offset of row 0's body.  Returns dE (exactly 0 when a and b hold the same
+// species: the table rows D'(A, A) vanish); A, B and the partner's row
+// offset and x through references.
 template <bool IS_INT, int NSH, int S, int SOFF>
-__device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, uint32_t pt, uint32_t rb, int x,
+__device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, uint32_t col0, uint32_t rb, int x,
                                                            int dir, uint32_t dt, int &A, int &B, uint32_t &brow,
                                                            int &xb)
 {
     using T = typename Acc<IS_INT>::T;
     const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
     A = (int)(SM8(po[4] + x) & 7u);
-    const uint32_t rbp = pt + (uint32_t)((kz + 1) * 4 + (ky + 1)) * rb;  // partner's row
+    // partner's row: slot (ky+1, kz+1) = 12 + 4 kz + ky (two shells) or 14 + 4 kz + ky
+    const uint32_t rbp = col0 + (uint32_t)((NSH >= 3 ? 14 : 12) + 4 * kz + ky) * rb;
     xb = x + SOFF + kx;
     B = (int)(SM8(rbp + xb) & 7u);
     brow = rbp;
-    if (A == B) return T(0);
     // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
     // trial-sublattice neighbours plus a.  A species >= 8 (invalid input)
     // shifts the 1 out of the word and is ignored.
     uint32_t H1 = 0x88888888u - NIB(B) + NIB(A);
     {
-        const uint32_t xa = pt + x + SOFF;
-        H1 += NIB(SM8(xa + 5 * rb)) + NIB(SM8(xa + 5 * rb + 1)) + NIB(SM8(xa + 6 * rb)) + NIB(SM8(xa + 6 * rb + 1)) +
-              NIB(SM8(xa + 9 * rb)) + NIB(SM8(xa + 9 * rb + 1)) + NIB(SM8(xa + 10 * rb)) + NIB(SM8(xa + 10 * rb + 1));
+        const uint32_t xa = col0 + x + SOFF;
+        const uint32_t r11 = xa + pslot<NSH>(1, 1) * rb, r21 = xa + pslot<NSH>(2, 1) * rb;
+        const uint32_t r12 = xa + pslot<NSH>(1, 2) * rb, r22 = xa + pslot<NSH>(2, 2) * rb;
+        H1 += NIB(SM8(r11)) + NIB(SM8(r11 + 1)) + NIB(SM8(r21)) + NIB(SM8(r21 + 1)) + NIB(SM8(r12)) +
+              NIB(SM8(r12 + 1)) + NIB(SM8(r22)) + NIB(SM8(r22 + 1));
         const uint32_t ob = po[0] + (uint32_t)(kz * 3 + ky) * rb + x + kx - 1;
         H1 -= NIB(SM8(ob)) + NIB(SM8(ob + 1)) + NIB(SM8(ob + rb)) + NIB(SM8(ob + rb + 1)) + NIB(SM8(ob + 3 * rb)) +
               NIB(SM8(ob + 3 * rb + 1)) + NIB(SM8(ob + 4 * rb)) + NIB(SM8(ob + 4 * rb + 1));
@@ -615,13 +545,16 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
     const T *D1 = Dt + (A * kMaxSpecies + B) * kMaxSpecies;
     T dE = dot_biased<IS_INT, S>(H1, D1);
     const uint32_t bx = rbp + xb;
+    // partner rows one slot down / up in z (compact layout: 3 or 4 rows apart)
+    const uint32_t zdn = NSH >= 3 ? 4 * rb : 3 * rb + (uint32_t)kz * rb;
+    const uint32_t zup = NSH >= 3 ? 4 * rb : 4 * rb - (uint32_t)kz * rb;
     if (NSH >= 2) {
         const uint32_t ax = po[4] + x;
         uint32_t H2 = 0x88888888u;
         H2 += NIB(SM8(ax - 1)) + NIB(SM8(ax + 1)) + NIB(SM8(po[3] + x)) + NIB(SM8(po[5] + x)) + NIB(SM8(po[1] + x)) +
               NIB(SM8(po[7] + x));
-        H2 -= NIB(SM8(bx - 1)) + NIB(SM8(bx + 1)) + NIB(SM8(bx - rb)) + NIB(SM8(bx + rb)) + NIB(SM8(bx - 4 * rb)) +
-              NIB(SM8(bx + 4 * rb));
+        H2 -= NIB(SM8(bx - 1)) + NIB(SM8(bx + 1)) + NIB(SM8(bx - rb)) + NIB(SM8(bx + rb)) + NIB(SM8(bx - zdn)) +
+              NIB(SM8(bx + zup));
         dE += dot_biased<IS_INT, S>(H2, D1 + kMaxSpecies * kMaxSpecies * kMaxSpecies);
     }
     if (NSH >= 3) {
@@ -639,45 +572,40 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
 }
 #undef NIB
 
-// Stores v at x (in [-1, nx]) of the halo-framed row whose body starts at
-// byte offset `row`, keeping the halo copies of the first and last four
-// cells in step.
-__device__ __forceinline__ void halo_store(uint32_t row, int x, int nx, unsigned char v)
+template <bool IS_INT, int NSH, int S, int SOFF, int KU, bool GUARD>
+__device__ __forceinline__ void fast_trials(const SweepParams &P, const uint32_t *po, uint32_t col0, uint32_t rb,
+                                            const uint32_t *wsm, int k0, int nk, int NLx, int nx, int dx, int lane,
+                                            float beta, int2 ti, uint32_t dt, typename Acc<IS_INT>::T &accE,
+                                            double &accEd, long long &accN)
 {
-    const int xr = x < 0 ? x + nx : (x >= nx ? x - nx : x);
-    g_smem[row + xr] = v;
-    if (xr < 4) g_smem[row + xr + nx] = v;
-    if (xr >= nx - 4) g_smem[row + xr - nx] = v;
-}
-
-// Bounded wait of one warp for the 8 neighbouring tiles of (ty, tz).
-__device__ bool wait_tile_warp(const SweepParams &P, const RepDesc &D, int ty, int tz, uint32_t need, int lane)
-{
-    const uint32_t *fp = nullptr;
-    if (lane < 9 && lane != 4) {
-        int nty = ty + (lane % 3) - 1, ntz = tz + (lane / 3) - 1;
-        nty = nty < 0 ? nty + D.NTy : (nty >= D.NTy ? nty - D.NTy : nty);
-        ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
-        fp = P.flags + D.tile0 + ntz * D.NTy + nty;
-    }
-    const uint64_t t0 = global_ns();
-    unsigned nap = 32;
-    for (;;) {
-        const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
-        if (__all_sync(0xffffffffu, ok)) return true;
-        int stop = 0;
-        if (lane == 0) {
-            if (ld_volatile_i32(P.abort_flag)) {
-                stop = 1;
-            } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
-                atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
-                atomicExch(P.abort_flag, 1);
-                stop = 1;
-            }
+    using T = typename Acc<IS_INT>::T;
+    T dE[KU];
+    int A[KU], B[KU], xb[KU], xs[KU];
+    uint32_t brow[KU];
+    bool acc[KU];
+#pragma unroll
+    for (int u = 0; u < KU; ++u) {
+        const int k = k0 + u, i = lane + 32 * k;
+        acc[u] = false;
+        if (!GUARD || (k < nk && i < NLx)) {
+            const int x = 4 * i + dx;
+            xs[u] = x;
+            const uint32_t w = wsm[(k * 4 + dx) * 32 + lane];
+            dE[u] = fast_dE<IS_INT, NSH, S, SOFF>(po, col0, rb, x, (int)(w >> kRBits), dt, A[u], B[u], brow[u], xb[u]);
+            acc[u] = metropolis<IS_INT>(dE[u], w & kRMask, beta, P.tab, ti);
         }
-        if (__shfl_sync(0xffffffffu, stop, 0)) return false;
-        __nanosleep(nap);
-        nap = nap < 512 ? nap * 2 : 512;
+    }
+#pragma unroll
+    for (int u = 0; u < KU; ++u) {
+        if (acc[u]) {
+            halo_store(po[4], xs[u], nx, (unsigned char)B[u]);
+            halo_store(brow[u], xb[u], nx, (unsigned char)A[u]);
+            if constexpr (IS_INT)
+                accE += dE[u];
+            else
+                accEd += (double)dE[u];
+            accN += 1;
+        }
     }
 }
 
@@ -686,34 +614,38 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
                                             uint64_t sweep, float beta, int2 ti, uint32_t dt, int lane,
                                             typename Acc<IS_INT>::T &accE, double &accEd, long long &accN)
 {
-    using T = typename Acc<IS_INT>::T;
     constexpr int sub = SOFF == -1 ? 0 : 1;
+    constexpr int rows = NSH >= 3 ? 25 : 21;
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
     const uint32_t rb = (uint32_t)P.rowB;
-    const int rows = NSH >= 3 ? 25 : 21;
     const bool vec = RD.vec != 0;
     // ---- per-row source (global) and destination (shared) of this column:
-    // lane rr computes row rr once; others read it by shuffle ----
+    // lane r computes row r once; the others read it by shuffle ----
     const int8_t *my_src = RD.occ;
     uint32_t my_dst = 0;
     if (lane < rows) {
-        int slot, gsub, dy, dz;
+        int gsub, dy, dz;
         if (lane < 9) {
-            slot = lane;
             dy = lane % 3 - 1;
             dz = lane / 3 - 1;
             gsub = sub;
         } else {
-            int k = lane - 9;
-            if (NSH < 3) k += (k >= 2) + (k >= 10) + 1;  // skip corner slots 0, 3, 12, 15
-            slot = 9 + k;
-            dy = (k & 3) - 1 + SOFF;
-            dz = (k >> 2) - 1 + SOFF;
+            const int k = lane - 9;
+            int sy, sz;
+            if (NSH >= 3) {
+                sy = k & 3;
+                sz = k >> 2;
+            } else {
+                sz = k < 2 ? 0 : (k < 6 ? 1 : (k < 10 ? 2 : 3));
+                sy = k < 2 ? k + 1 : (k < 6 ? k - 2 : (k < 10 ? k - 6 : k - 9));
+            }
+            dy = sy - 1 + SOFF;
+            dz = sz - 1 + SOFF;
             gsub = 1 - sub;
         }
         const int gy = wrapc(y0 + dy, ny), gz = wrapc(z0 + dz, nz);
         my_src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
-        my_dst = col + (uint32_t)slot * rb + 16;
+        my_dst = col + (uint32_t)lane * rb + 16;
     }
     // ---- stage the rows (L2-only copies: never a stale L1 line) ----
     {
@@ -767,9 +699,9 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
     uint32_t po[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) po[r] = col + (uint32_t)r * rb + 16;
-    const uint32_t pt = col + 9 * rb + 16;
+    const uint32_t col0 = col + 16;
     // ---- Philox words of this lane's link cells, kept in shared memory ----
-    uint32_t *wsm = (uint32_t *)(g_smem + col + 25 * rb);  // [k][dx][lane]
+    uint32_t *wsm = (uint32_t *)(g_smem + col + (uint32_t)rows * rb + 16);  // [k][dx][lane]
     const int nk = (NLx + 31) >> 5;
     const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
     const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
@@ -787,27 +719,21 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
     // ---- the four mini-steps of the group ----
 #pragma unroll 1
     for (int dx = 0; dx < 4; ++dx) {
+        if (NLx == 32 * nk && (nk & 3) == 0) {
 #pragma unroll 1
-        for (int k = 0; k < nk; ++k) {
-            const int i = lane + 32 * k;
-            if (i < NLx) {
-                const int x = 4 * i + dx;
-                const uint32_t w = wsm[(k * 4 + dx) * 32 + lane];
-                int A, B, xb;
-                uint32_t brow;
-                const T dE = fast_dE<IS_INT, NSH, S, SOFF>(po, pt, rb, x, (int)(w >> kRBits), dt, A, B, brow, xb);
-                if (metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti)) {
-                    if (A != B) {
-                        halo_store(po[4], x, nx, (unsigned char)B);
-                        halo_store(brow, xb, nx, (unsigned char)A);
-                    }
-                    if constexpr (IS_INT)
-                        accE += dE;
-                    else
-                        accEd += (double)dE;
-                    accN += 1;
-                }
-            }
+            for (int kk = 0; kk < nk; kk += 4)
+                fast_trials<IS_INT, NSH, S, SOFF, 4, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
+                                                            dt, accE, accEd, accN);
+        } else if (NLx == 32 * nk) {
+#pragma unroll 1
+            for (int kk = 0; kk < nk; ++kk)
+                fast_trials<IS_INT, NSH, S, SOFF, 1, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
+                                                            dt, accE, accEd, accN);
+        } else {
+#pragma unroll 1
+            for (int kk = 0; kk < nk; ++kk)
+                fast_trials<IS_INT, NSH, S, SOFF, 1, true>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
+                                                           dt, accE, accEd, accN);
         }
         __syncwarp();
     }
@@ -831,7 +757,7 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
                     gz = z0;
                 } else {
                     const int sy = 1 + ((wr - 1) & 1), sz = 1 + ((wr - 1) >> 1);
-                    slot = 9 + sz * 4 + sy;
+                    slot = pslot<NSH>(sy, sz);
                     gsub = 1 - sub;
                     gy = wrapc(y0 + sy - 1 + SOFF, ny);
                     gz = wrapc(z0 + sz - 1 + SOFF, nz);
@@ -1039,7 +965,7 @@ namespace {
 
 struct Plan {
     int Lx, Ly, Lz, G;
-    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0;
+    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0, nap_cap = 128;
     size_t smem;
     const void *kernel = nullptr;
 };
@@ -1154,70 +1080,74 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
     (void)occ;
     const int S = lats[0].nspecies;
     pl.kernel = nshells >= 3 ? pick_fast<IS_INT, 3>(S) : pick_fast<IS_INT, 2>(S);
-    pl.threads = tu.threads ? std::min(tu.threads, 256) : 256;  // the kernel's launch bound
-    const int nwarps = pl.threads / 32;
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
     e = cudaFuncSetAttribute(pl.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    long long ncols = 0;
-    for (int r = 0; r < R; ++r) ncols += (long long)(lats[r].ny / 4) * (lats[r].nz / 4);
-    int nkmax = 1;
-    for (int r = 0; r < R; ++r) nkmax = std::max(nkmax, (lats[r].nx / 4 + 31) / 32);
-    const size_t rows_bytes = (size_t)25 * rowB + (size_t)512 * nkmax;
-    auto smem_for = [&](int tpc) {
-        return (size_t)kDEntries * 4 + (size_t)nwarps * (((size_t)16 * tpc + rows_bytes + 15) / 16 * 16);
-    };
-    // resident warps at one tile slot, to size the default tile
-    int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, pl.threads, smem_for(4));
-    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) {
-        set_error("fast sweep kernel does not fit on an SM");
-        return SMC_ERR_UNSUPPORTED;
+    int nkmax = 1, maxNLx = 1;
+    for (int r = 0; r < R; ++r) {
+        nkmax = std::max(nkmax, (lats[r].nx / 4 + 31) / 32);
+        maxNLx = std::max(maxNLx, lats[r].nx / 4);
     }
-    if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
-    const long long warps_res = (long long)per_sm * ws->num_sms * nwarps;
-    pl.TY = tu.tile_y;
-    pl.TZ = tu.tile_z;
-    if (pl.TY <= 0 || pl.TZ <= 0) {
-        int c = 1;
-        while ((long long)(c * 2) * warps_res <= ncols) c *= 2;
-        int ty = 1, tz = 1;
-        while (ty * tz < c) {
-            if (ty <= tz) ty *= 2; else tz *= 2;
-        }
-        if (pl.TY <= 0) pl.TY = ty;
-        if (pl.TZ <= 0) pl.TZ = tz;
-    }
+    const size_t rows_bytes = (size_t)(nshells >= 3 ? 25 : 21) * rowB + 16 + (size_t)512 * nkmax;
+    // one column per tile unless tuned: the smallest unit of work keeps the
+    // neighbour pipeline fullest
+    pl.TY = tu.tile_y > 0 ? tu.tile_y : 1;
+    pl.TZ = tu.tile_z > 0 ? tu.tile_z : 1;
     pl.ntiles = 0;
     for (int r = 0; r < R; ++r)
         pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
-    for (int tpc_guess = 1;; tpc_guess *= 2) {
-        const size_t smem = smem_for(tpc_guess);
-        if (smem > dyn_max) {
-            set_error("fast sweep: shared memory per CTA too large (%zu bytes)", smem);
-            return SMC_ERR_UNSUPPORTED;
-        }
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, pl.threads, smem);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        if (per_sm < 1) {
-            set_error("fast sweep kernel does not fit on an SM (smem %zu)", smem);
-            return SMC_ERR_UNSUPPORTED;
-        }
-        if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
-        const int want = (pl.ntiles + nwarps - 1) / nwarps;
-        pl.grid = std::min(want, per_sm * ws->num_sms);
-        pl.tpc = (pl.ntiles + pl.grid * nwarps - 1) / (pl.grid * nwarps);
-        if (pl.tpc <= tpc_guess) {
-            pl.smem = smem;
-            pl.warp_bytes = (int)(((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
-            pl.tpc = tpc_guess;
-            break;
+    // Total warps NW: all resident at once (cooperative launch); preferably a
+    // divisor of the tile count so that every warp owns as many tiles as the
+    // others (an unevenly loaded warp makes its neighbours wait).
+    const int cand[2] = {128, 256};
+    int best_nw = 0;
+    for (int ci = 0; ci < 2; ++ci) {
+        const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // the kernel's launch bound is 256
+        if (tu.threads && ci > 0) break;
+        const int nwarps = threads / 32;
+        for (int tpc_guess = 1;; tpc_guess *= 2) {
+            const size_t smem =
+                (size_t)kDEntries * 4 + (size_t)nwarps * (((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
+            if (smem > dyn_max) break;
+            int per_sm = 0;
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, threads, smem);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+            if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+            if (per_sm < 1) break;
+            const long long res = (long long)per_sm * ws->num_sms * nwarps;
+            long long nw = 0;
+            for (long long c = std::min<long long>(res, pl.ntiles) / nwarps * nwarps; c >= nwarps; c -= nwarps)
+                if (pl.ntiles % c == 0) {
+                    nw = c;
+                    break;
+                }
+            const long long fill = std::min<long long>(res, pl.ntiles) / nwarps * nwarps;
+            if (nw * 2 < fill) nw = fill;  // no good divisor: fill the GPU, accept the imbalance
+            if (nw < nwarps) nw = nwarps;
+            const int tpc = (int)((pl.ntiles + nw - 1) / nw);
+            if (tpc <= tpc_guess) {
+                if (nw > best_nw) {
+                    best_nw = (int)nw;
+                    pl.threads = threads;
+                    pl.grid = (int)(nw / nwarps);
+                    pl.tpc = tpc_guess;
+                    pl.smem = smem;
+                    pl.warp_bytes = (int)(((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
+                }
+                break;
+            }
         }
     }
+    if (best_nw == 0) {
+        set_error("fast sweep kernel does not fit on an SM (rows of %d bytes)", rowB);
+        return SMC_ERR_UNSUPPORTED;
+    }
+    // sleep between progress polls: short for small columns (latency-bound),
+    // longer for long ones (a tile-group takes tens of microseconds)
+    pl.nap_cap = maxNLx >= 64 ? 1024 : 128;
     pl.CB = 1;
     return SMC_OK;
 }
@@ -1253,7 +1183,7 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
         const smc_lattice &l = lats[r];
         fast = fast && lc_edge(l.nx) == 4 && lc_edge(l.ny) == 4 && lc_edge(l.nz) == 4 && l.nx <= 1024 &&
                ((uintptr_t)occ[r] % 4 == 0);
-        rowB_fast = std::max(rowB_fast, ((l.nx + 15) & ~15) + 32);  // body + 16-byte halo frame each side
+        rowB_fast = std::max(rowB_fast, ((l.nx + 15) & ~15) + 16);  // body at +16, 4-byte halos
         if (l.nx != same_nx) same_nx = -1;
     }
     if (current_tuning().threads && current_tuning().threads % 32) fast = false;
@@ -1280,6 +1210,7 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     P.S = lats[0].nspecies;
     P.tpc = pl.tpc;
     P.warp_bytes = pl.warp_bytes;
+    P.nap_cap = pl.nap_cap;
     P.rowB = rowB_fast;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast) {
@@ -1578,7 +1509,7 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     int8_t *occs[1] = {occ};
     const bool fast = lc_edge(lat->nx) == 4 && lc_edge(lat->ny) == 4 && lc_edge(lat->nz) == 4 && lat->nx <= 1024 &&
                       ((uintptr_t)occ % 4 == 0);
-    const int rowB_fast = ((lat->nx + 15) & ~15) + 32;
+    const int rowB_fast = ((lat->nx + 15) & ~15) + 16;
     Plan pl;
     smc_status st = fast ? make_fast_plan<false>(R, lats, occs, &ws, m->nshells, rowB_fast, lat->nx, pl)
                          : make_plan<false>(R, lats, &ws, pl);
@@ -1603,6 +1534,7 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     P.S = lat->nspecies;
     P.tpc = pl.tpc;
     P.warp_bytes = pl.warp_bytes;
+    P.nap_cap = pl.nap_cap;
     P.rowB = rowB_fast;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast)
