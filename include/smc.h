@@ -35,7 +35,16 @@
  * Energies.  Pair: E = sum_i 1/2 sum_m sum_{v in shell m} V_m(s_i, s_{i+v}).
  *   MLP: E = sum_i f(x_i), x_i = [onehot(s_i) | shell-1 counts | shell-2
  *   counts | shell-3 counts] (5 entries each), f = W3 silu(W2 silu(W1 x + b1)
- *   + b2) + b3 with BF16 weights, FP32 biases and FP32 accumulation.
+ *   + b2) + b3 (MLPNet, Sec. IV-B).  Evaluated on the tensor cores with BF16
+ *   weights and inputs (the integer features are exact in BF16), FP32
+ *   accumulation, FP32 biases and output layer; the layer-1 activations are
+ *   rounded to BF16 before the second product, and silu(z) is computed as
+ *   h + h tanh(h), h = z/2, with the hardware tanh approximation.  A site's f
+ *   is a fixed function of its features (the same bits wherever it is
+ *   evaluated), so the MLP chains sample the Boltzmann distribution of that
+ *   BF16 energy exactly; its departure from FP64 is what the tests report.
+ *   MLP sweeps and traces need every axis a multiple of 4 cells and >= 8,
+ *   nx <= 1024, and occ 4-byte aligned.
  *
  * Memory and streams.  Pointers marked "device" are caller-owned device
  * memory (for example torch tensors); "host" pointers are read during the
@@ -115,8 +124,12 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  *   e_acc   device double, nullable: += sum of dE of accepted trials (eV),
  *           summed in a fixed order (bit-reproducible).
  *   n_acc   device int64, nullable: += number of accepted trials.
+ * MLP models keep a per-site energy cache E[i] = f(x_i) in the workspace
+ * (4 N bytes), filled at the start of every call and updated over the
+ * interaction zone of every accepted swap, so a trial evaluates only the 40
+ * post-swap energies of its zone.
  * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP models
- * in this entry point when unavailable), SMC_ERR_CUDA. */
+ * on lattices the MLP kernel does not take), SMC_ERR_CUDA. */
 smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
                      uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT,
                      double *e_acc, int64_t *n_acc, cudaStream_t stream);
@@ -154,7 +167,8 @@ smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int
  * reproduces smc_sweep(..., replica0 + r, ...) bit for bit.
  *   lats    host [R];  occ  host [R] array of device pointers.
  *   kT      host [R][nsweeps] (eV).
- *   e_acc, n_acc  device [R], nullable. */
+ *   e_acc, n_acc  device [R], nullable.
+ * MLP models: R must be 1 (SMC_ERR_UNSUPPORTED otherwise). */
 smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model *model,
                              int8_t *const *occ, uint64_t seed, uint32_t replica0,
                              uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
@@ -169,8 +183,10 @@ smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model
 smc_status smc_sro(const smc_lattice *lat, int32_t nshells, const int8_t *occ, int64_t *counts,
                    double *alpha, cudaStream_t stream);
 
-/* Total energy of occ.
- *   e      device double (eV), nullable.
+/* Total energy of occ.  MLP models: the site energies of the tensor-core
+ * evaluation summed in FP64 in a fixed order (bit-reproducible); pair + MLP
+ * models add the pair energy from the pair counts.
+ *   e      device double (eV), nullable (required for MLP models).
  *   e_int  device int64, nullable; integer models only: E in units of unit_ev
  *          (exact). */
 smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
@@ -189,6 +205,8 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
 /* Lock-step trace of one mini-step: applies mini-step k of sweep `sweep`
  * (as smc_sweep would) and records, per trial in link-cell order
  * c = (cz*NLy + cy)*NLx + cx, the dE it computed (eV) and its decision.
+ * MLP models recompute the pre-swap energies (no cache) with the sweep's
+ * arithmetic, so a sweep equals its 2 Lx Ly Lz traced mini-steps bit for bit.
  *   dE   device float [N/n_A], nullable;  acc  device uint8 [N/n_A], nullable. */
 smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ,
                               uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,

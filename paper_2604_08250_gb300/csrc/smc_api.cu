@@ -337,10 +337,8 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
     smc_status st = check_sweep_args(lat, model, occ, nsweeps, kT, nsweeps, sweep0);
     if (st != SMC_OK) return st;
     if (nsweeps == 0) return SMC_OK;
-    if (is_mlp(model)) {
-        set_error("MLP sweeps are not available in this build");
-        return SMC_ERR_UNSUPPORTED;
-    }
+    if (is_mlp(model))
+        return launch_mlp_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     int8_t *occs[1] = {occ};
     return launch_pair_sweep(1, lat, model, occs, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
@@ -397,8 +395,11 @@ smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model
     }
     if (nsweeps == 0) return SMC_OK;
     if (is_mlp(model)) {
-        set_error("MLP sweeps are not available in this build");
-        return SMC_ERR_UNSUPPORTED;
+        if (R != 1) {
+            set_error("batched MLP sweeps take one replica per call");
+            return SMC_ERR_UNSUPPORTED;
+        }
+        return launch_mlp_sweep(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     }
     return launch_pair_sweep(R, lats, model, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
@@ -415,10 +416,7 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
         set_error("mini-step %d out of range [0, %d)", k, nA);
         return SMC_ERR_ARG;
     }
-    if (is_mlp(model)) {
-        set_error("MLP traces are not available in this build");
-        return SMC_ERR_UNSUPPORTED;
-    }
+    if (is_mlp(model)) return launch_mlp_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
@@ -458,8 +456,11 @@ smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8
         return SMC_ERR_ARG;
     }
     if (is_mlp(model)) {
-        set_error("MLP energies are not available in this build");
-        return SMC_ERR_UNSUPPORTED;
+        if (!e) {
+            set_error("e is NULL");
+            return SMC_ERR_ARG;
+        }
+        return launch_mlp_energy(lat, model, occ, e, stream);
     }
     smc_status st;
     Workspace *ws = workspace(&st);

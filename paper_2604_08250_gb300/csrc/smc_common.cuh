@@ -150,6 +150,14 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
 smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                                  uint32_t replica, uint64_t sweep, int k, double kT, float *dE,
                                  uint8_t *acc, cudaStream_t stream);
+smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                            uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                            int64_t *n_acc, cudaStream_t stream);
+smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                            uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,
+                            cudaStream_t stream);
+smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const int8_t *occ, double *e,
+                             cudaStream_t stream);
 smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t *occ, unsigned long long *counts,
                               cudaStream_t stream);
 smc_status launch_init(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,

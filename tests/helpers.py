@@ -60,3 +60,135 @@ def read_kat():
                 w = [int(t, 16) for t in line.split()]
                 rows.append((w[0:4], w[4:6], w[6:10]))
     return rows
+
+
+# ---------------------------------------------------------------------------
+# MLP site energies: features and the error bound of the BF16 tensor-core path.
+# ---------------------------------------------------------------------------
+def site_neighbors(sites, dims):
+    """[len(sites), 26] neighbour indices of the given sites (shell 1, then
+    2, then 3, vectors in brute-force order) and the shell of each column."""
+    nx, ny, nz = dims
+    s = np.asarray(sites, dtype=np.int64).reshape(-1)
+    x, y, z = s % nx, (s // nx) % ny, (s // (nx * ny)) % nz
+    sub = s // (nx * ny * nz)
+    p = np.stack([2 * x + sub, 2 * y + sub, 2 * z + sub], axis=-1)
+    vecs, shell = [], []
+    for m in (1, 2, 3):
+        for v in shell_vectors_bruteforce(m):
+            vecs.append(v)
+            shell.append(m)
+    q = p[:, None, :] + np.array(vecs)[None, :, :]
+    qs = q[..., 0] % 2
+    cell = ((q - qs[..., None]) // 2) % np.array([nx, ny, nz])
+    idx = ((qs * nz + cell[..., 2]) * ny + cell[..., 1]) * nx + cell[..., 0]
+    return idx, np.array(shell)
+
+
+def mlp_features(occ, dims, sites, swap=None):
+    """[len(sites), 20] MLP inputs [onehot(5) | shell-1, -2, -3 species
+    counts]; with swap = (a, b) the species of a and b are exchanged first."""
+    occ = np.asarray(occ).astype(np.int64)
+    sites = np.asarray(sites, dtype=np.int64).reshape(-1)
+    nb, shell = site_neighbors(sites, dims)
+
+    def spec(idx):
+        v = occ[idx]
+        if swap is not None:
+            a, b = swap
+            v = np.where(idx == a, occ[b], np.where(idx == b, occ[a], v))
+        return v
+
+    X = np.zeros((sites.size, 20))
+    X[np.arange(sites.size), spec(sites)] = 1.0
+    sn = spec(nb)
+    for m in (1, 2, 3):
+        cols = sn[:, shell == m]
+        for q in range(5):
+            X[:, 5 * m + q] = (cols == q).sum(axis=1)
+    return X
+
+
+def omega(a, b, dims):
+    """Sites whose MLP energy a swap of a and b changes: a, b and their
+    neighbours within three shells (40 on BCC)."""
+    nb, _ = site_neighbors([a, b], dims)
+    return np.unique(np.concatenate([[a, b], nb.reshape(-1)]))
+
+
+def _silu(z):
+    return z / (1.0 + np.exp(-z))
+
+
+TANH_APPROX_REL = 2.0 ** -10  # hardware tanh approximation: documented ~2^-11, with a factor-2 margin
+
+
+def mlp_error_bound(X, w):
+    """First-order bound on |f_GPU(x) - f(x)| per row of X, for the tensor-core
+    evaluation: FP32 accumulation over K terms (error <= K 2^-22 of the sum of
+    magnitudes, generous for truncating adders), SiLU as h + h tanh(h) with a
+    relative tanh error TANH_APPROX_REL, layer-1 activations rounded to BF16
+    (relative 2^-8), |silu'| <= 1.1.  w holds FP64 w1, b1, w2, b2, w3, b3.
+    Returns (bound, f) with f the exact FP64 f(x)."""
+    u_bf16 = 2.0 ** -8
+
+    def gam(k):
+        return k * 2.0 ** -22
+
+    def e_silu(z):
+        return np.abs(z) * (0.5 * TANH_APPROX_REL + 2.0 ** -22)
+
+    w1, b1, w2, b2, w3, b3 = (w[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    z1 = X @ w1.T + b1
+    dz1 = gam(32) * (np.abs(X) @ np.abs(w1).T + np.abs(b1))
+    h1 = _silu(z1)
+    e1 = 1.1 * dz1 + e_silu(z1)
+    e1 = e1 + u_bf16 * (np.abs(h1) + e1)
+    z2 = h1 @ w2.T + b2
+    dz2 = e1 @ np.abs(w2).T + gam(64) * (np.abs(b2) + (np.abs(h1) + e1) @ np.abs(w2).T)
+    h2 = _silu(z2)
+    e2 = 1.1 * dz2 + e_silu(z2)
+    f = h2 @ w3 + b3
+    ef = e2 @ np.abs(w3) + gam(66) * (abs(b3) + (np.abs(h2) + e2) @ np.abs(w3))
+    return ef, f
+
+
+def bf16_round(v):
+    """Round to the nearest BF16 value (ties to even) through FP32."""
+    f = np.asarray(v, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def mlp_bf16_emulation(X, w):
+    """The BF16 evaluation order in FP64: exact layer 1, SiLU, layer-1
+    activations rounded to BF16, exact layer 2, SiLU, output.  Returns
+    (f_emu, bound) where bound limits |f_GPU - f_emu| per row: FP32
+    accumulation (K 2^-22 of the magnitudes), the tanh approximation
+    (TANH_APPROX_REL) and, where an activation lies closer to a BF16 rounding
+    boundary than its own error, one BF16 spacing for that activation."""
+    def gam(k):
+        return k * 2.0 ** -22
+
+    def e_silu(z):
+        return np.abs(z) * (0.5 * TANH_APPROX_REL + 2.0 ** -22)
+
+    w1, b1, w2, b2, w3, b3 = (w[k] for k in ("w1", "b1", "w2", "b2", "w3", "b3"))
+    z1 = X @ w1.T + b1
+    dz1 = gam(32) * (np.abs(X) @ np.abs(w1).T + np.abs(b1))
+    s1 = _silu(z1)
+    ds1 = 1.1 * dz1 + e_silu(z1) + 2.0 ** -23 * np.abs(s1)
+    h1 = bf16_round(s1)
+    mag = np.maximum(np.abs(s1), 1e-300)
+    spacing = 2.0 ** (np.floor(np.log2(mag)) - 7)
+    frac = np.abs(s1) / spacing
+    dist = np.abs(frac - np.floor(frac) - 0.5) * spacing  # distance to the nearest rounding boundary
+    dh1 = np.where(dist <= 2 * ds1, 2 * spacing, 0.0)
+    z2 = h1 @ w2.T + b2
+    dz2 = dh1 @ np.abs(w2).T + gam(64) * (np.abs(b2) + (np.abs(h1) + dh1) @ np.abs(w2).T)
+    s2 = _silu(z2)
+    ds2 = 1.1 * dz2 + e_silu(z2)
+    f = s2 @ w3 + b3
+    bound = ds2 @ np.abs(w3) + gam(66) * (abs(b3) + (np.abs(s2) + ds2) @ np.abs(w3))
+    return f, bound

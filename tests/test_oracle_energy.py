@@ -250,3 +250,34 @@ def test_mlp_delta_e_matches_recompute():
         sw[[a, b]] = sw[[b, a]]
         want = oracle.total_energy(lat, model, sw) - E0
         assert oracle.delta_e(lat, model, occ, a, b) == pytest.approx(want, abs=1e-10)
+
+
+def test_mlp_site_energies_match_numpy_restatement():
+    """The oracle's MLP site energies equal an independent numpy evaluation
+    (features from brute-force neighbour vectors, the network as matrix
+    products) on a random quinary lattice, with biases switched on; a wrong
+    feature column, shell or activation would show here."""
+    dims, S = (8, 12, 8), 5
+    lat = oracle.Lattice(*dims, S)
+    rng = np.random.default_rng(7)
+    occ = rng.integers(0, S, lat.nsites).astype(np.int8)
+    mlp = inputs.mlp_weights(9, out_scale=1.0)
+    mlp["b1"] = rng.normal(0, 0.3, 64).astype(np.float32)
+    mlp["b2"] = rng.normal(0, 0.3, 64).astype(np.float32)
+    mlp["b3"] = 0.25
+    model = oracle.Model(oracle.MLP, mlp=mlp)
+    w = {k: oracle._widen(mlp[k]).reshape(64, -1) if k in ("w1", "w2") else oracle._widen(mlp[k])
+         for k in ("w1", "w2", "w3", "b1", "b2")}
+    w["b3"] = 0.25
+    sites = rng.choice(lat.nsites, 300, replace=False)
+    _, f = helpers.mlp_error_bound(helpers.mlp_features(occ, dims, sites), w)
+    got = np.array([oracle.site_energy(lat, model, occ, int(i)) for i in sites])
+    assert np.allclose(got, f, rtol=1e-12, atol=1e-14)
+    # Omega has 40 sites, and dE is the sum of the energy changes over it
+    a = int(sites[0])
+    b = oracle.neighbor(lat, a, oracle.shell_vectors(1)[3])
+    om = helpers.omega(a, b, dims)
+    assert om.size == 40
+    _, f0 = helpers.mlp_error_bound(helpers.mlp_features(occ, dims, om), w)
+    _, f1 = helpers.mlp_error_bound(helpers.mlp_features(occ, dims, om, swap=(a, b)), w)
+    assert oracle.delta_e(lat, model, occ, a, b) == pytest.approx(f1.sum() - f0.sum(), rel=1e-10, abs=1e-13)
