@@ -32,6 +32,10 @@ from paper_2604_08250_gb300 import inputs  # noqa: E402
 
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
+# MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
+MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
+MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
+MLP_FLOP_PER_ATTEMPT = 40 * MLP_FLOP_PER_SITE_FWD  # post-swap energies of the 40-site zone (cached pre-swap)
 
 
 def peaks():
@@ -401,6 +405,46 @@ def run_extras(smc, torch, dev, pk):
     out["batched_64"] = {"replicas": len(lats), "edges_min_max": [int(edges.min()), int(edges.max())],
                          "total_sites": tot, "sweeps": nb, "attempts_per_s": batt,
                          "frac_of_measured_hbm": batt * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+    for o in occs:
+        del o
+    occs.clear()
+    # MLP site energies on the tensor cores: 256^3 Dirichlet quinary at 800 K
+    c4 = inputs.CONFIG4
+    n4 = c4["cells"][0]
+    lat4 = smc.Lattice(n4, n4, n4, S)
+    occ4 = torch.empty(lat4.nsites, dtype=torch.int8, device=dev)
+    smc.init_lattice(lat4, inputs.dirichlet_counts(lat4.nsites, S, c4["comp_seed"]), c4["mc_seed"], occ4)
+    mlp_model = smc.Model(smc.MLP_BF16, mlp=inputs.mlp_weights(c4["mlp_seed"]))
+    kT4 = inputs.K_B_EV * c4["T"]
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev)
+    nsw4 = 2
+    ms4 = timed(lambda: smc.sweep(lat4, mlp_model, occ4, c4["mc_seed"], 0, nsw4, kT4, n_acc=n_acc), reps=1)
+    att4 = lat4.nsites * nsw4 / (ms4 * 1e-3)
+    acc_rate = float(n_acc.item()) / (2 * lat4.nsites * nsw4)  # warm-up call + timed call
+    tfl = att4 * MLP_FLOP_PER_ATTEMPT / 1e12
+    out["mlp_256"] = {"cells": [n4] * 3, "sweeps_per_launch": nsw4, "ms_per_sweep": ms4 / nsw4,
+                      "attempts_per_s": att4, "job_s_200_sweeps": ms4 / nsw4 * c4["nsweeps"] / 1e3,
+                      "accept_rate": acc_rate, "achieved_tflops": tfl,
+                      "frac_of_measured_bf16_sustained": tfl / pk["bf16_tflops_sustained"],
+                      "flop_per_attempt": MLP_FLOP_PER_ATTEMPT}
+    e4 = torch.zeros(1, dtype=torch.float64, device=dev)
+    ems = timed(lambda: smc.energy(lat4, mlp_model, occ4, e4), reps=3)
+    out["mlp_energy_256"] = {"ms": ems, "achieved_tflops": lat4.nsites * MLP_FLOP_PER_SITE_FWD / (ems * 1e-3) / 1e12}
+    del occ4
+    # dE/dtheta of the pair + MLP energy at 512^3 (one configuration)
+    c5 = inputs.CONFIG5
+    n5 = c5["cells"][0]
+    lat5 = smc.Lattice(n5, n5, n5, S)
+    occ5 = torch.empty(lat5.nsites, dtype=torch.int8, device=dev)
+    smc.init_lattice(lat5, inputs.equiatomic_counts(lat5.nsites, S), c5["mc_seed"], occ5)
+    m5 = smc.Model(smc.PAIR_F32_MLP_BF16, c5["nshells"], inputs.pair_f32_coeffs(c5["coeff_seed"], c5["nshells"], S),
+                   mlp=inputs.mlp_weights(c5["mlp_seed"]))
+    g5 = torch.zeros(smc.grad_size(lat5, m5), dtype=torch.float32, device=dev)
+    gms5 = timed(lambda: smc.energy_grad(lat5, m5, occ5, g5), reps=2)
+    tf5 = lat5.nsites * MLP_FLOP_PER_SITE_GRAD / (gms5 * 1e-3) / 1e12
+    out["mlp_grad_512"] = {"cells": [n5] * 3, "ms_per_configuration": gms5, "params": int(g5.numel()),
+                           "achieved_tflops": tf5, "frac_of_measured_bf16_sustained": tf5 / pk["bf16_tflops_sustained"],
+                           "flop_per_site": MLP_FLOP_PER_SITE_GRAD}
     return out
 
 

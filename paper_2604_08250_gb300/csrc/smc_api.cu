@@ -492,10 +492,7 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
         set_error("occ and grad must be non-NULL");
         return SMC_ERR_ARG;
     }
-    if (is_mlp(model)) {
-        set_error("MLP gradients are not available in this build");
-        return SMC_ERR_UNSUPPORTED;
-    }
+    if (is_mlp(model)) return launch_mlp_grad(lat, model, occ, grad, stream);
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;

@@ -158,6 +158,8 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
                             cudaStream_t stream);
 smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const int8_t *occ, double *e,
                              cudaStream_t stream);
+smc_status launch_mlp_grad(const smc_lattice *lat, const smc_model *m, const int8_t *occ, float *grad,
+                           cudaStream_t stream);
 smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t *occ, unsigned long long *counts,
                               cudaStream_t stream);
 smc_status launch_init(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,

@@ -20,6 +20,9 @@ struct MlpBlock {
     float pad[3];
 };
 
+// Fills the kernels' weight block from a model's MLP weights (host).
+void make_mlp_block(const smc_model *m, MlpBlock &W);
+
 struct RepDesc {
     int8_t *occ;
     double *e_acc;

@@ -226,3 +226,101 @@ def set_tuning(tile_y=0, tile_z=0, threads=0, ctas_per_sm=0):
 
 def debug_set(what, value):
     _chk(lib().smc_debug_set(int(what), int(value)))
+
+
+# ---------------------------------------------------------------------------
+# Parameter vectors, autograd and observable gradients.
+# ---------------------------------------------------------------------------
+def _bf16_bits(a):
+    """float -> BF16 bit patterns, round to nearest even (through FP32)."""
+    u = np.ascontiguousarray(a, dtype=np.float32).view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) >> 16
+    return u.astype(np.uint16)
+
+
+def n_pair_params(nshells, S):
+    return nshells * S * (S + 1) // 2
+
+
+def model_from_theta(kind, nshells, S, theta):
+    """Model from a parameter vector in the smc_energy_grad layout: pair
+    coefficients V_m(p, q), p <= q, row-major over (m, p, q) (FP32 eV), then
+    the MLP parameters W1 [64][20], b1, W2 [64][64], b2, W3, b3 (weights are
+    rounded to BF16, the precision the kernels use)."""
+    th = np.asarray(theta, dtype=np.float64).reshape(-1)
+    k = 0
+    v = None
+    if kind in (PAIR_F32, PAIR_F32_MLP_BF16):
+        v = np.zeros((nshells, S, S), dtype=np.float32)
+        for m in range(nshells):
+            for p in range(S):
+                for q in range(p, S):
+                    v[m, p, q] = v[m, q, p] = th[k]
+                    k += 1
+    elif kind != MLP_BF16:
+        raise ValueError("parameter vectors are defined for PAIR_F32, MLP_BF16 and PAIR_F32_MLP_BF16 models")
+    mlp = None
+    if kind in (MLP_BF16, PAIR_F32_MLP_BF16):
+        sizes = (("w1", 64 * 20), ("b1", 64), ("w2", 64 * 64), ("b2", 64), ("w3", 64), ("b3", 1))
+        mlp = {}
+        for name, n in sizes:
+            mlp[name] = th[k:k + n]
+            k += n
+        for name in ("w1", "w2", "w3"):
+            mlp[name] = _bf16_bits(mlp[name])
+        mlp["b3"] = float(mlp["b3"][0])
+    if k != th.size:
+        raise ValueError(f"theta has {th.size} entries, the model needs {k}")
+    return Model(kind, nshells=nshells if v is not None else 0, v=v, mlp=mlp)
+
+
+def _autograd_function():
+    import torch
+
+    class SMCEnergy(torch.autograd.Function):
+        """E(theta) of the configuration occ.  theta is a 1-D tensor in the
+        smc_energy_grad layout (see model_from_theta); forward runs
+        smc_energy, backward grad_out * smc_energy_grad at the same theta."""
+
+        @staticmethod
+        def forward(ctx, theta, lat, occ, kind, nshells):
+            th = theta.detach().cpu().numpy()
+            model = model_from_theta(kind, nshells, lat.nspecies, th)
+            e = torch.zeros(1, dtype=torch.float64, device=occ.device)
+            energy(lat, model, occ, e)
+            ctx.lat, ctx.occ, ctx.model = lat, occ, model
+            return e.reshape(()).to(theta.dtype).to(theta.device)
+
+        @staticmethod
+        def backward(ctx, gout):
+            g = torch.zeros(grad_size(ctx.lat, ctx.model), dtype=torch.float32, device=ctx.occ.device)
+            energy_grad(ctx.lat, ctx.model, ctx.occ, g)
+            return gout * g.to(gout.dtype).to(gout.device), None, None, None, None
+
+    return SMCEnergy
+
+
+_SMCEnergy = None
+
+
+def smc_energy_fn(theta, lat, occ, kind, nshells=0):
+    """Differentiable E(theta) (torch.autograd) of the configuration occ."""
+    global _SMCEnergy
+    if _SMCEnergy is None:
+        _SMCEnergy = _autograd_function()
+    return _SMCEnergy.apply(theta, lat, occ, kind, nshells)
+
+
+def observable_gradient(A, G, beta):
+    """Canonical-ensemble derivative of an observable's mean with respect to
+    the energy parameters, d<A>/dtheta = -beta (<A dE/dtheta> - <A><dE/dtheta>),
+    from equilibrium samples: A [n, ...] (e.g. SRO per sample), G [n, P]
+    (dE/dtheta per sample).  Returns [..., P]."""
+    import torch
+    A = torch.as_tensor(A, dtype=torch.float64)
+    G = torch.as_tensor(G, dtype=torch.float64, device=A.device)
+    n = A.shape[0]
+    Ac = A.reshape(n, -1) - A.reshape(n, -1).mean(0)
+    Gc = G - G.mean(0)
+    cov = Ac.T @ Gc / n
+    return (-beta * cov).reshape(*A.shape[1:], G.shape[1])

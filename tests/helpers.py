@@ -192,3 +192,19 @@ def mlp_bf16_emulation(X, w):
     f = s2 @ w3 + b3
     bound = ds2 @ np.abs(w3) + gam(66) * (abs(b3) + (np.abs(s2) + ds2) @ np.abs(w3))
     return f, bound
+
+
+def mlp_grad_abs_terms(X, w):
+    """Per MLP parameter (gradient layout: W1, b1, W2, b2, W3, b3), the sum
+    over the rows of X of the magnitude of its gradient term in the
+    absolute-value network (|W| everywhere, |silu| <= |z|, |silu'| <= 1.1), so
+    that cancellations inside a term (the back-propagated d1 of a single
+    site, say) cannot make the scale smaller than the rounding it carries."""
+    w1, b1, w2, b2, w3 = (np.abs(w[k]) for k in ("w1", "b1", "w2", "b2", "w3"))
+    X = np.abs(X)
+    a1 = X @ w1.T + b1
+    a2 = a1 @ w2.T + b2
+    d2 = np.broadcast_to(1.1 * w3, a2.shape)
+    d1 = 1.1 * (d2 @ w2)
+    return np.concatenate([(d1.T @ X).reshape(-1), d1.sum(0), (d2.T @ a1).reshape(-1), d2.sum(0), a2.sum(0),
+                           [float(X.shape[0])]])

@@ -308,3 +308,40 @@ def test_config4_full_size_sampled(smc):
     assert np.all(np.abs(d_g[cs] - d_o) <= loose)
     assert np.sqrt(np.mean((d_g[cs] - emu) ** 2)) <= 0.5 * np.sqrt(np.mean((emu - d_o) ** 2))
     record("config4_256cubed_sampled", d_g[cs] - d_o, d_g[cs] - emu, loose, 0, len(cs))
+
+
+GRAD_REL = 2.0 ** -7 + 2.0 ** -9  # two BF16 roundings per term, sigmoid approximations, FP32 sums
+
+
+@pytest.mark.parametrize("dims,kind,ctas", [((8, 8, 8), 2, 0), ((12, 8, 8), 3, 0), ((2, 2, 2), 2, 0),
+                                            ((56, 56, 56), 2, 1)])
+def test_mlp_gradient_matches_oracle(smc, dims, kind, ctas):
+    """dE/dtheta (pair part exact, then the 5569 MLP parameters) against the
+    oracle's FP64 back-propagation: every MLP entry within GRAD_REL of the sum
+    of the magnitudes of its terms; dE/db3 = N exactly.  The 56^3 case with
+    one CTA per SM runs enough blocks per CTA to exercise the FP64 flushes."""
+    S = 5
+    gm, om, w, V = make_models(smc, kind, biases=True)
+    lat, occ, _ = start_state(smc, dims, S, 17)
+    n = smc.grad_size(lat, gm)
+    g = torch.zeros(n, dtype=torch.float32, device=dev())
+    try:
+        smc.set_tuning(ctas_per_sm=ctas)
+        smc.energy_grad(lat, gm, occ, g)
+        smc.check()
+    finally:
+        smc.set_tuning()
+    occ_h = occ.cpu().numpy()
+    want = oracle.energy_grad(oracle.Lattice(*dims, S), om, occ_h)
+    got = g.cpu().numpy().astype(np.float64)
+    npair = n - 5569
+    assert np.array_equal(got[:npair], want[:npair])
+    scale = helpers.mlp_grad_abs_terms(helpers.mlp_features(occ_h, dims, np.arange(lat.nsites)), w)
+    err = np.abs(got[npair:] - want[npair:])
+    assert np.all(err <= GRAD_REL * scale + 1e-7), (np.flatnonzero(err > GRAD_REL * scale + 1e-7)[:5],
+                                                     (err / (scale + 1e-30)).max())
+    assert got[-1] == lat.nsites
+    rel = float(np.linalg.norm(got[npair:] - want[npair:]) / np.linalg.norm(want[npair:]))
+    _STATS[f"grad_{dims[0]}x{dims[1]}x{dims[2]}_kind{kind}"] = {
+        "norm_rel_err": rel, "max_err_over_term_scale": float((err / (scale + 1e-30)).max())}
+    assert rel < 1e-3
