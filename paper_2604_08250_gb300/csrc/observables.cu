@@ -14,77 +14,89 @@
 
 namespace smc {
 
-// Per-site neighbour histograms, packed 8 bits per species, reduced across
-// the warp with redux.sync per (p, q) and accumulated in shared memory.
-__global__ void __launch_bounds__(256) k_pair_counts(const int8_t *__restrict__ occ, int nx, int ny, int nz,
-                                                     int nshells, int S, unsigned long long *counts)
+// Ordered pair counts by bonds.  Every unordered bond is visited once: shell 1
+// from its sublattice-0 end (all 8 vectors), shells 2 and 3 along half of
+// their vectors (+x, +y, +z; the 6 shell-3 vectors whose first non-zero
+// component is positive).  With c_m^{pq} the number of visited (site, vector)
+// pairs with s_i = p, s_{i+v} = q, the ordered count is
+// n_m^{pq} = c_m^{pq} + c_m^{qp} (the map (i, v) -> (i + v, -v) is a bijection
+// of the torus, aliasing included).  A warp walks whole rows (sub, z, y), lane
+// = x; each lane keeps 8-bit counters packed per (shell, own species) in
+// 64-bit words and the warp folds them into shared memory every 16 sites.
+template <int NSH>
+__global__ void __launch_bounds__(256) k_pair_counts(const int8_t *__restrict__ occ, int nx, int ny, int nz, int S,
+                                                     unsigned long long *counts)
 {
-    __shared__ unsigned int bins[kMaxShells * kMaxSpecies * kMaxSpecies];
-    for (int i = threadIdx.x; i < kMaxShells * kMaxSpecies * kMaxSpecies; i += blockDim.x) bins[i] = 0;
+    __shared__ unsigned long long bins[NSH * 64];
+    for (int i = threadIdx.x; i < NSH * 64; i += blockDim.x) bins[i] = 0;
     __syncthreads();
     const int lane = threadIdx.x & 31;
-    const long long N = 2LL * nx * ny * nz;
-    const long long wid = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
-    const long long nwt = ((long long)gridDim.x * blockDim.x) >> 5;
-    for (long long s0 = wid * 32; s0 < N; s0 += nwt * 32) {
-        const long long s = s0 + lane;
-        const bool valid = s < N;
-        int p = -1, x = 0, y = 0, z = 0, sub = 0;
-        if (valid) {
-            long long t = s;
-            x = (int)(t % nx);
-            t /= nx;
-            y = (int)(t % ny);
-            t /= ny;
-            z = (int)(t % nz);
-            sub = (int)(t / nz);
-            p = occ[s] & 7;
-        }
-        auto at = [&](int sb, int xx, int yy, int zz) -> int {
-            xx = wrapc(xx, nx);
-            yy = wrapc(yy, ny);
-            zz = wrapc(zz, nz);
-            return occ[((size_t)((sb * nz + zz) * ny + yy)) * nx + xx] & 7;
+    const long long nrows = 2LL * nz * ny;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned char *o = (const unsigned char *)occ;
+    for (long long row = w0; row < nrows; row += nw) {
+        const int sub = (int)(row / ((long long)nz * ny));
+        const int rem = (int)(row - (long long)sub * nz * ny);
+        const int z = rem / ny, y = rem - (rem / ny) * ny;
+        auto R = [&](int sb, int zz, int yy) {
+            return o + ((size_t)((sb * nz + wrapc(zz, nz)) * ny + wrapc(yy, ny))) * nx;
         };
-        for (int m = 0; m < nshells; ++m) {
-            unsigned long long h = 0;
-            if (valid) {
-                if (m == 0) {
-                    const int o = sub == 0 ? -1 : 0;  // other-sublattice cells x+o .. x+o+1
+        const unsigned char *self = R(sub, z, y);
+        const unsigned char *ry1 = R(sub, z, y + 1), *rym = R(sub, z, y - 1);
+        const unsigned char *rz1 = R(sub, z + 1, y), *rzm = R(sub, z - 1, y);
+        const unsigned char *rz1y1 = R(sub, z + 1, y + 1), *rzmy1 = R(sub, z - 1, y + 1);
+        // shell 1 from sublattice 0: the other sublattice's cells (x-1..x, y-1..y, z-1..z)
+        const unsigned char *p00 = R(1, z - 1, y - 1), *p01 = R(1, z - 1, y), *p10 = R(1, z, y - 1), *p11 = R(1, z, y);
+        for (int x0 = 0; x0 < nx; x0 += 32 * 16) {
+            unsigned long long acc[NSH][8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u)
-                        h += 1ull << (8 * at(1 - sub, x + o + ((u >> 2) & 1), y + o + ((u >> 1) & 1), z + o + (u & 1)));
-                } else if (m == 1) {
-                    h += 1ull << (8 * at(sub, x - 1, y, z));
-                    h += 1ull << (8 * at(sub, x + 1, y, z));
-                    h += 1ull << (8 * at(sub, x, y - 1, z));
-                    h += 1ull << (8 * at(sub, x, y + 1, z));
-                    h += 1ull << (8 * at(sub, x, y, z - 1));
-                    h += 1ull << (8 * at(sub, x, y, z + 1));
-                } else {
+            for (int m = 0; m < NSH; ++m)
 #pragma unroll
-                    for (int a = -1; a <= 1; a += 2)
+                for (int q = 0; q < 8; ++q) acc[m][q] = 0;
+            const int x1 = min(nx, x0 + 32 * 16);
+            for (int x = x0 + lane; x < x1; x += 32) {
+                const int xp = x + 1 == nx ? 0 : x + 1, xm = x == 0 ? nx - 1 : x - 1;
+                const int p = self[x] & 7;
+                unsigned long long h[3];
+                h[0] = 0;
+                if (sub == 0)
+                    h[0] = (1ull << (8 * (p00[xm] & 7))) + (1ull << (8 * (p00[x] & 7))) +
+                           (1ull << (8 * (p01[xm] & 7))) + (1ull << (8 * (p01[x] & 7))) +
+                           (1ull << (8 * (p10[xm] & 7))) + (1ull << (8 * (p10[x] & 7))) +
+                           (1ull << (8 * (p11[xm] & 7))) + (1ull << (8 * (p11[x] & 7)));
+                if (NSH >= 2)
+                    h[1] = (1ull << (8 * (self[xp] & 7))) + (1ull << (8 * (ry1[x] & 7))) + (1ull << (8 * (rz1[x] & 7)));
+                if (NSH >= 3)
+                    h[2] = (1ull << (8 * (ry1[xp] & 7))) + (1ull << (8 * (rym[xp] & 7))) +
+                           (1ull << (8 * (rz1[xp] & 7))) + (1ull << (8 * (rzm[xp] & 7))) +
+                           (1ull << (8 * (rz1y1[x] & 7))) + (1ull << (8 * (rzmy1[x] & 7)));
 #pragma unroll
-                        for (int b = -1; b <= 1; b += 2) {
-                            h += 1ull << (8 * at(sub, x + a, y + b, z));
-                            h += 1ull << (8 * at(sub, x + a, y, z + b));
-                            h += 1ull << (8 * at(sub, x, y + a, z + b));
+                for (int m = 0; m < NSH; ++m)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) acc[m][q] += (p == q) ? h[m] : 0ull;
+            }
+            // at most 16 sites per lane x 8 per bin: no 8-bit field has overflowed
+#pragma unroll
+            for (int m = 0; m < NSH; ++m)
+#pragma unroll
+                for (int pp = 0; pp < 8; ++pp)
+#pragma unroll
+                    for (int q = 0; q < 8; ++q)
+                        if (pp < S && q < S) {
+                            const unsigned v =
+                                __reduce_add_sync(0xffffffffu, (unsigned)((acc[m][pp] >> (8 * q)) & 0xFFu));
+                            if (lane == 0 && v) atomicAdd(&bins[m * 64 + pp * 8 + q], (unsigned long long)v);
                         }
-                }
-            }
-            for (int q = 0; q < S; ++q) {
-                const unsigned cnt = (unsigned)((h >> (8 * q)) & 0xFFu);
-                for (int pp = 0; pp < S; ++pp) {
-                    const unsigned tot = __reduce_add_sync(0xffffffffu, p == pp ? cnt : 0u);
-                    if (lane == 0 && tot) atomicAdd(&bins[(m * kMaxSpecies + pp) * kMaxSpecies + q], tot);
-                }
-            }
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < nshells * kMaxSpecies * kMaxSpecies; i += blockDim.x) {
-        const int m = i / (kMaxSpecies * kMaxSpecies), p = (i / kMaxSpecies) % kMaxSpecies, q = i % kMaxSpecies;
-        if (p < S && q < S && bins[i]) atomicAdd(counts + (m * S + p) * S + q, (unsigned long long)bins[i]);
+    for (int i = threadIdx.x; i < NSH * 64; i += blockDim.x) {
+        const int m = i / 64, pp = (i / 8) % 8, q = i % 8;
+        if (pp < S && q < S) {
+            const unsigned long long c = bins[i] + bins[m * 64 + q * 8 + pp];
+            if (c) atomicAdd(counts + (m * S + pp) * S + q, c);
+        }
     }
 }
 
@@ -97,11 +109,16 @@ smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t 
     const int S = lat->nspecies;
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nshells * S * S, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
-    const long long N = 2LL * lat->nx * lat->ny * lat->nz;
+    const long long rows = 2LL * lat->ny * lat->nz;
     const int threads = 256;
-    const long long want = (N + threads - 1) / threads;
-    const int blocks = (int)std::min<long long>(want, (long long)ws->num_sms * 8);
-    k_pair_counts<<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, nshells, S, counts);
+    const long long want = (rows + 7) / 8;
+    const int blocks = (int)std::max(1LL, std::min<long long>(want, (long long)ws->num_sms * 8));
+    if (nshells == 1)
+        k_pair_counts<1><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);
+    else if (nshells == 2)
+        k_pair_counts<2><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);
+    else
+        k_pair_counts<3><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);
     e = cudaGetLastError();
     return e == cudaSuccess ? SMC_OK : cuda_fail(e, "k_pair_counts");
 }

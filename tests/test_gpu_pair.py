@@ -204,7 +204,9 @@ def test_f32_sweep_kernel_equals_trace_kernel(smc, dims):
 
 
 def test_counts_sro_energy_grad_match_oracle(smc):
-    for dims, S, nsh in (((8, 8, 8), 5, 3), ((6, 10, 4), 3, 2), ((2, 2, 2), 2, 3), ((16, 16, 16), 8, 3)):
+    for dims, S, nsh in (((8, 8, 8), 5, 3), ((6, 10, 4), 3, 2), ((2, 2, 2), 2, 3), ((16, 16, 16), 8, 3),
+                         ((2, 6, 4), 3, 1), ((40, 8, 12), 5, 2), ((600, 2, 3), 4, 3), ((3, 5, 7), 2, 2),
+                         ((1100, 4, 2), 8, 3)):
         N = 2 * dims[0] * dims[1] * dims[2]
         counts = inputs.equiatomic_counts(N, S)
         lat, occ = gpu_state(smc, dims, S, counts, 21)
