@@ -1,6 +1,5 @@
 // sweep_mlp.cu -- swap-MC sweep, lock-step trace and energies with the MLP
-// site energy (MLPNet, Sec. IV-B; BF16 weights and activations on the tensor
-// cores, FP32 accumulation and SiLU).
+// site energy (MLPNet, Sec. IV-B), evaluated on the tcgen05 tensor cores.
 //
 // Site energy e_i = f(x_i), x_i = [onehot(s_i) | counts of each species among
 // the shell-1, shell-2 and shell-3 neighbours] (20 inputs), f = W3 silu(W2
@@ -9,33 +8,35 @@
 // within three shells (40 sites on BCC), so (Algorithm 1, the reduction of the
 // local energies over Omega before and after the swap)
 //   dE = sum_{j in Omega} f(x'_j) - f(x_j).
-// The post-swap energies f(x'_j) are evaluated on the tensor cores; the
-// pre-swap energies come from a per-site cache E[i] = f(x_i) that the same
-// tile routine fills (so both sides are bit-identical) and that accepted
-// trials update over their whole Omega.
+// The post-swap energies f(x'_j) are evaluated on the tensor cores
+// (mlp_tc.cuh); the pre-swap energies come from a per-site cache E[i] = f(x_i)
+// that the same evaluator fills (so both sides are bit-identical) and that
+// accepted trials update over their whole Omega.
 //
-// Sweep organisation follows the pair kernel: link-cell columns staged in
-// shared memory, 4 mini-steps per group, one warp per tile, neighbour progress
-// flags with bounded waits.  A column here stages 61 rows (the 5x5
-// trial-sublattice and 6x6 partner-sublattice rows of its 3-shell reach).
-// Within a mini-step the warp handles its trials in batches of 4: swap in
-// shared memory, build the 160 post-swap feature rows, run the MLP on them,
-// compare with the cached energies, keep or undo each swap.
+// Sweep organisation: link-cell columns staged in shared memory, 4 mini-steps
+// per group, neighbour progress flags with bounded waits, as in the pair
+// kernel, but one CTA of 128 threads per tile: a column stages 61 rows (the
+// 5x5 trial-sublattice and 6x6 partner-sublattice rows of its 3-shell reach)
+// and its trials run in batches of 3, whose 120 post-swap feature rows fill
+// one 128-row tensor-core tile (thread t builds and owns row t).
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
 
 #include "mlp_common.cuh"
+#include "mlp_tc.cuh"
 #include "sweep_common.cuh"
 
 namespace smc {
 
-constexpr int kOmega = 40;    // sites of a trial's interaction zone
-constexpr int kMlpTB = 4;     // trials per batch
-constexpr int kMlpRows = kMlpTB * kOmega;
+constexpr int kOmega = 40;       // sites of a trial's interaction zone
 constexpr int kMlpWinRows = 61;  // 25 trial-sublattice + 36 partner-sublattice rows
-constexpr int kMlpMaxWarps = 8;
+constexpr int kSweepThreads = 512;  // four warpgroups, each with its own tensor-core tiles
+constexpr int kMlpChunk = 64;    // trials of a mini-step evaluated together (40 rows each)
+constexpr int kTraceTB = 3;      // trials per trace step (120 rows: one tile)
+constexpr int kTcMaxCtasPerSm = 512 / (2 * kTcCols);  // for the 2-warpgroup kernels
+constexpr int kTinfo = 16;       // ints of per-trial information
 
 // Omega of a trial for each (trial sublattice, partner direction), relative
 // to the trial site's byte in row (0, 0) of its column window: `same` is the
@@ -53,170 +54,140 @@ struct MlpGeo {
     int pat23[2][2][18];  // shell-2 then shell-3 neighbour offsets from `same`
 };
 
-// Layout of the CTA-wide part of the MLP kernels' shared memory.
+// Shared memory of the MLP kernels: weights, the warpgroups' tiles, then
+// kernel-specific parts from END on.
+template <int NWG>
 struct MlpSmem {
-    static constexpr uint32_t D = 0;                    // pair table (kDEntries floats)
-    static constexpr uint32_t W1 = D + kDEntries * 4;   // 64 rows x 80 B
-    static constexpr uint32_t W2 = W1 + 64 * kW1RowB;   // 64 rows x 144 B
-    static constexpr uint32_t B1 = W2 + 64 * kW2RowB;   // 64 floats each
+    static constexpr uint32_t W1 = 0;
+    static constexpr uint32_t W2 = W1 + kTcW1;
+    static constexpr uint32_t X = W2 + kTcW2;        // [NWG] tiles
+    static constexpr uint32_t H = X + NWG * kTcX;    // [NWG] tiles
+    static constexpr uint32_t B1 = H + NWG * kTcH;
     static constexpr uint32_t B2 = B1 + 256;
     static constexpr uint32_t W3 = B2 + 256;
     static constexpr uint32_t B3 = W3 + 256;
-    static constexpr uint32_t GEO = B3 + 16;
-    static constexpr uint32_t END = (uint32_t)((GEO + sizeof(MlpGeo) + 15) / 16 * 16);
+    static constexpr uint32_t MBAR = B3 + 16;        // [NWG]
+    static constexpr uint32_t TSLOT = MBAR + 8 * NWG;
+    static constexpr uint32_t CTL = TSLOT + 4;       // CTA-wide flag
+    static constexpr uint32_t RED = (CTL + 4 + 15) / 16 * 16;  // 4 doubles / long longs for reductions
+    static constexpr uint32_t TINFO = RED + 64;      // int [kMlpChunk][kTinfo]
+    static constexpr uint32_t D = TINFO + kMlpChunk * kTinfo * 4;  // pair table (kDEntries floats)
+    static constexpr uint32_t GEO = D + kDEntries * 4;
+    static constexpr uint32_t END = (uint32_t)((GEO + sizeof(MlpGeo) + 127) / 128 * 128);
+    static_assert(X % 128 == 0 && H % 128 == 0 && W2 % 128 == 0, "tile alignment");
+    static_assert(MBAR % 8 == 0 && RED % 8 == 0, "alignment");
 };
+constexpr int kSweepWG = 4;  // warpgroups of the sweep kernel
+constexpr int kEvalWG = 2;   // warpgroups of the energy and trace kernels
 
-// f for the 16 feature rows at shared offset `rows` (stride kARowB).  Lane
-// (g = lane/4, t = lane%4) returns f of rows g and g+8 (the four lanes of a
-// quad agree).  A row's arithmetic does not depend on the other rows of the
-// tile or on its position in it, so a site's f is the same wherever it is
-// evaluated.
-__device__ __forceinline__ void mlp_tile16(uint32_t rows, int lane, float &f_lo, float &f_hi)
+// The evaluator of this thread's warpgroup.
+template <int NWG>
+__device__ __forceinline__ TcEval mlp_evaluator(long long timeout_ns, int *status, int *abort_flag)
 {
-    const int g = lane >> 2, t = lane & 3;
-    const float *b1 = (const float *)(g_smem + MlpSmem::B1);
-    const float *b2 = (const float *)(g_smem + MlpSmem::B2);
-    const float *w3 = (const float *)(g_smem + MlpSmem::W3);
-    const float b3 = *(const float *)(g_smem + MlpSmem::B3);
-    float acc[8][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int kc = 0; kc < 2; ++kc) {
-        const uint32_t ar = rows + kc * 32 + 4 * t;
-        const uint32_t a0 = lds32(ar + g * kARowB), a1 = lds32(ar + (g + 8) * kARowB);
-        const uint32_t a2 = lds32(ar + g * kARowB + 16), a3 = lds32(ar + (g + 8) * kARowB + 16);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t br = MlpSmem::W1 + (8 * j + g) * kW1RowB + kc * 32 + 4 * t;
-            mma_bf16(acc[j], a0, a1, a2, a3, lds32(br), lds32(br + 16));
-        }
-    }
-    // hidden layer 1: bias, SiLU, BF16 -> the A fragments of layer 2 (the
-    // m16n8k16 accumulator of n-block j holds columns 8j + 2t, 8j + 2t + 1
-    // of rows g, g+8, which is the A-fragment layout of k-chunk j/2)
-    uint32_t ha[4][4];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = 8 * j + 2 * t;
-        const float h0 = silu(acc[j][0] + b1[c]), h1 = silu(acc[j][1] + b1[c + 1]);
-        const float h2 = silu(acc[j][2] + b1[c]), h3 = silu(acc[j][3] + b1[c + 1]);
-        ha[j >> 1][(j & 1) * 2 + 0] = pack_bf16(h0, h1);
-        ha[j >> 1][(j & 1) * 2 + 1] = pack_bf16(h2, h3);
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-    for (int kc = 0; kc < 4; ++kc) {
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const uint32_t br = MlpSmem::W2 + (8 * j + g) * kW2RowB + kc * 32 + 4 * t;
-            mma_bf16(acc[j], ha[kc][0], ha[kc][1], ha[kc][2], ha[kc][3], lds32(br), lds32(br + 16));
-        }
-    }
-    // hidden layer 2 and the output layer (FP32)
-    float s_lo = 0.f, s_hi = 0.f;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int c = 8 * j + 2 * t;
-        s_lo = fmaf(w3[c], silu(acc[j][0] + b2[c]), s_lo);
-        s_lo = fmaf(w3[c + 1], silu(acc[j][1] + b2[c + 1]), s_lo);
-        s_hi = fmaf(w3[c], silu(acc[j][2] + b2[c]), s_hi);
-        s_hi = fmaf(w3[c + 1], silu(acc[j][3] + b2[c + 1]), s_hi);
-    }
-    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 1);
-    s_lo += __shfl_xor_sync(0xffffffffu, s_lo, 2);
-    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 1);
-    s_hi += __shfl_xor_sync(0xffffffffu, s_hi, 2);
-    f_lo = s_lo + b3;
-    f_hi = s_hi + b3;
+    using M = MlpSmem<NWG>;
+    const uint32_t wg = threadIdx.x >> 7;
+    TcEval E;
+    E.L = TcLayout{M::X + wg * kTcX, M::H + wg * kTcH, M::W1, M::W2, M::B1, M::B2, M::W3, M::B3, M::MBAR + 8 * wg,
+                   M::TSLOT};
+    E.timeout_ns = timeout_ns;
+    E.status = status;
+    E.abort_flag = abort_flag;
+    E.tmem = 0;
+    E.phase = 0;
+    E.bar = 1 + wg;
+    return E;
 }
 
-// Copies the MLP weights (and the pair table and Omega geometry when given)
-// into the CTA's shared memory in the layout mlp_tile16 reads.
-__device__ void load_mlp_smem(const MlpBlock *W, const float *Dsrc, const MlpGeo *geo)
+// Pair part of dE (pair + MLP models) from the packed post-swap neighbour
+// histograms of a (species B now) and b (species A now), 3 shells each; the
+// swapped partner is removed from shell 1.
+template <int NWG>
+__device__ __forceinline__ float pair_part(const SweepParams &P, const int *ha, const int *hb, int A, int B)
 {
+    const float *Dt = (const float *)(g_smem + MlpSmem<NWG>::D);
+    float dp = 0.f;
+    for (int m = 0; m < P.nshells; ++m) {
+        const float *D = Dt + ((m * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+        for (int q = 0; q < P.S; ++q) {
+            float ca = (float)(((uint32_t)ha[m] >> (4 * q)) & 15u);
+            float cb = (float)(((uint32_t)hb[m] >> (4 * q)) & 15u);
+            if (m == 0) {
+                ca -= (q == A) ? 1.f : 0.f;
+                cb -= (q == B) ? 1.f : 0.f;
+            }
+            dp = fmaf(ca - cb, D[q], dp);
+        }
+    }
+    return dp;
+}
+
+// Copies the model (weights, pair table, geometry) and sets up the evaluators.
+template <int NWG>
+__device__ void mlp_cta_setup(TcEval &E, const MlpBlock *W, const float *Dsrc, const MlpGeo *geo)
+{
+    tc_load_weights(W, E.L);
     const int tid = threadIdx.x, n = blockDim.x;
-    for (int i = tid; i < 64 * 16; i += n) {
-        const int r = i >> 4, c = i & 15;
-        *(uint32_t *)(g_smem + MlpSmem::W1 + r * kW1RowB + 4 * c) = ((const uint32_t *)W->w1)[r * 16 + c];
-    }
-    for (int i = tid; i < 64 * 32; i += n) {
-        const int r = i >> 5, c = i & 31;
-        *(uint32_t *)(g_smem + MlpSmem::W2 + r * kW2RowB + 4 * c) = ((const uint32_t *)W->w2)[r * 32 + c];
-    }
-    for (int i = tid; i < 64; i += n) {
-        ((float *)(g_smem + MlpSmem::B1))[i] = W->b1[i];
-        ((float *)(g_smem + MlpSmem::B2))[i] = W->b2[i];
-        ((float *)(g_smem + MlpSmem::W3))[i] = W->w3[i];
-    }
-    if (tid == 0) *(float *)(g_smem + MlpSmem::B3) = W->b3;
     if (Dsrc)
-        for (int i = tid; i < kDEntries; i += n) ((float *)(g_smem + MlpSmem::D))[i] = Dsrc[i];
+        for (int i = tid; i < kDEntries; i += n) ((float *)(g_smem + MlpSmem<NWG>::D))[i] = Dsrc[i];
     if (geo)
         for (int i = tid; i < (int)(sizeof(MlpGeo) / 4); i += n)
-            ((int *)(g_smem + MlpSmem::GEO))[i] = ((const int *)geo)[i];
+            ((int *)(g_smem + MlpSmem<NWG>::GEO))[i] = ((const int *)geo)[i];
+    tc_setup(E, NWG);
 }
 
 // ---------------------------------------------------------------------------
 // Per-site energies of the whole lattice: e[i] = f(x_i), optionally stored
-// (the sweep's cache), and their sum per CTA in a fixed order.  One warp per
-// 16 consecutive sites.
+// (the sweep's cache), and their sum per CTA in a fixed order.  Each
+// warpgroup takes 128 consecutive sites per tile.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_mlp_site_energy(const MlpBlock *W, const int8_t *__restrict__ occ, int nx,
-                                                         int ny, int nz, float *ecache, double *part)
+__global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBlock *W,
+                                                                   const int8_t *__restrict__ occ, int nx, int ny,
+                                                                   int nz, float *ecache, double *part,
+                                                                   long long timeout_ns, int *status, int *abort_flag)
 {
-    load_mlp_smem(W, nullptr, nullptr);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-    const uint32_t tile = MlpSmem::END + warp * 16 * kARowB;
+    constexpr int NWG = kEvalWG;
+    TcEval E = mlp_evaluator<NWG>(timeout_ns, status, abort_flag);
+    mlp_cta_setup<NWG>(E, W, nullptr, nullptr);
+    const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const long long N = 2LL * nx * ny * nz;
-    const long long ntile = (N + 15) / 16;
+    const long long ntile = (N + kTcRows - 1) / kTcRows;
     auto spec = [&](int sb, int xx, int yy, int zz) { return occ_at(occ, nx, ny, nz, sb, xx, yy, zz); };
-    double wsum = 0.0;
-    for (long long tl = (long long)blockIdx.x * nwarp + warp; tl < ntile; tl += (long long)gridDim.x * nwarp) {
-        if (lane < 16) {
-            const long long s = tl * 16 + lane;
-            int q0 = 0;
-            uint32_t h1 = 0, h2 = 0, h3 = 0;
-            if (s < N) {
-                long long r = s;
-                const int x = (int)(r % nx);
-                r /= nx;
-                const int y = (int)(r % ny);
-                r /= ny;
-                const int z = (int)(r % nz);
-                const int sub = (int)(r / nz);
-                q0 = occ[s] & 7;
-                site_hist(spec, sub, x, y, z, h1, h2, h3);
-            }
-            write_feature_row(tile + lane * kARowB, q0, h1, h2, h3);
+    double sum = 0.0;
+    for (long long tl = (long long)NWG * blockIdx.x + wg; tl < ntile; tl += (long long)NWG * gridDim.x) {
+        const long long s = tl * kTcRows + r;
+        int q0 = -1;
+        uint32_t h1 = 0, h2 = 0, h3 = 0;
+        if (s < N) {
+            long long t = s;
+            const int x = (int)(t % nx);
+            t /= nx;
+            const int y = (int)(t % ny);
+            t /= ny;
+            const int z = (int)(t % nz);
+            const int sub = (int)(t / nz);
+            q0 = occ[s] & 7;
+            site_hist(spec, sub, x, y, z, h1, h2, h3);
         }
-        __syncwarp();
-        float f_lo, f_hi;
-        mlp_tile16(tile, lane, f_lo, f_hi);
-        const int g = lane >> 2;
-        const long long s_lo = tl * 16 + g, s_hi = tl * 16 + g + 8;
-        if ((lane & 3) == 0 && ecache) {
-            if (s_lo < N) ecache[s_lo] = f_lo;
-            if (s_hi < N) ecache[s_hi] = f_hi;
+        tc_write_features(E.L, r, q0, h1, h2, h3);
+        fence_async_smem();
+        const float f = tc_eval(E);
+        if (s < N) {
+            if (ecache) ecache[s] = f;
+            sum += (double)f;
         }
-        // the 16 values in site order, summed by every lane alike
-        const float v_lo = (s_lo < N) ? f_lo : 0.f, v_hi = (s_hi < N) ? f_hi : 0.f;
-        double tsum = 0.0;
-        for (int gg = 0; gg < 8; ++gg) tsum += (double)__shfl_sync(0xffffffffu, v_lo, 4 * gg);
-        for (int gg = 0; gg < 8; ++gg) tsum += (double)__shfl_sync(0xffffffffu, v_hi, 4 * gg);
-        wsum += tsum;
-        __syncwarp();
     }
-    __shared__ double wpart[32];
-    if (lane == 0) wpart[warp] = wsum;
+    // CTA sum in thread order (the X tiles are free once both warpgroups are done)
+    double *red = (double *)(g_smem + MlpSmem<NWG>::X);
+    tc_fence_before();
     __syncthreads();
-    if (threadIdx.x == 0 && part) {
-        double s = 0.0;
-        for (int w = 0; w < nwarp; ++w) s += wpart[w];
-        part[blockIdx.x] = s;
+    red[tid] = sum;
+    __syncthreads();
+    if (tid == 0 && part) {
+        double t = 0.0;
+        for (int i = 0; i < 128 * NWG; ++i) t += red[i];
+        part[blockIdx.x] = t;
     }
+    tc_teardown(E, NWG);
 }
 
 // out (+)= sum of part[0 .. n-1], in index order.
@@ -231,131 +202,108 @@ __global__ void k_sum_parts(const double *part, int n, double *out, int accumula
         *out = s;
 }
 
-// Pair part of dE (pair + MLP models) from the post-swap feature rows of a
-// (row ra: species B now) and b (row rb: species A now).  Their shell counts
-// include the swapped partner, which is subtracted from shell 1.
-__device__ __forceinline__ float pair_part(const SweepParams &P, const float *Dt, uint32_t ra, uint32_t rbv, int A,
-                                           int B)
-{
-    const __nv_bfloat16 *xa = (const __nv_bfloat16 *)(g_smem + ra);
-    const __nv_bfloat16 *xb = (const __nv_bfloat16 *)(g_smem + rbv);
-    float dp = 0.f;
-    for (int m = 0; m < P.nshells; ++m) {
-        const float *D = Dt + ((m * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
-        for (int q = 0; q < P.S; ++q) {
-            float ca = __bfloat162float(xa[5 + 5 * m + q]);
-            float cb = __bfloat162float(xb[5 + 5 * m + q]);
-            if (m == 0) {
-                ca -= (q == A) ? 1.f : 0.f;
-                cb -= (q == B) ? 1.f : 0.f;
-            }
-            dp = fmaf(ca - cb, D[q], dp);
-        }
-    }
-    return dp;
-}
-
 // ---------------------------------------------------------------------------
 // The sweep.
 // ---------------------------------------------------------------------------
-struct MlpWarp {  // per-warp shared memory (offsets from the warp's base)
-    uint32_t win, A, fnew, eold, site, words, tinfo, end;
+struct SweepLayout {  // offsets after MlpSmem<kSweepWG>::END
+    uint32_t win, words, fval, diff, site, slots, end;
 };
 
-__host__ __device__ __forceinline__ MlpWarp mlp_warp_layout(int rb, int nk, int tpc)
+__host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int rb, int NLx, int tpc)
 {
-    MlpWarp L;
-    L.win = (uint32_t)(16 * tpc + 15) / 16 * 16;  // accumulator slots first
-    L.A = L.win + (uint32_t)((kMlpWinRows * rb + 16 + 15) / 16 * 16);
-    L.fnew = L.A + kMlpRows * kARowB;
-    L.eold = L.fnew + kMlpRows * 4;
-    L.site = L.eold + kMlpRows * 4;
-    L.words = L.site + kMlpRows * 4;
-    L.tinfo = L.words + (uint32_t)nk * 512;
-    L.end = L.tinfo + kMlpTB * 32;
+    SweepLayout L;
+    const uint32_t rows = (uint32_t)kOmega * (uint32_t)(NLx < kMlpChunk ? NLx : kMlpChunk);
+    L.win = MlpSmem<kSweepWG>::END;
+    L.words = L.win + (uint32_t)((kMlpWinRows * rb + 32 + 15) / 16 * 16);
+    L.fval = L.words + (uint32_t)((NLx * 16 + 15) / 16 * 16);
+    L.diff = L.fval + rows * 4;
+    L.site = L.diff + rows * 4;
+    L.slots = L.site + rows * 4;
+    L.end = L.slots + (uint32_t)(16 * tpc);
     return L;
 }
 
 template <bool HAS_PAIR, int SOFF>
-__device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &RD, uint32_t wb, const MlpWarp &L,
-                                           int y0, int z0, uint64_t sweep, float beta, int lane, double &accEd,
+__device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &RD, const SweepLayout &SL, TcEval &E,
+                                           int y0, int z0, uint64_t sweep, float beta, double &accEd,
                                            long long &accN)
 {
     constexpr int sub = SOFF == -1 ? 0 : 1;
     constexpr int lo = SOFF - 2;  // first partner-sublattice row (dy, dz) of the window
+    const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
     const uint32_t rb = (uint32_t)P.rowB;
-    const uint32_t col0 = wb + L.win + 16;  // row 0's body (4-byte halos on both sides)
-    const MlpGeo &geo = *(const MlpGeo *)(g_smem + MlpSmem::GEO);
-    // ---- stage the 61 rows ----
+    const uint32_t col0 = SL.win + 16;  // row 0's body (4-byte halos on both sides)
+    using M = MlpSmem<kSweepWG>;
+    const MlpGeo &geo = *(const MlpGeo *)(g_smem + M::GEO);
+    auto row_of = [&](int rr, int &gsub, int &gy, int &gz) {
+        int dy, dz;
+        if (rr < 25) {
+            dy = rr % 5 - 2;
+            dz = rr / 5 - 2;
+            gsub = sub;
+        } else {
+            dy = (rr - 25) % 6 + lo;
+            dz = (rr - 25) / 6 + lo;
+            gsub = 1 - sub;
+        }
+        gy = wrapc(y0 + dy, ny);
+        gz = wrapc(z0 + dz, nz);
+    };
+    // ---- stage the 61 rows, mask species, fill halos ----
     {
         const bool vec = RD.vec != 0;
         const int cpr = vec ? (nx >> 4) : (nx >> 2);
         const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
-        for (int rr = 0; rr < kMlpWinRows; ++rr) {
-            int gsub, dy, dz;
-            if (rr < 25) {
-                dy = rr % 5 - 2;
-                dz = rr / 5 - 2;
-                gsub = sub;
-            } else {
-                dy = (rr - 25) % 6 + lo;
-                dz = (rr - 25) / 6 + lo;
-                gsub = 1 - sub;
-            }
-            const int gy = wrapc(y0 + dy, ny), gz = wrapc(z0 + dz, nz);
+        for (int i = tid; i < kMlpWinRows * cpr; i += kSweepThreads) {
+            const int rr = i / cpr, c = i - rr * cpr;
+            int gsub, gy, gz;
+            row_of(rr, gsub, gy, gz);
             const int8_t *src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
             const uint32_t dst = col0 + (uint32_t)rr * rb;
-            if (vec) {
-                for (int c = lane; c < cpr; c += 32)
-                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + dst + 16 * c),
-                                 "l"(src + 16 * c)
-                                 : "memory");
-            } else {
-                for (int c = lane; c < cpr; c += 32)
-                    *(unsigned *)(g_smem + dst + 4 * c) = __ldcg((const unsigned *)src + c);
-            }
+            if (vec)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + dst + 16 * c),
+                             "l"(src + 16 * c)
+                             : "memory");
+            else
+                *(unsigned *)(g_smem + dst + 4 * c) = __ldcg((const unsigned *)src + c);
         }
         if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-        for (int rr = lane; rr < kMlpWinRows; rr += 32) {
+        __syncthreads();
+        const int wpr = nx >> 2;
+        for (int i = tid; i < kMlpWinRows * wpr; i += kSweepThreads) {
+            const int rr = i / wpr, c = i - rr * wpr;
+            *(unsigned *)(g_smem + col0 + rr * rb + 4 * c) &= 0x07070707u;
+        }
+        __syncthreads();
+        for (int rr = tid; rr < kMlpWinRows; rr += kSweepThreads) {
             unsigned char *row = g_smem + col0 + rr * rb;
-            for (int c = 0; c < nx; c += 4) *(unsigned *)(row + c) &= 0x07070707u;
             *(unsigned *)(row - 4) = *(const unsigned *)(row + nx - 4);
             *(unsigned *)(row + nx) = *(const unsigned *)row;
         }
-        __syncwarp();
     }
-    // ---- Philox words of the column's trial sites: [k][word][lane] ----
-    uint32_t *wsm = (uint32_t *)(g_smem + wb + L.words);
-    const int nk = (NLx + 31) >> 5;
+    // ---- Philox words of the column's trial sites: [link cell][word] ----
+    uint32_t *wsm = (uint32_t *)(g_smem + SL.words);
     const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
-    for (int k = 0; k < nk; ++k) {
-        const int i = lane + 32 * k;
-        if (i < NLx) {
-            const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
-                                  (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
-            wsm[(k * 4 + 0) * 32 + lane] = w.x;
-            wsm[(k * 4 + 1) * 32 + lane] = w.y;
-            wsm[(k * 4 + 2) * 32 + lane] = w.z;
-            wsm[(k * 4 + 3) * 32 + lane] = w.w;
-        }
+    for (int i = tid; i < NLx; i += kSweepThreads) {
+        const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
+                              (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
+        *(uint4 *)(wsm + 4 * i) = make_uint4(w.x, w.y, w.z, w.w);
     }
-    __syncwarp();
-    int *tinfo = (int *)(g_smem + wb + L.tinfo);  // per trial: dir, r, A, B, b row, b x, x, accepted
-    float *fnew = (float *)(g_smem + wb + L.fnew);
-    float *eold = (float *)(g_smem + wb + L.eold);
-    int *sites = (int *)(g_smem + wb + L.site);
-    const uint32_t A_tile = wb + L.A;
-    const float *Dt = (const float *)(g_smem + MlpSmem::D);
+    __syncthreads();
+    // per trial: dir, r, A, B, b row, b x, x, accepted, post-swap histograms of a (8-10) and b (11-13)
+    int *tinfo = (int *)(g_smem + M::TINFO);
+    float *fval = (float *)(g_smem + SL.fval);
+    float *diff = (float *)(g_smem + SL.diff);
+    int *sites = (int *)(g_smem + SL.site);
     const uint32_t arow = col0 + 12 * rb;
     for (int dx = 0; dx < 4; ++dx) {
-        for (int i0 = 0; i0 < NLx; i0 += kMlpTB) {
-            const int nb = min(kMlpTB, NLx - i0);
+        for (int i0 = 0; i0 < NLx; i0 += kMlpChunk) {
+            const int T = min(kMlpChunk, NLx - i0), nrow = T * kOmega;
             // -- decode the trials and swap in shared memory --
-            if (lane < nb) {
-                const int i = i0 + lane, x = 4 * i + dx;
-                const uint32_t w = wsm[((i >> 5) * 4 + dx) * 32 + (i & 31)];
+            if (tid < T) {
+                const int i = i0 + tid, x = 4 * i + dx;
+                const uint32_t w = wsm[4 * i + dx];
                 const int dir = (int)(w >> kRBits);
                 const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
                 const uint32_t brow = col0 + (uint32_t)(25 + (kz + 2) * 6 + (ky + 2)) * rb;
@@ -363,7 +311,7 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 const int A = g_smem[arow + x], B = g_smem[brow + xb];
                 halo_store(arow, x, nx, (unsigned char)B);
                 halo_store(brow, xb, nx, (unsigned char)A);
-                int *ti = tinfo + lane * 8;
+                int *ti = tinfo + tid * kTinfo;
                 ti[0] = dir;
                 ti[1] = (int)(w & kRMask);
                 ti[2] = A;
@@ -371,33 +319,24 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 ti[4] = (int)brow;
                 ti[5] = xb;
                 ti[6] = x;
+                ti[7] = 0;
             }
-            __syncwarp();
-            // -- post-swap feature rows; cached pre-swap energies --
-            const int nrow = nb * kOmega;
-            float eo[5];
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int q = lane + 32 * it;
-                eo[it] = 0.f;
-                if (q < nrow) {
-                    const int t = q / kOmega, e = q - t * kOmega;
-                    const OmegaEntry oe = geo.om[sub][tinfo[t * 8]][e];
+            __syncthreads();
+            // -- post-swap rows, 128 per tile, tiles alternating between the warpgroups --
+            const int ntile = (nrow + kTcRows - 1) / kTcRows;
+            for (int n = wg; n < ntile; n += kSweepWG) {
+                const int row = n * kTcRows + r;
+                float eo = 0.f;
+                int site = 0;
+                if (row < nrow) {
+                    const int t = row / kOmega, e = row - t * kOmega;
+                    int *ti = tinfo + t * kTinfo;
+                    const OmegaEntry oe = geo.om[sub][ti[0]][e];
                     const int ssub = oe.rel ? 1 - sub : sub;
-                    const int x = tinfo[t * 8 + 6];
+                    const int x = ti[6];
                     const int gx = wrapc(x + oe.dxo, nx), gy = wrapc(y0 + oe.dy, ny), gz = wrapc(z0 + oe.dz, nz);
-                    const int site = ((ssub * nz + gz) * ny + gy) * nx + gx;
-                    sites[q] = site;
-                    eo[it] = __ldcg(P.ecache + site);
-                }
-            }
-#pragma unroll
-            for (int it = 0; it < 5; ++it) {
-                const int q = lane + 32 * it;
-                if (q < nrow) {
-                    const int t = q / kOmega, e = q - t * kOmega;
-                    const OmegaEntry oe = geo.om[sub][tinfo[t * 8]][e];
-                    const int x = tinfo[t * 8 + 6];
+                    site = ((ssub * nz + gz) * ny + gy) * nx + gx;
+                    eo = __ldcg(P.ecache + site);
                     const uint32_t bs = col0 + (uint32_t)(oe.same + x), bo = col0 + (uint32_t)(oe.other + x);
                     const int *p1 = geo.pat1[sub][oe.rel];
                     const int *p23 = geo.pat23[sub][oe.rel];
@@ -408,31 +347,31 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                     for (int k = 0; k < 6; ++k) h2 += 1u << (4 * g_smem[bs + p23[k]]);
 #pragma unroll
                     for (int k = 6; k < 18; ++k) h3 += 1u << (4 * g_smem[bs + p23[k]]);
-                    write_feature_row(A_tile + q * kARowB, g_smem[bs], h1, h2, h3);
-                    eold[q] = eo[it];
+                    tc_write_features(E.L, r, g_smem[bs], h1, h2, h3);
+                    if (e < 2) {
+                        ti[8 + 3 * e] = (int)h1;
+                        ti[9 + 3 * e] = (int)h2;
+                        ti[10 + 3 * e] = (int)h3;
+                    }
+                } else {
+                    tc_write_features(E.L, r, -1, 0, 0, 0);
+                }
+                fence_async_smem();
+                const float f = tc_eval(E);
+                if (row < nrow) {
+                    fval[row] = f;
+                    diff[row] = f - eo;
+                    sites[row] = site;
                 }
             }
-            __syncwarp();
-            // -- the MLP on the rows, 16 at a time --
-            const int ntl = (nrow + 15) / 16;
-            for (int m = 0; m < ntl; ++m) {
-                float f_lo, f_hi;
-                mlp_tile16(A_tile + m * 16 * kARowB, lane, f_lo, f_hi);
-                if ((lane & 3) == 0) {
-                    fnew[m * 16 + (lane >> 2)] = f_lo;
-                    fnew[m * 16 + (lane >> 2) + 8] = f_hi;
-                }
-            }
-            __syncwarp();
+            __syncthreads();
             // -- decisions; rejected swaps are undone --
-            if (lane < nb) {
-                int *ti = tinfo + lane * 8;
+            if (tid < T) {
+                int *ti = tinfo + tid * kTinfo;
                 float dE = 0.f;
-                for (int e = 0; e < kOmega; ++e) dE += fnew[lane * kOmega + e] - eold[lane * kOmega + e];
+                for (int e = 0; e < kOmega; ++e) dE += diff[tid * kOmega + e];
                 const int A = ti[2], B = ti[3];
-                if (HAS_PAIR && A != B)
-                    dE += pair_part(P, Dt, A_tile + (lane * kOmega) * kARowB, A_tile + (lane * kOmega + 1) * kARowB,
-                                    A, B);
+                if (HAS_PAIR && A != B) dE += pair_part<kSweepWG>(P, ti + 8, ti + 11, A, B);
                 const bool acc = metropolis<false>(dE, (uint32_t)ti[1], beta, nullptr, make_int2(0, 0));
                 ti[7] = acc ? 1 : 0;
                 if (!acc) {
@@ -443,18 +382,19 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                     accN += 1;
                 }
             }
-            __syncwarp();
+            __syncthreads();
             // -- cached energies over the accepted trials' Omega --
-            for (int q = lane; q < nrow; q += 32)
-                if (tinfo[(q / kOmega) * 8 + 7]) P.ecache[sites[q]] = fnew[q];
-            __syncwarp();
+            for (int row = tid; row < nrow; row += kSweepThreads)
+                if (tinfo[(row / kOmega) * kTinfo + 7]) P.ecache[sites[row]] = fval[row];
+            __syncthreads();
         }
     }
     // ---- write back the trial row (0, 0) and the partner rows (SOFF..SOFF+1)^2 ----
     {
         const bool vec = RD.vec != 0;
         const int cpr = vec ? (nx >> 4) : (nx >> 2);
-        for (int wr = 0; wr < 5; ++wr) {
+        for (int i = tid; i < 5 * cpr; i += kSweepThreads) {
+            const int wr = i / cpr, c = i - wr * cpr;
             int rr, gsub, gy, gz;
             if (wr == 0) {
                 rr = 12;
@@ -470,35 +410,35 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
             }
             int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
             const unsigned char *srcs = g_smem + col0 + (uint32_t)rr * rb;
-            if (vec) {
-                for (int c = lane; c < cpr; c += 32) *((int4 *)dstg + c) = *((const int4 *)srcs + c);
-            } else {
-                for (int c = lane; c < cpr; c += 32) *((unsigned *)dstg + c) = *((const unsigned *)srcs + c);
-            }
+            if (vec)
+                *((int4 *)dstg + c) = *((const int4 *)srcs + c);
+            else
+                *((unsigned *)dstg + c) = *((const unsigned *)srcs + c);
         }
     }
-    __syncwarp();
+    __syncthreads();
 }
 
 template <bool HAS_PAIR>
-__global__ void __launch_bounds__(32 * kMlpMaxWarps, 1) k_sweep_mlp(const __grid_constant__ SweepParams P,
-                                                                    const __grid_constant__ MlpGeo G)
+__global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_constant__ SweepParams P,
+                                                                const __grid_constant__ MlpGeo G)
 {
-    load_mlp_smem(P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
-    __syncthreads();
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
+    using M = MlpSmem<kSweepWG>;
+    TcEval E = mlp_evaluator<kSweepWG>(P.timeout_ns, P.status, P.abort_flag);
+    mlp_cta_setup<kSweepWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const RepDesc &RD = P.rep[0];
-    const int nk = (RD.NLx + 31) >> 5;
-    const MlpWarp L = mlp_warp_layout(P.rowB, nk, P.tpc);
-    const uint32_t wb = MlpSmem::END + (uint32_t)warp * P.warp_bytes;
-    double *slot_e = (double *)(g_smem + wb);
-    long long *slot_n = (long long *)(g_smem + wb + 8 * P.tpc);
-    for (int i = lane; i < P.tpc; i += 32) {
+    const SweepLayout SL = mlp_sweep_layout(P.rowB, RD.NLx, P.tpc);
+    double *slot_e = (double *)(g_smem + SL.slots);
+    long long *slot_n = (long long *)(g_smem + SL.slots + 8 * P.tpc);
+    double *red_e = (double *)(g_smem + M::RED);
+    long long *red_n = (long long *)(g_smem + M::RED + 16);
+    for (int i = tid; i < P.tpc; i += kSweepThreads) {
         slot_e[i] = 0.0;
         slot_n[i] = 0;
     }
-    __syncwarp();
+    volatile int *ctl = (volatile int *)(g_smem + M::CTL);
+    __syncthreads();
     bool aborted = false;
     for (int t = 0; t < P.nsweeps && !aborted; ++t) {
         const uint64_t sweep = P.sweep0 + (uint64_t)t;
@@ -507,10 +447,15 @@ __global__ void __launch_bounds__(32 * kMlpMaxWarps, 1) k_sweep_mlp(const __grid
             const uint32_t gstep = (uint32_t)(t * P.G + g);
             const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4;
             int slotk = 0;
-            for (int tile = gw; tile < P.ntiles; tile += NW, ++slotk) {
+            for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++slotk) {
                 const int ty = tile % RD.NTy, tz = tile / RD.NTy;
                 // every earlier group of the 8 neighbouring tiles must be done
-                if (!wait_tile_warp(P, RD, ty, tz, gstep, lane)) {
+                if (warp == 0) {
+                    const bool ok = wait_tile_warp(P, RD, ty, tz, gstep, lane);
+                    if (lane == 0) *ctl = ok ? 0 : 1;
+                }
+                __syncthreads();
+                if (*ctl) {
                     aborted = true;
                     break;
                 }
@@ -521,91 +466,93 @@ __global__ void __launch_bounds__(32 * kMlpMaxWarps, 1) k_sweep_mlp(const __grid
                 for (int l = l0; l < l1; ++l)
                     for (int j = j0; j < j1; ++j) {
                         if (sub == 0)
-                            mlp_column<HAS_PAIR, -1>(P, RD, wb, L, 4 * j + dy, 4 * l + dz, sweep, beta, lane, accEd,
-                                                     accN);
+                            mlp_column<HAS_PAIR, -1>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
                         else
-                            mlp_column<HAS_PAIR, 0>(P, RD, wb, L, 4 * j + dy, 4 * l + dz, sweep, beta, lane, accEd,
-                                                    accN);
+                            mlp_column<HAS_PAIR, 0>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
                     }
-                const double e_w = warp_sum<double>(accEd);
-                const long long n_w = warp_sum<long long>(accN);
-                if (lane == 0) {
-                    slot_e[slotk] += e_w;
-                    slot_n[slotk] += n_w;
+                // the deciding threads are 0 .. kMlpChunk-1 (warps 0 and 1)
+                if (warp < 2) {
+                    const double e_w = warp_sum<double>(accEd);
+                    const long long n_w = warp_sum<long long>(accN);
+                    if (lane == 0) {
+                        red_e[warp] = e_w;
+                        red_n[warp] = n_w;
+                    }
                 }
-                __syncwarp();
-                if (lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, gstep + 1);
+                __syncthreads();
+                if (tid == 0) {
+                    slot_e[slotk] += red_e[0] + red_e[1];
+                    slot_n[slotk] += red_n[0] + red_n[1];
+                    if (tile != P.skip_tile) st_release_u32(P.flags + tile, gstep + 1);
+                }
             }
         }
     }
-    if (aborted) return;
-    // per-tile partial sums, then the last warp to finish adds them in tile order
-    if (lane == 0) {
+    if (!aborted && tid == 0) {
+        // per-tile partial sums; the last CTA to finish adds them in tile order
         int k = 0;
-        for (int tile = gw; tile < P.ntiles; tile += NW, ++k) {
+        for (int tile = blockIdx.x; tile < P.ntiles; tile += gridDim.x, ++k) {
             P.part_e[tile] = slot_e[k];
             P.part_n[tile] = slot_n[k];
         }
+        __threadfence();
+        const bool last = atomicAdd(P.ticket, 1u) == gridDim.x - 1;
+        if (last) {
+            __threadfence();
+            double se = 0.0;
+            long long sn = 0;
+            for (int k2 = 0; k2 < P.ntiles; ++k2) {
+                se += __ldcg(P.part_e + k2);
+                sn += __ldcg(P.part_n + k2);
+            }
+            if (RD.e_acc) *RD.e_acc += se;
+            if (RD.n_acc) *RD.n_acc += sn;
+        }
     }
-    __threadfence();
-    __syncwarp();
-    unsigned last = 0;
-    if (lane == 0) last = (atomicAdd(P.ticket, 1u) == (unsigned)NW - 1) ? 1u : 0u;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last || lane != 0) return;
-    __threadfence();
-    double se = 0.0;
-    long long sn = 0;
-    for (int k = 0; k < P.ntiles; ++k) {
-        se += __ldcg(P.part_e + k);
-        sn += __ldcg(P.part_n + k);
-    }
-    if (RD.e_acc) *RD.e_acc += se;
-    if (RD.n_acc) *RD.n_acc += sn;
+    tc_teardown(E, kSweepWG);
 }
 
 // ---------------------------------------------------------------------------
-// Lock-step trace of one mini-step: one warp per batch of 4 trials, features
-// read from global memory, pre-swap energies recomputed rather than cached;
-// same tile routine and summation order as the sweep.  Phase 2 (the pair
-// kernel's k_ministep_apply) applies the accepted swaps.
+// Lock-step trace of one mini-step: a CTA per batch of 3 trials, features
+// read from global memory, pre-swap energies recomputed rather than cached
+// (warpgroup 0 evaluates the pre-swap rows, warpgroup 1 the post-swap rows);
+// same evaluator and summation order as the sweep.  k_mlp_trace_apply
+// applies the accepted swaps.
 // ---------------------------------------------------------------------------
-constexpr uint32_t kTraceWarpBytes = 2 * kMlpRows * kARowB + 2 * kMlpRows * 4 + kMlpTB * 32;
-
 template <bool HAS_PAIR>
-__global__ void __launch_bounds__(128) k_mlp_trace_eval(const __grid_constant__ SweepParams P,
-                                                        const __grid_constant__ MlpGeo G, int k, float *dE_out,
-                                                        uint8_t *acc_out, int *swap_a, int *swap_b)
+__global__ void __launch_bounds__(128 * kEvalWG) k_mlp_trace_eval(const __grid_constant__ SweepParams P,
+                                                                const __grid_constant__ MlpGeo G, int k,
+                                                                float *dE_out, uint8_t *acc_out, int *swap_a,
+                                                                int *swap_b)
 {
-    load_mlp_smem(P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    using M = MlpSmem<kEvalWG>;
+    TcEval E = mlp_evaluator<kEvalWG>(P.timeout_ns, P.status, P.abort_flag);
+    mlp_cta_setup<kEvalWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
+    const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
+    const bool post = wg == 1;
     const RepDesc &RD = P.rep[0];
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz;
     const int ntr = RD.NLx * RD.NLy * RD.NLz;
     const int dx = k % 4, dy = (k / 4) % 4, dz = (k / 16) % 4, sub = k / 64;
     const int soff = sub == 0 ? -1 : 0;
-    const uint32_t wb = MlpSmem::END + warp * kTraceWarpBytes;
-    const uint32_t Apost = wb, Apre = wb + kMlpRows * kARowB;
-    float *fpost = (float *)(g_smem + wb + 2 * kMlpRows * kARowB);
-    float *fpre = fpost + kMlpRows;
-    int *tinfo = (int *)(fpre + kMlpRows);  // per trial: a, b, r, A, B, x, y, z
-    const float *Dt = (const float *)(g_smem + MlpSmem::D);
-    const MlpGeo &geo = *(const MlpGeo *)(g_smem + MlpSmem::GEO);
+    // per trial: a, b, r, A, B, x, y, z, dir, post-swap histograms of a (9-11) and b (12-14)
+    int *tinfo = (int *)(g_smem + M::TINFO);
+    float *fpre = (float *)(g_smem + M::END);
+    float *fpost = fpre + kTcRows;
+    const MlpGeo &geo = *(const MlpGeo *)(g_smem + M::GEO);
     const int8_t *occ = RD.occ;
-    for (int c0 = (blockIdx.x * nwarp + warp) * kMlpTB; c0 < ntr; c0 += gridDim.x * nwarp * kMlpTB) {
-        const int nb = min(kMlpTB, ntr - c0);
-        int mydir = 0;
-        if (lane < nb) {
-            const int c = c0 + lane;
+    for (int c0 = blockIdx.x * kTraceTB; c0 < ntr; c0 += gridDim.x * kTraceTB) {
+        const int nb = min(kTraceTB, ntr - c0);
+        if (tid < nb) {
+            const int c = c0 + tid;
             const int cx = c % RD.NLx, cy = (c / RD.NLx) % RD.NLy, cz = c / (RD.NLx * RD.NLy);
             const int x = 4 * cx + dx, y = 4 * cy + dy, z = 4 * cz + dz;
             const uint32_t s = (uint32_t)(((sub * nz + z) * ny + y) * nx + x);
             const uint32_t w = site_word(P.seed, RD.rep, P.sweep0, s);
-            mydir = (int)(w >> kRBits);
-            const int kx = (mydir >> 2) & 1, ky = (mydir >> 1) & 1, kz = mydir & 1;
+            const int dir = (int)(w >> kRBits);
+            const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
             const int bx = wrapc(x + soff + kx, nx), by = wrapc(y + soff + ky, ny), bz = wrapc(z + soff + kz, nz);
-            int *ti = tinfo + lane * 8;
+            int *ti = tinfo + tid * kTinfo;
             ti[0] = (int)s;
             ti[1] = (((1 - sub) * nz + bz) * ny + by) * nx + bx;
             ti[2] = (int)(w & kRMask);
@@ -614,22 +561,14 @@ __global__ void __launch_bounds__(128) k_mlp_trace_eval(const __grid_constant__ 
             ti[5] = x;
             ti[6] = y;
             ti[7] = z;
+            ti[8] = dir;
         }
-        int dirs[kMlpTB];
-#pragma unroll
-        for (int t = 0; t < kMlpTB; ++t) dirs[t] = __shfl_sync(0xffffffffu, mydir, t);
-        __syncwarp();
-        for (int q = lane; q < 2 * nb * kOmega; q += 32) {
-            const bool post = q < nb * kOmega;
-            const int qq = post ? q : q - nb * kOmega;
-            const int t = qq / kOmega, e = qq - t * kOmega;
-            const int *ti = tinfo + t * 8;
+        __syncthreads();
+        if (r < nb * kOmega) {
+            const int t = r / kOmega, e = r - t * kOmega;
+            int *ti = tinfo + t * kTinfo;
             const int a = ti[0], b = ti[1], A = ti[3], B = ti[4];
-            int dir = dirs[0];
-#pragma unroll
-            for (int u = 1; u < kMlpTB; ++u)
-                if (t == u) dir = dirs[u];
-            const OmegaEntry oe = geo.om[sub][dir][e];
+            const OmegaEntry oe = geo.om[sub][ti[8]][e];
             const int ssub = oe.rel ? 1 - sub : sub;
             const int gx = wrapc(ti[5] + oe.dxo, nx), gy = wrapc(ti[6] + oe.dy, ny), gz = wrapc(ti[7] + oe.dz, nz);
             auto spec = [&](int sb, int xx, int yy, int zz) -> int {
@@ -639,38 +578,35 @@ __global__ void __launch_bounds__(128) k_mlp_trace_eval(const __grid_constant__ 
             };
             uint32_t h1, h2, h3;
             site_hist(spec, ssub, gx, gy, gz, h1, h2, h3);
-            write_feature_row((post ? Apost : Apre) + qq * kARowB, spec(ssub, gx, gy, gz), h1, h2, h3);
-        }
-        __syncwarp();
-        const int ntl = (nb * kOmega + 15) / 16;
-        for (int m = 0; m < 2 * ntl; ++m) {
-            const bool post = m < ntl;
-            const int mm = post ? m : m - ntl;
-            float f_lo, f_hi;
-            mlp_tile16((post ? Apost : Apre) + mm * 16 * kARowB, lane, f_lo, f_hi);
-            if ((lane & 3) == 0) {
-                float *dst = post ? fpost : fpre;
-                dst[mm * 16 + (lane >> 2)] = f_lo;
-                dst[mm * 16 + (lane >> 2) + 8] = f_hi;
+            tc_write_features(E.L, r, spec(ssub, gx, gy, gz), h1, h2, h3);
+            if (post && e < 2) {
+                ti[9 + 3 * e] = (int)h1;
+                ti[10 + 3 * e] = (int)h2;
+                ti[11 + 3 * e] = (int)h3;
             }
+        } else {
+            tc_write_features(E.L, r, -1, 0, 0, 0);
         }
-        __syncwarp();
-        if (lane < nb) {
-            const int c = c0 + lane;
-            const int *ti = tinfo + lane * 8;
+        fence_async_smem();
+        const float f = tc_eval(E);
+        (post ? fpost : fpre)[r] = f;
+        __syncthreads();
+        if (tid < nb) {
+            const int c = c0 + tid;
+            const int *ti = tinfo + tid * kTinfo;
             float dE = 0.f;
-            for (int e = 0; e < kOmega; ++e) dE += fpost[lane * kOmega + e] - fpre[lane * kOmega + e];
+            for (int e = 0; e < kOmega; ++e) dE += fpost[tid * kOmega + e] - fpre[tid * kOmega + e];
             const int A = ti[3], B = ti[4];
-            if (HAS_PAIR && A != B)
-                dE += pair_part(P, Dt, Apost + (lane * kOmega) * kARowB, Apost + (lane * kOmega + 1) * kARowB, A, B);
+            if (HAS_PAIR && A != B) dE += pair_part<kEvalWG>(P, ti + 9, ti + 12, A, B);
             const bool acc = metropolis<false>(dE, (uint32_t)ti[2], P.temp.beta[0], nullptr, make_int2(0, 0));
             if (dE_out) dE_out[c] = dE;
             if (acc_out) acc_out[c] = acc ? 1 : 0;
             swap_a[c] = (acc && A != B) ? ti[0] : -1;
             swap_b[c] = ti[1];
         }
-        __syncwarp();
+        __syncthreads();
     }
+    tc_teardown(E, kEvalWG);
 }
 
 __global__ void k_mlp_trace_apply(int8_t *occ, int ntr, const int *swap_a, const int *swap_b)
@@ -833,22 +769,29 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 }  // namespace
 
 // E (+)= sum_i f(x_i); writes the per-site energies to ecache when non-NULL.
-// W is a device MlpBlock; part needs room for the grid's CTA count (<= 8 per SM).
+// W is a device MlpBlock; part needs room for kTcMaxCtasPerSm CTAs per SM;
+// abort_flag is a device word that starts at zero.
 static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const MlpBlock *W, const int8_t *occ,
-                                    float *ecache, double *part, double *e, int accumulate, cudaStream_t stream)
+                                    float *ecache, double *part, int *abort_flag, double *e, int accumulate,
+                                    cudaStream_t stream)
 {
-    const int threads = 128;
-    const size_t smem = MlpSmem::END + (size_t)(threads / 32) * 16 * kARowB;
+    const size_t smem = MlpSmem<kEvalWG>::END;
     cudaError_t err = cudaFuncSetAttribute(k_mlp_site_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute(k_mlp_site_energy)");
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_site_energy, threads, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_site_energy, 128 * kEvalWG, smem);
     if (err != cudaSuccess) return cuda_fail(err, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    per_sm = std::max(1, std::min(per_sm, 8));
+    if (per_sm > kTcMaxCtasPerSm) {
+        // more resident CTAs than tensor-memory allocations: a CTA would wait in tcgen05.alloc
+        set_error("internal error: MLP energy kernel occupancy exceeds tensor memory");
+        return SMC_ERR_STATE;
+    }
+    per_sm = std::max(1, per_sm);
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
-    const long long tiles = (N + 15) / 16;
-    const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ws->num_sms, (tiles + 3) / 4));
-    k_mlp_site_energy<<<grid, threads, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, part);
+    const long long tiles = (N + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ws->num_sms, tiles));
+    k_mlp_site_energy<<<grid, 128 * kEvalWG, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, part,
+                                                           debug_timeout_ns(), ws->status, abort_flag);
     err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_mlp_site_energy");
     if (e) {
@@ -865,16 +808,19 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
-    // scratch: [pair counts | MlpBlock | CTA partial sums]
-    const size_t off_w = round16(sizeof(unsigned long long) * kMaxShells * 64);
+    // scratch: [pair counts | abort word | MlpBlock | CTA partial sums]
+    const size_t off_abort = round16(sizeof(unsigned long long) * kMaxShells * 64);
+    const size_t off_w = off_abort + 16;
     const size_t off_part = round16(off_w + sizeof(MlpBlock));
-    const size_t need = off_part + sizeof(double) * 8 * (size_t)std::max(ws->num_sms, 1);
+    const size_t need = off_part + sizeof(double) * kTcMaxCtasPerSm * (size_t)std::max(ws->num_sms, 1);
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, need, &st);
     if (!scr) return st;
     static MlpBlock W;
     make_mlp_block(m, W);
     cudaError_t err = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemcpyAsync(MLP weights)");
+    err = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
+    if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync(abort word)");
     int accumulate = 0;
     if (m->kind == SMC_PAIR_F32_MLP_BF16) {
         unsigned long long *cnt = (unsigned long long *)scr;
@@ -884,16 +830,18 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
         if (st != SMC_OK) return st;
         accumulate = 1;
     }
-    return mlp_energy_launch(ws, lat, (const MlpBlock *)(scr + off_w), occ, nullptr, (double *)(scr + off_part), e,
-                             accumulate, stream);
+    return mlp_energy_launch(ws, lat, (const MlpBlock *)(scr + off_w), occ, nullptr, (double *)(scr + off_part),
+                             (int *)(scr + off_abort), e, accumulate, stream);
 }
 
 namespace {
 struct MlpPlan {
-    int threads = 0, grid = 0, tpc = 0, ntiles = 0, warp_bytes = 0;
+    int grid = 0, tpc = 0, ntiles = 0;
     size_t smem = 0;
 };
 
+// One CTA per tile at a time; all CTAs resident (cooperative launch), at most
+// as many per SM as tensor memory holds (kSweepWG x kTcCols columns each).
 smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kernel, MlpPlan &pl)
 {
     const Tuning tu = current_tuning();
@@ -903,49 +851,32 @@ smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kern
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    const int rb = mlp_rowB(lat->nx), nk = (lat->nx / 4 + 31) / 32;
+    const int rb = mlp_rowB(lat->nx), NLx = lat->nx / 4;
     pl.ntiles = (lat->ny / 4) * (lat->nz / 4);
-    int best = 0;
-    for (int nw_cta = kMlpMaxWarps; nw_cta >= 1; --nw_cta) {
-        if (tu.threads && tu.threads != 32 * nw_cta) continue;
-        for (int tpc_guess = 1; tpc_guess <= 4096; tpc_guess *= 2) {
-            const size_t wbytes = round16(mlp_warp_layout(rb, nk, tpc_guess).end);
-            const size_t smem = MlpSmem::END + (size_t)nw_cta * wbytes;
-            if (smem > dyn_max) break;
-            int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, 32 * nw_cta, smem);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-            if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
-            if (per_sm < 1) break;
-            const long long res = (long long)per_sm * ws->num_sms * nw_cta;
-            long long nw = 0;
-            for (long long c = std::min<long long>(res, pl.ntiles) / nw_cta * nw_cta; c >= nw_cta; c -= nw_cta)
-                if (pl.ntiles % c == 0) {
-                    nw = c;
-                    break;
-                }
-            const long long fill = std::min<long long>(res, pl.ntiles) / nw_cta * nw_cta;
-            if (nw * 2 < fill) nw = fill;
-            if (nw < nw_cta) nw = nw_cta;
-            const int tpc = (int)((pl.ntiles + nw - 1) / nw);
-            if (tpc <= tpc_guess) {
-                if (nw > best) {
-                    best = (int)nw;
-                    pl.threads = 32 * nw_cta;
-                    pl.grid = (int)(nw / nw_cta);
-                    pl.tpc = tpc_guess;
-                    pl.smem = smem;
-                    pl.warp_bytes = (int)wbytes;
-                }
-                break;
-            }
+    for (int tpc_guess = 1; tpc_guess <= 4096; tpc_guess *= 2) {
+        const size_t smem = mlp_sweep_layout(rb, NLx, tpc_guess).end;
+        if (smem > dyn_max) break;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSweepThreads, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        per_sm = std::min(per_sm, 512 / (kSweepWG * (int)kTcCols));  // tensor-memory columns
+        if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+        if (per_sm < 1) break;
+        // the CTA with the most tiles sets the pace: fill the GPU, then use as
+        // few CTAs as give that same maximum
+        const long long res = std::min<long long>((long long)per_sm * ws->num_sms, pl.ntiles);
+        const long long most = (pl.ntiles + res - 1) / res;
+        const long long nc = (pl.ntiles + most - 1) / most;
+        const int tpc = (int)most;
+        if (tpc <= tpc_guess) {
+            pl.grid = (int)nc;
+            pl.tpc = tpc_guess;
+            pl.smem = smem;
+            return SMC_OK;
         }
     }
-    if (!best) {
-        set_error("MLP sweep kernel does not fit on an SM (rows of %d bytes)", rb);
-        return SMC_ERR_UNSUPPORTED;
-    }
-    return SMC_OK;
+    set_error("MLP sweep kernel does not fit on an SM (rows of %d bytes)", rb);
+    return SMC_ERR_UNSUPPORTED;
 }
 }  // namespace
 
@@ -980,7 +911,6 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.nshells = has_pair ? m->nshells : 0;
     P.S = lat->nspecies;
     P.tpc = pl.tpc;
-    P.warp_bytes = pl.warp_bytes;
     P.nap_cap = 1024;
     P.rowB = rb;
     P.kind = m->kind;
@@ -1012,7 +942,8 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     const size_t off_pe = round16(nt * 4), off_pn = off_pe + nt * 8, off_misc = off_pn + nt * 8;
     const size_t off_w = round16(off_misc + 16);
     const size_t off_parts = round16(off_w + sizeof(MlpBlock));
-    const size_t off_cache = round16(off_parts + sizeof(double) * 8 * (size_t)std::max(ws->num_sms, 1));
+    const size_t off_cache =
+        round16(off_parts + sizeof(double) * kTcMaxCtasPerSm * (size_t)std::max(ws->num_sms, 1));
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_cache + N * 4, &st);
     if (!scr) return st;
     P.flags = (uint32_t *)scr;
@@ -1027,7 +958,10 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     make_mlp_block(m, W);
     cudaError_t e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
-    st = mlp_energy_launch(ws, lat, P.mlpw, occ, P.ecache, (double *)(scr + off_parts), nullptr, 0, stream);
+    e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
+    st = mlp_energy_launch(ws, lat, P.mlpw, occ, P.ecache, (double *)(scr + off_parts), P.abort_flag, nullptr, 0,
+                           stream);
     if (st != SMC_OK) return st;
 
     bool constant = true;
@@ -1043,7 +977,7 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
         e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
         void *args[] = {(void *)&P, (void *)&G};
-        e = cudaLaunchCooperativeKernel(kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream);
+        e = cudaLaunchCooperativeKernel(kernel, dim3(pl.grid), dim3(kSweepThreads), args, pl.smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(MLP sweep)");
     }
     return SMC_OK;
@@ -1075,6 +1009,8 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
     P.seed = seed;
     P.sweep0 = sweep;
     P.kind = m->kind;
+    P.timeout_ns = debug_timeout_ns();
+    P.status = ws->status;
     P.temp.beta[0] = (float)(1.0 / kT);
     RepDesc &d = P.rep[0];
     d.occ = occ;
@@ -1087,23 +1023,32 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
     d.rep = replica;
     if (has_pair) fill_pair_D(m, P.S, P);
     const int ntr = d.NLx * d.NLy * d.NLz;
-    const size_t off_w = round16((size_t)ntr * 8);
+    const size_t off_abort = round16((size_t)ntr * 8);
+    const size_t off_w = off_abort + 16;
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_w + sizeof(MlpBlock), &st);
     if (!scr) return st;
     int *swap_a = (int *)scr, *swap_b = swap_a + ntr;
+    P.abort_flag = (int *)(scr + off_abort);
     P.mlpw = (const MlpBlock *)(scr + off_w);
     static MlpBlock W;
     make_mlp_block(m, W);
     cudaError_t e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
-    const int threads = 128;
-    const size_t smem = MlpSmem::END + (size_t)(threads / 32) * kTraceWarpBytes;
+    e = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(abort word)");
+    const size_t smem = MlpSmem<kEvalWG>::END + 2 * kTcRows * sizeof(float);
     auto kern = has_pair ? k_mlp_trace_eval<true> : k_mlp_trace_eval<false>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mlp_trace_eval)");
-    const int per_block = (threads / 32) * kMlpTB;
-    const int blocks = (ntr + per_block - 1) / per_block;
-    kern<<<blocks, threads, smem, stream>>>(P, G, k, dE, acc, swap_a, swap_b);
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128 * kEvalWG, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm > kTcMaxCtasPerSm) {
+        set_error("internal error: MLP trace kernel occupancy exceeds tensor memory");
+        return SMC_ERR_STATE;
+    }
+    const int blocks = std::max(1, std::min((ntr + kTraceTB - 1) / kTraceTB, std::max(per_sm, 1) * ws->num_sms));
+    kern<<<blocks, 128 * kEvalWG, smem, stream>>>(P, G, k, dE, acc, swap_a, swap_b);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_mlp_trace_eval");
     k_mlp_trace_apply<<<(ntr + 127) / 128, 128, 0, stream>>>(occ, ntr, swap_a, swap_b);
