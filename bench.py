@@ -167,7 +167,12 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=0,
                     help="profiling driver: one sweep launch on an N^3 quinary FP32 lattice, nothing else")
     ap.add_argument("--profile-sweeps", type=int, default=1)
+    ap.add_argument("--profile-mlp", type=int, default=0,
+                    help="run the MLP workload (800 K) on a 256 x n x n box once, for ncu captures")
     args = ap.parse_args()
+    if args.profile_mlp:
+        profile_mlp(args.profile_mlp, args.profile_sweeps)
+        return
     if args.profile_sweep:
         profile_sweep(args.profile_sweep, args.profile_sweeps)
         return
@@ -331,6 +336,29 @@ def profile_sweep(n: int, nsweeps: int):
     smc.sweep(lat, model, occ, 1, 0, nsweeps, inputs.anneal_kT(1000)[:nsweeps])
     smc.check()
     print(json.dumps({"profile_sweep": n, "sweeps": nsweeps, "ok": True}))
+
+
+def profile_mlp(n: int, nsweeps: int):
+    """One MLP sweep launch (nsweeps sweeps; the energy-cache kernel runs
+    first) and one energy evaluation on a 256 x n x n box with the MLP
+    workload's composition, weights and temperature, for ncu captures
+    (-k regex:k_sweep_mlp or regex:k_mlp_site_energy)."""
+    import torch
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    smc.debug_set(smc.DBG_TIMEOUT_MS, 60000)  # replayed launches run slower under the profiler
+    c4 = inputs.CONFIG4
+    S = c4["nspecies"]
+    lat = smc.Lattice(256, n, n, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device="cuda")
+    smc.init_lattice(lat, inputs.dirichlet_counts(lat.nsites, S, c4["comp_seed"]), c4["mc_seed"], occ)
+    model = smc.Model(smc.MLP_BF16, mlp=inputs.mlp_weights(c4["mlp_seed"]))
+    smc.sweep(lat, model, occ, c4["mc_seed"], 0, nsweeps, inputs.K_B_EV * c4["T"])
+    e = torch.zeros(1, dtype=torch.float64, device="cuda")
+    smc.energy(lat, model, occ, e)
+    smc.check()
+    print(json.dumps({"profile_mlp": [256, n, n], "sweeps": nsweeps, "ok": True}))
 
 
 def kernel_traffic(name: str):

@@ -3,10 +3,9 @@
 //
 // A warpgroup of 128 threads evaluates f for a tile of 128 feature rows,
 // thread t owning row t:
-//   layer 1  D1[128 x 64] = X[128 x 32] (W1/2)^T   (2 MMAs, K = 16 each)
-//   epilogue h = D1 + b1/2 = z1/2, silu(z1) = h + h tanh(h) -> BF16 rows of
-//            the layer-2 operand
-//   layer 2  D2[128 x 64] = H1[128 x 64] (W2/2)^T  (4 MMAs)
+//   layer 1  D1[128 x 64] = [X | 1] [W1 | b1]^T / 2 = z1/2   (2 MMAs, K = 16 each)
+//   epilogue silu(z1) = h + h tanh(h), h = D1 -> BF16 rows of the layer-2 operand
+//   layer 2  D2[128 x 64] = [H1 | 1] [W2 | b2]^T / 2 = z2/2  (5 MMAs)
 //   epilogue f = b3 + sum_k W3[k] silu(z2)[k]   (FP32, k in order)
 // One thread issues the MMAs (tcgen05.mma.cta_group::1.kind::f16, BF16
 // inputs, FP32 accumulation) and commits them to an mbarrier; every warp then
@@ -25,15 +24,16 @@
 namespace smc {
 
 constexpr int kTcRows = 128;
+constexpr int kTcK2 = 80;               // layer-2 K: 64 activations, 3 ones for the bias, zero pad
 constexpr uint32_t kTcX = 128 * 64;     // X tile: 128 rows x 32 BF16
-constexpr uint32_t kTcH = 128 * 128;    // H1 tile: 128 rows x 64 BF16
+constexpr uint32_t kTcH = 128 * kTcK2 * 2;  // H1 tile: 128 rows x 80 BF16
 constexpr uint32_t kTcW1 = 64 * 64;     // W1: 64 x 32 BF16
-constexpr uint32_t kTcW2 = 64 * 128;    // W2: 64 x 64 BF16
+constexpr uint32_t kTcW2 = 64 * kTcK2 * 2;  // W2: 64 x 80 BF16
 constexpr uint32_t kTcCols = 128;       // TMEM columns per warpgroup (D1: 0-63, D2: 64-127)
 
-// Byte offset of element chunk kc (8 BF16) of row r in a K = 32 / K = 64 tile.
+// Byte offset of element chunk kc (8 BF16) of row r in a K = 32 / K = 80 tile.
 __host__ __device__ constexpr uint32_t tc_off32(uint32_t r, uint32_t kc) { return (r >> 3) * 512 + kc * 128 + (r & 7) * 16; }
-__host__ __device__ constexpr uint32_t tc_off64(uint32_t r, uint32_t kc) { return (r >> 3) * 1024 + kc * 128 + (r & 7) * 16; }
+__host__ __device__ constexpr uint32_t tc_off80(uint32_t r, uint32_t kc) { return (r >> 3) * 1280 + kc * 128 + (r & 7) * 16; }
 
 // Shared-memory matrix descriptor: start >> 4 (bits 0-13), leading byte
 // offset >> 4 (16-29), stride byte offset >> 4 (32-45), descriptor version 1
@@ -152,6 +152,9 @@ __device__ __forceinline__ void wg_sync(uint32_t bar) { asm volatile("bar.sync %
 // Copies the weights into the evaluator's layout, all scaled by 1/2 (exact:
 // a power of two): the products then give h = z/2 directly and
 // silu(z) = h + h tanh(h), bit for bit the values of the unscaled arithmetic.
+// The FP32 biases ride along as three BF16 parts (hi + mid + lo = b/2
+// exactly) in columns 20-22 of W1 and 64-66 of W2, against constant-one
+// columns of the X and H tiles, so the products already include them.
 __device__ __forceinline__ uint4 half_bf16x8(uint4 v)
 {
     uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -165,23 +168,53 @@ __device__ __forceinline__ uint4 half_bf16x8(uint4 v)
     return make_uint4(w[0], w[1], w[2], w[3]);
 }
 
+__device__ __forceinline__ void split3_bf16(float b, __nv_bfloat16 &hi, __nv_bfloat16 &mid, __nv_bfloat16 &lo)
+{
+    hi = __float2bfloat16_rn(b);
+    const float r1 = b - __bfloat162float(hi);
+    mid = __float2bfloat16_rn(r1);
+    lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
 static __device__ void tc_load_weights(const MlpBlock *W, const TcLayout &L)
 {
     const int tid = threadIdx.x, n = blockDim.x;
     for (int i = tid; i < 64 * 4; i += n) {  // W1: 64 rows x 4 chunks of 16 B
         const int r = i >> 2, kc = i & 3;
-        *(uint4 *)(g_smem + L.w1 + tc_off32(r, kc)) = half_bf16x8(((const uint4 *)W->w1)[r * 4 + kc]);
+        uint4 v = half_bf16x8(((const uint4 *)W->w1)[r * 4 + kc]);
+        if (kc == 2) {  // columns 16-23: inputs 16-19, then b1/2 in columns 20-22
+            __nv_bfloat16 hi, mid, lo;
+            split3_bf16(0.5f * W->b1[r], hi, mid, lo);
+            __nv_bfloat162 p2 = __halves2bfloat162(hi, mid), p3 = __halves2bfloat162(lo, __float2bfloat16_rn(0.f));
+            v.z = *reinterpret_cast<uint32_t *>(&p2);
+            v.w = *reinterpret_cast<uint32_t *>(&p3);
+        }
+        *(uint4 *)(g_smem + L.w1 + tc_off32(r, kc)) = v;
     }
-    for (int i = tid; i < 64 * 8; i += n) {  // W2: 64 rows x 8 chunks
-        const int r = i >> 3, kc = i & 7;
-        *(uint4 *)(g_smem + L.w2 + tc_off64(r, kc)) = half_bf16x8(((const uint4 *)W->w2)[r * 8 + kc]);
+    for (int i = tid; i < 64 * 10; i += n) {  // W2: 64 rows x 10 chunks
+        const int r = i / 10, kc = i - 10 * (i / 10);
+        uint4 v = make_uint4(0, 0, 0, 0);
+        if (kc < 8) {
+            v = half_bf16x8(((const uint4 *)W->w2)[r * 8 + kc]);
+        } else if (kc == 8) {  // columns 64-66: b2/2
+            __nv_bfloat16 hi, mid, lo;
+            split3_bf16(0.5f * W->b2[r], hi, mid, lo);
+            __nv_bfloat162 p0 = __halves2bfloat162(hi, mid), p1 = __halves2bfloat162(lo, __float2bfloat16_rn(0.f));
+            v.x = *reinterpret_cast<uint32_t *>(&p0);
+            v.y = *reinterpret_cast<uint32_t *>(&p1);
+        }
+        *(uint4 *)(g_smem + L.w2 + tc_off80(r, kc)) = v;
     }
-    for (int i = tid; i < 64; i += n) {
-        ((float *)(g_smem + L.b1))[i] = 0.5f * W->b1[i];
-        ((float *)(g_smem + L.b2))[i] = 0.5f * W->b2[i];
-        ((float *)(g_smem + L.w3))[i] = W->w3[i];
-    }
+    for (int i = tid; i < 64; i += n) ((float *)(g_smem + L.w3))[i] = W->w3[i];
     if (tid == 0) *(float *)(g_smem + L.b3) = W->b3;
+}
+
+// Constant columns 64-79 of this thread's row of its warpgroup's H tile:
+// ones in 64-66 (the bias parts of W2), zeros after.
+__device__ __forceinline__ void tc_init_h_row(const TcLayout &L, uint32_t r)
+{
+    *(uint4 *)(g_smem + L.h + tc_off80(r, 8)) = make_uint4(0x3F803F80u, 0x00003F80u, 0u, 0u);
+    *(uint4 *)(g_smem + L.h + tc_off80(r, 9)) = make_uint4(0u, 0u, 0u, 0u);
 }
 
 // silu(2h) = h + h tanh(h), with the hardware tanh approximation.
@@ -199,6 +232,7 @@ static __device__ void tc_setup(TcEval &E, int nwg)
 {
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     const int wg = threadIdx.x >> 7;
+    tc_init_h_row(E.L, threadIdx.x & 127);
     if ((threadIdx.x & 127) == 0) mbar_init(s0 + E.L.mbar, 1);
     if (threadIdx.x < 32) tc_alloc(s0 + E.L.tmem_slot, kTcCols * nwg);
     fence_async_smem();
@@ -239,6 +273,8 @@ __device__ __forceinline__ void tc_write_features(const TcLayout &L, uint32_t r,
                 x = (float)((h2 >> (4 * (col - 10))) & 15u);
             else if (col < 20)
                 x = (float)((h3 >> (4 * (col - 15))) & 15u);
+            else if (col < 23)
+                x = 1.f;  // against the bias parts of W1
             v[u] = x;
         }
         w[c] = pack_bf16(v[0], v[1]);
@@ -283,9 +319,7 @@ static __device__ float tc_eval(TcEval &E)
     E.phase ^= 1;
     tc_fence_after();
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
-    const float *b1 = (const float *)(g_smem + L.b1);
-    const float *b2 = (const float *)(g_smem + L.b2);
-    const float *w3 = (const float *)(g_smem + L.w3);
+    const float4 *w3 = (const float4 *)(g_smem + L.w3);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         uint32_t v[32];
@@ -295,12 +329,10 @@ static __device__ float tc_eval(TcEval &E)
         for (int kc = 0; kc < 4; ++kc) {
             uint32_t w[4];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int c = 32 * half + 8 * kc + 2 * u;
-                w[u] = pack_bf16(silu_of_half(__uint_as_float(v[8 * kc + 2 * u]) + b1[c]),
-                                 silu_of_half(__uint_as_float(v[8 * kc + 2 * u + 1]) + b1[c + 1]));
-            }
-            *(uint4 *)(g_smem + L.h + tc_off64(r, 4 * half + kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+            for (int u = 0; u < 4; ++u)
+                w[u] = pack_bf16(silu_of_half(__uint_as_float(v[8 * kc + 2 * u])),
+                                 silu_of_half(__uint_as_float(v[8 * kc + 2 * u + 1])));
+            *(uint4 *)(g_smem + L.h + tc_off80(r, 4 * half + kc)) = make_uint4(w[0], w[1], w[2], w[3]);
         }
     }
     fence_async_smem();
@@ -309,8 +341,8 @@ static __device__ float tc_eval(TcEval &E)
     if (r == 0) {
         tc_fence_after();
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
-            tc_mma(E.tmem + 64, tc_desc(s0 + L.h + k * 256, 128, 1024), tc_desc(s0 + L.w2 + k * 256, 128, 1024),
+        for (int k = 0; k < kTcK2 / 16; ++k)
+            tc_mma(E.tmem + 64, tc_desc(s0 + L.h + k * 256, 128, 1280), tc_desc(s0 + L.w2 + k * 256, 128, 1280),
                    k > 0);
         tc_commit(s0 + L.mbar);
     }
@@ -324,9 +356,12 @@ static __device__ float tc_eval(TcEval &E)
         tc_ld32(E.tmem + lane_base + 64 + 32 * half, v);
         tc_wait_ld(v);
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-            const int c = 32 * half + j;
-            acc = fmaf(w3[c], silu_of_half(__uint_as_float(v[j]) + b2[c]), acc);
+        for (int j4 = 0; j4 < 8; ++j4) {
+            const float4 w = w3[8 * half + j4];
+            acc = fmaf(w.x, silu_of_half(__uint_as_float(v[4 * j4])), acc);
+            acc = fmaf(w.y, silu_of_half(__uint_as_float(v[4 * j4 + 1])), acc);
+            acc = fmaf(w.z, silu_of_half(__uint_as_float(v[4 * j4 + 2])), acc);
+            acc = fmaf(w.w, silu_of_half(__uint_as_float(v[4 * j4 + 3])), acc);
         }
     }
     tc_fence_before();

@@ -61,6 +61,7 @@ struct SweepParams {
     const MlpBlock *mlpw; // MLP weights (device), MLP kinds only
     float *ecache;        // per-site MLP energy f(x_i) (device, N floats), MLP kinds only
     int rowB;             // fast kernel: row stride in shared memory
+    int mlp_chunk;        // MLP sweep: trials of a mini-step evaluated together
     union {
         float beta[kMaxBeta];
         int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab

@@ -33,7 +33,7 @@ namespace smc {
 constexpr int kOmega = 40;       // sites of a trial's interaction zone
 constexpr int kMlpWinRows = 61;  // 25 trial-sublattice + 36 partner-sublattice rows
 constexpr int kSweepThreads = 512;  // four warpgroups, each with its own tensor-core tiles
-constexpr int kMlpChunk = 64;    // trials of a mini-step evaluated together (40 rows each)
+constexpr int kMlpChunk = 64;    // most trials of a mini-step evaluated together (40 rows each)
 constexpr int kTraceTB = 3;      // trials per trace step (120 rows: one tile)
 constexpr int kTcMaxCtasPerSm = 512 / (2 * kTcCols);  // for the 2-warpgroup kernels
 constexpr int kTinfo = 16;       // ints of per-trial information
@@ -71,7 +71,8 @@ struct MlpSmem {
     static constexpr uint32_t CTL = TSLOT + 4;       // CTA-wide flag
     static constexpr uint32_t RED = (CTL + 4 + 15) / 16 * 16;  // 4 doubles / long longs for reductions
     static constexpr uint32_t TINFO = RED + 64;      // int [kMlpChunk][kTinfo]
-    static constexpr uint32_t D = TINFO + kMlpChunk * kTinfo * 4;  // pair table (kDEntries floats)
+    static constexpr uint32_t ACT = TINFO + kMlpChunk * kTinfo * 4;  // int [kMlpChunk]: trials with A != B
+    static constexpr uint32_t D = ACT + kMlpChunk * 4;  // pair table (kDEntries floats)
     static constexpr uint32_t GEO = D + kDEntries * 4;
     static constexpr uint32_t END = (uint32_t)((GEO + sizeof(MlpGeo) + 127) / 128 * 128);
     static_assert(X % 128 == 0 && H % 128 == 0 && W2 % 128 == 0, "tile alignment");
@@ -209,10 +210,10 @@ struct SweepLayout {  // offsets after MlpSmem<kSweepWG>::END
     uint32_t win, words, fval, diff, site, slots, end;
 };
 
-__host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int rb, int NLx, int tpc)
+__host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int rb, int NLx, int tpc, int chunk)
 {
     SweepLayout L;
-    const uint32_t rows = (uint32_t)kOmega * (uint32_t)(NLx < kMlpChunk ? NLx : kMlpChunk);
+    const uint32_t rows = (uint32_t)kOmega * (uint32_t)(NLx < chunk ? NLx : chunk);
     L.win = MlpSmem<kSweepWG>::END;
     L.words = L.win + (uint32_t)((kMlpWinRows * rb + 32 + 15) / 16 * 16);
     L.fval = L.words + (uint32_t)((NLx * 16 + 15) / 16 * 16);
@@ -221,6 +222,15 @@ __host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int rb, int NLx
     L.slots = L.site + rows * 4;
     L.end = L.slots + (uint32_t)(16 * tpc);
     return L;
+}
+
+__device__ __forceinline__ int warp_of(int tid) { return tid >> 5; }
+
+// Rank of an evaluated trial among the evaluated trials of its warp (or -1).
+__device__ __forceinline__ void tinfo_rank_store(int *tinfo, int tid, bool active, unsigned mask)
+{
+    if (active) tinfo[tid * kTinfo + 15] = __popc(mask & ((1u << (tid & 31)) - 1u));
+    else if (tid < kMlpChunk) tinfo[tid * kTinfo + 15] = -1;
 }
 
 template <bool HAS_PAIR, int SOFF>
@@ -298,9 +308,12 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
     int *sites = (int *)(g_smem + SL.site);
     const uint32_t arow = col0 + 12 * rb;
     for (int dx = 0; dx < 4; ++dx) {
-        for (int i0 = 0; i0 < NLx; i0 += kMlpChunk) {
-            const int T = min(kMlpChunk, NLx - i0), nrow = T * kOmega;
-            // -- decode the trials and swap in shared memory --
+        for (int i0 = 0; i0 < NLx; i0 += P.mlp_chunk) {
+            const int T = min(P.mlp_chunk, NLx - i0);
+            // -- decode the trials and swap in shared memory; a swap of two
+            //    equal species changes nothing (dE = 0, accepted): it is
+            //    counted but not evaluated --
+            int *act = (int *)(g_smem + M::ACT);
             if (tid < T) {
                 const int i = i0 + tid, x = 4 * i + dx;
                 const uint32_t w = wsm[4 * i + dx];
@@ -309,8 +322,10 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 const uint32_t brow = col0 + (uint32_t)(25 + (kz + 2) * 6 + (ky + 2)) * rb;
                 const int xb = x + SOFF + kx;
                 const int A = g_smem[arow + x], B = g_smem[brow + xb];
-                halo_store(arow, x, nx, (unsigned char)B);
-                halo_store(brow, xb, nx, (unsigned char)A);
+                if (A != B) {
+                    halo_store(arow, x, nx, (unsigned char)B);
+                    halo_store(brow, xb, nx, (unsigned char)A);
+                }
                 int *ti = tinfo + tid * kTinfo;
                 ti[0] = dir;
                 ti[1] = (int)(w & kRMask);
@@ -321,15 +336,29 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 ti[6] = x;
                 ti[7] = 0;
             }
+            if (warp_of(tid) < 2) {  // rank of each evaluated trial (warps 0 and 1 hold the T <= 64 trials)
+                const bool active = tid < T && tinfo[tid * kTinfo + 2] != tinfo[tid * kTinfo + 3];
+                const unsigned m = __ballot_sync(0xffffffffu, active);
+                if ((tid & 31) == 0) ((int *)(g_smem + M::RED))[tid >> 5] = __popc(m);
+                __syncwarp();
+                tinfo_rank_store(tinfo, tid, active, m);
+            }
             __syncthreads();
+            const int nact = ((const int *)(g_smem + M::RED))[0] + (T > 32 ? ((const int *)(g_smem + M::RED))[1] : 0);
+            if (tid < T && tinfo[tid * kTinfo + 15] >= 0) {
+                const int rk = tinfo[tid * kTinfo + 15] + (tid >= 32 ? ((const int *)(g_smem + M::RED))[0] : 0);
+                act[rk] = tid;
+            }
+            __syncthreads();
+            const int nrow_act = nact * kOmega;
             // -- post-swap rows, 128 per tile, tiles alternating between the warpgroups --
-            const int ntile = (nrow + kTcRows - 1) / kTcRows;
+            const int ntile = (nrow_act + kTcRows - 1) / kTcRows;
             for (int n = wg; n < ntile; n += kSweepWG) {
                 const int row = n * kTcRows + r;
                 float eo = 0.f;
                 int site = 0;
-                if (row < nrow) {
-                    const int t = row / kOmega, e = row - t * kOmega;
+                if (row < nrow_act) {
+                    const int t = act[row / kOmega], e = row - (row / kOmega) * kOmega;
                     int *ti = tinfo + t * kTinfo;
                     const OmegaEntry oe = geo.om[sub][ti[0]][e];
                     const int ssub = oe.rel ? 1 - sub : sub;
@@ -358,7 +387,7 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 }
                 fence_async_smem();
                 const float f = tc_eval(E);
-                if (row < nrow) {
+                if (row < nrow_act) {
                     fval[row] = f;
                     diff[row] = f - eo;
                     sites[row] = site;
@@ -368,24 +397,30 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
             // -- decisions; rejected swaps are undone --
             if (tid < T) {
                 int *ti = tinfo + tid * kTinfo;
-                float dE = 0.f;
-                for (int e = 0; e < kOmega; ++e) dE += diff[tid * kOmega + e];
                 const int A = ti[2], B = ti[3];
-                if (HAS_PAIR && A != B) dE += pair_part<kSweepWG>(P, ti + 8, ti + 11, A, B);
-                const bool acc = metropolis<false>(dE, (uint32_t)ti[1], beta, nullptr, make_int2(0, 0));
-                ti[7] = acc ? 1 : 0;
-                if (!acc) {
-                    halo_store(arow, ti[6], nx, (unsigned char)A);
-                    halo_store((uint32_t)ti[4], ti[5], nx, (unsigned char)B);
-                } else {
-                    accEd += (double)dE;
+                if (A == B) {
+                    ti[7] = 1;  // dE = 0: accepted, nothing changes
                     accN += 1;
+                } else {
+                    const int base = (ti[15] + (tid >= 32 ? ((const int *)(g_smem + M::RED))[0] : 0)) * kOmega;
+                    float dE = 0.f;
+                    for (int e = 0; e < kOmega; ++e) dE += diff[base + e];
+                    if (HAS_PAIR) dE += pair_part<kSweepWG>(P, ti + 8, ti + 11, A, B);
+                    const bool acc = metropolis<false>(dE, (uint32_t)ti[1], beta, nullptr, make_int2(0, 0));
+                    ti[7] = acc ? 1 : 0;
+                    if (!acc) {
+                        halo_store(arow, ti[6], nx, (unsigned char)A);
+                        halo_store((uint32_t)ti[4], ti[5], nx, (unsigned char)B);
+                    } else {
+                        accEd += (double)dE;
+                        accN += 1;
+                    }
                 }
             }
             __syncthreads();
             // -- cached energies over the accepted trials' Omega --
-            for (int row = tid; row < nrow; row += kSweepThreads)
-                if (tinfo[(row / kOmega) * kTinfo + 7]) P.ecache[sites[row]] = fval[row];
+            for (int row = tid; row < nrow_act; row += kSweepThreads)
+                if (tinfo[act[row / kOmega] * kTinfo + 7]) P.ecache[sites[row]] = fval[row];
             __syncthreads();
         }
     }
@@ -428,7 +463,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_con
     mlp_cta_setup<kSweepWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const RepDesc &RD = P.rep[0];
-    const SweepLayout SL = mlp_sweep_layout(P.rowB, RD.NLx, P.tpc);
+    const SweepLayout SL = mlp_sweep_layout(P.rowB, RD.NLx, P.tpc, P.mlp_chunk);
     double *slot_e = (double *)(g_smem + SL.slots);
     long long *slot_n = (long long *)(g_smem + SL.slots + 8 * P.tpc);
     double *red_e = (double *)(g_smem + M::RED);
@@ -836,7 +871,7 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
 
 namespace {
 struct MlpPlan {
-    int grid = 0, tpc = 0, ntiles = 0;
+    int grid = 0, tpc = 0, ntiles = 0, chunk = kMlpChunk;
     size_t smem = 0;
 };
 
@@ -853,8 +888,10 @@ smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kern
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     const int rb = mlp_rowB(lat->nx), NLx = lat->nx / 4;
     pl.ntiles = (lat->ny / 4) * (lat->nz / 4);
+    // the largest trial chunk (a multiple of 16, up to kMlpChunk) that fits
+    while (pl.chunk > 16 && mlp_sweep_layout(rb, NLx, 1, pl.chunk).end > dyn_max) pl.chunk -= 16;
     for (int tpc_guess = 1; tpc_guess <= 4096; tpc_guess *= 2) {
-        const size_t smem = mlp_sweep_layout(rb, NLx, tpc_guess).end;
+        const size_t smem = mlp_sweep_layout(rb, NLx, tpc_guess, pl.chunk).end;
         if (smem > dyn_max) break;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSweepThreads, smem);
@@ -913,6 +950,7 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.tpc = pl.tpc;
     P.nap_cap = 1024;
     P.rowB = rb;
+    P.mlp_chunk = pl.chunk;
     P.kind = m->kind;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     P.skip_tile = (int)debug_skip_tile();

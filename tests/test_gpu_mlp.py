@@ -167,7 +167,7 @@ def test_mlp_lockstep_against_oracle(smc, dims, kind, T, biases):
 
 
 @pytest.mark.parametrize("dims,kind", [((16, 16, 16), 2), ((24, 16, 8), 2), ((8, 8, 8), 2), ((16, 8, 12), 3),
-                                       ((8, 12, 20), 3)])
+                                       ((8, 12, 20), 3), ((1024, 8, 8), 2), ((300, 12, 8), 3)])
 def test_mlp_sweep_kernel_equals_trace_kernel(smc, dims, kind):
     """Two sweeps of the persistent kernel (cached energies, staged windows,
     neighbour flags) == 256 lock-step mini-steps (recomputed energies): same
