@@ -131,7 +131,8 @@ __device__ __forceinline__ void tc_wait_ld(uint32_t (&r)[32])
                  : "memory");
 }
 
-// Shared-memory offsets (from g_smem) of the pieces the evaluator uses.
+// Shared-memory offsets (from g_smem) of the pieces the evaluator uses
+// (mbar: two mbarriers, one per layer).
 struct TcLayout {
     uint32_t x, h, w1, w2, b1, b2, w3, b3, mbar, tmem_slot;
 };
@@ -141,7 +142,7 @@ struct TcLayout {
 struct TcEval {
     TcLayout L;
     uint32_t tmem;    // TMEM address of this warpgroup's first column (lane 0)
-    uint32_t phase;   // parity of the mbarrier phase to wait for next
+    uint32_t phase1, phase2;  // parities of the two mbarriers' next phases
     uint32_t bar;     // named barrier of the warpgroup (1 + warpgroup index)
     long long timeout_ns;
     int *status, *abort_flag;
@@ -233,14 +234,17 @@ static __device__ void tc_setup(TcEval &E, int nwg)
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     const int wg = threadIdx.x >> 7;
     tc_init_h_row(E.L, threadIdx.x & 127);
-    if ((threadIdx.x & 127) == 0) mbar_init(s0 + E.L.mbar, 1);
+    if ((threadIdx.x & 127) == 0) {
+        mbar_init(s0 + E.L.mbar, 1);
+        mbar_init(s0 + E.L.mbar + 8, 1);
+    }
     if (threadIdx.x < 32) tc_alloc(s0 + E.L.tmem_slot, kTcCols * nwg);
     fence_async_smem();
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
     E.tmem = *(const uint32_t *)(g_smem + E.L.tmem_slot) + kTcCols * wg;
-    E.phase = 0;
+    E.phase1 = E.phase2 = 0;
     E.bar = 1 + wg;
 }
 
@@ -297,13 +301,19 @@ __device__ __forceinline__ void tc_timeout(TcEval &E)
     atomicExch(E.abort_flag, 1);
 }
 
-// f of row (threadIdx.x mod 128) of the warpgroup's X tile.  The 128 threads
-// of the warpgroup call it after writing their rows (with fence_async_smem);
-// it synchronises the warpgroup, so a thread may rewrite its own X row as
-// soon as it returns.
-static __device__ float tc_eval(TcEval &E)
+// The evaluation of a tile in three stages, so that a warpgroup can overlap
+// the products of one tile with the gathers and epilogue of another:
+//   tc_issue1   (after the rows of the X tile are written and fenced)
+//               layer-1 products X -> D1, committed to mbarrier 1
+//   tc_stage2   waits for them, layer-1 epilogue D1 -> H, layer-2 products
+//               H -> D2 committed to mbarrier 2; the X tile is free again
+//   tc_finish   waits for them, returns f of row (threadIdx.x mod 128)
+// All 128 threads of the warpgroup call every stage.  Between tc_stage2 of
+// a tile and its tc_finish the warpgroup may write the next tile's X rows and
+// call tc_issue1 for it (D1 and D2 are distinct TMEM columns).
+static __device__ __forceinline__ void tc_issue1(TcEval &E)
 {
-    const int r = threadIdx.x & 127, wq = r >> 5;
+    const int r = threadIdx.x & 127;
     const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     const TcLayout &L = E.L;
     tc_fence_before();
@@ -315,11 +325,17 @@ static __device__ float tc_eval(TcEval &E)
             tc_mma(E.tmem, tc_desc(s0 + L.x + k * 256, 128, 512), tc_desc(s0 + L.w1 + k * 256, 128, 512), k > 0);
         tc_commit(s0 + L.mbar);
     }
-    if (!mbar_wait(s0 + L.mbar, E.phase, E.timeout_ns)) tc_timeout(E);
-    E.phase ^= 1;
+}
+
+static __device__ __forceinline__ void tc_stage2(TcEval &E)
+{
+    const int r = threadIdx.x & 127, wq = r >> 5;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    const TcLayout &L = E.L;
+    if (!mbar_wait(s0 + L.mbar, E.phase1, E.timeout_ns)) tc_timeout(E);
+    E.phase1 ^= 1;
     tc_fence_after();
     const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
-    const float4 *w3 = (const float4 *)(g_smem + L.w3);
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
         uint32_t v[32];
@@ -344,11 +360,20 @@ static __device__ float tc_eval(TcEval &E)
         for (int k = 0; k < kTcK2 / 16; ++k)
             tc_mma(E.tmem + 64, tc_desc(s0 + L.h + k * 256, 128, 1280), tc_desc(s0 + L.w2 + k * 256, 128, 1280),
                    k > 0);
-        tc_commit(s0 + L.mbar);
+        tc_commit(s0 + L.mbar + 8);
     }
-    if (!mbar_wait(s0 + L.mbar, E.phase, E.timeout_ns)) tc_timeout(E);
-    E.phase ^= 1;
+}
+
+static __device__ __forceinline__ float tc_finish(TcEval &E)
+{
+    const int r = threadIdx.x & 127, wq = r >> 5;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    const TcLayout &L = E.L;
+    if (!mbar_wait(s0 + L.mbar + 8, E.phase2, E.timeout_ns)) tc_timeout(E);
+    E.phase2 ^= 1;
     tc_fence_after();
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    const float4 *w3 = (const float4 *)(g_smem + L.w3);
     float acc = 0.f;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
@@ -366,6 +391,14 @@ static __device__ float tc_eval(TcEval &E)
     }
     tc_fence_before();
     return *(const float *)(g_smem + L.b3) + acc;
+}
+
+// f of row (threadIdx.x mod 128) of the warpgroup's X tile, unpipelined.
+static __device__ __forceinline__ float tc_eval(TcEval &E)
+{
+    tc_issue1(E);
+    tc_stage2(E);
+    return tc_finish(E);
 }
 
 }  // namespace smc

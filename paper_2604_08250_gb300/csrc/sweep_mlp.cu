@@ -8,17 +8,20 @@
 // within three shells (40 sites on BCC), so (Algorithm 1, the reduction of the
 // local energies over Omega before and after the swap)
 //   dE = sum_{j in Omega} f(x'_j) - f(x_j).
-// The post-swap energies f(x'_j) are evaluated on the tensor cores
-// (mlp_tc.cuh); the pre-swap energies come from a per-site cache E[i] = f(x_i)
-// that the same evaluator fills (so both sides are bit-identical) and that
-// accepted trials update over their whole Omega.
+// The sweep keeps two per-site caches, filled at the start of a call by the
+// energy kernel: the energies E[i] = f(x_i) and the features F[i] = {s_i,
+// packed shell counts}.  A trial reads F[j] and E[j] of its 40 zone sites;
+// x'_j = x_j with species A of a moved to B and B of b moved to A in the
+// shells where j sees them (a table from the geometry), so the post-swap rows
+// need no neighbour gathers.  The rows are evaluated on the tensor cores
+// (mlp_tc.cuh) and compared with E[j]; an accepted trial stores x'_j, f(x'_j)
+// and the two swapped species.  Energies of rows come from one evaluator
+// everywhere, so cached and fresh values are bit-identical.
 //
-// Sweep organisation: link-cell columns staged in shared memory, 4 mini-steps
-// per group, neighbour progress flags with bounded waits, as in the pair
-// kernel, but one CTA of 128 threads per tile: a column stages 61 rows (the
-// 5x5 trial-sublattice and 6x6 partner-sublattice rows of its 3-shell reach)
-// and its trials run in batches of 3, whose 120 post-swap feature rows fill
-// one 128-row tensor-core tile (thread t builds and owns row t).
+// Scheduling as in the pair kernel: link-cell columns, 4 mini-steps per
+// group, neighbour progress flags with bounded waits; one CTA of 4
+// warpgroups per tile evaluates up to 64 trials of a mini-step at a time in
+// 128-row tiles alternating between warpgroups.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -31,27 +34,22 @@
 namespace smc {
 
 constexpr int kOmega = 40;       // sites of a trial's interaction zone
-constexpr int kMlpWinRows = 61;  // 25 trial-sublattice + 36 partner-sublattice rows
 constexpr int kSweepThreads = 512;  // four warpgroups, each with its own tensor-core tiles
 constexpr int kMlpChunk = 64;    // most trials of a mini-step evaluated together (40 rows each)
 constexpr int kTraceTB = 3;      // trials per trace step (120 rows: one tile)
 constexpr int kTcMaxCtasPerSm = 512 / (2 * kTcCols);  // for the 2-warpgroup kernels
 constexpr int kTinfo = 16;       // ints of per-trial information
 
-// Omega of a trial for each (trial sublattice, partner direction), relative
-// to the trial site's byte in row (0, 0) of its column window: `same` is the
-// site's own offset, `other` the offset of the same cell in the other
-// sublattice's window (the anchor of its shell-1 neighbours); rel = 0 for the
-// trial sublattice, 1 for the partner's; (dxo, dy, dz) its cell offset.
-// Entry 0 is a, entry 1 is b.
+// Omega of a trial for each (trial sublattice, partner direction): rel = 0
+// for a site of the trial sublattice, 1 for the partner's; (dxo, dy, dz) its
+// cell offset from the trial site's cell.  Entry 0 is a, entry 1 is b.
 struct OmegaEntry {
-    int same, other;
     signed char rel, dy, dz, dxo;
+    signed char ma, mb;  // shell (1-3) in which the site sees a / b, 0 if none
+    signed char pad[2];
 };
 struct MlpGeo {
     OmegaEntry om[2][8][kOmega];
-    int pat1[2][2][8];    // shell-1 neighbour offsets from `other`, per (trial sublattice, rel)
-    int pat23[2][2][18];  // shell-2 then shell-3 neighbour offsets from `same`
 };
 
 // Shared memory of the MLP kernels: weights, the warpgroups' tiles, then
@@ -66,8 +64,8 @@ struct MlpSmem {
     static constexpr uint32_t B2 = B1 + 256;
     static constexpr uint32_t W3 = B2 + 256;
     static constexpr uint32_t B3 = W3 + 256;
-    static constexpr uint32_t MBAR = B3 + 16;        // [NWG]
-    static constexpr uint32_t TSLOT = MBAR + 8 * NWG;
+    static constexpr uint32_t MBAR = B3 + 16;        // [NWG][2]
+    static constexpr uint32_t TSLOT = MBAR + 16 * NWG;
     static constexpr uint32_t CTL = TSLOT + 4;       // CTA-wide flag
     static constexpr uint32_t RED = (CTL + 4 + 15) / 16 * 16;  // 4 doubles / long longs for reductions
     static constexpr uint32_t TINFO = RED + 64;      // int [kMlpChunk][kTinfo]
@@ -88,13 +86,13 @@ __device__ __forceinline__ TcEval mlp_evaluator(long long timeout_ns, int *statu
     using M = MlpSmem<NWG>;
     const uint32_t wg = threadIdx.x >> 7;
     TcEval E;
-    E.L = TcLayout{M::X + wg * kTcX, M::H + wg * kTcH, M::W1, M::W2, M::B1, M::B2, M::W3, M::B3, M::MBAR + 8 * wg,
+    E.L = TcLayout{M::X + wg * kTcX, M::H + wg * kTcH, M::W1, M::W2, M::B1, M::B2, M::W3, M::B3, M::MBAR + 16 * wg,
                    M::TSLOT};
     E.timeout_ns = timeout_ns;
     E.status = status;
     E.abort_flag = abort_flag;
     E.tmem = 0;
-    E.phase = 0;
+    E.phase1 = E.phase2 = 0;
     E.bar = 1 + wg;
     return E;
 }
@@ -143,7 +141,7 @@ __device__ void mlp_cta_setup(TcEval &E, const MlpBlock *W, const float *Dsrc, c
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBlock *W,
                                                                    const int8_t *__restrict__ occ, int nx, int ny,
-                                                                   int nz, float *ecache, double *part,
+                                                                   int nz, float *ecache, uint4 *fcache, double *part,
                                                                    long long timeout_ns, int *status, int *abort_flag)
 {
     constexpr int NWG = kEvalWG;
@@ -154,7 +152,8 @@ __global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBloc
     const long long ntile = (N + kTcRows - 1) / kTcRows;
     auto spec = [&](int sb, int xx, int yy, int zz) { return occ_at(occ, nx, ny, nz, sb, xx, yy, zz); };
     double sum = 0.0;
-    for (long long tl = (long long)NWG * blockIdx.x + wg; tl < ntile; tl += (long long)NWG * gridDim.x) {
+    // one tile's features into the X tile (zeros past the end)
+    auto build = [&](long long tl) {
         const long long s = tl * kTcRows + r;
         int q0 = -1;
         uint32_t h1 = 0, h2 = 0, h3 = 0;
@@ -168,14 +167,31 @@ __global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBloc
             const int sub = (int)(t / nz);
             q0 = occ[s] & 7;
             site_hist(spec, sub, x, y, z, h1, h2, h3);
+            if (fcache) fcache[s] = make_uint4((uint32_t)q0, h1, h2, h3);
         }
         tc_write_features(E.L, r, q0, h1, h2, h3);
         fence_async_smem();
-        const float f = tc_eval(E);
+    };
+    const long long step = (long long)NWG * gridDim.x;
+    long long tl = (long long)NWG * blockIdx.x + wg;
+    if (tl < ntile) {
+        build(tl);
+        tc_issue1(E);
+    }
+    while (tl < ntile) {
+        tc_stage2(E);
+        const long long nx_tl = tl + step;
+        if (nx_tl < ntile) {  // the next tile's gathers and layer-1 products overlap this tile's layer 2
+            build(nx_tl);
+            tc_issue1(E);
+        }
+        const float f = tc_finish(E);
+        const long long s = tl * kTcRows + r;
         if (s < N) {
             if (ecache) ecache[s] = f;
             sum += (double)f;
         }
+        tl = nx_tl;
     }
     // CTA sum in thread order (the X tiles are free once both warpgroups are done)
     double *red = (double *)(g_smem + MlpSmem<NWG>::X);
@@ -207,19 +223,19 @@ __global__ void k_sum_parts(const double *part, int n, double *out, int accumula
 // The sweep.
 // ---------------------------------------------------------------------------
 struct SweepLayout {  // offsets after MlpSmem<kSweepWG>::END
-    uint32_t win, words, fval, diff, site, slots, end;
+    uint32_t words, fval, diff, site, feat, slots, end;
 };
 
-__host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int rb, int NLx, int tpc, int chunk)
+__host__ __device__ __forceinline__ SweepLayout mlp_sweep_layout(int NLx, int tpc, int chunk)
 {
     SweepLayout L;
     const uint32_t rows = (uint32_t)kOmega * (uint32_t)(NLx < chunk ? NLx : chunk);
-    L.win = MlpSmem<kSweepWG>::END;
-    L.words = L.win + (uint32_t)((kMlpWinRows * rb + 32 + 15) / 16 * 16);
+    L.words = MlpSmem<kSweepWG>::END;
     L.fval = L.words + (uint32_t)((NLx * 16 + 15) / 16 * 16);
     L.diff = L.fval + rows * 4;
     L.site = L.diff + rows * 4;
-    L.slots = L.site + rows * 4;
+    L.feat = (L.site + rows * 4 + 15) / 16 * 16;
+    L.slots = L.feat + rows * 16;
     L.end = L.slots + (uint32_t)(16 * tpc);
     return L;
 }
@@ -233,106 +249,57 @@ __device__ __forceinline__ void tinfo_rank_store(int *tinfo, int tid, bool activ
     else if (tid < kMlpChunk) tinfo[tid * kTinfo + 15] = -1;
 }
 
+// The 4 mini-steps of one link-cell column (cells y0, z0 of the trial
+// sublattice; trials at x = 4 i + dx).
 template <bool HAS_PAIR, int SOFF>
 __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &RD, const SweepLayout &SL, TcEval &E,
                                            int y0, int z0, uint64_t sweep, float beta, double &accEd,
                                            long long &accN)
 {
     constexpr int sub = SOFF == -1 ? 0 : 1;
-    constexpr int lo = SOFF - 2;  // first partner-sublattice row (dy, dz) of the window
     const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
-    const uint32_t rb = (uint32_t)P.rowB;
-    const uint32_t col0 = SL.win + 16;  // row 0's body (4-byte halos on both sides)
     using M = MlpSmem<kSweepWG>;
     const MlpGeo &geo = *(const MlpGeo *)(g_smem + M::GEO);
-    auto row_of = [&](int rr, int &gsub, int &gy, int &gz) {
-        int dy, dz;
-        if (rr < 25) {
-            dy = rr % 5 - 2;
-            dz = rr / 5 - 2;
-            gsub = sub;
-        } else {
-            dy = (rr - 25) % 6 + lo;
-            dz = (rr - 25) / 6 + lo;
-            gsub = 1 - sub;
-        }
-        gy = wrapc(y0 + dy, ny);
-        gz = wrapc(z0 + dz, nz);
-    };
-    // ---- stage the 61 rows, mask species, fill halos ----
-    {
-        const bool vec = RD.vec != 0;
-        const int cpr = vec ? (nx >> 4) : (nx >> 2);
-        const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
-        for (int i = tid; i < kMlpWinRows * cpr; i += kSweepThreads) {
-            const int rr = i / cpr, c = i - rr * cpr;
-            int gsub, gy, gz;
-            row_of(rr, gsub, gy, gz);
-            const int8_t *src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
-            const uint32_t dst = col0 + (uint32_t)rr * rb;
-            if (vec)
-                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + dst + 16 * c),
-                             "l"(src + 16 * c)
-                             : "memory");
-            else
-                *(unsigned *)(g_smem + dst + 4 * c) = __ldcg((const unsigned *)src + c);
-        }
-        if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncthreads();
-        const int wpr = nx >> 2;
-        for (int i = tid; i < kMlpWinRows * wpr; i += kSweepThreads) {
-            const int rr = i / wpr, c = i - rr * wpr;
-            *(unsigned *)(g_smem + col0 + rr * rb + 4 * c) &= 0x07070707u;
-        }
-        __syncthreads();
-        for (int rr = tid; rr < kMlpWinRows; rr += kSweepThreads) {
-            unsigned char *row = g_smem + col0 + rr * rb;
-            *(unsigned *)(row - 4) = *(const unsigned *)(row + nx - 4);
-            *(unsigned *)(row + nx) = *(const unsigned *)row;
-        }
-    }
+    int8_t *occ = RD.occ;
     // ---- Philox words of the column's trial sites: [link cell][word] ----
     uint32_t *wsm = (uint32_t *)(g_smem + SL.words);
-    const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
+    const int rowsite = ((sub * nz + z0) * ny + y0) * nx;
     for (int i = tid; i < NLx; i += kSweepThreads) {
-        const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
+        const U4 w = philox10(U4{((uint32_t)rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep,
+                                 (uint32_t)(sweep >> 32)},
                               (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
         *(uint4 *)(wsm + 4 * i) = make_uint4(w.x, w.y, w.z, w.w);
     }
     __syncthreads();
-    // per trial: dir, r, A, B, b row, b x, x, accepted, post-swap histograms of a (8-10) and b (11-13)
+    // per trial: dir, r, A, B, a, b, x, accepted, post-swap histograms of a (8-10) and b (11-13), rank (15)
     int *tinfo = (int *)(g_smem + M::TINFO);
+    int *act = (int *)(g_smem + M::ACT);
+    const int *red_i = (const int *)(g_smem + M::RED);
     float *fval = (float *)(g_smem + SL.fval);
     float *diff = (float *)(g_smem + SL.diff);
     int *sites = (int *)(g_smem + SL.site);
-    const uint32_t arow = col0 + 12 * rb;
+    uint4 *feat = (uint4 *)(g_smem + SL.feat);
     for (int dx = 0; dx < 4; ++dx) {
         for (int i0 = 0; i0 < NLx; i0 += P.mlp_chunk) {
             const int T = min(P.mlp_chunk, NLx - i0);
-            // -- decode the trials and swap in shared memory; a swap of two
-            //    equal species changes nothing (dE = 0, accepted): it is
-            //    counted but not evaluated --
-            int *act = (int *)(g_smem + M::ACT);
+            // -- decode the trials; a swap of two equal species changes nothing
+            //    (dE = 0, accepted): it is counted but not evaluated --
             if (tid < T) {
                 const int i = i0 + tid, x = 4 * i + dx;
                 const uint32_t w = wsm[4 * i + dx];
                 const int dir = (int)(w >> kRBits);
                 const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
-                const uint32_t brow = col0 + (uint32_t)(25 + (kz + 2) * 6 + (ky + 2)) * rb;
-                const int xb = x + SOFF + kx;
-                const int A = g_smem[arow + x], B = g_smem[brow + xb];
-                if (A != B) {
-                    halo_store(arow, x, nx, (unsigned char)B);
-                    halo_store(brow, xb, nx, (unsigned char)A);
-                }
+                const int a = rowsite + x;
+                const int b = (((1 - sub) * nz + wrapc(z0 + SOFF + kz, nz)) * ny + wrapc(y0 + SOFF + ky, ny)) * nx +
+                              wrapc(x + SOFF + kx, nx);
                 int *ti = tinfo + tid * kTinfo;
                 ti[0] = dir;
                 ti[1] = (int)(w & kRMask);
-                ti[2] = A;
-                ti[3] = B;
-                ti[4] = (int)brow;
-                ti[5] = xb;
+                ti[2] = __ldcg(occ + a) & 7;
+                ti[3] = __ldcg(occ + b) & 7;
+                ti[4] = a;
+                ti[5] = b;
                 ti[6] = x;
                 ti[7] = 0;
             }
@@ -344,57 +311,80 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                 tinfo_rank_store(tinfo, tid, active, m);
             }
             __syncthreads();
-            const int nact = ((const int *)(g_smem + M::RED))[0] + (T > 32 ? ((const int *)(g_smem + M::RED))[1] : 0);
-            if (tid < T && tinfo[tid * kTinfo + 15] >= 0) {
-                const int rk = tinfo[tid * kTinfo + 15] + (tid >= 32 ? ((const int *)(g_smem + M::RED))[0] : 0);
-                act[rk] = tid;
-            }
+            const int nact = red_i[0] + (T > 32 ? red_i[1] : 0);
+            if (tid < T && tinfo[tid * kTinfo + 15] >= 0)
+                act[tinfo[tid * kTinfo + 15] + (tid >= 32 ? red_i[0] : 0)] = tid;
             __syncthreads();
             const int nrow_act = nact * kOmega;
-            // -- post-swap rows, 128 per tile, tiles alternating between the warpgroups --
+            // -- post-swap rows from the cached features: 128 per tile, tiles
+            //    alternating between the warpgroups; each warpgroup builds
+            //    tile n+1 and runs its layer-1 products while tile n's layer 2
+            //    is in flight --
             const int ntile = (nrow_act + kTcRows - 1) / kTcRows;
-            for (int n = wg; n < ntile; n += kSweepWG) {
+            auto build = [&](int n, float &eo, int &site) {
                 const int row = n * kTcRows + r;
-                float eo = 0.f;
-                int site = 0;
+                eo = 0.f;
+                site = 0;
                 if (row < nrow_act) {
                     const int t = act[row / kOmega], e = row - (row / kOmega) * kOmega;
                     int *ti = tinfo + t * kTinfo;
                     const OmegaEntry oe = geo.om[sub][ti[0]][e];
                     const int ssub = oe.rel ? 1 - sub : sub;
-                    const int x = ti[6];
-                    const int gx = wrapc(x + oe.dxo, nx), gy = wrapc(y0 + oe.dy, ny), gz = wrapc(z0 + oe.dz, nz);
+                    const int gx = wrapc(ti[6] + oe.dxo, nx), gy = wrapc(y0 + oe.dy, ny), gz = wrapc(z0 + oe.dz, nz);
                     site = ((ssub * nz + gz) * ny + gy) * nx + gx;
+                    const uint4 f = __ldcg(P.fcache + site);
                     eo = __ldcg(P.ecache + site);
-                    const uint32_t bs = col0 + (uint32_t)(oe.same + x), bo = col0 + (uint32_t)(oe.other + x);
-                    const int *p1 = geo.pat1[sub][oe.rel];
-                    const int *p23 = geo.pat23[sub][oe.rel];
-                    uint32_t h1 = 0, h2 = 0, h3 = 0;
+                    const int A = ti[2], B = ti[3];
+                    uint32_t q0 = f.x, h[3] = {f.y, f.z, f.w};
+                    if (e == 0) q0 = (uint32_t)B;
+                    if (e == 1) q0 = (uint32_t)A;
+                    const uint32_t dAB = (1u << (4 * B)) - (1u << (4 * A));  // a: A -> B (mod 2^32)
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) h1 += 1u << (4 * g_smem[bo + p1[k]]);
-#pragma unroll
-                    for (int k = 0; k < 6; ++k) h2 += 1u << (4 * g_smem[bs + p23[k]]);
-#pragma unroll
-                    for (int k = 6; k < 18; ++k) h3 += 1u << (4 * g_smem[bs + p23[k]]);
-                    tc_write_features(E.L, r, g_smem[bs], h1, h2, h3);
+                    for (int m = 0; m < 3; ++m) {
+                        if (oe.ma == m + 1) h[m] += dAB;
+                        if (oe.mb == m + 1) h[m] -= dAB;
+                    }
+                    tc_write_features(E.L, r, (int)q0, h[0], h[1], h[2]);
+                    feat[row] = make_uint4(q0, h[0], h[1], h[2]);
                     if (e < 2) {
-                        ti[8 + 3 * e] = (int)h1;
-                        ti[9 + 3 * e] = (int)h2;
-                        ti[10 + 3 * e] = (int)h3;
+                        ti[8 + 3 * e] = (int)h[0];
+                        ti[9 + 3 * e] = (int)h[1];
+                        ti[10 + 3 * e] = (int)h[2];
                     }
                 } else {
                     tc_write_features(E.L, r, -1, 0, 0, 0);
                 }
                 fence_async_smem();
-                const float f = tc_eval(E);
+            };
+            int n = wg;
+            float eo = 0.f;
+            int site = 0;
+            if (n < ntile) {
+                build(n, eo, site);
+                tc_issue1(E);
+            }
+            while (n < ntile) {
+                tc_stage2(E);
+                const int nn = n + kSweepWG;
+                float eo_n = 0.f;
+                int site_n = 0;
+                if (nn < ntile) {
+                    build(nn, eo_n, site_n);
+                    tc_issue1(E);
+                }
+                const float f = tc_finish(E);
+                const int row = n * kTcRows + r;
                 if (row < nrow_act) {
                     fval[row] = f;
                     diff[row] = f - eo;
                     sites[row] = site;
                 }
+                n = nn;
+                eo = eo_n;
+                site = site_n;
             }
             __syncthreads();
-            // -- decisions; rejected swaps are undone --
+            // -- decisions; an accepted swap is written to the occupancy --
             if (tid < T) {
                 int *ti = tinfo + tid * kTinfo;
                 const int A = ti[2], B = ti[3];
@@ -402,56 +392,30 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                     ti[7] = 1;  // dE = 0: accepted, nothing changes
                     accN += 1;
                 } else {
-                    const int base = (ti[15] + (tid >= 32 ? ((const int *)(g_smem + M::RED))[0] : 0)) * kOmega;
+                    const int base = (ti[15] + (tid >= 32 ? red_i[0] : 0)) * kOmega;
                     float dE = 0.f;
                     for (int e = 0; e < kOmega; ++e) dE += diff[base + e];
                     if (HAS_PAIR) dE += pair_part<kSweepWG>(P, ti + 8, ti + 11, A, B);
                     const bool acc = metropolis<false>(dE, (uint32_t)ti[1], beta, nullptr, make_int2(0, 0));
                     ti[7] = acc ? 1 : 0;
-                    if (!acc) {
-                        halo_store(arow, ti[6], nx, (unsigned char)A);
-                        halo_store((uint32_t)ti[4], ti[5], nx, (unsigned char)B);
-                    } else {
+                    if (acc) {
+                        occ[ti[4]] = (int8_t)B;
+                        occ[ti[5]] = (int8_t)A;
                         accEd += (double)dE;
                         accN += 1;
                     }
                 }
             }
             __syncthreads();
-            // -- cached energies over the accepted trials' Omega --
+            // -- caches over the accepted trials' Omega --
             for (int row = tid; row < nrow_act; row += kSweepThreads)
-                if (tinfo[act[row / kOmega] * kTinfo + 7]) P.ecache[sites[row]] = fval[row];
+                if (tinfo[act[row / kOmega] * kTinfo + 7]) {
+                    P.fcache[sites[row]] = feat[row];
+                    P.ecache[sites[row]] = fval[row];
+                }
             __syncthreads();
         }
     }
-    // ---- write back the trial row (0, 0) and the partner rows (SOFF..SOFF+1)^2 ----
-    {
-        const bool vec = RD.vec != 0;
-        const int cpr = vec ? (nx >> 4) : (nx >> 2);
-        for (int i = tid; i < 5 * cpr; i += kSweepThreads) {
-            const int wr = i / cpr, c = i - wr * cpr;
-            int rr, gsub, gy, gz;
-            if (wr == 0) {
-                rr = 12;
-                gsub = sub;
-                gy = y0;
-                gz = z0;
-            } else {
-                const int ddy = SOFF + ((wr - 1) & 1), ddz = SOFF + ((wr - 1) >> 1);
-                rr = 25 + (ddz - lo) * 6 + (ddy - lo);
-                gsub = 1 - sub;
-                gy = wrapc(y0 + ddy, ny);
-                gz = wrapc(z0 + ddz, nz);
-            }
-            int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
-            const unsigned char *srcs = g_smem + col0 + (uint32_t)rr * rb;
-            if (vec)
-                *((int4 *)dstg + c) = *((const int4 *)srcs + c);
-            else
-                *((unsigned *)dstg + c) = *((const unsigned *)srcs + c);
-        }
-    }
-    __syncthreads();
 }
 
 template <bool HAS_PAIR>
@@ -463,7 +427,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_con
     mlp_cta_setup<kSweepWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const RepDesc &RD = P.rep[0];
-    const SweepLayout SL = mlp_sweep_layout(P.rowB, RD.NLx, P.tpc, P.mlp_chunk);
+    const SweepLayout SL = mlp_sweep_layout(RD.NLx, P.tpc, P.mlp_chunk);
     double *slot_e = (double *)(g_smem + SL.slots);
     long long *slot_n = (long long *)(g_smem + SL.slots + 8 * P.tpc);
     double *red_e = (double *)(g_smem + M::RED);
@@ -684,20 +648,12 @@ void make_mlp_block(const smc_model *m, MlpBlock &W)
 
 namespace {
 
-// Window row (0 .. 60) of cell offset (dy, dz) in window w (0: trial
-// sublattice, rows -2..2; 1: partner sublattice, rows lo..lo+5), or -1.
-int win_row(int w, int lo, int dy, int dz)
-{
-    if (w == 0) return (dy < -2 || dy > 2 || dz < -2 || dz > 2) ? -1 : (dz + 2) * 5 + (dy + 2);
-    return (dy < lo || dy > lo + 5 || dz < lo || dz > lo + 5) ? -1 : 25 + (dz - lo) * 6 + (dy - lo);
-}
-
 struct Cell {
-    int w, x, y, z;  // window (sublattice relative to the trial's) and cell offset
+    int w, x, y, z;  // sublattice relative to the trial's (0 same, 1 other) and cell offset
 };
 
 // The 26 neighbours (8 shell-1, 6 shell-2, 12 shell-3) of a site of
-// sublattice s at window w, cell c, in that order.
+// sublattice s at relative sublattice w, cell c.
 void neighbours(int s, const Cell &c, Cell out[26])
 {
     int n = 0;
@@ -714,28 +670,22 @@ void neighbours(int s, const Cell &c, Cell out[26])
         }
 }
 
-// Builds Omega and the neighbour patterns for row stride rb; fails if a site
-// or a neighbour falls outside the staged window (a geometry error).
-bool build_mlp_geo(int rb, MlpGeo &G)
+// Shell (1-3) of the vector between two sites given by their sublattice and
+// cell, from its squared length in half-cell units (3, 4, 8), else 0.
+int shell_between(int sa, const Cell &a, int sb, const Cell &b)
+{
+    const int dx = 2 * (a.x - b.x) + (sa - sb), dy = 2 * (a.y - b.y) + (sa - sb), dz = 2 * (a.z - b.z) + (sa - sb);
+    const int d2 = dx * dx + dy * dy + dz * dz;
+    return d2 == 3 ? 1 : (d2 == 4 ? 2 : (d2 == 8 ? 3 : 0));
+}
+
+// Omega of every (trial sublattice, partner direction) with the shells in
+// which each zone site sees a and b; fails on a geometry inconsistency.
+bool build_mlp_geo(MlpGeo &G)
 {
     memset(&G, 0, sizeof G);
     for (int ts = 0; ts < 2; ++ts) {
-        const int soff = ts == 0 ? -1 : 0, lo = soff - 2;
-        const int width[2] = {5, 6};
-        for (int w = 0; w < 2; ++w) {
-            const int s = w == 0 ? ts : 1 - ts;
-            const int o = s == 0 ? -1 : 0;
-            for (int u = 0; u < 8; ++u) {
-                const int ex = o + ((u >> 2) & 1), ey = o + ((u >> 1) & 1), ez = o + (u & 1);
-                G.pat1[ts][w][u] = (ez * width[1 - w] + ey) * rb + ex;
-            }
-            Cell nb[26];
-            neighbours(s, Cell{w, 0, 0, 0}, nb);
-            for (int k = 0; k < 18; ++k) {
-                const Cell &c = nb[8 + k];
-                G.pat23[ts][w][k] = (c.z * width[w] + c.y) * rb + c.x;
-            }
-        }
+        const int soff = ts == 0 ? -1 : 0;
         for (int dir = 0; dir < 8; ++dir) {
             std::vector<Cell> om;
             auto add = [&](const Cell &c) {
@@ -752,42 +702,29 @@ bool build_mlp_geo(int rb, MlpGeo &G)
                 neighbours(c.w == 0 ? ts : 1 - ts, c, nb);
                 for (auto &n : nb) add(n);
             }
-            if ((int)om.size() != kOmega) return false;
+            if ((int)om.size() != kOmega || shell_between(ts, a, 1 - ts, b) != 1) return false;
             for (int e = 0; e < kOmega; ++e) {
                 const Cell &c = om[e];
-                const int r_same = win_row(c.w, lo, c.y, c.z), r_other = (1 - c.w) == 0
-                                                                          ? (c.z + 2) * 5 + (c.y + 2)
-                                                                          : 25 + (c.z - lo) * 6 + (c.y - lo);
-                if (r_same < 0 || c.x < -3 || c.x > 3) return false;
+                const int sc = c.w == 0 ? ts : 1 - ts;
                 OmegaEntry &oe = G.om[ts][dir][e];
-                oe.same = r_same * rb + c.x;
-                oe.other = r_other * rb + c.x;
                 oe.rel = (signed char)c.w;
                 oe.dxo = (signed char)c.x;
                 oe.dy = (signed char)c.y;
                 oe.dz = (signed char)c.z;
-                // every neighbour read must land on its own row of the window
-                Cell nb[26];
-                neighbours(c.w == 0 ? ts : 1 - ts, c, nb);
-                for (int k = 0; k < 26; ++k) {
-                    const int r = win_row(nb[k].w, lo, nb[k].y, nb[k].z);
-                    if (r < 0 || nb[k].x < -4 || nb[k].x > 4) return false;
-                    const int off = k < 8 ? oe.other + G.pat1[ts][c.w][k] : oe.same + G.pat23[ts][c.w][k - 8];
-                    if (off != r * rb + nb[k].x) return false;
-                }
+                oe.ma = (signed char)shell_between(sc, c, ts, a);
+                oe.mb = (signed char)shell_between(sc, c, 1 - ts, b);
+                if (c.x < -3 || c.x > 3 || c.y < -3 || c.y > 3 || c.z < -3 || c.z > 3) return false;
+                if (e >= 2 && oe.ma == 0 && oe.mb == 0) return false;  // every zone site sees a or b
             }
         }
     }
     return true;
 }
 
-bool mlp_shape_ok(const smc_lattice *lat, const int8_t *occ)
+bool mlp_shape_ok(const smc_lattice *lat)
 {
-    return lc_edge(lat->nx) == 4 && lc_edge(lat->ny) == 4 && lc_edge(lat->nz) == 4 && lat->nx <= 1024 &&
-           ((uintptr_t)occ % 4 == 0);
+    return lc_edge(lat->nx) == 4 && lc_edge(lat->ny) == 4 && lc_edge(lat->nz) == 4;
 }
-
-int mlp_rowB(int nx) { return ((nx + 15) & ~15) + 16; }
 
 void fill_pair_D(const smc_model *m, int S, SweepParams &P)
 {
@@ -803,12 +740,13 @@ size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
 }  // namespace
 
-// E (+)= sum_i f(x_i); writes the per-site energies to ecache when non-NULL.
+// E (+)= sum_i f(x_i); writes the per-site energies to ecache and the
+// features to fcache when non-NULL.
 // W is a device MlpBlock; part needs room for kTcMaxCtasPerSm CTAs per SM;
 // abort_flag is a device word that starts at zero.
 static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const MlpBlock *W, const int8_t *occ,
-                                    float *ecache, double *part, int *abort_flag, double *e, int accumulate,
-                                    cudaStream_t stream)
+                                    float *ecache, uint4 *fcache, double *part, int *abort_flag, double *e,
+                                    int accumulate, cudaStream_t stream)
 {
     const size_t smem = MlpSmem<kEvalWG>::END;
     cudaError_t err = cudaFuncSetAttribute(k_mlp_site_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -825,7 +763,7 @@ static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
     const long long tiles = (N + kTcRows - 1) / kTcRows;
     const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ws->num_sms, tiles));
-    k_mlp_site_energy<<<grid, 128 * kEvalWG, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, part,
+    k_mlp_site_energy<<<grid, 128 * kEvalWG, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, fcache, part,
                                                            debug_timeout_ns(), ws->status, abort_flag);
     err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_mlp_site_energy");
@@ -865,7 +803,7 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
         if (st != SMC_OK) return st;
         accumulate = 1;
     }
-    return mlp_energy_launch(ws, lat, (const MlpBlock *)(scr + off_w), occ, nullptr, (double *)(scr + off_part),
+    return mlp_energy_launch(ws, lat, (const MlpBlock *)(scr + off_w), occ, nullptr, nullptr, (double *)(scr + off_part),
                              (int *)(scr + off_abort), e, accumulate, stream);
 }
 
@@ -886,12 +824,12 @@ smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kern
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
     e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
-    const int rb = mlp_rowB(lat->nx), NLx = lat->nx / 4;
+    const int NLx = lat->nx / 4;
     pl.ntiles = (lat->ny / 4) * (lat->nz / 4);
     // the largest trial chunk (a multiple of 16, up to kMlpChunk) that fits
-    while (pl.chunk > 16 && mlp_sweep_layout(rb, NLx, 1, pl.chunk).end > dyn_max) pl.chunk -= 16;
+    while (pl.chunk > 16 && mlp_sweep_layout(NLx, 1, pl.chunk).end > dyn_max) pl.chunk -= 16;
     for (int tpc_guess = 1; tpc_guess <= 4096; tpc_guess *= 2) {
-        const size_t smem = mlp_sweep_layout(rb, NLx, tpc_guess, pl.chunk).end;
+        const size_t smem = mlp_sweep_layout(NLx, tpc_guess, pl.chunk).end;
         if (smem > dyn_max) break;
         int per_sm = 0;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSweepThreads, smem);
@@ -912,7 +850,7 @@ smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kern
             return SMC_OK;
         }
     }
-    set_error("MLP sweep kernel does not fit on an SM (rows of %d bytes)", rb);
+    set_error("MLP sweep kernel does not fit on an SM (nx = %d)", lat->nx);
     return SMC_ERR_UNSUPPORTED;
 }
 }  // namespace
@@ -921,8 +859,8 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
                             uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
                             int64_t *n_acc, cudaStream_t stream)
 {
-    if (!mlp_shape_ok(lat, occ)) {
-        set_error("MLP sweeps need every axis a multiple of 4 cells and >= 8, nx <= 1024 and 4-byte aligned occ");
+    if (!mlp_shape_ok(lat)) {
+        set_error("MLP sweeps need every axis a multiple of 4 cells and >= 8");
         return SMC_ERR_UNSUPPORTED;
     }
     smc_status st;
@@ -933,9 +871,8 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     MlpPlan pl;
     st = make_mlp_plan(ws, lat, kernel, pl);
     if (st != SMC_OK) return st;
-    const int rb = mlp_rowB(lat->nx);
     static MlpGeo G;
-    if (!build_mlp_geo(rb, G)) {
+    if (!build_mlp_geo(G)) {
         set_error("internal error: MLP interaction-zone geometry");
         return SMC_ERR_STATE;
     }
@@ -949,7 +886,6 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.S = lat->nspecies;
     P.tpc = pl.tpc;
     P.nap_cap = 1024;
-    P.rowB = rb;
     P.mlp_chunk = pl.chunk;
     P.kind = m->kind;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
@@ -974,7 +910,7 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ % 16 == 0);
     if (has_pair) fill_pair_D(m, P.S, P);
 
-    // workspace: [flags | part_e | part_n | ticket, abort | MlpBlock | energy parts | E cache]
+    // workspace: [flags | part_e | part_n | ticket, abort | MlpBlock | energy parts | E cache | F cache]
     const size_t nt = (size_t)P.ntiles;
     const size_t N = 2ull * lat->nx * lat->ny * lat->nz;
     const size_t off_pe = round16(nt * 4), off_pn = off_pe + nt * 8, off_misc = off_pn + nt * 8;
@@ -982,7 +918,8 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     const size_t off_parts = round16(off_w + sizeof(MlpBlock));
     const size_t off_cache =
         round16(off_parts + sizeof(double) * kTcMaxCtasPerSm * (size_t)std::max(ws->num_sms, 1));
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_cache + N * 4, &st);
+    const size_t off_fcache = round16(off_cache + N * 4);
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_fcache + N * 16, &st);
     if (!scr) return st;
     P.flags = (uint32_t *)scr;
     P.part_e = (double *)(scr + off_pe);
@@ -992,14 +929,15 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.status = ws->status;
     P.mlpw = (const MlpBlock *)(scr + off_w);
     P.ecache = (float *)(scr + off_cache);
+    P.fcache = (uint4 *)(scr + off_fcache);
     static MlpBlock W;
     make_mlp_block(m, W);
     cudaError_t e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
     e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
-    st = mlp_energy_launch(ws, lat, P.mlpw, occ, P.ecache, (double *)(scr + off_parts), P.abort_flag, nullptr, 0,
-                           stream);
+    st = mlp_energy_launch(ws, lat, P.mlpw, occ, P.ecache, P.fcache, (double *)(scr + off_parts), P.abort_flag,
+                           nullptr, 0, stream);
     if (st != SMC_OK) return st;
 
     bool constant = true;
@@ -1034,7 +972,7 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
     if (!ws) return st;
     const bool has_pair = m->kind == SMC_PAIR_F32_MLP_BF16;
     static MlpGeo G;
-    if (!build_mlp_geo(mlp_rowB(lat->nx), G)) {
+    if (!build_mlp_geo(G)) {
         set_error("internal error: MLP interaction-zone geometry");
         return SMC_ERR_STATE;
     }
