@@ -28,7 +28,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from paper_2604_08250_gb300 import inputs  # noqa: E402
+from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
@@ -245,13 +245,8 @@ def main():
         if dist:
             dist.barrier()
     smc.check()
-    total_ms = float(sum(step_ms))
-    if dist:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     attempts_step = prob["N"] * nsw
-    value = world * attempts_step * args.steps / (total_ms * 1e-3)
+    value, total_ms = replicas.job_throughput(float(sum(step_ms)), attempts_step * args.steps, dist, dev)
     sweep_launch_s = float(np.mean(sweep_ms)) * 1e-3
     achieved = BYTES_PER_ATTEMPT * attempts_step / sweep_launch_s / 1e9
 
@@ -274,12 +269,7 @@ def main():
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_ms.append((time.perf_counter() - t0) * 1e3)
-    e2e_total = float(sum(e2e_ms))
-    if dist:
-        t = torch.tensor([e2e_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_total = float(t.item())
-    e2e_value = world * attempts_step * args.steps / (e2e_total * 1e-3)
+    e2e_value, _ = replicas.job_throughput(float(sum(e2e_ms)), attempts_step * args.steps, dist, dev)
 
     extras = {}
     if not args.no_extras and rank == 0:
