@@ -1,315 +1,335 @@
 // mlp_grad.cu -- dE/dtheta of the MLP energy E = sum_i f(x_i) with respect to
 // every MLP parameter (W1, b1, W2, b2, W3, b3), by back-propagation at every
-// site, on the tensor cores.
+// site, on the tcgen05 tensor cores.
 //
 // For one site, with z1 = W1 x + b1, h1 = silu(z1), z2 = W2 h1 + b2,
 // h2 = silu(z2), f = W3 h2 + b3:
 //   d2 = W3 .* silu'(z2),  d1 = (W2^T d2) .* silu'(z1),
 //   dE/dW3 = sum_i h2,  dE/db3 = N,  dE/dW2 = sum_i d2 h1^T,  dE/db2 = sum_i d2,
 //   dE/dW1 = sum_i d1 x^T,  dE/db1 = sum_i d1.
-// A CTA of 4 warps takes 64 sites at a time: each warp runs the forward and
-// backward passes of 16 sites (m16n8k16 BF16 products with the sites as rows)
-// and leaves x, h1, d2 and d1 in shared memory as BF16; then the weight
-// gradients, contractions over the 64 sites, are split across the warps by
-// output rows (ldmatrix.trans turns the site-major tiles into operands).
-// Register accumulators are flushed into an FP64 per-CTA copy every
-// kFlushEvery blocks; the CTA copies are added in CTA order by a second
-// kernel, so the result is bit-reproducible for a given device.
+// A warpgroup takes 128 sites per tile, thread t owning site t (TMEM lane t):
+//   layer 1   D1 = [X | 1] [W1 | b1]^T / 2 = z1/2                (2 MMAs)
+//   epilogue  h1 = silu(z1) -> H tile (BF16), silu'(z1) kept in registers
+//   layer 2   D2 = [H | 1] [W2 | b2]^T / 2 = z2/2                (5 MMAs)
+//   epilogue  h2, d2 -> columns 0-63, 64-127 of the Z tile (BF16)
+//   back      D3 = D2tile W2 (d2 rows, W2 unscaled)             (4 MMAs)
+//   epilogue  d1 = D3 .* silu'(z1) -> columns 128-191 of Z
+// The tiles are site-major (each site's values contiguous), which makes them,
+// read with MN-major descriptors (leading byte offset = stride between 8-site
+// groups, stride byte offset = 128 B between 8-value groups), the operands of
+// the contractions over sites, accumulated in TMEM across tiles:
+//   G1[128 x 80] += [h2 | d2]^T [h1 | 1]  ->  rows 64-127: dW2, db2 (col 64);
+//                                           rows 0-63, col 64: dW3
+//   G2[128 x 32] += [d2 | d1]^T [x | 1]   ->  rows 64-127: dW1 (cols 0-19),
+//                                           db1 (col 20)
+// (8 MMAs each, K = 16 sites).  Every kFlushEvery tile rounds the
+// accumulators are added into an FP64 copy per CTA; a second kernel adds the
+// CTA copies in CTA order, so the result is bit-reproducible for a device.
 #include <algorithm>
 #include <cstring>
 
 #include "mlp_common.cuh"
+#include "mlp_tc.cuh"
 #include "sweep_common.cuh"
 
 namespace smc {
 
-constexpr int kGradWarps = 4;
-constexpr int kGradSites = 16 * kGradWarps;
+constexpr int kGradWG = 2;
+constexpr int kGradThreads = 128 * kGradWG;
 constexpr int kMlpParams = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1;
-constexpr int kFlushEvery = 32;
-// offsets of the parameter groups in the gradient vector
+constexpr int kFlushEvery = 8;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + 64 * 20, kOffW2 = kOffB1 + 64, kOffB2 = kOffW2 + 64 * 64,
               kOffW3 = kOffB2 + 64, kOffB3 = kOffW3 + 64;
+constexpr uint32_t kZRow = 3 * 64 * 2;     // Z tile: h2 | d2 | d1, 192 BF16 per site
+constexpr uint32_t kZ = 128 * kZRow;       // 48 KB
+constexpr uint32_t kW2T = 64 * 64 * 2;     // W2 transposed, K-major [j][k], K = 64
+// TMEM columns of a warpgroup (256 allocated per warpgroup)
+constexpr uint32_t kColD1 = 0, kColD2 = 64, kColG1 = 128, kColG2 = 208;
 
 struct GradSmem {
-    static constexpr uint32_t W1 = 0;                          // [64 out][32 in] BF16, stride 80 B
-    static constexpr uint32_t W2 = W1 + 64 * kW1RowB;          // [64 out][64 in], stride 144 B
-    static constexpr uint32_t W2T = W2 + 64 * kW2RowB;         // transposed: [64 in][64 out]
-    static constexpr uint32_t B1 = W2T + 64 * kW2RowB;         // FP32 [64]
-    static constexpr uint32_t B2 = B1 + 256;
-    static constexpr uint32_t W3 = B2 + 256;
-    static constexpr uint32_t X = W3 + 256;                    // [64 sites][32] BF16, stride 80 B
-    static constexpr uint32_t H1 = X + kGradSites * kARowB;    // [64 sites][64] BF16, stride 144 B
-    static constexpr uint32_t D2 = H1 + kGradSites * kW2RowB;
-    static constexpr uint32_t DL = D2 + kGradSites * kW2RowB;  // d1
-    static constexpr uint32_t ACC = DL + kGradSites * kW2RowB;  // FP64 [kMlpParams]
-    static constexpr uint32_t WACC = (ACC + kMlpParams * 8 + 15) / 16 * 16;  // FP64 [warps][3][64]
-    static constexpr uint32_t END = WACC + kGradWarps * 3 * 64 * 8;
+    static constexpr uint32_t W1 = 0;
+    static constexpr uint32_t W2 = W1 + kTcW1;
+    static constexpr uint32_t W2T = W2 + kTcW2;
+    static constexpr uint32_t W3 = W2T + kW2T;
+    static constexpr uint32_t B3 = W3 + 256;
+    static constexpr uint32_t WG = (B3 + 16 + 127) / 128 * 128;  // per-warpgroup tiles from here
+    static constexpr uint32_t X = 0, H = X + kTcX, Z = H + kTcH, WGSIZE = Z + kZ;  // offsets within a warpgroup
+    static constexpr uint32_t MBAR = WG + kGradWG * WGSIZE;      // [kGradWG][4]
+    static constexpr uint32_t TSLOT = MBAR + 32 * kGradWG;
+    static constexpr uint32_t CNT = TSLOT + 8;                   // long long [kGradWG]
+    static constexpr uint32_t ACC = (CNT + 8 * kGradWG + 15) / 16 * 16;  // FP64 [kMlpParams]
+    static constexpr uint32_t END = ACC + kMlpParams * 8;
 };
+static_assert(GradSmem::WG % 128 == 0 && GradSmem::WGSIZE % 128 == 0, "tile alignment");
 
-__device__ __forceinline__ float sigmoid_approx(float z)
+// Byte offset of chunk kc (8 BF16) of row r in the K = 64 transposed-W2 tile.
+__host__ __device__ constexpr uint32_t w2t_off(uint32_t r, uint32_t kc) { return (r >> 3) * 1024 + kc * 128 + (r & 7) * 16; }
+// Z-tile byte offset of BF16 chunk kc (8 values) of site row r.
+__host__ __device__ constexpr uint32_t z_off(uint32_t r, uint32_t kc) { return (r >> 3) * (kZRow * 8) + kc * 128 + (r & 7) * 16; }
+
+// silu(2h) and silu'(2h) from h with t = tanh(h): h + h t and (1+t)(1+h(1-t))/2.
+__device__ __forceinline__ void silu_pair(float h, float &s, float &ds)
 {
     float t;
-    const float h = 0.5f * z;
     asm("tanh.approx.f32 %0, %1;" : "=f"(t) : "f"(h));
-    return fmaf(0.5f, t, 0.5f);
+    s = fmaf(h, t, h);
+    ds = 0.5f * (1.f + t) * fmaf(h, 1.f - t, 1.f);
 }
 
-__device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3)
+__device__ __forceinline__ void grad_wait(uint32_t mbar, uint32_t &phase, long long timeout_ns, int *status,
+                                          int *abort_flag)
 {
-    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-                 : "r"(addr));
+    if (!mbar_wait(mbar, phase, timeout_ns)) {
+        atomicCAS(status, 0, (int)SMC_ERR_TIMEOUT);
+        atomicExch(abort_flag, 1);
+    }
+    phase ^= 1;
+    tc_fence_after();
 }
 
-__global__ void __launch_bounds__(32 * kGradWarps) k_mlp_grad(const MlpBlock *W, const int8_t *__restrict__ occ,
-                                                              int nx, int ny, int nz, double *part)
+__global__ void __launch_bounds__(kGradThreads, 1) k_mlp_grad(const MlpBlock *W, const int8_t *__restrict__ occ,
+                                                              int nx, int ny, int nz, double *part,
+                                                              long long timeout_ns, int *status, int *abort_flag)
 {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int g = lane >> 2, t = lane & 3;
-    for (int i = tid; i < 64 * 16; i += blockDim.x) {
-        const int r = i >> 4, c = i & 15;
-        *(uint32_t *)(g_smem + GradSmem::W1 + r * kW1RowB + 4 * c) = ((const uint32_t *)W->w1)[r * 16 + c];
-    }
-    for (int i = tid; i < 64 * 64; i += blockDim.x) {
-        const int k = i >> 6, j = i & 63;  // W2[k][j]
-        const uint16_t v = W->w2[i];
-        *(uint16_t *)(g_smem + GradSmem::W2 + k * kW2RowB + 2 * j) = v;
-        *(uint16_t *)(g_smem + GradSmem::W2T + j * kW2RowB + 2 * k) = v;
-    }
-    for (int i = tid; i < 64; i += blockDim.x) {
-        ((float *)(g_smem + GradSmem::B1))[i] = W->b1[i];
-        ((float *)(g_smem + GradSmem::B2))[i] = W->b2[i];
-        ((float *)(g_smem + GradSmem::W3))[i] = W->w3[i];
+    const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7, wq = r >> 5;
+    const uint32_t s0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    const uint32_t base = GradSmem::WG + wg * GradSmem::WGSIZE;
+    TcLayout L{base + GradSmem::X, base + GradSmem::H, GradSmem::W1, GradSmem::W2, 0, 0, GradSmem::W3, GradSmem::B3,
+               GradSmem::MBAR + 32 * wg, GradSmem::TSLOT};
+    const uint32_t Zt = base + GradSmem::Z;
+    // weights: W1, W2 halved with the biases folded in; W2 transposed, unscaled
+    tc_load_weights(W, L);
+    for (int i = tid; i < 64 * 64; i += kGradThreads) {
+        const int k = i >> 6, j = i & 63;  // W2[k][j] -> W2T[j][k]
+        *(uint16_t *)(g_smem + GradSmem::W2T + w2t_off(j, k >> 3) + 2 * (k & 7)) = W->w2[i];
     }
     double *acc64 = (double *)(g_smem + GradSmem::ACC);
-    double *wacc = (double *)(g_smem + GradSmem::WACC);
-    for (int i = tid; i < kMlpParams; i += blockDim.x) acc64[i] = 0.0;
-    for (int i = tid; i < kGradWarps * 3 * 64; i += blockDim.x) wacc[i] = 0.0;
+    for (int i = tid; i < kMlpParams; i += kGradThreads) acc64[i] = 0.0;
+    tc_init_h_row(L, r);
+    if (r == 0)
+        for (int b = 0; b < 4; ++b) mbar_init(s0 + L.mbar + 8 * b, 1);
+    if (tid < 32) tc_alloc(s0 + GradSmem::TSLOT, 512);
+    fence_async_smem();
+    tc_fence_before();
     __syncthreads();
-    const float *b1 = (const float *)(g_smem + GradSmem::B1);
-    const float *b2 = (const float *)(g_smem + GradSmem::B2);
-    const float *w3 = (const float *)(g_smem + GradSmem::W3);
-    const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    tc_fence_after();
+    const uint32_t tmem = *(const uint32_t *)(g_smem + GradSmem::TSLOT) + 256 * wg;
+    const uint32_t bar = 1 + wg;
+    const uint32_t lane_base = (uint32_t)(32 * wq) << 16;
+    uint32_t ph[4] = {0, 0, 0, 0};
+    const float4 *w3 = (const float4 *)(g_smem + GradSmem::W3);
     auto spec = [&](int sb, int xx, int yy, int zz) { return occ_at(occ, nx, ny, nz, sb, xx, yy, zz); };
-
-    float gw2[8][4], gw1[4][4], aw3[16], ab2[16], ab1[16];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) gw2[j][0] = gw2[j][1] = gw2[j][2] = gw2[j][3] = 0.f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) gw1[j][0] = gw1[j][1] = gw1[j][2] = gw1[j][3] = 0.f;
-#pragma unroll
-    for (int j = 0; j < 16; ++j) aw3[j] = ab2[j] = ab1[j] = 0.f;
+    constexpr uint32_t kIdG1 = tc_idesc(128, 80, true, true), kIdG2 = tc_idesc(128, 32, true, true);
+    const long long N = 2LL * nx * ny * nz;
+    const long long ntile = (N + kTcRows - 1) / kTcRows;
+    const long long rounds = (ntile + (long long)kGradWG * gridDim.x - 1) / ((long long)kGradWG * gridDim.x);
     long long nvalid = 0;
+    uint32_t g_acc = 0;  // 0: the next weight-gradient products start the accumulators afresh
 
-    // adds the register accumulators into the CTA's FP64 copy and clears them
+    // adds the TMEM accumulators of this warpgroup into the FP64 copy
     auto flush = [&]() {
-#pragma unroll
-        for (int j = 0; j < 8; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = 16 * warp + g + 8 * (e >> 1), n = 8 * j + 2 * t + (e & 1);
-                acc64[kOffW2 + m * 64 + n] += (double)gw2[j][e];
-                gw2[j][e] = 0.f;
+        uint32_t v[32];
+        if (r >= 64) {
+            const int k = r - 64;
+            for (int c = 0; c < 64; c += 32) {
+                tc_ld32(tmem + lane_base + kColG1 + c, v);
+                tc_wait_ld(v);
+                for (int j = 0; j < 32; ++j) acc64[kOffW2 + k * 64 + c + j] += (double)__uint_as_float(v[j]);
             }
-#pragma unroll
-        for (int j = 0; j < 4; ++j)
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const int m = 16 * warp + g + 8 * (e >> 1), n = 8 * j + 2 * t + (e & 1);
-                if (n < 20) acc64[kOffW1 + m * 20 + n] += (double)gw1[j][e];
-                gw1[j][e] = 0.f;
-            }
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            float a = aw3[q], b = ab2[q], c = ab1[q];
-#pragma unroll
-            for (int o = 4; o < 32; o <<= 1) {
-                a += __shfl_xor_sync(0xffffffffu, a, o);
-                b += __shfl_xor_sync(0xffffffffu, b, o);
-                c += __shfl_xor_sync(0xffffffffu, c, o);
-            }
-            if (g == 0) {
-                const int col = 8 * (q >> 1) + 2 * t + (q & 1);
-                wacc[(warp * 3 + 0) * 64 + col] += (double)a;
-                wacc[(warp * 3 + 1) * 64 + col] += (double)b;
-                wacc[(warp * 3 + 2) * 64 + col] += (double)c;
-            }
-            aw3[q] = ab2[q] = ab1[q] = 0.f;
         }
+        uint32_t u[16];
+        tc_ld16(tmem + lane_base + kColG1 + 64, u);
+        tc_wait_ld16(u);
+        if (r < 64)
+            acc64[kOffW3 + r] += (double)__uint_as_float(u[0]);
+        else
+            acc64[kOffB2 + r - 64] += (double)__uint_as_float(u[0]);
+        tc_ld32(tmem + lane_base + kColG2, v);
+        tc_wait_ld(v);
+        if (r >= 64) {
+            const int j = r - 64;
+            for (int i = 0; i < 20; ++i) acc64[kOffW1 + j * 20 + i] += (double)__uint_as_float(v[i]);
+            acc64[kOffB1 + j] += (double)__uint_as_float(v[20]);
+        }
+        tc_fence_before();
     };
 
-    const long long N = 2LL * nx * ny * nz;
-    const long long nblk = (N + kGradSites - 1) / kGradSites;
-    const uint32_t xrow = GradSmem::X + (uint32_t)(warp * 16) * kARowB;
-    int it = 0;
-    for (long long blk = blockIdx.x; blk < nblk; blk += gridDim.x) {
-        const long long sbase = blk * kGradSites + warp * 16;
-        if (lane < 16) {
-            const long long s = sbase + lane;
-            int q0 = 0;
+    for (long long rd = 0; rd < rounds; ++rd) {
+        const long long tl = (rd * gridDim.x + blockIdx.x) * kGradWG + wg;
+        if (tl < ntile) {
+            // ---- features of site s (row r) ----
+            const long long s = tl * kTcRows + r;
+            const bool valid = s < N;
+            int q0 = -1;
             uint32_t h1 = 0, h2 = 0, h3 = 0;
-            if (s < N) {
-                long long r = s;
-                const int x = (int)(r % nx);
-                r /= nx;
-                const int y = (int)(r % ny);
-                r /= ny;
-                const int z = (int)(r % nz);
-                const int sub = (int)(r / nz);
+            if (valid) {
+                long long t = s;
+                const int x = (int)(t % nx);
+                t /= nx;
+                const int y = (int)(t % ny);
+                t /= ny;
+                const int z = (int)(t % nz);
+                const int sub = (int)(t / nz);
                 q0 = occ[s] & 7;
                 site_hist(spec, sub, x, y, z, h1, h2, h3);
                 ++nvalid;
             }
-            write_feature_row(xrow + lane * kARowB, q0, h1, h2, h3);
+            tc_write_features(L, r, q0, h1, h2, h3);
+            fence_async_smem();
+            tc_fence_before();
+            wg_sync(bar);
+            if (r == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int k = 0; k < 2; ++k)
+                    tc_mma(tmem + kColD1, tc_desc(s0 + L.x + k * 256, 128, 512), tc_desc(s0 + L.w1 + k * 256, 128, 512),
+                           k > 0);
+                tc_commit(s0 + L.mbar);
+            }
+            grad_wait(s0 + L.mbar, ph[0], timeout_ns, status, abort_flag);
+            // ---- layer-1 epilogue: h1 -> H, silu'(z1) kept ----
+            float ds1[64];
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                tc_ld32(tmem + lane_base + kColD1 + 32 * half, v);
+                tc_wait_ld(v);
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 32 * half + 8 * kc + 2 * u;
+                        float sa, sb;
+                        silu_pair(__uint_as_float(v[8 * kc + 2 * u]), sa, ds1[c]);
+                        silu_pair(__uint_as_float(v[8 * kc + 2 * u + 1]), sb, ds1[c + 1]);
+                        w[u] = pack_bf16(sa, sb);
+                    }
+                    *(uint4 *)(g_smem + L.h + tc_off80(r, 4 * half + kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            wg_sync(bar);
+            if (r == 0) {
+                tc_fence_after();
+#pragma unroll
+                for (int k = 0; k < kTcK2 / 16; ++k)
+                    tc_mma(tmem + kColD2, tc_desc(s0 + L.h + k * 256, 128, 1280),
+                           tc_desc(s0 + L.w2 + k * 256, 128, 1280), k > 0);
+                tc_commit(s0 + L.mbar + 8);
+            }
+            grad_wait(s0 + L.mbar + 8, ph[1], timeout_ns, status, abort_flag);
+            // ---- layer-2 epilogue: h2 and d2 = W3 .* silu'(z2) -> Z ----
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                tc_ld32(tmem + lane_base + kColD2 + 32 * half, v);
+                tc_wait_ld(v);
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    uint32_t wh[4], wd[4];
+                    const float4 wa = w3[8 * half + 2 * kc], wb = w3[8 * half + 2 * kc + 1];
+                    const float wv[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        float sa, sb, da, db;
+                        silu_pair(__uint_as_float(v[8 * kc + 2 * u]), sa, da);
+                        silu_pair(__uint_as_float(v[8 * kc + 2 * u + 1]), sb, db);
+                        const float m = valid ? 1.f : 0.f;
+                        wh[u] = pack_bf16(m * sa, m * sb);
+                        wd[u] = pack_bf16(m * wv[2 * u] * da, m * wv[2 * u + 1] * db);
+                    }
+                    *(uint4 *)(g_smem + Zt + z_off(r, 4 * half + kc)) = make_uint4(wh[0], wh[1], wh[2], wh[3]);
+                    *(uint4 *)(g_smem + Zt + z_off(r, 8 + 4 * half + kc)) = make_uint4(wd[0], wd[1], wd[2], wd[3]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            wg_sync(bar);
+            if (r == 0) {
+                tc_fence_after();
+                // back-propagation through W2: D3 = d2 W2 (into the D1 columns)
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                    tc_mma(tmem + kColD1, tc_desc(s0 + Zt + 1024 + k * 256, 128, kZRow * 8),
+                           tc_desc(s0 + GradSmem::W2T + k * 256, 128, 1024), k > 0);
+                // G1 += [h2 | d2]^T [h1 | 1], contraction over the 128 sites
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    tc_mma_i(tmem + kColG1, tc_desc(s0 + Zt + k * 2 * kZRow * 8, kZRow * 8, 128),
+                             tc_desc(s0 + L.h + k * 2 * 1280, 1280, 128), kIdG1, (k > 0) | g_acc);
+                tc_commit(s0 + L.mbar + 16);
+            }
+            grad_wait(s0 + L.mbar + 16, ph[2], timeout_ns, status, abort_flag);
+            // ---- back epilogue: d1 = D3 .* silu'(z1) -> Z ----
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                uint32_t v[32];
+                tc_ld32(tmem + lane_base + kColD1 + 32 * half, v);
+                tc_wait_ld(v);
+#pragma unroll
+                for (int kc = 0; kc < 4; ++kc) {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) {
+                        const int c = 32 * half + 8 * kc + 2 * u;
+                        const float m = valid ? 1.f : 0.f;
+                        w[u] = pack_bf16(m * __uint_as_float(v[8 * kc + 2 * u]) * ds1[c],
+                                         m * __uint_as_float(v[8 * kc + 2 * u + 1]) * ds1[c + 1]);
+                    }
+                    *(uint4 *)(g_smem + Zt + z_off(r, 16 + 4 * half + kc)) = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+            fence_async_smem();
+            tc_fence_before();
+            wg_sync(bar);
+            if (r == 0) {
+                tc_fence_after();
+                // G2 += [d2 | d1]^T [x | 1]
+#pragma unroll
+                for (int k = 0; k < 8; ++k)
+                    tc_mma_i(tmem + kColG2, tc_desc(s0 + Zt + 1024 + k * 2 * kZRow * 8, kZRow * 8, 128),
+                             tc_desc(s0 + L.x + k * 2 * 512, 512, 128), kIdG2, (k > 0) | g_acc);
+                tc_commit(s0 + L.mbar + 24);
+            }
+            grad_wait(s0 + L.mbar + 24, ph[3], timeout_ns, status, abort_flag);  // X, H, Z free again
+            g_acc = 1;
         }
-        __syncwarp();
-        const float v_lo = (sbase + g < N) ? 1.f : 0.f, v_hi = (sbase + g + 8 < N) ? 1.f : 0.f;
-        // ---- forward, layer 1 ----
-        float acc[8][4];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-        for (int kc = 0; kc < 2; ++kc) {
-            const uint32_t ar = xrow + kc * 32 + 4 * t;
-            const uint32_t a0 = lds32(ar + g * kARowB), a1 = lds32(ar + (g + 8) * kARowB);
-            const uint32_t a2 = lds32(ar + g * kARowB + 16), a3 = lds32(ar + (g + 8) * kARowB + 16);
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t br = GradSmem::W1 + (8 * j + g) * kW1RowB + kc * 32 + 4 * t;
-                mma_bf16(acc[j], a0, a1, a2, a3, lds32(br), lds32(br + 16));
+        // ---- every kFlushEvery rounds (and after the last): FP64 accumulation ----
+        if ((rd + 1) % kFlushEvery == 0 || rd + 1 == rounds) {
+            tc_fence_before();
+            __syncthreads();
+            tc_fence_after();
+            for (int w = 0; w < kGradWG; ++w) {
+                if (wg == w && g_acc) flush();
+                __syncthreads();
             }
-        }
-        uint32_t ha[4][4];
-        float sp1[8][4];
-        const uint32_t h1row = GradSmem::H1 + (uint32_t)(warp * 16 + g) * kW2RowB;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = 8 * j + 2 * t;
-            float h[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float z = acc[j][e] + b1[c + (e & 1)];
-                const float sg = sigmoid_approx(z);
-                h[e] = z * sg;
-                sp1[j][e] = sg * fmaf(z, 1.f - sg, 1.f);
-            }
-            ha[j >> 1][(j & 1) * 2 + 0] = pack_bf16(h[0], h[1]);
-            ha[j >> 1][(j & 1) * 2 + 1] = pack_bf16(h[2], h[3]);
-            *(uint32_t *)(g_smem + h1row + 2 * c) = ha[j >> 1][(j & 1) * 2 + 0];
-            *(uint32_t *)(g_smem + h1row + 8 * kW2RowB + 2 * c) = ha[j >> 1][(j & 1) * 2 + 1];
-        }
-        // ---- forward, layer 2; output-layer gradients ----
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t br = GradSmem::W2 + (8 * j + g) * kW2RowB + kc * 32 + 4 * t;
-                mma_bf16(acc[j], ha[kc][0], ha[kc][1], ha[kc][2], ha[kc][3], lds32(br), lds32(br + 16));
-            }
-        uint32_t da[4][4];
-        const uint32_t d2row = GradSmem::D2 + (uint32_t)(warp * 16 + g) * kW2RowB;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = 8 * j + 2 * t;
-            float d[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                const float z = acc[j][e] + b2[c + (e & 1)];
-                const float sg = sigmoid_approx(z);
-                const float v = (e < 2) ? v_lo : v_hi;
-                aw3[2 * j + (e & 1)] = fmaf(z * sg, v, aw3[2 * j + (e & 1)]);
-                d[e] = w3[c + (e & 1)] * (sg * fmaf(z, 1.f - sg, 1.f)) * v;
-                ab2[2 * j + (e & 1)] += d[e];
-            }
-            da[j >> 1][(j & 1) * 2 + 0] = pack_bf16(d[0], d[1]);
-            da[j >> 1][(j & 1) * 2 + 1] = pack_bf16(d[2], d[3]);
-            *(uint32_t *)(g_smem + d2row + 2 * c) = da[j >> 1][(j & 1) * 2 + 0];
-            *(uint32_t *)(g_smem + d2row + 8 * kW2RowB + 2 * c) = da[j >> 1][(j & 1) * 2 + 1];
-        }
-        // ---- backward to layer 1: d1 = (d2 W2) .* silu'(z1) ----
-#pragma unroll
-        for (int j = 0; j < 8; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc)
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t br = GradSmem::W2T + (8 * j + g) * kW2RowB + kc * 32 + 4 * t;
-                mma_bf16(acc[j], da[kc][0], da[kc][1], da[kc][2], da[kc][3], lds32(br), lds32(br + 16));
-            }
-        const uint32_t dlrow = GradSmem::DL + (uint32_t)(warp * 16 + g) * kW2RowB;
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-            const int c = 8 * j + 2 * t;
-            float d[4];
-#pragma unroll
-            for (int e = 0; e < 4; ++e) {
-                d[e] = acc[j][e] * sp1[j][e];
-                ab1[2 * j + (e & 1)] += d[e];
-            }
-            *(uint32_t *)(g_smem + dlrow + 2 * c) = pack_bf16(d[0], d[1]);
-            *(uint32_t *)(g_smem + dlrow + 8 * kW2RowB + 2 * c) = pack_bf16(d[2], d[3]);
-        }
-        __syncthreads();
-        // ---- weight gradients over the 64 sites: warp w owns output rows 16w..16w+15 ----
-#pragma unroll
-        for (int kc = 0; kc < 4; ++kc) {
-            const int sa = kc * 16 + (lane & 7) + ((lane >> 4) << 3);  // A: sites of matrix (lane >> 3)
-            const int ca = 16 * warp + ((lane >> 3) & 1) * 8;
-            const int sb = kc * 16 + (lane & 7) + ((lane >> 3) & 1) * 8;  // B: sites of matrix (lane >> 3)
-            uint32_t a0, a1, a2, a3;
-            ldsm_x4_trans(smem0 + GradSmem::D2 + sa * kW2RowB + 2 * ca, a0, a1, a2, a3);
-#pragma unroll
-            for (int np = 0; np < 4; ++np) {
-                uint32_t b0, b1v, b2v, b3;
-                const int cb = 8 * (2 * np + (lane >> 4));
-                ldsm_x4_trans(smem0 + GradSmem::H1 + sb * kW2RowB + 2 * cb, b0, b1v, b2v, b3);
-                mma_bf16(gw2[2 * np], a0, a1, a2, a3, b0, b1v);
-                mma_bf16(gw2[2 * np + 1], a0, a1, a2, a3, b2v, b3);
-            }
-            ldsm_x4_trans(smem0 + GradSmem::DL + sa * kW2RowB + 2 * ca, a0, a1, a2, a3);
-#pragma unroll
-            for (int np = 0; np < 2; ++np) {
-                uint32_t b0, b1v, b2v, b3;
-                const int cb = 8 * (2 * np + (lane >> 4));
-                ldsm_x4_trans(smem0 + GradSmem::X + sb * kARowB + 2 * cb, b0, b1v, b2v, b3);
-                mma_bf16(gw1[2 * np], a0, a1, a2, a3, b0, b1v);
-                mma_bf16(gw1[2 * np + 1], a0, a1, a2, a3, b2v, b3);
-            }
-        }
-        __syncthreads();
-        if (++it == kFlushEvery) {
-            flush();
-            it = 0;
+            tc_fence_after();
+            g_acc = 0;
         }
     }
-    flush();
-    // site count of the CTA (each valid site was counted by one lane)
+    // site count, then the CTA's FP64 vector
     for (int o = 16; o > 0; o >>= 1) nvalid += __shfl_xor_sync(0xffffffffu, nvalid, o);
-    __shared__ long long cnt[kGradWarps];
-    if (lane == 0) cnt[warp] = nvalid;
+    long long *cnt = (long long *)(g_smem + GradSmem::CNT);
     __syncthreads();
-    for (int c = tid; c < 64; c += blockDim.x) {
-        double sw3 = 0.0, sb2 = 0.0, sb1 = 0.0;
-        for (int w = 0; w < kGradWarps; ++w) {
-            sw3 += wacc[(w * 3 + 0) * 64 + c];
-            sb2 += wacc[(w * 3 + 1) * 64 + c];
-            sb1 += wacc[(w * 3 + 2) * 64 + c];
-        }
-        acc64[kOffW3 + c] = sw3;
-        acc64[kOffB2 + c] = sb2;
-        acc64[kOffB1 + c] = sb1;
-    }
+    if (tid == 0)
+        for (int w = 0; w < kGradWG; ++w) cnt[w] = 0;
+    __syncthreads();
+    if ((tid & 31) == 0) atomicAdd((unsigned long long *)&cnt[wg], (unsigned long long)nvalid);
+    __syncthreads();
     if (tid == 0) {
         long long n = 0;
-        for (int w = 0; w < kGradWarps; ++w) n += cnt[w];
+        for (int w = 0; w < kGradWG; ++w) n += cnt[w];
         acc64[kOffB3] = (double)n;
     }
     __syncthreads();
     double *dst = part + (size_t)blockIdx.x * kMlpParams;
-    for (int i = tid; i < kMlpParams; i += blockDim.x) dst[i] = acc64[i];
+    for (int i = tid; i < kMlpParams; i += kGradThreads) dst[i] = acc64[i];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tid < 32) tc_dealloc(*(const uint32_t *)(g_smem + GradSmem::TSLOT), 512);
 }
 
 // grad[i] = sum over CTAs of part[cta][i], in CTA order.
@@ -328,24 +348,22 @@ smc_status launch_mlp_grad(const smc_lattice *lat, const smc_model *m, const int
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
-    const int threads = 32 * kGradWarps;
     const size_t smem = GradSmem::END;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mlp_grad)");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_grad, threads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_grad, kGradThreads, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (per_sm < 1) {
-        set_error("MLP gradient kernel does not fit on an SM");
-        return SMC_ERR_UNSUPPORTED;
+    if (per_sm != 1) {  // each CTA holds all 512 tensor-memory columns of its SM
+        set_error("MLP gradient kernel occupancy %d (expected 1 CTA per SM)", per_sm);
+        return SMC_ERR_STATE;
     }
-    const Tuning tu = current_tuning();
-    if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
-    const long long nblk = (N + kGradSites - 1) / kGradSites;
-    const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ws->num_sms, nblk));
-    // scratch: [pair counts | MlpBlock | CTA partials]
-    const size_t off_w = (sizeof(unsigned long long) * kMaxShells * 64 + 15) / 16 * 16;
+    const long long ntile = (N + kTcRows - 1) / kTcRows;
+    const int grid = (int)std::max(1LL, std::min<long long>((long long)ws->num_sms, (ntile + kGradWG - 1) / kGradWG));
+    // scratch: [pair counts | abort word | MlpBlock | CTA partials]
+    const size_t off_abort = (sizeof(unsigned long long) * kMaxShells * 64 + 15) / 16 * 16;
+    const size_t off_w = off_abort + 16;
     const size_t off_part = (off_w + sizeof(MlpBlock) + 15) / 16 * 16;
     unsigned char *scr =
         (unsigned char *)workspace_scratch(ws, off_part + sizeof(double) * kMlpParams * (size_t)grid, &st);
@@ -363,9 +381,11 @@ smc_status launch_mlp_grad(const smc_lattice *lat, const smc_model *m, const int
     make_mlp_block(m, W);
     e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
+    e = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(abort word)");
     double *part = (double *)(scr + off_part);
-    k_mlp_grad<<<grid, threads, smem, stream>>>((const MlpBlock *)(scr + off_w), occ, lat->nx, lat->ny, lat->nz,
-                                                part);
+    k_mlp_grad<<<grid, kGradThreads, smem, stream>>>((const MlpBlock *)(scr + off_w), occ, lat->nx, lat->ny, lat->nz,
+                                                     part, debug_timeout_ns(), ws->status, (int *)(scr + off_abort));
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_mlp_grad");
     k_mlp_grad_finish<<<(kMlpParams + 255) / 256, 256, 0, stream>>>(part, grid, grad + npair);
