@@ -33,6 +33,7 @@ from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
 # MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
+INSTR_PER_TRIAL_512 = 357.1  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
 MLP_FLOP_PER_ATTEMPT = 40 * MLP_FLOP_PER_SITE_FWD  # post-swap energies of the 40-site zone (cached pre-swap)
@@ -45,7 +46,7 @@ def peaks():
             d = json.load(f)
         return {"hbm_gbs": float(d["hbm_gbs"]), "bf16_tflops": float(d["bf16_tflops"]),
                 "bf16_tflops_sustained": float(d.get("bf16_tflops_sustained", d["bf16_tflops"])),
-                "source": "measured"}
+                "sm_max_mhz": float(d.get("sm_max_mhz", 2070.0)), "source": "measured"}
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "source": "fallback"}
 
 
@@ -410,9 +411,17 @@ def run_extras(smc, torch, dev, pk):
     nsw = 4
     ms = timed(lambda: smc.sweep(lat, model, occ, 1, 0, nsw, kT[:nsw]), reps=2)
     att = lat.nsites * nsw / (ms * 1e-3)
+    # integer-issue ceiling beside the HBM one: every SM issues at most 4 warp
+    # instructions (128 lanes) per clock, and one trial costs the measured
+    # instructions per trial (profiles/k_sweep_fast_bcc512.md)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    issue_cap = sms * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / INSTR_PER_TRIAL_512
     out["hbm_512"] = {"cells": [n, n, n], "sweeps_per_launch": nsw, "ms_per_sweep": ms / nsw,
                       "attempts_per_s": att, "achieved_gbs": att * BYTES_PER_ATTEMPT / 1e9,
-                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"],
+                      "alu": {"instructions_per_trial": INSTR_PER_TRIAL_512, "issue_ceiling_attempts_per_s": issue_cap,
+                              "frac_of_issue_ceiling": att / issue_cap,
+                              "source": "ncu smsp__inst_executed.sum x 32 / trials, 512^3 sweep"}}
     # gradient of E (pair part) at the 512^3 configuration vs one plain sweep of it
     g = torch.zeros(smc.grad_size(lat, model), dtype=torch.float32, device=dev)
     gms = timed(lambda: smc.energy_grad(lat, model, occ, g), reps=3)
