@@ -89,6 +89,11 @@ def lib():
                                          C.c_uint64, C.c_int32, C.c_double, P(C.c_double),
                                          P(C.c_uint8), P(C.c_int64), P(C.c_int64)]
         L.orc_ministep_trace.restype = C.c_int64
+        L.orc_slab_ghost_cells.argtypes = [P(_Model)]
+        L.orc_slab_ministep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int32, C.c_int32, C.c_int32,
+                                        C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32, C.c_double,
+                                        P(C.c_double), P(C.c_int64)]
+        L.orc_slab_ministep.restype = C.c_int64
         L.orc_grad_size.argtypes = [P(_Lat), P(_Model)]
         L.orc_grad_size.restype = C.c_int64
         L.orc_energy_grad.argtypes = [P(_Lat), P(_Model), P(C.c_int8), P(C.c_double)]
@@ -255,6 +260,24 @@ def ministep_trace(lat, model, occ, seed, sweep_index, k, kT, replica=0):
     if n < 0:
         raise ValueError("orc_ministep_trace rejected its arguments")
     return dE, acc.astype(bool), a, b
+
+
+def slab_ghost_cells(model) -> int:
+    return int(lib().orc_slab_ghost_cells(C.byref(model._c)))
+
+
+def slab_ministep(lat, model, occ_loc, x0, w, g, seed, sweep_index, k, kT, replica=0):
+    """Mini-step k on one x-slab: occ_loc holds cells [x0 - g, x0 + w + g) of
+    the box `lat` as a [2][nz][ny][w + 2g] int8 array, updated in place.
+    Returns (sum of accepted dE, accepted count, trials)."""
+    e = C.c_double(0.0)
+    n = C.c_int64(0)
+    nt = lib().orc_slab_ministep(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ_loc), C.c_int8),
+                                 int(x0), int(w), int(g), C.c_uint64(seed), C.c_uint32(replica),
+                                 C.c_uint64(sweep_index), int(k), float(kT), C.byref(e), C.byref(n))
+    if nt < 0:
+        raise ValueError("orc_slab_ministep rejected its arguments")
+    return e.value, n.value, int(nt)
 
 
 def energy_grad(lat, model, occ) -> np.ndarray:

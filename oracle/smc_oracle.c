@@ -506,12 +506,14 @@ static int make_table(const orc_model *m, double kT, acc_tab *at)
     return 0;
 }
 
-/* One trial: returns 1 if accepted; *dE_out gets dE. */
-static int one_trial(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
-                     uint32_t replica, uint64_t sweep, int64_t a, double kT, const acc_tab *at,
-                     double *dE_out, int64_t *b_out)
+/* One trial at site a of `lat` whose random word is that of site id `a_rng`
+ * (the same site in the whole box; a_rng = a unless `lat` is one slab of it).
+ * Returns 1 if accepted; *dE_out gets dE. */
+static int one_trial_at(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
+                        uint32_t replica, uint64_t sweep, int64_t a, int64_t a_rng, double kT,
+                        const acc_tab *at, double *dE_out, int64_t *b_out)
 {
-    uint32_t w = site_word(seed, replica, sweep, a);
+    uint32_t w = site_word(seed, replica, sweep, a_rng);
     int dir = (int)(w >> R_BITS);
     uint32_t r = w & ((1u << R_BITS) - 1u);
     const int *v = g_shell_v[1][dir];
@@ -530,6 +532,13 @@ static int one_trial(const orc_lattice *lat, const orc_model *m, int8_t *occ, ui
     *dE_out = dE;
     if (b_out) *b_out = b;
     return acc;
+}
+
+static int one_trial(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
+                     uint32_t replica, uint64_t sweep, int64_t a, double kT, const acc_tab *at,
+                     double *dE_out, int64_t *b_out)
+{
+    return one_trial_at(lat, m, occ, seed, replica, sweep, a, a, kT, at, dE_out, b_out);
 }
 
 /* Algorithm 1 as printed, for one mini-step: sigma1 = sigma0, every trial
@@ -668,6 +677,67 @@ int64_t orc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *o
     }
     free(at.T);
     return NC;
+}
+
+/* ------------------------------------------------------------------------ */
+/* One x-slab of the box (Sec. III-B, 1D slab decomposition).  A slab owns   */
+/* the cells x0 <= x < x0 + w of every sublattice, y and z, and holds g more */
+/* cells on each side (ghosts, x taken modulo nx) in occ_loc, laid out as a  */
+/* box of w + 2g cells along x: [sub][z][y][x - x0 + g].  The trials of      */
+/* mini-step k whose site lies in the slab run exactly as in the whole box:  */
+/* same link cells in the same order, random words of the global site ids.   */
+/* Reads reach g cells past the slab at most, so the local box never wraps.  */
+/* ------------------------------------------------------------------------ */
+
+/* Cells a trial reads beyond its own cell along x.  Positions along x are
+ * integers (sublattice 0) or half-integers (sublattice 1) in units of the
+ * cell edge.  The partner b sits 1/2 away; every shell-1..3 vector moves x
+ * by 1 at most.  Pair models read the shells of a and b: 1.5 from a, which
+ * is 2 cells.  MLP models change the energies of Omega (a, b and their
+ * shell-1..3 neighbours, 1.5 from a), and each of those reads its own
+ * shells: 2.5 from a, which is 3 cells. */
+int orc_slab_ghost_cells(const orc_model *m)
+{
+    return has_mlp(m) ? 3 : 2;
+}
+
+int64_t orc_slab_ministep(const orc_lattice *glat, const orc_model *m, int8_t *occ_loc,
+                          int32_t x0, int32_t w, int32_t g, uint64_t seed, uint32_t replica,
+                          uint64_t sweep, int32_t k, double kT, double *e_acc, int64_t *n_acc)
+{
+    geom_init();
+    if (!lattice_ok(glat) || !model_ok(glat, m)) return -1;
+    sched sc;
+    make_sched(glat, &sc);
+    if (glat->nx < 8 || sc.L[0] != 4 || k < 0 || k >= sc.nA) return -1;
+    if (x0 < 0 || w < 4 || x0 % 4 != 0 || w % 4 != 0 || x0 + w > glat->nx) return -1;
+    if (g < orc_slab_ghost_cells(m) || g > w) return -1;
+    orc_lattice loc = *glat;
+    loc.nx = w + 2 * g;
+    if (!lattice_ok(&loc)) return -1;
+    acc_tab at;
+    if (make_table(m, kT, &at) != 0) return -1;
+    int dx = k % 4, r = k / 4;
+    int dy = r % sc.L[1];
+    r /= sc.L[1];
+    int dz = r % sc.L[2];
+    int sub = r / sc.L[2];
+    int64_t nt = 0;
+    for (int cz = 0; cz < sc.NL[2]; ++cz)
+        for (int cy = 0; cy < sc.NL[1]; ++cy)
+            for (int cx = x0 / 4; cx < (x0 + w) / 4; ++cx) {
+                int x = cx * 4 + dx, y = cy * sc.L[1] + dy, z = cz * sc.L[2] + dz;
+                int64_t a_glob = site_id(glat, sub, x, y, z);
+                int64_t a_loc = site_id(&loc, sub, x - x0 + g, y, z);
+                double dE;
+                if (one_trial_at(&loc, m, occ_loc, seed, replica, sweep, a_loc, a_glob, kT, &at, &dE, NULL)) {
+                    if (e_acc) *e_acc += dE;
+                    if (n_acc) *n_acc += 1;
+                }
+                ++nt;
+            }
+    free(at.T);
+    return nt;
 }
 
 /* ------------------------------------------------------------------------ */

@@ -107,6 +107,18 @@ int64_t orc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *o
                            double kT, double *dE, uint8_t *acc, int64_t *site_a,
                            int64_t *site_b);
 
+/* 1D slab decomposition along x (Sec. III-B).  orc_slab_ghost_cells: the
+ * cells a trial reads past its own along x (2 for pair models, 3 with the
+ * MLP).  orc_slab_ministep: the trials of mini-step k whose sites lie in
+ * cells [x0, x0 + w) of the box `glat`, on occ_loc = that slab plus g ghost
+ * cells per side ([sub][z][y][x - x0 + g], w + 2g cells along x, x modulo
+ * nx).  Needs nx >= 8 with nx % 4 == 0, x0 and w multiples of 4 and
+ * ghost cells <= g <= w.  Returns the number of trials, or -1. */
+int orc_slab_ghost_cells(const orc_model *m);
+int64_t orc_slab_ministep(const orc_lattice *glat, const orc_model *m, int8_t *occ_loc,
+                          int32_t x0, int32_t w, int32_t g, uint64_t seed, uint32_t replica,
+                          uint64_t sweep, int32_t k, double kT, double *e_acc, int64_t *n_acc);
+
 /* dE/dtheta: pair part [nshells][S(S+1)/2] (p <= q), then (MLP models) the
  * 5569 MLP parameters in the order W1, b1, W2, b2, W3, b3. */
 int64_t orc_grad_size(const orc_lattice *lat, const orc_model *m);
