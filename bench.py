@@ -33,7 +33,7 @@ from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
 # MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
-INSTR_PER_TRIAL_512 = 357.1  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
+INSTR_PER_TRIAL_512 = 352.9  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
 MLP_FLOP_PER_ATTEMPT = 40 * MLP_FLOP_PER_SITE_FWD  # post-swap energies of the 40-site zone (cached pre-swap)

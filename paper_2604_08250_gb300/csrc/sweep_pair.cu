@@ -463,11 +463,21 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
 // c[S-1] = -sum_{q<S-1} c[q].  The kernel's table row for (m, A, B) holds
 // D'[q] = D[q] - D[S-1] for q < S-1 and, in entry 7, -8 sum_q D'[q] (the
 // 4-bit fields of shells 1 and 2 carry a bias of 8).
+// In shared memory the fast kernel keeps the table rows (m, A, B) of its
+// species template ST compactly, RS = fast_rs(ST) words each: D'[0..ST-2],
+// then the bias.  An odd stride for ST = 2 and 5 sends the rows of the up
+// to 25 (A, B) pairs a warp reads at once to distinct banks.
+__host__ __device__ constexpr int fast_rs(int ST) { return ST == 8 ? 8 : (ST | 1); }
+__host__ __device__ constexpr int fast_d_bytes(int NSH, int ST)
+{
+    return ((NSH >= 3 ? 3 : 2) * ST * ST * fast_rs(ST) * 4 + 15) / 16 * 16;
+}
+
 template <bool IS_INT, int S>
 __device__ __forceinline__ typename Acc<IS_INT>::T dot_biased(uint32_t H, const typename Acc<IS_INT>::T *D)
 {
     using T = typename Acc<IS_INT>::T;
-    T acc = D[7];
+    T acc = D[S - 1];
 #pragma unroll
     for (int q = 0; q < S - 1; ++q) {
         const int f = (int)((H >> (4 * q)) & 15u);
@@ -541,8 +551,9 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
         H1 -= NIB(SM8(ob)) + NIB(SM8(ob + 1)) + NIB(SM8(ob + rb)) + NIB(SM8(ob + rb + 1)) + NIB(SM8(ob + 3 * rb)) +
               NIB(SM8(ob + 3 * rb + 1)) + NIB(SM8(ob + 4 * rb)) + NIB(SM8(ob + 4 * rb + 1));
     }
+    constexpr int RS = fast_rs(S), SH = S * S * RS;
     const T *Dt = (const T *)(g_smem + dt);
-    const T *D1 = Dt + (A * kMaxSpecies + B) * kMaxSpecies;
+    const T *D1 = Dt + (A * S + B) * RS;
     T dE = dot_biased<IS_INT, S>(H1, D1);
     const uint32_t bx = rbp + xb;
     // partner rows one slot down / up in z (compact layout: 3 or 4 rows apart)
@@ -555,7 +566,7 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
               NIB(SM8(po[7] + x));
         H2 -= NIB(SM8(bx - 1)) + NIB(SM8(bx + 1)) + NIB(SM8(bx - rb)) + NIB(SM8(bx + rb)) + NIB(SM8(bx - zdn)) +
               NIB(SM8(bx + zup));
-        dE += dot_biased<IS_INT, S>(H2, D1 + kMaxSpecies * kMaxSpecies * kMaxSpecies);
+        dE += dot_biased<IS_INT, S>(H2, D1 + SH);
     }
     if (NSH >= 3) {
         const uint32_t Ha = NIB(SM8(po[0] + x)) + NIB(SM8(po[2] + x)) + NIB(SM8(po[6] + x)) + NIB(SM8(po[8] + x)) +
@@ -566,7 +577,7 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
                             NIB(SM8(bx + 5 * rb)) + NIB(SM8(bx - rb - 1)) + NIB(SM8(bx - rb + 1)) +
                             NIB(SM8(bx + rb - 1)) + NIB(SM8(bx + rb + 1)) + NIB(SM8(bx - 4 * rb - 1)) +
                             NIB(SM8(bx - 4 * rb + 1)) + NIB(SM8(bx + 4 * rb - 1)) + NIB(SM8(bx + 4 * rb + 1));
-        dE += dot_diff<IS_INT, S>(Ha, Hb, D1 + 2 * kMaxSpecies * kMaxSpecies * kMaxSpecies);
+        dE += dot_diff<IS_INT, S>(Ha, Hb, D1 + 2 * SH);
     }
     return dE;
 }
@@ -575,8 +586,8 @@ __device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, u
 template <bool IS_INT, int NSH, int S, int SOFF, int KU, bool GUARD>
 __device__ __forceinline__ void fast_trials(const SweepParams &P, const uint32_t *po, uint32_t col0, uint32_t rb,
                                             const uint32_t *wsm, int k0, int nk, int NLx, int nx, int dx, int lane,
-                                            float beta, int2 ti, uint32_t dt, typename Acc<IS_INT>::T &accE,
-                                            double &accEd, long long &accN)
+                                            float beta, int2 ti, uint32_t dt, typename Acc<IS_INT>::T &colE,
+                                            long long &accN)
 {
     using T = typename Acc<IS_INT>::T;
     T dE[KU];
@@ -600,10 +611,7 @@ __device__ __forceinline__ void fast_trials(const SweepParams &P, const uint32_t
         if (acc[u]) {
             halo_store(po[4], xs[u], nx, (unsigned char)B[u]);
             halo_store(brow[u], xb[u], nx, (unsigned char)A[u]);
-            if constexpr (IS_INT)
-                accE += dE[u];
-            else
-                accEd += (double)dE[u];
+            colE += dE[u];
             accN += 1;
         }
     }
@@ -614,6 +622,7 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
                                             uint64_t sweep, float beta, int2 ti, uint32_t dt, int lane,
                                             typename Acc<IS_INT>::T &accE, double &accEd, long long &accN)
 {
+    using T = typename Acc<IS_INT>::T;
     constexpr int sub = SOFF == -1 ? 0 : 1;
     constexpr int rows = NSH >= 3 ? 25 : 21;
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
@@ -687,56 +696,67 @@ __device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc 
                 }
             }
         }
-        if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
-        __syncwarp();
-        // periodic halos: 4 bytes before and after each row body
-        if (lane < rows) {
-            *(unsigned *)(g_smem + my_dst - 4) = *(const unsigned *)(g_smem + my_dst + nx - 4);
-            *(unsigned *)(g_smem + my_dst + nx) = *(const unsigned *)(g_smem + my_dst);
-        }
-        __syncwarp();
     }
+    // ---- Philox words of this lane's link cells, kept in shared memory
+    // (computed while the row copies are in flight) ----
+    uint32_t *wsm = (uint32_t *)(g_smem + col + (uint32_t)rows * rb + 16);  // [k][dx][lane]
+    const int nk = (NLx + 31) >> 5;
+    {
+        const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
+        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+#pragma unroll 1
+        for (int k = 0; k < nk; ++k) {
+            const int i = lane + 32 * k;
+            if (i < NLx) {
+                const U4 w =
+                    philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
+                wsm[(k * 4 + 0) * 32 + lane] = w.x;
+                wsm[(k * 4 + 1) * 32 + lane] = w.y;
+                wsm[(k * 4 + 2) * 32 + lane] = w.z;
+                wsm[(k * 4 + 3) * 32 + lane] = w.w;
+            }
+        }
+    }
+    if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncwarp();
+    // periodic halos: 4 bytes before and after each row body
+    if (lane < rows) {
+        *(unsigned *)(g_smem + my_dst - 4) = *(const unsigned *)(g_smem + my_dst + nx - 4);
+        *(unsigned *)(g_smem + my_dst + nx) = *(const unsigned *)(g_smem + my_dst);
+    }
+    __syncwarp();
     uint32_t po[9];
 #pragma unroll
     for (int r = 0; r < 9; ++r) po[r] = col + (uint32_t)r * rb + 16;
     const uint32_t col0 = col + 16;
-    // ---- Philox words of this lane's link cells, kept in shared memory ----
-    uint32_t *wsm = (uint32_t *)(g_smem + col + (uint32_t)rows * rb + 16);  // [k][dx][lane]
-    const int nk = (NLx + 31) >> 5;
-    const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
-    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-#pragma unroll 1
-    for (int k = 0; k < nk; ++k) {
-        const int i = lane + 32 * k;
-        if (i < NLx) {
-            const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
-            wsm[(k * 4 + 0) * 32 + lane] = w.x;
-            wsm[(k * 4 + 1) * 32 + lane] = w.y;
-            wsm[(k * 4 + 2) * 32 + lane] = w.z;
-            wsm[(k * 4 + 3) * 32 + lane] = w.w;
-        }
-    }
     // ---- the four mini-steps of the group ----
+    // accepted dE of this lane's trials in the column (at most nx / 8 of
+    // them), in the kernel's type; widened to FP64 once per column
+    T colE = T(0);
 #pragma unroll 1
     for (int dx = 0; dx < 4; ++dx) {
         if (NLx == 32 * nk && (nk & 3) == 0) {
 #pragma unroll 1
             for (int kk = 0; kk < nk; kk += 4)
                 fast_trials<IS_INT, NSH, S, SOFF, 4, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                            dt, accE, accEd, accN);
+                                                            dt, colE, accN);
         } else if (NLx == 32 * nk) {
 #pragma unroll 1
             for (int kk = 0; kk < nk; ++kk)
                 fast_trials<IS_INT, NSH, S, SOFF, 1, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                            dt, accE, accEd, accN);
+                                                            dt, colE, accN);
         } else {
 #pragma unroll 1
             for (int kk = 0; kk < nk; ++kk)
                 fast_trials<IS_INT, NSH, S, SOFF, 1, true>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                           dt, accE, accEd, accN);
+                                                           dt, colE, accN);
         }
         __syncwarp();
     }
+    if constexpr (IS_INT)
+        accE += colE;
+    else
+        accEd += (double)colE;
     // ---- write back trial row (0,0) and partner rows (s_off..s_off+1)^2 ----
     {
         const int cpr = vec ? (nx >> 4) : (nx >> 2);
@@ -782,15 +802,19 @@ __global__ void __launch_bounds__(256, 2) k_sweep_fast(const __grid_constant__ S
     unsigned char *smem = g_smem;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
+    // compact table: row (m, A, B) of RS words = D'[0..S-2], bias
+    constexpr int RS = fast_rs(S), NDE = (NSH >= 3 ? 3 : 2) * S * S * RS;
     T *Dt = (T *)smem;
-    for (int i = tid; i < kDEntries; i += blockDim.x) {
+    for (int i = tid; i < NDE; i += blockDim.x) {
+        const int q = i % RS, row = i / RS, mm = row / (S * S), A = (row / S) % S, B = row % S;
+        const int src = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + (q == S - 1 ? 7 : q);
         if constexpr (IS_INT)
-            Dt[i] = P.D.di[i];
+            Dt[i] = q < S ? P.D.di[src] : 0;
         else
-            Dt[i] = P.D.df[i];
+            Dt[i] = q < S ? P.D.df[src] : 0.f;
     }
     __syncthreads();
-    unsigned char *wbase = smem + kDEntries * 4 + (size_t)warp * P.warp_bytes;
+    unsigned char *wbase = smem + fast_d_bytes(NSH, S) + (size_t)warp * P.warp_bytes;
     double *slot_e = (double *)wbase;
     long long *slot_n = (long long *)(slot_e + P.tpc);
     const uint32_t col = (uint32_t)((unsigned char *)(slot_n + P.tpc) - smem);
@@ -965,7 +989,7 @@ namespace {
 
 struct Plan {
     int Lx, Ly, Lz, G;
-    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0, nap_cap = 128;
+    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0, nap_cap = 128, rowB = 0;
     size_t smem;
     const void *kernel = nullptr;
 };
@@ -1069,9 +1093,69 @@ const void *pick_fast(int S)
 // Plan of the warp-per-tile kernel: tiles of TY x TZ columns, one warp each
 // (a warp owns ceil(ntiles / warps) tiles), shared memory = D table + per warp
 // (accumulator slots + 25 rows).
+// Warp count of the warp-per-tile kernel.  Warp w owns tiles w, w + NW, ...
+// and CTA b lands on SM b mod num_sms (then b + num_sms, ...), so an SM's
+// time is the sum of its warps' tile counts.  Among all CTA counts that fit
+// at once, take the one with the smallest busiest-SM load (ties: more warps,
+// which hide latency better): e.g. 16384 tiles on 152 SMs x 2 CTAs x 8 warps
+// are best served by all 2432 warps (busiest SM 112 tiles), not by 2048
+// (128 tiles, 48 SMs half idle).
+static long long balanced_warps(long long ntiles, int nwarps, int per_sm, int num_sms)
+{
+    // SM 0 is always the busiest: it holds the most CTAs, and its k-th CTA
+    // (index k num_sms) has the lowest index, i.e. the most extra tiles,
+    // among the SMs' k-th CTAs.
+    const long long max_ctas = std::min<long long>((long long)per_sm * num_sms, (ntiles + nwarps - 1) / nwarps);
+    long long best = nwarps, best_load = -1;
+    for (long long ctas = 1; ctas <= max_ctas; ++ctas) {
+        const long long nw = ctas * nwarps, q = ntiles / nw, rmd = ntiles % nw;
+        long long worst = 0;
+        for (long long b = 0; b < ctas; b += num_sms)
+            worst += q * nwarps + std::max<long long>(0, std::min<long long>(rmd - b * nwarps, nwarps));
+        if (best_load < 0 || worst <= best_load) {
+            best_load = worst;
+            best = nw;
+        }
+    }
+    return best;
+}
+
+template <bool IS_INT>
+smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
+                                   int rowB, int same_nx, Plan &pl);
+
+// The plan depends only on the shapes, the model's shell and species
+// counts, the tuning and the device, so repeated calls (short chunks of a
+// long run, one call per sample) reuse it instead of searching again.
 template <bool IS_INT>
 smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
                           int rowB, int same_nx, Plan &pl)
+{
+    static std::vector<long long> key_cached;
+    static Plan plan_cached;
+    const Tuning tu = current_tuning();
+    std::vector<long long> key = {R, nshells, rowB, same_nx, lats[0].nspecies, ws->device, ws->num_sms,
+                                  (long long)ws->smem_optin, tu.tile_y, tu.tile_z, tu.threads, tu.ctas_per_sm};
+    for (int r = 0; r < R; ++r) {
+        key.push_back(lats[r].nx);
+        key.push_back(lats[r].ny);
+        key.push_back(lats[r].nz);
+    }
+    if (key == key_cached) {
+        pl = plan_cached;
+        return SMC_OK;
+    }
+    const smc_status st = make_fast_plan_uncached<IS_INT>(R, lats, occ, ws, nshells, rowB, same_nx, pl);
+    if (st == SMC_OK) {
+        key_cached = key;
+        plan_cached = pl;
+    }
+    return st;
+}
+
+template <bool IS_INT>
+smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
+                                   int rowB, int same_nx, Plan &pl)
 {
     const Tuning tu = current_tuning();
     pl.Lx = pl.Ly = pl.Lz = 4;
@@ -1079,7 +1163,9 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
     (void)same_nx;
     (void)occ;
     const int S = lats[0].nspecies;
-    pl.kernel = nshells >= 3 ? pick_fast<IS_INT, 3>(S) : pick_fast<IS_INT, 2>(S);
+    const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
+    const int nsh_t = nshells >= 3 ? 3 : 2;
+    pl.kernel = nsh_t == 3 ? pick_fast<IS_INT, 3>(S) : pick_fast<IS_INT, 2>(S);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
@@ -1091,7 +1177,6 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
         nkmax = std::max(nkmax, (lats[r].nx / 4 + 31) / 32);
         maxNLx = std::max(maxNLx, lats[r].nx / 4);
     }
-    const size_t rows_bytes = (size_t)(nshells >= 3 ? 25 : 21) * rowB + 16 + (size_t)512 * nkmax;
     // one column per tile unless tuned: the smallest unit of work keeps the
     // neighbour pipeline fullest
     pl.TY = tu.tile_y > 0 ? tu.tile_y : 1;
@@ -1099,49 +1184,50 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
     pl.ntiles = 0;
     for (int r = 0; r < R; ++r)
         pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
+    const size_t dbytes = (size_t)fast_d_bytes(nsh_t, ST);
     // Total warps NW: all resident at once (cooperative launch); preferably a
     // divisor of the tile count so that every warp owns as many tiles as the
     // others (an unevenly loaded warp makes its neighbours wait).
-    const int cand[2] = {128, 256};
-    int best_nw = 0;
-    for (int ci = 0; ci < 2; ++ci) {
-        const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // the kernel's launch bound is 256
-        if (tu.threads && ci > 0) break;
-        const int nwarps = threads / 32;
-        for (int tpc_guess = 1;; tpc_guess *= 2) {
-            const size_t smem =
-                (size_t)kDEntries * 4 + (size_t)nwarps * (((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
-            if (smem > dyn_max) break;
-            int per_sm = 0;
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, threads, smem);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-            if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
-            if (per_sm < 1) break;
-            const long long res = (long long)per_sm * ws->num_sms * nwarps;
-            long long nw = 0;
-            for (long long c = std::min<long long>(res, pl.ntiles) / nwarps * nwarps; c >= nwarps; c -= nwarps)
-                if (pl.ntiles % c == 0) {
-                    nw = c;
+    auto search = [&](int rb, Plan &out) -> long long {
+        const size_t rows_bytes = (size_t)(nsh_t >= 3 ? 25 : 21) * rb + 16 + (size_t)512 * nkmax;
+        const int cand[2] = {128, 256};
+        long long best_nw = 0;
+        for (int ci = 0; ci < 2; ++ci) {
+            const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // launch bound is 256
+            if (tu.threads && ci > 0) break;
+            const int nwarps = threads / 32;
+            for (int tpc_guess = 1;; tpc_guess *= 2) {
+                const size_t wb = ((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16;
+                const size_t smem = dbytes + (size_t)nwarps * wb;
+                if (smem > dyn_max) break;
+                int per_sm = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, threads, smem) != cudaSuccess)
+                    return -1;
+                if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+                if (per_sm < 1) break;
+                const long long res = (long long)per_sm * ws->num_sms * nwarps;
+                const long long nw = balanced_warps(pl.ntiles, nwarps, per_sm, ws->num_sms);
+                (void)res;
+                const int tpc = (int)((pl.ntiles + nw - 1) / nw);
+                if (tpc <= tpc_guess) {
+                    if (nw > best_nw) {
+                        best_nw = nw;
+                        out.threads = threads;
+                        out.grid = (int)(nw / nwarps);
+                        out.tpc = tpc_guess;
+                        out.smem = smem;
+                        out.warp_bytes = (int)wb;
+                        out.rowB = rb;
+                    }
                     break;
                 }
-            const long long fill = std::min<long long>(res, pl.ntiles) / nwarps * nwarps;
-            if (nw * 2 < fill) nw = fill;  // no good divisor: fill the GPU, accept the imbalance
-            if (nw < nwarps) nw = nwarps;
-            const int tpc = (int)((pl.ntiles + nw - 1) / nw);
-            if (tpc <= tpc_guess) {
-                if (nw > best_nw) {
-                    best_nw = (int)nw;
-                    pl.threads = threads;
-                    pl.grid = (int)(nw / nwarps);
-                    pl.tpc = tpc_guess;
-                    pl.smem = smem;
-                    pl.warp_bytes = (int)(((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16);
-                }
-                break;
             }
         }
-    }
-    if (best_nw == 0) {
+        return best_nw;
+    };
+    const long long nw = search(rowB, pl);
+    if (nw < 0) return cuda_fail(cudaGetLastError(), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (nw == 0) {
         set_error("fast sweep kernel does not fit on an SM (rows of %d bytes)", rowB);
         return SMC_ERR_UNSUPPORTED;
     }
@@ -1211,7 +1297,7 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     P.tpc = pl.tpc;
     P.warp_bytes = pl.warp_bytes;
     P.nap_cap = pl.nap_cap;
-    P.rowB = rowB_fast;
+    P.rowB = fast ? pl.rowB : rowB_fast;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast) {
         // Groups with dy >= 1 conflict with neighbouring columns only two
@@ -1535,7 +1621,7 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     P.tpc = pl.tpc;
     P.warp_bytes = pl.warp_bytes;
     P.nap_cap = pl.nap_cap;
-    P.rowB = rowB_fast;
+    P.rowB = fast ? pl.rowB : rowB_fast;
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast)
         for (int g = 0; g < pl.G; ++g) P.lag[g] = (g % pl.Ly) == 0 ? 1 : 2;
