@@ -20,7 +20,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "smc_oracle.c")
 
-PAIR_I32, PAIR_F32, MLP, PAIR_F32_MLP = 0, 1, 2, 3
+PAIR_I32, PAIR_F32, MLP, PAIR_F32_MLP, QSRO = 0, 1, 2, 3, 4
 MLP_IN, MLP_HID = 20, 64
 MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
 
@@ -50,7 +50,8 @@ class _Model(C.Structure):
                 ("w1", C.POINTER(C.c_double)), ("w2", C.POINTER(C.c_double)),
                 ("w3", C.POINTER(C.c_double)),
                 ("b1", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)),
-                ("b3", C.c_double)]
+                ("b3", C.c_double),
+                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_double)]
 
 
 _lib = None
@@ -131,9 +132,12 @@ class Model:
     """Energy model.  ``v`` is [nshells][S][S] (int32 units or float32 eV);
     ``mlp`` is a dict with w1/w2/w3 (uint16 BF16 bit patterns, or float64
     values for finite-difference checks) and b1/b2 (float32/float64), b3.
+    qSRO models take ``v`` = V_m^{pp'} (float32, symmetric), ``qsro_w`` =
+    W_m^p [nshells][S] (float32) and ``qsro_c`` = C (a float32 value).
     BF16 and FP32 values are widened to FP64 exactly."""
 
-    def __init__(self, kind: int, nshells: int = 0, v=None, unit_ev: float = 1e-4, mlp=None):
+    def __init__(self, kind: int, nshells: int = 0, v=None, unit_ev: float = 1e-4, mlp=None, qsro_w=None,
+                 qsro_c: float = 0.0):
         self.kind, self.nshells, self.unit_ev = int(kind), int(nshells), float(unit_ev)
         self._keep = []
         c = _Model()
@@ -141,9 +145,13 @@ class Model:
         if kind == PAIR_I32:
             self.v = np.ascontiguousarray(v, dtype=np.int32)
             c.v_i32 = _ptr(self.v, C.c_int32)
-        elif kind in (PAIR_F32, PAIR_F32_MLP):
+        elif kind in (PAIR_F32, PAIR_F32_MLP, QSRO):
             self.v = np.ascontiguousarray(v, dtype=np.float32)
             c.v_f32 = _ptr(self.v, C.c_float)
+        if kind == QSRO:
+            self.qsro_w = np.ascontiguousarray(qsro_w, dtype=np.float32)
+            c.qsro_w = _ptr(self.qsro_w, C.c_float)
+            c.qsro_c = float(np.float32(qsro_c))
         if kind in (MLP, PAIR_F32_MLP):
             self.mlp = {k: _widen(mlp[k]) for k in ("w1", "w2", "w3", "b1", "b2")}
             assert self.mlp["w1"].size == MLP_HID * MLP_IN

@@ -260,6 +260,44 @@ static int has_mlp(const orc_model *m)
     return m->kind == ORC_MLP || m->kind == ORC_PAIR_F32_MLP;
 }
 
+/* Local energy of the qSRO model (Sec. IV-B, Eq. quadratic_local_SRO):
+ *   E_i = sum_{m, p' <= p} V_m^{pp'} pi_m^{pp'} + sum_{m, p} W_m^p (pi_m^{pp})^2 + C,
+ *   pi_m^{pp'} = n_m^{pp'} / sum_{pp'} n_m^{pp'},
+ * with n_m^{pp'} the number of pairs (i, j), j in shell m of i, whose two
+ * species are {p, p'} (counted once per unordered pair, p' <= p).  The
+ * linear sum runs over p' <= p, same-element pairs included; the constant
+ * lambda sum W^2 (a training regulariser) is left out. */
+static double qsro_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i)
+{
+    int S = lat->nspecies;
+    double e = m->qsro_c;
+    for (int sh = 1; sh <= m->nshells; ++sh) {
+        double n[ORC_MAX_SPECIES][ORC_MAX_SPECIES];
+        memset(n, 0, sizeof n);
+        double total = 0.0;
+        for (int t = 0; t < g_shell_n[sh]; ++t) {
+            const int *v = g_shell_v[sh][t];
+            int64_t j = orc_neighbor(lat, i, v[0], v[1], v[2]);
+            int p = occ[i], q = occ[j];
+            if (q > p) {
+                int tmp = p;
+                p = q;
+                q = tmp;
+            }
+            n[p][q] += 1.0;
+            total += 1.0;
+        }
+        for (int p = 0; p < S; ++p)
+            for (int q = 0; q <= p; ++q)
+                e += (double)m->v_f32[((sh - 1) * S + p) * S + q] * (n[p][q] / total);
+        for (int p = 0; p < S; ++p) {
+            double pi = n[p][p] / total;
+            e += (double)m->qsro_w[(sh - 1) * S + p] * pi * pi;
+        }
+    }
+    return e;
+}
+
 /* Twice the pair site energy of an integer model (an integer). */
 static int64_t site_energy2_i64(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i)
 {
@@ -280,6 +318,7 @@ double orc_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t 
     int S = lat->nspecies;
     double e = 0.0;
     if (m->kind == ORC_PAIR_I32) return 0.5 * (double)site_energy2_i64(lat, m, occ, i);
+    if (m->kind == ORC_QSRO) return qsro_site_energy(lat, m, occ, i);
     if (has_pair(m)) {
         double sum = 0.0;
         for (int sh = 1; sh <= m->nshells; ++sh)
@@ -320,7 +359,7 @@ int64_t orc_total_energy_i64(const orc_lattice *lat, const orc_model *m, const i
  * shells away. */
 static int model_reach(const orc_model *m)
 {
-    int r = has_pair(m) ? m->nshells : 0;
+    int r = (has_pair(m) || m->kind == ORC_QSRO) ? m->nshells : 0;
     if (has_mlp(m) && r < 3) r = 3;
     return r;
 }
@@ -612,8 +651,9 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
 
 static int model_ok(const orc_lattice *lat, const orc_model *m)
 {
-    if (m->kind < ORC_PAIR_I32 || m->kind > ORC_PAIR_F32_MLP) return 0;
-    if (has_pair(m) && (m->nshells < 1 || m->nshells > 3)) return 0;
+    if (m->kind < ORC_PAIR_I32 || m->kind > ORC_QSRO) return 0;
+    if ((has_pair(m) || m->kind == ORC_QSRO) && (m->nshells < 1 || m->nshells > 3)) return 0;
+    if (m->kind == ORC_QSRO && (!m->v_f32 || !m->qsro_w)) return 0;
     if (m->kind == ORC_PAIR_I32 && (!m->v_i32 || !(m->unit_ev > 0.0))) return 0;
     if ((m->kind == ORC_PAIR_F32 || m->kind == ORC_PAIR_F32_MLP) && !m->v_f32) return 0;
     if (has_mlp(m) && (!m->w1 || !m->w2 || !m->w3 || !m->b1 || !m->b2)) return 0;
@@ -693,12 +733,12 @@ int64_t orc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *o
  * integers (sublattice 0) or half-integers (sublattice 1) in units of the
  * cell edge.  The partner b sits 1/2 away; every shell-1..3 vector moves x
  * by 1 at most.  Pair models read the shells of a and b: 1.5 from a, which
- * is 2 cells.  MLP models change the energies of Omega (a, b and their
- * shell-1..3 neighbours, 1.5 from a), and each of those reads its own
+ * is 2 cells.  MLP and qSRO models change the energies of Omega (a, b and
+ * their shell neighbours, 1.5 from a), and each of those reads its own
  * shells: 2.5 from a, which is 3 cells. */
 int orc_slab_ghost_cells(const orc_model *m)
 {
-    return has_mlp(m) ? 3 : 2;
+    return (has_mlp(m) || m->kind == ORC_QSRO) ? 3 : 2;
 }
 
 int64_t orc_slab_ministep(const orc_lattice *glat, const orc_model *m, int8_t *occ_loc,
@@ -812,7 +852,7 @@ static void mlp_backprop(const orc_model *m, const double x[ORC_MLP_IN], double 
 int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *occ, double *grad)
 {
     geom_init();
-    if (!lattice_ok(lat) || !model_ok(lat, m)) return -1;
+    if (!lattice_ok(lat) || !model_ok(lat, m) || m->kind == ORC_QSRO) return -1;
     int S = lat->nspecies;
     int64_t n = orc_grad_size(lat, m), N = orc_nsites(lat);
     for (int64_t t = 0; t < n; ++t) grad[t] = 0.0;

@@ -44,7 +44,7 @@ extern "C" {
 #define ORC_MLP_HID 64
 #define ORC_MLP_SPECIES 5
 
-enum { ORC_PAIR_I32 = 0, ORC_PAIR_F32 = 1, ORC_MLP = 2, ORC_PAIR_F32_MLP = 3 };
+enum { ORC_PAIR_I32 = 0, ORC_PAIR_F32 = 1, ORC_MLP = 2, ORC_PAIR_F32_MLP = 3, ORC_QSRO = 4 };
 
 typedef struct {
     int32_t nx, ny, nz;   /* cells per axis, each >= 2 */
@@ -55,14 +55,16 @@ typedef struct {
  * biases exactly).  Layouts: w1[64][20], w2[64][64], w3[64] (row = output
  * unit). */
 typedef struct {
-    int32_t kind;            /* ORC_PAIR_I32 .. ORC_PAIR_F32_MLP */
+    int32_t kind;            /* ORC_PAIR_I32 .. ORC_QSRO */
     int32_t nshells;         /* pair shells used, 1..3 */
     const int32_t *v_i32;    /* [nshells][S][S], integer units */
-    const float *v_f32;      /* [nshells][S][S], eV */
+    const float *v_f32;      /* [nshells][S][S], eV (qSRO: V_m^{pp'}) */
     double unit_ev;          /* eV per integer unit (integer model) */
     const double *w1, *w2, *w3;
     const double *b1, *b2;
     double b3;
+    const float *qsro_w;     /* qSRO: W_m^p, [nshells][S], eV */
+    double qsro_c;           /* qSRO: C, eV per site */
 } orc_model;
 
 /* Philox4x32-10 block function: out = Philox(ctr, key). */

@@ -61,6 +61,19 @@ def pair_f32_coeffs(seed: int, nshells: int = 2, nspecies: int = 5, sigma_ev: fl
     return _symmetric(rng.normal(0.0, sigma_ev, size=n), nshells, nspecies, np.float64).astype(np.float32)
 
 
+def qsro_coeffs(seed: int, nshells: int = 2, nspecies: int = 5, sigma_v_ev: float = 0.100,
+                sigma_w_ev: float = 0.050, c_ev: float = -4.0):
+    """qSRO parameters (V_m^{pp'} symmetric [nshells][S][S], W_m^p
+    [nshells][S], C), FP32: V ~ N(0, sigma_v), W ~ N(0, sigma_w) eV.  Site
+    energies weigh pair fractions (sums of 1), so these are the pair model's
+    coefficients times a coordination number in size."""
+    rng = np.random.default_rng(seed)
+    n = nshells * nspecies * (nspecies + 1) // 2
+    V = _symmetric(rng.normal(0.0, sigma_v_ev, size=n), nshells, nspecies, np.float64).astype(np.float32)
+    W = rng.normal(0.0, sigma_w_ev, size=(nshells, nspecies)).astype(np.float32)
+    return V, W, float(np.float32(c_ev))
+
+
 def ordering_coeffs_b2() -> np.ndarray:
     """Binary ordering interactions whose ground state is B2 (CsCl):
     unlike first neighbours attract, like second neighbours attract."""
