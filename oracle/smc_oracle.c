@@ -805,7 +805,43 @@ int64_t orc_grad_size(const orc_lattice *lat, const orc_model *m)
     int64_t n = 0;
     if (has_pair(m)) n += (int64_t)m->nshells * S * (S + 1) / 2;
     if (has_mlp(m)) n += MLP_NPARAM;
+    if (m->kind == ORC_QSRO) n += (int64_t)m->nshells * S * (S + 1) / 2 + (int64_t)m->nshells * S + 1;
     return n;
+}
+
+/* dE/dtheta of the qSRO energy (Eq. quadratic_local_SRO), term by term:
+ * dE/dV_m^{pp'} = sum_i pi_m^{pp'}(i) (one parameter per unordered pair),
+ * dE/dW_m^p = sum_i pi_m^{pp}(i)^2, dE/dC = N. */
+static void qsro_grad(const orc_lattice *lat, const orc_model *m, const int8_t *occ, double *grad)
+{
+    int S = lat->nspecies, per = S * (S + 1) / 2;
+    int64_t N = orc_nsites(lat);
+    double *gV = grad, *gW = grad + (int64_t)m->nshells * per, *gC = gW + (int64_t)m->nshells * S;
+    for (int64_t i = 0; i < N; ++i)
+        for (int sh = 1; sh <= m->nshells; ++sh) {
+            double n[ORC_MAX_SPECIES][ORC_MAX_SPECIES];
+            memset(n, 0, sizeof n);
+            double total = 0.0;
+            for (int t = 0; t < g_shell_n[sh]; ++t) {
+                const int *v = g_shell_v[sh][t];
+                int64_t j = orc_neighbor(lat, i, v[0], v[1], v[2]);
+                int p = occ[i], q = occ[j];
+                if (q > p) {
+                    int tmp = p;
+                    p = q;
+                    q = tmp;
+                }
+                n[p][q] += 1.0;
+                total += 1.0;
+            }
+            for (int p = 0; p < S; ++p)
+                for (int q = 0; q <= p; ++q) gV[(sh - 1) * per + pair_param_index(S, p, q)] += n[p][q] / total;
+            for (int p = 0; p < S; ++p) {
+                double pi = n[p][p] / total;
+                gW[(sh - 1) * S + p] += pi * pi;
+            }
+        }
+    *gC = (double)N;
 }
 
 static double dsilu(double z)
@@ -852,10 +888,14 @@ static void mlp_backprop(const orc_model *m, const double x[ORC_MLP_IN], double 
 int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *occ, double *grad)
 {
     geom_init();
-    if (!lattice_ok(lat) || !model_ok(lat, m) || m->kind == ORC_QSRO) return -1;
+    if (!lattice_ok(lat) || !model_ok(lat, m)) return -1;
     int S = lat->nspecies;
     int64_t n = orc_grad_size(lat, m), N = orc_nsites(lat);
     for (int64_t t = 0; t < n; ++t) grad[t] = 0.0;
+    if (m->kind == ORC_QSRO) {
+        qsro_grad(lat, m, occ, grad);
+        return 0;
+    }
     double *gm = grad;
     if (has_pair(m)) {
         int per = S * (S + 1) / 2;

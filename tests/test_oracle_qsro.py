@@ -158,3 +158,40 @@ def test_chain_matches_enumeration_16_site():
     bm = Es[nsw - keep:].reshape(nb, -1).mean(1)
     se = bm.std(ddof=1) / math.sqrt(nb)
     assert abs(bm.mean() - exact) < 3 * se, (bm.mean(), exact, se)
+
+
+def test_gradient_equals_finite_differences():
+    """E is linear in every qSRO parameter, so central differences over the
+    FP32-representable perturbation are exact up to rounding.  Layout:
+    [V_m^{pq}, p <= q][W_m^p][C]."""
+    S, nsh = 3, 3
+    V, W, C = inputs.qsro_coeffs(5, nsh, S)
+    lat = oracle.Lattice(4, 4, 5, S)
+    occ = oracle.init_lattice(lat, inputs.dirichlet_counts(lat.nsites, S, 1), 1)
+    g = oracle.energy_grad(lat, oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C), occ)
+    per = S * (S + 1) // 2
+    assert g.size == nsh * per + nsh * S + 1
+
+    def energy(V_, W_, C_):
+        return oracle.total_energy(lat, oracle.Model(oracle.QSRO, nsh, V_, qsro_w=W_, qsro_c=C_), occ)
+
+    h = np.float32(2.0 ** -6)
+    i = 0
+    for m in range(nsh):
+        for p in range(S):
+            for q in range(p, S):
+                Vp, Vm = V.copy(), V.copy()
+                Vp[m, p, q] = Vp[m, q, p] = V[m, p, q] + h
+                Vm[m, p, q] = Vm[m, q, p] = V[m, p, q] - h
+                fd = (energy(Vp, W, C) - energy(Vm, W, C)) / (float(Vp[m, p, q]) - float(Vm[m, p, q]))
+                assert g[i] == pytest.approx(fd, rel=1e-9, abs=1e-9), (m, p, q)
+                i += 1
+    for m in range(nsh):
+        for p in range(S):
+            Wp, Wm = W.copy(), W.copy()
+            Wp[m, p] += h
+            Wm[m, p] -= h
+            fd = (energy(V, Wp, C) - energy(V, Wm, C)) / (float(Wp[m, p]) - float(Wm[m, p]))
+            assert g[i] == pytest.approx(fd, rel=1e-9, abs=1e-9), (m, p)
+            i += 1
+    assert g[i] == lat.nsites
