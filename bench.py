@@ -33,6 +33,7 @@ from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
 # MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
+QSRO_SEED, QSRO_SHELLS, QSRO_ZONE = 7, 2, 40  # qSRO workload parameters; 40-site interaction zone
 INSTR_PER_TRIAL_512 = 352.9  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
@@ -172,12 +173,17 @@ def main():
                     help="measure tanh.approx / ex2.approx throughput (the MLP path's SFU ceiling)")
     ap.add_argument("--profile-mlp", type=int, default=0,
                     help="run the MLP workload (800 K) on a 256 x n x n box once, for ncu captures")
+    ap.add_argument("--profile-qsro", type=int, default=0,
+                    help="run the qSRO workload (800 K) on an N^3 box once, for ncu captures")
     args = ap.parse_args()
     if args.probe_sfu:
         probe_sfu()
         return
     if args.profile_mlp:
         profile_mlp(args.profile_mlp, args.profile_sweeps)
+        return
+    if args.profile_qsro:
+        profile_qsro(args.profile_qsro, args.profile_sweeps)
         return
     if args.profile_sweep:
         profile_sweep(args.profile_sweep, args.profile_sweeps)
@@ -344,6 +350,36 @@ def probe_sfu():
     subprocess.run([exe], check=True)
 
 
+def qsro_setup(smc, n: int, dev):
+    """qSRO workload: N^3 cells, the MLP workload's Dirichlet quinary
+    composition, 2-shell qSRO parameters (seed 7), 800 K."""
+    c4 = inputs.CONFIG4
+    S = c4["nspecies"]
+    V, W, C = inputs.qsro_coeffs(QSRO_SEED, QSRO_SHELLS, S)
+    model = smc.Model(smc.QSRO_F32, QSRO_SHELLS, V, qsro_w=W, qsro_c=C)
+    import torch
+    lat = smc.Lattice(n, n, n, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device=dev)
+    smc.init_lattice(lat, inputs.dirichlet_counts(lat.nsites, S, c4["comp_seed"]), c4["mc_seed"], occ)
+    return lat, occ, model, inputs.K_B_EV * c4["T"]
+
+
+def profile_qsro(n: int, nsweeps: int):
+    """One qSRO sweep launch (the feature-cache kernel runs first) on an N^3
+    box, for ncu captures (-k regex:k_sweep_mlp)."""
+    import torch
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    smc.debug_set(smc.DBG_TIMEOUT_MS, 60000)  # replayed launches run slower under the profiler
+    lat, occ, model, kT = qsro_setup(smc, n, "cuda")
+    smc.sweep(lat, model, occ, inputs.CONFIG4["mc_seed"], 0, nsweeps, kT)
+    smc.check()
+    del occ
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_qsro": n, "sweeps": nsweeps, "ok": True}))
+
+
 def profile_mlp(n: int, nsweeps: int):
     """One MLP sweep launch (nsweeps sweeps; the energy-cache kernel runs
     first) and one energy evaluation on a 256 x n x n box with the MLP
@@ -473,6 +509,24 @@ def run_extras(smc, torch, dev, pk):
     ems = timed(lambda: smc.energy(lat4, mlp_model, occ4, e4), reps=3)
     out["mlp_energy_256"] = {"ms": ems, "achieved_tflops": lat4.nsites * MLP_FLOP_PER_SITE_FWD / (ems * 1e-3) / 1e12}
     del occ4
+    # qSRO site energies (Eq. quadratic_local_SRO) on the cached-feature sweep, 256^3 at 800 K
+    latq, occq, qm, kTq = qsro_setup(smc, 256, dev)
+    nq = torch.zeros(1, dtype=torch.int64, device=dev)
+    nswq = 4
+    msq = timed(lambda: smc.sweep(latq, qm, occq, 1, 0, nswq, kTq, n_acc=nq), reps=1)
+    attq = latq.nsites * nswq / (msq * 1e-3)
+    accq = float(nq.item()) / (2 * latq.nsites * nswq)
+    # bytes the design moves per attempt: 40 zone feature rows read (16 B), and
+    # rewritten when accepted, plus the two species read and written
+    bq = QSRO_ZONE * 16 * (1 + accq) + 2 + 2 * accq
+    out["qsro_256"] = {"cells": [256] * 3, "shells": QSRO_SHELLS, "sweeps_per_launch": nswq,
+                       "ms_per_sweep": msq / nswq, "attempts_per_s": attq, "accept_rate": accq,
+                       "cache_bytes_per_attempt": bq, "achieved_gbs": attq * bq / 1e9,
+                       "frac_of_measured_hbm": attq * bq / 1e9 / pk["hbm_gbs"]}
+    eq = torch.zeros(1, dtype=torch.float64, device=dev)
+    emsq = timed(lambda: smc.energy(latq, qm, occq, eq), reps=3)
+    out["qsro_energy_256"] = {"ms": emsq}
+    del occq
     # dE/dtheta of the pair + MLP energy at 512^3 (one configuration)
     c5 = inputs.CONFIG5
     n5 = c5["cells"][0]

@@ -88,22 +88,31 @@ enum {
     SMC_PAIR_I32 = 0,          /* integer pair coefficients (exact path) */
     SMC_PAIR_F32 = 1,          /* FP32 pair coefficients, eV */
     SMC_MLP_BF16 = 2,          /* BF16 MLP site energies */
-    SMC_PAIR_F32_MLP_BF16 = 3  /* sum of the two */
+    SMC_PAIR_F32_MLP_BF16 = 3, /* sum of the two */
+    SMC_QSRO_F32 = 4           /* qSRO site energies (Sec. IV-B), FP32 parameters */
 };
 
 /* Energy model (all pointers host memory, read during the call).
  * Pair coefficients V_m(p, q) (Sec. IV-B, effective pair interactions) are
  * [nshells][S][S], symmetric in p, q.  MLP weights are BF16 bit patterns in
- * row-major [out][in] order: w1 [64][20], w2 [64][64], w3 [64]. */
+ * row-major [out][in] order: w1 [64][20], w2 [64][64], w3 [64].
+ * qSRO (Sec. IV-B, Eq. quadratic_local_SRO): the local energy of site i is
+ *   E_i = sum_{m, p'<=p} V_m^{pp'} pi_m^{pp'} + sum_{m,p} W_m^p (pi_m^{pp})^2 + C
+ * with pi_m^{pp'} the fraction of the pairs (i, j), j in shell m of i, whose
+ * species are {p, p'}; V_m^{pp'} in v_f32 ([nshells][S][S], symmetric),
+ * W_m^p in qsro_w ([nshells][S]), C in qsro_c.  The constant lambda sum W^2
+ * of the paper's equation is a training regulariser and is not part of E. */
 typedef struct {
-    int32_t kind;            /* SMC_PAIR_I32 .. SMC_PAIR_F32_MLP_BF16 */
-    int32_t nshells;         /* pair shells 1..3 (ignored for SMC_MLP_BF16) */
+    int32_t kind;            /* SMC_PAIR_I32 .. SMC_QSRO_F32 */
+    int32_t nshells;         /* pair / qSRO shells 1..3 (ignored for SMC_MLP_BF16) */
     const int32_t *v_i32;    /* SMC_PAIR_I32: units of unit_ev, |V| <= 2^24 */
-    const float *v_f32;      /* SMC_PAIR_F32*: eV */
+    const float *v_f32;      /* SMC_PAIR_F32*, SMC_QSRO_F32: eV */
     double unit_ev;          /* SMC_PAIR_I32: eV per integer unit (> 0) */
     const uint16_t *mlp_w1, *mlp_w2, *mlp_w3;
     const float *mlp_b1, *mlp_b2;
     float mlp_b3;
+    const float *qsro_w;     /* SMC_QSRO_F32: W_m^p, [nshells][S], eV */
+    float qsro_c;            /* SMC_QSRO_F32: C, eV per site */
 } smc_model;
 
 /* Composition-conserving random initial configuration (the starting state

@@ -141,7 +141,11 @@ bool lattice_valid(const smc_lattice *lat, bool mlp)
 }
 
 static bool is_mlp(const smc_model *m) { return m->kind == SMC_MLP_BF16 || m->kind == SMC_PAIR_F32_MLP_BF16; }
-static bool has_pair(const smc_model *m) { return m->kind != SMC_MLP_BF16; }
+static bool is_qsro(const smc_model *m) { return m->kind == SMC_QSRO_F32; }
+static bool has_pair(const smc_model *m)
+{
+    return m->kind == SMC_PAIR_I32 || m->kind == SMC_PAIR_F32 || m->kind == SMC_PAIR_F32_MLP_BF16;
+}
 
 bool model_valid(const smc_lattice *lat, const smc_model *m)
 {
@@ -149,7 +153,7 @@ bool model_valid(const smc_lattice *lat, const smc_model *m)
         set_error("model is NULL");
         return false;
     }
-    if (m->kind < SMC_PAIR_I32 || m->kind > SMC_PAIR_F32_MLP_BF16) {
+    if (m->kind < SMC_PAIR_I32 || m->kind > SMC_QSRO_F32) {
         set_error("unknown model kind %d", m->kind);
         return false;
     }
@@ -183,6 +187,34 @@ bool model_valid(const smc_lattice *lat, const smc_model *m)
                         return false;
                     }
                 }
+    }
+    if (is_qsro(m)) {
+        if (m->nshells < 1 || m->nshells > kMaxShells) {
+            set_error("nshells must be in [1, 3] (got %d)", m->nshells);
+            return false;
+        }
+        if (!m->v_f32 || !m->qsro_w) {
+            set_error("qSRO model needs v_f32 and qsro_w");
+            return false;
+        }
+        for (int mm = 0; mm < m->nshells; ++mm)
+            for (int p = 0; p < S; ++p) {
+                if (!std::isfinite(m->qsro_w[mm * S + p])) {
+                    set_error("qSRO W must be finite (shell %d, species %d)", mm + 1, p);
+                    return false;
+                }
+                for (int q = 0; q < S; ++q) {
+                    const float a = m->v_f32[(mm * S + p) * S + q], b = m->v_f32[(mm * S + q) * S + p];
+                    if (!std::isfinite(a) || a != b) {
+                        set_error("qSRO V must be finite and symmetric (shell %d, %d-%d)", mm + 1, p, q);
+                        return false;
+                    }
+                }
+            }
+        if (!std::isfinite(m->qsro_c)) {
+            set_error("qSRO C must be finite");
+            return false;
+        }
     }
     if (is_mlp(m)) {
         if (!m->mlp_w1 || !m->mlp_w2 || !m->mlp_w3 || !m->mlp_b1 || !m->mlp_b2) {
@@ -339,6 +371,8 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
     if (nsweeps == 0) return SMC_OK;
     if (is_mlp(model))
         return launch_mlp_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+    if (is_qsro(model))
+        return launch_qsro_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     int8_t *occs[1] = {occ};
     return launch_pair_sweep(1, lat, model, occs, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
@@ -394,11 +428,13 @@ smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model
         return SMC_ERR_ARG;
     }
     if (nsweeps == 0) return SMC_OK;
-    if (is_mlp(model)) {
+    if (is_mlp(model) || is_qsro(model)) {
         if (R != 1) {
-            set_error("batched MLP sweeps take one replica per call");
+            set_error("batched MLP and qSRO sweeps take one replica per call");
             return SMC_ERR_UNSUPPORTED;
         }
+        if (is_qsro(model))
+            return launch_qsro_sweep(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
         return launch_mlp_sweep(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     }
     return launch_pair_sweep(R, lats, model, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
@@ -417,6 +453,7 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
         return SMC_ERR_ARG;
     }
     if (is_mlp(model)) return launch_mlp_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
+    if (is_qsro(model)) return launch_qsro_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
@@ -455,11 +492,12 @@ smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8
         set_error("e_int is only defined for integer models");
         return SMC_ERR_ARG;
     }
-    if (is_mlp(model)) {
+    if (is_mlp(model) || is_qsro(model)) {
         if (!e) {
             set_error("e is NULL");
             return SMC_ERR_ARG;
         }
+        if (is_qsro(model)) return launch_qsro_energy(lat, model, occ, e, stream);
         return launch_mlp_energy(lat, model, occ, e, stream);
     }
     smc_status st;
@@ -480,6 +518,7 @@ int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model)
     int64_t n = 0;
     if (has_pair(model)) n += (int64_t)model->nshells * S * (S + 1) / 2;
     if (is_mlp(model)) n += 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1;
+    if (is_qsro(model)) n += (int64_t)model->nshells * S * (S + 1) / 2 + (int64_t)model->nshells * S + 1;
     return n;
 }
 
@@ -493,6 +532,7 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
         return SMC_ERR_ARG;
     }
     if (is_mlp(model)) return launch_mlp_grad(lat, model, occ, grad, stream);
+    if (is_qsro(model)) return launch_qsro_grad(lat, model, occ, grad, stream);
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;

@@ -985,6 +985,33 @@ __global__ void k_ministep_apply(int8_t *occ, int ntr, const int *swap_a, const 
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
+// Warp count of the warp-per-tile kernel.  Warp w owns tiles w, w + NW, ...
+// and CTA b lands on SM b mod num_sms (then b + num_sms, ...), so an SM's
+// time is the sum of its warps' tile counts.  Among all CTA counts that fit
+// at once, take the one with the smallest busiest-SM load (ties: more warps,
+// which hide latency better): e.g. 16384 tiles on 152 SMs x 2 CTAs x 8 warps
+// are best served by all 2432 warps (busiest SM 112 tiles), not by 2048
+// (128 tiles, 48 SMs half idle).
+long long balanced_warps(long long ntiles, int nwarps, int per_sm, int num_sms)
+{
+    // SM 0 is always the busiest: it holds the most CTAs, and its k-th CTA
+    // (index k num_sms) has the lowest index, i.e. the most extra tiles,
+    // among the SMs' k-th CTAs.
+    const long long max_ctas = std::min<long long>((long long)per_sm * num_sms, (ntiles + nwarps - 1) / nwarps);
+    long long best = nwarps, best_load = -1;
+    for (long long ctas = 1; ctas <= max_ctas; ++ctas) {
+        const long long nw = ctas * nwarps, q = ntiles / nw, rmd = ntiles % nw;
+        long long worst = 0;
+        for (long long b = 0; b < ctas; b += num_sms)
+            worst += q * nwarps + std::max<long long>(0, std::min<long long>(rmd - b * nwarps, nwarps));
+        if (best_load < 0 || worst <= best_load) {
+            best_load = worst;
+            best = nw;
+        }
+    }
+    return best;
+}
+
 namespace {
 
 struct Plan {
@@ -1093,33 +1120,6 @@ const void *pick_fast(int S)
 // Plan of the warp-per-tile kernel: tiles of TY x TZ columns, one warp each
 // (a warp owns ceil(ntiles / warps) tiles), shared memory = D table + per warp
 // (accumulator slots + 25 rows).
-// Warp count of the warp-per-tile kernel.  Warp w owns tiles w, w + NW, ...
-// and CTA b lands on SM b mod num_sms (then b + num_sms, ...), so an SM's
-// time is the sum of its warps' tile counts.  Among all CTA counts that fit
-// at once, take the one with the smallest busiest-SM load (ties: more warps,
-// which hide latency better): e.g. 16384 tiles on 152 SMs x 2 CTAs x 8 warps
-// are best served by all 2432 warps (busiest SM 112 tiles), not by 2048
-// (128 tiles, 48 SMs half idle).
-static long long balanced_warps(long long ntiles, int nwarps, int per_sm, int num_sms)
-{
-    // SM 0 is always the busiest: it holds the most CTAs, and its k-th CTA
-    // (index k num_sms) has the lowest index, i.e. the most extra tiles,
-    // among the SMs' k-th CTAs.
-    const long long max_ctas = std::min<long long>((long long)per_sm * num_sms, (ntiles + nwarps - 1) / nwarps);
-    long long best = nwarps, best_load = -1;
-    for (long long ctas = 1; ctas <= max_ctas; ++ctas) {
-        const long long nw = ctas * nwarps, q = ntiles / nw, rmd = ntiles % nw;
-        long long worst = 0;
-        for (long long b = 0; b < ctas; b += num_sms)
-            worst += q * nwarps + std::max<long long>(0, std::min<long long>(rmd - b * nwarps, nwarps));
-        if (best_load < 0 || worst <= best_load) {
-            best_load = worst;
-            best = nw;
-        }
-    }
-    return best;
-}
-
 template <bool IS_INT>
 smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
                                    int rowB, int same_nx, Plan &pl);

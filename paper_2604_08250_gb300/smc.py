@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsmc.so")
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_UNSUPPORTED, SMC_ERR_CUDA, SMC_ERR_TIMEOUT, SMC_ERR_STATE = 0, -1, -2, -3, -4, -5
-PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16 = 0, 1, 2, 3
+PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16, QSRO_F32 = 0, 1, 2, 3, 4
 DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH = 1, 2
 MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -43,7 +43,8 @@ class _Model(C.Structure):
                 ("mlp_w1", C.POINTER(C.c_uint16)), ("mlp_w2", C.POINTER(C.c_uint16)),
                 ("mlp_w3", C.POINTER(C.c_uint16)),
                 ("mlp_b1", C.POINTER(C.c_float)), ("mlp_b2", C.POINTER(C.c_float)),
-                ("mlp_b3", C.c_float)]
+                ("mlp_b3", C.c_float),
+                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_float)]
 
 
 class _Tuning(C.Structure):
@@ -128,18 +129,24 @@ class Lattice:
 class Model:
     """Energy model: pair coefficients v [nshells][S][S] (int32 units of unit_ev,
     or float32 eV) and/or an MLP given as a dict of BF16 bit patterns
-    (w1 [64,20], w2 [64,64], w3 [64], uint16) and FP32 biases (b1, b2, b3)."""
+    (w1 [64,20], w2 [64,64], w3 [64], uint16) and FP32 biases (b1, b2, b3).
+    qSRO: v = V_m^{pp'} (float32, symmetric), qsro_w = W_m^p [nshells][S]
+    (float32), qsro_c = C."""
 
-    def __init__(self, kind, nshells=0, v=None, unit_ev=1e-4, mlp=None):
+    def __init__(self, kind, nshells=0, v=None, unit_ev=1e-4, mlp=None, qsro_w=None, qsro_c=0.0):
         self.kind, self.nshells, self.unit_ev = int(kind), int(nshells), float(unit_ev)
         c = _Model()
         c.kind, c.nshells, c.unit_ev = self.kind, self.nshells, self.unit_ev
         if kind == PAIR_I32:
             self.v = np.ascontiguousarray(v, dtype=np.int32)
             c.v_i32 = self.v.ctypes.data_as(C.POINTER(C.c_int32))
-        elif kind in (PAIR_F32, PAIR_F32_MLP_BF16):
+        elif kind in (PAIR_F32, PAIR_F32_MLP_BF16, QSRO_F32):
             self.v = np.ascontiguousarray(v, dtype=np.float32)
             c.v_f32 = self.v.ctypes.data_as(C.POINTER(C.c_float))
+        if kind == QSRO_F32:
+            self.qsro_w = np.ascontiguousarray(qsro_w, dtype=np.float32)
+            c.qsro_w = self.qsro_w.ctypes.data_as(C.POINTER(C.c_float))
+            c.qsro_c = float(qsro_c)
         if kind in (MLP_BF16, PAIR_F32_MLP_BF16):
             self.mlp = {k: np.ascontiguousarray(mlp[k], dtype=np.uint16).reshape(-1) for k in ("w1", "w2", "w3")}
             for k in ("b1", "b2"):

@@ -1,0 +1,197 @@
+"""GPU parity of the qSRO path (Sec. IV-B, Eq. quadratic_local_SRO) against
+the FP64 oracle, through the C ABI.
+
+The sweep evaluates a trial's dE as the sum over its 40-site interaction
+zone of f(x') - f(x) in FP32: for a and b from their full site energies
+(without the constant C), for the other zone sites from the one or two
+count changes the swap makes.  Every trial's dE must lie within DE_TOL_EV of
+the FP64 oracle and decide the same, except where the acceptance threshold
+lies between the two values (the oracle then follows the GPU).  The sweep
+kernel (features from its cache) must equal its traced mini-steps (features
+counted from the occupancy) bit for bit.  Energies and dE/dtheta come from
+exact integer counts in FP64."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_08250_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DE_TOL_EV = 1e-5  # FP32 dE vs FP64 (the bound the floating-point paths meet)
+
+
+@pytest.fixture(scope="module")
+def smc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_08250_gb300 import build, smc as s
+    build.build()
+    s.lib()
+    return s
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def models(smc, nsh, S, seed=7):
+    V, W, C = inputs.qsro_coeffs(seed, nsh, S)
+    return (smc.Model(smc.QSRO_F32, nsh, V, qsro_w=W, qsro_c=C),
+            oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C))
+
+
+def state(smc, dims, S, seed):
+    N = 2 * dims[0] * dims[1] * dims[2]
+    lat = smc.Lattice(*dims, S)
+    occ = torch.empty(N, dtype=torch.int8, device=dev())
+    smc.init_lattice(lat, inputs.dirichlet_counts(N, S, seed), seed, occ)
+    return lat, occ
+
+
+def accept_threshold(r, kT):
+    """dE at which the test (r + 1/2) 2^-29 < exp(-dE / kT) flips."""
+    return -kT * math.log((r + 0.5) * 2.0 ** -29)
+
+
+def site_r(seed, replica, sweep, a):
+    """r of site a: the low 29 bits of its Philox word (the oracle's RNG)."""
+    w = oracle.philox4x32_10([a >> 2, replica, sweep & 0xFFFFFFFF, sweep >> 32],
+                             [seed & 0xFFFFFFFF, seed >> 32])[a & 3]
+    return int(w) & ((1 << 29) - 1)
+
+
+@pytest.mark.parametrize("dims,nsh,kT", [((8, 8, 8), 2, 0.07), ((12, 8, 16), 3, 0.05), ((8, 12, 8), 1, 0.1)])
+def test_lockstep_vs_oracle(smc, dims, nsh, kT):
+    S = 5
+    gm, om = models(smc, nsh, S)
+    lat, occ = state(smc, dims, S, 3)
+    olat = oracle.Lattice(*dims, S)
+    ref = occ.cpu().numpy().copy()
+    nA, _ = oracle.schedule(olat)
+    nt = lat.nsites // nA
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    worst, flips, n_acc = 0.0, 0, 0
+    for t in range(2):
+        for k in range(nA):
+            smc.ministep_trace(lat, gm, occ, 11, t, k, kT, dE=dE, acc=acc)
+            smc.check()
+            want, wacc, a, b = oracle.ministep_trace(olat, om, ref, 11, t, k, kT)
+            got, gacc = dE.cpu().numpy().astype(np.float64), acc.cpu().numpy().astype(bool)
+            err = np.abs(got - want)
+            worst = max(worst, float(err.max()))
+            assert np.all(err <= DE_TOL_EV), (t, k, float(err.max()))
+            bad = np.nonzero(gacc != wacc)[0]
+            for i in bad:  # a flip needs the acceptance threshold between the two dE values
+                thr = accept_threshold(site_r(11, 0, t, int(a[i])), kT)
+                lo, hi = sorted((got[i], want[i]))
+                slack = 1e-6 * kT  # the GPU evaluates exp in FP32
+                assert lo - slack <= thr <= hi + slack, (t, k, i, got[i], want[i], thr)
+            flips += len(bad)
+            n_acc += int(gacc.sum())
+            if len(bad):
+                ref[:] = occ.cpu().numpy()
+            else:
+                assert np.array_equal(occ.cpu().numpy(), ref), (t, k)
+    assert n_acc > 0 and worst < DE_TOL_EV
+    assert flips <= 2
+
+
+@pytest.mark.parametrize("dims,nsh", [((8, 8, 8), 2), ((12, 8, 16), 3), ((32, 32, 32), 2), ((16, 8, 8), 1)])
+def test_sweep_equals_trace(smc, dims, nsh):
+    S = 5
+    gm, _ = models(smc, nsh, S, seed=9)
+    lat, occ = state(smc, dims, S, 5)
+    occ2 = occ.clone()
+    kT = [0.06, 0.09]
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.sweep(lat, gm, occ, 4, 10, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    nA = 2 * 4 * 4 * 4
+    nt = lat.nsites // nA
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    n2 = 0
+    for t in range(2):
+        for k in range(nA):
+            smc.ministep_trace(lat, gm, occ2, 4, 10 + t, k, kT[t], dE=dE, acc=acc)
+            n2 += int(acc.sum().item())
+    smc.check()
+    assert torch.equal(occ, occ2)
+    assert int(n_acc.item()) == n2
+
+
+def test_energy_and_bookkeeping(smc):
+    S, nsh, dims = 5, 3, (16, 8, 12)
+    gm, om = models(smc, nsh, S)
+    lat, occ = state(smc, dims, S, 2)
+    olat = oracle.Lattice(*dims, S)
+    e0 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, gm, occ, e0)
+    smc.check()
+    assert float(e0.item()) == pytest.approx(oracle.total_energy(olat, om, occ.cpu().numpy()), rel=1e-12)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.sweep(lat, gm, occ, 3, 0, 3, 0.08, e_acc=e_acc, n_acc=n_acc)
+    e1 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, gm, occ, e1)
+    smc.check()
+    host = occ.cpu().numpy()
+    assert float(e1.item()) == pytest.approx(oracle.total_energy(olat, om, host), rel=1e-12)
+    # accepted FP32 dE against the exact change: within DE_TOL_EV per trial as a random walk (6 sigma)
+    n = int(n_acc.item())
+    assert abs(float(e1.item()) - float(e0.item()) - float(e_acc.item())) <= 6 * math.sqrt(n) * DE_TOL_EV / math.sqrt(3)
+    assert np.array_equal(np.bincount(host, minlength=S), inputs.dirichlet_counts(lat.nsites, S, 2))
+
+
+@pytest.mark.parametrize("nsh", [1, 3])
+def test_gradient_vs_oracle(smc, nsh):
+    S, dims = 4, (8, 8, 8)
+    gm, om = models(smc, nsh, S, seed=12)
+    lat, occ = state(smc, dims, S, 6)
+    g = torch.zeros(smc.grad_size(lat, gm), dtype=torch.float32, device=dev())
+    smc.energy_grad(lat, gm, occ, g)
+    smc.check()
+    want = oracle.energy_grad(oracle.Lattice(*dims, S), om, occ.cpu().numpy())
+    assert g.numel() == want.size
+    np.testing.assert_allclose(g.cpu().numpy().astype(np.float64), want, rtol=2 ** -23, atol=1e-6)
+
+
+def test_unsupported_and_invalid(smc):
+    S = 5
+    gm, _ = models(smc, 2, S)
+    lat, occ = state(smc, (6, 8, 8), S, 1)  # 6 cells: one link cell along x
+    with pytest.raises(smc.SMCError):
+        smc.sweep(lat, gm, occ, 1, 0, 1, 0.1)
+    lat2, occ2 = state(smc, (8, 8, 8), S, 1)
+    with pytest.raises(smc.SMCError):
+        smc.sweep_batched([lat2, lat2], gm, [occ2, occ2.clone()], 1, 0, 1, [0.1, 0.1])
+    V, W, C = inputs.qsro_coeffs(1, 2, S)
+    V[0, 0, 1] += 0.5  # not symmetric
+    with pytest.raises(smc.SMCError):
+        smc.sweep(lat2, smc.Model(smc.QSRO_F32, 2, V, qsro_w=W, qsro_c=C), occ2, 1, 0, 1, 0.1)
+
+
+def test_full_size_256_sampled(smc):
+    """256^3 cells, five species, 2-shell qSRO: one sweep, then mini-step 0 of
+    the next sweep traced on the GPU and by the oracle on the copied lattice;
+    every trial within DE_TOL_EV, composition conserved."""
+    S, nsh, dims = 5, 2, (256, 256, 256)
+    gm, om = models(smc, nsh, S)
+    lat, occ = state(smc, dims, S, 1)
+    counts = inputs.dirichlet_counts(lat.nsites, S, 1)
+    smc.sweep(lat, gm, occ, 1, 0, 1, 0.07)
+    smc.check()
+    ref = occ.cpu().numpy().copy()
+    nt = lat.nsites // 128
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    smc.ministep_trace(lat, gm, occ, 1, 1, 0, 0.07, dE=dE)
+    smc.check()
+    want, _, _, _ = oracle.ministep_trace(oracle.Lattice(*dims, S), om, ref, 1, 1, 0, 0.07)
+    err = np.abs(dE.cpu().numpy().astype(np.float64) - want)
+    assert float(err.max()) <= DE_TOL_EV
+    assert np.array_equal(np.bincount(occ.cpu().numpy(), minlength=S), counts)
