@@ -132,6 +132,25 @@ def cpu_baseline(prob, mini_steps: int):
     return ntr / dt, ntr, dt
 
 
+def cpu_baseline_qsro(mini_steps: int):
+    """The oracle on the qSRO workload's model and composition: the first
+    `mini_steps` mini-steps of sweep 0 of a 128^3 box (32,768 trials each)."""
+    import oracle
+    c4 = inputs.CONFIG4
+    S = c4["nspecies"]
+    V, W, C = inputs.qsro_coeffs(QSRO_SEED, QSRO_SHELLS, S)
+    lat = oracle.Lattice(128, 128, 128, S)
+    model = oracle.Model(oracle.QSRO, QSRO_SHELLS, V, qsro_w=W, qsro_c=C)
+    occ = oracle.init_lattice(lat, inputs.dirichlet_counts(lat.nsites, S, c4["comp_seed"]), c4["mc_seed"])
+    t0 = time.perf_counter()
+    ntr = 0
+    for k in range(mini_steps):
+        dE, _, _, _ = oracle.ministep_trace(lat, model, occ, c4["mc_seed"], 0, k, inputs.K_B_EV * c4["T"])
+        ntr += len(dE)
+    dt = time.perf_counter() - t0
+    return ntr / dt, ntr, dt
+
+
 def run_reference(args, rank):
     """Reference arm: the serial CPU oracle on the same workload and metric,
     a bounded sample of the job per step."""
@@ -292,6 +311,11 @@ def main():
         cpu = {"value": rate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_mini_steps} mini-steps (x32768 trials) of sweep 0 of the 128^3 job, "
                          f"serial C oracle, {dt:.1f} s"}
+        if extras:
+            qrate, qntr, qdt = cpu_baseline_qsro(2)
+            cpu["qsro"] = {"value": qrate, "unit": "attempts/s", "cores": 1, "kind": "oracle",
+                           "sample": f"2 mini-steps (x32768 trials) of the qSRO workload's model on a 128^3 box, "
+                                     f"serial C oracle, {qdt:.1f} s"}
     if dist:
         dist.barrier()
         dist.destroy_process_group()
