@@ -4,8 +4,8 @@
  * Canonical, composition-conserving Metropolis swap Monte Carlo on a BCC
  * alloy lattice, scheduled over non-interacting link cells (SMC-X, Sec. II-A;
  * SMC-AI, Sec. III-A and Algorithm 1).  Energies come from pair interactions
- * over neighbour shells or from a small BF16 MLP on per-shell species counts
- * (MLPNet, Sec. IV-B).
+ * over neighbour shells, from the qSRO model of local pair fractions, or from
+ * a small BF16 MLP on per-shell species counts (Sec. IV-B).
  *
  * Conventions shared by every entry point
  * ---------------------------------------
@@ -136,9 +136,13 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  * MLP models keep a per-site energy cache E[i] = f(x_i) in the workspace
  * (4 N bytes), filled at the start of every call and updated over the
  * interaction zone of every accepted swap, so a trial evaluates only the 40
- * post-swap energies of its zone.
- * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP models
- * on lattices the MLP kernel does not take), SMC_ERR_CUDA. */
+ * post-swap energies of its zone.  MLP and qSRO models keep the per-site
+ * features (species and per-shell species counts, 16 N bytes) the same way;
+ * a qSRO trial sums its zone's f(x') - f(x) in FP32 (C left out, where it
+ * cancels), within 1e-5 eV of FP64.  Both need every axis a multiple of 4
+ * cells and >= 8, nx <= 1024.
+ * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP or
+ * qSRO models on lattices their kernels do not take), SMC_ERR_CUDA. */
 smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
                      uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT,
                      double *e_acc, int64_t *n_acc, cudaStream_t stream);
@@ -177,7 +181,7 @@ smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int
  *   lats    host [R];  occ  host [R] array of device pointers.
  *   kT      host [R][nsweeps] (eV).
  *   e_acc, n_acc  device [R], nullable.
- * MLP models: R must be 1 (SMC_ERR_UNSUPPORTED otherwise). */
+ * MLP and qSRO models: R must be 1 (SMC_ERR_UNSUPPORTED otherwise). */
 smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model *model,
                              int8_t *const *occ, uint64_t seed, uint32_t replica0,
                              uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
@@ -194,8 +198,11 @@ smc_status smc_sro(const smc_lattice *lat, int32_t nshells, const int8_t *occ, i
 
 /* Total energy of occ.  MLP models: the site energies of the tensor-core
  * evaluation summed in FP64 in a fixed order (bit-reproducible); pair + MLP
- * models add the pair energy from the pair counts.
- *   e      device double (eV), nullable (required for MLP models).
+ * models add the pair energy from the pair counts.  qSRO models: in FP64
+ * from exact integer counts, sum V_m^{pq} n_m^{pq} / z_m + sum W_m^p Q_m^p /
+ * z_m^2 + N C, with n the ordered pair counts and Q_m^p the sum over sites
+ * of species p of their squared same-element count in shell m.
+ *   e      device double (eV), nullable (required for MLP and qSRO models).
  *   e_int  device int64, nullable; integer models only: E in units of unit_ev
  *          (exact). */
 smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
@@ -205,7 +212,9 @@ smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8
  * Layout: pair part [nshells][S(S+1)/2] with (p, q), p <= q, row-major over
  * p then q (one parameter per unordered pair: dE/dV_m^{pq} = n_m^{pq} for
  * p != q, n_m^{pp}/2 for p = q), then for MLP models the 5569 MLP parameters
- * W1, b1, W2, b2, W3, b3.
+ * W1, b1, W2, b2, W3, b3.  qSRO models: [V_m^{pq}, p <= q]
+ * ((n_m^{pq} + n_m^{qp}) / z_m for p != q, n_m^{pp} / z_m for p = q), then
+ * [W_m^p] (Q_m^p / z_m^2), then C (N).
  *   grad   device float [smc_grad_size(lat, model)]. */
 int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model);
 smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
@@ -215,7 +224,9 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
  * (as smc_sweep would) and records, per trial in link-cell order
  * c = (cz*NLy + cy)*NLx + cx, the dE it computed (eV) and its decision.
  * MLP models recompute the pre-swap energies (no cache) with the sweep's
- * arithmetic, so a sweep equals its 2 Lx Ly Lz traced mini-steps bit for bit.
+ * arithmetic, and qSRO models count the features from occ with the sweep's
+ * row arithmetic, so a sweep equals its 2 Lx Ly Lz traced mini-steps bit for
+ * bit.
  *   dE   device float [N/n_A], nullable;  acc  device uint8 [N/n_A], nullable. */
 smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ,
                               uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,
