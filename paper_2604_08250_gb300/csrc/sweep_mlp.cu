@@ -895,10 +895,22 @@ __global__ void __launch_bounds__(kQsroSweepThreads) k_sweep_qsro(const __grid_c
 {
     __shared__ float Q[kQsroParams];
     __shared__ OmegaEntry geo[2 * 8 * kQsroGeoStride];
+    __shared__ int nrel[2 * 8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     for (int i = tid; i < kQsroParams; i += blockDim.x) Q[i] = P.D.df[i];
-    for (int i = tid; i < 2 * 8 * kOmega; i += blockDim.x)
-        geo[(i / kOmega) * kQsroGeoStride + i % kOmega] = (&G.om[0][0][0])[i];
+    // per (sublattice, direction): the zone entries whose row can be nonzero
+    // for this model's shells (a, b, and the sites that see exactly one of
+    // them within those shells), in entry order; the others add exactly 0
+    // to dE and change only counts of shells the model does not read
+    if (tid < 16) {
+        int n = 0;
+        for (int e = 0; e < kOmega; ++e) {
+            const OmegaEntry oe = (&G.om[0][0][0])[tid * kOmega + e];
+            const bool ina = oe.ma >= 1 && oe.ma <= P.nshells, inb = oe.mb >= 1 && oe.mb <= P.nshells;
+            if (e < 2 || ((ina || inb) && oe.ma != oe.mb)) geo[tid * kQsroGeoStride + n++] = oe;
+        }
+        nrel[tid] = n;
+    }
     const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
     const RepDesc &RD = P.rep[0];
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx, nk = (NLx + 31) >> 5;
@@ -961,6 +973,7 @@ __global__ void __launch_bounds__(kQsroSweepThreads) k_sweep_qsro(const __grid_c
                             continue;
                         }
                         const OmegaEntry *om = geo + (sub * 8 + dir) * kQsroGeoStride;
+                        const int nr = nrel[sub * 8 + dir];
                         auto zone_site = [&](const OmegaEntry &oe) {
                             const int ssub = oe.rel ? 1 - sub : sub;
                             return ((ssub * nz + wrapc(z0 + oe.dz, nz)) * ny + wrapc(y0 + oe.dy, ny)) * nx +
@@ -970,15 +983,17 @@ __global__ void __launch_bounds__(kQsroSweepThreads) k_sweep_qsro(const __grid_c
                         // rows in entry order
                         float dE = 0.f;
 #pragma unroll 1
-                        for (int e0 = 0; e0 < kOmega; e0 += kQsroBatch) {
+                        for (int e0 = 0; e0 < nr; e0 += kQsroBatch) {
                             uint4 f[kQsroBatch];
 #pragma unroll
-                            for (int u = 0; u < kQsroBatch; ++u) f[u] = __ldcg(P.fcache + zone_site(om[e0 + u]));
+                            for (int u = 0; u < kQsroBatch; ++u)
+                                if (e0 + u < nr) f[u] = __ldcg(P.fcache + zone_site(om[e0 + u]));
 #pragma unroll
-                            for (int u = 0; u < kQsroBatch; ++u) {
-                                const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
-                                dE += qsro_row(Q, P.nshells, P.S, om[e0 + u], e0 + u, A, B, f[u].x, h);
-                            }
+                            for (int u = 0; u < kQsroBatch; ++u)
+                                if (e0 + u < nr) {
+                                    const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
+                                    dE += qsro_row(Q, P.nshells, P.S, om[e0 + u], e0 + u, A, B, f[u].x, h);
+                                }
                         }
                         if (metropolis<false>(dE, w & kRMask, beta, nullptr, make_int2(0, 0))) {
                             occ[a] = (int8_t)B;
@@ -986,21 +1001,23 @@ __global__ void __launch_bounds__(kQsroSweepThreads) k_sweep_qsro(const __grid_c
                             colE += dE;
                             accN += 1;
 #pragma unroll 1
-                            for (int e0 = 0; e0 < kOmega; e0 += kQsroBatch) {
+                            for (int e0 = 0; e0 < nr; e0 += kQsroBatch) {
                                 uint4 f[kQsroBatch];
                                 int site[kQsroBatch];
 #pragma unroll
-                                for (int u = 0; u < kQsroBatch; ++u) {
-                                    site[u] = zone_site(om[e0 + u]);
-                                    f[u] = __ldcg(P.fcache + site[u]);
-                                }
+                                for (int u = 0; u < kQsroBatch; ++u)
+                                    if (e0 + u < nr) {
+                                        site[u] = zone_site(om[e0 + u]);
+                                        f[u] = __ldcg(P.fcache + site[u]);
+                                    }
 #pragma unroll
-                                for (int u = 0; u < kQsroBatch; ++u) {
-                                    const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
-                                    uint32_t q0n, hn[3];
-                                    qsro_post(om[e0 + u], e0 + u, A, B, f[u].x, h, q0n, hn);
-                                    __stcg(P.fcache + site[u], make_uint4(q0n, hn[0], hn[1], hn[2]));
-                                }
+                                for (int u = 0; u < kQsroBatch; ++u)
+                                    if (e0 + u < nr) {
+                                        const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
+                                        uint32_t q0n, hn[3];
+                                        qsro_post(om[e0 + u], e0 + u, A, B, f[u].x, h, q0n, hn);
+                                        __stcg(P.fcache + site[u], make_uint4(q0n, hn[0], hn[1], hn[2]));
+                                    }
                             }
                         }
                     }
