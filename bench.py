@@ -33,7 +33,10 @@ from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
 # MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
-QSRO_SEED, QSRO_SHELLS, QSRO_ZONE = 7, 2, 40  # qSRO workload parameters; 40-site interaction zone
+QSRO_SEED, QSRO_SHELLS = 7, 2  # qSRO workload parameters
+# zone rows a qSRO trial evaluates (a, b and the sites that see exactly one
+# of them within the model's shells), counted from the BCC geometry
+QSRO_ROWS = {1: 16, 2: 22, 3: 40}
 INSTR_PER_TRIAL_512 = 352.9  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
@@ -550,9 +553,9 @@ def run_extras(smc, torch, dev, pk):
     msq = timed(lambda: smc.sweep(latq, qm, occq, 1, 0, nswq, kTq, n_acc=nq), reps=1)
     attq = latq.nsites * nswq / (msq * 1e-3)
     accq = float(nq.item()) / (2 * latq.nsites * nswq)
-    # bytes the design moves per attempt: 40 zone feature rows read (16 B), and
-    # rewritten when accepted, plus the two species read and written
-    bq = QSRO_ZONE * 16 * (1 + accq) + 2 + 2 * accq
+    # bytes the design moves per attempt: the evaluated zone rows' features
+    # read (16 B each) and rewritten when accepted, the two species read and written
+    bq = QSRO_ROWS[QSRO_SHELLS] * 16 * (1 + accq) + 2 + 2 * accq
     out["qsro_256"] = {"cells": [256] * 3, "shells": QSRO_SHELLS, "sweeps_per_launch": nswq,
                        "ms_per_sweep": msq / nswq, "attempts_per_s": attq, "accept_rate": accq,
                        "cache_bytes_per_attempt": bq, "achieved_gbs": attq * bq / 1e9,
