@@ -20,8 +20,8 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_HERE, "liboracle.so")
 _SRC = os.path.join(_HERE, "smc_oracle.c")
 
-PAIR_I32, PAIR_F32, MLP, PAIR_F32_MLP, QSRO = 0, 1, 2, 3, 4
-MLP_IN, MLP_HID = 20, 64
+PAIR_I32, PAIR_F32, MLP, PAIR_F32_MLP, QSRO, MLPNET = 0, 1, 2, 3, 4, 5
+MLP_IN, MLP_HID, NET_HID = 20, 64, 96
 MLP_NPARAM = MLP_HID * MLP_IN + MLP_HID + MLP_HID * MLP_HID + MLP_HID + MLP_HID + 1
 
 
@@ -51,7 +51,11 @@ class _Model(C.Structure):
                 ("w3", C.POINTER(C.c_double)),
                 ("b1", C.POINTER(C.c_double)), ("b2", C.POINTER(C.c_double)),
                 ("b3", C.c_double),
-                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_double)]
+                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_double),
+                ("net_w0", C.POINTER(C.c_double)), ("net_w1", C.POINTER(C.c_double)),
+                ("net_w2", C.POINTER(C.c_double)), ("net_w3", C.POINTER(C.c_double)),
+                ("net_b0", C.POINTER(C.c_double)), ("net_b1", C.POINTER(C.c_double)),
+                ("net_b2", C.POINTER(C.c_double)), ("net_b3", C.c_double)]
 
 
 _lib = None
@@ -99,6 +103,8 @@ def lib():
         L.orc_grad_size.restype = C.c_int64
         L.orc_energy_grad.argtypes = [P(_Lat), P(_Model), P(C.c_int8), P(C.c_double)]
         L.orc_mlp_eval.argtypes = [P(_Model), P(C.c_double)]
+        L.orc_mlpnet_eval.argtypes = [P(_Model), P(C.c_double)]
+        L.orc_mlpnet_eval.restype = C.c_double
         L.orc_mlp_eval.restype = C.c_double
         _lib = L
     return _lib
@@ -137,7 +143,7 @@ class Model:
     BF16 and FP32 values are widened to FP64 exactly."""
 
     def __init__(self, kind: int, nshells: int = 0, v=None, unit_ev: float = 1e-4, mlp=None, qsro_w=None,
-                 qsro_c: float = 0.0):
+                 qsro_c: float = 0.0, net=None):
         self.kind, self.nshells, self.unit_ev = int(kind), int(nshells), float(unit_ev)
         self._keep = []
         c = _Model()
@@ -152,6 +158,14 @@ class Model:
             self.qsro_w = np.ascontiguousarray(qsro_w, dtype=np.float32)
             c.qsro_w = _ptr(self.qsro_w, C.c_float)
             c.qsro_c = float(np.float32(qsro_c))
+        if kind == MLPNET:  # net: w0..w3 (BF16 bit patterns or floats), b0..b2, b3
+            self.net = {k: _widen(net[k]) for k in ("w0", "w1", "w2", "w3", "b0", "b1", "b2")}
+            sizes = dict(w0=NET_HID * MLP_IN, w1=NET_HID * NET_HID, w2=NET_HID * NET_HID, w3=NET_HID,
+                         b0=NET_HID, b1=NET_HID, b2=NET_HID)
+            for k, n in sizes.items():
+                assert self.net[k].size == n, k
+                setattr(c, "net_" + k, _ptr(self.net[k], C.c_double))
+            c.net_b3 = float(net["b3"])
         if kind in (MLP, PAIR_F32_MLP):
             self.mlp = {k: _widen(mlp[k]) for k in ("w1", "w2", "w3", "b1", "b2")}
             assert self.mlp["w1"].size == MLP_HID * MLP_IN
@@ -295,6 +309,12 @@ def energy_grad(lat, model, occ) -> np.ndarray:
     if rc != 0:
         raise ValueError("orc_energy_grad rejected its arguments")
     return g
+
+
+def mlpnet_eval(model, x) -> float:
+    xa = np.ascontiguousarray(x, dtype=np.float64)
+    assert xa.size == MLP_IN
+    return lib().orc_mlpnet_eval(C.byref(model._c), _ptr(xa, C.c_double))
 
 
 def mlp_eval(model, x) -> float:

@@ -238,6 +238,38 @@ double orc_mlp_eval(const orc_model *m, const double x[ORC_MLP_IN])
     return f;
 }
 
+/* MLPNet (Sec. IV-B): an input layer and two hidden layers of 96 units,
+ * each followed by ReLU, then a linear regression layer:
+ *   h1 = relu(W0 x + b0), h2 = relu(W1 h1 + b1), h3 = relu(W2 h2 + b2),
+ *   f = W3 h3 + b3. */
+static double relu(double z)
+{
+    return z > 0.0 ? z : 0.0;
+}
+
+double orc_mlpnet_eval(const orc_model *m, const double x[ORC_MLP_IN])
+{
+    double h1[ORC_NET_HID], h2[ORC_NET_HID], h3[ORC_NET_HID];
+    for (int j = 0; j < ORC_NET_HID; ++j) {
+        double z = m->net_b0[j];
+        for (int i = 0; i < ORC_MLP_IN; ++i) z += m->net_w0[j * ORC_MLP_IN + i] * x[i];
+        h1[j] = relu(z);
+    }
+    for (int k = 0; k < ORC_NET_HID; ++k) {
+        double z = m->net_b1[k];
+        for (int j = 0; j < ORC_NET_HID; ++j) z += m->net_w1[k * ORC_NET_HID + j] * h1[j];
+        h2[k] = relu(z);
+    }
+    for (int k = 0; k < ORC_NET_HID; ++k) {
+        double z = m->net_b2[k];
+        for (int j = 0; j < ORC_NET_HID; ++j) z += m->net_w2[k * ORC_NET_HID + j] * h2[j];
+        h3[k] = relu(z);
+    }
+    double f = m->net_b3;
+    for (int k = 0; k < ORC_NET_HID; ++k) f += m->net_w3[k] * h3[k];
+    return f;
+}
+
 static void mlp_features(const orc_lattice *lat, const int8_t *occ, int64_t i, double x[ORC_MLP_IN])
 {
     for (int t = 0; t < ORC_MLP_IN; ++t) x[t] = 0.0;
@@ -319,6 +351,11 @@ double orc_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t 
     double e = 0.0;
     if (m->kind == ORC_PAIR_I32) return 0.5 * (double)site_energy2_i64(lat, m, occ, i);
     if (m->kind == ORC_QSRO) return qsro_site_energy(lat, m, occ, i);
+    if (m->kind == ORC_MLPNET) {
+        double x[ORC_MLP_IN];
+        mlp_features(lat, occ, i, x);
+        return orc_mlpnet_eval(m, x);
+    }
     if (has_pair(m)) {
         double sum = 0.0;
         for (int sh = 1; sh <= m->nshells; ++sh)
@@ -360,7 +397,7 @@ int64_t orc_total_energy_i64(const orc_lattice *lat, const orc_model *m, const i
 static int model_reach(const orc_model *m)
 {
     int r = (has_pair(m) || m->kind == ORC_QSRO) ? m->nshells : 0;
-    if (has_mlp(m) && r < 3) r = 3;
+    if ((has_mlp(m) || m->kind == ORC_MLPNET) && r < 3) r = 3;
     return r;
 }
 
@@ -651,7 +688,10 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
 
 static int model_ok(const orc_lattice *lat, const orc_model *m)
 {
-    if (m->kind < ORC_PAIR_I32 || m->kind > ORC_QSRO) return 0;
+    if (m->kind < ORC_PAIR_I32 || m->kind > ORC_MLPNET) return 0;
+    if (m->kind == ORC_MLPNET && (!m->net_w0 || !m->net_w1 || !m->net_w2 || !m->net_w3 || !m->net_b0 ||
+                                  !m->net_b1 || !m->net_b2 || lat->nspecies > ORC_MLP_SPECIES))
+        return 0;
     if ((has_pair(m) || m->kind == ORC_QSRO) && (m->nshells < 1 || m->nshells > 3)) return 0;
     if (m->kind == ORC_QSRO && (!m->v_f32 || !m->qsro_w)) return 0;
     if (m->kind == ORC_PAIR_I32 && (!m->v_i32 || !(m->unit_ev > 0.0))) return 0;
@@ -738,7 +778,7 @@ int64_t orc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *o
  * shells: 2.5 from a, which is 3 cells. */
 int orc_slab_ghost_cells(const orc_model *m)
 {
-    return (has_mlp(m) || m->kind == ORC_QSRO) ? 3 : 2;
+    return (has_mlp(m) || m->kind == ORC_QSRO || m->kind == ORC_MLPNET) ? 3 : 2;
 }
 
 int64_t orc_slab_ministep(const orc_lattice *glat, const orc_model *m, int8_t *occ_loc,
@@ -888,7 +928,7 @@ static void mlp_backprop(const orc_model *m, const double x[ORC_MLP_IN], double 
 int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *occ, double *grad)
 {
     geom_init();
-    if (!lattice_ok(lat) || !model_ok(lat, m)) return -1;
+    if (!lattice_ok(lat) || !model_ok(lat, m) || m->kind == ORC_MLPNET) return -1;
     int S = lat->nspecies;
     int64_t n = orc_grad_size(lat, m), N = orc_nsites(lat);
     for (int64_t t = 0; t < n; ++t) grad[t] = 0.0;

@@ -43,8 +43,9 @@ extern "C" {
 #define ORC_MLP_IN 20
 #define ORC_MLP_HID 64
 #define ORC_MLP_SPECIES 5
+#define ORC_NET_HID 96
 
-enum { ORC_PAIR_I32 = 0, ORC_PAIR_F32 = 1, ORC_MLP = 2, ORC_PAIR_F32_MLP = 3, ORC_QSRO = 4 };
+enum { ORC_PAIR_I32 = 0, ORC_PAIR_F32 = 1, ORC_MLP = 2, ORC_PAIR_F32_MLP = 3, ORC_QSRO = 4, ORC_MLPNET = 5 };
 
 typedef struct {
     int32_t nx, ny, nz;   /* cells per axis, each >= 2 */
@@ -65,6 +66,11 @@ typedef struct {
     double b3;
     const float *qsro_w;     /* qSRO: W_m^p, [nshells][S], eV */
     double qsro_c;           /* qSRO: C, eV per site */
+    /* MLPNet (Sec. IV-B): W0 [96][20], W1 [96][96], W2 [96][96], W3 [96],
+     * b0, b1, b2 [96], b3 (row = output unit), FP64 */
+    const double *net_w0, *net_w1, *net_w2, *net_w3;
+    const double *net_b0, *net_b1, *net_b2;
+    double net_b3;
 } orc_model;
 
 /* Philox4x32-10 block function: out = Philox(ctr, key). */
@@ -128,6 +134,8 @@ int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *oc
 
 /* MLP site function on an explicit feature vector (for tests). */
 double orc_mlp_eval(const orc_model *m, const double x[ORC_MLP_IN]);
+/* MLPNet site function on an explicit feature vector (for tests). */
+double orc_mlpnet_eval(const orc_model *m, const double x[ORC_MLP_IN]);
 
 #ifdef __cplusplus
 }

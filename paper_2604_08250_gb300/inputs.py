@@ -118,6 +118,35 @@ def mlp_weights(seed: int, n_in: int = 20, n_hid: int = 64, out_scale: float = 0
     }
 
 
+def mlpnet_weights(seed: int, n_in: int = 20, n_hid: int = 96, out_scale: float = 0.01,
+                   bias_sigma: float = 0.05) -> dict:
+    """MLPNet at the paper's shape (20 -> 96 -> 96 -> 96 -> 1, ReLU): He-uniform
+    weights U(+-sqrt(6/fan_in)) from default_rng(seed) rounded to BF16, FP32
+    biases N(0, bias_sigma) (so the bias path is exercised), output layer
+    multiplied by out_scale before rounding (site energies of a few meV)."""
+    rng = np.random.default_rng(seed)
+
+    def he(fan_out, fan_in):
+        lim = np.sqrt(6.0 / fan_in)
+        return rng.uniform(-lim, lim, size=(fan_out, fan_in))
+
+    w0 = he(n_hid, n_in)
+    w1 = he(n_hid, n_hid)
+    w2 = he(n_hid, n_hid)
+    w3 = he(1, n_hid)[0] * out_scale
+    bias = [rng.normal(0.0, bias_sigma, n_hid).astype(np.float32) for _ in range(3)]
+    return {
+        "w0": to_bf16_bits(w0.astype(np.float32)).reshape(-1),
+        "w1": to_bf16_bits(w1.astype(np.float32)).reshape(-1),
+        "w2": to_bf16_bits(w2.astype(np.float32)).reshape(-1),
+        "w3": to_bf16_bits(w3.astype(np.float32)).reshape(-1),
+        "b0": bias[0],
+        "b1": bias[1],
+        "b2": bias[2],
+        "b3": float(np.float32(rng.normal(0.0, 0.001))),
+    }
+
+
 def anneal_kT(nsweeps: int = 1000, t_start: float = 3000.0, t_end: float = 300.0) -> np.ndarray:
     """Linear anneal T_t = t_start + (t_end - t_start) t/(nsweeps-1), kT in eV."""
     t = np.arange(nsweeps, dtype=np.float64)
