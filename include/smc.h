@@ -89,7 +89,8 @@ enum {
     SMC_PAIR_F32 = 1,          /* FP32 pair coefficients, eV */
     SMC_MLP_BF16 = 2,          /* BF16 MLP site energies */
     SMC_PAIR_F32_MLP_BF16 = 3, /* sum of the two */
-    SMC_QSRO_F32 = 4           /* qSRO site energies (Sec. IV-B), FP32 parameters */
+    SMC_QSRO_F32 = 4,          /* qSRO site energies (Sec. IV-B), FP32 parameters */
+    SMC_MLPNET_BF16 = 5        /* MLPNet at the paper's shape (Sec. IV-B): 96-wide, ReLU, BF16 */
 };
 
 /* Energy model (all pointers host memory, read during the call).
@@ -103,7 +104,7 @@ enum {
  * W_m^p in qsro_w ([nshells][S]), C in qsro_c.  The constant lambda sum W^2
  * of the paper's equation is a training regulariser and is not part of E. */
 typedef struct {
-    int32_t kind;            /* SMC_PAIR_I32 .. SMC_QSRO_F32 */
+    int32_t kind;            /* SMC_PAIR_I32 .. SMC_MLPNET_BF16 */
     int32_t nshells;         /* pair / qSRO shells 1..3 (ignored for SMC_MLP_BF16) */
     const int32_t *v_i32;    /* SMC_PAIR_I32: units of unit_ev, |V| <= 2^24 */
     const float *v_f32;      /* SMC_PAIR_F32*, SMC_QSRO_F32: eV */
@@ -113,6 +114,12 @@ typedef struct {
     float mlp_b3;
     const float *qsro_w;     /* SMC_QSRO_F32: W_m^p, [nshells][S], eV */
     float qsro_c;            /* SMC_QSRO_F32: C, eV per site */
+    /* SMC_MLPNET_BF16: f = W3 h3 + b3, h3 = relu(W2 h2 + b2), h2 = relu(W1 h1
+     * + b1), h1 = relu(W0 x + b0) on the MLP's 20 features; BF16 bit patterns
+     * w0 [96][20], w1 [96][96], w2 [96][96], w3 [96], FP32 biases. */
+    const uint16_t *net_w0, *net_w1, *net_w2, *net_w3;
+    const float *net_b0, *net_b1, *net_b2;
+    float net_b3;
 } smc_model;
 
 /* Composition-conserving random initial configuration (the starting state

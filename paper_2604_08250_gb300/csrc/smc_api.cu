@@ -140,7 +140,10 @@ bool lattice_valid(const smc_lattice *lat, bool mlp)
     return true;
 }
 
-static bool is_mlp(const smc_model *m) { return m->kind == SMC_MLP_BF16 || m->kind == SMC_PAIR_F32_MLP_BF16; }
+static bool is_mlp(const smc_model *m)
+{
+    return m->kind == SMC_MLP_BF16 || m->kind == SMC_PAIR_F32_MLP_BF16 || m->kind == SMC_MLPNET_BF16;
+}
 static bool is_qsro(const smc_model *m) { return m->kind == SMC_QSRO_F32; }
 static bool has_pair(const smc_model *m)
 {
@@ -153,7 +156,7 @@ bool model_valid(const smc_lattice *lat, const smc_model *m)
         set_error("model is NULL");
         return false;
     }
-    if (m->kind < SMC_PAIR_I32 || m->kind > SMC_QSRO_F32) {
+    if (m->kind < SMC_PAIR_I32 || m->kind > SMC_MLPNET_BF16) {
         set_error("unknown model kind %d", m->kind);
         return false;
     }
@@ -216,7 +219,16 @@ bool model_valid(const smc_lattice *lat, const smc_model *m)
             return false;
         }
     }
-    if (is_mlp(m)) {
+    if (m->kind == SMC_MLPNET_BF16) {
+        if (!m->net_w0 || !m->net_w1 || !m->net_w2 || !m->net_w3 || !m->net_b0 || !m->net_b1 || !m->net_b2) {
+            set_error("MLPNet model needs w0, w1, w2, w3, b0, b1, b2");
+            return false;
+        }
+        if (S > 5) {
+            set_error("MLP models support at most 5 species");
+            return false;
+        }
+    } else if (is_mlp(m)) {
         if (!m->mlp_w1 || !m->mlp_w2 || !m->mlp_w3 || !m->mlp_b1 || !m->mlp_b2) {
             set_error("MLP model needs w1, w2, w3, b1, b2");
             return false;
@@ -517,6 +529,7 @@ int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model)
     const int S = lat->nspecies;
     int64_t n = 0;
     if (has_pair(model)) n += (int64_t)model->nshells * S * (S + 1) / 2;
+    if (model->kind == SMC_MLPNET_BF16) return -1;
     if (is_mlp(model)) n += 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1;
     if (is_qsro(model)) n += (int64_t)model->nshells * S * (S + 1) / 2 + (int64_t)model->nshells * S + 1;
     return n;
@@ -530,6 +543,10 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
     if (!occ || !grad) {
         set_error("occ and grad must be non-NULL");
         return SMC_ERR_ARG;
+    }
+    if (model->kind == SMC_MLPNET_BF16) {
+        set_error("smc_energy_grad does not take MLPNet models");
+        return SMC_ERR_UNSUPPORTED;
     }
     if (is_mlp(model)) return launch_mlp_grad(lat, model, occ, grad, stream);
     if (is_qsro(model)) return launch_qsro_grad(lat, model, occ, grad, stream);

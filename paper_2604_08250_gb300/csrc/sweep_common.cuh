@@ -58,7 +58,7 @@ struct SweepParams {
     int warp_bytes;       // fast kernel: shared-memory bytes per warp
     int nap_cap;          // fast kernel: longest sleep between progress polls (ns)
     int kind;             // model kind (SMC_PAIR_I32 .. SMC_PAIR_F32_MLP_BF16)
-    const MlpBlock *mlpw; // MLP weights (device), MLP kinds only
+    const void *mlpw;     // network weights (device MlpBlock or NetBlock), MLP kinds only
     float *ecache;        // per-site MLP energy f(x_i) (device, N floats), MLP kinds only
     uint4 *fcache;        // per-site MLP features {species, shell-1, -2, -3 packed counts} (device, N)
     int rowB;             // fast kernel: row stride in shared memory

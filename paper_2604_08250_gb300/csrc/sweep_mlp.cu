@@ -25,16 +25,17 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "mlp_common.cuh"
 #include "mlp_tc.cuh"
+#include "mlpnet_tc.cuh"
 #include "sweep_common.cuh"
 
 namespace smc {
 
 constexpr int kOmega = 40;       // sites of a trial's interaction zone
-constexpr int kSweepThreads = 512;  // four warpgroups, each with its own tensor-core tiles
 constexpr int kMlpChunk = 64;    // most trials of a mini-step evaluated together (40 rows each)
 constexpr int kTraceTB = 3;      // trials per trace step (120 rows: one tile)
 constexpr int kTcMaxCtasPerSm = 512 / (2 * kTcCols);  // for the 2-warpgroup kernels
@@ -76,8 +77,62 @@ struct MlpSmem {
     static_assert(X % 128 == 0 && H % 128 == 0 && W2 % 128 == 0, "tile alignment");
     static_assert(MBAR % 8 == 0 && RED % 8 == 0, "alignment");
 };
-constexpr int kSweepWG = 4;  // warpgroups of the sweep kernel
+constexpr int kSweepWG = 4;  // warpgroups of the sweep kernel (64-wide network)
 constexpr int kEvalWG = 2;   // warpgroups of the energy and trace kernels
+
+// Shared memory of the MLPNet kernels (96-wide, three ReLU layers): the same
+// kernel-specific parts as MlpSmem from CTL on, without the pair table.
+template <int NWG>
+struct NetSmem {
+    static constexpr uint32_t W0 = 0;
+    static constexpr uint32_t W1 = W0 + kNetW0;
+    static constexpr uint32_t W2 = W1 + kNetW12;
+    static constexpr uint32_t X = W2 + kNetW12;      // [NWG] tiles
+    static constexpr uint32_t H = X + NWG * kNetX;   // [NWG] tiles
+    static constexpr uint32_t W3 = H + NWG * kNetHt;
+    static constexpr uint32_t B3 = W3 + kNetHid * 4;
+    static constexpr uint32_t MBAR = B3 + 16;        // [NWG][2]
+    static constexpr uint32_t TSLOT = MBAR + 16 * NWG;
+    static constexpr uint32_t CTL = TSLOT + 4;
+    static constexpr uint32_t RED = (CTL + 4 + 15) / 16 * 16;
+    static constexpr uint32_t TINFO = RED + 64;
+    static constexpr uint32_t ACT = TINFO + kMlpChunk * kTinfo * 4;
+    static constexpr uint32_t GEO = ACT + kMlpChunk * 4;
+    static constexpr uint32_t END = (uint32_t)((GEO + sizeof(MlpGeo) + 127) / 128 * 128);
+    static_assert(X % 128 == 0 && H % 128 == 0 && W1 % 128 == 0 && W2 % 128 == 0, "tile alignment");
+    static_assert(MBAR % 8 == 0 && RED % 8 == 0, "alignment");
+};
+
+// The two site-energy networks the MLP kernels run: evaluator, layouts and
+// warpgroups of the sweep.
+struct NetSilu64 {  // MLP of mlp_tc.cuh: 20 -> 64 -> 64 -> 1, SiLU
+    using Eval = TcEval;
+    using Block = MlpBlock;
+    template <int NWG>
+    using Smem = MlpSmem<NWG>;
+    static constexpr int kSweepNWG = kSweepWG;
+    template <int NWG>
+    static __device__ TcLayout layout(uint32_t wg)
+    {
+        using M = MlpSmem<NWG>;
+        return TcLayout{M::X + wg * kTcX, M::H + wg * kTcH, M::W1, M::W2, M::B1, M::B2, M::W3, M::B3,
+                        M::MBAR + 16 * wg, M::TSLOT};
+    }
+};
+struct NetRelu96 {  // MLPNet of mlpnet_tc.cuh: 20 -> 96 -> 96 -> 96 -> 1, ReLU
+    using Eval = NetEval;
+    using Block = NetBlock;
+    template <int NWG>
+    using Smem = NetSmem<NWG>;
+    static constexpr int kSweepNWG = 2;  // the 28 KB hidden tiles of four would not fit
+    template <int NWG>
+    static __device__ NetLayout layout(uint32_t wg)
+    {
+        using M = NetSmem<NWG>;
+        return NetLayout{M::X + wg * kNetX, M::H + wg * kNetHt, M::W0, M::W1, M::W2, M::W3, M::B3, M::MBAR + 16 * wg,
+                         M::TSLOT};
+    }
+};
 
 // Site-energy models of the tensor-core sweep.
 constexpr int kModeMlp = 0, kModeMlpPair = 1;
@@ -155,14 +210,12 @@ __device__ __forceinline__ float qsro_row(const float *Q, int nsh, int S, const 
 }
 
 // The evaluator of this thread's warpgroup.
-template <int NWG>
-__device__ __forceinline__ TcEval mlp_evaluator(long long timeout_ns, int *status, int *abort_flag)
+template <class Net, int NWG>
+__device__ __forceinline__ typename Net::Eval mlp_evaluator(long long timeout_ns, int *status, int *abort_flag)
 {
-    using M = MlpSmem<NWG>;
     const uint32_t wg = threadIdx.x >> 7;
-    TcEval E;
-    E.L = TcLayout{M::X + wg * kTcX, M::H + wg * kTcH, M::W1, M::W2, M::B1, M::B2, M::W3, M::B3, M::MBAR + 16 * wg,
-                   M::TSLOT};
+    typename Net::Eval E;
+    E.L = Net::template layout<NWG>(wg);
     E.timeout_ns = timeout_ns;
     E.status = status;
     E.abort_flag = abort_flag;
@@ -196,16 +249,18 @@ __device__ __forceinline__ float pair_part(const SweepParams &P, const int *ha, 
 }
 
 // Copies the model (weights, pair table, geometry) and sets up the evaluators.
-template <int NWG>
-__device__ void mlp_cta_setup(TcEval &E, const MlpBlock *W, const float *Dsrc, const MlpGeo *geo)
+template <class Net, int NWG>
+__device__ void mlp_cta_setup(typename Net::Eval &E, const void *W, const float *Dsrc, const MlpGeo *geo)
 {
-    tc_load_weights(W, E.L);
+    using M = typename Net::template Smem<NWG>;
+    tc_load_weights((const typename Net::Block *)W, E.L);
     const int tid = threadIdx.x, n = blockDim.x;
-    if (Dsrc)
-        for (int i = tid; i < kDEntries; i += n) ((float *)(g_smem + MlpSmem<NWG>::D))[i] = Dsrc[i];
+    if constexpr (std::is_same<Net, NetSilu64>::value) {
+        if (Dsrc)
+            for (int i = tid; i < kDEntries; i += n) ((float *)(g_smem + M::D))[i] = Dsrc[i];
+    }
     if (geo)
-        for (int i = tid; i < (int)(sizeof(MlpGeo) / 4); i += n)
-            ((int *)(g_smem + MlpSmem<NWG>::GEO))[i] = ((const int *)geo)[i];
+        for (int i = tid; i < (int)(sizeof(MlpGeo) / 4); i += n) ((int *)(g_smem + M::GEO))[i] = ((const int *)geo)[i];
     tc_setup(E, NWG);
 }
 
@@ -214,14 +269,16 @@ __device__ void mlp_cta_setup(TcEval &E, const MlpBlock *W, const float *Dsrc, c
 // (the sweep's cache), and their sum per CTA in a fixed order.  Each
 // warpgroup takes 128 consecutive sites per tile.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBlock *W,
-                                                                   const int8_t *__restrict__ occ, int nx, int ny,
-                                                                   int nz, float *ecache, uint4 *fcache, double *part,
-                                                                   long long timeout_ns, int *status, int *abort_flag)
+template <class Net>
+__global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const void *W, const int8_t *__restrict__ occ,
+                                                                   int nx, int ny, int nz, float *ecache,
+                                                                   uint4 *fcache, double *part, long long timeout_ns,
+                                                                   int *status, int *abort_flag)
 {
     constexpr int NWG = kEvalWG;
-    TcEval E = mlp_evaluator<NWG>(timeout_ns, status, abort_flag);
-    mlp_cta_setup<NWG>(E, W, nullptr, nullptr);
+    using M = typename Net::template Smem<NWG>;
+    typename Net::Eval E = mlp_evaluator<Net, NWG>(timeout_ns, status, abort_flag);
+    mlp_cta_setup<Net, NWG>(E, W, nullptr, nullptr);
     const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const long long N = 2LL * nx * ny * nz;
     const long long ntile = (N + kTcRows - 1) / kTcRows;
@@ -269,7 +326,7 @@ __global__ void __launch_bounds__(128 * kEvalWG) k_mlp_site_energy(const MlpBloc
         tl = nx_tl;
     }
     // CTA sum in thread order (the X tiles are free once both warpgroups are done)
-    double *red = (double *)(g_smem + MlpSmem<NWG>::X);
+    double *red = (double *)(g_smem + M::X);
     tc_fence_before();
     __syncthreads();
     red[tid] = sum;
@@ -327,22 +384,23 @@ __device__ __forceinline__ void tinfo_rank_store(int *tinfo, int tid, bool activ
 
 // The 4 mini-steps of one link-cell column (cells y0, z0 of the trial
 // sublattice; trials at x = 4 i + dx).
-template <int MODE, int SOFF>
-__device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &RD, const SweepLayout &SL, TcEval &E,
-                                           int y0, int z0, uint64_t sweep, float beta, double &accEd,
-                                           long long &accN)
+template <class Net, int MODE, int SOFF>
+__device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &RD, const SweepLayout &SL,
+                                           typename Net::Eval &E, int y0, int z0, uint64_t sweep, float beta,
+                                           double &accEd, long long &accN)
 {
     constexpr bool HAS_PAIR = MODE == kModeMlpPair;
     constexpr int sub = SOFF == -1 ? 0 : 1;
+    constexpr int NWG = Net::kSweepNWG, kThreads = 128 * NWG;
     const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
-    using M = MlpSmem<kSweepWG>;
+    using M = typename Net::template Smem<NWG>;
     const MlpGeo &geo = *(const MlpGeo *)(g_smem + M::GEO);
     int8_t *occ = RD.occ;
     // ---- Philox words of the column's trial sites: [link cell][word] ----
     uint32_t *wsm = (uint32_t *)(g_smem + SL.words);
     const int rowsite = ((sub * nz + z0) * ny + y0) * nx;
-    for (int i = tid; i < NLx; i += kSweepThreads) {
+    for (int i = tid; i < NLx; i += kThreads) {
         const U4 w = philox10(U4{((uint32_t)rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep,
                                  (uint32_t)(sweep >> 32)},
                               (uint32_t)P.seed, (uint32_t)(P.seed >> 32));
@@ -442,7 +500,7 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
             }
             while (n < ntile) {
                 tc_stage2(E);
-                const int nn = n + kSweepWG;
+                const int nn = n + NWG;
                 float eo_n = 0.f;
                 int site_n = 0;
                 if (nn < ntile) {
@@ -472,7 +530,7 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
                     const int base = (ti[15] + (tid >= 32 ? red_i[0] : 0)) * kOmega;
                     float dE = 0.f;
                     for (int e = 0; e < kOmega; ++e) dE += diff[base + e];
-                    if (HAS_PAIR) dE += pair_part<kSweepWG>(P, ti + 8, ti + 11, A, B);
+                    if (HAS_PAIR) dE += pair_part<NWG>(P, ti + 8, ti + 11, A, B);
                     const bool acc = metropolis<false>(dE, (uint32_t)ti[1], beta, nullptr, make_int2(0, 0));
                     ti[7] = acc ? 1 : 0;
                     if (acc) {
@@ -485,7 +543,7 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
             }
             __syncthreads();
             // -- caches over the accepted trials' Omega --
-            for (int row = tid; row < nrow_act; row += kSweepThreads)
+            for (int row = tid; row < nrow_act; row += kThreads)
                 if (tinfo[act[row / kOmega] * kTinfo + 7]) {
                     P.fcache[sites[row]] = feat[row];
                     P.ecache[sites[row]] = fval[row];
@@ -495,21 +553,22 @@ __device__ __forceinline__ void mlp_column(const SweepParams &P, const RepDesc &
     }
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_constant__ SweepParams P,
-                                                                const __grid_constant__ MlpGeo G)
+template <class Net, int MODE>
+__global__ void __launch_bounds__(128 * Net::kSweepNWG, 1) k_sweep_mlp(const __grid_constant__ SweepParams P,
+                                                                       const __grid_constant__ MlpGeo G)
 {
-    using M = MlpSmem<kSweepWG>;
-    TcEval E = mlp_evaluator<kSweepWG>(P.timeout_ns, P.status, P.abort_flag);
-    mlp_cta_setup<kSweepWG>(E, P.mlpw, MODE == kModeMlpPair ? P.D.df : nullptr, &G);
+    constexpr int NWG = Net::kSweepNWG, kThreads = 128 * NWG;
+    using M = typename Net::template Smem<NWG>;
+    typename Net::Eval E = mlp_evaluator<Net, NWG>(P.timeout_ns, P.status, P.abort_flag);
+    mlp_cta_setup<Net, NWG>(E, P.mlpw, MODE == kModeMlpPair ? P.D.df : nullptr, &G);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const RepDesc &RD = P.rep[0];
-    const SweepLayout SL = mlp_sweep_layout(RD.NLx, P.tpc, P.mlp_chunk);
+    const SweepLayout SL = mlp_sweep_layout(RD.NLx, P.tpc, P.mlp_chunk, M::END);
     double *slot_e = (double *)(g_smem + SL.slots);
     long long *slot_n = (long long *)(g_smem + SL.slots + 8 * P.tpc);
     double *red_e = (double *)(g_smem + M::RED);
     long long *red_n = (long long *)(g_smem + M::RED + 16);
-    for (int i = tid; i < P.tpc; i += kSweepThreads) {
+    for (int i = tid; i < P.tpc; i += kThreads) {
         slot_e[i] = 0.0;
         slot_n[i] = 0;
     }
@@ -542,9 +601,9 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_con
                 for (int l = l0; l < l1; ++l)
                     for (int j = j0; j < j1; ++j) {
                         if (sub == 0)
-                            mlp_column<MODE, -1>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
+                            mlp_column<Net, MODE, -1>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
                         else
-                            mlp_column<MODE, 0>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
+                            mlp_column<Net, MODE, 0>(P, RD, SL, E, 4 * j + dy, 4 * l + dz, sweep, beta, accEd, accN);
                     }
                 // the deciding threads are 0 .. kMlpChunk-1 (warps 0 and 1)
                 if (warp < 2) {
@@ -585,7 +644,7 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_con
             if (RD.n_acc) *RD.n_acc += sn;
         }
     }
-    tc_teardown(E, kSweepWG);
+    tc_teardown(E, NWG);
 }
 
 // ---------------------------------------------------------------------------
@@ -595,15 +654,15 @@ __global__ void __launch_bounds__(kSweepThreads, 1) k_sweep_mlp(const __grid_con
 // same evaluator and summation order as the sweep.  k_mlp_trace_apply
 // applies the accepted swaps.
 // ---------------------------------------------------------------------------
-template <bool HAS_PAIR>
+template <class Net, bool HAS_PAIR>
 __global__ void __launch_bounds__(128 * kEvalWG) k_mlp_trace_eval(const __grid_constant__ SweepParams P,
                                                                 const __grid_constant__ MlpGeo G, int k,
                                                                 float *dE_out, uint8_t *acc_out, int *swap_a,
                                                                 int *swap_b)
 {
-    using M = MlpSmem<kEvalWG>;
-    TcEval E = mlp_evaluator<kEvalWG>(P.timeout_ns, P.status, P.abort_flag);
-    mlp_cta_setup<kEvalWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
+    using M = typename Net::template Smem<kEvalWG>;
+    typename Net::Eval E = mlp_evaluator<Net, kEvalWG>(P.timeout_ns, P.status, P.abort_flag);
+    mlp_cta_setup<Net, kEvalWG>(E, P.mlpw, HAS_PAIR ? P.D.df : nullptr, &G);
     const int tid = threadIdx.x, r = tid & 127, wg = tid >> 7;
     const bool post = wg == 1;
     const RepDesc &RD = P.rep[0];
@@ -1180,21 +1239,66 @@ void fill_pair_D(const smc_model *m, int S, SweepParams &P)
 
 size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 
+bool is_mlpnet(const smc_model *m) { return m->kind == SMC_MLPNET_BF16; }
+
+// The MLPNet kernels' weight block: W0 padded to 32 inputs, W3 widened to FP32.
+void make_net_block(const smc_model *m, NetBlock &W)
+{
+    memset(&W, 0, sizeof W);
+    for (int j = 0; j < kNetHid; ++j)
+        for (int i = 0; i < 20; ++i) W.w0[j * 32 + i] = m->net_w0[j * 20 + i];
+    for (int i = 0; i < kNetHid * kNetHid; ++i) {
+        W.w1[i] = m->net_w1[i];
+        W.w2[i] = m->net_w2[i];
+    }
+    for (int j = 0; j < kNetHid; ++j) {
+        W.b0[j] = m->net_b0[j];
+        W.b1[j] = m->net_b1[j];
+        W.b2[j] = m->net_b2[j];
+        W.w3[j] = bf16_bits_to_float(m->net_w3[j]);
+    }
+    W.b3 = m->net_b3;
+}
+
+// Copies the model's weight block (MlpBlock or NetBlock) to dst (device).
+smc_status copy_weights(const smc_model *m, void *dst, cudaStream_t stream)
+{
+    static MlpBlock Wm;
+    static NetBlock Wn;
+    const void *src;
+    size_t n;
+    if (is_mlpnet(m)) {
+        make_net_block(m, Wn);
+        src = &Wn;
+        n = sizeof Wn;
+    } else {
+        make_mlp_block(m, Wm);
+        src = &Wm;
+        n = sizeof Wm;
+    }
+    const cudaError_t e = cudaMemcpyAsync(dst, src, n, cudaMemcpyHostToDevice, stream);
+    return e == cudaSuccess ? SMC_OK : cuda_fail(e, "cudaMemcpyAsync(network weights)");
+}
+
+constexpr size_t kWeightBytes = sizeof(MlpBlock) > sizeof(NetBlock) ? sizeof(MlpBlock) : sizeof(NetBlock);
+
 }  // namespace
 
 // E (+)= sum_i f(x_i); writes the per-site energies to ecache and the
 // features to fcache when non-NULL.
-// W is a device MlpBlock; part needs room for kTcMaxCtasPerSm CTAs per SM;
+// W is the device weight block of Net; part needs room for kTcMaxCtasPerSm CTAs per SM;
 // abort_flag is a device word that starts at zero.
-static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const MlpBlock *W, const int8_t *occ,
+template <class Net>
+static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const void *W, const int8_t *occ,
                                     float *ecache, uint4 *fcache, double *part, int *abort_flag, double *e,
                                     int accumulate, cudaStream_t stream)
 {
-    const size_t smem = MlpSmem<kEvalWG>::END;
-    cudaError_t err = cudaFuncSetAttribute(k_mlp_site_energy, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const size_t smem = Net::template Smem<kEvalWG>::END;
+    auto kern = k_mlp_site_energy<Net>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute(k_mlp_site_energy)");
     int per_sm = 0;
-    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_mlp_site_energy, 128 * kEvalWG, smem);
+    err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128 * kEvalWG, smem);
     if (err != cudaSuccess) return cuda_fail(err, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm > kTcMaxCtasPerSm) {
         // more resident CTAs than tensor-memory allocations: a CTA would wait in tcgen05.alloc
@@ -1205,7 +1309,7 @@ static smc_status mlp_energy_launch(Workspace *ws, const smc_lattice *lat, const
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
     const long long tiles = (N + kTcRows - 1) / kTcRows;
     const int grid = (int)std::max(1LL, std::min<long long>((long long)per_sm * ws->num_sms, tiles));
-    k_mlp_site_energy<<<grid, 128 * kEvalWG, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, fcache, part,
+    kern<<<grid, 128 * kEvalWG, smem, stream>>>(W, occ, lat->nx, lat->ny, lat->nz, ecache, fcache, part,
                                                            debug_timeout_ns(), ws->status, abort_flag);
     err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_mlp_site_energy");
@@ -1223,18 +1327,16 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
-    // scratch: [pair counts | abort word | MlpBlock | CTA partial sums]
+    // scratch: [pair counts | abort word | weight block | CTA partial sums]
     const size_t off_abort = round16(sizeof(unsigned long long) * kMaxShells * 64);
     const size_t off_w = off_abort + 16;
-    const size_t off_part = round16(off_w + sizeof(MlpBlock));
+    const size_t off_part = round16(off_w + kWeightBytes);
     const size_t need = off_part + sizeof(double) * kTcMaxCtasPerSm * (size_t)std::max(ws->num_sms, 1);
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, need, &st);
     if (!scr) return st;
-    static MlpBlock W;
-    make_mlp_block(m, W);
-    cudaError_t err = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaMemcpyAsync(MLP weights)");
-    err = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
+    st = copy_weights(m, scr + off_w, stream);
+    if (st != SMC_OK) return st;
+    cudaError_t err = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync(abort word)");
     int accumulate = 0;
     if (m->kind == SMC_PAIR_F32_MLP_BF16) {
@@ -1245,8 +1347,11 @@ smc_status launch_mlp_energy(const smc_lattice *lat, const smc_model *m, const i
         if (st != SMC_OK) return st;
         accumulate = 1;
     }
-    return mlp_energy_launch(ws, lat, (const MlpBlock *)(scr + off_w), occ, nullptr, nullptr, (double *)(scr + off_part),
-                             (int *)(scr + off_abort), e, accumulate, stream);
+    if (is_mlpnet(m))
+        return mlp_energy_launch<NetRelu96>(ws, lat, scr + off_w, occ, nullptr, nullptr, (double *)(scr + off_part),
+                                            (int *)(scr + off_abort), e, accumulate, stream);
+    return mlp_energy_launch<NetSilu64>(ws, lat, scr + off_w, occ, nullptr, nullptr, (double *)(scr + off_part),
+                                        (int *)(scr + off_abort), e, accumulate, stream);
 }
 
 namespace {
@@ -1258,8 +1363,8 @@ struct MlpPlan {
 // One CTA per tile at a time; all CTAs resident (cooperative launch), at most
 // as many per SM as tensor memory holds (kSweepWG x kTcCols columns each)
 // when the kernel uses it.  `base`: end of the kernel's fixed shared memory.
-smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kernel, uint32_t base, bool tmem,
-                         MlpPlan &pl)
+smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kernel, uint32_t base, int threads,
+                         int tmem_cols, MlpPlan &pl)
 {
     const Tuning tu = current_tuning();
     cudaFuncAttributes fa;
@@ -1276,9 +1381,9 @@ smc_status make_mlp_plan(Workspace *ws, const smc_lattice *lat, const void *kern
         const size_t smem = mlp_sweep_layout(NLx, tpc_guess, pl.chunk, base).end;
         if (smem > dyn_max) break;
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kSweepThreads, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
         if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        if (tmem) per_sm = std::min(per_sm, 512 / (kSweepWG * (int)kTcCols));  // tensor-memory columns
+        if (tmem_cols > 0) per_sm = std::min(per_sm, 512 / tmem_cols);  // tensor-memory columns
         if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
         if (per_sm < 1) break;
         // the CTA with the most tiles sets the pace: fill the GPU, then use as
@@ -1310,10 +1415,15 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
-    const bool has_pair = m->kind == SMC_PAIR_F32_MLP_BF16;
-    const void *kernel = has_pair ? (const void *)k_sweep_mlp<kModeMlpPair> : (const void *)k_sweep_mlp<kModeMlp>;
+    const bool has_pair = m->kind == SMC_PAIR_F32_MLP_BF16, net = is_mlpnet(m);
+    const void *kernel = net ? (const void *)k_sweep_mlp<NetRelu96, kModeMlp>
+                             : (has_pair ? (const void *)k_sweep_mlp<NetSilu64, kModeMlpPair>
+                                         : (const void *)k_sweep_mlp<NetSilu64, kModeMlp>);
+    const int threads = 128 * (net ? NetRelu96::kSweepNWG : NetSilu64::kSweepNWG);
     MlpPlan pl;
-    st = make_mlp_plan(ws, lat, kernel, MlpSmem<kSweepWG>::END, true, pl);
+    st = net ? make_mlp_plan(ws, lat, kernel, NetSmem<NetRelu96::kSweepNWG>::END, threads,
+                             NetRelu96::kSweepNWG * (int)kNetCols, pl)
+             : make_mlp_plan(ws, lat, kernel, MlpSmem<kSweepWG>::END, threads, kSweepWG * (int)kTcCols, pl);
     if (st != SMC_OK) return st;
     static MlpGeo G;
     if (!build_mlp_geo(G)) {
@@ -1354,12 +1464,12 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ % 16 == 0);
     if (has_pair) fill_pair_D(m, P.S, P);
 
-    // workspace: [flags | part_e | part_n | ticket, abort | MlpBlock | energy parts | E cache | F cache]
+    // workspace: [flags | part_e | part_n | ticket, abort | weights | energy parts | E cache | F cache]
     const size_t nt = (size_t)P.ntiles;
     const size_t N = 2ull * lat->nx * lat->ny * lat->nz;
     const size_t off_pe = round16(nt * 4), off_pn = off_pe + nt * 8, off_misc = off_pn + nt * 8;
     const size_t off_w = round16(off_misc + 16);
-    const size_t off_parts = round16(off_w + sizeof(MlpBlock));
+    const size_t off_parts = round16(off_w + kWeightBytes);
     const size_t off_cache =
         round16(off_parts + sizeof(double) * kTcMaxCtasPerSm * (size_t)std::max(ws->num_sms, 1));
     const size_t off_fcache = round16(off_cache + N * 4);
@@ -1371,17 +1481,17 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.ticket = (unsigned *)(scr + off_misc);
     P.abort_flag = (int *)(scr + off_misc + 4);
     P.status = ws->status;
-    P.mlpw = (const MlpBlock *)(scr + off_w);
+    P.mlpw = scr + off_w;
     P.ecache = (float *)(scr + off_cache);
     P.fcache = (uint4 *)(scr + off_fcache);
-    static MlpBlock W;
-    make_mlp_block(m, W);
-    cudaError_t e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
-    e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
+    st = copy_weights(m, scr + off_w, stream);
+    if (st != SMC_OK) return st;
+    cudaError_t e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
-    st = mlp_energy_launch(ws, lat, P.mlpw, occ, P.ecache, P.fcache, (double *)(scr + off_parts), P.abort_flag,
-                           nullptr, 0, stream);
+    st = net ? mlp_energy_launch<NetRelu96>(ws, lat, P.mlpw, occ, P.ecache, P.fcache, (double *)(scr + off_parts),
+                                            P.abort_flag, nullptr, 0, stream)
+             : mlp_energy_launch<NetSilu64>(ws, lat, P.mlpw, occ, P.ecache, P.fcache, (double *)(scr + off_parts),
+                                            P.abort_flag, nullptr, 0, stream);
     if (st != SMC_OK) return st;
 
     bool constant = true;
@@ -1397,7 +1507,7 @@ smc_status launch_mlp_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
         e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
         void *args[] = {(void *)&P, (void *)&G};
-        e = cudaLaunchCooperativeKernel(kernel, dim3(pl.grid), dim3(kSweepThreads), args, pl.smem, stream);
+        e = cudaLaunchCooperativeKernel(kernel, dim3(pl.grid), dim3(threads), args, pl.smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(MLP sweep)");
     }
     return SMC_OK;
@@ -1445,19 +1555,19 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
     const int ntr = d.NLx * d.NLy * d.NLz;
     const size_t off_abort = round16((size_t)ntr * 8);
     const size_t off_w = off_abort + 16;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_w + sizeof(MlpBlock), &st);
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_w + kWeightBytes, &st);
     if (!scr) return st;
     int *swap_a = (int *)scr, *swap_b = swap_a + ntr;
     P.abort_flag = (int *)(scr + off_abort);
-    P.mlpw = (const MlpBlock *)(scr + off_w);
-    static MlpBlock W;
-    make_mlp_block(m, W);
-    cudaError_t e = cudaMemcpyAsync(scr + off_w, &W, sizeof W, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(MLP weights)");
-    e = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
+    P.mlpw = scr + off_w;
+    st = copy_weights(m, scr + off_w, stream);
+    if (st != SMC_OK) return st;
+    cudaError_t e = cudaMemsetAsync(scr + off_abort, 0, 16, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(abort word)");
-    const size_t smem = MlpSmem<kEvalWG>::END + 2 * kTcRows * sizeof(float);
-    auto kern = has_pair ? k_mlp_trace_eval<true> : k_mlp_trace_eval<false>;
+    const bool net = is_mlpnet(m);
+    const size_t smem = (net ? NetSmem<kEvalWG>::END : MlpSmem<kEvalWG>::END) + 2 * kTcRows * sizeof(float);
+    auto kern = net ? k_mlp_trace_eval<NetRelu96, false>
+                    : (has_pair ? k_mlp_trace_eval<NetSilu64, true> : k_mlp_trace_eval<NetSilu64, false>);
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(k_mlp_trace_eval)");
     int per_sm = 0;

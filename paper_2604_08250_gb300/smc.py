@@ -16,7 +16,7 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libsmc.so")
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_UNSUPPORTED, SMC_ERR_CUDA, SMC_ERR_TIMEOUT, SMC_ERR_STATE = 0, -1, -2, -3, -4, -5
-PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16, QSRO_F32 = 0, 1, 2, 3, 4
+PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16, QSRO_F32, MLPNET_BF16 = 0, 1, 2, 3, 4, 5
 DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH = 1, 2
 MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 
@@ -44,7 +44,11 @@ class _Model(C.Structure):
                 ("mlp_w3", C.POINTER(C.c_uint16)),
                 ("mlp_b1", C.POINTER(C.c_float)), ("mlp_b2", C.POINTER(C.c_float)),
                 ("mlp_b3", C.c_float),
-                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_float)]
+                ("qsro_w", C.POINTER(C.c_float)), ("qsro_c", C.c_float),
+                ("net_w0", C.POINTER(C.c_uint16)), ("net_w1", C.POINTER(C.c_uint16)),
+                ("net_w2", C.POINTER(C.c_uint16)), ("net_w3", C.POINTER(C.c_uint16)),
+                ("net_b0", C.POINTER(C.c_float)), ("net_b1", C.POINTER(C.c_float)),
+                ("net_b2", C.POINTER(C.c_float)), ("net_b3", C.c_float)]
 
 
 class _Tuning(C.Structure):
@@ -133,7 +137,7 @@ class Model:
     qSRO: v = V_m^{pp'} (float32, symmetric), qsro_w = W_m^p [nshells][S]
     (float32), qsro_c = C."""
 
-    def __init__(self, kind, nshells=0, v=None, unit_ev=1e-4, mlp=None, qsro_w=None, qsro_c=0.0):
+    def __init__(self, kind, nshells=0, v=None, unit_ev=1e-4, mlp=None, qsro_w=None, qsro_c=0.0, net=None):
         self.kind, self.nshells, self.unit_ev = int(kind), int(nshells), float(unit_ev)
         c = _Model()
         c.kind, c.nshells, c.unit_ev = self.kind, self.nshells, self.unit_ev
@@ -147,6 +151,15 @@ class Model:
             self.qsro_w = np.ascontiguousarray(qsro_w, dtype=np.float32)
             c.qsro_w = self.qsro_w.ctypes.data_as(C.POINTER(C.c_float))
             c.qsro_c = float(qsro_c)
+        if kind == MLPNET_BF16:  # net: w0..w3 BF16 bit patterns, b0..b2 FP32, b3
+            self.net = {k: np.ascontiguousarray(net[k], dtype=np.uint16).reshape(-1) for k in ("w0", "w1", "w2", "w3")}
+            for k in ("b0", "b1", "b2"):
+                self.net[k] = np.ascontiguousarray(net[k], dtype=np.float32).reshape(-1)
+            for k in ("w0", "w1", "w2", "w3"):
+                setattr(c, "net_" + k, self.net[k].ctypes.data_as(C.POINTER(C.c_uint16)))
+            for k in ("b0", "b1", "b2"):
+                setattr(c, "net_" + k, self.net[k].ctypes.data_as(C.POINTER(C.c_float)))
+            c.net_b3 = float(net["b3"])
         if kind in (MLP_BF16, PAIR_F32_MLP_BF16):
             self.mlp = {k: np.ascontiguousarray(mlp[k], dtype=np.uint16).reshape(-1) for k in ("w1", "w2", "w3")}
             for k in ("b1", "b2"):

@@ -208,3 +208,45 @@ def mlp_grad_abs_terms(X, w):
     d1 = 1.1 * (d2 @ w2)
     return np.concatenate([(d1.T @ X).reshape(-1), d1.sum(0), (d2.T @ a1).reshape(-1), d2.sum(0), a2.sum(0),
                            [float(X.shape[0])]])
+
+
+def _bf16_spacing_near_boundary(a, da):
+    """Two BF16 spacings where a value lies within 2 da of a BF16 rounding
+    boundary (where the GPU's FP32 value may round the other way), else 0."""
+    mag = np.maximum(np.abs(a), 1e-300)
+    spacing = 2.0 ** (np.floor(np.log2(mag)) - 7)
+    frac = np.abs(a) / spacing
+    dist = np.abs(frac - np.floor(frac) - 0.5) * spacing
+    return np.where(dist <= 2 * da, 2 * spacing, 0.0)
+
+
+def mlpnet_bf16_emulation(X, w):
+    """MLPNet's BF16 evaluation order in FP64: exact layer products, ReLU, the
+    activations of the first two layers rounded to BF16 (the operands of the
+    next products), FP32 output layer.  Returns (f_emu, bound) where bound
+    limits |f_GPU - f_emu| per row: FP32 accumulation (K 2^-22 of the
+    magnitudes), one BF16 step where an activation lies within its own error
+    of a rounding boundary, and the error itself where ReLU's kink is that
+    close."""
+    def gam(k):
+        return k * 2.0 ** -22
+
+    def act(z, dz):
+        a = np.maximum(z, 0.0)
+        h = bf16_round(a)
+        dh = _bf16_spacing_near_boundary(a, dz) + np.where(np.abs(z) <= dz, 2 * dz, 0.0)
+        return h, dh
+
+    w0, b0, w1, b1, w2, b2, w3, b3 = (w[k] for k in ("w0", "b0", "w1", "b1", "w2", "b2", "w3", "b3"))
+    z0 = X @ w0.T + b0
+    dz0 = gam(32) * (np.abs(X) @ np.abs(w0).T + np.abs(b0))
+    h1, dh1 = act(z0, dz0)
+    z1 = h1 @ w1.T + b1
+    dz1 = dh1 @ np.abs(w1).T + gam(112) * (np.abs(b1) + (np.abs(h1) + dh1) @ np.abs(w1).T)
+    h2, dh2 = act(z1, dz1)
+    z2 = h2 @ w2.T + b2
+    dz2 = dh2 @ np.abs(w2).T + gam(112) * (np.abs(b2) + (np.abs(h2) + dh2) @ np.abs(w2).T)
+    h3 = np.maximum(z2, 0.0)
+    f = h3 @ w3 + b3
+    bound = (dz2 + 2.0 ** -23 * h3) @ np.abs(w3) + gam(98) * (abs(b3) + (h3 + dz2) @ np.abs(w3))
+    return f, bound

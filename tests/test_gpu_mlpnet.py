@@ -1,0 +1,177 @@
+"""GPU parity of MLPNet at the paper's shape (Sec. IV-B: 20 -> 96 -> 96 ->
+96 -> 1, ReLU; BF16 weights and activations on the tensor cores, FP32
+accumulation) against the FP64 oracle, through the C ABI.
+
+Every trial's dE must lie within the tight bound of an FP64 emulation of the
+BF16 evaluation order (tests/helpers.mlpnet_bf16_emulation), and decide as
+the FP64 oracle except where the acceptance threshold lies between the GPU's
+and the oracle's values (the run then follows the GPU).  The sweep kernel
+(cached pre-swap energies and features) must equal its traced mini-steps
+(recomputed energies) bit for bit.  Statistics go to
+$SMC_STATS_DIR/mlpnet_dE_errors.json when that is set."""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_08250_gb300 import inputs
+from tests import helpers
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K_B = inputs.K_B_EV
+_STATS = {}
+
+
+@pytest.fixture(scope="module")
+def smc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_08250_gb300 import build, smc as s
+    build.build()
+    s.lib()
+    yield s
+    d = os.environ.get("SMC_STATS_DIR")
+    if d and _STATS:
+        os.makedirs(d, exist_ok=True)
+        with open(os.path.join(d, "mlpnet_dE_errors.json"), "w") as f:
+            json.dump(_STATS, f, indent=1, sort_keys=True)
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def models(smc, seed=4):
+    net = inputs.mlpnet_weights(seed)
+    w = {k: oracle._widen(net[k]) for k in ("w0", "w1", "w2", "w3", "b0", "b1", "b2")}
+    w["w0"] = w["w0"].reshape(96, 20)
+    w["w1"] = w["w1"].reshape(96, 96)
+    w["w2"] = w["w2"].reshape(96, 96)
+    w["b3"] = float(net["b3"])
+    return smc.Model(smc.MLPNET_BF16, net=net), oracle.Model(oracle.MLPNET, net=net), w
+
+
+def start(smc, dims, S, seed):
+    N = 2 * dims[0] * dims[1] * dims[2]
+    counts = inputs.dirichlet_counts(N, S, 4)
+    lat = smc.Lattice(*dims, S)
+    occ = torch.empty(N, dtype=torch.int8, device=dev())
+    smc.init_lattice(lat, counts, seed, occ)
+    return lat, occ, counts
+
+
+def emulated(occ_h, dims, a, b, w, dE64):
+    """Per trial: dE of the BF16 emulation and the bound on |dE_GPU - it|."""
+    nt = len(a)
+    oms = [helpers.omega(int(a[t]), int(b[t]), dims) for t in range(nt)]
+    Xpre = helpers.mlp_features(occ_h, dims, np.concatenate(oms))
+    Xpost = np.concatenate([helpers.mlp_features(occ_h, dims, oms[t], swap=(int(a[t]), int(b[t])))
+                            for t in range(nt)])
+    g_pre, b_pre = helpers.mlpnet_bf16_emulation(Xpre, w)
+    g_post, b_post = helpers.mlpnet_bf16_emulation(Xpost, w)
+
+    def per(v):
+        return v.reshape(nt, -1).sum(axis=1)
+
+    sum_err = 80 * 2.0 ** -24 * per(np.abs(g_pre) + np.abs(g_post))
+    return per(g_post - g_pre), (per(b_pre + b_post) + sum_err) * 1.05 + 1e-12
+
+
+def threshold(seed, sweep, a, kT):
+    w = oracle.philox4x32_10([a >> 2, 0, sweep & 0xFFFFFFFF, sweep >> 32], [seed & 0xFFFFFFFF, seed >> 32])[a & 3]
+    return -kT * math.log(((int(w) & ((1 << 29) - 1)) + 0.5) * 2.0 ** -29)
+
+
+@pytest.mark.parametrize("dims,T,ks", [((8, 8, 8), 800.0, range(128)), ((16, 8, 12), 500.0, range(0, 128, 5)),
+                                       ((64, 64, 64), 800.0, [0])])
+def test_lockstep_against_oracle(smc, dims, T, ks):
+    S, seed, kT = 5, 11, K_B * T
+    gm, om, w = models(smc)
+    lat, occ, _ = start(smc, dims, S, seed)
+    olat = oracle.Lattice(*dims, S)
+    nt = lat.nsites // 128
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    errs, emus, flips, n = [], [], 0, 0
+    for k in ks:
+        occ_h = occ.cpu().numpy().copy()
+        smc.ministep_trace(lat, gm, occ, seed, 0, k, kT, dE, acc)
+        smc.check()
+        d_o, a_o, a, b = oracle.ministep_trace(olat, om, occ_h.copy(), seed, 0, k, kT)
+        d_g = dE.cpu().numpy().astype(np.float64)
+        a_g = acc.cpu().numpy().astype(bool)
+        emu, tight = emulated(occ_h, dims, a, b, w, d_o)
+        assert np.all(np.abs(d_g - emu) <= tight), (k, float(np.abs(d_g - emu).max()))
+        err = d_g - d_o
+        for t in np.flatnonzero(a_g != a_o):
+            thr = threshold(seed, 0, int(a[t]), kT)
+            lo, hi = sorted((d_g[t], d_o[t]))
+            assert lo - 1e-6 * kT <= thr <= hi + 1e-6 * kT, (k, t, d_g[t], d_o[t], thr)
+            flips += 1
+        errs.append(err)
+        emus.append(d_g - emu)
+        n += nt
+    errs, emus = np.concatenate(errs), np.concatenate(emus)
+    _STATS[f"lockstep_{dims[0]}x{dims[1]}x{dims[2]}_T{int(T)}"] = {
+        "trials": int(n), "rms_err_vs_fp64_eV": float(np.sqrt(np.mean(errs ** 2))),
+        "max_abs_err_vs_fp64_eV": float(np.abs(errs).max()),
+        "rms_err_vs_bf16_emulation_eV": float(np.sqrt(np.mean(emus ** 2))), "decision_flips": int(flips)}
+    # a flip is legitimate only across the threshold (checked above); how many
+    # occur depends on the BF16 error against kT, and is recorded
+    assert np.sqrt(np.mean(emus ** 2)) <= 0.05 * np.sqrt(np.mean(errs ** 2))
+
+
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 8, 12), (32, 32, 32), (300, 12, 8)])
+def test_sweep_equals_trace(smc, dims):
+    S, seed, kT = 5, 21, K_B * 800.0
+    gm, _, _ = models(smc, seed=6)
+    lat, occ, counts = start(smc, dims, S, seed)
+    occ2 = occ.clone()
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.sweep(lat, gm, occ, seed, 5, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    smc.check()
+    nt = lat.nsites // 128
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    tot, cnt, mag = 0.0, 0, 0.0
+    for t in range(2):
+        for k in range(128):
+            smc.ministep_trace(lat, gm, occ2, seed, 5 + t, k, kT, dE, acc)
+            d = dE.cpu().numpy().astype(np.float64)
+            a = acc.cpu().numpy().astype(bool)
+            tot += d[a].sum()
+            mag += np.abs(d[a]).sum()
+            cnt += int(a.sum())
+    smc.check()
+    assert torch.equal(occ, occ2)
+    assert int(n_acc.item()) == cnt
+    assert abs(e_acc.item() - tot) <= 1e-12 * mag + 1e-15
+    assert np.array_equal(np.bincount(occ.cpu().numpy(), minlength=S), counts)
+
+
+def test_energy_against_emulation_and_oracle(smc):
+    S, dims = 5, (16, 8, 12)
+    gm, om, w = models(smc)
+    lat, occ, _ = start(smc, dims, S, 3)
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, gm, occ, e)
+    smc.check()
+    occ_h = occ.cpu().numpy()
+    f, bound = helpers.mlpnet_bf16_emulation(helpers.mlp_features(occ_h, dims, np.arange(lat.nsites)), w)
+    assert abs(float(e.item()) - f.sum()) <= bound.sum() + 1e-9 * np.abs(f).sum()
+    e64 = oracle.total_energy(oracle.Lattice(*dims, S), om, occ_h)
+    assert abs(float(e.item()) - e64) <= 0.02 * abs(e64)  # BF16 activations
+
+
+def test_gradient_is_not_offered(smc):
+    gm, _, _ = models(smc)
+    lat, occ, _ = start(smc, (8, 8, 8), 5, 1)
+    assert smc.grad_size(lat, gm) == -1
+    with pytest.raises(smc.SMCError):
+        smc.energy_grad(lat, gm, occ, torch.zeros(8, dtype=torch.float32, device=dev()))
