@@ -33,6 +33,10 @@ from paper_2604_08250_gb300 import inputs, replicas  # noqa: E402
 METRIC = "MC swap attempts/s on 1 GB300 (% HBM roofline); batched & grad vs plain sweep"
 BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pair model)
 # MLP 20-64-64-1: dense products per site evaluation, forward only and forward + backward
+# MLPNet (20 -> 96 -> 96 -> 96 -> 1): 2 (20 96 + 96 96 + 96 96 + 96) FLOP per
+# site evaluation, 40 post-swap evaluations per attempt (pre-swap energies cached)
+NET_FLOP_PER_SITE = 2 * (20 * 96 + 96 * 96 + 96 * 96 + 96)
+NET_FLOP_PER_ATTEMPT = 40 * NET_FLOP_PER_SITE
 QSRO_SEED, QSRO_SHELLS = 7, 2  # qSRO workload parameters
 # zone rows a qSRO trial evaluates (a, b and the sites that see exactly one
 # of them within the model's shells), counted from the BCC geometry
@@ -195,6 +199,8 @@ def main():
                     help="measure tanh.approx / ex2.approx throughput (the MLP path's SFU ceiling)")
     ap.add_argument("--profile-mlp", type=int, default=0,
                     help="run the MLP workload (800 K) on a 256 x n x n box once, for ncu captures")
+    ap.add_argument("--profile-mlpnet", type=int, default=0,
+                    help="as --profile-mlp, with MLPNet at the paper's shape")
     ap.add_argument("--profile-qsro", type=int, default=0,
                     help="run the qSRO workload (800 K) on an N^3 box once, for ncu captures")
     args = ap.parse_args()
@@ -203,6 +209,9 @@ def main():
         return
     if args.profile_mlp:
         profile_mlp(args.profile_mlp, args.profile_sweeps)
+        return
+    if args.profile_mlpnet:
+        profile_mlp(args.profile_mlpnet, args.profile_sweeps, net=True)
         return
     if args.profile_qsro:
         profile_qsro(args.profile_qsro, args.profile_sweeps)
@@ -407,11 +416,12 @@ def profile_qsro(n: int, nsweeps: int):
     print(json.dumps({"profile_qsro": n, "sweeps": nsweeps, "ok": True}))
 
 
-def profile_mlp(n: int, nsweeps: int):
+def profile_mlp(n: int, nsweeps: int, net: bool = False):
     """One MLP sweep launch (nsweeps sweeps; the energy-cache kernel runs
     first) and one energy evaluation on a 256 x n x n box with the MLP
     workload's composition, weights and temperature, for ncu captures
-    (-k regex:k_sweep_mlp or regex:k_mlp_site_energy)."""
+    (-k regex:k_sweep_mlp or regex:k_mlp_site_energy); net: MLPNet at the
+    paper's shape instead of the 64-wide network."""
     import torch
     from paper_2604_08250_gb300 import build as _b
     from paper_2604_08250_gb300 import smc
@@ -422,12 +432,15 @@ def profile_mlp(n: int, nsweeps: int):
     lat = smc.Lattice(256, n, n, S)
     occ = torch.empty(lat.nsites, dtype=torch.int8, device="cuda")
     smc.init_lattice(lat, inputs.dirichlet_counts(lat.nsites, S, c4["comp_seed"]), c4["mc_seed"], occ)
-    model = smc.Model(smc.MLP_BF16, mlp=inputs.mlp_weights(c4["mlp_seed"]))
+    if net:
+        model = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(c4["mlp_seed"]))
+    else:
+        model = smc.Model(smc.MLP_BF16, mlp=inputs.mlp_weights(c4["mlp_seed"]))
     smc.sweep(lat, model, occ, c4["mc_seed"], 0, nsweeps, inputs.K_B_EV * c4["T"])
     e = torch.zeros(1, dtype=torch.float64, device="cuda")
     smc.energy(lat, model, occ, e)
     smc.check()
-    print(json.dumps({"profile_mlp": [256, n, n], "sweeps": nsweeps, "ok": True}))
+    print(json.dumps({"profile_mlp": [256, n, n], "net": net, "sweeps": nsweeps, "ok": True}))
 
 
 def kernel_traffic(name: str):
@@ -545,6 +558,20 @@ def run_extras(smc, torch, dev, pk):
     e4 = torch.zeros(1, dtype=torch.float64, device=dev)
     ems = timed(lambda: smc.energy(lat4, mlp_model, occ4, e4), reps=3)
     out["mlp_energy_256"] = {"ms": ems, "achieved_tflops": lat4.nsites * MLP_FLOP_PER_SITE_FWD / (ems * 1e-3) / 1e12}
+    # MLPNet at the paper's shape on the same lattice and temperature
+    net_model = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(c4["mlp_seed"]))
+    n_accn = torch.zeros(1, dtype=torch.int64, device=dev)
+    msn = timed(lambda: smc.sweep(lat4, net_model, occ4, c4["mc_seed"], 0, nsw4, kT4, n_acc=n_accn), reps=1)
+    attn = lat4.nsites * nsw4 / (msn * 1e-3)
+    tfn = attn * NET_FLOP_PER_ATTEMPT / 1e12
+    out["mlpnet_256"] = {"cells": [n4] * 3, "sweeps_per_launch": nsw4, "ms_per_sweep": msn / nsw4,
+                         "attempts_per_s": attn, "accept_rate": float(n_accn.item()) / (2 * lat4.nsites * nsw4),
+                         "achieved_tflops": tfn, "frac_of_measured_bf16_sustained": tfn / pk["bf16_tflops_sustained"],
+                         "flop_per_attempt": NET_FLOP_PER_ATTEMPT}
+    en = torch.zeros(1, dtype=torch.float64, device=dev)
+    emsn = timed(lambda: smc.energy(lat4, net_model, occ4, en), reps=3)
+    out["mlpnet_energy_256"] = {"ms": emsn,
+                                "achieved_tflops": lat4.nsites * NET_FLOP_PER_SITE / (emsn * 1e-3) / 1e12}
     del occ4
     # qSRO site energies (Eq. quadratic_local_SRO) on the cached-feature sweep, 256^3 at 800 K
     latq, occq, qm, kTq = qsro_setup(smc, 256, dev)
