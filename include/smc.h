@@ -43,6 +43,11 @@
  *   is a fixed function of its features (the same bits wherever it is
  *   evaluated), so the MLP chains sample the Boltzmann distribution of that
  *   BF16 energy exactly; its departure from FP64 is what the tests report.
+ *   MLPNet (SMC_MLPNET_BF16, the paper's shape): the same features,
+ *   h1 = relu(W0 x + b0), h2 = relu(W1 h1 + b1), h3 = relu(W2 h2 + b2),
+ *   f = W3 h3 + b3, 96 units per layer, with the same BF16 / FP32 split (the
+ *   activations of the first two layers rounded to BF16); it runs everywhere
+ *   the MLP does except smc_energy_grad.
  *   MLP sweeps and traces need every axis a multiple of 4 cells and >= 8,
  *   nx <= 1024, and occ 4-byte aligned.
  *
@@ -221,7 +226,8 @@ smc_status smc_energy(const smc_lattice *lat, const smc_model *model, const int8
  * p != q, n_m^{pp}/2 for p = q), then for MLP models the 5569 MLP parameters
  * W1, b1, W2, b2, W3, b3.  qSRO models: [V_m^{pq}, p <= q]
  * ((n_m^{pq} + n_m^{qp}) / z_m for p != q, n_m^{pp} / z_m for p = q), then
- * [W_m^p] (Q_m^p / z_m^2), then C (N).
+ * [W_m^p] (Q_m^p / z_m^2), then C (N).  MLPNet models: not offered
+ * (smc_grad_size returns -1, smc_energy_grad SMC_ERR_UNSUPPORTED).
  *   grad   device float [smc_grad_size(lat, model)]. */
 int64_t smc_grad_size(const smc_lattice *lat, const smc_model *model);
 smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const int8_t *occ,
