@@ -99,6 +99,24 @@ def lib():
                                         C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32, C.c_double,
                                         P(C.c_double), P(C.c_int64)]
         L.orc_slab_ministep.restype = C.c_int64
+        L.orc_fcc_nsites.argtypes = [P(_Lat)]
+        L.orc_fcc_nsites.restype = C.c_int64
+        L.orc_fcc_neighbor.argtypes = [P(_Lat), C.c_int64, C.c_int, C.c_int, C.c_int]
+        L.orc_fcc_neighbor.restype = C.c_int64
+        L.orc_fcc_shell_vectors.argtypes = [C.c_int, P(C.c_int)]
+        L.orc_fcc_schedule.argtypes = [P(_Lat), P(C.c_int32)]
+        L.orc_fcc_total_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+        L.orc_fcc_total_energy.restype = C.c_double
+        L.orc_fcc_total_energy_i64.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+        L.orc_fcc_total_energy_i64.restype = C.c_int64
+        L.orc_fcc_delta_e.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64, C.c_int64]
+        L.orc_fcc_delta_e.restype = C.c_double
+        L.orc_fcc_sweep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
+                                    P(C.c_double), P(C.c_double), P(C.c_int64)]
+        L.orc_fcc_ministep_trace.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64,
+                                             C.c_int32, C.c_double, P(C.c_double), P(C.c_uint8), P(C.c_int64),
+                                             P(C.c_int64)]
+        L.orc_fcc_ministep_trace.restype = C.c_int64
         L.orc_grad_size.argtypes = [P(_Lat), P(_Model)]
         L.orc_grad_size.restype = C.c_int64
         L.orc_energy_grad.argtypes = [P(_Lat), P(_Model), P(C.c_int8), P(C.c_double)]
@@ -300,6 +318,74 @@ def slab_ministep(lat, model, occ_loc, x0, w, g, seed, sweep_index, k, kT, repli
     if nt < 0:
         raise ValueError("orc_slab_ministep rejected its arguments")
     return e.value, n.value, int(nt)
+
+
+# ---- FCC lattice (pair models): a Lattice(nx, ny, nz, S) read as nx x ny x nz
+# cubic cells of 4 sites; N = 4 nx ny nz ----
+def fcc_nsites(lat) -> int:
+    return 4 * lat.nx * lat.ny * lat.nz
+
+
+def fcc_shell_vectors(shell: int) -> np.ndarray:
+    buf = np.zeros((24, 3), dtype=np.int32)
+    n = lib().orc_fcc_shell_vectors(shell, _ptr(buf, C.c_int))
+    return buf[:n].copy()
+
+
+def fcc_neighbor(lat, s: int, v) -> int:
+    return int(lib().orc_fcc_neighbor(C.byref(lat._c), int(s), int(v[0]), int(v[1]), int(v[2])))
+
+
+def fcc_schedule(lat):
+    L = np.zeros(3, dtype=np.int32)
+    nA = lib().orc_fcc_schedule(C.byref(lat._c), _ptr(L, C.c_int32))
+    return int(nA), tuple(int(x) for x in L)
+
+
+def fcc_init_lattice(lat, counts, seed: int, replica: int = 0) -> np.ndarray:
+    """The composition-conserving start state: the site order of the BCC init
+    over the same N = 4 nx ny nz site ids."""
+    return init_lattice(Lattice(2 * lat.nx, lat.ny, lat.nz, lat.nspecies), counts, seed, replica)
+
+
+def fcc_total_energy(lat, model, occ) -> float:
+    return lib().orc_fcc_total_energy(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ), C.c_int8))
+
+
+def fcc_total_energy_i64(lat, model, occ) -> int:
+    return int(lib().orc_fcc_total_energy_i64(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ), C.c_int8)))
+
+
+def fcc_delta_e(lat, model, occ, a, b) -> float:
+    return lib().orc_fcc_delta_e(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ), C.c_int8), int(a), int(b))
+
+
+def fcc_sweep(lat, model, occ, seed, sweep0, nsweeps, kT, replica=0):
+    kTa = np.ascontiguousarray(np.broadcast_to(np.asarray(kT, dtype=np.float64), (nsweeps,)))
+    e = C.c_double(0.0)
+    n = C.c_int64(0)
+    rc = lib().orc_fcc_sweep(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ), C.c_int8), C.c_uint64(seed),
+                             C.c_uint32(replica), C.c_uint64(sweep0), int(nsweeps), _ptr(kTa, C.c_double),
+                             C.byref(e), C.byref(n))
+    if rc != 0:
+        raise ValueError("orc_fcc_sweep rejected its arguments")
+    return e.value, n.value
+
+
+def fcc_ministep_trace(lat, model, occ, seed, sweep_index, k, kT, replica=0):
+    nA, _ = fcc_schedule(lat)
+    nt = fcc_nsites(lat) // nA
+    dE = np.zeros(nt, dtype=np.float64)
+    acc = np.zeros(nt, dtype=np.uint8)
+    a = np.zeros(nt, dtype=np.int64)
+    b = np.zeros(nt, dtype=np.int64)
+    n = lib().orc_fcc_ministep_trace(C.byref(lat._c), C.byref(model._c), _ptr(_occ(occ), C.c_int8),
+                                     C.c_uint64(seed), C.c_uint32(replica), C.c_uint64(sweep_index), int(k), float(kT),
+                                     _ptr(dE, C.c_double), _ptr(acc, C.c_uint8), _ptr(a, C.c_int64),
+                                     _ptr(b, C.c_int64))
+    if n < 0:
+        raise ValueError("orc_fcc_ministep_trace rejected its arguments")
+    return dE, acc.astype(bool), a, b
 
 
 def energy_grad(lat, model, occ) -> np.ndarray:

@@ -957,3 +957,269 @@ int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *oc
     }
     return 0;
 }
+
+/* ======================================================================== */
+/* FCC lattice (the paper's lattice, Sec. IV-C and Sec. V-C), pair models.   */
+/* nx x ny x nz cubic cells (each >= 1), 4 sites per cell at the half-unit   */
+/* offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3); site id     */
+/* s = ((sub*nz + z)*ny + y)*nx + x, N = 4 nx ny nz.  Shells 1-3: 12 vectors */
+/* of squared half-unit length 2, 6 of length 4, 24 of length 6, each in     */
+/* lexicographic order of (vx, vy, vz).  Link cells as for BCC (edge 4 along */
+/* an axis of n >= 8 cells, n % 4 == 0, else the whole axis); a sweep is     */
+/* n_A = 4 Lx Ly Lz mini-steps, k = ((sub Lz + dz) Ly + dy) Lx + dx.         */
+/* Random numbers: Philox4x32-10 with key seed and counter (s, replica,      */
+/* sweep lo, sweep hi) per trial site s: r = word 0 & (2^29 - 1) for the     */
+/* Metropolis test, partner index floor(12 word 1 / 2^32).                   */
+/* ======================================================================== */
+static const int g_fcc_basis[4][3] = {{0, 0, 0}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}};
+static int g_fcc_n[4];
+static int g_fcc_v[4][24][3];
+static int g_fcc_ready = 0;
+
+int orc_fcc_shell_vectors(int shell, int out[][3])
+{
+    if (shell < 1 || shell > 3) return 0;
+    int n = 0, want = 2 * shell;
+    for (int x = -2; x <= 2; ++x)
+        for (int y = -2; y <= 2; ++y)
+            for (int z = -2; z <= 2; ++z)
+                if (x * x + y * y + z * z == want && ((x + y + z) & 1) == 0) {
+                    out[n][0] = x;
+                    out[n][1] = y;
+                    out[n][2] = z;
+                    ++n;
+                }
+    return n;
+}
+
+static void fcc_init(void)
+{
+    if (g_fcc_ready) return;
+    for (int m = 1; m <= 3; ++m) g_fcc_n[m] = orc_fcc_shell_vectors(m, g_fcc_v[m]);
+    g_fcc_ready = 1;
+}
+
+int64_t orc_fcc_nsites(const orc_lattice *lat)
+{
+    return 4LL * lat->nx * lat->ny * lat->nz;
+}
+
+static int fcc_lattice_ok(const orc_lattice *lat)
+{
+    if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1) return 0;
+    if (lat->nspecies < 1 || lat->nspecies > ORC_MAX_SPECIES) return 0;
+    return orc_fcc_nsites(lat) < (1LL << 31);
+}
+
+static int64_t fcc_site_id(const orc_lattice *lat, int sub, int x, int y, int z)
+{
+    return (((int64_t)sub * lat->nz + z) * lat->ny + y) * lat->nx + x;
+}
+
+/* Site reached from s by v (half units): position 2 cell + basis + v; its
+ * parities name the sublattice. */
+int64_t orc_fcc_neighbor(const orc_lattice *lat, int64_t s, int vx, int vy, int vz)
+{
+    int64_t t = s;
+    int x = (int)(t % lat->nx);
+    t /= lat->nx;
+    int y = (int)(t % lat->ny);
+    t /= lat->ny;
+    int z = (int)(t % lat->nz);
+    int sub = (int)(t / lat->nz);
+    int64_t p[3] = {2LL * x + g_fcc_basis[sub][0] + vx, 2LL * y + g_fcc_basis[sub][1] + vy,
+                    2LL * z + g_fcc_basis[sub][2] + vz};
+    int par = (int)(((p[0] & 1) << 2) | ((p[1] & 1) << 1) | (p[2] & 1));
+    int nsub;
+    switch (par) {
+    case 0: nsub = 0; break;
+    case 6: nsub = 1; break;  /* (1,1,0) */
+    case 5: nsub = 2; break;  /* (1,0,1) */
+    case 3: nsub = 3; break;  /* (0,1,1) */
+    default: return -1;
+    }
+    int64_t c[3];
+    for (int d = 0; d < 3; ++d) c[d] = (p[d] - (p[d] & 1)) / 2;
+    return fcc_site_id(lat, nsub, (int)floor_mod(c[0], lat->nx), (int)floor_mod(c[1], lat->ny),
+                       (int)floor_mod(c[2], lat->nz));
+}
+
+int orc_fcc_schedule(const orc_lattice *lat, int32_t L[3])
+{
+    L[0] = lc_edge(lat->nx);
+    L[1] = lc_edge(lat->ny);
+    L[2] = lc_edge(lat->nz);
+    return 4 * L[0] * L[1] * L[2];
+}
+
+static int fcc_model_ok(const orc_model *m)
+{
+    if (m->kind != ORC_PAIR_I32 && m->kind != ORC_PAIR_F32) return 0;
+    if (m->nshells < 1 || m->nshells > 3) return 0;
+    if (m->kind == ORC_PAIR_I32) return m->v_i32 && m->unit_ev > 0.0;
+    return m->v_f32 != NULL;
+}
+
+/* Twice the pair site energy (integer models) or the site energy (FP). */
+static double fcc_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i,
+                              int64_t *e2)
+{
+    int S = lat->nspecies;
+    int64_t acc2 = 0;
+    double acc = 0.0;
+    for (int sh = 1; sh <= m->nshells; ++sh)
+        for (int t = 0; t < g_fcc_n[sh]; ++t) {
+            const int *v = g_fcc_v[sh][t];
+            int64_t j = orc_fcc_neighbor(lat, i, v[0], v[1], v[2]);
+            int idx = ((sh - 1) * S + occ[i]) * S + occ[j];
+            if (m->kind == ORC_PAIR_I32)
+                acc2 += m->v_i32[idx];
+            else
+                acc += (double)m->v_f32[idx];
+        }
+    if (e2) *e2 = acc2;
+    return m->kind == ORC_PAIR_I32 ? 0.5 * (double)acc2 : 0.5 * acc;
+}
+
+double orc_fcc_total_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ)
+{
+    fcc_init();
+    double e = 0.0;
+    int64_t N = orc_fcc_nsites(lat);
+    for (int64_t i = 0; i < N; ++i) e += fcc_site_energy(lat, m, occ, i, NULL);
+    return e;
+}
+
+int64_t orc_fcc_total_energy_i64(const orc_lattice *lat, const orc_model *m, const int8_t *occ)
+{
+    fcc_init();
+    int64_t N = orc_fcc_nsites(lat), tot = 0, e2;
+    for (int64_t i = 0; i < N; ++i) {
+        fcc_site_energy(lat, m, occ, i, &e2);
+        tot += e2;
+    }
+    return tot / 2;
+}
+
+/* dE of swapping a and b: the local energies of a, b and every site within
+ * the model's shells of either, before and after (Algorithm 1 lines 4-8). */
+double orc_fcc_delta_e(const orc_lattice *lat, const orc_model *m, int8_t *occ, int64_t a, int64_t b)
+{
+    fcc_init();
+    int64_t om[2 + 2 * (12 + 6 + 24)];
+    int n = 0;
+    om[n++] = a;
+    om[n++] = b;
+    for (int sh = 1; sh <= m->nshells; ++sh)
+        for (int t = 0; t < g_fcc_n[sh]; ++t) {
+            const int *v = g_fcc_v[sh][t];
+            om[n++] = orc_fcc_neighbor(lat, a, v[0], v[1], v[2]);
+            om[n++] = orc_fcc_neighbor(lat, b, v[0], v[1], v[2]);
+        }
+    qsort(om, (size_t)n, sizeof(int64_t), cmp_i64);
+    int u = 0;
+    for (int t = 0; t < n; ++t)
+        if (u == 0 || om[t] != om[u - 1]) om[u++] = om[t];
+    int8_t sa = occ[a], sb = occ[b];
+    int64_t e0i = 0, e1i = 0, e2;
+    double e0 = 0.0, e1 = 0.0;
+    for (int t = 0; t < u; ++t) {
+        e0 += fcc_site_energy(lat, m, occ, om[t], &e2);
+        e0i += e2;
+    }
+    occ[a] = sb;
+    occ[b] = sa;
+    for (int t = 0; t < u; ++t) {
+        e1 += fcc_site_energy(lat, m, occ, om[t], &e2);
+        e1i += e2;
+    }
+    occ[a] = sa;
+    occ[b] = sb;
+    if (m->kind == ORC_PAIR_I32) return (double)((e1i - e0i) / 2);
+    return e1 - e0;
+}
+
+static void fcc_words(uint64_t seed, uint32_t replica, uint64_t sweep, int64_t s, uint32_t *r, int *dir)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {(uint32_t)s, replica, (uint32_t)sweep, (uint32_t)(sweep >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    *r = out[0] & ((1u << R_BITS) - 1u);
+    *dir = (int)(((uint64_t)out[1] * 12u) >> 32);
+}
+
+/* Mini-step k: every link cell's trial, in increasing link-cell order. */
+static int64_t fcc_ministep(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
+                            uint32_t replica, uint64_t sweep, int k, double kT, const acc_tab *at, double *dE_out,
+                            uint8_t *acc_out, int64_t *a_out, int64_t *b_out, double *e_acc, int64_t *n_acc)
+{
+    int32_t L[3];
+    int nA = orc_fcc_schedule(lat, L);
+    (void)nA;
+    int NL[3] = {lat->nx / L[0], lat->ny / L[1], lat->nz / L[2]};
+    int dx = k % L[0], r = k / L[0];
+    int dy = r % L[1];
+    r /= L[1];
+    int dz = r % L[2];
+    int sub = r / L[2];
+    int64_t c = 0;
+    for (int cz = 0; cz < NL[2]; ++cz)
+        for (int cy = 0; cy < NL[1]; ++cy)
+            for (int cx = 0; cx < NL[0]; ++cx, ++c) {
+                int64_t a = fcc_site_id(lat, sub, cx * L[0] + dx, cy * L[1] + dy, cz * L[2] + dz);
+                uint32_t rr;
+                int dir;
+                fcc_words(seed, replica, sweep, a, &rr, &dir);
+                const int *v = g_fcc_v[1][dir];
+                int64_t b = orc_fcc_neighbor(lat, a, v[0], v[1], v[2]);
+                double dE = orc_fcc_delta_e(lat, m, occ, a, b);
+                int acc = m->kind == ORC_PAIR_I32 ? accept_int((int64_t)dE, rr, at->T, at->len)
+                                                  : accept_fp(dE, rr, kT);
+                if (acc) {
+                    int8_t t = occ[a];
+                    occ[a] = occ[b];
+                    occ[b] = t;
+                    if (e_acc) *e_acc += dE;
+                    if (n_acc) *n_acc += 1;
+                }
+                if (dE_out) dE_out[c] = dE;
+                if (acc_out) acc_out[c] = (uint8_t)acc;
+                if (a_out) a_out[c] = a;
+                if (b_out) b_out[c] = b;
+            }
+    return c;
+}
+
+int orc_fcc_sweep(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed, uint32_t replica,
+                  uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc, int64_t *n_acc)
+{
+    fcc_init();
+    if (!fcc_lattice_ok(lat) || !fcc_model_ok(m) || nsweeps < 0) return -1;
+    int32_t L[3];
+    int nA = orc_fcc_schedule(lat, L);
+    for (int32_t t = 0; t < nsweeps; ++t) {
+        acc_tab at;
+        if (make_table(m, kT[t], &at) != 0) return -1;
+        for (int k = 0; k < nA; ++k)
+            fcc_ministep(lat, m, occ, seed, replica, sweep0 + (uint64_t)t, k, kT[t], &at, NULL, NULL, NULL, NULL,
+                         e_acc, n_acc);
+        free(at.T);
+    }
+    return 0;
+}
+
+int64_t orc_fcc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
+                               uint32_t replica, uint64_t sweep, int32_t k, double kT, double *dE, uint8_t *acc,
+                               int64_t *site_a, int64_t *site_b)
+{
+    fcc_init();
+    if (!fcc_lattice_ok(lat) || !fcc_model_ok(m)) return -1;
+    int32_t L[3];
+    if (k < 0 || k >= orc_fcc_schedule(lat, L)) return -1;
+    acc_tab at;
+    if (make_table(m, kT, &at) != 0) return -1;
+    int64_t n = fcc_ministep(lat, m, occ, seed, replica, sweep, k, kT, &at, dE, acc, site_a, site_b, NULL, NULL);
+    free(at.T);
+    return n;
+}

@@ -137,6 +137,24 @@ double orc_mlp_eval(const orc_model *m, const double x[ORC_MLP_IN]);
 /* MLPNet site function on an explicit feature vector (for tests). */
 double orc_mlpnet_eval(const orc_model *m, const double x[ORC_MLP_IN]);
 
+/* FCC lattice (pair models): nx x ny x nz cubic cells of 4 sites (half-unit
+ * offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1)); shells of 12, 6 and 24
+ * half-unit vectors in lexicographic order; n_A = 4 Lx Ly Lz mini-steps;
+ * per trial site s, Philox(counter (s, replica, sweep lo, sweep hi)):
+ * r = word 0 & (2^29 - 1), partner index floor(12 word 1 / 2^32). */
+int64_t orc_fcc_nsites(const orc_lattice *lat);
+int64_t orc_fcc_neighbor(const orc_lattice *lat, int64_t s, int vx, int vy, int vz);
+int orc_fcc_shell_vectors(int shell, int out[][3]);
+int orc_fcc_schedule(const orc_lattice *lat, int32_t L[3]);
+double orc_fcc_total_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ);
+int64_t orc_fcc_total_energy_i64(const orc_lattice *lat, const orc_model *m, const int8_t *occ);
+double orc_fcc_delta_e(const orc_lattice *lat, const orc_model *m, int8_t *occ, int64_t a, int64_t b);
+int orc_fcc_sweep(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed, uint32_t replica,
+                  uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc, int64_t *n_acc);
+int64_t orc_fcc_ministep_trace(const orc_lattice *lat, const orc_model *m, int8_t *occ, uint64_t seed,
+                               uint32_t replica, uint64_t sweep, int32_t k, double kT, double *dE, uint8_t *acc,
+                               int64_t *site_a, int64_t *site_b);
+
 #ifdef __cplusplus
 }
 #endif
