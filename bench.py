@@ -203,7 +203,12 @@ def main():
                     help="as --profile-mlp, with MLPNet at the paper's shape")
     ap.add_argument("--profile-qsro", type=int, default=0,
                     help="run the qSRO workload (800 K) on an N^3 box once, for ncu captures")
+    ap.add_argument("--profile-fcc", type=int, default=0,
+                    help="run FCC sweeps (800 K) on an N^3 box of cubic cells once, for ncu captures")
     args = ap.parse_args()
+    if args.profile_fcc:
+        profile_fcc(args.profile_fcc, args.profile_sweeps)
+        return
     if args.probe_sfu:
         probe_sfu()
         return
@@ -400,6 +405,30 @@ def qsro_setup(smc, n: int, dev):
     return lat, occ, model, inputs.K_B_EV * c4["T"]
 
 
+def fcc_setup(smc, n: int, dev):
+    """FCC workload: N^3 cubic cells (4 N^3 sites), equiatomic quinary, FP32
+    3-shell pair coefficients (seed 3), 800 K."""
+    import torch
+    S = 5
+    lat = smc.Lattice(n, n, n, S)
+    occ = torch.empty(smc.fcc_nsites(lat), dtype=torch.int8, device=dev)
+    smc.fcc_init_lattice(lat, inputs.equiatomic_counts(smc.fcc_nsites(lat), S), 1, occ)
+    model = smc.Model(smc.PAIR_F32, 3, inputs.pair_f32_coeffs(3, 3, S))
+    return lat, occ, model, inputs.K_B_EV * 800.0
+
+
+def profile_fcc(n: int, nsweeps: int):
+    """FCC sweeps on an N^3 box, for ncu captures (-k regex:k_fcc_ministep)."""
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    lat, occ, model, kT = fcc_setup(smc, n, "cuda")
+    smc.fcc_sweep(lat, model, occ, 1, 0, nsweeps, kT)
+    smc.check()
+    del occ
+    print(json.dumps({"profile_fcc": n, "sweeps": nsweeps, "ok": True}))
+
+
 def profile_qsro(n: int, nsweeps: int):
     """One qSRO sweep launch (the feature-cache kernel runs first) on an N^3
     box, for ncu captures (-k regex:k_sweep_mlp)."""
@@ -591,6 +620,19 @@ def run_extras(smc, torch, dev, pk):
     emsq = timed(lambda: smc.energy(latq, qm, occq, eq), reps=3)
     out["qsro_energy_256"] = {"ms": emsq}
     del occq
+    # FCC lattice (Sec. IV-C), FP32 3-shell quinary pair model, 256^3 cubic cells, 800 K
+    latf, occf, fm, kTf = fcc_setup(smc, 256, dev)
+    nf = torch.zeros(1, dtype=torch.int64, device=dev)
+    nswf = 2
+    msf = timed(lambda: smc.fcc_sweep(latf, fm, occf, 1, 0, nswf, kTf, n_acc=nf), reps=1)
+    Nf = smc.fcc_nsites(latf)
+    out["fcc_256"] = {"cells": [256] * 3, "sites": Nf, "shells": 3, "sweeps_per_launch": nswf,
+                      "launches_per_sweep": 256, "ms_per_sweep": msf / nswf,
+                      "attempts_per_s": Nf * nswf / (msf * 1e-3),
+                      "accept_rate": float(nf.item()) / (2 * Nf * nswf)}
+    ef = torch.zeros(1, dtype=torch.float64, device=dev)
+    out["fcc_energy_256"] = {"ms": timed(lambda: smc.fcc_energy(latf, fm, occf, ef), reps=3)}
+    del occf
     # dE/dtheta of the pair + MLP energy at 512^3 (one configuration)
     c5 = inputs.CONFIG5
     n5 = c5["cells"][0]

@@ -142,8 +142,9 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  *   occ     device [N] int8, updated in place.
  *   kT      host [nsweeps], temperature of each sweep in eV (> 0, may be +inf
  *           for floating-point models).
- *   e_acc   device double, nullable: += sum of dE of accepted trials (eV),
- *           summed in a fixed order (bit-reproducible).
+ *   e_acc   device double, nullable: += sum of dE of accepted trials (eV;
+ *           integer units of unit_ev for SMC_PAIR_I32), summed in a fixed
+ *           order (bit-reproducible).
  *   n_acc   device int64, nullable: += number of accepted trials.
  * MLP models keep a per-site energy cache E[i] = f(x_i) in the workspace
  * (4 N bytes), filled at the start of every call and updated over the
@@ -244,6 +245,32 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
 smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ,
                               uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,
                               double kT, float *dE, uint8_t *acc, cudaStream_t stream);
+
+/* FCC lattice (the paper's lattice, Sec. IV-C), pair models (SMC_PAIR_I32,
+ * SMC_PAIR_F32).  lat gives nx x ny x nz cubic cells of 4 sites at the
+ * half-unit offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3),
+ * N = 4 nx ny nz, site s = ((sub*nz + z)*ny + y)*nx + x; every axis a
+ * multiple of 4 and >= 8 cells (4x4x4 link cells, n_A = 256 mini-steps,
+ * k = ((sub*4 + dz)*4 + dy)*4 + dx, Sec. V-C).  Shell m: the half-unit
+ * vectors of squared length 2m with an even component sum (12, 6, 24), in
+ * lexicographic order.  Random numbers: per trial site s,
+ * w = Philox4x32-10(key seed, counter (s, replica, sweep lo, sweep hi)),
+ * r = w0 & (2^29 - 1) for the Metropolis test, partner = floor(12 w1 / 2^32).
+ * smc_fcc_init_lattice: the composition-conserving start state (the
+ * smc_init_lattice order over the same N site ids).  The other calls have
+ * the arguments and errors of their BCC counterparts; e_acc sums per link
+ * cell and then in link-cell order; smc_fcc_ministep_trace runs the sweep
+ * kernel on one mini-step and records its per-trial dE and decisions. */
+smc_status smc_fcc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,
+                                int8_t *occ, cudaStream_t stream);
+smc_status smc_fcc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                         uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
+                         int64_t *n_acc, cudaStream_t stream);
+smc_status smc_fcc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                                  uint32_t replica, uint64_t sweep, int32_t k, double kT, float *dE, uint8_t *acc,
+                                  cudaStream_t stream);
+smc_status smc_fcc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ, double *e,
+                          int64_t *e_int, cudaStream_t stream);
 
 /* Philox4x32-10 block function on the device, for tests: out[4i..4i+3] =
  * Philox(ctr[4i..4i+3], key[2i..2i+1]).  All pointers device memory. */

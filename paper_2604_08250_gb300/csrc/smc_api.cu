@@ -469,6 +469,131 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
+// ---- FCC lattice (Sec. IV-C), pair models ----
+
+static bool fcc_lattice_valid(const smc_lattice *lat)
+{
+    if (!lat) {
+        set_error("lattice is NULL");
+        return false;
+    }
+    if (lat->nx < 1 || lat->ny < 1 || lat->nz < 1) {
+        set_error("lattice dimensions must be >= 1 (got %d x %d x %d)", lat->nx, lat->ny, lat->nz);
+        return false;
+    }
+    if (lat->nspecies < 1 || lat->nspecies > kMaxSpecies) {
+        set_error("nspecies must be in [1, %d] (got %d)", kMaxSpecies, lat->nspecies);
+        return false;
+    }
+    if (4LL * lat->nx * lat->ny * lat->nz >= (1LL << 31)) {
+        set_error("lattice too large: N = %lld sites (limit 2^31 - 1)", 4LL * lat->nx * lat->ny * lat->nz);
+        return false;
+    }
+    return true;
+}
+
+static smc_status fcc_check(const smc_lattice *lat, const smc_model *model, const void *occ, bool sweep)
+{
+    if (!fcc_lattice_valid(lat) || !model_valid(lat, model)) return SMC_ERR_ARG;
+    if (model->kind != SMC_PAIR_I32 && model->kind != SMC_PAIR_F32) {
+        set_error("the FCC lattice takes pair models (SMC_PAIR_I32, SMC_PAIR_F32) only");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    if (!occ) {
+        set_error("occ is NULL");
+        return SMC_ERR_ARG;
+    }
+    if (sweep && !fcc_shape_ok(lat)) {
+        set_error("FCC sweeps need every axis a multiple of 4 and >= 8 cells (got %d x %d x %d)", lat->nx, lat->ny,
+                  lat->nz);
+        return SMC_ERR_UNSUPPORTED;
+    }
+    return SMC_OK;
+}
+
+smc_status smc_fcc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,
+                                int8_t *occ, cudaStream_t stream)
+{
+    if (!fcc_lattice_valid(lat)) return SMC_ERR_ARG;
+    // the same start-state order over N = 4 nx ny nz ids: a BCC box of 2nx x ny x nz
+    const smc_lattice twice = {2 * lat->nx, lat->ny, lat->nz, lat->nspecies};
+    return smc_init_lattice(&twice, counts, seed, replica, occ, stream);
+}
+
+smc_status smc_fcc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                         uint32_t replica, uint64_t sweep0, int32_t nsweeps, const double *kT, double *e_acc,
+                         int64_t *n_acc, cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = fcc_check(lat, model, occ, true);
+    if (st != SMC_OK) return st;
+    if (nsweeps < 0 || nsweeps > (1 << 24)) {
+        set_error("nsweeps must be in [0, 2^24]");
+        return SMC_ERR_ARG;
+    }
+    if (nsweeps > 0 && !kT) {
+        set_error("kT is NULL");
+        return SMC_ERR_ARG;
+    }
+    if (sweep0 + (uint64_t)nsweeps > 0xFFFFFFFFFFFFFFFEull || sweep0 + (uint64_t)nsweeps < sweep0) {
+        set_error("sweep indices reach the reserved values 2^64-2, 2^64-1");
+        return SMC_ERR_ARG;
+    }
+    for (int i = 0; i < nsweeps; ++i) {
+        const double t = kT[i];
+        if (!(t > 0.0) || (model->kind == SMC_PAIR_I32 && !std::isfinite(t))) {
+            set_error("kT[%d] = %g is invalid (must be > 0; finite for integer models)", i, t);
+            return SMC_ERR_ARG;
+        }
+        if (model->kind == SMC_PAIR_I32 && model->unit_ev / t < 29.0 * 0.6931471805599453 / (double)(1 << 24)) {
+            set_error("kT[%d] too high for the integer acceptance table", i);
+            return SMC_ERR_UNSUPPORTED;
+        }
+    }
+    if (nsweeps == 0) return SMC_OK;
+    return launch_fcc_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, nullptr, nullptr, -1,
+                            stream);
+}
+
+smc_status smc_fcc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
+                                  uint32_t replica, uint64_t sweep, int32_t k, double kT, float *dE, uint8_t *acc,
+                                  cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = fcc_check(lat, model, occ, true);
+    if (st != SMC_OK) return st;
+    if (k < 0 || k >= 256) {
+        set_error("mini-step %d out of range [0, 256)", k);
+        return SMC_ERR_ARG;
+    }
+    if (sweep > 0xFFFFFFFFFFFFFFFDull) {
+        set_error("sweep index reaches the reserved values 2^64-2, 2^64-1");
+        return SMC_ERR_ARG;
+    }
+    if (!(kT > 0.0) || (model->kind == SMC_PAIR_I32 && !std::isfinite(kT))) {
+        set_error("kT = %g is invalid (must be > 0; finite for integer models)", kT);
+        return SMC_ERR_ARG;
+    }
+    if (model->kind == SMC_PAIR_I32 && model->unit_ev / kT < 29.0 * 0.6931471805599453 / (double)(1 << 24)) {
+        set_error("kT too high for the integer acceptance table");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    return launch_fcc_sweep(lat, model, occ, seed, replica, sweep, 1, &kT, nullptr, nullptr, dE, acc, k, stream);
+}
+
+smc_status smc_fcc_energy(const smc_lattice *lat, const smc_model *model, const int8_t *occ, double *e,
+                          int64_t *e_int, cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = fcc_check(lat, model, occ, false);
+    if (st != SMC_OK) return st;
+    if (e_int && model->kind != SMC_PAIR_I32) {
+        set_error("e_int is only defined for integer models");
+        return SMC_ERR_ARG;
+    }
+    return launch_fcc_energy(lat, model, occ, e, e_int, stream);
+}
+
 smc_status smc_sro(const smc_lattice *lat, int32_t nshells, const int8_t *occ, int64_t *counts, double *alpha,
                    cudaStream_t stream)
 {

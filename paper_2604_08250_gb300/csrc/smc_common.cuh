@@ -8,6 +8,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/smc.h"
 
 namespace smc {
@@ -153,6 +155,13 @@ smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int
 // Warp count of a warp-per-tile kernel (warp w owns tiles w, w + NW, ...)
 // that gives the busiest SM the fewest tiles (defined in sweep_pair.cu).
 long long balanced_warps(long long ntiles, int nwarps, int per_sm, int num_sms);
+std::vector<uint32_t> int_table(double unit_ev, double kT);
+bool fcc_shape_ok(const smc_lattice *lat);
+smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                            uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                            int64_t *n_acc, float *trace_dE, uint8_t *trace_acc, int trace_k, cudaStream_t stream);
+smc_status launch_fcc_energy(const smc_lattice *lat, const smc_model *m, const int8_t *occ, double *e,
+                             int64_t *e_int, cudaStream_t stream);
 smc_status launch_qsro_sweep(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                              uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
                              int64_t *n_acc, cudaStream_t stream);

@@ -1238,6 +1238,8 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const
     return SMC_OK;
 }
 
+}  // namespace
+
 // Integer acceptance table T[d] = floor(2^29 exp(-d unit / kT)) for d = 0 ..
 // len-1 (T[len] = 0), in FP64 on the host.
 std::vector<uint32_t> int_table(double unit_ev, double kT)
@@ -1250,8 +1252,6 @@ std::vector<uint32_t> int_table(double unit_ev, double kT)
     }
     return t;
 }
-
-}  // namespace
 
 template <bool IS_INT>
 static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,

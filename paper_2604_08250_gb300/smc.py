@@ -23,7 +23,8 @@ MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 # Every symbol declared in include/smc.h.
 EXPORTS = ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy", "smc_grad_size",
            "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check", "smc_last_error",
-           "smc_set_tuning", "smc_debug_set")
+           "smc_set_tuning", "smc_debug_set", "smc_fcc_init_lattice", "smc_fcc_sweep", "smc_fcc_ministep_trace",
+           "smc_fcc_energy")
 
 
 class SMCError(RuntimeError):
@@ -83,13 +84,20 @@ def lib():
         L.smc_energy_grad.argtypes = [P(_Lat), P(_Model), vp, vp, vp]
         L.smc_ministep_trace.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64,
                                          C.c_int32, C.c_double, vp, vp, vp]
+        L.smc_fcc_init_lattice.argtypes = [P(_Lat), P(C.c_int64), C.c_uint64, C.c_uint32, vp, vp]
+        L.smc_fcc_sweep.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
+                                    P(C.c_double), vp, vp, vp]
+        L.smc_fcc_ministep_trace.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64,
+                                             C.c_int32, C.c_double, vp, vp, vp]
+        L.smc_fcc_energy.argtypes = [P(_Lat), P(_Model), vp, vp, vp, vp]
         L.smc_philox4x32_10.argtypes = [vp, vp, vp, C.c_int64, vp]
         L.smc_check.argtypes = [vp]
         L.smc_set_tuning.argtypes = [P(_Tuning)]
         L.smc_debug_set.argtypes = [C.c_int32, C.c_int64]
         for name in ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy",
                      "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check",
-                     "smc_set_tuning", "smc_debug_set"):
+                     "smc_set_tuning", "smc_debug_set", "smc_fcc_init_lattice", "smc_fcc_sweep",
+                     "smc_fcc_ministep_trace", "smc_fcc_energy"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -225,6 +233,39 @@ def ministep_trace(lat, model, occ, seed, sweep_index, k, kT, dE=None, acc=None,
     _chk(lib().smc_ministep_trace(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), C.c_uint64(seed),
                                   C.c_uint32(replica), C.c_uint64(sweep_index), int(k), float(kT),
                                   _dptr(dE, torch.float32), _dptr(acc, torch.uint8), _stream()))
+
+
+def fcc_nsites(lat) -> int:
+    """Sites of lat read as nx x ny x nz FCC cubic cells (4 per cell)."""
+    return 4 * lat.nx * lat.ny * lat.nz
+
+
+def fcc_init_lattice(lat, counts, seed, occ, replica=0):
+    cnt = np.ascontiguousarray(counts, dtype=np.int64)
+    _chk(lib().smc_fcc_init_lattice(C.byref(lat._c), cnt.ctypes.data_as(C.POINTER(C.c_int64)), C.c_uint64(seed),
+                                    C.c_uint32(replica), _dptr(occ), _stream()))
+
+
+def fcc_sweep(lat, model, occ, seed, sweep0, nsweeps, kT, replica=0, e_acc=None, n_acc=None):
+    import torch
+    kTa = np.ascontiguousarray(np.broadcast_to(np.asarray(kT, dtype=np.float64), (nsweeps,)))
+    _chk(lib().smc_fcc_sweep(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), C.c_uint64(seed),
+                             C.c_uint32(replica), C.c_uint64(sweep0), int(nsweeps),
+                             kTa.ctypes.data_as(C.POINTER(C.c_double)), _dptr(e_acc, torch.float64),
+                             _dptr(n_acc, torch.int64), _stream()))
+
+
+def fcc_ministep_trace(lat, model, occ, seed, sweep_index, k, kT, dE=None, acc=None, replica=0):
+    import torch
+    _chk(lib().smc_fcc_ministep_trace(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8),
+                                      C.c_uint64(seed), C.c_uint32(replica), C.c_uint64(sweep_index), int(k),
+                                      float(kT), _dptr(dE, torch.float32), _dptr(acc, torch.uint8), _stream()))
+
+
+def fcc_energy(lat, model, occ, e=None, e_int=None):
+    import torch
+    _chk(lib().smc_fcc_energy(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8),
+                              _dptr(e, torch.float64), _dptr(e_int, torch.int64), _stream()))
 
 
 def philox4x32_10(ctr, key, out):

@@ -46,3 +46,22 @@ def test_argument_errors_need_no_gpu(L):
     assert smc.grad_size(smc.Lattice(4, 4, 4, 5), smc.Model(smc.PAIR_F32_MLP_BF16, 2, [[[0.0] * 5] * 5] * 2,
                          mlp={"w1": [0] * 1280, "w2": [0] * 4096, "w3": [0] * 64, "b1": [0.0] * 64,
                               "b2": [0.0] * 64, "b3": 0.0})) == 30 + smc.MLP_NPARAM
+
+
+def test_fcc_argument_errors_need_no_gpu(L):
+    V = [[[0, 1], [1, 0]]]
+    m = smc.Model(smc.PAIR_I32, 1, V, unit_ev=1e-4)
+    kT = (ctypes.c_double * 1)(0.05)
+    for dims in ((6, 8, 8), (8, 8, 4)):
+        lat = smc.Lattice(*dims, 2)
+        rc = L.smc_fcc_sweep(ctypes.byref(lat._c), ctypes.byref(m._c), ctypes.c_void_p(16), 1, 0, 0, 1, kT, None,
+                             None, None)
+        assert rc == smc.SMC_ERR_UNSUPPORTED
+        assert b"multiple of 4" in L.smc_last_error()
+    lat = smc.Lattice(8, 8, 8, 2)
+    rc = L.smc_fcc_ministep_trace(ctypes.byref(lat._c), ctypes.byref(m._c), ctypes.c_void_p(16), 1, 0, 0, 256,
+                                  0.05, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
+    assert rc == smc.SMC_ERR_ARG and b"mini-step" in L.smc_last_error()
+    q = smc.Model(smc.QSRO_F32, 1, [[[0.0, 0.0], [0.0, 0.0]]], qsro_w=[[[0.0, 0.0], [0.0, 0.0]]])
+    rc = L.smc_fcc_energy(ctypes.byref(lat._c), ctypes.byref(q._c), ctypes.c_void_p(16), None, None, None)
+    assert rc == smc.SMC_ERR_UNSUPPORTED and b"pair models" in L.smc_last_error()

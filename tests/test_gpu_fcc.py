@@ -1,0 +1,216 @@
+"""GPU parity of the FCC lattice (Sec. IV-C; 4x4x4 link cells, 256
+mini-steps as in Sec. V-C) with pair models against the CPU oracle, through
+the C ABI.
+
+Integer models: the start state, trajectories, accepted counts, accepted
+energy sums and total energies bit-exact.  FP32 models: every trial's dE
+within DE_TOL_EV of the FP64 oracle and the same decision, mini-step by
+mini-step (lock-step; a decision flip resynchronises the oracle); the sweep
+equals its traced mini-steps bit for bit; energies from exact pair counts in
+FP64."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2604_08250_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DE_TOL_EV = 1e-5  # FP32 dE vs FP64
+
+
+@pytest.fixture(scope="module")
+def smc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2604_08250_gb300 import build, smc as s
+    build.build()
+    s.lib()
+    return s
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def _state(smc, dims, S, seed, counts=None):
+    lat = smc.Lattice(*dims, S)
+    N = smc.fcc_nsites(lat)
+    counts = inputs.equiatomic_counts(N, S) if counts is None else counts
+    olat = oracle.Lattice(*dims, S)
+    if min(dims[1:]) >= 2:
+        occ = torch.empty(N, dtype=torch.int8, device=dev())
+        smc.fcc_init_lattice(lat, counts, seed, occ)
+        ref = oracle.fcc_init_lattice(olat, counts, seed)
+    else:  # the start-state order needs ny, nz >= 2: a seeded permutation instead
+        ref = np.random.default_rng(seed).permutation(np.repeat(np.arange(S), counts)).astype(np.int8)
+        occ = torch.from_numpy(ref.copy()).to(dev())
+    return lat, occ, olat, ref
+
+
+@pytest.mark.parametrize("dims,S", [((8, 8, 8), 2), ((12, 8, 16), 5), ((3, 5, 2), 8)])
+def test_init_matches_oracle(smc, dims, S):
+    counts = inputs.dirichlet_counts(4 * dims[0] * dims[1] * dims[2], S, 4)
+    lat, occ, olat, ref = _state(smc, dims, S, 6, counts)
+    assert np.array_equal(occ.cpu().numpy(), ref)
+    assert np.array_equal(np.bincount(ref, minlength=S), counts)
+
+
+@pytest.mark.parametrize("dims,S,nsh,nsw", [((8, 8, 8), 2, 1, 3), ((12, 8, 16), 5, 2, 2), ((16, 16, 16), 8, 3, 1),
+                                            ((8, 12, 8), 3, 3, 2)])
+def test_int_trajectory_bit_exact(smc, dims, S, nsh, nsw):
+    V = inputs.pair_int_coeffs(nsh + S, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 2)
+    model = smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-4)
+    omodel = oracle.Model(oracle.PAIR_I32, nsh, V, unit_ev=1e-4)
+    kT = inputs.ladder_kT(nsw, 300.0, 1500.0) if nsw > 1 else [0.05]
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    e0 = oracle.fcc_total_energy_i64(olat, omodel, ref)
+    smc.fcc_sweep(lat, model, occ, 7, 3, nsw, kT, e_acc=e_acc, n_acc=n_acc)
+    oe, on = oracle.fcc_sweep(olat, omodel, ref, 7, 3, nsw, kT)
+    smc.check()
+    assert np.array_equal(occ.cpu().numpy(), ref)
+    assert int(n_acc.item()) == on and on > 0
+    assert float(e_acc.item()) == oe
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    e_int = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e, e_int=e_int)
+    assert int(e_int.item()) == oracle.fcc_total_energy_i64(olat, omodel, ref) == e0 + int(oe)
+    assert float(e.item()) == pytest.approx(int(e_int.item()) * 1e-4, rel=1e-15)
+
+
+def test_int_trace_matches_oracle_per_trial(smc):
+    """dE, decision and the resulting state of single mini-steps."""
+    dims, S, nsh = (12, 8, 8), 4, 3
+    V = inputs.pair_int_coeffs(21, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 5)
+    model = smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-4)
+    omodel = oracle.Model(oracle.PAIR_I32, nsh, V, unit_ev=1e-4)
+    nt = oracle.fcc_nsites(olat) // 256
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    for k in (0, 1, 63, 64, 130, 255):
+        smc.fcc_ministep_trace(lat, model, occ, 11, 4, k, 0.04, dE=dE, acc=acc)
+        odE, oacc, _, _ = oracle.fcc_ministep_trace(olat, omodel, ref, 11, 4, k, 0.04)
+        assert np.array_equal(dE.cpu().numpy().astype(np.float64), odE)
+        assert np.array_equal(acc.cpu().numpy().astype(bool), oacc)
+        assert np.array_equal(occ.cpu().numpy(), ref)
+
+
+@pytest.mark.parametrize("dims,kT", [((8, 8, 8), 0.05), ((12, 8, 16), 0.03)])
+def test_f32_lockstep_against_oracle(smc, dims, kT):
+    S, nsh = 5, 3
+    V = inputs.pair_f32_coeffs(8, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 3)
+    model = smc.Model(smc.PAIR_F32, nsh, V)
+    omodel = oracle.Model(oracle.PAIR_F32, nsh, V)
+    nt = oracle.fcc_nsites(olat) // 256
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    flips, worst = 0, 0.0
+    for k in range(256):
+        smc.fcc_ministep_trace(lat, model, occ, 9, 0, k, kT, dE=dE, acc=acc)
+        odE, oacc, _, _ = oracle.fcc_ministep_trace(olat, omodel, ref, 9, 0, k, kT)
+        g = dE.cpu().numpy().astype(np.float64)
+        worst = max(worst, float(np.abs(g - odE).max()))
+        assert np.all(np.abs(g - odE) <= DE_TOL_EV)
+        ga = acc.cpu().numpy().astype(bool)
+        if not np.array_equal(ga, oacc):
+            flips += int((ga != oacc).sum())
+            ref[:] = occ.cpu().numpy()
+        else:
+            assert np.array_equal(occ.cpu().numpy(), ref)
+    assert flips <= 1, flips
+    assert worst < 1e-6
+
+
+def test_f32_sweep_equals_trace_and_energy_closes(smc):
+    dims, S, nsh = (8, 16, 12), 6, 2
+    V = inputs.pair_f32_coeffs(4, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 8)
+    model = smc.Model(smc.PAIR_F32, nsh, V)
+    omodel = oracle.Model(oracle.PAIR_F32, nsh, V)
+    occ2 = occ.clone()
+    kT = [0.05, 0.08]
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.fcc_sweep(lat, model, occ, 4, 10, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    for t in range(2):
+        for k in range(256):
+            smc.fcc_ministep_trace(lat, model, occ2, 4, 10 + t, k, kT[t])
+    smc.check()
+    assert torch.equal(occ, occ2)
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e)
+    after = occ.cpu().numpy()
+    assert float(e.item()) == pytest.approx(oracle.fcc_total_energy(olat, omodel, after), rel=1e-12, abs=1e-9)
+    # each accepted dE: 84 FP32 terms of |.| <= 2 max|V|; errors add like a random walk
+    n = int(n_acc.item())
+    tol = 6 * math.sqrt(max(n, 1)) * 84 * 2.0 ** -24 * 84 * 2 * float(np.abs(V).max())
+    assert abs(float(e.item()) - (oracle.fcc_total_energy(olat, omodel, ref) + float(e_acc.item()))) <= tol
+
+
+@pytest.mark.parametrize("dims,S,nsh,kind", [((4, 5, 3), 3, 3, "int"), ((2, 1, 1), 2, 2, "f32"),
+                                             ((16, 8, 24), 8, 3, "f32"), ((1, 1, 1), 4, 1, "int")])
+def test_energy_matches_oracle(smc, dims, S, nsh, kind):
+    """Any box, including ones too small to sweep (shells alias)."""
+    lat, occ, olat, ref = _state(smc, dims, S, 12, inputs.dirichlet_counts(4 * dims[0] * dims[1] * dims[2], S, 1))
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    if kind == "int":
+        V = inputs.pair_int_coeffs(2, nsh, S)
+        e_int = torch.zeros(1, dtype=torch.int64, device=dev())
+        smc.fcc_energy(lat, smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-4), occ, e=e, e_int=e_int)
+        assert int(e_int.item()) == oracle.fcc_total_energy_i64(olat, oracle.Model(oracle.PAIR_I32, nsh, V,
+                                                                                   unit_ev=1e-4), ref)
+    else:
+        V = inputs.pair_f32_coeffs(2, nsh, S)
+        smc.fcc_energy(lat, smc.Model(smc.PAIR_F32, nsh, V), occ, e=e)
+        want = oracle.fcc_total_energy(olat, oracle.Model(oracle.PAIR_F32, nsh, V), ref)
+        assert float(e.item()) == pytest.approx(want, rel=1e-12, abs=1e-12)
+
+
+def test_large_int_values_do_not_overflow(smc):
+    """|V| at the 2^24 limit (a dE of 84 such terms can pass 2^31): the
+    trajectory and the accepted sum stay exact."""
+    dims, S, nsh = (8, 8, 8), 2, 3
+    V = np.zeros((nsh, S, S), dtype=np.int32)
+    V[:, 0, 1] = V[:, 1, 0] = -(1 << 24)
+    V[:, 1, 1] = 1 << 24
+    lat, occ, olat, ref = _state(smc, dims, S, 1)
+    model = smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-6)
+    omodel = oracle.Model(oracle.PAIR_I32, nsh, V, unit_ev=1e-6)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.fcc_sweep(lat, model, occ, 3, 0, 2, [0.05, 0.05], e_acc=e_acc, n_acc=n_acc)
+    oe, on = oracle.fcc_sweep(olat, omodel, ref, 3, 0, 2, [0.05, 0.05])
+    smc.check()
+    assert np.array_equal(occ.cpu().numpy(), ref)
+    assert int(n_acc.item()) == on and float(e_acc.item()) == oe
+
+
+def test_unsupported_inputs_raise(smc):
+    S = 2
+    V = inputs.pair_int_coeffs(1, 2, S)
+    model = smc.Model(smc.PAIR_I32, 2, V, unit_ev=1e-4)
+    for dims in ((6, 8, 8), (8, 4, 8), (8, 8, 10)):
+        lat = smc.Lattice(*dims, S)
+        occ = torch.zeros(smc.fcc_nsites(lat), dtype=torch.int8, device=dev())
+        with pytest.raises(smc.SMCError):
+            smc.fcc_sweep(lat, model, occ, 1, 0, 1, [0.05])
+    lat = smc.Lattice(8, 8, 8, S)
+    occ = torch.zeros(smc.fcc_nsites(lat), dtype=torch.int8, device=dev())
+    with pytest.raises(smc.SMCError):
+        smc.fcc_ministep_trace(lat, model, occ, 1, 0, 256, 0.05,
+                               dE=torch.zeros(8, dtype=torch.float32, device=dev()),
+                               acc=torch.zeros(8, dtype=torch.uint8, device=dev()))
+    with pytest.raises(smc.SMCError):
+        smc.fcc_sweep(lat, model, occ, 1, 0, 1, [-1.0])
+    mlp = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(1))
+    with pytest.raises(smc.SMCError):
+        smc.fcc_sweep(lat, mlp, occ, 1, 0, 1, [0.05])
+    with pytest.raises(smc.SMCError):
+        smc.fcc_init_lattice(lat, [10, 10], 1, occ)
