@@ -16,9 +16,20 @@
 // CPU for 1-3 shells), and consecutive launches are ordered by the stream.
 // dE sums the changed bonds: with every axis at least 8 cells no shell
 // aliases, so a's neighbours other than b and b's other than a each flip
-// one bond.  The same kernel records the trace (dE, decision) of a
-// mini-step, so a sweep equals its traced mini-steps bit for bit.
+// one bond, dE = sum_j D_m(q_j) over a's zone - sum_j D_m(q_j) over b's,
+// D_m(q) = V_m(B, q) - V_m(A, q).  The same kernel records the trace (dE,
+// decision) of a mini-step, so a sweep equals its traced mini-steps bit for
+// bit.
+//
+// Link cells away from the box faces (1 <= c < NL-1 on every axis) reach
+// every neighbour of a and b without a periodic wrap: a neighbour is the
+// site id plus a delta that depends only on the sublattice and the vector.
+// Those trials run in the first blocks with the deltas, the D rows and the
+// first-shell sublattice map in shared memory; the link cells on the faces
+// run in the last blocks with wrapped coordinates.  Both sum in the same
+// order, so the split changes no result.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstring>
 #include <type_traits>
@@ -30,9 +41,17 @@ namespace smc {
 
 namespace {
 
+// Per-call tables (32-bit words): D rows T[m][A][B][q] = V_m(B,q) - V_m(A,q)
+// (stride 8), index deltas D[sub][t] of the 42 shell vectors without wrap,
+// first-shell sublattice map N1[sub][dir], packed vectors (v + 2, 4 bits each).
+constexpr int kFccT = kMaxShells * 8 * 8 * 8, kFccD = kFccT, kFccN1 = kFccD + 4 * 42, kFccVec = kFccN1 + 4 * 12,
+              kFccWords = kFccVec + 42;
+
 struct FccParams {
     int nx, ny, nz, S, nshells, nA_cells;  // nA_cells: link cells (trials per mini-step)
-    int NLx, NLy;
+    int NLx, NLy, NLz;
+    int n_int, n_bnd, int_blocks;          // interior / face link cells, blocks of the interior part
+    const uint32_t *tables;
     uint64_t seed;
     uint32_t replica;
     uint64_t sweep;
@@ -51,62 +70,124 @@ struct FccParams {
 __constant__ signed char c_fcc_vec[4][24][3];  // shells 1-3 at [1..3]
 __constant__ int c_fcc_n[4];
 
-__device__ __forceinline__ int fcc_neighbor(const FccParams &P, int s, const signed char *v)
+// Half-unit position of a site and its wrapped neighbour along v.
+struct FccPos {
+    int x, y, z;  // 2 * cell + basis
+};
+
+__device__ __forceinline__ FccPos fcc_pos(int sub, int x, int y, int z)
 {
-    int t = s;
-    const int x = t % P.nx;
-    t /= P.nx;
-    const int y = t % P.ny;
-    t /= P.ny;
-    const int z = t % P.nz;
-    const int sub = t / P.nz;
-    const int bx = (sub == 1 || sub == 2) ? 1 : 0, by = (sub == 1 || sub == 3) ? 1 : 0,
-              bz = (sub == 2 || sub == 3) ? 1 : 0;
-    const int px = 2 * x + bx + v[0], py = 2 * y + by + v[1], pz = 2 * z + bz + v[2];
-    const int ox = px & 1, oy = py & 1, oz = pz & 1;
-    const int nsub = ox ? (oy ? 1 : 2) : (oy ? 3 : 0);
-    const int cx = wrapc((px - ox) >> 1, P.nx), cy = wrapc((py - oy) >> 1, P.ny), cz = wrapc((pz - oz) >> 1, P.nz);
+    return FccPos{2 * x + ((sub == 1 || sub == 2) ? 1 : 0), 2 * y + ((sub == 1 || sub == 3) ? 1 : 0),
+                  2 * z + ((sub == 2 || sub == 3) ? 1 : 0)};
+}
+
+__device__ __forceinline__ int fcc_site_at(const FccParams &P, int px, int py, int pz)
+{
+    const int ox = px & 1, oy = py & 1;
+    const int nsub = (0x6C >> ((ox << 2) | (oy << 1))) & 3;  // parities (1,1) -> 1, (1,0) -> 2, (0,1) -> 3
+    const int cx = wrapc(px >> 1, P.nx), cy = wrapc(py >> 1, P.ny), cz = wrapc(pz >> 1, P.nz);
     return ((nsub * P.nz + cz) * P.ny + cy) * P.nx + cx;
 }
 
-template <bool IS_INT>
+__device__ __forceinline__ int3 fcc_unpack(int w) { return make_int3((w & 15) - 2, ((w >> 4) & 15) - 2, ((w >> 8) & 15) - 2); }
+
+// Shell-vector index t (shell 1: 0-11, shell 2: 12-17, shell 3: 18-41) -> D-row offset.
+__host__ __device__ constexpr int fcc_shell_off(int t) { return t < 12 ? 0 : (t < 18 ? 512 : 1024); }
+
+// The t-th link cell on the box faces: z faces, then y faces, then x faces.
+__device__ __forceinline__ int3 fcc_face_cell(int j, int NLx, int NLy, int NLz)
+{
+    const int fz = NLx * NLy;
+    if (j < 2 * fz) {
+        const int r = j % fz;
+        return make_int3(r % NLx, r / NLx, j < fz ? 0 : NLz - 1);
+    }
+    j -= 2 * fz;
+    const int fy = NLx * (NLz - 2);
+    if (j < 2 * fy) {
+        const int r = j % fy;
+        return make_int3(r % NLx, j < fy ? 0 : NLy - 1, 1 + r / NLx);
+    }
+    j -= 2 * fy;
+    const int fx = (NLy - 2) * (NLz - 2);
+    const int r = j % fx;
+    return make_int3(j < fx ? 0 : NLx - 1, 1 + r % (NLy - 2), 1 + r / (NLy - 2));
+}
+
+template <bool IS_INT, int NSH>
 __global__ void __launch_bounds__(256) k_fcc_ministep(const __grid_constant__ FccParams P, int k)
 {
     using T = typename Acc<IS_INT>::T;
-    const int c = blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= P.nA_cells) return;
+    using Word = typename std::conditional<IS_INT, int, float>::type;
+    // integer models sum in 64 bits (84 terms of |V| <= 2^24 can pass 2^31)
+    using Wide = typename std::conditional<IS_INT, long long, float>::type;
+    constexpr int NV = NSH == 1 ? 12 : (NSH == 2 ? 18 : 42);
+    __shared__ uint32_t sm[kFccWords];
+    for (int i = threadIdx.x; i < kFccWords; i += blockDim.x) sm[i] = __ldg(P.tables + i);
+    __syncthreads();
+    const Word *sT = reinterpret_cast<const Word *>(sm);
+    const int *sD = reinterpret_cast<const int *>(sm + kFccD);
+    const int *sN1 = reinterpret_cast<const int *>(sm + kFccN1);
+    const int *sV = reinterpret_cast<const int *>(sm + kFccVec);
+
     const int dx = k & 3, dy = (k >> 2) & 3, dz = (k >> 4) & 3, sub = k >> 6;
-    const int cx = c % P.NLx, cy = (c / P.NLx) % P.NLy, cz = c / (P.NLx * P.NLy);
-    const int a = ((sub * P.nz + 4 * cz + dz) * P.ny + 4 * cy + dy) * P.nx + 4 * cx + dx;
+    const bool interior = (int)blockIdx.x < P.int_blocks;
+    int3 cc;
+    if (interior) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= P.n_int) return;
+        const int wx = P.NLx - 2, wy = P.NLy - 2;
+        cc = make_int3(1 + i % wx, 1 + (i / wx) % wy, 1 + i / (wx * wy));
+    } else {
+        const int j = (blockIdx.x - P.int_blocks) * blockDim.x + threadIdx.x;
+        if (j >= P.n_bnd) return;
+        cc = fcc_face_cell(j, P.NLx, P.NLy, P.NLz);
+    }
+    const int c = (cc.z * P.NLy + cc.y) * P.NLx + cc.x;
+    const int x = 4 * cc.x + dx, y = 4 * cc.y + dy, z = 4 * cc.z + dz;
+    const int a = ((sub * P.nz + z) * P.ny + y) * P.nx + x;
     const U4 w = philox10(U4{(uint32_t)a, P.replica, (uint32_t)P.sweep, (uint32_t)(P.sweep >> 32)}, (uint32_t)P.seed,
                           (uint32_t)(P.seed >> 32));
     const uint32_t r = w.x & kRMask;
-    const int dir = (int)(((uint64_t)w.y * 12u) >> 32);
-    const int b = fcc_neighbor(P, a, c_fcc_vec[1][dir]);
+    const int dir = (int)(((uint64_t)w.y * 12u) >> 32), opp = 11 - dir;  // shell 1 is centrally symmetric
+    const FccPos pa = fcc_pos(sub, x, y, z);
+    const int3 v1 = fcc_unpack(sV[dir]);
+    const FccPos pb{pa.x + v1.x, pa.y + v1.y, pa.z + v1.z};
     int8_t *occ = P.occ;
-    const int A = occ[a] & 7, B = occ[b] & 7, S = P.S;
-    // integer models sum in 64 bits (84 terms of |V| <= 2^24 can pass 2^31)
-    using Wide = typename std::conditional<IS_INT, long long, float>::type;
+    const int b = interior ? a + sD[sub * 42 + dir] : fcc_site_at(P, pb.x, pb.y, pb.z);
+    const int A = occ[a] & 7, B = occ[b] & 7;
+    const Word *row = sT + (A * 8 + B) * 8;
     Wide dw = Wide(0);
-    for (int m = 1; m <= P.nshells; ++m) {
-        const int base = (m - 1) * S * S;
-        for (int t = 0; t < c_fcc_n[m]; ++t) {
-            const int ja = fcc_neighbor(P, a, c_fcc_vec[m][t]);
-            if (ja != b) {
-                const int q = occ[ja] & 7;
-                if constexpr (IS_INT)
-                    dw += (long long)P.vi[base + B * S + q] - P.vi[base + A * S + q];
-                else
-                    dw += P.vf[base + B * S + q] - P.vf[base + A * S + q];
-            }
-            const int jb = fcc_neighbor(P, b, c_fcc_vec[m][t]);
-            if (jb != a) {
-                const int q = occ[jb] & 7;
-                if constexpr (IS_INT)
-                    dw += (long long)P.vi[base + A * S + q] - P.vi[base + B * S + q];
-                else
-                    dw += P.vf[base + A * S + q] - P.vf[base + B * S + q];
-            }
+    if (interior) {
+        // all 2 NV species loads first (independent, in flight together), then the sums
+        const int *da = sD + sub * 42, *db = sD + sN1[sub * 12 + dir] * 42;
+        int qa[NV], qb[NV];
+#pragma unroll
+        for (int t = 0; t < NV; ++t) qa[t] = occ[a + da[t]];
+#pragma unroll
+        for (int t = 0; t < NV; ++t) qb[t] = occ[b + db[t]];
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const Word v = row[fcc_shell_off(t) + (qa[t] & 7)];
+            if (t >= 12 || t != dir) dw += (Wide)v;
+        }
+#pragma unroll
+        for (int t = 0; t < NV; ++t) {
+            const Word v = row[fcc_shell_off(t) + (qb[t] & 7)];
+            if (t >= 12 || t != opp) dw -= (Wide)v;
+        }
+    } else {
+#pragma unroll 6
+        for (int t = 0; t < NV; ++t) {
+            const int3 v = fcc_unpack(sV[t]);
+            const Word e = row[fcc_shell_off(t) + (occ[fcc_site_at(P, pa.x + v.x, pa.y + v.y, pa.z + v.z)] & 7)];
+            if (t >= 12 || t != dir) dw += (Wide)e;
+        }
+#pragma unroll 6
+        for (int t = 0; t < NV; ++t) {
+            const int3 v = fcc_unpack(sV[t]);
+            const Word e = row[fcc_shell_off(t) + (occ[fcc_site_at(P, pb.x + v.x, pb.y + v.y, pb.z + v.z)] & 7)];
+            if (t >= 12 || t != opp) dw -= (Wide)e;
         }
     }
     // a dE beyond the int range is rejected anyway (the acceptance table is shorter)
@@ -153,9 +234,12 @@ __global__ void __launch_bounds__(256) k_fcc_pair_counts(const __grid_constant__
     const int N = 4 * P.nx * P.ny * P.nz, S = P.S;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int p = P.occ[s] & 7;
+        const int x = s % P.nx, y = (s / P.nx) % P.ny, z = (s / (P.nx * P.ny)) % P.nz, sub = s / (P.nx * P.ny * P.nz);
+        const FccPos ps = fcc_pos(sub, x, y, z);
         for (int m = 1; m <= P.nshells; ++m)
             for (int t = 0; t < c_fcc_n[m]; ++t) {
-                const int q = P.occ[fcc_neighbor(P, s, c_fcc_vec[m][t])] & 7;
+                const signed char *v = c_fcc_vec[m][t];
+                const int q = P.occ[fcc_site_at(P, ps.x + v[0], ps.y + v[1], ps.z + v[2])] & 7;
                 atomicAdd(&cnt[((m - 1) * S + p) * S + q], 1u);
             }
     }
@@ -222,7 +306,8 @@ smc_status fcc_params(const smc_lattice *lat, const smc_model *m, int8_t *occ, F
     P.nshells = m->nshells;
     P.NLx = lat->nx / 4;
     P.NLy = lat->ny / 4;
-    P.nA_cells = (lat->nx / 4) * (lat->ny / 4) * (lat->nz / 4);
+    P.NLz = lat->nz / 4;
+    P.nA_cells = P.NLx * P.NLy * P.NLz;
     P.occ = occ;
     const int n = m->nshells * P.S * P.S;
     for (int i = 0; i < n; ++i) {
@@ -232,6 +317,67 @@ smc_status fcc_params(const smc_lattice *lat, const smc_model *m, int8_t *occ, F
             P.vf[i] = m->v_f32[i];
     }
     return fcc_tables();
+}
+
+// The per-call table block of k_fcc_ministep (layout at kFccT .. kFccWords).
+smc_status fcc_sweep_tables(const smc_lattice *lat, const smc_model *m, std::vector<uint32_t> &w)
+{
+    std::vector<std::array<int, 3>> vec;
+    for (int sh = 1; sh <= 3; ++sh)
+        for (int x = -2; x <= 2; ++x)
+            for (int y = -2; y <= 2; ++y)
+                for (int z = -2; z <= 2; ++z)
+                    if (x * x + y * y + z * z == 2 * sh && ((x + y + z) & 1) == 0) vec.push_back({x, y, z});
+    bool ok = vec.size() == 42;
+    for (int i = 0; ok && i < 12; ++i)
+        for (int d = 0; d < 3; ++d) ok = ok && vec[11 - i][d] == -vec[i][d];
+    for (int t = 0; ok && t < 42; ++t) ok = fcc_shell_off(t) == 512 * ((t >= 12) + (t >= 18));
+    if (!ok) {
+        set_error("internal error: FCC shell table");
+        return SMC_ERR_STATE;
+    }
+    w.assign(kFccWords, 0u);
+    const int S = lat->nspecies;
+    for (int sh = 0; sh < m->nshells; ++sh)
+        for (int A = 0; A < S; ++A)
+            for (int B = 0; B < S; ++B)
+                for (int q = 0; q < S; ++q) {
+                    const int o = sh * 512 + (A * 8 + B) * 8 + q;
+                    const int ib = (sh * S + B) * S + q, ia = (sh * S + A) * S + q;
+                    if (m->kind == SMC_PAIR_I32) {
+                        w[o] = (uint32_t)(m->v_i32[ib] - m->v_i32[ia]);
+                    } else {
+                        const float d = m->v_f32[ib] - m->v_f32[ia];
+                        memcpy(&w[o], &d, 4);
+                    }
+                }
+    const long long NC = (long long)lat->nx * lat->ny * lat->nz;
+    for (int sub = 0; sub < 4; ++sub) {
+        const int b[3] = {(sub == 1 || sub == 2) ? 1 : 0, (sub == 1 || sub == 3) ? 1 : 0, (sub == 2 || sub == 3) ? 1 : 0};
+        for (int t = 0; t < 42; ++t) {
+            int q[3], dc[3];
+            for (int d = 0; d < 3; ++d) {
+                q[d] = b[d] + vec[t][d];
+                dc[d] = q[d] >= 0 ? q[d] / 2 : -((1 - q[d]) / 2);  // floor(q / 2)
+            }
+            const int par = ((q[0] & 1) << 2) | ((q[1] & 1) << 1) | (q[2] & 1);
+            const int nsub = par == 0 ? 0 : (par == 6 ? 1 : (par == 5 ? 2 : 3));
+            const long long delta = (nsub - sub) * NC + ((long long)dc[2] * lat->ny + dc[1]) * lat->nx + dc[0];
+            w[kFccD + sub * 42 + t] = (uint32_t)(int32_t)delta;
+            if (t < 12) w[kFccN1 + sub * 12 + t] = (uint32_t)nsub;
+        }
+    }
+    for (int t = 0; t < 42; ++t)
+        w[kFccVec + t] = (uint32_t)((vec[t][0] + 2) | ((vec[t][1] + 2) << 4) | ((vec[t][2] + 2) << 8));
+    return SMC_OK;
+}
+
+using FccKernel = void (*)(FccParams, int);
+
+template <bool IS_INT>
+FccKernel pick_fcc(int nshells)
+{
+    return nshells == 1 ? k_fcc_ministep<IS_INT, 1> : (nshells == 2 ? k_fcc_ministep<IS_INT, 2> : k_fcc_ministep<IS_INT, 3>);
 }
 
 }  // namespace
@@ -265,20 +411,31 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
             tinfo[t] = make_int2((int)tabs.size(), (int)tb.size());
             tabs.insert(tabs.end(), tb.begin(), tb.end());
         }
-    const size_t off_pn = (size_t)nc * 8, off_tab = off_pn + (size_t)nc * 8;
+    std::vector<uint32_t> words;
+    st = fcc_sweep_tables(lat, m, words);
+    if (st != SMC_OK) return st;
+    // workspace: [part_e | part_n | ministep tables | acceptance tables]
+    const size_t off_pn = (size_t)nc * 8, off_w = off_pn + (size_t)nc * 8, off_tab = off_w + words.size() * 4;
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_tab + tabs.size() * 4 + 16, &st);
     if (!scr) return st;
-    cudaError_t e = cudaMemsetAsync(scr, 0, off_tab, stream);
+    cudaError_t e = cudaMemsetAsync(scr, 0, off_w, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(FCC partial sums)");
+    e = cudaMemcpyAsync(scr + off_w, words.data(), words.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(FCC tables)");
     if (!tabs.empty()) {
         e = cudaMemcpyAsync(scr + off_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance tables)");
     }
+    P.tables = (const uint32_t *)(scr + off_w);
     P.tab = (const uint32_t *)(scr + off_tab);
     P.part_e = (double *)scr;
     P.part_n = (long long *)(scr + off_pn);
-    const int threads = 256, blocks = (nc + threads - 1) / threads;
-    auto kern = is_int ? k_fcc_ministep<true> : k_fcc_ministep<false>;
+    const int threads = 256;
+    P.n_int = (P.NLx > 2 && P.NLy > 2 && P.NLz > 2) ? (P.NLx - 2) * (P.NLy - 2) * (P.NLz - 2) : 0;
+    P.n_bnd = nc - P.n_int;
+    P.int_blocks = (P.n_int + threads - 1) / threads;
+    const int blocks = P.int_blocks + (P.n_bnd + threads - 1) / threads;
+    const FccKernel kern = is_int ? pick_fcc<true>(m->nshells) : pick_fcc<false>(m->nshells);
     for (int t = 0; t < nsweeps; ++t) {
         P.sweep = sweep0 + (uint64_t)t;
         P.beta = (float)(1.0 / kT[t]);

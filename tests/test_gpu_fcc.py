@@ -60,8 +60,10 @@ def test_init_matches_oracle(smc, dims, S):
 
 
 @pytest.mark.parametrize("dims,S,nsh,nsw", [((8, 8, 8), 2, 1, 3), ((12, 8, 16), 5, 2, 2), ((16, 16, 16), 8, 3, 1),
-                                            ((8, 12, 8), 3, 3, 2)])
+                                            ((8, 12, 8), 3, 3, 2), ((24, 24, 24), 5, 3, 1), ((28, 20, 24), 4, 2, 1)])
 def test_int_trajectory_bit_exact(smc, dims, S, nsh, nsw):
+    """Boxes of 2 link cells per axis run on the face path only; 24^3 and
+    28 x 20 x 24 put most trials on the interior path."""
     V = inputs.pair_int_coeffs(nsh + S, nsh, S)
     lat, occ, olat, ref = _state(smc, dims, S, 2)
     model = smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-4)
@@ -214,3 +216,49 @@ def test_unsupported_inputs_raise(smc):
         smc.fcc_sweep(lat, mlp, occ, 1, 0, 1, [0.05])
     with pytest.raises(smc.SMCError):
         smc.fcc_init_lattice(lat, [10, 10], 1, occ)
+
+
+def test_full_size_sampled_trials(smc):
+    """256^3 cubic cells (67M sites), FP32 3-shell quinary at 800 K: the
+    start state equals the oracle's everywhere; on it, mini-step 137 of
+    sweep 1 (any state is a valid input to one mini-step) gives at 400
+    sampled link cells (faces and interior) the oracle's dE of the same
+    trial (a from the schedule, b from its Philox word) and decision, and
+    the swap is applied where accepted."""
+    n, S, seed, sweep, k = 256, 5, 1, 1, 137
+    lat = smc.Lattice(n, n, n, S)
+    N = smc.fcc_nsites(lat)
+    V = inputs.pair_f32_coeffs(3, 3, S)
+    model = smc.Model(smc.PAIR_F32, 3, V)
+    kT = inputs.K_B_EV * 800.0
+    occ = torch.empty(N, dtype=torch.int8, device=dev())
+    smc.fcc_init_lattice(lat, inputs.equiatomic_counts(N, S), seed, occ)
+    olat, omodel = oracle.Lattice(n, n, n, S), oracle.Model(oracle.PAIR_F32, 3, V)
+    pre = oracle.fcc_init_lattice(olat, inputs.equiatomic_counts(N, S), seed)
+    assert np.array_equal(occ.cpu().numpy(), pre)
+    NL = n // 4
+    dE = torch.zeros(NL ** 3, dtype=torch.float32, device=dev())
+    acc = torch.zeros(NL ** 3, dtype=torch.uint8, device=dev())
+    smc.fcc_ministep_trace(lat, model, occ, seed, sweep, k, kT, dE=dE, acc=acc)
+    smc.check()
+    post, g_dE, g_acc = occ.cpu().numpy(), dE.cpu().numpy(), acc.cpu().numpy()
+    v1 = oracle.fcc_shell_vectors(1)
+    rng = np.random.default_rng(5)
+    cells = [(0, 0, 0), (NL - 1, NL - 1, NL - 1), (0, 5, 9), (NL - 1, 2, 30), (3, 0, 4), (7, NL - 1, 1)]
+    cells += [tuple(int(v) for v in rng.integers(0, NL, 3)) for _ in range(394)]
+    dx, dy, dz, sub = k % 4, (k // 4) % 4, (k // 16) % 4, k // 64
+    for cx, cy, cz in cells:
+        c = (cz * NL + cy) * NL + cx
+        a = ((sub * n + 4 * cz + dz) * n + 4 * cy + dy) * n + 4 * cx + dx
+        w = oracle.philox4x32_10([a & 0xFFFFFFFF, 0, sweep, 0], [seed, 0])
+        b = oracle.fcc_neighbor(olat, a, v1[(int(w[1]) * 12) >> 32])
+        ref = oracle.fcc_delta_e(olat, omodel, pre, a, b)
+        assert abs(float(g_dE[c]) - ref) <= DE_TOL_EV, (c, float(g_dE[c]), ref)
+        u = (float(int(w[0]) & ((1 << 29) - 1)) + 0.5) / 2.0 ** 29
+        want = ref <= 0 or u < math.exp(-ref / kT)
+        if abs(ref + kT * math.log(u)) > DE_TOL_EV:
+            assert bool(g_acc[c]) == want, c
+        if g_acc[c]:
+            assert post[a] == pre[b] and post[b] == pre[a]
+        else:
+            assert post[a] == pre[a] and post[b] == pre[b]
