@@ -292,40 +292,52 @@ static int has_mlp(const orc_model *m)
     return m->kind == ORC_MLP || m->kind == ORC_PAIR_F32_MLP;
 }
 
+#define ORC_MAX_NEIGH 24 /* largest shell of either lattice (FCC shell 3) */
+
 /* Local energy of the qSRO model (Sec. IV-B, Eq. quadratic_local_SRO):
  *   E_i = sum_{m, p' <= p} V_m^{pp'} pi_m^{pp'} + sum_{m, p} W_m^p (pi_m^{pp})^2 + C,
  *   pi_m^{pp'} = n_m^{pp'} / sum_{pp'} n_m^{pp'},
  * with n_m^{pp'} the number of pairs (i, j), j in shell m of i, whose two
  * species are {p, p'} (counted once per unordered pair, p' <= p).  The
  * linear sum runs over p' <= p, same-element pairs included; the constant
- * lambda sum W^2 (a training regulariser) is left out. */
+ * lambda sum W^2 (a training regulariser) is left out.
+ * qsro_shell_terms: the shell-sh part of E_i from the species q[0..z-1] of
+ * the z shell-sh neighbours of a site of species si (any lattice). */
+static double qsro_shell_terms(const orc_model *m, int S, int sh, int si, const int *q, int z)
+{
+    double n[ORC_MAX_SPECIES][ORC_MAX_SPECIES];
+    memset(n, 0, sizeof n);
+    double total = 0.0;
+    for (int t = 0; t < z; ++t) {
+        int p = si, r = q[t];
+        if (r > p) {
+            int tmp = p;
+            p = r;
+            r = tmp;
+        }
+        n[p][r] += 1.0;
+        total += 1.0;
+    }
+    double e = 0.0;
+    for (int p = 0; p < S; ++p)
+        for (int r = 0; r <= p; ++r) e += (double)m->v_f32[((sh - 1) * S + p) * S + r] * (n[p][r] / total);
+    for (int p = 0; p < S; ++p) {
+        double pi = n[p][p] / total;
+        e += (double)m->qsro_w[(sh - 1) * S + p] * pi * pi;
+    }
+    return e;
+}
+
 static double qsro_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i)
 {
-    int S = lat->nspecies;
     double e = m->qsro_c;
+    int q[ORC_MAX_NEIGH];
     for (int sh = 1; sh <= m->nshells; ++sh) {
-        double n[ORC_MAX_SPECIES][ORC_MAX_SPECIES];
-        memset(n, 0, sizeof n);
-        double total = 0.0;
         for (int t = 0; t < g_shell_n[sh]; ++t) {
             const int *v = g_shell_v[sh][t];
-            int64_t j = orc_neighbor(lat, i, v[0], v[1], v[2]);
-            int p = occ[i], q = occ[j];
-            if (q > p) {
-                int tmp = p;
-                p = q;
-                q = tmp;
-            }
-            n[p][q] += 1.0;
-            total += 1.0;
+            q[t] = occ[orc_neighbor(lat, i, v[0], v[1], v[2])];
         }
-        for (int p = 0; p < S; ++p)
-            for (int q = 0; q <= p; ++q)
-                e += (double)m->v_f32[((sh - 1) * S + p) * S + q] * (n[p][q] / total);
-        for (int p = 0; p < S; ++p) {
-            double pi = n[p][p] / total;
-            e += (double)m->qsro_w[(sh - 1) * S + p] * pi * pi;
-        }
+        e += qsro_shell_terms(m, lat->nspecies, sh, occ[i], q, g_shell_n[sh]);
     }
     return e;
 }
@@ -959,7 +971,8 @@ int orc_energy_grad(const orc_lattice *lat, const orc_model *m, const int8_t *oc
 }
 
 /* ======================================================================== */
-/* FCC lattice (the paper's lattice, Sec. IV-C and Sec. V-C), pair models.   */
+/* FCC lattice (the paper's lattice, Sec. IV-C and Sec. V-C), pair and qSRO */
+/* models.                                                                   */
 /* nx x ny x nz cubic cells (each >= 1), 4 sites per cell at the half-unit   */
 /* offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3); site id     */
 /* s = ((sub*nz + z)*ny + y)*nx + x, N = 4 nx ny nz.  Shells 1-3: 12 vectors */
@@ -1054,16 +1067,38 @@ int orc_fcc_schedule(const orc_lattice *lat, int32_t L[3])
 
 static int fcc_model_ok(const orc_model *m)
 {
-    if (m->kind != ORC_PAIR_I32 && m->kind != ORC_PAIR_F32) return 0;
+    if (m->kind != ORC_PAIR_I32 && m->kind != ORC_PAIR_F32 && m->kind != ORC_QSRO) return 0;
     if (m->nshells < 1 || m->nshells > 3) return 0;
     if (m->kind == ORC_PAIR_I32) return m->v_i32 && m->unit_ev > 0.0;
+    if (m->kind == ORC_QSRO) return m->v_f32 && m->qsro_w;
     return m->v_f32 != NULL;
 }
 
-/* Twice the pair site energy (integer models) or the site energy (FP). */
+/* qSRO local energy (Eq. quadratic_local_SRO) with the FCC shells (12, 6, 24
+ * neighbours). */
+static double fcc_qsro_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i)
+{
+    double e = m->qsro_c;
+    int q[ORC_MAX_NEIGH];
+    for (int sh = 1; sh <= m->nshells; ++sh) {
+        for (int t = 0; t < g_fcc_n[sh]; ++t) {
+            const int *v = g_fcc_v[sh][t];
+            q[t] = occ[orc_fcc_neighbor(lat, i, v[0], v[1], v[2])];
+        }
+        e += qsro_shell_terms(m, lat->nspecies, sh, occ[i], q, g_fcc_n[sh]);
+    }
+    return e;
+}
+
+/* Pair models: the site energy, and twice it exactly for integer models
+ * (e2).  qSRO: the local energy E_i. */
 static double fcc_site_energy(const orc_lattice *lat, const orc_model *m, const int8_t *occ, int64_t i,
                               int64_t *e2)
 {
+    if (m->kind == ORC_QSRO) {
+        if (e2) *e2 = 0;
+        return fcc_qsro_site_energy(lat, m, occ, i);
+    }
     int S = lat->nspecies;
     int64_t acc2 = 0;
     double acc = 0.0;
