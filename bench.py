@@ -205,9 +205,14 @@ def main():
                     help="run the qSRO workload (800 K) on an N^3 box once, for ncu captures")
     ap.add_argument("--profile-fcc", type=int, default=0,
                     help="run FCC sweeps (800 K) on an N^3 box of cubic cells once, for ncu captures")
+    ap.add_argument("--profile-fcc-qsro", type=int, default=0,
+                    help="as --profile-fcc with the qSRO workload (Fe29Co29Ni28Al7Ti7, 2 shells)")
     args = ap.parse_args()
     if args.profile_fcc:
         profile_fcc(args.profile_fcc, args.profile_sweeps)
+        return
+    if args.profile_fcc_qsro:
+        profile_fcc(args.profile_fcc_qsro, args.profile_sweeps, qsro=True)
         return
     if args.probe_sfu:
         probe_sfu()
@@ -405,28 +410,35 @@ def qsro_setup(smc, n: int, dev):
     return lat, occ, model, inputs.K_B_EV * c4["T"]
 
 
-def fcc_setup(smc, n: int, dev):
-    """FCC workload: N^3 cubic cells (4 N^3 sites), equiatomic quinary, FP32
-    3-shell pair coefficients (seed 3), 800 K."""
+def fcc_setup(smc, n: int, dev, qsro: bool = False):
+    """FCC workloads, N^3 cubic cells (4 N^3 sites), 800 K: equiatomic
+    quinary with FP32 3-shell pair coefficients (seed 3); or (qsro) the
+    paper's Fe29Co29Ni28Al7Ti7 with 2-shell qSRO parameters (seed 7)."""
     import torch
     S = 5
     lat = smc.Lattice(n, n, n, S)
-    occ = torch.empty(smc.fcc_nsites(lat), dtype=torch.int8, device=dev)
-    smc.fcc_init_lattice(lat, inputs.equiatomic_counts(smc.fcc_nsites(lat), S), 1, occ)
-    model = smc.Model(smc.PAIR_F32, 3, inputs.pair_f32_coeffs(3, 3, S))
+    N = smc.fcc_nsites(lat)
+    occ = torch.empty(N, dtype=torch.int8, device=dev)
+    if qsro:
+        smc.fcc_init_lattice(lat, inputs.fraction_counts(N, inputs.HEA_FRACTIONS), 1, occ)
+        V, W, C = inputs.qsro_coeffs(QSRO_SEED, 2, S)
+        model = smc.Model(smc.QSRO_F32, 2, V, qsro_w=W, qsro_c=C)
+    else:
+        smc.fcc_init_lattice(lat, inputs.equiatomic_counts(N, S), 1, occ)
+        model = smc.Model(smc.PAIR_F32, 3, inputs.pair_f32_coeffs(3, 3, S))
     return lat, occ, model, inputs.K_B_EV * 800.0
 
 
-def profile_fcc(n: int, nsweeps: int):
-    """FCC sweeps on an N^3 box, for ncu captures (-k regex:k_fcc_ministep)."""
+def profile_fcc(n: int, nsweeps: int, qsro: bool = False):
+    """FCC sweeps on an N^3 box, for ncu captures (-k regex:k_fcc_)."""
     from paper_2604_08250_gb300 import build as _b
     from paper_2604_08250_gb300 import smc
     _b.build()
-    lat, occ, model, kT = fcc_setup(smc, n, "cuda")
+    lat, occ, model, kT = fcc_setup(smc, n, "cuda", qsro=qsro)
     smc.fcc_sweep(lat, model, occ, 1, 0, nsweeps, kT)
     smc.check()
     del occ
-    print(json.dumps({"profile_fcc": n, "sweeps": nsweeps, "ok": True}))
+    print(json.dumps({"profile_fcc": n, "qsro": qsro, "sweeps": nsweeps, "ok": True}))
 
 
 def profile_qsro(n: int, nsweeps: int):
@@ -633,6 +645,20 @@ def run_extras(smc, torch, dev, pk):
     ef = torch.zeros(1, dtype=torch.float64, device=dev)
     out["fcc_energy_256"] = {"ms": timed(lambda: smc.fcc_energy(latf, fm, occf, ef), reps=3)}
     del occf
+    # the paper's workload shape: qSRO on the FCC lattice, Fe29Co29Ni28Al7Ti7, 2 shells, 256^3 cells, 800 K
+    latq, occq, qm, kTq = fcc_setup(smc, 256, dev, qsro=True)
+    nq = torch.zeros(1, dtype=torch.int64, device=dev)
+    nswq = 2
+    msq = timed(lambda: smc.fcc_sweep(latq, qm, occq, 1, 0, nswq, kTq, n_acc=nq), reps=1)
+    Nq = smc.fcc_nsites(latq)
+    out["fcc_qsro_256"] = {"cells": [256] * 3, "sites": Nq, "shells": 2, "composition": "Fe29Co29Ni28Al7Ti7",
+                           "sweeps_per_launch": nswq, "launches_per_sweep": 256, "ms_per_sweep": msq / nswq,
+                           "attempts_per_s": Nq * nswq / (msq * 1e-3),
+                           "accept_rate": float(nq.item()) / (2 * Nq * nswq),
+                           "paper_context_attempts_per_s": {"H100 SMC-X": 3.71e7, "H100 SMC-AI": 1.87e7}}
+    eq = torch.zeros(1, dtype=torch.float64, device=dev)
+    out["fcc_qsro_energy_256"] = {"ms": timed(lambda: smc.fcc_energy(latq, qm, occq, eq), reps=3)}
+    del occq
     # dE/dtheta of the pair + MLP energy at 512^3 (one configuration)
     c5 = inputs.CONFIG5
     n5 = c5["cells"][0]

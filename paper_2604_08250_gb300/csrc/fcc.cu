@@ -65,7 +65,18 @@ struct FccParams {
     uint8_t *acc_out;
     int vi[kMaxShells * kMaxSpecies * kMaxSpecies];
     float vf[kMaxShells * kMaxSpecies * kMaxSpecies];
+    float wq[kMaxShells * kMaxSpecies];  // qSRO W_m^p
+    double qc;                           // qSRO C
+    uint32_t *qcache;                    // qSRO: own-species counts per shell of every site (bytes 0-2)
 };
+
+// qSRO per-call tables (32-bit words): Dz[m][A][B][q] = (V_m(B,q) - V_m(A,q)) / z_m,
+// Wz[m][p] = W_m^p / z_m^2, per partner direction the zone entries (half-unit
+// offset index w = (x+3) + 7 (y+3) + 49 (z+3), shell to a at bit 9, shell to
+// b at bit 11), the offset index of each first-shell vector, and the index
+// deltas of every offset per sublattice.
+constexpr int kQZmax = 58, kQT = kMaxShells * 512, kQW = kQT, kQZ = kQW + kMaxShells * 8, kQV1 = kQZ + 12 * kQZmax,
+              kQDel = kQV1 + 12, kQWords = kQDel + 4 * 343;
 
 __constant__ signed char c_fcc_vec[4][24][3];  // shells 1-3 at [1..3]
 __constant__ int c_fcc_n[4];
@@ -209,6 +220,163 @@ __global__ void __launch_bounds__(256) k_fcc_ministep(const __grid_constant__ Fc
     if (P.acc_out) P.acc_out[c] = acc ? 1 : 0;
 }
 
+__device__ __forceinline__ int3 fcc_woff(int w) { return make_int3(w % 7 - 3, (w / 7) % 7 - 3, w / 49 - 3); }
+
+// qSRO cache: for every site, the number of its shell-m neighbours of its own
+// species, in byte m-1.
+__global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ FccParams P)
+{
+    const int N = 4 * P.nx * P.ny * P.nz;
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+        const int p = P.occ[s] & 7;
+        const int x = s % P.nx, y = (s / P.nx) % P.ny, z = (s / (P.nx * P.ny)) % P.nz, sub = s / (P.nx * P.ny * P.nz);
+        const FccPos ps = fcc_pos(sub, x, y, z);
+        uint32_t q = 0;
+        for (int m = 1; m <= P.nshells; ++m)
+            for (int t = 0; t < c_fcc_n[m]; ++t) {
+                const signed char *v = c_fcc_vec[m][t];
+                if ((P.occ[fcc_site_at(P, ps.x + v[0], ps.y + v[1], ps.z + v[2])] & 7) == p) q += 1u << (8 * (m - 1));
+            }
+        P.qcache[s] = q;
+    }
+}
+
+// One qSRO trial per thread (Eq. quadratic_local_SRO with the FCC shells).
+// Site j's energy changes only through the species of its neighbours a and
+// b: with a in shell ma of j and b in shell mb (0 = neither),
+//   linear part  D_ma(s_j)/z_ma - D_mb(s_j)/z_mb,  D_m(q) = V_m(B,q) - V_m(A,q),
+//   W part       (s_j = A or B, ma != mb) from j's cached own-species counts.
+// a and b change their own species: their linear parts sum to the same
+// D terms again (V symmetric), and their W parts use the counts of A and B
+// around each (b counted in a's shell 1 and a in b's).  C cancels.
+template <int NSH>
+__global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant__ FccParams P, int k)
+{
+    constexpr int NZ = NSH == 1 ? 18 : (NSH == 2 ? 26 : 58);
+    __shared__ uint32_t sm[kQWords];
+    for (int i = threadIdx.x; i < kQWords; i += blockDim.x) sm[i] = __ldg(P.tables + i);
+    __syncthreads();
+    const float *sT = reinterpret_cast<const float *>(sm);
+    const float *sW = reinterpret_cast<const float *>(sm + kQW);
+    const int *sZ = reinterpret_cast<const int *>(sm + kQZ);
+    const int *sV1 = reinterpret_cast<const int *>(sm + kQV1);
+
+    const int dx = k & 3, dy = (k >> 2) & 3, dz = (k >> 4) & 3, sub = k >> 6;
+    const bool interior = (int)blockIdx.x < P.int_blocks;
+    int3 cc;
+    if (interior) {
+        const int i = blockIdx.x * blockDim.x + threadIdx.x;
+        if (i >= P.n_int) return;
+        const int wx = P.NLx - 2, wy = P.NLy - 2;
+        cc = make_int3(1 + i % wx, 1 + (i / wx) % wy, 1 + i / (wx * wy));
+    } else {
+        const int j = (blockIdx.x - P.int_blocks) * blockDim.x + threadIdx.x;
+        if (j >= P.n_bnd) return;
+        cc = fcc_face_cell(j, P.NLx, P.NLy, P.NLz);
+    }
+    const int c = (cc.z * P.NLy + cc.y) * P.NLx + cc.x;
+    const int x = 4 * cc.x + dx, y = 4 * cc.y + dy, z = 4 * cc.z + dz;
+    const int a = ((sub * P.nz + z) * P.ny + y) * P.nx + x;
+    const U4 w4 = philox10(U4{(uint32_t)a, P.replica, (uint32_t)P.sweep, (uint32_t)(P.sweep >> 32)}, (uint32_t)P.seed,
+                           (uint32_t)(P.seed >> 32));
+    const uint32_t r = w4.x & kRMask;
+    const int dir = (int)(((uint64_t)w4.y * 12u) >> 32);
+    const FccPos pa = fcc_pos(sub, x, y, z);
+    const int *del = reinterpret_cast<const int *>(sm + kQDel) + sub * 343;
+    const int wb = sV1[dir];
+    const int3 v1 = fcc_woff(wb);
+    const int b = interior ? a + del[wb] : fcc_site_at(P, pa.x + v1.x, pa.y + v1.y, pa.z + v1.z);
+    int8_t *occ = P.occ;
+    uint32_t *Qc = P.qcache;
+    const int A = occ[a] & 7, B = occ[b] & 7;
+    const int *zone = sZ + dir * kQZmax;
+    // packed per-shell counts (byte m-1): species A / B around a and around b
+    uint32_t cAa = 0, cBa = 1u, cAb = 1u, cBb = 0;  // b (species B) is in a's shell 1, a (A) in b's
+    float dE = 0.f;
+    if (A != B) {
+        const float *row = sT + (A * 8 + B) * 8;
+        float lin = 0.f, wz = 0.f;
+#pragma unroll 2
+        for (int i = 0; i < NZ; ++i) {
+            const int e = zone[i];
+            const int w = e & 511, ma = (e >> 9) & 3, mb = (e >> 11) & 3;
+            int j;
+            if (interior) {
+                j = a + del[w];
+            } else {
+                const int3 d = fcc_woff(w);
+                j = fcc_site_at(P, pa.x + d.x, pa.y + d.y, pa.z + d.z);
+            }
+            const int sj = occ[j] & 7;
+            const uint32_t isA = sj == A, isB = sj == B;
+            if (ma) {
+                lin += row[(ma - 1) * 512 + sj];
+                cAa += isA << (8 * (ma - 1));
+                cBa += isB << (8 * (ma - 1));
+            }
+            if (mb) {
+                lin -= row[(mb - 1) * 512 + sj];
+                cAb += isA << (8 * (mb - 1));
+                cBb += isB << (8 * (mb - 1));
+            }
+            if ((isA | isB) && ma != mb) {
+                const uint32_t q = Qc[j];
+                const int p = isA ? A : B;
+                if (ma) {
+                    const int n = (q >> (8 * (ma - 1))) & 255;
+                    wz += sW[(ma - 1) * 8 + p] * (float)(isA ? 1 - 2 * n : 2 * n + 1);
+                }
+                if (mb) {
+                    const int n = (q >> (8 * (mb - 1))) & 255;
+                    wz += sW[(mb - 1) * 8 + p] * (float)(isA ? 2 * n + 1 : 1 - 2 * n);
+                }
+            }
+        }
+        float wa = 0.f, wbb = 0.f;
+#pragma unroll
+        for (int m = 0; m < NSH; ++m) {
+            const int nAa = (cAa >> (8 * m)) & 255, nBa = ((cBa >> (8 * m)) & 255) - (m == 0 ? 1 : 0);
+            const int nAb = ((cAb >> (8 * m)) & 255) - (m == 0 ? 1 : 0), nBb = (cBb >> (8 * m)) & 255;
+            wa += sW[m * 8 + B] * (float)(nBa * nBa) - sW[m * 8 + A] * (float)(nAa * nAa);
+            wbb += sW[m * 8 + A] * (float)(nAb * nAb) - sW[m * 8 + B] * (float)(nBb * nBb);
+        }
+        dE = 2.f * lin + wa + wbb + wz;
+    }
+    const bool acc = metropolis<false>(dE, r, P.beta, P.tab, P.tinfo);
+    if (acc) {
+        if (A != B) {
+            occ[a] = (int8_t)B;
+            occ[b] = (int8_t)A;
+            Qc[a] = cBa - 1u;  // a now B: B neighbours other than b
+            Qc[b] = cAb - 1u;
+            for (int i = 0; i < NZ; ++i) {
+                const int e = zone[i];
+                const int w = e & 511, ma = (e >> 9) & 3, mb = (e >> 11) & 3;
+                if (ma == mb) continue;
+                int j;
+                if (interior) {
+                    j = a + del[w];
+                } else {
+                    const int3 d = fcc_woff(w);
+                    j = fcc_site_at(P, pa.x + d.x, pa.y + d.y, pa.z + d.z);
+                }
+                const int sj = occ[j] & 7;
+                if (sj != A && sj != B) continue;
+                int dq = 0;  // A sites lose a (shell ma) and gain b (shell mb); B sites the reverse
+                if (ma) dq += (sj == A ? -1 : 1) * (1 << (8 * (ma - 1)));
+                if (mb) dq += (sj == A ? 1 : -1) * (1 << (8 * (mb - 1)));
+                Qc[j] += (uint32_t)dq;
+            }
+        }
+        if (P.part_e) {
+            P.part_e[c] += (double)dE;
+            P.part_n[c] += 1;
+        }
+    }
+    if (P.dE_out) P.dE_out[c] = dE;
+    if (P.acc_out) P.acc_out[c] = acc ? 1 : 0;
+}
+
 // e_acc += sum of part_e, n_acc += sum of part_n, in link-cell order.
 __global__ void k_fcc_reduce(const double *part_e, const long long *part_n, int n, double *e_acc, long long *n_acc)
 {
@@ -225,27 +393,38 @@ __global__ void k_fcc_reduce(const double *part_e, const long long *part_n, int 
 
 // Ordered pair counts n_m^{pq} (each site's shell-m neighbours), per-block
 // shared counters flushed with 64-bit atomics.
+// With sq non-null also Q_m^p = sum over sites of species p of the squared
+// number of their shell-m neighbours of species p (the qSRO W term).
 __global__ void __launch_bounds__(256) k_fcc_pair_counts(const __grid_constant__ FccParams P,
-                                                         unsigned long long *counts)
+                                                         unsigned long long *counts, unsigned long long *sq)
 {
     __shared__ unsigned int cnt[kMaxShells * kMaxSpecies * kMaxSpecies];
+    __shared__ unsigned int csq[kMaxShells * kMaxSpecies];
     for (int i = threadIdx.x; i < kMaxShells * kMaxSpecies * kMaxSpecies; i += blockDim.x) cnt[i] = 0;
+    for (int i = threadIdx.x; i < kMaxShells * kMaxSpecies; i += blockDim.x) csq[i] = 0;
     __syncthreads();
     const int N = 4 * P.nx * P.ny * P.nz, S = P.S;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
         const int p = P.occ[s] & 7;
         const int x = s % P.nx, y = (s / P.nx) % P.ny, z = (s / (P.nx * P.ny)) % P.nz, sub = s / (P.nx * P.ny * P.nz);
         const FccPos ps = fcc_pos(sub, x, y, z);
-        for (int m = 1; m <= P.nshells; ++m)
+        for (int m = 1; m <= P.nshells; ++m) {
+            unsigned int own = 0;
             for (int t = 0; t < c_fcc_n[m]; ++t) {
                 const signed char *v = c_fcc_vec[m][t];
                 const int q = P.occ[fcc_site_at(P, ps.x + v[0], ps.y + v[1], ps.z + v[2])] & 7;
                 atomicAdd(&cnt[((m - 1) * S + p) * S + q], 1u);
+                own += q == p;
             }
+            if (sq && own) atomicAdd(&csq[(m - 1) * kMaxSpecies + p], own * own);
+        }
     }
     __syncthreads();
     for (int i = threadIdx.x; i < P.nshells * S * S; i += blockDim.x)
         if (cnt[i]) atomicAdd(counts + i, (unsigned long long)cnt[i]);
+    if (sq)
+        for (int i = threadIdx.x; i < kMaxShells * kMaxSpecies; i += blockDim.x)
+            if (csq[i]) atomicAdd(sq + i, (unsigned long long)csq[i]);
 }
 
 // E = 1/2 sum_m sum_{p,q} V_m(p, q) n_m^{pq}, exactly in int64 (integer
@@ -261,6 +440,15 @@ __global__ void k_fcc_energy_finish(const __grid_constant__ FccParams P, const u
         tot /= 2;  // every bond counted from both ends
         if (e_int) *e_int = tot;
         if (e) *e = (double)tot * unit;
+    } else if (e && P.qcache) {  // qSRO: E = N C + sum V n / z_m + sum W Q / z_m^2
+        const double z[3] = {12.0, 6.0, 24.0};
+        const unsigned long long *sq = counts + kMaxShells * 64;
+        double tot = 4.0 * P.nx * P.ny * P.nz * P.qc;
+        for (int i = 0; i < n; ++i) tot += (double)P.vf[i] * (double)counts[i] / z[i / (P.S * P.S)];
+        for (int m = 0; m < P.nshells; ++m)
+            for (int p = 0; p < P.S; ++p)
+                tot += (double)P.wq[m * P.S + p] * (double)sq[m * kMaxSpecies + p] / (z[m] * z[m]);
+        *e = tot;
     } else if (e) {
         double tot = 0.0;
         for (int i = 0; i < n; ++i) tot += (double)P.vf[i] * (double)counts[i];
@@ -316,7 +504,81 @@ smc_status fcc_params(const smc_lattice *lat, const smc_model *m, int8_t *occ, F
         else
             P.vf[i] = m->v_f32[i];
     }
+    if (m->kind == SMC_QSRO_F32) {
+        for (int i = 0; i < m->nshells * P.S; ++i) P.wq[i] = m->qsro_w[i];
+        P.qc = m->qsro_c;
+    }
     return fcc_tables();
+}
+
+// Shell of a half-unit offset (1-3 within nshells, else 0).
+int fcc_shell_of(int x, int y, int z, int nshells)
+{
+    const int d = x * x + y * y + z * z;
+    if (d == 0 || (d & 1) || ((x + y + z) & 1)) return 0;
+    return d / 2 <= nshells ? d / 2 : 0;
+}
+
+// The per-call table block of k_fcc_qsro_ministep (layout at kQT .. kQWords).
+smc_status fcc_qsro_tables(const smc_lattice *lat, const smc_model *m, std::vector<uint32_t> &w)
+{
+    const int S = lat->nspecies, nsh = m->nshells;
+    const double z[3] = {12.0, 6.0, 24.0};
+    w.assign(kQWords, 0u);
+    for (int sh = 0; sh < nsh; ++sh) {
+        for (int A = 0; A < S; ++A)
+            for (int B = 0; B < S; ++B)
+                for (int q = 0; q < S; ++q) {
+                    const float d = (float)(((double)m->v_f32[(sh * S + B) * S + q] - m->v_f32[(sh * S + A) * S + q]) / z[sh]);
+                    memcpy(&w[sh * 512 + (A * 8 + B) * 8 + q], &d, 4);
+                }
+        for (int p = 0; p < S; ++p) {
+            const float v = (float)((double)m->qsro_w[sh * S + p] / (z[sh] * z[sh]));
+            memcpy(&w[kQW + sh * 8 + p], &v, 4);
+        }
+    }
+    auto widx = [](int x, int y, int z) { return (x + 3) + 7 * (y + 3) + 49 * (z + 3); };
+    std::vector<std::array<int, 3>> v1;
+    for (int x = -2; x <= 2; ++x)
+        for (int y = -2; y <= 2; ++y)
+            for (int zz = -2; zz <= 2; ++zz)
+                if (x * x + y * y + zz * zz == 2 && ((x + y + zz) & 1) == 0) v1.push_back({x, y, zz});
+    const int want = nsh == 1 ? 18 : (nsh == 2 ? 26 : 58);
+    for (int d = 0; d < 12; ++d) {
+        w[kQV1 + d] = (uint32_t)widx(v1[d][0], v1[d][1], v1[d][2]);
+        int n = 0;
+        for (int x = -3; x <= 3; ++x)
+            for (int y = -3; y <= 3; ++y)
+                for (int zz = -3; zz <= 3; ++zz) {
+                    if ((x == 0 && y == 0 && zz == 0) || (x == v1[d][0] && y == v1[d][1] && zz == v1[d][2])) continue;
+                    const int ma = fcc_shell_of(x, y, zz, nsh);
+                    const int mb = fcc_shell_of(x - v1[d][0], y - v1[d][1], zz - v1[d][2], nsh);
+                    if (!ma && !mb) continue;
+                    if (n < kQZmax) w[kQZ + d * kQZmax + n] = (uint32_t)(widx(x, y, zz) | (ma << 9) | (mb << 11));
+                    ++n;
+                }
+        if (n != want) {
+            set_error("internal error: FCC qSRO zone has %d sites (want %d)", n, want);
+            return SMC_ERR_STATE;
+        }
+    }
+    const long long NC = (long long)lat->nx * lat->ny * lat->nz;
+    for (int sub = 0; sub < 4; ++sub) {
+        const int b[3] = {(sub == 1 || sub == 2) ? 1 : 0, (sub == 1 || sub == 3) ? 1 : 0, (sub == 2 || sub == 3) ? 1 : 0};
+        for (int x = -3; x <= 3; ++x)
+            for (int y = -3; y <= 3; ++y)
+                for (int zz = -3; zz <= 3; ++zz) {
+                    if ((x + y + zz) & 1) continue;
+                    const int q[3] = {b[0] + x, b[1] + y, b[2] + zz};
+                    int dc[3];
+                    for (int k = 0; k < 3; ++k) dc[k] = q[k] >= 0 ? q[k] / 2 : -((1 - q[k]) / 2);  // floor(q / 2)
+                    const int par = ((q[0] & 1) << 2) | ((q[1] & 1) << 1) | (q[2] & 1);
+                    const int nsub = par == 0 ? 0 : (par == 6 ? 1 : (par == 5 ? 2 : 3));
+                    const long long delta = (nsub - sub) * NC + ((long long)dc[2] * lat->ny + dc[1]) * lat->nx + dc[0];
+                    w[kQDel + sub * 343 + widx(x, y, zz)] = (uint32_t)(int32_t)delta;
+                }
+    }
+    return SMC_OK;
 }
 
 // The per-call table block of k_fcc_ministep (layout at kFccT .. kFccWords).
@@ -411,12 +673,15 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
             tinfo[t] = make_int2((int)tabs.size(), (int)tb.size());
             tabs.insert(tabs.end(), tb.begin(), tb.end());
         }
+    const bool is_qsro = m->kind == SMC_QSRO_F32;
     std::vector<uint32_t> words;
-    st = fcc_sweep_tables(lat, m, words);
+    st = is_qsro ? fcc_qsro_tables(lat, m, words) : fcc_sweep_tables(lat, m, words);
     if (st != SMC_OK) return st;
-    // workspace: [part_e | part_n | ministep tables | acceptance tables]
+    // workspace: [part_e | part_n | ministep tables | acceptance tables | qSRO count cache]
     const size_t off_pn = (size_t)nc * 8, off_w = off_pn + (size_t)nc * 8, off_tab = off_w + words.size() * 4;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_tab + tabs.size() * 4 + 16, &st);
+    const size_t off_q = (off_tab + tabs.size() * 4 + 255) / 256 * 256;
+    const size_t N = 4ull * lat->nx * lat->ny * lat->nz;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_q + (is_qsro ? N * 4 : 16), &st);
     if (!scr) return st;
     cudaError_t e = cudaMemsetAsync(scr, 0, off_w, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(FCC partial sums)");
@@ -435,7 +700,16 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.n_bnd = nc - P.n_int;
     P.int_blocks = (P.n_int + threads - 1) / threads;
     const int blocks = P.int_blocks + (P.n_bnd + threads - 1) / threads;
-    const FccKernel kern = is_int ? pick_fcc<true>(m->nshells) : pick_fcc<false>(m->nshells);
+    const FccKernel kern = is_qsro ? (m->nshells == 1 ? k_fcc_qsro_ministep<1>
+                                                       : (m->nshells == 2 ? k_fcc_qsro_ministep<2> : k_fcc_qsro_ministep<3>))
+                                   : (is_int ? pick_fcc<true>(m->nshells) : pick_fcc<false>(m->nshells));
+    if (is_qsro) {  // the count cache, from the occupancy at the start of every call
+        P.qcache = (uint32_t *)(scr + off_q);
+        const int cb = (int)std::max<size_t>(1, std::min<size_t>((N + 255) / 256, (size_t)ws->num_sms * 16));
+        k_fcc_qsro_cache<<<cb, 256, 0, stream>>>(P);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "k_fcc_qsro_cache");
+    }
     for (int t = 0; t < nsweeps; ++t) {
         P.sweep = sweep0 + (uint64_t)t;
         P.beta = (float)(1.0 / kT[t]);
@@ -464,14 +738,17 @@ smc_status launch_fcc_energy(const smc_lattice *lat, const smc_model *m, const i
     static FccParams P;
     st = fcc_params(lat, m, const_cast<int8_t *>(occ), P);
     if (st != SMC_OK) return st;
-    unsigned long long *cnt =
-        (unsigned long long *)workspace_scratch(ws, sizeof(unsigned long long) * kMaxShells * 64, &st);
+    // [ordered pair counts n_m^{pq} | qSRO squared own-species counts Q_m^p]
+    const size_t cbytes = sizeof(unsigned long long) * kMaxShells * (64 + kMaxSpecies);
+    unsigned long long *cnt = (unsigned long long *)workspace_scratch(ws, cbytes, &st);
     if (!cnt) return st;
-    cudaError_t err = cudaMemsetAsync(cnt, 0, sizeof(unsigned long long) * kMaxShells * 64, stream);
+    cudaError_t err = cudaMemsetAsync(cnt, 0, cbytes, stream);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync(FCC counts)");
+    const bool is_qsro = m->kind == SMC_QSRO_F32;
+    if (is_qsro) P.qcache = reinterpret_cast<uint32_t *>(cnt);  // marks the qSRO energy (not dereferenced)
     const long long N = 4LL * lat->nx * lat->ny * lat->nz;
     const int blocks = (int)std::max(1LL, std::min<long long>((N + 255) / 256, (long long)ws->num_sms * 8));
-    k_fcc_pair_counts<<<blocks, 256, 0, stream>>>(P, cnt);
+    k_fcc_pair_counts<<<blocks, 256, 0, stream>>>(P, cnt, is_qsro ? cnt + kMaxShells * 64 : nullptr);
     err = cudaGetLastError();
     if (err != cudaSuccess) return cuda_fail(err, "k_fcc_pair_counts");
     k_fcc_energy_finish<<<1, 32, 0, stream>>>(P, cnt, m->kind == SMC_PAIR_I32 ? 1 : 0, m->unit_ev, e,

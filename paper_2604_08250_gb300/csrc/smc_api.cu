@@ -495,8 +495,8 @@ static bool fcc_lattice_valid(const smc_lattice *lat)
 static smc_status fcc_check(const smc_lattice *lat, const smc_model *model, const void *occ, bool sweep)
 {
     if (!fcc_lattice_valid(lat) || !model_valid(lat, model)) return SMC_ERR_ARG;
-    if (model->kind != SMC_PAIR_I32 && model->kind != SMC_PAIR_F32) {
-        set_error("the FCC lattice takes pair models (SMC_PAIR_I32, SMC_PAIR_F32) only");
+    if (model->kind != SMC_PAIR_I32 && model->kind != SMC_PAIR_F32 && model->kind != SMC_QSRO_F32) {
+        set_error("the FCC lattice takes pair models (SMC_PAIR_I32, SMC_PAIR_F32) and qSRO models only");
         return SMC_ERR_UNSUPPORTED;
     }
     if (!occ) {

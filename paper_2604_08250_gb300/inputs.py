@@ -35,6 +35,20 @@ def dirichlet_counts(nsites: int, nspecies: int, seed: int, alpha: float = 5.0) 
     return c
 
 
+# The paper's alloy Fe29 Co29 Ni28 Al7 Ti7 (Sec. IV-C), species 0-4 in that order.
+HEA_FRACTIONS = (0.29, 0.29, 0.28, 0.07, 0.07)
+
+
+def fraction_counts(nsites: int, fractions) -> np.ndarray:
+    """Integer counts of the given composition by the largest-remainder rule."""
+    raw = np.asarray(fractions, dtype=np.float64) / float(np.sum(fractions)) * nsites
+    c = np.floor(raw).astype(np.int64)
+    short = int(nsites - c.sum())
+    order = np.argsort(-(raw - c), kind="stable")
+    c[order[:short]] += 1
+    return c
+
+
 def _symmetric(unique: np.ndarray, nshells: int, S: int, dtype) -> np.ndarray:
     v = np.zeros((nshells, S, S), dtype=dtype)
     t = 0

@@ -6,7 +6,7 @@ import re
 
 import pytest
 
-from paper_2604_08250_gb300 import build, smc
+from paper_2604_08250_gb300 import build, inputs, smc
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -62,6 +62,6 @@ def test_fcc_argument_errors_need_no_gpu(L):
     rc = L.smc_fcc_ministep_trace(ctypes.byref(lat._c), ctypes.byref(m._c), ctypes.c_void_p(16), 1, 0, 0, 256,
                                   0.05, ctypes.c_void_p(16), ctypes.c_void_p(16), None)
     assert rc == smc.SMC_ERR_ARG and b"mini-step" in L.smc_last_error()
-    q = smc.Model(smc.QSRO_F32, 1, [[[0.0, 0.0], [0.0, 0.0]]], qsro_w=[[[0.0, 0.0], [0.0, 0.0]]])
+    q = smc.Model(smc.MLP_BF16, mlp=inputs.mlp_weights(1))
     rc = L.smc_fcc_energy(ctypes.byref(lat._c), ctypes.byref(q._c), ctypes.c_void_p(16), None, None, None)
     assert rc == smc.SMC_ERR_UNSUPPORTED and b"pair models" in L.smc_last_error()

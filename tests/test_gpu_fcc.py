@@ -211,7 +211,7 @@ def test_unsupported_inputs_raise(smc):
                                acc=torch.zeros(8, dtype=torch.uint8, device=dev()))
     with pytest.raises(smc.SMCError):
         smc.fcc_sweep(lat, model, occ, 1, 0, 1, [-1.0])
-    mlp = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(1))
+    mlp = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(1))  # neither pair nor qSRO
     with pytest.raises(smc.SMCError):
         smc.fcc_sweep(lat, mlp, occ, 1, 0, 1, [0.05])
     with pytest.raises(smc.SMCError):
@@ -246,6 +246,128 @@ def test_full_size_sampled_trials(smc):
     rng = np.random.default_rng(5)
     cells = [(0, 0, 0), (NL - 1, NL - 1, NL - 1), (0, 5, 9), (NL - 1, 2, 30), (3, 0, 4), (7, NL - 1, 1)]
     cells += [tuple(int(v) for v in rng.integers(0, NL, 3)) for _ in range(394)]
+    dx, dy, dz, sub = k % 4, (k // 4) % 4, (k // 16) % 4, k // 64
+    for cx, cy, cz in cells:
+        c = (cz * NL + cy) * NL + cx
+        a = ((sub * n + 4 * cz + dz) * n + 4 * cy + dy) * n + 4 * cx + dx
+        w = oracle.philox4x32_10([a & 0xFFFFFFFF, 0, sweep, 0], [seed, 0])
+        b = oracle.fcc_neighbor(olat, a, v1[(int(w[1]) * 12) >> 32])
+        ref = oracle.fcc_delta_e(olat, omodel, pre, a, b)
+        assert abs(float(g_dE[c]) - ref) <= DE_TOL_EV, (c, float(g_dE[c]), ref)
+        u = (float(int(w[0]) & ((1 << 29) - 1)) + 0.5) / 2.0 ** 29
+        want = ref <= 0 or u < math.exp(-ref / kT)
+        if abs(ref + kT * math.log(u)) > DE_TOL_EV:
+            assert bool(g_acc[c]) == want, c
+        if g_acc[c]:
+            assert post[a] == pre[b] and post[b] == pre[a]
+        else:
+            assert post[a] == pre[a] and post[b] == pre[b]
+
+
+# ---- qSRO on the FCC lattice (Eq. quadratic_local_SRO) ----
+
+def _qsro_models(smc, seed, nsh, S):
+    V, W, C = inputs.qsro_coeffs(seed, nsh, S)
+    return (smc.Model(smc.QSRO_F32, nsh, V, qsro_w=W, qsro_c=C),
+            oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C))
+
+
+@pytest.mark.parametrize("dims,nsh,S", [((8, 8, 8), 3, 5), ((12, 8, 16), 2, 4), ((24, 24, 24), 3, 5)])
+def test_qsro_lockstep_against_oracle(smc, dims, nsh, S):
+    """Every trial of a sweep (24^3: 64 of the 256 mini-steps, mostly interior
+    link cells): dE within 1e-5 eV of the FP64 oracle, the same decisions
+    (a flip resynchronises the oracle), 800 K."""
+    model, omodel = _qsro_models(smc, 7 + nsh, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 4)
+    kT = inputs.K_B_EV * 800.0
+    nt = oracle.fcc_nsites(olat) // 256
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    flips, worst, nacc = 0, 0.0, 0
+    ks = range(256) if dims[0] < 24 else range(0, 256, 4)
+    for k in ks:
+        smc.fcc_ministep_trace(lat, model, occ, 9, 1, k, kT, dE=dE, acc=acc)
+        odE, oacc, _, _ = oracle.fcc_ministep_trace(olat, omodel, ref, 9, 1, k, kT)
+        g = dE.cpu().numpy().astype(np.float64)
+        worst = max(worst, float(np.abs(g - odE).max()))
+        assert np.all(np.abs(g - odE) <= DE_TOL_EV), k
+        ga = acc.cpu().numpy().astype(bool)
+        nacc += int(ga.sum())
+        if not np.array_equal(ga, oacc):
+            flips += int((ga != oacc).sum())
+            ref[:] = occ.cpu().numpy()
+        else:
+            assert np.array_equal(occ.cpu().numpy(), ref)
+    assert flips <= 1, flips
+    assert worst < 2e-6
+    assert nacc > 0
+
+
+@pytest.mark.parametrize("dims,nsh", [((8, 16, 12), 3), ((24, 24, 24), 3), ((16, 8, 8), 1), ((12, 12, 8), 2)])
+def test_qsro_sweep_equals_trace_and_energy_closes(smc, dims, nsh):
+    """The sweep keeps the own-species count cache across its mini-steps;
+    every traced mini-step rebuilds it from the occupancy: the trajectories
+    must agree bit for bit.  E(after) - E(before) = e_acc within FP32
+    rounding; the energy equals the oracle's sum of site energies."""
+    S = 5
+    model, omodel = _qsro_models(smc, 3 * nsh, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 8)
+    occ2 = occ.clone()
+    kT = [inputs.K_B_EV * 800.0, inputs.K_B_EV * 1200.0]
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.fcc_sweep(lat, model, occ, 4, 10, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    for t in range(2):
+        for k in range(256):
+            smc.fcc_ministep_trace(lat, model, occ2, 4, 10 + t, k, kT[t])
+    smc.check()
+    assert torch.equal(occ, occ2)
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e)
+    after = occ.cpu().numpy()
+    assert np.array_equal(np.bincount(after, minlength=S), np.bincount(ref, minlength=S))
+    assert float(e.item()) == pytest.approx(oracle.fcc_total_energy(olat, omodel, after), rel=1e-12)
+    n = int(n_acc.item())
+    assert n > 0
+    # each accepted dE: about 130 FP32 terms of |.| <= 0.1 eV; errors add like a random walk
+    tol = 6 * math.sqrt(n) * 130 * 2.0 ** -24 * 0.5
+    assert abs(float(e.item()) - (oracle.fcc_total_energy(olat, omodel, ref) + float(e_acc.item()))) <= tol
+
+
+@pytest.mark.parametrize("dims,nsh", [((4, 5, 3), 3), ((8, 8, 8), 2), ((16, 8, 24), 3), ((2, 1, 1), 1)])
+def test_qsro_energy_matches_oracle(smc, dims, nsh):
+    S = 4
+    model, omodel = _qsro_models(smc, 40 + nsh, nsh, S)
+    lat, occ, olat, ref = _state(smc, dims, S, 12, inputs.dirichlet_counts(4 * dims[0] * dims[1] * dims[2], S, 2))
+    e = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e)
+    assert float(e.item()) == pytest.approx(oracle.fcc_total_energy(olat, omodel, ref), rel=1e-12)
+
+
+def test_qsro_full_size_sampled_trials(smc):
+    """256^3 cubic cells (67M sites), 3-shell quinary qSRO at 800 K on the
+    oracle's start state: mini-step 77 of sweep 2 at 300 sampled link cells
+    against the oracle's dE and decision, the swap applied where accepted."""
+    n, S, seed, sweep, k = 256, 5, 1, 2, 77
+    lat = smc.Lattice(n, n, n, S)
+    N = smc.fcc_nsites(lat)
+    model, omodel = _qsro_models(smc, 7, 3, S)
+    kT = inputs.K_B_EV * 800.0
+    occ = torch.empty(N, dtype=torch.int8, device=dev())
+    smc.fcc_init_lattice(lat, inputs.equiatomic_counts(N, S), seed, occ)
+    olat = oracle.Lattice(n, n, n, S)
+    pre = oracle.fcc_init_lattice(olat, inputs.equiatomic_counts(N, S), seed)
+    assert np.array_equal(occ.cpu().numpy(), pre)
+    NL = n // 4
+    dE = torch.zeros(NL ** 3, dtype=torch.float32, device=dev())
+    acc = torch.zeros(NL ** 3, dtype=torch.uint8, device=dev())
+    smc.fcc_ministep_trace(lat, model, occ, seed, sweep, k, kT, dE=dE, acc=acc)
+    smc.check()
+    post, g_dE, g_acc = occ.cpu().numpy(), dE.cpu().numpy(), acc.cpu().numpy()
+    v1 = oracle.fcc_shell_vectors(1)
+    rng = np.random.default_rng(6)
+    cells = [(0, 0, 0), (NL - 1, NL - 1, NL - 1), (0, 5, 9), (NL - 1, 2, 30)]
+    cells += [tuple(int(v) for v in rng.integers(0, NL, 3)) for _ in range(296)]
     dx, dy, dz, sub = k % 4, (k // 4) % 4, (k // 16) % 4, k // 64
     for cx, cy, cz in cells:
         c = (cz * NL + cy) * NL + cx
