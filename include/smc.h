@@ -247,7 +247,9 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
                               double kT, float *dE, uint8_t *acc, cudaStream_t stream);
 
 /* FCC lattice (the paper's lattice, Sec. IV-C), pair models (SMC_PAIR_I32,
- * SMC_PAIR_F32).  lat gives nx x ny x nz cubic cells of 4 sites at the
+ * SMC_PAIR_F32) and the qSRO model (SMC_QSRO_F32, Eq. quadratic_local_SRO
+ * with the FCC shells, z_m = 12, 6, 24; the sweep keeps a 4 N-byte cache of
+ * own-species counts in the workspace).  lat gives nx x ny x nz cubic cells of 4 sites at the
  * half-unit offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3),
  * N = 4 nx ny nz, site s = ((sub*nz + z)*ny + y)*nx + x; every axis a
  * multiple of 4 and >= 8 cells (4x4x4 link cells, n_A = 256 mini-steps,
@@ -260,7 +262,10 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
  * smc_init_lattice order over the same N site ids).  The other calls have
  * the arguments and errors of their BCC counterparts; e_acc sums per link
  * cell and then in link-cell order; smc_fcc_ministep_trace runs the sweep
- * kernel on one mini-step and records its per-trial dE and decisions. */
+ * kernel on one mini-step and records its per-trial dE and decisions.
+ * Errors: SMC_ERR_UNSUPPORTED for other model kinds, and for sweeps and
+ * traces on a box whose axes are not multiples of 4 of at least 8 cells
+ * (smc_fcc_energy takes any box of at least 1 cell per axis). */
 smc_status smc_fcc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint64_t seed, uint32_t replica,
                                 int8_t *occ, cudaStream_t stream);
 smc_status smc_fcc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
