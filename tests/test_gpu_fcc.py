@@ -85,9 +85,11 @@ def test_int_trajectory_bit_exact(smc, dims, S, nsh, nsw):
     assert float(e.item()) == pytest.approx(int(e_int.item()) * 1e-4, rel=1e-15)
 
 
-def test_int_trace_matches_oracle_per_trial(smc):
-    """dE, decision and the resulting state of single mini-steps."""
-    dims, S, nsh = (12, 8, 8), 4, 3
+@pytest.mark.parametrize("dims", [(12, 8, 8), (1040, 8, 8), (1032, 8, 12)])
+def test_int_trace_matches_oracle_per_trial(smc, dims):
+    """dE, decision and the resulting state of single mini-steps, on boxes
+    with 2, 260 and 258 link cells along x."""
+    S, nsh = 4, 3
     V = inputs.pair_int_coeffs(21, nsh, S)
     lat, occ, olat, ref = _state(smc, dims, S, 5)
     model = smc.Model(smc.PAIR_I32, nsh, V, unit_ev=1e-4)
