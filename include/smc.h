@@ -248,8 +248,8 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
 
 /* FCC lattice (the paper's lattice, Sec. IV-C), pair models (SMC_PAIR_I32,
  * SMC_PAIR_F32) and the qSRO model (SMC_QSRO_F32, Eq. quadratic_local_SRO
- * with the FCC shells, z_m = 12, 6, 24; the sweep keeps a 4 N-byte cache of
- * own-species counts in the workspace).  lat gives nx x ny x nz cubic cells of 4 sites at the
+ * with the FCC shells, z_m = 12, 6, 24; the sweep keeps a cache of
+ * own-species counts in the workspace, N bytes for 1-2 shells, 2 N for 3).  lat gives nx x ny x nz cubic cells of 4 sites at the
  * half-unit offsets (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3),
  * N = 4 nx ny nz, site s = ((sub*nz + z)*ny + y)*nx + x; every axis a
  * multiple of 4 and >= 8 cells (4x4x4 link cells, n_A = 256 mini-steps,

@@ -72,8 +72,13 @@ struct FccParams {
     float vf[kMaxShells * kMaxSpecies * kMaxSpecies];
     float wq[kMaxShells * kMaxSpecies];  // qSRO W_m^p
     double qc;                           // qSRO C
-    uint32_t *qcache;                    // qSRO: own-species counts per shell of every site (bytes 0-2)
+    void *qcache;  // qSRO: own-species counts per shell of every site (1 byte for 1-2 shells, 2 for 3)
 };
+
+// Own-species count fields of the qSRO cache: shell 1 in bits 0-3 (<= 12),
+// shell 2 in bits 4-6 (<= 6), shell 3 in bits 7-11 (<= 24).
+__host__ __device__ constexpr int fcc_qoff(int m) { return m == 0 ? 0 : (m == 1 ? 4 : 7); }
+__host__ __device__ constexpr int fcc_qmask(int m) { return m == 0 ? 15 : (m == 1 ? 7 : 31); }
 
 // qSRO per-call tables (32-bit words): Dz[m][A][B][q] = (V_m(B,q) - V_m(A,q)) / z_m,
 // Wz[m][p] = W_m^p / z_m^2, per partner direction the zone entries (half-unit
@@ -228,7 +233,7 @@ __global__ void __launch_bounds__(256) k_fcc_ministep(const __grid_constant__ Fc
 __device__ __forceinline__ int3 fcc_woff(int w) { return make_int3(w % 7 - 3, (w / 7) % 7 - 3, w / 49 - 3); }
 
 // qSRO cache: for every site, the number of its shell-m neighbours of its own
-// species, in byte m-1.
+// species, in field m (fcc_qoff).
 __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ FccParams P)
 {
     const int N = 4 * P.nx * P.ny * P.nz;
@@ -240,9 +245,12 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ 
         for (int m = 1; m <= P.nshells; ++m)
             for (int t = 0; t < c_fcc_n[m]; ++t) {
                 const signed char *v = c_fcc_vec[m][t];
-                if ((P.occ[fcc_site_at(P, ps.x + v[0], ps.y + v[1], ps.z + v[2])] & 7) == p) q += 1u << (8 * (m - 1));
+                if ((P.occ[fcc_site_at(P, ps.x + v[0], ps.y + v[1], ps.z + v[2])] & 7) == p) q += 1u << fcc_qoff(m - 1);
             }
-        P.qcache[s] = q;
+        if (P.nshells == 3)
+            static_cast<uint16_t *>(P.qcache)[s] = (uint16_t)q;
+        else
+            static_cast<uint8_t *>(P.qcache)[s] = (uint8_t)q;
     }
 }
 
@@ -257,6 +265,7 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ 
 template <int NSH>
 __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant__ FccParams P, int k)
 {
+    using QT = typename std::conditional<NSH == 3, uint16_t, uint8_t>::type;
     constexpr int NZ = NSH == 1 ? 18 : (NSH == 2 ? 26 : 58);
     __shared__ uint32_t sm[kQWords];
     for (int i = threadIdx.x; i < kQWords; i += blockDim.x) sm[i] = __ldg(P.tables + i);
@@ -292,7 +301,7 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
     const int3 v1 = fcc_woff(wb);
     const int b = interior ? a + del[wb] : fcc_site_at(P, pa.x + v1.x, pa.y + v1.y, pa.z + v1.z);
     int8_t *occ = P.occ;
-    uint32_t *Qc = P.qcache;
+    QT *Qc = static_cast<QT *>(P.qcache);
     const int A = occ[a] & 7, B = occ[b] & 7;
     const int *zone = sZ + dir * kQZmax;
     // packed per-shell counts (byte m-1): species A / B around a and around b
@@ -325,14 +334,14 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
                 cBb += isB << (8 * (mb - 1));
             }
             if ((isA | isB) && ma != mb) {
-                const uint32_t q = Qc[j];
+                const int q = Qc[j];
                 const int p = isA ? A : B;
                 if (ma) {
-                    const int n = (q >> (8 * (ma - 1))) & 255;
+                    const int n = (q >> fcc_qoff(ma - 1)) & fcc_qmask(ma - 1);
                     wz += sW[(ma - 1) * 8 + p] * (float)(isA ? 1 - 2 * n : 2 * n + 1);
                 }
                 if (mb) {
-                    const int n = (q >> (8 * (mb - 1))) & 255;
+                    const int n = (q >> fcc_qoff(mb - 1)) & fcc_qmask(mb - 1);
                     wz += sW[(mb - 1) * 8 + p] * (float)(isA ? 2 * n + 1 : 1 - 2 * n);
                 }
             }
@@ -352,8 +361,14 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
         if (A != B) {
             occ[a] = (int8_t)B;
             occ[b] = (int8_t)A;
-            Qc[a] = cBa - 1u;  // a now B: B neighbours other than b
-            Qc[b] = cAb - 1u;
+            int qa = 0, qb = 0;  // a now B: its B neighbours other than b; b now A likewise
+#pragma unroll
+            for (int m = 0; m < NSH; ++m) {
+                qa += (int)(((cBa >> (8 * m)) & 255u) - (m == 0 ? 1u : 0u)) << fcc_qoff(m);
+                qb += (int)(((cAb >> (8 * m)) & 255u) - (m == 0 ? 1u : 0u)) << fcc_qoff(m);
+            }
+            Qc[a] = (QT)qa;
+            Qc[b] = (QT)qb;
             for (int i = 0; i < NZ; ++i) {
                 const int e = zone[i];
                 const int w = e & 511, ma = (e >> 9) & 3, mb = (e >> 11) & 3;
@@ -368,9 +383,9 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
                 const int sj = occ[j] & 7;
                 if (sj != A && sj != B) continue;
                 int dq = 0;  // A sites lose a (shell ma) and gain b (shell mb); B sites the reverse
-                if (ma) dq += (sj == A ? -1 : 1) * (1 << (8 * (ma - 1)));
-                if (mb) dq += (sj == A ? 1 : -1) * (1 << (8 * (mb - 1)));
-                Qc[j] += (uint32_t)dq;
+                if (ma) dq += (sj == A ? -1 : 1) * (1 << fcc_qoff(ma - 1));
+                if (mb) dq += (sj == A ? 1 : -1) * (1 << fcc_qoff(mb - 1));
+                Qc[j] = (QT)(Qc[j] + dq);
             }
         }
         if (P.part_e) {
@@ -686,7 +701,8 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     const size_t off_pn = (size_t)nc * 8, off_w = off_pn + (size_t)nc * 8, off_tab = off_w + words.size() * 4;
     const size_t off_q = (off_tab + tabs.size() * 4 + 255) / 256 * 256;
     const size_t N = 4ull * lat->nx * lat->ny * lat->nz;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_q + (is_qsro ? N * 4 : 16), &st);
+    const size_t qbytes = m->nshells == 3 ? 2 : 1;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_q + (is_qsro ? N * qbytes : 16), &st);
     if (!scr) return st;
     cudaError_t e = cudaMemsetAsync(scr, 0, off_w, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(FCC partial sums)");
@@ -709,7 +725,7 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
                                                        : (m->nshells == 2 ? k_fcc_qsro_ministep<2> : k_fcc_qsro_ministep<3>))
                                    : (is_int ? pick_fcc<true>(m->nshells) : pick_fcc<false>(m->nshells));
     if (is_qsro) {  // the count cache, from the occupancy at the start of every call
-        P.qcache = (uint32_t *)(scr + off_q);
+        P.qcache = scr + off_q;
         const int cb = (int)std::max<size_t>(1, std::min<size_t>((N + 255) / 256, (size_t)ws->num_sms * 16));
         k_fcc_qsro_cache<<<cb, 256, 0, stream>>>(P);
         e = cudaGetLastError();
@@ -750,7 +766,7 @@ smc_status launch_fcc_energy(const smc_lattice *lat, const smc_model *m, const i
     cudaError_t err = cudaMemsetAsync(cnt, 0, cbytes, stream);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync(FCC counts)");
     const bool is_qsro = m->kind == SMC_QSRO_F32;
-    if (is_qsro) P.qcache = reinterpret_cast<uint32_t *>(cnt);  // marks the qSRO energy (not dereferenced)
+    if (is_qsro) P.qcache = cnt;  // marks the qSRO energy (not dereferenced)
     const long long N = 4LL * lat->nx * lat->ny * lat->nz;
     const int blocks = (int)std::max(1LL, std::min<long long>((N + 255) / 256, (long long)ws->num_sms * 8));
     k_fcc_pair_counts<<<blocks, 256, 0, stream>>>(P, cnt, is_qsro ? cnt + kMaxShells * 64 : nullptr);
