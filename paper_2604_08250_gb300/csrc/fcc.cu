@@ -80,6 +80,33 @@ struct FccParams {
 __host__ __device__ constexpr int fcc_qoff(int m) { return m == 0 ? 0 : (m == 1 ? 4 : 7); }
 __host__ __device__ constexpr int fcc_qmask(int m) { return m == 0 ? 15 : (m == 1 ? 7 : 31); }
 
+// Zone categories of a qSRO trial, (shell to a) * 4 + (shell to b), with their
+// sizes: the same for every partner direction (the 12 are equivalent under
+// the cubic point group, which keeps shells).  The zone table of each
+// direction lists its sites in this category order.
+__host__ __device__ constexpr int fcc_zone_ncat(int nsh) { return nsh == 1 ? 3 : (nsh == 2 ? 7 : 14); }
+__host__ __device__ constexpr int fcc_zone_cat(int nsh, int i, int *count)
+{
+    constexpr int c1[3][2] = {{4, 7}, {1, 7}, {5, 4}};
+    constexpr int c2[7][2] = {{4, 5}, {8, 4}, {1, 5}, {2, 4}, {5, 4}, {6, 2}, {9, 2}};
+    constexpr int c3[14][2] = {{4, 1},  {8, 2},  {12, 14}, {1, 1}, {2, 2},  {3, 14}, {5, 4},
+                               {6, 2},  {7, 4},  {9, 2},   {11, 2}, {13, 4}, {14, 2}, {15, 4}};
+    const int *e = nsh == 1 ? c1[i] : (nsh == 2 ? c2[i] : c3[i]);
+    *count = e[1];
+    return e[0];
+}
+// category code of the e-th zone site
+__host__ __device__ constexpr int fcc_zone_code(int nsh, int e)
+{
+    int n = 0, code = 0;
+    for (int i = 0; i < fcc_zone_ncat(nsh); ++i) {
+        code = fcc_zone_cat(nsh, i, &n);
+        if (e < n) return code;
+        e -= n;
+    }
+    return 0;
+}
+
 // qSRO per-call tables (32-bit words): Dz[m][A][B][q] = (V_m(B,q) - V_m(A,q)) / z_m,
 // Wz[m][p] = W_m^p / z_m^2, per partner direction the zone entries (half-unit
 // offset index w = (x+3) + 7 (y+3) + 49 (z+3), shell to a at bit 9, shell to
@@ -261,7 +288,8 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ 
 //   W part       (s_j = A or B, ma != mb) from j's cached own-species counts.
 // a and b change their own species: their linear parts sum to the same
 // D terms again (V symmetric), and their W parts use the counts of A and B
-// around each (b counted in a's shell 1 and a in b's).  C cancels.
+// around each (b counted in a's shell 1 and a in b's).  C cancels.  The zone
+// is walked in category order, so ma and mb are compile-time constants.
 template <int NSH>
 __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant__ FccParams P, int k)
 {
@@ -304,23 +332,28 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
     QT *Qc = static_cast<QT *>(P.qcache);
     const int A = occ[a] & 7, B = occ[b] & 7;
     const int *zone = sZ + dir * kQZmax;
+    auto site = [&](int e) {
+        const int w = zone[e];
+        if (interior) return a + del[w];
+        const int3 d = fcc_woff(w);
+        return fcc_site_at(P, pa.x + d.x, pa.y + d.y, pa.z + d.z);
+    };
     // packed per-shell counts (byte m-1): species A / B around a and around b
     uint32_t cAa = 0, cBa = 1u, cAb = 1u, cBb = 0;  // b (species B) is in a's shell 1, a (A) in b's
     float dE = 0.f;
     if (A != B) {
         const float *row = sT + (A * 8 + B) * 8;
+        float wA[NSH], wB[NSH];  // W_m^A / z_m^2, W_m^B / z_m^2
+#pragma unroll
+        for (int m = 0; m < NSH; ++m) {
+            wA[m] = sW[m * 8 + A];
+            wB[m] = sW[m * 8 + B];
+        }
         float lin = 0.f, wz = 0.f;
-#pragma unroll 2
-        for (int i = 0; i < NZ; ++i) {
-            const int e = zone[i];
-            const int w = e & 511, ma = (e >> 9) & 3, mb = (e >> 11) & 3;
-            int j;
-            if (interior) {
-                j = a + del[w];
-            } else {
-                const int3 d = fcc_woff(w);
-                j = fcc_site_at(P, pa.x + d.x, pa.y + d.y, pa.z + d.z);
-            }
+#pragma unroll
+        for (int e = 0; e < NZ; ++e) {
+            const int code = fcc_zone_code(NSH, e), ma = code >> 2, mb = code & 3;
+            const int j = site(e);
             const int sj = occ[j] & 7;
             const uint32_t isA = sj == A, isB = sj == B;
             if (ma) {
@@ -333,17 +366,18 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
                 cAb += isA << (8 * (mb - 1));
                 cBb += isB << (8 * (mb - 1));
             }
-            if ((isA | isB) && ma != mb) {
+            if (ma != mb) {
                 const int q = Qc[j];
-                const int p = isA ? A : B;
+                float t = 0.f;  // a leaves j's shell ma as A and arrives as B; b the reverse in shell mb
                 if (ma) {
                     const int n = (q >> fcc_qoff(ma - 1)) & fcc_qmask(ma - 1);
-                    wz += sW[(ma - 1) * 8 + p] * (float)(isA ? 1 - 2 * n : 2 * n + 1);
+                    t += isA ? wA[ma - 1] * (float)(1 - 2 * n) : (isB ? wB[ma - 1] * (float)(2 * n + 1) : 0.f);
                 }
                 if (mb) {
                     const int n = (q >> fcc_qoff(mb - 1)) & fcc_qmask(mb - 1);
-                    wz += sW[(mb - 1) * 8 + p] * (float)(isA ? 2 * n + 1 : 1 - 2 * n);
+                    t += isA ? wA[mb - 1] * (float)(2 * n + 1) : (isB ? wB[mb - 1] * (float)(1 - 2 * n) : 0.f);
                 }
+                wz += t;
             }
         }
         float wa = 0.f, wbb = 0.f;
@@ -351,8 +385,8 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
         for (int m = 0; m < NSH; ++m) {
             const int nAa = (cAa >> (8 * m)) & 255, nBa = ((cBa >> (8 * m)) & 255) - (m == 0 ? 1 : 0);
             const int nAb = ((cAb >> (8 * m)) & 255) - (m == 0 ? 1 : 0), nBb = (cBb >> (8 * m)) & 255;
-            wa += sW[m * 8 + B] * (float)(nBa * nBa) - sW[m * 8 + A] * (float)(nAa * nAa);
-            wbb += sW[m * 8 + A] * (float)(nAb * nAb) - sW[m * 8 + B] * (float)(nBb * nBb);
+            wa += wB[m] * (float)(nBa * nBa) - wA[m] * (float)(nAa * nAa);
+            wbb += wA[m] * (float)(nAb * nAb) - wB[m] * (float)(nBb * nBb);
         }
         dE = 2.f * lin + wa + wbb + wz;
     }
@@ -369,23 +403,16 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
             }
             Qc[a] = (QT)qa;
             Qc[b] = (QT)qb;
-            for (int i = 0; i < NZ; ++i) {
-                const int e = zone[i];
-                const int w = e & 511, ma = (e >> 9) & 3, mb = (e >> 11) & 3;
+#pragma unroll
+            for (int e = 0; e < NZ; ++e) {
+                const int code = fcc_zone_code(NSH, e), ma = code >> 2, mb = code & 3;
                 if (ma == mb) continue;
-                int j;
-                if (interior) {
-                    j = a + del[w];
-                } else {
-                    const int3 d = fcc_woff(w);
-                    j = fcc_site_at(P, pa.x + d.x, pa.y + d.y, pa.z + d.z);
-                }
+                const int j = site(e);
                 const int sj = occ[j] & 7;
-                if (sj != A && sj != B) continue;
-                int dq = 0;  // A sites lose a (shell ma) and gain b (shell mb); B sites the reverse
-                if (ma) dq += (sj == A ? -1 : 1) * (1 << fcc_qoff(ma - 1));
-                if (mb) dq += (sj == A ? 1 : -1) * (1 << fcc_qoff(mb - 1));
-                Qc[j] = (QT)(Qc[j] + dq);
+                // A sites lose a (shell ma) and gain b (shell mb); B sites the reverse
+                const int d = (ma ? 1 << fcc_qoff(ma - 1) : 0) - (mb ? 1 << fcc_qoff(mb - 1) : 0);
+                if (sj == A) Qc[j] = (QT)(Qc[j] - d);
+                if (sj == B) Qc[j] = (QT)(Qc[j] + d);
             }
         }
         if (P.part_e) {
@@ -567,16 +594,27 @@ smc_status fcc_qsro_tables(const smc_lattice *lat, const smc_model *m, std::vect
     for (int d = 0; d < 12; ++d) {
         w[kQV1 + d] = (uint32_t)widx(v1[d][0], v1[d][1], v1[d][2]);
         int n = 0;
-        for (int x = -3; x <= 3; ++x)
-            for (int y = -3; y <= 3; ++y)
-                for (int zz = -3; zz <= 3; ++zz) {
-                    if ((x == 0 && y == 0 && zz == 0) || (x == v1[d][0] && y == v1[d][1] && zz == v1[d][2])) continue;
-                    const int ma = fcc_shell_of(x, y, zz, nsh);
-                    const int mb = fcc_shell_of(x - v1[d][0], y - v1[d][1], zz - v1[d][2], nsh);
-                    if (!ma && !mb) continue;
-                    if (n < kQZmax) w[kQZ + d * kQZmax + n] = (uint32_t)(widx(x, y, zz) | (ma << 9) | (mb << 11));
-                    ++n;
-                }
+        for (int ci = 0; ci < fcc_zone_ncat(nsh); ++ci) {
+            int cnt = 0;
+            const int code = fcc_zone_cat(nsh, ci, &cnt);
+            int got = 0;
+            for (int x = -3; x <= 3; ++x)
+                for (int y = -3; y <= 3; ++y)
+                    for (int zz = -3; zz <= 3; ++zz) {
+                        if ((x == 0 && y == 0 && zz == 0) || (x == v1[d][0] && y == v1[d][1] && zz == v1[d][2]))
+                            continue;
+                        const int ma = fcc_shell_of(x, y, zz, nsh);
+                        const int mb = fcc_shell_of(x - v1[d][0], y - v1[d][1], zz - v1[d][2], nsh);
+                        if (ma * 4 + mb != code) continue;
+                        if (n < kQZmax) w[kQZ + d * kQZmax + n] = (uint32_t)widx(x, y, zz);
+                        ++n;
+                        ++got;
+                    }
+            if (got != cnt) {
+                set_error("internal error: FCC qSRO zone category %d has %d sites (want %d)", code, got, cnt);
+                return SMC_ERR_STATE;
+            }
+        }
         if (n != want) {
             set_error("internal error: FCC qSRO zone has %d sites (want %d)", n, want);
             return SMC_ERR_STATE;
