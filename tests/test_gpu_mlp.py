@@ -67,12 +67,13 @@ def make_models(smc, kind, S=5, mlp_seed=4, coeff_seed=5, nshells=2, out_scale=0
 
 
 def start_state(smc, dims, S, seed, counts_seed=4):
+    """The oracle's start state on the device, and on the host (the oracle
+    never reads a configuration the GPU produced)."""
     N = 2 * dims[0] * dims[1] * dims[2]
     counts = inputs.dirichlet_counts(N, S, counts_seed)
     lat = smc.Lattice(*dims, S)
-    occ = torch.empty(N, dtype=torch.int8, device=dev())
-    smc.init_lattice(lat, counts, seed, occ)
-    return lat, occ, counts
+    ref = oracle.init_lattice(oracle.Lattice(*dims, S), counts, seed)
+    return lat, torch.from_numpy(ref.copy()).to(dev()), counts, ref
 
 
 def trial_reference(occ_h, dims, a, b, w, dE64, V=None):
@@ -125,20 +126,20 @@ def test_mlp_lockstep_against_oracle(smc, dims, kind, T, biases):
     """Every trial of a full sweep: |dE_GPU - dE_emulated| within the tight
     bound, |dE_GPU - dE_FP64| within the worst-case bound, the sign agreeing
     beyond it; a decision flip only where the acceptance threshold lies between
-    the oracle's dE and the GPU's (the run continues from the GPU's state)."""
+    the oracle's dE and the GPU's (the run continues from the oracle's state)."""
     S, seed, kT = 5, 11, K_B * T
     gm, om, w, V = make_models(smc, kind, biases=biases)
-    lat, occ, _ = start_state(smc, dims, S, seed)
+    lat, occ, _, ref = start_state(smc, dims, S, seed)
     olat = oracle.Lattice(*dims, S)
     nt = lat.nsites // 128
     dE = torch.zeros(nt, dtype=torch.float32, device=dev())
     acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
     errs, emus, bnds, flips, n = [], [], [], 0, 0
     for k in range(128):
-        occ_h = occ.cpu().numpy().copy()
+        occ_h = ref.copy()  # the pre-step state, the oracle's
         smc.ministep_trace(lat, gm, occ, seed, 0, k, kT, dE, acc)
         smc.check()
-        d_o, a_o, a, b = oracle.ministep_trace(olat, om, occ_h.copy(), seed, 0, k, kT)
+        d_o, a_o, a, b = oracle.ministep_trace(olat, om, ref, seed, 0, k, kT)
         d_g = dE.cpu().numpy().astype(np.float64)
         a_g = acc.cpu().numpy().astype(bool)
         emu, tight, loose = trial_reference(occ_h, dims, a, b, w, d_o, V)
@@ -152,6 +153,8 @@ def test_mlp_lockstep_against_oracle(smc, dims, kind, T, biases):
             slack = abs(err[t]) * (1 + 1e-6)
             assert abs(d_o[t] - thr) <= slack + 1e-6 * thr or abs(d_o[t]) <= slack, (k, t, d_o[t], thr)
             flips += 1
+        if np.any(a_g != a_o):  # the GPU continues from the oracle's state
+            occ.copy_(torch.from_numpy(ref.copy()).to(dev()))
         errs.append(err)
         emus.append(e_emu)
         bnds.append(loose)
@@ -175,7 +178,7 @@ def test_mlp_sweep_kernel_equals_trace_kernel(smc, dims, kind):
     to FP64 summation order."""
     S, seed, kT = 5, 21, K_B * 800.0
     gm, _, _, _ = make_models(smc, kind)
-    lat, occ, counts = start_state(smc, dims, S, seed)
+    lat, occ, counts, _ = start_state(smc, dims, S, seed)
     occ2 = occ.clone()
     e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
     n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
@@ -205,11 +208,10 @@ def test_mlp_energy_matches_oracle(smc, dims, kind, biases):
     """smc_energy = sum_i f(x_i) (+ pair energy) within the summed per-site bound."""
     S, seed = 5, 3
     gm, om, w, V = make_models(smc, kind, biases=biases)
-    lat, occ, _ = start_state(smc, dims, S, seed)
+    lat, occ, _, occ_h = start_state(smc, dims, S, seed)
     e = torch.zeros(1, dtype=torch.float64, device=dev())
     smc.energy(lat, gm, occ, e)
     smc.check()
-    occ_h = occ.cpu().numpy()
     want = oracle.total_energy(oracle.Lattice(*dims, S), om, occ_h)
     eb, f = helpers.mlp_error_bound(helpers.mlp_features(occ_h, dims, np.arange(lat.nsites)), w)
     tol = eb.sum() + lat.nsites * 2.0 ** -40 * np.abs(f).sum() + 1e-12
@@ -223,7 +225,7 @@ def test_mlp_energy_bookkeeping_and_composition(smc):
     bounds of both, and the composition is unchanged."""
     dims, S, seed, kT = (16, 16, 16), 5, 8, K_B * 800.0
     gm, _, w, _ = make_models(smc, 2)
-    lat, occ, counts = start_state(smc, dims, S, seed)
+    lat, occ, counts, _ = start_state(smc, dims, S, seed)
     e0 = torch.zeros(1, dtype=torch.float64, device=dev())
     e1 = torch.zeros(1, dtype=torch.float64, device=dev())
     e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
@@ -267,7 +269,7 @@ def test_config4_full_size_sampled(smc):
     kT = K_B * c["T"]
     seed = c["mc_seed"]
     gm, om, w, _ = make_models(smc, 2, mlp_seed=c["mlp_seed"])
-    lat, occ, counts = start_state(smc, dims, S, seed, counts_seed=c["comp_seed"])
+    lat, occ, counts, ref = start_state(smc, dims, S, seed, counts_seed=c["comp_seed"])
     occ2 = occ.clone()
     n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
     smc.sweep(lat, gm, occ, seed, 0, 1, kT, n_acc=n_acc)
@@ -280,15 +282,17 @@ def test_config4_full_size_sampled(smc):
     nv = oracle.shell_vectors(1)
     rng = np.random.default_rng(0)
     for k in range(128):
-        if k == k_s:
-            occ_h = occ2.cpu().numpy().copy()
         smc.ministep_trace(lat, gm, occ2, seed, 0, k, kT, dE, acc)
-        if k == k_s:
-            d_g = dE.cpu().numpy().astype(np.float64)
     smc.check()
     assert torch.equal(occ, occ2)
     assert np.array_equal(np.bincount(occ.cpu().numpy(), minlength=S), counts)
     assert 0 < n_acc.item() < lat.nsites
+    # mini-step k_s on the oracle's start state (a valid input to any mini-step)
+    occ_h = ref
+    occ2.copy_(torch.from_numpy(ref.copy()).to(dev()))
+    smc.ministep_trace(lat, gm, occ2, seed, 0, k_s, kT, dE, acc)
+    smc.check()
+    d_g = dE.cpu().numpy().astype(np.float64)
     # sampled trials of mini-step k_s against the oracle
     nx, ny, nz = dims
     NLx, NLy = nx // 4, ny // 4
@@ -322,7 +326,7 @@ def test_mlp_gradient_matches_oracle(smc, dims, kind, ctas):
     one CTA per SM runs enough blocks per CTA to exercise the FP64 flushes."""
     S = 5
     gm, om, w, V = make_models(smc, kind, biases=True)
-    lat, occ, _ = start_state(smc, dims, S, 17)
+    lat, occ, _, occ_h = start_state(smc, dims, S, 17)
     n = smc.grad_size(lat, gm)
     g = torch.zeros(n, dtype=torch.float32, device=dev())
     try:
@@ -331,7 +335,6 @@ def test_mlp_gradient_matches_oracle(smc, dims, kind, ctas):
         smc.check()
     finally:
         smc.set_tuning()
-    occ_h = occ.cpu().numpy()
     want = oracle.energy_grad(oracle.Lattice(*dims, S), om, occ_h)
     got = g.cpu().numpy().astype(np.float64)
     npair = n - 5569

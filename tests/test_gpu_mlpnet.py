@@ -57,12 +57,13 @@ def models(smc, seed=4):
 
 
 def start(smc, dims, S, seed):
+    """The oracle's start state on the device, and on the host (the oracle
+    never reads a configuration the GPU produced)."""
     N = 2 * dims[0] * dims[1] * dims[2]
     counts = inputs.dirichlet_counts(N, S, 4)
     lat = smc.Lattice(*dims, S)
-    occ = torch.empty(N, dtype=torch.int8, device=dev())
-    smc.init_lattice(lat, counts, seed, occ)
-    return lat, occ, counts
+    ref = oracle.init_lattice(oracle.Lattice(*dims, S), counts, seed)
+    return lat, torch.from_numpy(ref.copy()).to(dev()), counts, ref
 
 
 def emulated(occ_h, dims, a, b, w, dE64):
@@ -92,17 +93,17 @@ def threshold(seed, sweep, a, kT):
 def test_lockstep_against_oracle(smc, dims, T, ks):
     S, seed, kT = 5, 11, K_B * T
     gm, om, w = models(smc)
-    lat, occ, _ = start(smc, dims, S, seed)
+    lat, occ, counts, ref = start(smc, dims, S, seed)
     olat = oracle.Lattice(*dims, S)
     nt = lat.nsites // 128
     dE = torch.zeros(nt, dtype=torch.float32, device=dev())
     acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
     errs, emus, flips, n = [], [], 0, 0
     for k in ks:
-        occ_h = occ.cpu().numpy().copy()
+        occ_h = ref.copy()  # the pre-step state, the oracle's
         smc.ministep_trace(lat, gm, occ, seed, 0, k, kT, dE, acc)
         smc.check()
-        d_o, a_o, a, b = oracle.ministep_trace(olat, om, occ_h.copy(), seed, 0, k, kT)
+        d_o, a_o, a, b = oracle.ministep_trace(olat, om, ref, seed, 0, k, kT)
         d_g = dE.cpu().numpy().astype(np.float64)
         a_g = acc.cpu().numpy().astype(bool)
         emu, tight = emulated(occ_h, dims, a, b, w, d_o)
@@ -113,6 +114,8 @@ def test_lockstep_against_oracle(smc, dims, T, ks):
             lo, hi = sorted((d_g[t], d_o[t]))
             assert lo - 1e-6 * kT <= thr <= hi + 1e-6 * kT, (k, t, d_g[t], d_o[t], thr)
             flips += 1
+        if np.any(a_g != a_o):  # the GPU continues from the oracle's state
+            occ.copy_(torch.from_numpy(ref.copy()).to(dev()))
         errs.append(err)
         emus.append(d_g - emu)
         n += nt
@@ -130,7 +133,7 @@ def test_lockstep_against_oracle(smc, dims, T, ks):
 def test_sweep_equals_trace(smc, dims):
     S, seed, kT = 5, 21, K_B * 800.0
     gm, _, _ = models(smc, seed=6)
-    lat, occ, counts = start(smc, dims, S, seed)
+    lat, occ, counts, _ = start(smc, dims, S, seed)
     occ2 = occ.clone()
     e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
     n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
@@ -158,11 +161,10 @@ def test_sweep_equals_trace(smc, dims):
 def test_energy_against_emulation_and_oracle(smc):
     S, dims = 5, (16, 8, 12)
     gm, om, w = models(smc)
-    lat, occ, _ = start(smc, dims, S, 3)
+    lat, occ, _, occ_h = start(smc, dims, S, 3)
     e = torch.zeros(1, dtype=torch.float64, device=dev())
     smc.energy(lat, gm, occ, e)
     smc.check()
-    occ_h = occ.cpu().numpy()
     f, bound = helpers.mlpnet_bf16_emulation(helpers.mlp_features(occ_h, dims, np.arange(lat.nsites)), w)
     assert abs(float(e.item()) - f.sum()) <= bound.sum() + 1e-9 * np.abs(f).sum()
     e64 = oracle.total_energy(oracle.Lattice(*dims, S), om, occ_h)
@@ -171,7 +173,7 @@ def test_energy_against_emulation_and_oracle(smc):
 
 def test_gradient_is_not_offered(smc):
     gm, _, _ = models(smc)
-    lat, occ, _ = start(smc, (8, 8, 8), 5, 1)
+    lat, occ, _, _ = start(smc, (8, 8, 8), 5, 1)
     assert smc.grad_size(lat, gm) == -1
     with pytest.raises(smc.SMCError):
         smc.energy_grad(lat, gm, occ, torch.zeros(8, dtype=torch.float32, device=dev()))

@@ -161,7 +161,8 @@ def test_f32_lockstep_against_oracle(smc, dims, kT):
     """Every trial of every mini-step of two sweeps: |dE_gpu - dE_oracle| <=
     1e-5 eV and the same decision (flips resynchronise the oracle)."""
     V, counts, lat, occ, model, olat, omodel = _f32_setup(smc, dims)
-    ref = occ.cpu().numpy().copy()
+    ref = oracle.init_lattice(olat, counts, 3)  # the oracle's own start state (== the GPU's)
+    assert np.array_equal(occ.cpu().numpy(), ref)
     nA, _ = oracle.schedule(olat)
     nt = olat.nsites // nA
     dE = torch.zeros(nt, dtype=torch.float32, device=dev())
@@ -176,9 +177,9 @@ def test_f32_lockstep_against_oracle(smc, dims, kT):
             worst = max(worst, float(np.abs(g - odE).max()))
             assert np.all(np.abs(g - odE) <= DE_TOL_EV)
             ga = acc.cpu().numpy().astype(bool)
-            if not np.array_equal(ga, oacc):
+            if not np.array_equal(ga, oacc):  # the GPU continues from the oracle's state
                 flips += int((ga != oacc).sum())
-                ref[:] = occ.cpu().numpy()
+                occ.copy_(torch.from_numpy(ref.copy()).to(dev()))
             else:
                 assert np.array_equal(occ.cpu().numpy(), ref)
     assert flips <= 1, flips
@@ -279,9 +280,10 @@ def test_timeout_is_reported_and_gpu_stays_usable(smc):
 
 
 def test_config2_full_size_sampled(smc):
-    """128^3 cells, quinary, FP32 2-shell model: one sweep at 3000 K, then
-    mini-step 0 of the next sweep traced and compared trial by trial on a
-    sample; composition conserved; accumulated dE equals the recomputed E."""
+    """128^3 cells, quinary, FP32 2-shell model: two sweeps of the anneal
+    (composition conserved, accumulated dE equal to the recomputed E), then
+    on the oracle's start state mini-step 0 of sweep 2 traced and compared
+    trial by trial."""
     c = inputs.CONFIG2
     dims, S = c["cells"], c["nspecies"]
     V = inputs.pair_f32_coeffs(c["coeff_seed"], 2, S)
@@ -300,8 +302,10 @@ def test_config2_full_size_sampled(smc):
     err = abs(float(e1.item()) - (float(e0.item()) + float(e_acc.item())))
     assert err <= acc_tol(int(n_acc.item()), V, dims[0]), (err, int(n_acc.item()))
     assert np.array_equal(np.bincount(occ.cpu().numpy(), minlength=S), counts)
+    # mini-step 0 of sweep 2 on the oracle's start state (a valid input to any mini-step)
     olat, omodel = oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V)
-    ref = occ.cpu().numpy().copy()
+    ref = oracle.init_lattice(olat, counts, c["mc_seed"])
+    occ.copy_(torch.from_numpy(ref.copy()).to(dev()))
     nt = olat.nsites // 128
     dE = torch.zeros(nt, dtype=torch.float32, device=dev())
     acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
