@@ -5,7 +5,7 @@ the C ABI.
 Integer models: the start state, trajectories, accepted counts, accepted
 energy sums and total energies bit-exact.  FP32 models: every trial's dE
 within DE_TOL_EV of the FP64 oracle and the same decision, mini-step by
-mini-step (lock-step; a decision flip resynchronises the oracle); the sweep
+mini-step (lock-step; after a decision flip the GPU continues from the oracle's state); the sweep
 equals its traced mini-steps bit for bit; energies from exact pair counts in
 FP64."""
 import math
@@ -276,7 +276,7 @@ def _qsro_models(smc, seed, nsh, S):
 def test_qsro_lockstep_against_oracle(smc, dims, nsh, S):
     """Every trial of a sweep (24^3: 64 of the 256 mini-steps, mostly interior
     link cells): dE within 1e-5 eV of the FP64 oracle, the same decisions
-    (a flip resynchronises the oracle), 800 K."""
+    (after a flip the GPU continues from the oracle's state), 800 K."""
     model, omodel = _qsro_models(smc, 7 + nsh, nsh, S)
     lat, occ, olat, ref = _state(smc, dims, S, 4)
     kT = inputs.K_B_EV * 800.0

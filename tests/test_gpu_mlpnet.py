@@ -5,9 +5,9 @@ accumulation) against the FP64 oracle, through the C ABI.
 Every trial's dE must lie within the tight bound of an FP64 emulation of the
 BF16 evaluation order (tests/helpers.mlpnet_bf16_emulation), and decide as
 the FP64 oracle except where the acceptance threshold lies between the GPU's
-and the oracle's values (the run then follows the GPU).  The sweep kernel
-(cached pre-swap energies and features) must equal its traced mini-steps
-(recomputed energies) bit for bit.  Statistics go to
+and the oracle's values (the GPU then continues from the oracle's state).
+The sweep kernel (cached pre-swap energies and features) must equal its
+traced mini-steps (recomputed energies) bit for bit.  Statistics go to
 $SMC_STATS_DIR/mlpnet_dE_errors.json when that is set."""
 import json
 import math

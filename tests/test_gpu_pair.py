@@ -2,7 +2,8 @@
 
 Integer models: bit-exact trajectories, energies, counts.  FP32 models: every
 trial's dE within 1e-5 eV of the FP64 oracle and identical decisions, checked
-mini-step by mini-step (lock-step, resynchronising on a decision flip)."""
+mini-step by mini-step (lock-step; after a decision flip the GPU continues
+from the oracle's state)."""
 import math
 
 import numpy as np
@@ -159,7 +160,8 @@ def _f32_setup(smc, dims, S=5, seed=3, vseed=2):
 @pytest.mark.parametrize("dims,kT", [((8, 8, 8), 0.06), ((16, 12, 8), 0.03), ((12, 8, 6), 0.2)])
 def test_f32_lockstep_against_oracle(smc, dims, kT):
     """Every trial of every mini-step of two sweeps: |dE_gpu - dE_oracle| <=
-    1e-5 eV and the same decision (flips resynchronise the oracle)."""
+    1e-5 eV and the same decision (after a flip the GPU continues from the
+    oracle's state)."""
     V, counts, lat, occ, model, olat, omodel = _f32_setup(smc, dims)
     ref = oracle.init_lattice(olat, counts, 3)  # the oracle's own start state (== the GPU's)
     assert np.array_equal(occ.cpu().numpy(), ref)

@@ -6,9 +6,9 @@ zone of f(x') - f(x) in FP32: for a and b from their full site energies
 (without the constant C), for the other zone sites from the one or two
 count changes the swap makes.  Every trial's dE must lie within DE_TOL_EV of
 the FP64 oracle and decide the same, except where the acceptance threshold
-lies between the two values (the oracle then follows the GPU).  The sweep
-kernel (features from its cache) must equal its traced mini-steps (features
-counted from the occupancy) bit for bit.  Energies and dE/dtheta come from
+lies between the two values (the GPU then continues from the oracle's
+state).  The sweep kernel (features from its cache) must equal its traced
+mini-steps (features counted from the occupancy) bit for bit.  Energies and dE/dtheta come from
 exact integer counts in FP64."""
 import math
 
