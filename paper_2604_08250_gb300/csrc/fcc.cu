@@ -1,5 +1,6 @@
 // fcc.cu -- swap Monte Carlo on the FCC lattice (the paper's lattice, Sec.
-// IV-C; 4x4x4 link cells and 256 mini-steps as in Sec. V-C) with pair models.
+// IV-C; 4x4x4 link cells and 256 mini-steps as in Sec. V-C) with pair models
+// and the qSRO model (Sec. IV-B, Eq. quadratic_local_SRO).
 //
 // Geometry: nx x ny x nz cubic cells of 4 sites at half-unit offsets
 // (0,0,0), (1,1,0), (1,0,1), (0,1,1) (sublattices 0-3), site id
@@ -722,7 +723,7 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.seed = seed;
     P.replica = replica;
     const int nc = P.nA_cells;
-    // workspace: [part_e | part_n | acceptance tables]
+    // integer acceptance tables of every sweep of the call, back to back
     std::vector<uint32_t> tabs;
     std::vector<int2> tinfo((size_t)std::max(nsweeps, 1));
     if (is_int)
