@@ -261,7 +261,8 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
  * smc_fcc_init_lattice: the composition-conserving start state (the
  * smc_init_lattice order over the same N site ids).  The other calls have
  * the arguments and errors of their BCC counterparts; e_acc sums per link
- * cell and then in link-cell order; smc_fcc_ministep_trace runs the sweep
+ * cell, then over the link cells in a fixed order (bit-reproducible);
+ * smc_fcc_ministep_trace runs the sweep
  * kernel on one mini-step and records its per-trial dE and decisions.
  * Errors: SMC_ERR_UNSUPPORTED for other model kinds, and for sweeps and
  * traces on a box whose axes are not multiples of 4 of at least 8 cells

@@ -425,18 +425,36 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
     if (P.acc_out) P.acc_out[c] = acc ? 1 : 0;
 }
 
-// e_acc += sum of part_e, n_acc += sum of part_n, in link-cell order.
-__global__ void k_fcc_reduce(const double *part_e, const long long *part_n, int n, double *e_acc, long long *n_acc)
+// e_acc += sum of part_e, n_acc += sum of part_n, in a fixed order: thread t
+// sums link cells t, t + 1024, ... in turn, then a fixed pairwise tree over
+// the 1024 partial sums (one block of kFccReduceThreads).
+constexpr int kFccReduceThreads = 1024;
+__global__ void __launch_bounds__(kFccReduceThreads) k_fcc_reduce(const double *part_e, const long long *part_n, int n,
+                                                                  double *e_acc, long long *n_acc)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double se[kFccReduceThreads];
+    __shared__ long long sn[kFccReduceThreads];
+    const int t = threadIdx.x;
     double e = 0.0;
     long long c = 0;
-    for (int i = 0; i < n; ++i) {
+    for (int i = t; i < n; i += kFccReduceThreads) {
         e += part_e[i];
         c += part_n[i];
     }
-    if (e_acc) *e_acc += e;
-    if (n_acc) *n_acc += c;
+    se[t] = e;
+    sn[t] = c;
+    __syncthreads();
+    for (int h = kFccReduceThreads / 2; h > 0; h >>= 1) {
+        if (t < h) {
+            se[t] += se[t + h];
+            sn[t] += sn[t + h];
+        }
+        __syncthreads();
+    }
+    if (t == 0) {
+        if (e_acc) *e_acc += se[0];
+        if (n_acc) *n_acc += sn[0];
+    }
 }
 
 // Ordered pair counts n_m^{pq} (each site's shell-m neighbours), per-block
@@ -782,7 +800,7 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
         if (e != cudaSuccess) return cuda_fail(e, "k_fcc_ministep");
     }
     if (e_acc || n_acc) {
-        k_fcc_reduce<<<1, 32, 0, stream>>>(P.part_e, P.part_n, nc, e_acc, (long long *)n_acc);
+        k_fcc_reduce<<<1, kFccReduceThreads, 0, stream>>>(P.part_e, P.part_n, nc, e_acc, (long long *)n_acc);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "k_fcc_reduce");
     }
