@@ -53,7 +53,9 @@ namespace {
 constexpr int kFccT = kMaxShells * 8 * 8 * 8, kFccD = kFccT, kFccN1 = kFccD + 4 * 42, kFccVec = kFccN1 + 4 * 12,
               kFccWords = kFccVec + 42;
 
-struct FccParams {
+// What the mini-step and cache kernels read (a small launch parameter block:
+// 256 launches per sweep).
+struct FccStep {
     int nx, ny, nz, S, nshells, nA_cells;  // nA_cells: link cells (trials per mini-step)
     int NLx, NLy, NLz;
     int n_int, n_bnd, bnd_blocks;          // interior / face link cells, blocks of the face part (run first)
@@ -69,11 +71,15 @@ struct FccParams {
     long long *part_n;
     float *dE_out;        // trace (nullable)
     uint8_t *acc_out;
+    void *qcache;  // qSRO: own-species counts per shell of every site (1 byte for 1-2 shells, 2 for 3)
+};
+
+// The model as the energy kernels read it.
+struct FccParams : FccStep {
     int vi[kMaxShells * kMaxSpecies * kMaxSpecies];
     float vf[kMaxShells * kMaxSpecies * kMaxSpecies];
     float wq[kMaxShells * kMaxSpecies];  // qSRO W_m^p
     double qc;                           // qSRO C
-    void *qcache;  // qSRO: own-species counts per shell of every site (1 byte for 1-2 shells, 2 for 3)
 };
 
 // Own-species count fields of the qSRO cache: shell 1 in bits 0-3 (<= 12),
@@ -130,7 +136,7 @@ __device__ __forceinline__ FccPos fcc_pos(int sub, int x, int y, int z)
                   2 * z + ((sub == 2 || sub == 3) ? 1 : 0)};
 }
 
-__device__ __forceinline__ int fcc_site_at(const FccParams &P, int px, int py, int pz)
+__device__ __forceinline__ int fcc_site_at(const FccStep &P, int px, int py, int pz)
 {
     const int ox = px & 1, oy = py & 1;
     const int nsub = (0x6C >> ((ox << 2) | (oy << 1))) & 3;  // parities (1,1) -> 1, (1,0) -> 2, (0,1) -> 3
@@ -164,7 +170,7 @@ __device__ __forceinline__ int3 fcc_face_cell(int j, int NLx, int NLy, int NLz)
 }
 
 template <bool IS_INT, int NSH>
-__global__ void __launch_bounds__(256) k_fcc_ministep(const __grid_constant__ FccParams P, int k)
+__global__ void __launch_bounds__(256) k_fcc_ministep(const __grid_constant__ FccStep P, int k)
 {
     using T = typename Acc<IS_INT>::T;
     using Word = typename std::conditional<IS_INT, int, float>::type;
@@ -262,7 +268,7 @@ __device__ __forceinline__ int3 fcc_woff(int w) { return make_int3(w % 7 - 3, (w
 
 // qSRO cache: for every site, the number of its shell-m neighbours of its own
 // species, in field m (fcc_qoff).
-__global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ FccParams P)
+__global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ FccStep P)
 {
     const int N = 4 * P.nx * P.ny * P.nz;
     for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
@@ -292,7 +298,7 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ 
 // around each (b counted in a's shell 1 and a in b's).  C cancels.  The zone
 // is walked in category order, so ma and mb are compile-time constants.
 template <int NSH>
-__global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant__ FccParams P, int k)
+__global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant__ FccStep P, int k)
 {
     using QT = typename std::conditional<NSH == 3, uint16_t, uint8_t>::type;
     constexpr int NZ = NSH == 1 ? 18 : (NSH == 2 ? 26 : 58);
@@ -711,7 +717,7 @@ smc_status fcc_sweep_tables(const smc_lattice *lat, const smc_model *m, std::vec
     return SMC_OK;
 }
 
-using FccKernel = void (*)(FccParams, int);
+using FccKernel = void (*)(FccStep, int);
 
 template <bool IS_INT>
 FccKernel pick_fcc(int nshells)
@@ -784,7 +790,7 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     if (is_qsro) {  // the count cache, from the occupancy at the start of every call
         P.qcache = scr + off_q;
         const int cb = (int)std::max<size_t>(1, std::min<size_t>((N + 255) / 256, (size_t)ws->num_sms * 16));
-        k_fcc_qsro_cache<<<cb, 256, 0, stream>>>(P);
+        k_fcc_qsro_cache<<<cb, 256, 0, stream>>>(static_cast<const FccStep &>(P));
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "k_fcc_qsro_cache");
     }
@@ -795,7 +801,8 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
         const int k0 = trace_k >= 0 ? trace_k : 0, k1 = trace_k >= 0 ? trace_k + 1 : 256;
         P.dE_out = trace_dE;
         P.acc_out = trace_acc;
-        for (int k = k0; k < k1; ++k) kern<<<blocks, threads, 0, stream>>>(P, k);
+        const FccStep step = P;
+        for (int k = k0; k < k1; ++k) kern<<<blocks, threads, 0, stream>>>(step, k);
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "k_fcc_ministep");
     }
