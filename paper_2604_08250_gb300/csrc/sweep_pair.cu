@@ -1187,11 +1187,17 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const
     const size_t dbytes = (size_t)fast_d_bytes(nsh_t, ST);
     // Total warps NW: all resident at once (cooperative launch); preferably a
     // divisor of the tile count so that every warp owns as many tiles as the
-    // others (an unevenly loaded warp makes its neighbours wait).
+    // others (an unevenly loaded warp makes its neighbours wait).  Between
+    // CTA sizes giving as many warps, the one whose CTAs spread evenly over
+    // the SMs (at most one per SM, or a multiple of the SM count) wins: a
+    // warp that shares its scheduler with more warps than the others runs
+    // slower and its neighbours wait for it (128^3: 1,024 warps as 128 CTAs
+    // of 8 run a sweep in 199 us, as 256 CTAs of 4 in 226 us).
     auto search = [&](int rb, Plan &out) -> long long {
         const size_t rows_bytes = (size_t)(nsh_t >= 3 ? 25 : 21) * rb + 16 + (size_t)512 * nkmax;
         const int cand[2] = {128, 256};
         long long best_nw = 0;
+        bool best_even = false;
         for (int ci = 0; ci < 2; ++ci) {
             const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // launch bound is 256
             if (tu.threads && ci > 0) break;
@@ -1210,8 +1216,11 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const
                 (void)res;
                 const int tpc = (int)((pl.ntiles + nw - 1) / nw);
                 if (tpc <= tpc_guess) {
-                    if (nw > best_nw) {
+                    const long long grid = nw / nwarps;
+                    const bool even = grid <= ws->num_sms || grid % ws->num_sms == 0;
+                    if (nw > best_nw || (nw == best_nw && even && !best_even)) {
                         best_nw = nw;
+                        best_even = even;
                         out.threads = threads;
                         out.grid = (int)(nw / nwarps);
                         out.tpc = tpc_guess;
