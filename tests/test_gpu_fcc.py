@@ -272,7 +272,8 @@ def _qsro_models(smc, seed, nsh, S):
             oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C))
 
 
-@pytest.mark.parametrize("dims,nsh,S", [((8, 8, 8), 3, 5), ((12, 8, 16), 2, 4), ((24, 24, 24), 3, 5)])
+@pytest.mark.parametrize("dims,nsh,S", [((8, 8, 8), 3, 5), ((12, 8, 16), 2, 4), ((24, 24, 24), 3, 5),
+                                        ((8, 12, 8), 2, 8), ((12, 8, 8), 1, 2)])
 def test_qsro_lockstep_against_oracle(smc, dims, nsh, S):
     """Every trial of a sweep (24^3: 64 of the 256 mini-steps, mostly interior
     link cells): dE within 1e-5 eV of the FP64 oracle, the same decisions
