@@ -9,6 +9,7 @@
 //   alpha_m^{pq} = 1 - n_m^{pq} / (N c_p z_m c_q),
 //   dE/dV_m^{pq} = n_m^{pq} (p < q),  n_m^{pp} / 2 (p = q).
 #include <algorithm>
+#include <cstdint>
 
 #include "smc_common.cuh"
 
@@ -100,6 +101,148 @@ __global__ void __launch_bounds__(256) k_pair_counts(const int8_t *__restrict__ 
     }
 }
 
+// The same counts for rows of nx % 16 == 0 bytes, with 16-byte loads: lane l
+// of a warp takes sites x = 16 l .. 16 l + 15 of a 512-site chunk of the row
+// and reads each neighbour row once as a uint4 (plus one 4-byte word for the
+// byte before or after the 16), instead of 16 byte loads; the species count
+// S is a template parameter so that a site's histogram goes to its own
+// species' counters in S selects.
+__device__ __forceinline__ unsigned fcount_byte(const uint4 &w, int k)
+{
+    const unsigned v = k < 4 ? w.x : (k < 8 ? w.y : (k < 12 ? w.z : w.w));
+    return (v >> (8 * (k & 3))) & 7u;
+}
+
+template <int NSH, int S>
+__global__ void __launch_bounds__(256) k_pair_counts16(const int8_t *__restrict__ occ, int nx, int ny, int nz,
+                                                       unsigned long long *counts)
+{
+    __shared__ unsigned long long bins[NSH * 64];
+    for (int i = threadIdx.x; i < NSH * 64; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const long long nrows = 2LL * nz * ny;
+    const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+    const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+    const unsigned char *o = (const unsigned char *)occ;
+    const int nw4 = nx >> 2;
+    for (long long row = w0; row < nrows; row += nw) {
+        const int sub = (int)(row / ((long long)nz * ny));
+        const int rem = (int)(row - (long long)sub * nz * ny);
+        const int z = rem / ny, y = rem - (rem / ny) * ny;
+        auto R = [&](int sb, int zz, int yy) {
+            return o + ((size_t)((sb * nz + wrapc(zz, nz)) * ny + wrapc(yy, ny))) * nx;
+        };
+        for (int x0 = 0; x0 < nx; x0 += 32 * 16) {
+            unsigned long long acc[NSH][S];
+#pragma unroll
+            for (int m = 0; m < NSH; ++m)
+#pragma unroll
+                for (int q = 0; q < S; ++q) acc[m][q] = 0;
+            const int xb = x0 + 16 * lane;
+            if (xb < nx) {
+                const int wprev = (xb >> 2) == 0 ? nw4 - 1 : (xb >> 2) - 1, wnext = ((xb + 16) >> 2) % nw4;
+                auto V = [&](const unsigned char *r) { return __ldg(reinterpret_cast<const uint4 *>(r + xb)); };
+                auto PREV = [&](const unsigned char *r) { return (__ldg(reinterpret_cast<const unsigned *>(r) + wprev) >> 24) & 7u; };
+                auto NEXT = [&](const unsigned char *r) { return __ldg(reinterpret_cast<const unsigned *>(r) + wnext) & 7u; };
+                const unsigned char *self = R(sub, z, y);
+                const uint4 vs = V(self);
+                unsigned ns = 0;
+                uint4 v00, v01, v10, v11, vy1, vz1, vym, vzm, vz1y1, vzmy1;
+                unsigned p00 = 0, p01 = 0, p10 = 0, p11 = 0, ny1 = 0, nym = 0, nz1 = 0, nzm = 0;
+                if (sub == 0) {
+                    const unsigned char *r00 = R(1, z - 1, y - 1), *r01 = R(1, z - 1, y), *r10 = R(1, z, y - 1),
+                                        *r11 = R(1, z, y);
+                    v00 = V(r00);
+                    v01 = V(r01);
+                    v10 = V(r10);
+                    v11 = V(r11);
+                    p00 = PREV(r00);
+                    p01 = PREV(r01);
+                    p10 = PREV(r10);
+                    p11 = PREV(r11);
+                }
+                if (NSH >= 2) {
+                    const unsigned char *ry1 = R(sub, z, y + 1), *rz1 = R(sub, z + 1, y);
+                    ns = NEXT(self);
+                    vy1 = V(ry1);
+                    vz1 = V(rz1);
+                    if (NSH >= 3) {
+                        const unsigned char *rym = R(sub, z, y - 1), *rzm = R(sub, z - 1, y);
+                        ny1 = NEXT(ry1);
+                        nz1 = NEXT(rz1);
+                        vym = V(rym);
+                        vzm = V(rzm);
+                        nym = NEXT(rym);
+                        nzm = NEXT(rzm);
+                        vz1y1 = V(R(sub, z + 1, y + 1));
+                        vzmy1 = V(R(sub, z - 1, y + 1));
+                    }
+                }
+                // byte k of a row window, k = -1 and 16 from the neighbouring words
+                auto B = [&](const uint4 &w, unsigned prev, unsigned next, int k) -> unsigned {
+                    return k < 0 ? prev : (k > 15 ? next : fcount_byte(w, k));
+                };
+#pragma unroll
+                for (int k = 0; k < 16; ++k) {
+                    const unsigned p = fcount_byte(vs, k);
+                    unsigned long long h[3] = {0ull, 0ull, 0ull};
+                    if (sub == 0)
+                        h[0] = (1ull << (8 * B(v00, p00, 0, k - 1))) + (1ull << (8 * fcount_byte(v00, k))) +
+                               (1ull << (8 * B(v01, p01, 0, k - 1))) + (1ull << (8 * fcount_byte(v01, k))) +
+                               (1ull << (8 * B(v10, p10, 0, k - 1))) + (1ull << (8 * fcount_byte(v10, k))) +
+                               (1ull << (8 * B(v11, p11, 0, k - 1))) + (1ull << (8 * fcount_byte(v11, k)));
+                    if (NSH >= 2)
+                        h[1] = (1ull << (8 * B(vs, 0, ns, k + 1))) + (1ull << (8 * fcount_byte(vy1, k))) +
+                               (1ull << (8 * fcount_byte(vz1, k)));
+                    if (NSH >= 3)
+                        h[2] = (1ull << (8 * B(vy1, 0, ny1, k + 1))) + (1ull << (8 * B(vym, 0, nym, k + 1))) +
+                               (1ull << (8 * B(vz1, 0, nz1, k + 1))) + (1ull << (8 * B(vzm, 0, nzm, k + 1))) +
+                               (1ull << (8 * fcount_byte(vz1y1, k))) + (1ull << (8 * fcount_byte(vzmy1, k)));
+#pragma unroll
+                    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+                        for (int q = 0; q < S; ++q) acc[m][q] += (p == (unsigned)q) ? h[m] : 0ull;
+                }
+            }
+            // 16 sites per lane x at most 8 per bin: no 8-bit field has overflowed
+#pragma unroll
+            for (int m = 0; m < NSH; ++m)
+#pragma unroll
+                for (int pp = 0; pp < S; ++pp)
+#pragma unroll
+                    for (int q = 0; q < S; ++q) {
+                        const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)((acc[m][pp] >> (8 * q)) & 0xFFu));
+                        if (lane == 0 && v) atomicAdd(&bins[m * 64 + pp * 8 + q], (unsigned long long)v);
+                    }
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NSH * 64; i += blockDim.x) {
+        const int m = i / 64, pp = (i / 8) % 8, q = i % 8;
+        if (pp < S && q < S) {
+            const unsigned long long c = bins[i] + bins[m * 64 + q * 8 + pp];
+            if (c) atomicAdd(counts + (m * S + pp) * S + q, c);
+        }
+    }
+}
+
+template <int NSH>
+void launch_counts16(int S, int blocks, int threads, const int8_t *occ, int nx, int ny, int nz,
+                     unsigned long long *counts, cudaStream_t stream)
+{
+    switch (S) {
+    case 1: k_pair_counts16<NSH, 1><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 2: k_pair_counts16<NSH, 2><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 3: k_pair_counts16<NSH, 3><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 4: k_pair_counts16<NSH, 4><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 5: k_pair_counts16<NSH, 5><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 6: k_pair_counts16<NSH, 6><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    case 7: k_pair_counts16<NSH, 7><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    default: k_pair_counts16<NSH, 8><<<blocks, threads, 0, stream>>>(occ, nx, ny, nz, counts); break;
+    }
+}
+
 smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t *occ, unsigned long long *counts,
                               cudaStream_t stream)
 {
@@ -113,7 +256,14 @@ smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t 
     const int threads = 256;
     const long long want = (rows + 7) / 8;
     const int blocks = (int)std::max(1LL, std::min<long long>(want, (long long)ws->num_sms * 8));
-    if (nshells == 1)
+    if (lat->nx % 16 == 0 && reinterpret_cast<uintptr_t>(occ) % 16 == 0) {
+        if (nshells == 1)
+            launch_counts16<1>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+        else if (nshells == 2)
+            launch_counts16<2>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+        else
+            launch_counts16<3>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+    } else if (nshells == 1)
         k_pair_counts<1><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);
     else if (nshells == 2)
         k_pair_counts<2><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);

@@ -213,7 +213,10 @@ def test_f32_sweep_kernel_equals_trace_kernel(smc, dims):
 def test_counts_sro_energy_grad_match_oracle(smc):
     for dims, S, nsh in (((8, 8, 8), 5, 3), ((6, 10, 4), 3, 2), ((2, 2, 2), 2, 3), ((16, 16, 16), 8, 3),
                          ((2, 6, 4), 3, 1), ((40, 8, 12), 5, 2), ((600, 2, 3), 4, 3), ((3, 5, 7), 2, 2),
-                         ((1100, 4, 2), 8, 3)):
+                         ((1100, 4, 2), 8, 3),
+                         # rows of a multiple of 16 cells take the 16-byte-load kernel
+                         ((32, 8, 12), 5, 2), ((48, 2, 4), 3, 1), ((16, 6, 10), 2, 3), ((528, 4, 2), 4, 3),
+                         ((1024, 2, 2), 7, 2), ((64, 4, 4), 6, 1)):
         N = 2 * dims[0] * dims[1] * dims[2]
         counts = inputs.equiatomic_counts(N, S)
         lat, occ = gpu_state(smc, dims, S, counts, 21)
