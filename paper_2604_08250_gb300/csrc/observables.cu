@@ -101,7 +101,8 @@ __global__ void __launch_bounds__(256) k_pair_counts(const int8_t *__restrict__ 
     }
 }
 
-// The same counts for rows of nx % 16 == 0 bytes, with 16-byte loads: lane l
+// The same counts for rows of nx % 16 == 0 bytes (and a 16-byte aligned
+// occupancy array), with 16-byte loads: lane l
 // of a warp takes sites x = 16 l .. 16 l + 15 of a 512-site chunk of the row
 // and reads each neighbour row once as a uint4 (plus one 4-byte word for the
 // byte before or after the 16), instead of 16 byte loads; the species count
