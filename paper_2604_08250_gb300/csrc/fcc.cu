@@ -38,6 +38,7 @@
 #include <array>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <type_traits>
 #include <vector>
 
@@ -747,14 +748,19 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
     P.seed = seed;
     P.replica = replica;
     const int nc = P.nA_cells;
-    // integer acceptance tables of every sweep of the call, back to back
+    // integer acceptance tables, one per distinct kT of the call, back to back
     std::vector<uint32_t> tabs;
     std::vector<int2> tinfo((size_t)std::max(nsweeps, 1));
+    std::map<double, int2> tindex;
     if (is_int)
         for (int t = 0; t < nsweeps; ++t) {
-            const std::vector<uint32_t> tb = int_table(m->unit_ev, kT[t]);
-            tinfo[t] = make_int2((int)tabs.size(), (int)tb.size());
-            tabs.insert(tabs.end(), tb.begin(), tb.end());
+            auto it = tindex.find(kT[t]);
+            if (it == tindex.end()) {
+                const std::vector<uint32_t> tb = int_table(m->unit_ev, kT[t]);
+                it = tindex.emplace(kT[t], make_int2((int)tabs.size(), (int)tb.size())).first;
+                tabs.insert(tabs.end(), tb.begin(), tb.end());
+            }
+            tinfo[t] = it->second;
         }
     const bool is_qsro = m->kind == SMC_QSRO_F32;
     std::vector<uint32_t> words;
