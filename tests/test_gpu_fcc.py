@@ -384,3 +384,32 @@ def test_qsro_full_size_sampled_trials(smc):
             assert post[a] == pre[b] and post[b] == pre[a]
         else:
             assert post[a] == pre[a] and post[b] == pre[b]
+
+
+def test_degenerate_cases(smc):
+    """One species (dE = 0 everywhere: all accepted, nothing moves) and, for
+    FP32 pair and qSRO models, infinite temperature (every trial accepted
+    whatever dE: trajectories equal the oracle's bit for bit)."""
+    dims = (8, 8, 12)
+    N = 4 * dims[0] * dims[1] * dims[2]
+    lat1 = smc.Lattice(*dims, 1)
+    occ1 = torch.zeros(N, dtype=torch.int8, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_sweep(lat1, smc.Model(smc.PAIR_I32, 3, np.zeros((3, 1, 1), dtype=np.int32), unit_ev=1e-4), occ1, 1, 0,
+                  2, 0.05, e_acc=e_acc, n_acc=n_acc)
+    smc.check()
+    assert int(n_acc.item()) == 2 * N and float(e_acc.item()) == 0.0
+    assert int(occ1.abs().sum().item()) == 0
+    S = 5
+    for kind in ("pair", "qsro"):
+        lat, occ, olat, ref = _state(smc, dims, S, 9)
+        if kind == "pair":
+            V = inputs.pair_f32_coeffs(6, 2, S)
+            gm, om = smc.Model(smc.PAIR_F32, 2, V), oracle.Model(oracle.PAIR_F32, 2, V)
+        else:
+            gm, om = _qsro_models(smc, 6, 2, S)
+        smc.fcc_sweep(lat, gm, occ, 4, 0, 2, float("inf"))
+        oracle.fcc_sweep(olat, om, ref, 4, 0, 2, float("inf"))
+        smc.check()
+        assert np.array_equal(occ.cpu().numpy(), ref), kind

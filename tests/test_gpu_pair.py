@@ -319,3 +319,39 @@ def test_config2_full_size_sampled(smc):
     g = dE.cpu().numpy().astype(np.float64)
     assert np.abs(g - odE).max() <= DE_TOL_EV
     assert (acc.cpu().numpy().astype(bool) != oacc).sum() <= 1
+
+
+def test_degenerate_cases(smc):
+    """One species: every trial swaps equal species (dE = 0, accepted, nothing
+    moves); no sweeps: nothing changes; infinite temperature (FP models):
+    every trial accepted whatever dE, so the FP32 trajectory equals the
+    oracle's bit for bit."""
+    dims = (8, 12, 8)
+    N = 2 * dims[0] * dims[1] * dims[2]
+    lat1 = smc.Lattice(*dims, 1)
+    occ1 = torch.zeros(N, dtype=torch.int8, device=dev())
+    m1 = smc.Model(smc.PAIR_I32, 2, np.zeros((2, 1, 1), dtype=np.int32), unit_ev=1e-4)
+    e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
+    smc.sweep(lat1, m1, occ1, 1, 0, 2, 0.05, e_acc=e_acc, n_acc=n_acc)
+    smc.check()
+    assert int(n_acc.item()) == 2 * N and float(e_acc.item()) == 0.0
+    assert int(occ1.abs().sum().item()) == 0
+    _, on = oracle.sweep(oracle.Lattice(*dims, 1), oracle.Model(oracle.PAIR_I32, 2, np.zeros((2, 1, 1), np.int32),
+                                                                unit_ev=1e-4), np.zeros(N, np.int8), 1, 0, 2, 0.05)
+    assert on == 2 * N
+    # no sweeps
+    S = 5
+    V = inputs.pair_f32_coeffs(4, 2, S)
+    counts = inputs.equiatomic_counts(N, S)
+    lat, occ = gpu_state(smc, dims, S, counts, 2)
+    before = occ.clone()
+    smc.sweep(lat, smc.Model(smc.PAIR_F32, 2, V), occ, 1, 0, 0, [], e_acc=e_acc, n_acc=n_acc)
+    smc.check()
+    assert torch.equal(occ, before) and int(n_acc.item()) == 2 * N
+    # infinite temperature
+    ref = oracle.init_lattice(oracle.Lattice(*dims, S), counts, 2)
+    smc.sweep(lat, smc.Model(smc.PAIR_F32, 2, V), occ, 3, 0, 2, float("inf"))
+    oracle.sweep(oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V), ref, 3, 0, 2, float("inf"))
+    smc.check()
+    assert np.array_equal(occ.cpu().numpy(), ref)
