@@ -102,26 +102,33 @@ __global__ void __launch_bounds__(256) k_pair_counts(const int8_t *__restrict__ 
 }
 
 // The same counts for rows of nx % 16 == 0 bytes (and a 16-byte aligned
-// occupancy array), with 16-byte loads: lane l
-// of a warp takes sites x = 16 l .. 16 l + 15 of a 512-site chunk of the row
-// and reads each neighbour row once as a uint4 (plus one 4-byte word for the
-// byte before or after the 16), instead of 16 byte loads; the species count
-// S is a template parameter so that a site's histogram goes to its own
-// species' counters in S selects.
+// occupancy array), with 16-byte loads: lane l of a warp takes sites
+// x = 16 l .. 16 l + 15 of a 512-site chunk of the row and reads each
+// neighbour row once as a uint4 (plus one 4-byte word for the byte before or
+// after the 16).  A site's neighbour histogram per shell is 8 4-bit fields in
+// one word (at most 8 neighbours per shell); its even and odd fields are
+// added, as 8-bit fields, to the lane's counters of its own species, kept in
+// shared memory [shell][species][lane] (at most 16 x 8 per field per chunk).
+constexpr int kCountWarps = 4;
+
 __device__ __forceinline__ unsigned fcount_byte(const uint4 &w, int k)
 {
     const unsigned v = k < 4 ? w.x : (k < 8 ? w.y : (k < 12 ? w.z : w.w));
     return (v >> (8 * (k & 3))) & 7u;
 }
 
+__device__ __forceinline__ unsigned fcount_nib(unsigned species) { return 1u << (4 * species); }
+
 template <int NSH, int S>
-__global__ void __launch_bounds__(256) k_pair_counts16(const int8_t *__restrict__ occ, int nx, int ny, int nz,
-                                                       unsigned long long *counts)
+__global__ void __launch_bounds__(32 * kCountWarps) k_pair_counts16(const int8_t *__restrict__ occ, int nx, int ny,
+                                                                    int nz, unsigned long long *counts)
 {
     __shared__ unsigned long long bins[NSH * 64];
+    __shared__ uint2 acc_all[kCountWarps][NSH][S][32];
     for (int i = threadIdx.x; i < NSH * 64; i += blockDim.x) bins[i] = 0;
     __syncthreads();
-    const int lane = threadIdx.x & 31;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint2(*acc)[S][32] = acc_all[warp];
     const long long nrows = 2LL * nz * ny;
     const long long w0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
     const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -135,11 +142,10 @@ __global__ void __launch_bounds__(256) k_pair_counts16(const int8_t *__restrict_
             return o + ((size_t)((sb * nz + wrapc(zz, nz)) * ny + wrapc(yy, ny))) * nx;
         };
         for (int x0 = 0; x0 < nx; x0 += 32 * 16) {
-            unsigned long long acc[NSH][S];
 #pragma unroll
             for (int m = 0; m < NSH; ++m)
 #pragma unroll
-                for (int q = 0; q < S; ++q) acc[m][q] = 0;
+                for (int p = 0; p < S; ++p) acc[m][p][lane] = make_uint2(0u, 0u);
             const int xb = x0 + 16 * lane;
             if (xb < nx) {
                 const int wprev = (xb >> 2) == 0 ? nw4 - 1 : (xb >> 2) - 1, wnext = ((xb + 16) >> 2) % nw4;
@@ -187,35 +193,46 @@ __global__ void __launch_bounds__(256) k_pair_counts16(const int8_t *__restrict_
 #pragma unroll
                 for (int k = 0; k < 16; ++k) {
                     const unsigned p = fcount_byte(vs, k);
-                    unsigned long long h[3] = {0ull, 0ull, 0ull};
+                    unsigned h[3] = {0u, 0u, 0u};
                     if (sub == 0)
-                        h[0] = (1ull << (8 * B(v00, p00, 0, k - 1))) + (1ull << (8 * fcount_byte(v00, k))) +
-                               (1ull << (8 * B(v01, p01, 0, k - 1))) + (1ull << (8 * fcount_byte(v01, k))) +
-                               (1ull << (8 * B(v10, p10, 0, k - 1))) + (1ull << (8 * fcount_byte(v10, k))) +
-                               (1ull << (8 * B(v11, p11, 0, k - 1))) + (1ull << (8 * fcount_byte(v11, k)));
+                        h[0] = fcount_nib(B(v00, p00, 0, k - 1)) + fcount_nib(fcount_byte(v00, k)) +
+                               fcount_nib(B(v01, p01, 0, k - 1)) + fcount_nib(fcount_byte(v01, k)) +
+                               fcount_nib(B(v10, p10, 0, k - 1)) + fcount_nib(fcount_byte(v10, k)) +
+                               fcount_nib(B(v11, p11, 0, k - 1)) + fcount_nib(fcount_byte(v11, k));
                     if (NSH >= 2)
-                        h[1] = (1ull << (8 * B(vs, 0, ns, k + 1))) + (1ull << (8 * fcount_byte(vy1, k))) +
-                               (1ull << (8 * fcount_byte(vz1, k)));
+                        h[1] = fcount_nib(B(vs, 0, ns, k + 1)) + fcount_nib(fcount_byte(vy1, k)) +
+                               fcount_nib(fcount_byte(vz1, k));
                     if (NSH >= 3)
-                        h[2] = (1ull << (8 * B(vy1, 0, ny1, k + 1))) + (1ull << (8 * B(vym, 0, nym, k + 1))) +
-                               (1ull << (8 * B(vz1, 0, nz1, k + 1))) + (1ull << (8 * B(vzm, 0, nzm, k + 1))) +
-                               (1ull << (8 * fcount_byte(vz1y1, k))) + (1ull << (8 * fcount_byte(vzmy1, k)));
+                        h[2] = fcount_nib(B(vy1, 0, ny1, k + 1)) + fcount_nib(B(vym, 0, nym, k + 1)) +
+                               fcount_nib(B(vz1, 0, nz1, k + 1)) + fcount_nib(B(vzm, 0, nzm, k + 1)) +
+                               fcount_nib(fcount_byte(vz1y1, k)) + fcount_nib(fcount_byte(vzmy1, k));
+                    if (p < (unsigned)S) {
 #pragma unroll
-                    for (int m = 0; m < NSH; ++m)
-#pragma unroll
-                        for (int q = 0; q < S; ++q) acc[m][q] += (p == (unsigned)q) ? h[m] : 0ull;
+                        for (int m = 0; m < NSH; ++m) {
+                            if (m == 0 && sub != 0) continue;  // shell 1 is counted from sublattice 0
+                            uint2 a = acc[m][p][lane];
+                            a.x += h[m] & 0x0F0F0F0Fu;         // q = 0, 2, 4, 6
+                            a.y += (h[m] >> 4) & 0x0F0F0F0Fu;  // q = 1, 3, 5, 7
+                            acc[m][p][lane] = a;
+                        }
+                    }
                 }
             }
-            // 16 sites per lane x at most 8 per bin: no 8-bit field has overflowed
+            __syncwarp();
+            // 16 sites per lane x at most 8 per field: no 8-bit field has overflowed
 #pragma unroll
             for (int m = 0; m < NSH; ++m)
 #pragma unroll
-                for (int pp = 0; pp < S; ++pp)
+                for (int pp = 0; pp < S; ++pp) {
+                    const uint2 a = acc[m][pp][lane];
 #pragma unroll
                     for (int q = 0; q < S; ++q) {
-                        const unsigned v = __reduce_add_sync(0xffffffffu, (unsigned)((acc[m][pp] >> (8 * q)) & 0xFFu));
+                        const unsigned f = ((q & 1) ? a.y : a.x) >> (8 * (q >> 1));
+                        const unsigned v = __reduce_add_sync(0xffffffffu, f & 0xFFu);
                         if (lane == 0 && v) atomicAdd(&bins[m * 64 + pp * 8 + q], (unsigned long long)v);
                     }
+                }
+            __syncwarp();
         }
     }
     __syncthreads();
@@ -258,12 +275,15 @@ smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t 
     const long long want = (rows + 7) / 8;
     const int blocks = (int)std::max(1LL, std::min<long long>(want, (long long)ws->num_sms * 8));
     if (lat->nx % 16 == 0 && reinterpret_cast<uintptr_t>(occ) % 16 == 0) {
+        const int t16 = 32 * kCountWarps;
+        const int b16 = (int)std::max(1LL, std::min<long long>((rows + kCountWarps - 1) / kCountWarps,
+                                                               (long long)ws->num_sms * 16));
         if (nshells == 1)
-            launch_counts16<1>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+            launch_counts16<1>(S, b16, t16, occ, lat->nx, lat->ny, lat->nz, counts, stream);
         else if (nshells == 2)
-            launch_counts16<2>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+            launch_counts16<2>(S, b16, t16, occ, lat->nx, lat->ny, lat->nz, counts, stream);
         else
-            launch_counts16<3>(S, blocks, threads, occ, lat->nx, lat->ny, lat->nz, counts, stream);
+            launch_counts16<3>(S, b16, t16, occ, lat->nx, lat->ny, lat->nz, counts, stream);
     } else if (nshells == 1)
         k_pair_counts<1><<<blocks, threads, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, S, counts);
     else if (nshells == 2)
