@@ -61,70 +61,75 @@ class _Model(C.Structure):
 _lib = None
 
 
+def bind(L):
+    """Declares the C signatures on a loaded oracle library (also used by the
+    tests that load deliberately broken builds of the oracle)."""
+    P = C.POINTER
+    L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
+    L.orc_nsites.argtypes = [P(_Lat)]
+    L.orc_nsites.restype = C.c_int64
+    L.orc_neighbor.argtypes = [P(_Lat), C.c_int64, C.c_int, C.c_int, C.c_int]
+    L.orc_neighbor.restype = C.c_int64
+    L.orc_shell_vectors.argtypes = [C.c_int, P(C.c_int)]
+    L.orc_schedule.argtypes = [P(_Lat), P(C.c_int32)]
+    L.orc_init_lattice.argtypes = [P(_Lat), P(C.c_int64), C.c_uint64, C.c_uint32, P(C.c_int8)]
+    L.orc_site_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64]
+    L.orc_site_energy.restype = C.c_double
+    L.orc_total_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+    L.orc_total_energy.restype = C.c_double
+    L.orc_total_energy_i64.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+    L.orc_total_energy_i64.restype = C.c_int64
+    L.orc_delta_e.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64, C.c_int64]
+    L.orc_delta_e.restype = C.c_double
+    L.orc_pair_counts.argtypes = [P(_Lat), C.c_int, P(C.c_int8), P(C.c_int64)]
+    L.orc_sro.argtypes = [P(_Lat), C.c_int, P(C.c_int8), P(C.c_double)]
+    L.orc_accept_table.argtypes = [C.c_double, C.c_double, P(C.c_uint32), C.c_int64]
+    L.orc_accept_table.restype = C.c_int64
+    L.orc_sweep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32,
+                            C.c_uint64, C.c_int32, P(C.c_double), P(C.c_double),
+                            P(C.c_int64), C.c_int]
+    L.orc_ministep_trace.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32,
+                                     C.c_uint64, C.c_int32, C.c_double, P(C.c_double),
+                                     P(C.c_uint8), P(C.c_int64), P(C.c_int64)]
+    L.orc_ministep_trace.restype = C.c_int64
+    L.orc_slab_ghost_cells.argtypes = [P(_Model)]
+    L.orc_slab_ministep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int32, C.c_int32, C.c_int32,
+                                    C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32, C.c_double,
+                                    P(C.c_double), P(C.c_int64)]
+    L.orc_slab_ministep.restype = C.c_int64
+    L.orc_fcc_nsites.argtypes = [P(_Lat)]
+    L.orc_fcc_nsites.restype = C.c_int64
+    L.orc_fcc_neighbor.argtypes = [P(_Lat), C.c_int64, C.c_int, C.c_int, C.c_int]
+    L.orc_fcc_neighbor.restype = C.c_int64
+    L.orc_fcc_shell_vectors.argtypes = [C.c_int, P(C.c_int)]
+    L.orc_fcc_schedule.argtypes = [P(_Lat), P(C.c_int32)]
+    L.orc_fcc_total_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+    L.orc_fcc_total_energy.restype = C.c_double
+    L.orc_fcc_total_energy_i64.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
+    L.orc_fcc_total_energy_i64.restype = C.c_int64
+    L.orc_fcc_delta_e.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64, C.c_int64]
+    L.orc_fcc_delta_e.restype = C.c_double
+    L.orc_fcc_sweep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
+                                P(C.c_double), P(C.c_double), P(C.c_int64)]
+    L.orc_fcc_ministep_trace.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64,
+                                         C.c_int32, C.c_double, P(C.c_double), P(C.c_uint8), P(C.c_int64),
+                                         P(C.c_int64)]
+    L.orc_fcc_ministep_trace.restype = C.c_int64
+    L.orc_grad_size.argtypes = [P(_Lat), P(_Model)]
+    L.orc_grad_size.restype = C.c_int64
+    L.orc_energy_grad.argtypes = [P(_Lat), P(_Model), P(C.c_int8), P(C.c_double)]
+    L.orc_mlp_eval.argtypes = [P(_Model), P(C.c_double)]
+    L.orc_mlpnet_eval.argtypes = [P(_Model), P(C.c_double)]
+    L.orc_mlpnet_eval.restype = C.c_double
+    L.orc_mlp_eval.restype = C.c_double
+    return L
+
+
 def lib():
     global _lib
     if _lib is None:
         build()
-        L = C.CDLL(_LIB_PATH)
-        P = C.POINTER
-        L.orc_philox4x32_10.argtypes = [P(C.c_uint32), P(C.c_uint32), P(C.c_uint32)]
-        L.orc_nsites.argtypes = [P(_Lat)]
-        L.orc_nsites.restype = C.c_int64
-        L.orc_neighbor.argtypes = [P(_Lat), C.c_int64, C.c_int, C.c_int, C.c_int]
-        L.orc_neighbor.restype = C.c_int64
-        L.orc_shell_vectors.argtypes = [C.c_int, P(C.c_int)]
-        L.orc_schedule.argtypes = [P(_Lat), P(C.c_int32)]
-        L.orc_init_lattice.argtypes = [P(_Lat), P(C.c_int64), C.c_uint64, C.c_uint32, P(C.c_int8)]
-        L.orc_site_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64]
-        L.orc_site_energy.restype = C.c_double
-        L.orc_total_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
-        L.orc_total_energy.restype = C.c_double
-        L.orc_total_energy_i64.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
-        L.orc_total_energy_i64.restype = C.c_int64
-        L.orc_delta_e.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64, C.c_int64]
-        L.orc_delta_e.restype = C.c_double
-        L.orc_pair_counts.argtypes = [P(_Lat), C.c_int, P(C.c_int8), P(C.c_int64)]
-        L.orc_sro.argtypes = [P(_Lat), C.c_int, P(C.c_int8), P(C.c_double)]
-        L.orc_accept_table.argtypes = [C.c_double, C.c_double, P(C.c_uint32), C.c_int64]
-        L.orc_accept_table.restype = C.c_int64
-        L.orc_sweep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32,
-                                C.c_uint64, C.c_int32, P(C.c_double), P(C.c_double),
-                                P(C.c_int64), C.c_int]
-        L.orc_ministep_trace.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32,
-                                         C.c_uint64, C.c_int32, C.c_double, P(C.c_double),
-                                         P(C.c_uint8), P(C.c_int64), P(C.c_int64)]
-        L.orc_ministep_trace.restype = C.c_int64
-        L.orc_slab_ghost_cells.argtypes = [P(_Model)]
-        L.orc_slab_ministep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int32, C.c_int32, C.c_int32,
-                                        C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32, C.c_double,
-                                        P(C.c_double), P(C.c_int64)]
-        L.orc_slab_ministep.restype = C.c_int64
-        L.orc_fcc_nsites.argtypes = [P(_Lat)]
-        L.orc_fcc_nsites.restype = C.c_int64
-        L.orc_fcc_neighbor.argtypes = [P(_Lat), C.c_int64, C.c_int, C.c_int, C.c_int]
-        L.orc_fcc_neighbor.restype = C.c_int64
-        L.orc_fcc_shell_vectors.argtypes = [C.c_int, P(C.c_int)]
-        L.orc_fcc_schedule.argtypes = [P(_Lat), P(C.c_int32)]
-        L.orc_fcc_total_energy.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
-        L.orc_fcc_total_energy.restype = C.c_double
-        L.orc_fcc_total_energy_i64.argtypes = [P(_Lat), P(_Model), P(C.c_int8)]
-        L.orc_fcc_total_energy_i64.restype = C.c_int64
-        L.orc_fcc_delta_e.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_int64, C.c_int64]
-        L.orc_fcc_delta_e.restype = C.c_double
-        L.orc_fcc_sweep.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64, C.c_int32,
-                                    P(C.c_double), P(C.c_double), P(C.c_int64)]
-        L.orc_fcc_ministep_trace.argtypes = [P(_Lat), P(_Model), P(C.c_int8), C.c_uint64, C.c_uint32, C.c_uint64,
-                                             C.c_int32, C.c_double, P(C.c_double), P(C.c_uint8), P(C.c_int64),
-                                             P(C.c_int64)]
-        L.orc_fcc_ministep_trace.restype = C.c_int64
-        L.orc_grad_size.argtypes = [P(_Lat), P(_Model)]
-        L.orc_grad_size.restype = C.c_int64
-        L.orc_energy_grad.argtypes = [P(_Lat), P(_Model), P(C.c_int8), P(C.c_double)]
-        L.orc_mlp_eval.argtypes = [P(_Model), P(C.c_double)]
-        L.orc_mlpnet_eval.argtypes = [P(_Model), P(C.c_double)]
-        L.orc_mlpnet_eval.restype = C.c_double
-        L.orc_mlp_eval.restype = C.c_double
-        _lib = L
+        _lib = bind(C.CDLL(_LIB_PATH))
     return _lib
 
 
