@@ -1,8 +1,8 @@
 """Planted mistakes in the oracle: each one is a one-line change to
 oracle/smc_oracle.c compiled into a temporary library, and at least one pin
 must fail on it.  This checks that the pins test the oracle's arithmetic
-(geometry, RNG, pair and qSRO energies, the zone of dE, the network), not
-themselves.  The broken builds are loaded only inside these tests."""
+(geometry, RNG, pair and qSRO energies and gradients, the zone of dE, the
+network, the acceptance rule), not themselves.  The broken builds are loaded only inside these tests."""
 import ctypes
 import os
 import subprocess
@@ -13,6 +13,7 @@ import oracle
 from tests import test_oracle_energy as energy_pins
 from tests import test_oracle_fcc as fcc_pins
 from tests import test_oracle_geometry_rng as geo_pins
+from tests import test_oracle_mc as mc_pins
 from tests import test_oracle_mlpnet as net_pins
 from tests import test_oracle_qsro as qsro_pins
 
@@ -36,6 +37,14 @@ MUTANTS = {
                                  lambda: fcc_pins.test_qsro_delta_e_is_the_change_of_the_total(2, (8, 8, 8))]),
     "mlpnet_second_relu_dropped": ([("        h2[k] = relu(z);", "        h2[k] = z;")],
                                    [lambda: net_pins.test_dead_layer_closed_forms(1)]),
+    "metropolis_at_twice_the_temperature": ([("    return u < exp(-dE / kT);", "    return u < exp(-dE / (2.0 * kT));")],
+                                            [qsro_pins.test_chain_matches_enumeration_16_site]),
+    "integer_table_at_twice_the_temperature": ([("double t = floor(R_SCALE * exp(-(double)d * unit_ev / kT));",
+                                                 "double t = floor(R_SCALE * exp(-(double)d * unit_ev / (2.0 * kT)));")],
+                                               [lambda: mc_pins.test_boltzmann_enumeration_16_site(0.025)]),
+    "qsro_gradient_of_w_linear": ([("                gW[(sh - 1) * S + p] += pi * pi;",
+                                    "                gW[(sh - 1) * S + p] += pi;")],
+                                  [qsro_pins.test_gradient_equals_finite_differences]),
 }
 
 
