@@ -42,6 +42,12 @@ MUTANTS = {
     "integer_table_at_twice_the_temperature": ([("double t = floor(R_SCALE * exp(-(double)d * unit_ev / kT));",
                                                  "double t = floor(R_SCALE * exp(-(double)d * unit_ev / (2.0 * kT)));")],
                                                [lambda: mc_pins.test_boltzmann_enumeration_16_site(0.025)]),
+    "bcc_neighbor_wraps_y_by_nx": ([("    int64_t cy = floor_mod((py - nsub) / 2, lat->ny);",
+                                     "    int64_t cy = floor_mod((py - nsub) / 2, lat->nx);")],
+                                   [lambda: geo_pins.test_neighbor_matches_bruteforce((4, 6, 8))]),
+    "mlp_features_count_own_species": ([("            x[ORC_MLP_SPECIES * m + occ[j]] += 1.0;",
+                                         "            x[ORC_MLP_SPECIES * m + occ[i]] += 1.0;")],
+                                       [energy_pins.test_mlp_features_on_b2]),
     "qsro_gradient_of_w_linear": ([("                gW[(sh - 1) * S + p] += pi * pi;",
                                     "                gW[(sh - 1) * S + p] += pi;")],
                                   [qsro_pins.test_gradient_equals_finite_differences]),
