@@ -355,3 +355,54 @@ def test_degenerate_cases(smc):
     oracle.sweep(oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V), ref, 3, 0, 2, float("inf"))
     smc.check()
     assert np.array_equal(occ.cpu().numpy(), ref)
+
+
+def test_maximum_size_sampled_trials(smc):
+    """A lattice near the largest the API takes (N < 2^31): 1008 x 1024 x 1024
+    cells, N = 2,113,929,216 sites, a seeded random quinary occupancy.  One
+    traced mini-step (the trial index arithmetic near 2^31) against the
+    oracle's dE and decision at 300 sampled trials, the swaps applied where
+    accepted; the energy then changes by the sum of the accepted dE."""
+    dims, S, seed, kT = (1008, 1024, 1024), 5, 3, 0.07
+    N = 2 * dims[0] * dims[1] * dims[2]
+    assert N < 2 ** 31
+    pre = np.random.default_rng(seed).integers(0, S, N, dtype=np.int8)
+    lat = smc.Lattice(*dims, S)
+    V = inputs.pair_f32_coeffs(5, 2, S)
+    model = smc.Model(smc.PAIR_F32, 2, V)
+    occ = torch.from_numpy(pre).to(dev())
+    e0 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, model, occ, e=e0)
+    k = 97  # sublattice 1, dx 1, dy 0, dz 2 on 4 x 4 x 4 link cells
+    nt = N // 128
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    smc.ministep_trace(lat, model, occ, seed, 1, k, kT, dE=dE, acc=acc)
+    e1 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.energy(lat, model, occ, e=e1)
+    smc.check()
+    g_dE, g_acc = dE.cpu().numpy(), acc.cpu().numpy().astype(bool)
+    olat, omodel = oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V)
+    nv = oracle.shell_vectors(1)
+    NLx, NLy, NLz = dims[0] // 4, dims[1] // 4, dims[2] // 4
+    dx, dy, dz, sub = k % 4, (k // 4) % 4, (k // 16) % 4, k // 64
+    rng = np.random.default_rng(8)
+    cs = np.concatenate([[0, nt - 1], rng.integers(0, nt, 298)])
+    post_a = []
+    for c in cs:
+        cx, cy, cz = c % NLx, (c // NLx) % NLy, c // (NLx * NLy)
+        a = int(((sub * dims[2] + 4 * cz + dz) * dims[1] + 4 * cy + dy) * dims[0] + 4 * cx + dx)
+        wd = oracle.philox4x32_10([a >> 2, 0, 1, 0], [seed, 0])[a & 3]
+        b = oracle.neighbor(olat, a, nv[int(wd) >> 29])
+        ref = oracle.delta_e(olat, omodel, pre, a, b)
+        assert abs(float(g_dE[c]) - ref) <= DE_TOL_EV, (int(c), float(g_dE[c]), ref)
+        u = (float(int(wd) & ((1 << 29) - 1)) + 0.5) / 2.0 ** 29
+        if abs(ref + kT * math.log(u)) > DE_TOL_EV:
+            assert bool(g_acc[c]) == (ref <= 0 or u < math.exp(-ref / kT)), int(c)
+        post_a.append((a, b, bool(g_acc[c])))
+    got = occ[torch.tensor([p for t in post_a for p in t[:2]], device=dev())].cpu().numpy().reshape(-1, 2)
+    for (a, b, ac), (ga, gb) in zip(post_a, got):
+        assert (ga, gb) == ((pre[b], pre[a]) if ac else (pre[a], pre[b]))
+    # energy bookkeeping of the whole mini-step (FP32 dE per trial, FP64 energies)
+    de_sum = float(g_dE[g_acc].astype(np.float64).sum())
+    assert abs(float(e1.item()) - float(e0.item()) - de_sum) <= 6 * math.sqrt(max(int(g_acc.sum()), 1)) * DE_TOL_EV
