@@ -272,7 +272,10 @@ __device__ __forceinline__ int3 fcc_woff(int w) { return make_int3(w % 7 - 3, (w
 __global__ void __launch_bounds__(256) k_fcc_qsro_cache(const __grid_constant__ FccStep P)
 {
     const int N = 4 * P.nx * P.ny * P.nz;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    // 64-bit loop index: N may be within one stride of 2^31
+    for (long long si = blockIdx.x * (long long)blockDim.x + threadIdx.x; si < N;
+         si += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)si;
         const int p = P.occ[s] & 7;
         const int x = s % P.nx, y = (s / P.nx) % P.ny, z = (s / (P.nx * P.ny)) % P.nz, sub = s / (P.nx * P.ny * P.nz);
         const FccPos ps = fcc_pos(sub, x, y, z);
@@ -477,7 +480,10 @@ __global__ void __launch_bounds__(256) k_fcc_pair_counts(const __grid_constant__
     for (int i = threadIdx.x; i < kMaxShells * kMaxSpecies; i += blockDim.x) csq[i] = 0;
     __syncthreads();
     const int N = 4 * P.nx * P.ny * P.nz, S = P.S;
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < N; s += gridDim.x * blockDim.x) {
+    // 64-bit loop index: N may be within one stride of 2^31
+    for (long long si = blockIdx.x * (long long)blockDim.x + threadIdx.x; si < N;
+         si += (long long)gridDim.x * blockDim.x) {
+        const int s = (int)si;
         const int p = P.occ[s] & 7;
         const int x = s % P.nx, y = (s / P.nx) % P.ny, z = (s / (P.nx * P.ny)) % P.nz, sub = s / (P.nx * P.ny * P.nz);
         const FccPos ps = fcc_pos(sub, x, y, z);

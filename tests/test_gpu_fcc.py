@@ -413,3 +413,51 @@ def test_degenerate_cases(smc):
         oracle.fcc_sweep(olat, om, ref, 4, 0, 2, float("inf"))
         smc.check()
         assert np.array_equal(occ.cpu().numpy(), ref), kind
+
+
+def test_maximum_size_sampled_trials(smc):
+    """Near the largest FCC lattice the API takes (N < 2^31): 1024 x 1024 x 508
+    cubic cells, N = 2,130,706,432 sites, a seeded random quinary occupancy;
+    one traced pair mini-step against the oracle's dE and decision at 200
+    sampled trials, the swaps applied where accepted; the energy (64-bit site
+    loop) changes by the sum of the accepted dE."""
+    dims, S, seed, kT, k = (1024, 1024, 508), 5, 4, 0.07, 141
+    N = 4 * dims[0] * dims[1] * dims[2]
+    assert N < 2 ** 31
+    pre = np.random.default_rng(seed).integers(0, S, N, dtype=np.int8)
+    lat = smc.Lattice(*dims, S)
+    V = inputs.pair_f32_coeffs(9, 2, S)
+    model = smc.Model(smc.PAIR_F32, 2, V)
+    occ = torch.from_numpy(pre).to(dev())
+    e0 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e0)
+    NL = [d // 4 for d in dims]
+    nt = NL[0] * NL[1] * NL[2]
+    dE = torch.zeros(nt, dtype=torch.float32, device=dev())
+    acc = torch.zeros(nt, dtype=torch.uint8, device=dev())
+    smc.fcc_ministep_trace(lat, model, occ, seed, 2, k, kT, dE=dE, acc=acc)
+    e1 = torch.zeros(1, dtype=torch.float64, device=dev())
+    smc.fcc_energy(lat, model, occ, e=e1)
+    smc.check()
+    g_dE, g_acc = dE.cpu().numpy(), acc.cpu().numpy().astype(bool)
+    olat, omodel = oracle.Lattice(*dims, S), oracle.Model(oracle.PAIR_F32, 2, V)
+    v1 = oracle.fcc_shell_vectors(1)
+    dx, dy, dz, sub = k % 4, (k // 4) % 4, (k // 16) % 4, k // 64
+    rng = np.random.default_rng(2)
+    sites = []
+    for c in np.concatenate([[0, nt - 1], rng.integers(0, nt, 198)]):
+        cx, cy, cz = c % NL[0], (c // NL[0]) % NL[1], c // (NL[0] * NL[1])
+        a = int(((sub * dims[2] + 4 * cz + dz) * dims[1] + 4 * cy + dy) * dims[0] + 4 * cx + dx)
+        w = oracle.philox4x32_10([a & 0xFFFFFFFF, 0, 2, 0], [seed, 0])
+        b = oracle.fcc_neighbor(olat, a, v1[(int(w[1]) * 12) >> 32])
+        ref = oracle.fcc_delta_e(olat, omodel, pre, a, b)
+        assert abs(float(g_dE[c]) - ref) <= DE_TOL_EV, (int(c), float(g_dE[c]), ref)
+        u = (float(int(w[0]) & ((1 << 29) - 1)) + 0.5) / 2.0 ** 29
+        if abs(ref + kT * math.log(u)) > DE_TOL_EV:
+            assert bool(g_acc[c]) == (ref <= 0 or u < math.exp(-ref / kT)), int(c)
+        sites.append((a, b, bool(g_acc[c])))
+    got = occ[torch.tensor([p for t in sites for p in t[:2]], device=dev())].cpu().numpy().reshape(-1, 2)
+    for (a, b, ac), (ga, gb) in zip(sites, got):
+        assert (ga, gb) == ((pre[b], pre[a]) if ac else (pre[a], pre[b]))
+    de_sum = float(g_dE[g_acc].astype(np.float64).sum())
+    assert abs(float(e1.item()) - float(e0.item()) - de_sum) <= 6 * math.sqrt(max(int(g_acc.sum()), 1)) * DE_TOL_EV
