@@ -38,9 +38,9 @@ BYTES_PER_ATTEMPT = 24.0  # 22 B read set + 2 B written per trial (two-shell pai
 NET_FLOP_PER_SITE = 2 * (20 * 96 + 96 * 96 + 96 * 96 + 96)
 NET_FLOP_PER_ATTEMPT = 40 * NET_FLOP_PER_SITE
 QSRO_SEED, QSRO_SHELLS = 7, 2  # qSRO workload parameters
-# zone rows a qSRO trial evaluates (a, b and the sites that see exactly one
-# of them within the model's shells), counted from the BCC geometry
-QSRO_ROWS = {1: 16, 2: 22, 3: 40}
+# zone sites of a qSRO trial besides a and b (within the model's shells of
+# either), counted from the BCC geometry
+QSRO_ZONE = {1: 14, 2: 20, 3: 38}
 INSTR_PER_TRIAL_512 = 352.9  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
@@ -622,13 +622,15 @@ def run_extras(smc, torch, dev, pk):
     msq = timed(lambda: smc.sweep(latq, qm, occq, 1, 0, nswq, kTq, n_acc=nq), reps=1)
     attq = latq.nsites * nswq / (msq * 1e-3)
     accq = float(nq.item()) / (2 * latq.nsites * nswq)
-    # bytes the design moves per attempt: the evaluated zone rows' features
-    # read (16 B each) and rewritten when accepted, the two species read and written
-    bq = QSRO_ROWS[QSRO_SHELLS] * 16 * (1 + accq) + 2 + 2 * accq
+    # bytes the design moves per attempt: species of a, b and the zone and the
+    # zone's count-cache entries read (1 B each for 2 shells); when accepted the
+    # two species and the cache entries of a, b and the zone written
+    zq = QSRO_ZONE[QSRO_SHELLS]
+    bq = 2 + 2 * zq + accq * (2 + 2 + zq)
     out["qsro_256"] = {"cells": [256] * 3, "shells": QSRO_SHELLS, "sweeps_per_launch": nswq,
-                       "ms_per_sweep": msq / nswq, "attempts_per_s": attq, "accept_rate": accq,
-                       "cache_bytes_per_attempt": bq, "achieved_gbs": attq * bq / 1e9,
-                       "frac_of_measured_hbm": attq * bq / 1e9 / pk["hbm_gbs"]}
+                       "launches_per_sweep": 128, "ms_per_sweep": msq / nswq, "attempts_per_s": attq,
+                       "accept_rate": accq, "bytes_per_attempt": bq, "achieved_gbs": attq * bq / 1e9,
+                       "note": "67 MB of species and count cache: L2-resident, bound by load latency"}
     eq = torch.zeros(1, dtype=torch.float64, device=dev)
     emsq = timed(lambda: smc.energy(latq, qm, occq, eq), reps=3)
     out["qsro_energy_256"] = {"ms": emsq}

@@ -351,6 +351,11 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
     };
     // packed per-shell counts (byte m-1): species A / B around a and around b
     uint32_t cAa = 0, cBa = 1u, cAb = 1u, cBb = 0;  // b (species B) is in a's shell 1, a (A) in b's
+    // species | count cache << 4 of every zone site, kept for the update of
+    // an accepted swap: reloading them there would put a global round trip
+    // behind every cache store of the walk (the compiler cannot prove occ
+    // and the cache apart)
+    uint32_t zq[NZ];
     float dE = 0.f;
     if (A != B) {
         const float *row = sT + (A * 8 + B) * 8;
@@ -377,8 +382,10 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
                 cAb += isA << (8 * (mb - 1));
                 cBb += isB << (8 * (mb - 1));
             }
+            zq[e] = (uint32_t)sj;
             if (ma != mb) {
                 const int q = Qc[j];
+                zq[e] |= (uint32_t)q << 4;
                 float t = 0.f;  // a leaves j's shell ma as A and arrives as B; b the reverse in shell mb
                 if (ma) {
                     const int n = (q >> fcc_qoff(ma - 1)) & fcc_qmask(ma - 1);
@@ -418,12 +425,11 @@ __global__ void __launch_bounds__(256) k_fcc_qsro_ministep(const __grid_constant
             for (int e = 0; e < NZ; ++e) {
                 const int code = fcc_zone_code(NSH, e), ma = code >> 2, mb = code & 3;
                 if (ma == mb) continue;
-                const int j = site(e);
-                const int sj = occ[j] & 7;
+                const int sj = (int)(zq[e] & 15u), q = (int)(zq[e] >> 4);
                 // A sites lose a (shell ma) and gain b (shell mb); B sites the reverse
                 const int d = (ma ? 1 << fcc_qoff(ma - 1) : 0) - (mb ? 1 << fcc_qoff(mb - 1) : 0);
-                if (sj == A) Qc[j] = (QT)(Qc[j] - d);
-                if (sj == B) Qc[j] = (QT)(Qc[j] + d);
+                if (sj == A) Qc[site(e)] = (QT)(q - d);
+                if (sj == B) Qc[site(e)] = (QT)(q + d);
             }
         }
         if (P.part_e) {

@@ -384,7 +384,8 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
     if (is_mlp(model))
         return launch_mlp_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     if (is_qsro(model))
-        return launch_qsro_sweep(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+        return launch_qsro_ministeps(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, nullptr, nullptr,
+                                     -1, stream);
     int8_t *occs[1] = {occ};
     return launch_pair_sweep(1, lat, model, occs, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
@@ -446,7 +447,8 @@ smc_status smc_sweep_batched(int32_t R, const smc_lattice *lats, const smc_model
             return SMC_ERR_UNSUPPORTED;
         }
         if (is_qsro(model))
-            return launch_qsro_sweep(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
+            return launch_qsro_ministeps(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, nullptr,
+                                         nullptr, -1, stream);
         return launch_mlp_sweep(lats, model, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
     }
     return launch_pair_sweep(R, lats, model, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
@@ -465,7 +467,7 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
         return SMC_ERR_ARG;
     }
     if (is_mlp(model)) return launch_mlp_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
-    if (is_qsro(model)) return launch_qsro_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
+    if (is_qsro(model)) return launch_qsro_ministeps(lat, model, occ, seed, replica, sweep, 1, &kT, nullptr, nullptr, dE, acc, k, stream);
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 

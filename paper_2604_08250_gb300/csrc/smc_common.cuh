@@ -162,12 +162,10 @@ smc_status launch_fcc_sweep(const smc_lattice *lat, const smc_model *m, int8_t *
                             int64_t *n_acc, float *trace_dE, uint8_t *trace_acc, int trace_k, cudaStream_t stream);
 smc_status launch_fcc_energy(const smc_lattice *lat, const smc_model *m, const int8_t *occ, double *e,
                              int64_t *e_int, cudaStream_t stream);
-smc_status launch_qsro_sweep(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
-                             uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
-                             int64_t *n_acc, cudaStream_t stream);
-smc_status launch_qsro_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
-                             uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,
-                             cudaStream_t stream);
+smc_status launch_qsro_ministeps(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
+                                 uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                                 int64_t *n_acc, float *trace_dE, uint8_t *trace_acc, int trace_k,
+                                 cudaStream_t stream);
 smc_status launch_qsro_energy(const smc_lattice *lat, const smc_model *m, const int8_t *occ, double *e,
                               cudaStream_t stream);
 smc_status launch_qsro_grad(const smc_lattice *lat, const smc_model *m, const int8_t *occ, float *grad,

@@ -137,78 +137,6 @@ struct NetRelu96 {  // MLPNet of mlpnet_tc.cuh: 20 -> 96 -> 96 -> 96 -> 1, ReLU
 // Site-energy models of the tensor-core sweep.
 constexpr int kModeMlp = 0, kModeMlpPair = 1;
 
-// qSRO parameters as the kernels read them (FP32): v[m][p][q] = V_m^{pq} / z_m
-// at [(m * 8 + p) * 8 + q], w[m][p] = W_m^p / z_m^2 at kQsroV + m * 8 + p.
-constexpr int kQsroV = kMaxShells * kMaxSpecies * kMaxSpecies;
-constexpr int kQsroParams = kQsroV + kMaxShells * kMaxSpecies;
-
-// qSRO local energy without C (Sec. IV-B, Eq. quadratic_local_SRO) of a
-// site of species s with packed per-shell species counts h[m]: the pairs of
-// shell m have fractions c_m[q] / z_m, so
-//   f = sum_{m < nsh} [ sum_q v[m][s][q] c_m[q] + w[m][s] c_m[s]^2 ].
-__device__ __forceinline__ float qsro_f(const float *Q, int nsh, int S, int s, const uint32_t h[3])
-{
-    float e = 0.f;
-    for (int m = 0; m < nsh; ++m) {
-        const float *v = Q + (m * kMaxSpecies + s) * kMaxSpecies;
-        for (int q = 0; q < S; ++q) e = fmaf((float)((h[m] >> (4 * q)) & 15u), v[q], e);
-        const float cs = (float)((h[m] >> (4 * s)) & 15u);
-        e = fmaf(cs * cs, Q[kQsroV + m * kMaxSpecies + s], e);
-    }
-    return e;
-}
-
-// f(x') - f(x) of a zone site of species s (neither a nor b) that sees a in
-// shell ma and b in shell mb (0: not within the model's shells), when a
-// turns A -> B and b turns B -> A (A != B).  In shell ma the count of B
-// rises and that of A falls by one, in shell mb the reverse; the same-element
-// count c_s changes by ds, so its square by 2 c_s ds + ds^2 (exact integers).
-__device__ __forceinline__ float qsro_zone_delta(const float *Q, int nsh, int s, const uint32_t h[3], int ma, int mb,
-                                                 int A, int B)
-{
-    float d = 0.f;
-    if (ma == mb) return d;  // both in one shell: the changes cancel
-    for (int k = 0; k < 2; ++k) {
-        const int m = k == 0 ? ma : mb;
-        if (m < 1 || m > nsh) continue;
-        const int sg = k == 0 ? 1 : -1;
-        const float *v = Q + ((m - 1) * kMaxSpecies + s) * kMaxSpecies;
-        d += (float)sg * (v[B] - v[A]);
-        const int cs = (int)((h[m - 1] >> (4 * s)) & 15u);
-        const int ds = (s == B ? sg : 0) - (s == A ? sg : 0);
-        d = fmaf((float)(2 * cs * ds + ds * ds), Q[kQsroV + (m - 1) * kMaxSpecies + s], d);
-    }
-    return d;
-}
-
-// Post-swap features of zone entry e (0 = a, 1 = b) from its pre-swap ones:
-// a turns A -> B and b turns B -> A.
-__device__ __forceinline__ void qsro_post(const OmegaEntry &oe, int e, int A, int B, uint32_t q0, const uint32_t h[3],
-                                          uint32_t &q0n, uint32_t hn[3])
-{
-    const uint32_t dAB = (1u << (4 * B)) - (1u << (4 * A));  // a: A -> B (mod 2^32)
-    q0n = e == 0 ? (uint32_t)B : (e == 1 ? (uint32_t)A : q0);
-#pragma unroll
-    for (int m = 0; m < 3; ++m) {
-        hn[m] = h[m];
-        if (oe.ma == m + 1) hn[m] += dAB;
-        if (oe.mb == m + 1) hn[m] -= dAB;
-    }
-}
-
-// f(x') - f(x) of zone entry e: full site energies for a and b, the count
-// changes for the others.  Every kernel sums these in entry order from 0.
-__device__ __forceinline__ float qsro_row(const float *Q, int nsh, int S, const OmegaEntry &oe, int e, int A, int B,
-                                          uint32_t q0, const uint32_t h[3])
-{
-    if (e < 2) {
-        uint32_t q0n, hn[3];
-        qsro_post(oe, e, A, B, q0, h, q0n, hn);
-        return qsro_f(Q, nsh, S, (int)q0n, hn) - qsro_f(Q, nsh, S, (int)q0, h);
-    }
-    return qsro_zone_delta(Q, nsh, (int)q0, h, oe.ma, oe.mb, A, B);
-}
-
 // The evaluator of this thread's warpgroup.
 template <class Net, int NWG>
 __device__ __forceinline__ typename Net::Eval mlp_evaluator(long long timeout_ns, int *status, int *abort_flag)
@@ -757,13 +685,13 @@ __global__ void k_mlp_trace_apply(int8_t *occ, int ntr, const int *swap_a, const
 }
 
 // ---------------------------------------------------------------------------
-// qSRO per-site pass: the packed features of every site (the sweep's cache)
-// and/or, per shell m and species p, Q_m^p = sum over sites of species p of
-// c_m[p]^2 (the same-element counts squared), reduced across each warp and
-// added with 64-bit atomics: exact integers whatever the launch shape.
+// qSRO per-site pass: per shell m and species p, Q_m^p = sum over sites of
+// species p of c_m[p]^2 (the same-element counts squared), reduced across
+// each warp and added with 64-bit atomics: exact integers whatever the launch
+// shape.
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256) k_qsro_sites(const int8_t *__restrict__ occ, int nx, int ny, int nz, int nsh,
-                                                    uint4 *fcache, unsigned long long *quad)
+                                                    unsigned long long *quad)
 {
     const long long N = 2LL * nx * ny * nz;
     const int lane = threadIdx.x & 31;
@@ -789,9 +717,8 @@ __global__ void __launch_bounds__(256) k_qsro_sites(const int8_t *__restrict__ o
             const int sub = (int)(t / nz);
             q0 = occ[s] & 7;
             site_hist(spec, sub, x, y, z, h[0], h[1], h[2]);
-            if (fcache) fcache[s] = make_uint4((uint32_t)q0, h[0], h[1], h[2]);
         }
-        if (quad) {
+        {
 #pragma unroll
             for (int m = 0; m < kMaxShells; ++m) {
                 const uint32_t c = q0 >= 0 ? (h[m] >> (4 * q0)) & 15u : 0u;
@@ -804,7 +731,7 @@ __global__ void __launch_bounds__(256) k_qsro_sites(const int8_t *__restrict__ o
             }
         }
     }
-    if (quad && lane == 0)
+    if (lane == 0)
 #pragma unroll
         for (int m = 0; m < kMaxShells; ++m)
 #pragma unroll
@@ -852,273 +779,6 @@ __global__ void k_qsro_finish(QsroRaw Q, const unsigned long long *cnt, const un
             for (int p = 0; p < S; ++p) grad[i++] = (float)((double)quad[m * kMaxSpecies + p] / (z[m] * z[m]));
         grad[i] = (float)N;
     }
-}
-
-// Lock-step trace of one qSRO mini-step: a CTA per batch of kTraceTB trials,
-// features counted from the occupancy (the sweep reads the same integers
-// from its cache), the sweep's row arithmetic and summation order.
-__global__ void __launch_bounds__(128) k_qsro_trace_eval(const __grid_constant__ SweepParams P,
-                                                         const __grid_constant__ MlpGeo G, int k, float *dE_out,
-                                                         uint8_t *acc_out, int *swap_a, int *swap_b)
-{
-    __shared__ float Q[kQsroParams];
-    __shared__ int tinfo[kTraceTB * kTinfo];
-    __shared__ float dsm[kTraceTB * kOmega];
-    __shared__ MlpGeo geo;
-    const int tid = threadIdx.x;
-    for (int i = tid; i < kQsroParams; i += blockDim.x) Q[i] = P.D.df[i];
-    for (int i = tid; i < (int)(sizeof(MlpGeo) / 4); i += blockDim.x) ((int *)&geo)[i] = ((const int *)&G)[i];
-    const RepDesc &RD = P.rep[0];
-    const int nx = RD.nx, ny = RD.ny, nz = RD.nz;
-    const int ntr = RD.NLx * RD.NLy * RD.NLz;
-    const int dx = k % 4, dy = (k / 4) % 4, dz = (k / 16) % 4, sub = k / 64;
-    const int soff = sub == 0 ? -1 : 0;
-    const int8_t *occ = RD.occ;
-    auto spec = [&](int sb, int xx, int yy, int zz) { return occ_at(occ, nx, ny, nz, sb, xx, yy, zz); };
-    __syncthreads();
-    for (int c0 = blockIdx.x * kTraceTB; c0 < ntr; c0 += gridDim.x * kTraceTB) {
-        const int nb = min(kTraceTB, ntr - c0);
-        if (tid < nb) {
-            const int c = c0 + tid;
-            const int cx = c % RD.NLx, cy = (c / RD.NLx) % RD.NLy, cz = c / (RD.NLx * RD.NLy);
-            const int x = 4 * cx + dx, y = 4 * cy + dy, z = 4 * cz + dz;
-            const uint32_t s = (uint32_t)(((sub * nz + z) * ny + y) * nx + x);
-            const uint32_t w = site_word(P.seed, RD.rep, P.sweep0, s);
-            const int dir = (int)(w >> kRBits);
-            const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
-            const int bx = wrapc(x + soff + kx, nx), by = wrapc(y + soff + ky, ny), bz = wrapc(z + soff + kz, nz);
-            int *ti = tinfo + tid * kTinfo;
-            ti[0] = (int)s;
-            ti[1] = (((1 - sub) * nz + bz) * ny + by) * nx + bx;
-            ti[2] = (int)(w & kRMask);
-            ti[3] = occ[s] & 7;
-            ti[4] = occ[ti[1]] & 7;
-            ti[5] = x;
-            ti[6] = y;
-            ti[7] = z;
-            ti[8] = dir;
-        }
-        __syncthreads();
-        if (tid < nb * kOmega) {
-            const int t = tid / kOmega, e = tid - t * kOmega;
-            const int *ti = tinfo + t * kTinfo;
-            const int A = ti[3], B = ti[4];
-            float d = 0.f;
-            if (A != B) {
-                const OmegaEntry oe = geo.om[sub][ti[8]][e];
-                const int ssub = oe.rel ? 1 - sub : sub;
-                const int gx = wrapc(ti[5] + oe.dxo, nx), gy = wrapc(ti[6] + oe.dy, ny), gz = wrapc(ti[7] + oe.dz, nz);
-                uint32_t h[3];
-                site_hist(spec, ssub, gx, gy, gz, h[0], h[1], h[2]);
-                d = qsro_row(Q, P.nshells, P.S, oe, e, A, B, (uint32_t)spec(ssub, gx, gy, gz), h);
-            }
-            dsm[tid] = d;
-        }
-        __syncthreads();
-        if (tid < nb) {
-            const int c = c0 + tid;
-            const int *ti = tinfo + tid * kTinfo;
-            const int A = ti[3], B = ti[4];
-            float dE = 0.f;
-            if (A != B)
-                for (int e = 0; e < kOmega; ++e) dE += dsm[tid * kOmega + e];
-            const bool acc = metropolis<false>(dE, (uint32_t)ti[2], P.temp.beta[0], nullptr, make_int2(0, 0));
-            if (dE_out) dE_out[c] = dE;
-            if (acc_out) acc_out[c] = acc ? 1 : 0;
-            swap_a[c] = (acc && A != B) ? ti[0] : -1;
-            swap_b[c] = ti[1];
-        }
-        __syncthreads();
-    }
-}
-
-// ---------------------------------------------------------------------------
-// qSRO sweep: a warp per link-cell column (tile), as in the pair sweep.  Lane
-// i runs the trials of link cells i, i + 32, ... of each of the group's four
-// mini-steps: it reads A and B, sums the 40 zone rows f(x') - f(x) in entry
-// order from the feature cache, decides, and for an accepted swap writes the
-// two species and its zone's post-swap features.  The trials of a mini-step
-// have disjoint zones (the link cells' independence), so the lanes need no
-// more than a warp barrier between mini-steps; neighbouring tiles are ordered
-// by the progress flags (every group waits for the previous group of its 8
-// neighbours).  Shared memory: the parameters and zone table, then per warp
-// the column's Philox words [k][dx][lane] and the per-tile partial sums.
-// ---------------------------------------------------------------------------
-constexpr int kQsroSweepThreads = 256;
-constexpr int kQsroBatch = 8;     // zone rows whose feature loads are in flight together
-constexpr int kQsroGeoStride = 41;  // entries per (sublattice, direction): the 8 directions start on distinct banks
-static_assert(kOmega % kQsroBatch == 0, "zone rows come in whole batches");
-
-__global__ void __launch_bounds__(kQsroSweepThreads) k_sweep_qsro(const __grid_constant__ SweepParams P,
-                                                                  const __grid_constant__ MlpGeo G)
-{
-    __shared__ float Q[kQsroParams];
-    __shared__ OmegaEntry geo[2 * 8 * kQsroGeoStride];
-    __shared__ int nrel[2 * 8];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    for (int i = tid; i < kQsroParams; i += blockDim.x) Q[i] = P.D.df[i];
-    // per (sublattice, direction): the zone entries whose row can be nonzero
-    // for this model's shells (a, b, and the sites that see exactly one of
-    // them within those shells), in entry order; the others add exactly 0
-    // to dE and change only counts of shells the model does not read
-    if (tid < 16) {
-        int n = 0;
-        for (int e = 0; e < kOmega; ++e) {
-            const OmegaEntry oe = (&G.om[0][0][0])[tid * kOmega + e];
-            const bool ina = oe.ma >= 1 && oe.ma <= P.nshells, inb = oe.mb >= 1 && oe.mb <= P.nshells;
-            if (e < 2 || ((ina || inb) && oe.ma != oe.mb)) geo[tid * kQsroGeoStride + n++] = oe;
-        }
-        nrel[tid] = n;
-    }
-    const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
-    const RepDesc &RD = P.rep[0];
-    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx, nk = (NLx + 31) >> 5;
-    unsigned char *wbase = g_smem + (size_t)warp * P.warp_bytes;
-    uint32_t *wsm = (uint32_t *)wbase;  // [nk][4][32]
-    double *slot_e = (double *)(wbase + 512 * nk);
-    long long *slot_n = (long long *)(slot_e + P.tpc);
-    for (int i = lane; i < P.tpc; i += 32) {
-        slot_e[i] = 0.0;
-        slot_n[i] = 0;
-    }
-    __syncthreads();
-    int8_t *occ = RD.occ;
-    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-    bool aborted = false;
-    for (int t = 0; t < P.nsweeps && !aborted; ++t) {
-        const uint64_t sweep = P.sweep0 + (uint64_t)t;
-        const float beta = P.temp.beta[P.beta_stride ? t : 0];
-        for (int g = 0; g < P.G && !aborted; ++g) {
-            const uint32_t gstep = (uint32_t)(t * P.G + g);
-            const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4, soff = sub == 0 ? -1 : 0;
-            int slotk = 0;
-            for (int tile = gw; tile < P.ntiles; tile += NW, ++slotk) {
-                const int ty = tile % RD.NTy, tz = tile / RD.NTy;
-                if (!wait_tile_warp(P, RD, ty, tz, gstep, lane)) {
-                    aborted = true;
-                    break;
-                }
-                const int y0 = 4 * ty + dy, z0 = 4 * tz + dz;
-                const int rowsite = ((sub * nz + z0) * ny + y0) * nx;
-                for (int k = 0; k < nk; ++k) {
-                    const int i = lane + 32 * k;
-                    if (i < NLx) {
-                        const U4 w = philox10(U4{((uint32_t)rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep,
-                                                 (uint32_t)(sweep >> 32)},
-                                              k0, k1);
-                        wsm[(k * 4 + 0) * 32 + lane] = w.x;
-                        wsm[(k * 4 + 1) * 32 + lane] = w.y;
-                        wsm[(k * 4 + 2) * 32 + lane] = w.z;
-                        wsm[(k * 4 + 3) * 32 + lane] = w.w;
-                    }
-                }
-                float colE = 0.f;
-                long long accN = 0;
-                for (int dx = 0; dx < 4; ++dx) {
-                    for (int k = 0; k < nk; ++k) {
-                        const int i = lane + 32 * k;
-                        if (i >= NLx) continue;
-                        const int x = 4 * i + dx;
-                        const uint32_t w = wsm[(k * 4 + dx) * 32 + lane];
-                        const int dir = (int)(w >> kRBits);
-                        const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
-                        const int a = rowsite + x;
-                        const int b = (((1 - sub) * nz + wrapc(z0 + soff + kz, nz)) * ny + wrapc(y0 + soff + ky, ny)) *
-                                          nx +
-                                      wrapc(x + soff + kx, nx);
-                        const int A = __ldcg(occ + a) & 7, B = __ldcg(occ + b) & 7;
-                        if (A == B) {  // dE = 0: accepted, nothing changes
-                            accN += 1;
-                            continue;
-                        }
-                        const OmegaEntry *om = geo + (sub * 8 + dir) * kQsroGeoStride;
-                        const int nr = nrel[sub * 8 + dir];
-                        auto zone_site = [&](const OmegaEntry &oe) {
-                            const int ssub = oe.rel ? 1 - sub : sub;
-                            return ((ssub * nz + wrapc(z0 + oe.dz, nz)) * ny + wrapc(y0 + oe.dy, ny)) * nx +
-                                   wrapc(x + oe.dxo, nx);
-                        };
-                        // rows in batches: the batch's loads first, then its
-                        // rows in entry order
-                        float dE = 0.f;
-#pragma unroll 1
-                        for (int e0 = 0; e0 < nr; e0 += kQsroBatch) {
-                            uint4 f[kQsroBatch];
-#pragma unroll
-                            for (int u = 0; u < kQsroBatch; ++u)
-                                if (e0 + u < nr) f[u] = __ldcg(P.fcache + zone_site(om[e0 + u]));
-#pragma unroll
-                            for (int u = 0; u < kQsroBatch; ++u)
-                                if (e0 + u < nr) {
-                                    const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
-                                    dE += qsro_row(Q, P.nshells, P.S, om[e0 + u], e0 + u, A, B, f[u].x, h);
-                                }
-                        }
-                        if (metropolis<false>(dE, w & kRMask, beta, nullptr, make_int2(0, 0))) {
-                            occ[a] = (int8_t)B;
-                            occ[b] = (int8_t)A;
-                            colE += dE;
-                            accN += 1;
-#pragma unroll 1
-                            for (int e0 = 0; e0 < nr; e0 += kQsroBatch) {
-                                uint4 f[kQsroBatch];
-                                int site[kQsroBatch];
-#pragma unroll
-                                for (int u = 0; u < kQsroBatch; ++u)
-                                    if (e0 + u < nr) {
-                                        site[u] = zone_site(om[e0 + u]);
-                                        f[u] = __ldcg(P.fcache + site[u]);
-                                    }
-#pragma unroll
-                                for (int u = 0; u < kQsroBatch; ++u)
-                                    if (e0 + u < nr) {
-                                        const uint32_t h[3] = {f[u].y, f[u].z, f[u].w};
-                                        uint32_t q0n, hn[3];
-                                        qsro_post(om[e0 + u], e0 + u, A, B, f[u].x, h, q0n, hn);
-                                        __stcg(P.fcache + site[u], make_uint4(q0n, hn[0], hn[1], hn[2]));
-                                    }
-                            }
-                        }
-                    }
-                    __syncwarp();
-                }
-                const double e_w = warp_sum<double>((double)colE);
-                const long long n_w = warp_sum<long long>(accN);
-                if (lane == 0) {
-                    slot_e[slotk] += e_w;
-                    slot_n[slotk] += n_w;
-                }
-                // every lane's stores, then one release by lane 0 (the warp
-                // barrier orders the other lanes' stores before it)
-                __syncwarp();
-                if (lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, gstep + 1);
-            }
-        }
-    }
-    if (aborted) return;
-    // per-tile partial sums; the last warp to finish adds them in tile order
-    if (lane == 0) {
-        int k = 0;
-        for (int tile = gw; tile < P.ntiles; tile += NW, ++k) {
-            P.part_e[tile] = slot_e[k];
-            P.part_n[tile] = slot_n[k];
-        }
-    }
-    __threadfence();
-    __syncwarp();
-    unsigned last = 0;
-    if (lane == 0) last = (atomicAdd(P.ticket, 1u) == (unsigned)NW - 1) ? 1u : 0u;
-    last = __shfl_sync(0xffffffffu, last, 0);
-    if (!last || lane != 0) return;
-    __threadfence();
-    double se = 0.0;
-    long long sn = 0;
-    for (int k = 0; k < P.ntiles; ++k) {
-        se += __ldcg(P.part_e + k);
-        sn += __ldcg(P.part_n + k);
-    }
-    if (RD.e_acc) *RD.e_acc += se;
-    if (RD.n_acc) *RD.n_acc += sn;
 }
 
 // ---------------------------------------------------------------------------
@@ -1593,21 +1253,6 @@ smc_status launch_mlp_trace(const smc_lattice *lat, const smc_model *m, int8_t *
 namespace {
 constexpr double kShellZ[3] = {8.0, 6.0, 12.0};
 
-// FP32 kernel parameters: V_m^{pq} / z_m and W_m^p / z_m^2, each quotient
-// formed in FP64 and rounded once.
-void fill_qsro_params(const smc_model *m, int S, SweepParams &P)
-{
-    for (int i = 0; i < kQsroParams; ++i) P.D.df[i] = 0.f;
-    for (int mm = 0; mm < m->nshells; ++mm) {
-        for (int p = 0; p < S; ++p)
-            for (int q = 0; q < S; ++q)
-                P.D.df[(mm * kMaxSpecies + p) * kMaxSpecies + q] =
-                    (float)((double)m->v_f32[(mm * S + p) * S + q] / kShellZ[mm]);
-        for (int p = 0; p < S; ++p)
-            P.D.df[kQsroV + mm * kMaxSpecies + p] = (float)((double)m->qsro_w[mm * S + p] / (kShellZ[mm] * kShellZ[mm]));
-    }
-}
-
 QsroRaw make_qsro_raw(const smc_model *m, int S)
 {
     QsroRaw Q;
@@ -1623,12 +1268,12 @@ QsroRaw make_qsro_raw(const smc_model *m, int S)
     return Q;
 }
 
-smc_status qsro_sites_launch(Workspace *ws, const smc_lattice *lat, int nsh, const int8_t *occ, uint4 *fcache,
+smc_status qsro_sites_launch(Workspace *ws, const smc_lattice *lat, int nsh, const int8_t *occ,
                              unsigned long long *quad, cudaStream_t stream)
 {
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
     const int blocks = (int)std::max(1LL, std::min<long long>((N + 255) / 256, (long long)ws->num_sms * 8));
-    k_qsro_sites<<<blocks, 256, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, nsh, fcache, quad);
+    k_qsro_sites<<<blocks, 256, 0, stream>>>(occ, lat->nx, lat->ny, lat->nz, nsh, quad);
     const cudaError_t e = cudaGetLastError();
     return e == cudaSuccess ? SMC_OK : cuda_fail(e, "k_qsro_sites");
 }
@@ -1649,7 +1294,7 @@ smc_status qsro_counts_finish(const smc_lattice *lat, const smc_model *m, const 
     if (st != SMC_OK) return st;
     cudaError_t err = cudaMemsetAsync(quad, 0, sizeof(unsigned long long) * kMaxShells * kMaxSpecies, stream);
     if (err != cudaSuccess) return cuda_fail(err, "cudaMemsetAsync(qSRO sums)");
-    st = qsro_sites_launch(ws, lat, m->nshells, occ, nullptr, quad, stream);
+    st = qsro_sites_launch(ws, lat, m->nshells, occ, quad, stream);
     if (st != SMC_OK) return st;
     const long long N = 2LL * lat->nx * lat->ny * lat->nz;
     k_qsro_finish<<<1, 32, 0, stream>>>(make_qsro_raw(m, lat->nspecies), cnt, quad, N, e, grad);
@@ -1668,178 +1313,6 @@ smc_status launch_qsro_grad(const smc_lattice *lat, const smc_model *m, const in
                             cudaStream_t stream)
 {
     return qsro_counts_finish(lat, m, occ, nullptr, grad, stream);
-}
-
-smc_status launch_qsro_sweep(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
-                             uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
-                             int64_t *n_acc, cudaStream_t stream)
-{
-    if (!mlp_shape_ok(lat)) {
-        set_error("qSRO sweeps need every axis a multiple of 4 cells and >= 8, nx <= 1024");
-        return SMC_ERR_UNSUPPORTED;
-    }
-    smc_status st;
-    Workspace *ws = workspace(&st);
-    if (!ws) return st;
-    const void *kernel = (const void *)k_sweep_qsro;
-    // plan: warps of 8 per CTA, all resident, tiles spread so that the
-    // busiest SM holds the fewest
-    const int NLx = lat->nx / 4, nk = (NLx + 31) / 32, nwarps = kQsroSweepThreads / 32;
-    const int ntiles = (lat->ny / 4) * (lat->nz / 4);
-    cudaFuncAttributes fa;
-    cudaError_t err = cudaFuncGetAttributes(&fa, kernel);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaFuncGetAttributes");
-    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
-    err = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
-    if (err != cudaSuccess) return cuda_fail(err, "cudaFuncSetAttribute");
-    int grid = 0, tpc = 0, warp_bytes = 0;
-    size_t smem = 0;
-    for (int tpc_guess = 1; tpc_guess <= 65536; tpc_guess *= 2) {
-        const int wb = 512 * nk + 16 * tpc_guess;
-        const size_t sm = (size_t)nwarps * wb;
-        if (sm > dyn_max) break;
-        int per_sm = 0;
-        err = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kQsroSweepThreads, sm);
-        if (err != cudaSuccess) return cuda_fail(err, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        if (current_tuning().ctas_per_sm > 0) per_sm = std::min(per_sm, current_tuning().ctas_per_sm);
-        if (per_sm < 1) break;
-        const long long nw = balanced_warps(ntiles, nwarps, per_sm, ws->num_sms);
-        const int need = (int)((ntiles + nw - 1) / nw);
-        if (need <= tpc_guess) {
-            grid = (int)(nw / nwarps);
-            tpc = tpc_guess;
-            warp_bytes = wb;
-            smem = sm;
-            break;
-        }
-    }
-    if (grid == 0) {
-        set_error("qSRO sweep kernel does not fit on an SM (nx = %d)", lat->nx);
-        return SMC_ERR_UNSUPPORTED;
-    }
-    static MlpGeo G;
-    if (!build_mlp_geo(G)) {
-        set_error("internal error: interaction-zone geometry");
-        return SMC_ERR_STATE;
-    }
-    static SweepParams P;
-    memset(&P, 0, sizeof P);
-    P.R = 1;
-    P.G = 32;
-    P.Lx = P.Ly = P.Lz = 4;
-    P.TY = P.TZ = P.CB = 1;
-    P.nshells = m->nshells;
-    P.S = lat->nspecies;
-    P.tpc = tpc;
-    P.warp_bytes = warp_bytes;
-    P.nap_cap = NLx >= 64 ? 1024 : 128;
-    P.kind = m->kind;
-    for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
-    P.skip_tile = (int)debug_skip_tile();
-    P.seed = seed;
-    P.timeout_ns = debug_timeout_ns();
-    P.ntiles = ntiles;
-    RepDesc &d = P.rep[0];
-    d.occ = occ;
-    d.e_acc = e_acc;
-    d.n_acc = (long long *)n_acc;
-    d.nx = lat->nx;
-    d.ny = lat->ny;
-    d.nz = lat->nz;
-    d.NLx = d.nx / 4;
-    d.NLy = d.ny / 4;
-    d.NLz = d.nz / 4;
-    d.NTy = d.NLy;
-    d.NTz = d.NLz;
-    d.tile0 = 0;
-    d.rep = replica;
-    d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ % 16 == 0);
-    fill_qsro_params(m, P.S, P);
-
-    // workspace: [flags | part_e | part_n | ticket, abort | F cache]
-    const size_t nt = (size_t)P.ntiles;
-    const size_t N = 2ull * lat->nx * lat->ny * lat->nz;
-    const size_t off_pe = round16(nt * 4), off_pn = off_pe + nt * 8, off_misc = off_pn + nt * 8;
-    const size_t off_fcache = round16(off_misc + 16);
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_fcache + N * 16, &st);
-    if (!scr) return st;
-    P.flags = (uint32_t *)scr;
-    P.part_e = (double *)(scr + off_pe);
-    P.part_n = (long long *)(scr + off_pn);
-    P.ticket = (unsigned *)(scr + off_misc);
-    P.abort_flag = (int *)(scr + off_misc + 4);
-    P.status = ws->status;
-    P.fcache = (uint4 *)(scr + off_fcache);
-    st = qsro_sites_launch(ws, lat, m->nshells, occ, P.fcache, nullptr, stream);
-    if (st != SMC_OK) return st;
-
-    bool constant = true;
-    for (int t = 1; t < nsweeps; ++t)
-        if (kT[t] != kT[0]) constant = false;
-    const int chunk = constant ? nsweeps : kMaxBeta;
-    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
-        const int nc = std::min(chunk, nsweeps - t0);
-        P.sweep0 = sweep0 + (uint64_t)t0;
-        P.nsweeps = nc;
-        P.beta_stride = constant ? 0 : 1;
-        for (int t = 0; t < (constant ? 1 : nc); ++t) P.temp.beta[t] = (float)(1.0 / kT[t0 + t]);
-        cudaError_t e = cudaMemsetAsync(scr, 0, off_misc + 16, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
-        void *args[] = {(void *)&P, (void *)&G};
-        e = cudaLaunchCooperativeKernel(kernel, dim3(grid), dim3(kQsroSweepThreads), args, smem, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(qSRO sweep)");
-    }
-    return SMC_OK;
-}
-
-smc_status launch_qsro_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
-                             uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,
-                             cudaStream_t stream)
-{
-    if (lc_edge(lat->nx) != 4 || lc_edge(lat->ny) != 4 || lc_edge(lat->nz) != 4) {
-        set_error("qSRO traces need every axis a multiple of 4 cells and >= 8");
-        return SMC_ERR_UNSUPPORTED;
-    }
-    smc_status st;
-    Workspace *ws = workspace(&st);
-    if (!ws) return st;
-    static MlpGeo G;
-    if (!build_mlp_geo(G)) {
-        set_error("internal error: interaction-zone geometry");
-        return SMC_ERR_STATE;
-    }
-    static SweepParams P;
-    memset(&P, 0, sizeof P);
-    P.R = 1;
-    P.Lx = P.Ly = P.Lz = 4;
-    P.nshells = m->nshells;
-    P.S = lat->nspecies;
-    P.seed = seed;
-    P.sweep0 = sweep;
-    P.kind = m->kind;
-    P.temp.beta[0] = (float)(1.0 / kT);
-    RepDesc &d = P.rep[0];
-    d.occ = occ;
-    d.nx = lat->nx;
-    d.ny = lat->ny;
-    d.nz = lat->nz;
-    d.NLx = d.nx / 4;
-    d.NLy = d.ny / 4;
-    d.NLz = d.nz / 4;
-    d.rep = replica;
-    fill_qsro_params(m, P.S, P);
-    const int ntr = d.NLx * d.NLy * d.NLz;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, (size_t)ntr * 8, &st);
-    if (!scr) return st;
-    int *swap_a = (int *)scr, *swap_b = swap_a + ntr;
-    const int blocks = std::max(1, std::min((ntr + kTraceTB - 1) / kTraceTB, 8 * ws->num_sms));
-    k_qsro_trace_eval<<<blocks, 128, 0, stream>>>(P, G, k, dE, acc, swap_a, swap_b);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "k_qsro_trace_eval");
-    k_mlp_trace_apply<<<(ntr + 127) / 128, 128, 0, stream>>>(occ, ntr, swap_a, swap_b);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "k_mlp_trace_apply");
-    return SMC_OK;
 }
 
 }  // namespace smc

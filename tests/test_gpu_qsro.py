@@ -1,15 +1,15 @@
 """GPU parity of the qSRO path (Sec. IV-B, Eq. quadratic_local_SRO) against
 the FP64 oracle, through the C ABI.
 
-The sweep evaluates a trial's dE as the sum over its 40-site interaction
-zone of f(x') - f(x) in FP32: for a and b from their full site energies
-(without the constant C), for the other zone sites from the one or two
-count changes the swap makes.  Every trial's dE must lie within DE_TOL_EV of
-the FP64 oracle and decide the same, except where the acceptance threshold
-lies between the two values (the GPU then continues from the oracle's
-state).  The sweep kernel (features from its cache) must equal its traced
-mini-steps (features counted from the occupancy) bit for bit.  Energies and dE/dtheta come from
-exact integer counts in FP64."""
+The sweep evaluates a trial's dE in FP32 from the species of a, b and the
+sites within the model's shells of either, and from those sites' cached
+own-species counts (the W terms).  Every trial's dE must lie within
+DE_TOL_EV of the FP64 oracle and decide the same, except where the
+acceptance threshold lies between the two values (the GPU then continues
+from the oracle's state).  A sweep (its count cache carried through all its
+mini-steps) must equal its traced mini-steps (the cache rebuilt from the
+occupancy at each) bit for bit.  Energies and dE/dtheta come from exact
+integer counts in FP64."""
 import math
 
 import numpy as np
