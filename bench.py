@@ -443,8 +443,8 @@ def profile_fcc(n: int, nsweeps: int, qsro: bool = False):
 
 
 def profile_qsro(n: int, nsweeps: int):
-    """One qSRO sweep launch (the feature-cache kernel runs first) on an N^3
-    box, for ncu captures (-k regex:k_sweep_mlp)."""
+    """qSRO sweeps on an N^3 box (the count-cache kernel k_bq_cache, then 128
+    mini-step launches of k_bq_ministep per sweep), for ncu captures."""
     import torch
     from paper_2604_08250_gb300 import build as _b
     from paper_2604_08250_gb300 import smc
