@@ -149,11 +149,15 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  * MLP models keep a per-site energy cache E[i] = f(x_i) in the workspace
  * (4 N bytes), filled at the start of every call and updated over the
  * interaction zone of every accepted swap, so a trial evaluates only the 40
- * post-swap energies of its zone.  MLP and qSRO models keep the per-site
- * features (species and per-shell species counts, 16 N bytes) the same way;
- * a qSRO trial sums its zone's f(x') - f(x) in FP32 (C left out, where it
- * cancels), within 1e-5 eV of FP64.  Both need every axis a multiple of 4
- * cells and >= 8, nx <= 1024.
+ * post-swap energies of its zone, and the per-site features (species and
+ * per-shell species counts, 16 N bytes) the same way; they need every axis
+ * a multiple of 4 cells and >= 8, nx <= 1024.  qSRO models keep each site's
+ * own-species count per shell (N bytes for 1-2 shells, 2 N for 3), built at
+ * the start of every call and updated by accepted swaps; a trial's dE comes
+ * from the species of a, b and the sites within the model's shells of
+ * either, and from those sites' counts, in FP32 (C left out, where it
+ * cancels), within 1e-5 eV of FP64.  They need every axis a multiple of 4
+ * cells and >= 8.
  * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP or
  * qSRO models on lattices their kernels do not take), SMC_ERR_CUDA. */
 smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
@@ -238,9 +242,9 @@ smc_status smc_energy_grad(const smc_lattice *lat, const smc_model *model, const
  * (as smc_sweep would) and records, per trial in link-cell order
  * c = (cz*NLy + cy)*NLx + cx, the dE it computed (eV) and its decision.
  * MLP models recompute the pre-swap energies (no cache) with the sweep's
- * arithmetic, and qSRO models count the features from occ with the sweep's
- * row arithmetic, so a sweep equals its 2 Lx Ly Lz traced mini-steps bit for
- * bit.
+ * arithmetic, and qSRO models rebuild the own-species counts from occ and
+ * run the sweep's kernel, so a sweep equals its 2 Lx Ly Lz traced
+ * mini-steps bit for bit.
  *   dE   device float [N/n_A], nullable;  acc  device uint8 [N/n_A], nullable. */
 smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, int8_t *occ,
                               uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,
