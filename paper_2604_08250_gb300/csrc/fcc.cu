@@ -541,11 +541,14 @@ __global__ void k_fcc_energy_finish(const __grid_constant__ FccParams P, const u
     }
 }
 
-bool g_fcc_tables = false;
+uint64_t g_fcc_tables = 0;  // bit d: the constant tables are on device d (each device has its own copy)
 
 smc_status fcc_tables()
 {
-    if (g_fcc_tables) return SMC_OK;
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+    if (dev < 64 && (g_fcc_tables >> dev & 1u)) return SMC_OK;
     signed char v[4][24][3] = {};
     int n[4] = {0, 0, 0, 0};
     for (int m = 1; m <= 3; ++m)
@@ -565,7 +568,7 @@ smc_status fcc_tables()
     cudaError_t e = cudaMemcpyToSymbol(c_fcc_vec, v, sizeof v);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_fcc_n, n, sizeof n);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyToSymbol(FCC shells)");
-    g_fcc_tables = true;
+    if (dev < 64) g_fcc_tables |= 1ull << dev;
     return SMC_OK;
 }
 

@@ -316,11 +316,14 @@ int bq_shell(int x, int y, int z, int nsh)
     return m <= nsh ? m : 0;
 }
 
-bool g_bq_shells = false;
+uint64_t g_bq_shells = 0;  // bit d: the shell vectors are on device d (each device has its own copy)
 
 smc_status bq_shell_tables()
 {
-    if (g_bq_shells) return SMC_OK;
+    int dev = 0;
+    cudaError_t de = cudaGetDevice(&dev);
+    if (de != cudaSuccess) return cuda_fail(de, "cudaGetDevice");
+    if (dev < 64 && (g_bq_shells >> dev & 1u)) return SMC_OK;
     signed char v[4][12][3] = {};
     int n[4] = {0, 0, 0, 0};
     for (int x = -2; x <= 2; ++x)
@@ -340,7 +343,7 @@ smc_status bq_shell_tables()
     cudaError_t e = cudaMemcpyToSymbol(c_bq_vec, v, sizeof v);
     if (e == cudaSuccess) e = cudaMemcpyToSymbol(c_bq_n, n, sizeof n);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyToSymbol(BCC shells)");
-    g_bq_shells = true;
+    if (dev < 64) g_bq_shells |= 1ull << dev;
     return SMC_OK;
 }
 
