@@ -22,6 +22,7 @@ import pytest
 
 import oracle
 from paper_2604_08250_gb300 import inputs
+from tests import helpers
 
 Z = (8, 6, 12)  # coordination numbers of shells 1-3 of BCC
 
@@ -195,3 +196,34 @@ def test_gradient_equals_finite_differences():
             assert g[i] == pytest.approx(fd, rel=1e-9, abs=1e-9), (m, p)
             i += 1
     assert g[i] == lat.nsites
+
+
+@pytest.mark.parametrize("nsh,others", [(1, 14), (2, 20), (3, 38)])
+def test_a_swap_changes_site_energies_only_in_its_zone(nsh, others):
+    """Swapping a with a first-shell partner b changes the qSRO site energy
+    of a, b and of sites that hold a or b within the model's shells, and of
+    no other site.  Those sites number 14 / 20 / 38 besides a and b for 1 / 2
+    / 3 shells, and none holds a and b in one shell (a and b lie on different
+    sublattices, shells 1 and 2-3 join different and equal sublattices)."""
+    dims, S = (8, 8, 8), 5
+    lat = oracle.Lattice(*dims, S)
+    V, W, C = inputs.qsro_coeffs(21 + nsh, nsh, S)
+    model = oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C)
+    tabs = [helpers.neighbor_table(*dims, m) for m in range(1, nsh + 1)]
+    rng = np.random.default_rng(nsh)
+    occ = rng.integers(0, S, size=lat.nsites).astype(np.int8)
+    for a in (0, 517, lat.nsites - 1):
+        for b in tabs[0][a]:
+            b = int(b)
+            shell_of = [{int(j): m for m, t in enumerate(tabs) for j in t[s]} for s in (a, b)]
+            assert not any(shell_of[0][j] == shell_of[1][j] for j in set(shell_of[0]) & set(shell_of[1]))
+            zone = (set(shell_of[0]) | set(shell_of[1])) - {a, b}
+            assert len(zone) == others
+            o = occ.copy()
+            o[b] = (o[a] + 1) % S  # a and b differ
+            before = np.array([oracle.site_energy(lat, model, o, i) for i in range(lat.nsites)])
+            o[a], o[b] = o[b], o[a]
+            after = np.array([oracle.site_energy(lat, model, o, i) for i in range(lat.nsites)])
+            changed = set(np.nonzero(before != after)[0].tolist())
+            assert changed <= zone | {a, b}
+            assert {a, b} <= changed
