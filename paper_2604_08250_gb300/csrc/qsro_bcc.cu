@@ -25,7 +25,6 @@
 // partner direction word >> 29, r = word & (2^29 - 1).
 #include <algorithm>
 #include <cstring>
-#include <map>
 #include <type_traits>
 #include <vector>
 
@@ -35,6 +34,12 @@ namespace smc {
 
 namespace {
 
+// Per-call tables (32-bit words, staged into shared memory by every block):
+// Dz[m][A][B][q] = (V_m(B,q) - V_m(A,q)) / z_m at m * 512 + (A * 8 + B) * 8 + q,
+// Wz[m][p] = W_m^p / z_m^2 at kBqW + m * 8 + p, per partner direction the
+// zone's offset indices w = (x+3) + 7 (y+3) + 49 (z+3) (half units) in
+// category order at kBqZ, the partner's offset index at kBqV1 + dir, and the
+// site-index delta of every offset per sublattice at kBqDel + sub * 343.
 constexpr int kBqZmax = 38, kBqT = kMaxShells * 512, kBqW = kBqT, kBqZ = kBqW + kMaxShells * 8,
               kBqV1 = kBqZ + 8 * kBqZmax, kBqDel = kBqV1 + 8, kBqWords = kBqDel + 2 * 343;
 
