@@ -467,7 +467,9 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
         return SMC_ERR_ARG;
     }
     if (is_mlp(model)) return launch_mlp_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
-    if (is_qsro(model)) return launch_qsro_ministeps(lat, model, occ, seed, replica, sweep, 1, &kT, nullptr, nullptr, dE, acc, k, stream);
+    if (is_qsro(model))
+        return launch_qsro_ministeps(lat, model, occ, seed, replica, sweep, 1, &kT, nullptr, nullptr, dE, acc, k,
+                                     stream);
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
