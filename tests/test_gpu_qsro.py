@@ -65,9 +65,9 @@ def site_r(seed, replica, sweep, a):
     return int(w) & ((1 << 29) - 1)
 
 
-@pytest.mark.parametrize("dims,nsh,kT", [((8, 8, 8), 2, 0.07), ((12, 8, 16), 3, 0.05), ((8, 12, 8), 1, 0.1)])
-def test_lockstep_vs_oracle(smc, dims, nsh, kT):
-    S = 5
+@pytest.mark.parametrize("dims,nsh,kT,S", [((8, 8, 8), 2, 0.07, 5), ((12, 8, 16), 3, 0.05, 5), ((8, 12, 8), 1, 0.1, 5),
+                                          ((8, 8, 12), 3, 0.06, 8), ((12, 12, 8), 2, 0.05, 2)])
+def test_lockstep_vs_oracle(smc, dims, nsh, kT, S):
     gm, om = models(smc, nsh, S)
     lat, occ, ref = state(smc, dims, S, 3)
     olat = oracle.Lattice(*dims, S)
