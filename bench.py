@@ -195,8 +195,6 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=0,
                     help="profiling driver: one sweep launch on an N^3 quinary FP32 lattice, nothing else")
     ap.add_argument("--profile-sweeps", type=int, default=1)
-    ap.add_argument("--probe-sfu", action="store_true",
-                    help="measure tanh.approx / ex2.approx throughput (the MLP path's SFU ceiling)")
     ap.add_argument("--profile-mlp", type=int, default=0,
                     help="run the MLP workload (800 K) on a 256 x n x n box once, for ncu captures")
     ap.add_argument("--profile-mlpnet", type=int, default=0,
@@ -213,9 +211,6 @@ def main():
         return
     if args.profile_fcc_qsro:
         profile_fcc(args.profile_fcc_qsro, args.profile_sweeps, qsro=True)
-        return
-    if args.probe_sfu:
-        probe_sfu()
         return
     if args.profile_mlp:
         profile_mlp(args.profile_mlp, args.profile_sweeps)
@@ -384,16 +379,6 @@ def profile_sweep(n: int, nsweeps: int):
     smc.sweep(lat, model, occ, 1, 0, nsweeps, inputs.anneal_kT(1000)[:nsweeps])
     smc.check()
     print(json.dumps({"profile_sweep": n, "sweeps": nsweeps, "ok": True}))
-
-
-def probe_sfu():
-    """Builds and runs paper_2604_08250_gb300/probes/sfu_rate.cu (prints its JSON line)."""
-    from paper_2604_08250_gb300 import build as _b
-    src = os.path.join(ROOT, "paper_2604_08250_gb300", "probes", "sfu_rate.cu")
-    exe = os.path.join(_b.BUILD, "sfu_rate")
-    os.makedirs(_b.BUILD, exist_ok=True)
-    subprocess.run([_b._nvcc()] + _b.ARCH + ["-O3", "-o", exe, src], check=True)
-    subprocess.run([exe], check=True)
 
 
 def qsro_setup(smc, n: int, dev):

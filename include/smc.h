@@ -107,7 +107,11 @@ enum {
  * with pi_m^{pp'} the fraction of the pairs (i, j), j in shell m of i, whose
  * species are {p, p'}; V_m^{pp'} in v_f32 ([nshells][S][S], symmetric),
  * W_m^p in qsro_w ([nshells][S]), C in qsro_c.  The constant lambda sum W^2
- * of the paper's equation is a training regulariser and is not part of E. */
+ * of the paper's equation is a training regulariser and is not part of E.
+ * The paper's linear sum runs over p' < p; with same-element terms included
+ * the model equals the paper's with V'^{pq} = V^{pq} - (V^{pp} + V^{qq})/2
+ * plus sum_m sum_p N_p V_m^{pp}, a constant at fixed composition, so every
+ * dE is the paper form's dE with V' (and V^{pp} = 0 gives that form as is). */
 typedef struct {
     int32_t kind;            /* SMC_PAIR_I32 .. SMC_MLPNET_BF16 */
     int32_t nshells;         /* pair / qSRO shells 1..3 (ignored for SMC_MLP_BF16) */
@@ -170,22 +174,28 @@ smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ
  * their own allocator and must not see a library allocate on its own.  The
  * paper has no counterpart; it is a deployment convenience.
  *
- * It runs the same kernels as smc_sweep for SMC_PAIR_F32 models (same
- * trajectory and e_acc for the same arguments and tuning), but its scratch
- * memory (progress flags and partial sums of at most 16384 link-cell tiles)
- * lives in a fixed 320 KB array inside the library that every GPU which loads
- * the library keeps until the process exits.  It calls no cudaMalloc,
- * cudaFree or allocating library routine.
- *   status  device int32, nullable: set to 0 at the start of the call and to
- *           SMC_ERR_TIMEOUT if a device-side progress wait timed out.
+ * It runs the same kernels as smc_sweep for SMC_PAIR_F32 models: for the
+ * same arguments and tuning it gives the same trajectory, and e_acc and
+ * n_acc bit for bit.  Its scratch memory (progress flags and partial sums of
+ * at most 16384 link-cell tiles) lives in a fixed 320 KB array inside the
+ * library that every GPU which loads the library keeps until the process
+ * exits.  It calls no cudaMalloc, cudaFree or allocating library routine,
+ * and it does not touch the library workspace (smc_check does not see its
+ * device-side failures: they go to `status`).
+ *   status  device int32, required: set to 0 at the start of the call (also
+ *           when nsweeps == 0) and to SMC_ERR_TIMEOUT if a device-side
+ *           progress wait timed out, which leaves the trajectory incomplete.
  *   other arguments as for smc_sweep.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) while that device is current; make that first call
- * before any stream capture.  Every call shares the array and rewrites it, so
- * calls that overlap on the GPU (different streams, or a second process
- * thread) race; serialise them on one stream.
- * Errors: SMC_ERR_ARG as smc_sweep; SMC_ERR_UNSUPPORTED for other model
- * kinds or for lattices needing more than 16384 tiles; SMC_ERR_CUDA. */
+ * Every call looks up the array's device address (cudaGetSymbolAddress)
+ * with the caller's device current; the first call on a device also loads
+ * the library's kernels there, so make it before any stream capture.  Every
+ * call shares the array and rewrites it (the flags and partial sums it needs
+ * are cleared at the start of each launch), so calls that overlap on the GPU
+ * (different streams, or a second host thread) race; serialise them on one
+ * stream.
+ * Errors: SMC_ERR_ARG as smc_sweep, and for a NULL status; SMC_ERR_UNSUPPORTED
+ * for other model kinds or for lattices needing more than 16384 tiles;
+ * SMC_ERR_CUDA. */
 smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int8_t *occ,
                              uint64_t seed, uint32_t replica, uint64_t sweep0, int32_t nsweeps,
                              const double *kT, double *e_acc, int64_t *n_acc, int32_t *status,

@@ -401,8 +401,8 @@ smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int
         set_error("smc_sweep_noalloc supports SMC_PAIR_F32 models only");
         return SMC_ERR_UNSUPPORTED;
     }
-    if (!occ || nsweeps < 0 || (nsweeps > 0 && !kT)) {
-        set_error("occ and kT must be non-NULL and nsweeps >= 0");
+    if (!occ || !status || nsweeps < 0 || (nsweeps > 0 && !kT)) {
+        set_error("occ, status and kT must be non-NULL and nsweeps >= 0");
         return SMC_ERR_ARG;
     }
     if (sweep0 + (uint64_t)nsweeps > 0xFFFFFFFFFFFFFFFEull || sweep0 + (uint64_t)nsweeps < sweep0) {
@@ -418,7 +418,10 @@ smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int
         set_error("too many sweeps in one call");
         return SMC_ERR_ARG;
     }
-    if (nsweeps == 0) return SMC_OK;
+    if (nsweeps == 0) {
+        const cudaError_t e = cudaMemsetAsync(status, 0, sizeof(int32_t), stream);
+        return e == cudaSuccess ? SMC_OK : cuda_fail(e, "cudaMemsetAsync(status)");
+    }
     return launch_pair_sweep_noalloc(lat, model, occ, seed, replica, sweep0, nsweeps, kT, e_acc, n_acc, status,
                                      stream);
 }

@@ -1557,10 +1557,13 @@ smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int
 // whose memory is owned by their own pool and must not see the library
 // allocate behind its back -- so this entry point keeps its scratch (progress
 // flags, per-tile partial sums, ticket and abort words) in the file-scope
-// array below instead of the library workspace.  Every GPU that loads the
-// library holds the array until the process exits.  Host code must not use
-// the array's name as a device address: its device address is looked up once
-// per device with cudaGetSymbolAddress while that device is current.
+// array below instead of the library workspace, and reports device-side
+// failures in the caller's status word.  Every GPU that loads the library
+// holds the array until the process exits.  Host code must not use the
+// array's name as a device address: the address is looked up with
+// cudaGetSymbolAddress on every call, with the caller's device current (the
+// lookup allocates nothing once the module is loaded, and stays valid after
+// the context is re-created).
 // ---------------------------------------------------------------------------
 constexpr int kNoAllocMaxTiles = 16384;
 constexpr size_t kNoAllocFlagsOff = 256;
@@ -1570,8 +1573,6 @@ constexpr size_t kNoAllocBytes = kNoAllocPartNOff + (size_t)kNoAllocMaxTiles * 8
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
 
-static unsigned char *g_noalloc_ptr[64];  // device address per device, set on first use
-
 smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                                      uint32_t replica, uint64_t sweep0, int nsweeps, const double *kT,
                                      double *e_acc, int64_t *n_acc, int32_t *status, cudaStream_t stream)
@@ -1579,17 +1580,10 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= 64) {
-        set_error("device index %d out of range", dev);
-        return SMC_ERR_UNSUPPORTED;
-    }
-    if (!g_noalloc_ptr[dev]) {
-        void *ptr = nullptr;
-        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
-        g_noalloc_ptr[dev] = (unsigned char *)ptr;
-    }
-    unsigned char *scr = g_noalloc_ptr[dev];
+    void *sym = nullptr;
+    e = cudaGetSymbolAddress(&sym, g_noalloc_scratch);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(no-alloc scratch)");
+    unsigned char *scr = (unsigned char *)sym;
     // Device attributes the plans need, queried directly (no workspace).
     Workspace ws;
     int sms = 0, optin = 0;
@@ -1635,7 +1629,7 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast)
         for (int g = 0; g < pl.G; ++g) P.lag[g] = (g % pl.Ly) == 0 ? 1 : 2;
-    P.skip_tile = -1;
+    P.skip_tile = (int)debug_skip_tile();
     P.seed = seed;
     P.timeout_ns = debug_timeout_ns();
     RepDesc &d = P.rep[0];
@@ -1690,19 +1684,18 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     P.part_n = (long long *)(scr + kNoAllocPartNOff);
     P.ticket = (unsigned *)(scr + 0);
     P.abort_flag = (int *)(scr + 4);
-    P.status = status ? (int *)status : (int *)(scr + 8);
+    P.status = (int *)status;
     P.tab = nullptr;
-    if (status) {
-        e = cudaMemsetAsync(status, 0, sizeof(int32_t), stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
-    }
+    e = cudaMemsetAsync(status, 0, sizeof(int32_t), stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
     for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
         const int nc = std::min(chunk, nsweeps - t0);
         P.sweep0 = sweep0 + (uint64_t)t0;
         P.nsweeps = nc;
         P.beta_stride = constant ? 0 : nc;
         for (int t = 0; t < (constant ? 1 : nc); ++t) P.temp.beta[t] = (float)(1.0 / kT[t0 + t]);
-        // the array keeps the last call's contents: zero what must start at zero
+        // the array keeps the last call's contents: zero what must start at
+        // zero (ticket, abort word, flags and partial sums of this call's tiles)
         e = cudaMemsetAsync(scr, 0, kNoAllocFlagsOff + (size_t)P.ntiles * 4, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartEOff, 0, (size_t)P.ntiles * 8, stream);
         if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartNOff, 0, (size_t)P.ntiles * 8, stream);

@@ -38,8 +38,13 @@ def dev():
     return torch.device("cuda:0")
 
 
-def models(smc, nsh, S, seed=7):
+def models(smc, nsh, S, seed=7, zero_diag=False):
+    """zero_diag: V^{pp} = 0, so that the linear sum over p' <= p is the
+    paper's sum over p' < p exactly."""
     V, W, C = inputs.qsro_coeffs(seed, nsh, S)
+    if zero_diag:
+        for m in range(nsh):
+            np.fill_diagonal(V[m], 0.0)
     return (smc.Model(smc.QSRO_F32, nsh, V, qsro_w=W, qsro_c=C),
             oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C))
 
@@ -65,10 +70,12 @@ def site_r(seed, replica, sweep, a):
     return int(w) & ((1 << 29) - 1)
 
 
-@pytest.mark.parametrize("dims,nsh,kT,S", [((8, 8, 8), 2, 0.07, 5), ((12, 8, 16), 3, 0.05, 5), ((8, 12, 8), 1, 0.1, 5),
-                                          ((8, 8, 12), 3, 0.06, 8), ((12, 12, 8), 2, 0.05, 2)])
-def test_lockstep_vs_oracle(smc, dims, nsh, kT, S):
-    gm, om = models(smc, nsh, S)
+@pytest.mark.parametrize("dims,nsh,kT,S,zero_diag", [((8, 8, 8), 2, 0.07, 5, False), ((12, 8, 16), 3, 0.05, 5, False),
+                                                    ((8, 12, 8), 1, 0.1, 5, False), ((8, 8, 12), 3, 0.06, 8, False),
+                                                    ((12, 12, 8), 2, 0.05, 2, False), ((8, 8, 8), 2, 0.07, 5, True),
+                                                    ((12, 8, 8), 3, 0.05, 5, True)])
+def test_lockstep_vs_oracle(smc, dims, nsh, kT, S, zero_diag):
+    gm, om = models(smc, nsh, S, zero_diag=zero_diag)
     lat, occ, ref = state(smc, dims, S, 3)
     olat = oracle.Lattice(*dims, S)
     nA, _ = oracle.schedule(olat)

@@ -2,7 +2,7 @@
 
 On the 16-site binary lattice (2x2x2 cells) the canonical averages <E>,
 <alpha> and d<alpha>/dtheta are known exactly by enumeration; GPU sweeps must
-reproduce them within 4 batch-means standard errors, the derivative through
+reproduce them within 3 batch-means standard errors, the derivative through
 the fluctuation formula on per-sample dE/dtheta from smc_energy_grad.
 SMCEnergy must give smc_energy forward and smc_energy_grad backward."""
 import numpy as np
@@ -64,10 +64,10 @@ def test_gpu_chain_matches_enumeration_16_site(smc, kT):
     smc.check()
     Es, As, Gs = Es.cpu().numpy(), As.cpu().numpy(), Gs.cpu().numpy().astype(np.float64)
     m, se = batch_se(Es)
-    assert abs(m - mE) <= 4 * se + 1e-9, (m, mE, se)
+    assert abs(m - mE) <= 3 * se + 1e-9, (m, mE, se, (m - mE) / se)
     a01 = As[:, 0, 0, 1]
     m, se = batch_se(a01)
-    assert abs(m - mA[0, 0, 1]) <= 4 * se + 1e-9, (m, mA[0, 0, 1], se)
+    assert abs(m - mA[0, 0, 1]) <= 3 * se + 1e-9, (m, mA[0, 0, 1], se, (m - mA[0, 0, 1]) / se)
     # d<alpha_1^{01}>/dtheta from the samples; standard error from contiguous batches
     nb = 20
     per = np.stack([smc.observable_gradient(torch.tensor(a[:, None]), torch.tensor(g), beta).numpy()[0]
@@ -75,7 +75,7 @@ def test_gpu_chain_matches_enumeration_16_site(smc, kT):
     est = smc.observable_gradient(torch.tensor(a01[:, None]), torch.tensor(Gs), beta).numpy()[0]
     se = per.std(axis=0, ddof=1) / np.sqrt(nb)
     want = dA[0, 0, 1]
-    assert np.all(np.abs(est - want) <= 4 * se + 1e-6 * np.abs(want).max() + 1e-9), (est, want, se)
+    assert np.all(np.abs(est - want) <= 3 * se + 1e-6 * np.abs(want).max() + 1e-9), (est, want, se, (est - want) / se)
 
 
 @pytest.mark.parametrize("kind", [2, 3])

@@ -48,6 +48,10 @@ MUTANTS = {
     "mlp_features_count_own_species": ([("            x[ORC_MLP_SPECIES * m + occ[j]] += 1.0;",
                                          "            x[ORC_MLP_SPECIES * m + occ[i]] += 1.0;")],
                                        [energy_pins.test_mlp_features_on_b2]),
+    "qsro_linear_diagonal_doubled": ([("for (int r = 0; r <= p; ++r) e += (double)m->v_f32[((sh - 1) * S + p) * S + r] * (n[p][r] / total);",
+                                       "for (int r = 0; r <= p; ++r) e += (double)m->v_f32[((sh - 1) * S + p) * S + r] * ((r == p ? 2.0 : 1.0) * n[p][r] / total);")],
+                                     [lambda: qsro_pins.test_linear_sum_is_the_strict_form_reparametrised("fcc", 2, True),
+                                      lambda: qsro_pins.test_linear_sum_is_the_strict_form_reparametrised("bcc", 1, False)]),
     "qsro_gradient_of_w_linear": ([("                gW[(sh - 1) * S + p] += pi * pi;",
                                     "                gW[(sh - 1) * S + p] += pi;")],
                                   [qsro_pins.test_gradient_equals_finite_differences]),

@@ -227,3 +227,78 @@ def test_a_swap_changes_site_energies_only_in_its_zone(nsh, others):
             changed = set(np.nonzero(before != after)[0].tolist())
             assert changed <= zone | {a, b}
             assert {a, b} <= changed
+
+
+def _strict_form_total(occ, V, W, C, tables):
+    """Eq. quadratic_local_SRO as the paper prints it: the linear sum over
+    p' < p, i.e. over the pairs (i, j) of unlike species only, each with
+    weight V_m^{s_i s_j} / z_m; the quadratic term W_m^{s_i} (pi_m^{ss})^2
+    with pi_m^{ss} the fraction of i's shell-m neighbours of i's own species;
+    C per site.  Written from the equation with brute-force neighbour tables,
+    independently of the oracle."""
+    occ = np.asarray(occ).astype(np.int64)
+    E = len(occ) * float(C)
+    for m, nb in enumerate(tables):
+        z = nb.shape[1]
+        si, sj = occ[:, None], occ[nb]
+        E += float((V[m].astype(np.float64)[si, sj] * (sj != si)).sum()) / z
+        E += float((W[m].astype(np.float64)[occ] * ((sj == si).sum(1) / z) ** 2).sum())
+    return E
+
+
+def _fcc_tables(dims, nsh):
+    from tests.test_oracle_fcc import brute_shells
+    sh = brute_shells(dims)
+    return [np.array([sorted(s) for s in sh[m]]) for m in range(1, nsh + 1)]
+
+
+@pytest.mark.parametrize("lattice", ["bcc", "fcc"])
+@pytest.mark.parametrize("nsh", [1, 2, 3])
+@pytest.mark.parametrize("with_w", [False, True])
+def test_linear_sum_is_the_strict_form_reparametrised(lattice, nsh, with_w):
+    """The oracle sums the linear qSRO term over p' <= p with a full
+    symmetric V.  The paper's sum runs over p' < p.  The two describe the same
+    model: with V'^{pq} = V^{pq} - (V^{pp} + V^{qq}) / 2 (zero diagonal),
+    E_oracle(V) = E_strict(V') + sum_m sum_p N_p V_m^{pp}, a constant at fixed
+    composition, so every dE of the oracle is the strict form's dE with V'.
+    Checked on totals and swaps, BCC and FCC, with and without the W term."""
+    S = 4
+    V, W, C = inputs.qsro_coeffs(40 + nsh, nsh, S)
+    if not with_w:
+        W = np.zeros_like(W)
+    V64 = V.astype(np.float64)
+    d = np.stack([np.diag(V64[m]) for m in range(nsh)])
+    Vs = V64 - (d[:, :, None] + d[:, None, :]) / 2.0
+    if lattice == "bcc":
+        dims = (4, 4, 6)
+        lat = oracle.Lattice(*dims, S)
+        N = lat.nsites
+        tables = [helpers.neighbor_table(*dims, m) for m in range(1, nsh + 1)]
+        total, dE = oracle.total_energy, oracle.delta_e
+        occ = oracle.init_lattice(lat, inputs.dirichlet_counts(N, S, nsh), nsh)
+        first = tables[0]
+    else:
+        dims = (4, 4, 4)
+        lat = oracle.Lattice(*dims, S)
+        N = oracle.fcc_nsites(lat)
+        tables = _fcc_tables(dims, nsh)
+        total, dE = oracle.fcc_total_energy, oracle.fcc_delta_e
+        occ = oracle.fcc_init_lattice(lat, inputs.dirichlet_counts(N, S, nsh), nsh)
+        first = tables[0]
+    model = oracle.Model(oracle.QSRO, nsh, V, qsro_w=W, qsro_c=C)
+    Np = np.bincount(occ, minlength=S)
+    const = float((d * Np[None, :]).sum())
+    scale = float(np.abs(V64).max()) * N
+    e_or = total(lat, model, occ)
+    assert e_or == pytest.approx(_strict_form_total(occ, Vs, W, C, tables) + const, rel=1e-12, abs=1e-12 * scale)
+    rng = np.random.default_rng(nsh + 10 * with_w)
+    for _ in range(12):
+        a = int(rng.integers(N))
+        b = int(first[a][rng.integers(first.shape[1])])
+        if occ[a] == occ[b]:
+            continue
+        d_or = dE(lat, model, occ, a, b)
+        e0 = _strict_form_total(occ, Vs, W, C, tables)
+        occ[a], occ[b] = occ[b], occ[a]
+        e1 = _strict_form_total(occ, Vs, W, C, tables)
+        assert d_or == pytest.approx(e1 - e0, rel=1e-10, abs=1e-12)
