@@ -16,7 +16,7 @@
  *   (MLP models: <= 5).
  * Shells.  1: 8 neighbours at sqrt(3)a/2, ordered lexicographically in
  *   (+-1/2)^3 with - before +; 2: 6 at a; 3: 12 at sqrt(2)a.
- * Link cells and mini-steps (Sec. II-A; Algorithm 1 lines 1-2).  The link-cell
+ * Link cells and mini-steps (Sec. II-A; Algorithm 1).  The link-cell
  *   edge along an axis of n cells is 4 if n >= 8 and n % 4 == 0, else n.
  *   A sweep is n_A = 2 Lx Ly Lz mini-steps; mini-step k visits the offset
  *   (sub, dx, dy, dz) with k = ((sub*Lz + dz)*Ly + dy)*Lx + dx, and every link
@@ -27,7 +27,7 @@
  *   partner = shell-1 vector [word >> 29], r = word & (2^29 - 1).  Results do
  *   not depend on the launch configuration.  Sweep indices 2^64-2 and 2^64-1
  *   are reserved for the initial configuration.
- * Metropolis (Algorithm 1 line 9).  Integer models: accept iff dE <= 0 or
+ * Metropolis (Algorithm 1).  Integer models: accept iff dE <= 0 or
  *   r < floor(2^29 exp(-dE unit_ev / kT)) (table built on the host in FP64).
  *   Floating-point models: accept iff dE <= 0 or (r + 1/2) 2^-29 <
  *   exp(-dE / kT) evaluated in FP32.  A swap of two equal species is an
@@ -313,10 +313,21 @@ typedef struct {
 } smc_tuning;
 smc_status smc_set_tuning(const smc_tuning *t);
 
-/* Test hooks.  SMC_DBG_TIMEOUT_MS sets the progress-wait limit (default
- * 2000 ms); SMC_DBG_SKIP_PUBLISH makes the tile with that index never publish
- * its progress so that its neighbours time out (-1 = off). */
-enum { SMC_DBG_TIMEOUT_MS = 1, SMC_DBG_SKIP_PUBLISH = 2 };
+/* Test and tuning hooks.  SMC_DBG_TIMEOUT_MS sets the progress-wait limit
+ * (default 2000 ms); SMC_DBG_SKIP_PUBLISH makes the tile with that index never
+ * publish its progress so that its neighbours time out (-1 = off).
+ * SMC_DBG_FAST_TEAM (1, 2 or 4 warps per link-cell column),
+ * SMC_DBG_FAST_BUFFERS (1 or 2 row buffers per column) and
+ * SMC_DBG_FAST_STAGING (1: one bulk copy per row; 2: 16-byte cp.async) fix
+ * those launch choices of the pair sweep on lattices with four-cell link
+ * cells on every axis (0 = automatic); results never depend on them. */
+enum {
+    SMC_DBG_TIMEOUT_MS = 1,
+    SMC_DBG_SKIP_PUBLISH = 2,
+    SMC_DBG_FAST_TEAM = 3,
+    SMC_DBG_FAST_BUFFERS = 4,
+    SMC_DBG_FAST_STAGING = 5
+};
 smc_status smc_debug_set(int32_t what, int64_t value);
 
 #ifdef __cplusplus

@@ -440,7 +440,7 @@ static int build_omega(const orc_lattice *lat, const orc_model *m, int64_t a, in
     return u;
 }
 
-/* dE of swapping a and b, by Algorithm 1 lines 4-8: local energies of Omega
+/* dE of swapping a and b, by Algorithm 1: local energies of Omega
  * before (E0) and after (E1) the swap, reduced over Omega. */
 double orc_delta_e(const orc_lattice *lat, const orc_model *m, int8_t *occ, int64_t a, int64_t b)
 {
@@ -512,7 +512,7 @@ void orc_sro(const orc_lattice *lat, int nshells, const int8_t *occ, double *alp
 }
 
 /* ------------------------------------------------------------------------ */
-/* Metropolis criterion (Algorithm 1 line 9).                                */
+/* Metropolis criterion (Algorithm 1).                                */
 /* ------------------------------------------------------------------------ */
 #define R_BITS 29
 #define R_SCALE 536870912.0 /* 2^29 */
@@ -629,7 +629,7 @@ static int one_trial(const orc_lattice *lat, const orc_model *m, int8_t *occ, ui
     return one_trial_at(lat, m, occ, seed, replica, sweep, a, a, kT, at, dE_out, b_out);
 }
 
-/* Algorithm 1 as printed, for one mini-step: sigma1 = sigma0, every trial
+/* The steps of Algorithm 1 in its order, for one mini-step: sigma1 = sigma0, every trial
  * swapped in sigma1, local energies E0 (sigma0) and E1 (sigma1) of all sites,
  * reduction over each Omega, Metropolis, accepted sites copied to sigma0. */
 static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t *occ,
@@ -644,7 +644,7 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
     int64_t *A = (int64_t *)malloc(sizeof(int64_t) * (size_t)NC);
     int64_t *B = (int64_t *)malloc(sizeof(int64_t) * (size_t)NC);
     uint32_t *R = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)NC);
-    memcpy(s1, occ, (size_t)N); /* line 3 */
+    memcpy(s1, occ, (size_t)N); /* the auxiliary copy sigma1 */
     for (int64_t c = 0; c < NC; ++c) {
         int64_t a = trial_site(lat, sc, k, c);
         uint32_t w = site_word(seed, replica, sweep, a);
@@ -653,12 +653,12 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
         B[c] = orc_neighbor(lat, a, v[0], v[1], v[2]);
         R[c] = w & ((1u << R_BITS) - 1u);
     }
-    for (int64_t c = 0; c < NC; ++c) { /* line 5 */
+    for (int64_t c = 0; c < NC; ++c) { /* every trial swap made in sigma1 */
         int8_t t = s1[A[c]];
         s1[A[c]] = s1[B[c]];
         s1[B[c]] = t;
     }
-    for (int64_t i = 0; i < N; ++i) { /* lines 4 and 6 */
+    for (int64_t i = 0; i < N; ++i) { /* local energies E0 of sigma0, E1 of sigma1 */
         if (m->kind == ORC_PAIR_I32) {
             E0[i] = (double)site_energy2_i64(lat, m, occ, i);
             E1[i] = (double)site_energy2_i64(lat, m, s1, i);
@@ -670,7 +670,7 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
     int64_t om[2 + 4 * 26];
     for (int64_t c = 0; c < NC; ++c) {
         int n = build_omega(lat, m, A[c], B[c], om);
-        double eb0 = 0.0, eb1 = 0.0; /* lines 7-8 */
+        double eb0 = 0.0, eb1 = 0.0; /* the reductions over Omega */
         for (int t = 0; t < n; ++t) {
             eb0 += E0[om[t]];
             eb1 += E1[om[t]];
@@ -683,7 +683,7 @@ static void ministep_literal(const orc_lattice *lat, const orc_model *m, int8_t 
         } else {
             acc = accept_fp(dE, R[c], kT);
         }
-        if (acc) { /* lines 10-12 */
+        if (acc) { /* an accepted swap is copied back to sigma0 */
             occ[A[c]] = s1[A[c]];
             occ[B[c]] = s1[B[c]];
             if (e_acc) *e_acc += dE;
@@ -1137,7 +1137,7 @@ int64_t orc_fcc_total_energy_i64(const orc_lattice *lat, const orc_model *m, con
 }
 
 /* dE of swapping a and b: the local energies of a, b and every site within
- * the model's shells of either, before and after (Algorithm 1 lines 4-8). */
+ * the model's shells of either, before and after (Algorithm 1). */
 double orc_fcc_delta_e(const orc_lattice *lat, const orc_model *m, int8_t *occ, int64_t a, int64_t b)
 {
     fcc_init();

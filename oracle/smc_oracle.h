@@ -18,7 +18,7 @@
  *       shell 1 (8):  (+-1,+-1,+-1), ordered lexicographically, - before +;
  *       shell 2 (6):  (+-2,0,0), (0,+-2,0), (0,0,+-2);
  *       shell 3 (12): two non-zero components, each +-2.
- *   - Link cells (Sec. II-A, Algorithm 1 line 2): edge L = 4 cells along an
+ *   - Link cells (Sec. II-A, Algorithm 1): edge L = 4 cells along an
  *     axis whose length n is >= 8 and a multiple of 4, else L = n (one cell
  *     along that axis).  n_A = 2*Lx*Ly*Lz mini-steps per sweep; mini-step k
  *     visits offset (sub, dx, dy, dz) with k = ((sub*Lz + dz)*Ly + dy)*Lx + dx.
@@ -26,7 +26,7 @@
  *     counter = (s >> 2, replica, sweep lo, sweep hi); site s uses output
  *     word s & 3.  Partner direction = word >> 29 (index into shell 1),
  *     acceptance number r = word & (2^29 - 1).
- *   - Metropolis (Algorithm 1 line 9): integer models accept iff dE <= 0 or
+ *   - Metropolis (Algorithm 1): integer models accept iff dE <= 0 or
  *     r < T[dE], T[d] = floor(2^29 exp(-d*unit/kT)); floating-point models
  *     accept iff dE <= 0 or (r + 1/2) 2^-29 < exp(-dE/kT).
  */

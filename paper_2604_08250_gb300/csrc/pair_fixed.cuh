@@ -1,0 +1,121 @@
+// pair_fixed.cuh -- dE of a pair-model swap trial in exact fixed point, from
+// per-shell species histograms (Algorithm 1 with pair site energies).
+//
+// For a trial a <-> b with species A = s_a, B = s_b and
+// D_m[q] = V_m(B, q) - V_m(A, q),
+//   dE = sum_m sum_q c_m[q] D_m[q],
+//   c_m[q] = #{j in N_m(a) \ b : s_j = q} - #{j in N_m(b) \ a : s_j = q}.
+// Each shell holds as many neighbours of a (without b) as of b (without a),
+// so sum_q c_m[q] = 0 and the reference species R = S - 1 drops out:
+//   dE = sum_m sum_{q < R} c_m[q] D'_m[q],  D'_m[q] = D_m[q] - D_m[R].
+// The coefficients are taken in fixed point, Q_m[q] = round(D'_m[q] 2^sigma)
+// (integer models: sigma = 0 and Q = D' exactly), and the counts live in
+// 8-bit fields of 32-bit words, biased by b_m (8 for shells 1-2, whose
+// |c| <= 7, and 16 for shell 3, |c| <= 12): word w of shell m holds
+// c_m[4w + j] + b_m in byte j.  Then
+//   dE_fix = sum_m sum_w dot4(H_m^w, Q_m^w) - sum_m b_m sum_q Q_m[q]
+// where dot4 is a four-byte dot product.  Q is split into four byte planes,
+// Q = P0 + 2^8 P1 + 2^16 P2 + 2^24 P3 (P3 signed), so that every dot4 is one
+// dp4a instruction; all of it is int32 arithmetic modulo 2^32, which is exact
+// because the true dE_fix lies in (-2^31, 2^31) (sigma is chosen so).  The
+// result dE_fix 2^-sigma differs from the exact dE of the FP32 coefficients
+// by at most sum_q |c_m[q]| 2^-(sigma+1) <= 13 * 2^-sigma for two shells.
+//
+// A site of species s adds 1 << (8 s) to the low word (zero for s >= 4: the
+// shift amount is clamped, not wrapped) and 1 << (8 s - 32) to the high word
+// (species 4..7; zero for s < 4).  The sweep kernels keep species multiplied
+// by 8 in memory during a launch, so the shift amount is the stored byte.
+#pragma once
+
+#include "sweep_common.cuh"
+
+namespace smc {
+
+// Words of a table row (A, B): shells x species words x 4 byte planes, then
+// the bias word, padded to a multiple of 4 words (16-byte loads).
+__host__ __device__ constexpr int qrow_words(int NSH, int SW) { return (NSH * SW * 4 + 1 + 3) / 4 * 4; }
+constexpr int kQRows = kMaxSpecies * kMaxSpecies;  // row A * 8 + B
+constexpr int kMaxQRowWords = 28;                  // three shells, two species words
+static_assert(qrow_words(3, 2) == kMaxQRowWords, "row size");
+constexpr float kAcceptBias = 30.0f;               // 2^30 = twice the range of the acceptance word r
+
+__device__ __forceinline__ uint32_t nib8(uint32_t v8)
+{
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(v8));  // clamped: 0 for v8 >= 32
+    return r;
+}
+__device__ __forceinline__ uint32_t nib8hi(uint32_t v8)
+{
+    uint32_t r;
+    asm("shl.b32 %0, %1, %2;" : "=r"(r) : "r"(1u), "r"(v8 - 32u));  // 0 for v8 < 32 (huge shift)
+    return r;
+}
+__device__ __forceinline__ uint32_t dp4a_uu(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t dp4a_us(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ float ex2_approx(float x)
+{
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+// dE_fix of the histogram words H[m][w] against table row `row` (smem or
+// global, 16-byte aligned).
+template <int NSH, int SW>
+__device__ __forceinline__ int32_t dot_fixed(const uint32_t (&H)[NSH][SW], const uint32_t *row)
+{
+    constexpr int NB = NSH * SW * 4;
+    uint32_t p0 = row[NB], p1 = 0u, p2 = 0u, p3 = 0u;
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int w = 0; w < SW; ++w) {
+            const uint4 q = *(const uint4 *)(row + (m * SW + w) * 4);
+            p0 = dp4a_uu(H[m][w], q.x, p0);
+            p1 = dp4a_uu(H[m][w], q.y, p1);
+            p2 = dp4a_uu(H[m][w], q.z, p2);
+            p3 = dp4a_us(H[m][w], q.w, p3);
+        }
+    return (int32_t)(p0 + (p1 << 8) + (p2 << 16) + (p3 << 24));
+}
+
+// Metropolis decision on dE_fix.  Integer models (sigma = 0): dE <= 0 or
+// r < T[dE] (host FP64 table).  Floating-point models: dE <= 0 or
+// r + 1/2 < 2^29 exp(-dE / kT).  With 2^30 exp(-dE / kT) = 2^x,
+// x = dE_fix cx + 30 and cx = -log2(e) 2^-sigma / kT (host FP64, rounded to
+// FP32), u = 2^x from ex2.approx, the test is 2r + 1 < u, and since 2r + 1 is
+// an integer this is exactly 2r + 1 < ceil(u) in integers.
+template <bool IS_INT>
+__device__ __forceinline__ bool accept_fixed(int32_t dE, uint32_t r, float cx, const uint32_t *tab, int2 ti)
+{
+    if constexpr (IS_INT) {
+        if (dE <= 0) return true;
+        return dE < ti.y && r < __ldg(tab + ti.x + dE);
+    } else {
+        const float u = ex2_approx(fmaf((float)dE, cx, kAcceptBias));
+        const int thr = __float2int_ru(u);  // saturates for u >= 2^31 (then dE < 0)
+        return (dE <= 0) | ((int)(2u * r + 1u) < thr);
+    }
+}
+
+// Host: fixed-point table of a pair model (rows A * 8 + B, A, B < 8; rows of
+// species >= S are zero).  Returns false if a coefficient is not finite.
+struct PairTable {
+    int nsh = 2, sw = 1, rw = 12, sigma = 0;
+    double scale = 1.0;  // eV (or units) per dE_fix unit: 2^-sigma
+    std::vector<uint32_t> rows;
+};
+bool build_pair_table(const smc_model *m, int S, PairTable &t);
+
+}  // namespace smc

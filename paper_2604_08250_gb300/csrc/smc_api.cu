@@ -17,6 +17,7 @@ static std::mutex g_lock;  // the workspace and parameter blocks are shared
 static thread_local Tuning g_tuning;
 static int64_t g_timeout_ns = 2000LL * 1000 * 1000;
 static int64_t g_skip_tile = -1;
+static int g_fast_team = 0, g_fast_nbuf = 0, g_fast_stage = 0;
 
 void set_error(const char *fmt, ...)
 {
@@ -35,6 +36,9 @@ smc_status cuda_fail(cudaError_t e, const char *what)
 Tuning current_tuning() { return g_tuning; }
 int64_t debug_timeout_ns() { return g_timeout_ns; }
 int64_t debug_skip_tile() { return g_skip_tile; }
+int debug_fast_team() { return g_fast_team; }
+int debug_fast_nbuf() { return g_fast_nbuf; }
+int debug_fast_stage() { return g_fast_stage; }
 
 static Workspace g_ws[64];
 
@@ -267,6 +271,9 @@ smc_status smc_check(cudaStream_t stream)
         e = cudaMemcpy(ws->status, &zero, sizeof zero, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(status reset)");
         if (code == SMC_ERR_TIMEOUT) set_error("a device-side progress wait timed out");
+        if (code == SMC_ERR_ARG)
+            set_error("an occupancy value lies outside [0, nspecies) (the sweep took it modulo 8; the result is "
+                      "undefined)");
         return (smc_status)code;
     }
     return SMC_OK;
@@ -303,6 +310,30 @@ smc_status smc_debug_set(int32_t what, int64_t value)
     }
     if (what == SMC_DBG_SKIP_PUBLISH) {
         g_skip_tile = value;
+        return SMC_OK;
+    }
+    if (what == SMC_DBG_FAST_TEAM) {
+        if (value != 0 && value != 1 && value != 2 && value != 4) {
+            set_error("team size must be 0, 1, 2 or 4");
+            return SMC_ERR_ARG;
+        }
+        g_fast_team = (int)value;
+        return SMC_OK;
+    }
+    if (what == SMC_DBG_FAST_BUFFERS) {
+        if (value < 0 || value > 2) {
+            set_error("buffer count must be 0, 1 or 2");
+            return SMC_ERR_ARG;
+        }
+        g_fast_nbuf = (int)value;
+        return SMC_OK;
+    }
+    if (what == SMC_DBG_FAST_STAGING) {
+        if (value < 0 || value > 2) {
+            set_error("staging must be 0, 1 or 2");
+            return SMC_ERR_ARG;
+        }
+        g_fast_stage = (int)value;
         return SMC_OK;
     }
     set_error("unknown debug key %d", what);

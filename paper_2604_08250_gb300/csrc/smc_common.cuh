@@ -138,6 +138,9 @@ struct Tuning {
 Tuning current_tuning();
 int64_t debug_timeout_ns();
 int64_t debug_skip_tile();
+int debug_fast_team();
+int debug_fast_nbuf();
+int debug_fast_stage();
 
 bool lattice_valid(const smc_lattice *lat, bool mlp);
 bool model_valid(const smc_lattice *lat, const smc_model *m);

@@ -8,6 +8,9 @@ namespace smc {
 
 constexpr int kMaxBeta = 1024;
 constexpr int kMaxGroups = 64;
+// Fixed-point pair tables (pair_fixed.cuh): 64 rows (A * 8 + B) of at most
+// 28 words.
+constexpr int kPairQWords = 64 * 28;
 
 // MLP weights as the kernels read them (device memory, one copy per call):
 // W1 padded from 20 to 32 inputs, BF16 bit patterns, row = output unit; W2
@@ -44,7 +47,11 @@ struct SweepParams {
     int beta_stride;  // 0: one value per replica; else values per (replica, sweep)
     int tpc;          // accumulator slots per CTA (>= tiles owned by any CTA)
     int skip_tile;
-    int pad0;
+    int maxNLx;           // fast kernel: most link cells along x of any replica
+    int team;             // fast kernel: warps sharing one column (1, 2 or 4)
+    int team_bytes;       // fast kernel: shared-memory bytes per team
+    int nbuf;             // fast kernel: row buffers per team (1 or 2)
+    int stage;            // fast kernel: row staging by bulk copies (0) or 16-byte cp.async (1)
     uint64_t seed, sweep0;
     long long timeout_ns;
     uint32_t *flags;
@@ -63,10 +70,14 @@ struct SweepParams {
     uint4 *fcache;        // per-site MLP features {species, shell-1, -2, -3 packed counts} (device, N)
     int rowB;             // fast kernel: row stride in shared memory
     int mlp_chunk;        // MLP sweep: trials of a mini-step evaluated together
+    int qrow;             // pair kernels: words per fixed-point table row
+    int pad1;
+    double escale;        // pair kernels: eV (integer models: units) per dE_fix unit, 2^-sigma
     union {
-        float beta[kMaxBeta];
+        float beta[kMaxBeta];        // MLP and qSRO kernels: 1 / kT; pair kernels: cx = -log2(e) 2^-sigma / kT
         int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
     } temp;
+    uint32_t qtab[kPairQWords];  // pair kernels: fixed-point table rows (pair_fixed.cuh)
     union {
         int di[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];
         float df[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];

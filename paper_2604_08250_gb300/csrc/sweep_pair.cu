@@ -1,4 +1,4 @@
-// sweep_pair.cu -- persistent swap-MC sweep kernel for pair models.
+// sweep_pair.cu -- persistent swap-MC sweep kernels for pair models.
 //
 // Algorithm 1 of the paper runs n_A sequential mini-steps per sweep; in each,
 // every link cell (LC) tries to swap its site at the mini-step's offset with
@@ -9,28 +9,32 @@
 // group, the trials of one x-row of LCs (a "column", fixed (cy, cz)) read and
 // write only that row's neighbourhood: rows y0-2..y0+2, z0-2..z0+2 of the two
 // sublattices, where y0 = cy*Ly + dy, z0 = cz*Lz + dz.  Distinct columns of a
-// group touch disjoint rows, so a column's Lx mini-steps run inside one CTA
-// in lock-step with only CTA-level barriers, on a copy of those rows in
-// shared memory.  Columns are grouped into rectangular tiles; a tile may start
-// group G only after its 8 neighbouring tiles have finished group G-1
-// (per-tile progress flags in global memory, bounded waits).  Trials in the
-// same mini-step are independent, and a column's dependencies reach only the
-// adjacent columns, so this reproduces the sequential mini-step order exactly.
+// group touch disjoint rows, so a column's Lx mini-steps run in lock-step on
+// a copy of those rows in shared memory.  Columns are grouped into
+// rectangular tiles; a tile may start group G only after its 8 neighbouring
+// tiles have finished group G - lag (per-tile progress flags in global
+// memory, bounded waits).  Trials in the same mini-step are independent, and
+// a column's dependencies reach only the adjacent columns, so this reproduces
+// the sequential mini-step order exactly.
 //
 // dE of a trial (a -> b) is the pair-model energy change written through the
 // first-neighbour histograms: with D_m[q] = V_m(s_b, q) - V_m(s_a, q),
 //   dE = sum_m [ sum_{j in N_m(a)\b} D_m[s_j] - sum_{j in N_m(b)\a} D_m[s_j] ],
-// which equals the Omega-reduced local-energy difference of Algorithm 1
-// lines 4-8 for pair site energies e_i = 1/2 sum_v V(s_i, s_{i+v}).
+// which equals the Omega-reduced local-energy difference of Algorithm 1 for
+// pair site energies e_i = 1/2 sum_v V(s_i, s_{i+v}).  Every kernel here
+// evaluates it in the exact fixed point of pair_fixed.cuh, so the sweep
+// kernels and the lock-step trace agree bit for bit.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
 #include <vector>
 
-#include "sweep_common.cuh"
+#include "pair_fixed.cuh"
 
 namespace smc {
+
+static_assert(kPairQWords == kQRows * kMaxQRowWords, "table size");
 
 // Slot of row y0 + delta inside a window [lo, lo + W) along an axis of n cells.
 // For n >= W the window rows are distinct and slot = delta - lo; otherwise the
@@ -82,15 +86,29 @@ struct ColView {
     }
 };
 
-// dE of swapping the trial site a (own sublattice, x) with its partner in
-// direction `dir` (bits kx, ky, kz -> vector 2k-1 in half units).
-// Returns the species A, B and the partner's coordinates through pointers.
-template <bool IS_INT, class View>
-__device__ __forceinline__ typename Acc<IS_INT>::T trial_dE(const View &cv, int x, int nx, int s_off,
-                                                            int dir, int nshells, int S, const void *Dtab,
-                                                            int &A, int &B, int &ex, int &ey, int &ez)
+// Histogram words of one shell (SW words of four 8-bit fields).
+template <int SW>
+__device__ __forceinline__ void hadd(uint32_t (&h)[SW], uint32_t v8)
 {
-    using T = typename Acc<IS_INT>::T;
+    h[0] += nib8(v8);
+    if constexpr (SW == 2) h[1] += nib8hi(v8);
+}
+template <int SW>
+__device__ __forceinline__ void hsub(uint32_t (&h)[SW], uint32_t v8)
+{
+    h[0] -= nib8(v8);
+    if constexpr (SW == 2) h[1] -= nib8hi(v8);
+}
+
+// dE_fix of swapping the trial site a (own sublattice, x) with its partner
+// in direction `dir` (bits kx, ky, kz -> vector 2k-1 in half units), from raw
+// species read through a view.  Returns the species A, B and the partner's
+// offsets through references.
+template <int NSH, int SW, class View>
+__device__ __forceinline__ int32_t trial_dE_hist(const View &cv, int x, int nx, int s_off, int dir,
+                                                 const uint32_t *qt, int qrow, int &A, int &B, int &ex, int &ey,
+                                                 int &ez)
+{
     const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
     ex = kx + s_off;
     ey = ky + s_off;
@@ -100,16 +118,19 @@ __device__ __forceinline__ typename Acc<IS_INT>::T trial_dE(const View &cv, int 
     A = cv.O(0, 0)[x] & 7;
     const int bx = xo(ex);
     B = cv.T(ey, ez)[bx] & 7;
-    if (A == B) return T(0);
-    const T *D = (const T *)Dtab;
-    const T *D1 = D + ((0 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
-    T dE = T(0);
+    if (A == B) return 0;
+    auto sp = [](const unsigned char *row, int xx) { return (uint32_t)(row[xx] & 7) << 3; };
+    uint32_t H[NSH][SW];
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int w = 0; w < SW; ++w) H[m][w] = m < 2 ? 0x08080808u : 0x10101010u;
     // shell 1 of a (partner sublattice), all but b
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
         if (u == dir) continue;
         const int fx = ((u >> 2) & 1) + s_off, fy = ((u >> 1) & 1) + s_off, fz = (u & 1) + s_off;
-        dE += D1[cv.T(fy, fz)[xo(fx)] & 7];
+        hadd<SW>(H[0], sp(cv.T(fy, fz), xo(fx)));
     }
     // shell 1 of b (trial sublattice), all but a
     const int sb = -1 - s_off;
@@ -118,32 +139,38 @@ __device__ __forceinline__ typename Acc<IS_INT>::T trial_dE(const View &cv, int 
     for (int u = 0; u < 8; ++u) {
         if (u == nd) continue;
         const int gx = ex + ((u >> 2) & 1) + sb, gy = ey + ((u >> 1) & 1) + sb, gz = ez + (u & 1) + sb;
-        dE -= D1[cv.O(gy, gz)[xo(gx)] & 7];
+        hsub<SW>(H[0], sp(cv.O(gy, gz), xo(gx)));
     }
-    if (nshells >= 2) {
-        const T *D2 = D + ((1 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+    {
         const unsigned char *o00 = cv.O(0, 0);
-        dE += D2[o00[xm1] & 7] + D2[o00[xp1] & 7] + D2[cv.O(-1, 0)[x] & 7] + D2[cv.O(1, 0)[x] & 7] +
-              D2[cv.O(0, -1)[x] & 7] + D2[cv.O(0, 1)[x] & 7];
+        hadd<SW>(H[1], sp(o00, xm1));
+        hadd<SW>(H[1], sp(o00, xp1));
+        hadd<SW>(H[1], sp(cv.O(-1, 0), x));
+        hadd<SW>(H[1], sp(cv.O(1, 0), x));
+        hadd<SW>(H[1], sp(cv.O(0, -1), x));
+        hadd<SW>(H[1], sp(cv.O(0, 1), x));
         const unsigned char *tb = cv.T(ey, ez);
-        dE -= D2[tb[xo(ex - 1)] & 7] + D2[tb[xo(ex + 1)] & 7] + D2[cv.T(ey - 1, ez)[bx] & 7] +
-              D2[cv.T(ey + 1, ez)[bx] & 7] + D2[cv.T(ey, ez - 1)[bx] & 7] + D2[cv.T(ey, ez + 1)[bx] & 7];
+        hsub<SW>(H[1], sp(tb, xo(ex - 1)));
+        hsub<SW>(H[1], sp(tb, xo(ex + 1)));
+        hsub<SW>(H[1], sp(cv.T(ey - 1, ez), bx));
+        hsub<SW>(H[1], sp(cv.T(ey + 1, ez), bx));
+        hsub<SW>(H[1], sp(cv.T(ey, ez - 1), bx));
+        hsub<SW>(H[1], sp(cv.T(ey, ez + 1), bx));
     }
-    if (nshells >= 3) {
-        const T *D3 = D + ((2 * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
+    if constexpr (NSH >= 3) {
 #pragma unroll
         for (int p = -1; p <= 1; p += 2)
 #pragma unroll
             for (int q = -1; q <= 1; q += 2) {
-                dE += D3[cv.O(p, q)[x] & 7];           // (0, +-1, +-1)
-                dE += D3[cv.O(p, 0)[xo(q)] & 7];       // (+-1, +-1, 0)
-                dE += D3[cv.O(0, p)[xo(q)] & 7];       // (+-1, 0, +-1)
-                dE -= D3[cv.T(ey + p, ez + q)[bx] & 7];
-                dE -= D3[cv.T(ey + p, ez)[xo(ex + q)] & 7];
-                dE -= D3[cv.T(ey, ez + p)[xo(ex + q)] & 7];
+                hadd<SW>(H[2], sp(cv.O(p, q), x));      // (0, +-1, +-1)
+                hadd<SW>(H[2], sp(cv.O(p, 0), xo(q)));  // (+-1, +-1, 0)
+                hadd<SW>(H[2], sp(cv.O(0, p), xo(q)));  // (+-1, 0, +-1)
+                hsub<SW>(H[2], sp(cv.T(ey + p, ez + q), bx));
+                hsub<SW>(H[2], sp(cv.T(ey + p, ez), xo(ex + q)));
+                hsub<SW>(H[2], sp(cv.T(ey, ez + p), xo(ex + q)));
             }
     }
-    return dE;
+    return dot_fixed<NSH, SW>(H, qt + (A * 8 + B) * qrow);
 }
 
 // Waits until the 8 neighbouring tiles of (ty, tz) have completed `need`
@@ -183,26 +210,24 @@ __device__ bool wait_tile(const SweepParams &P, const RepDesc &D, int ty, int tz
     return *s_stop == 0;
 }
 
-template <bool IS_INT>
+// General path: any lattice (link-cell edges 4 or the whole axis).  A CTA
+// owns tiles of columns, stages CB columns' rows into shared memory at a
+// time and runs their mini-steps with CTA barriers between them.  Species
+// are read raw (this path does not use the scaled storage of the fast path).
+template <bool IS_INT, int NSH, int SW>
 __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ SweepParams P)
 {
-    using T = typename Acc<IS_INT>::T;
     extern __shared__ __align__(16) unsigned char smem[];
     __shared__ int s_stop;
     __shared__ int s_last;
     const int tid = threadIdx.x, nthr = blockDim.x, lane = tid & 31, warp = tid >> 5, nwarp = nthr >> 5;
 
-    T *Dt = (T *)smem;
-    double *slot_e = (double *)(smem + kDEntries * 4);
+    uint32_t *Qt = (uint32_t *)smem;
+    double *slot_e = (double *)(smem + (size_t)kQRows * P.qrow * 4);
     long long *slot_n = (long long *)(slot_e + P.tpc * nwarp);
     unsigned char *colbuf = (unsigned char *)(slot_n + P.tpc * nwarp);
 
-    for (int i = tid; i < kDEntries; i += nthr) {
-        if constexpr (IS_INT)
-            Dt[i] = P.D.di[i];
-        else
-            Dt[i] = P.D.df[i];
-    }
+    for (int i = tid; i < kQRows * P.qrow; i += nthr) Qt[i] = P.qtab[i];
     for (int i = tid; i < P.tpc * nwarp; i += nthr) {
         slot_e[i] = 0.0;
         slot_n[i] = 0;
@@ -227,12 +252,12 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
                     aborted = true;
                     break;
                 }
-                float beta = 0.f;
+                float cx = 0.f;
                 int2 ti = make_int2(0, 0);
                 if constexpr (IS_INT)
                     ti = P.temp.tabinfo[P.beta_stride ? r * P.beta_stride + t : r];
                 else
-                    beta = P.temp.beta[P.beta_stride ? r * P.beta_stride + t : r];
+                    cx = P.temp.beta[P.beta_stride ? r * P.beta_stride + t : r];
 
                 const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
                 const int rowB = (nx + 15) & ~15;
@@ -245,9 +270,7 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
                 const int rows_own = oy0.cnt * oz0.cnt, rows_oth = ty0.cnt * tz0.cnt;
                 const int rows_col = rows_own + rows_oth;
                 const int col_bytes = rows_col * rowB;
-                T accE = T(0);
-                double accE_d = 0.0;
-                long long accN = 0;
+                long long accE = 0, accN = 0;
 
                 for (int cb = 0; cb < ncols; cb += P.CB) {
                     const int nc = min(P.CB, ncols - cb);
@@ -315,17 +338,14 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
                             const uint32_t s = (uint32_t)(((sub * nz + z0) * ny + y0) * nx + x);
                             const uint32_t w = site_word(P.seed, RD.rep, sweep, s);
                             int A, B, ex, ey, ez;
-                            const T dE = trial_dE<IS_INT, ColView>(cv, x, nx, s_off, (int)(w >> kRBits),
-                                                                   P.nshells, P.S, Dt, A, B, ex, ey, ez);
-                            if (metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti)) {
+                            const int32_t dE = trial_dE_hist<NSH, SW, ColView>(cv, x, nx, s_off, (int)(w >> kRBits),
+                                                                               Qt, P.qrow, A, B, ex, ey, ez);
+                            if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
                                 if (A != B) {
                                     cv.O(0, 0)[x] = (unsigned char)B;
                                     cv.T(ey, ez)[wrapc(x + ex, nx)] = (unsigned char)A;
                                 }
-                                if constexpr (IS_INT)
-                                    accE += dE;
-                                else
-                                    accE_d += (double)dE;
+                                accE += dE;
                                 accN += 1;
                             }
                         }
@@ -376,11 +396,7 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
                 }
 
                 // ---- per-tile accumulation (fixed order) and publication ----
-                double e_w;
-                if constexpr (IS_INT)
-                    e_w = (double)warp_sum<long long>((long long)accE);
-                else
-                    e_w = warp_sum<double>(accE_d);
+                const double e_w = (double)warp_sum<long long>(accE);
                 const long long n_w = warp_sum<long long>(accN);
                 if (lane == 0) {
                     slot_e[slotk * nwarp + warp] += e_w;
@@ -430,463 +446,670 @@ __global__ void __launch_bounds__(512) k_sweep_pair(const __grid_constant__ Swee
             se += __ldcg(P.part_e + RD.tile0 + k);
             sn += __ldcg(P.part_n + RD.tile0 + k);
         }
-        if (RD.e_acc) *RD.e_acc += se;
+        if (RD.e_acc) *RD.e_acc += se * P.escale;
         if (RD.n_acc) *RD.n_acc += sn;
     }
 }
 
 // ---------------------------------------------------------------------------
 // Fast path: every axis holds >= 2 four-cell link cells (Lx = Ly = Lz = 4).
-// One warp owns a tile of columns and runs it without CTA barriers: it waits
-// for its tile's neighbours, stages the column's rows in its own shared
-// memory, runs the 4 mini-steps of the group (lane i handles link cells
-// i, i+32, ...), writes back the 5 rows the group may change and publishes
-// its progress.  Philox is evaluated once per link cell and group: the four
-// trial sites of a link cell's x-row, x = 4i .. 4i+3, share the counter
-// s >> 2 and use its four output words.
+// One warp owns tiles of columns and runs them without CTA barriers: for
+// each column it waits for the tile's neighbours, stages the column's rows
+// in its own shared memory, runs the 4 mini-steps of the group (lane i
+// handles link cells i, i+32, ...), writes back the 5 rows the group may
+// change and, after the tile's last column, publishes its progress.
 //
-// Shared-memory rows of a column (stride rb = padded nx + 32): the row body
-// starts 16 bytes in and is framed by a 4-byte periodic halo on each side,
-// so x-2 .. x+2 need no wrap.  Trial-sublattice rows (dy, dz) in [-1, 1]^2
-// are at index (dz+1)*3 + (dy+1); partner-sublattice rows (sy, sz) in
-// [0, 4)^2, i.e. (dy, dz) = (s_off-1+sy, s_off-1+sz), at 9 + sz*4 + sy.
-// Two-shell models never read the four partner corner rows (not loaded).
-// A neighbour of species q adds 1 << (4q) to a histogram of 4-bit counts.
+// Staging is one bulk copy per row (cp.async.bulk, completing on an
+// mbarrier), and a warp keeps two column buffers: while it runs the trials
+// of one column, the rows of the next are in flight.  The next column is
+// fetched early only when that cannot read stale rows: a column of the same
+// tile and group (distinct columns of a group touch disjoint rows), or a
+// column of another tile whose neighbours have already published the group
+// it needs.  Philox runs once per link cell and group: the four trial sites
+// of a link cell's x-row, x = 4i .. 4i+3, share the counter s >> 2.
 //
-// dE through the histograms: with c_m[q] = #{j in N_m(a)\b: s_j = q} -
-// #{j in N_m(b)\a: s_j = q} and D_m[q] = V_m(s_b, q) - V_m(s_a, q),
-// dE = sum_m sum_q c_m[q] D_m[q].  For shells 1 and 2, c + 8 lies in [1, 15]
-// and one biased word holds all of c_m; shell 3 keeps the two counts apart.
+// During a launch every species byte holds 8 s (the shift of its histogram
+// field; a pass before and after the launch converts), so a neighbour adds
+// nib8(byte) to its shell's word.
+//
+// Shared-memory rows of a column (stride rb): the row body starts 16 bytes
+// in and is framed by a 4-byte periodic halo on each side, so x-2 .. x+2
+// need no wrap.  Trial-sublattice rows (dy, dz) in [-1, 1]^2 are at index
+// (dz+1)*3 + (dy+1); partner-sublattice rows (sy, sz) in [0, 4)^2, i.e.
+// (dy, dz) = (s_off-1+sy, s_off-1+sz), at pslot(sy, sz).  Two-shell models
+// never read the four partner corner rows (not loaded).
 // ---------------------------------------------------------------------------
-// Sum over the first S-1 species only: every shell holds the same number of
-// neighbours of a (without b) as of b (without a), so sum_q c[q] = 0 and
-// c[S-1] = -sum_{q<S-1} c[q].  The kernel's table row for (m, A, B) holds
-// D'[q] = D[q] - D[S-1] for q < S-1 and, in entry 7, -8 sum_q D'[q] (the
-// 4-bit fields of shells 1 and 2 carry a bias of 8).
-// In shared memory the fast kernel keeps the table rows (m, A, B) of its
-// species template ST compactly, RS = fast_rs(ST) words each: D'[0..ST-2],
-// then the bias.  An odd stride for ST = 2 and 5 sends the rows of the up
-// to 25 (A, B) pairs a warp reads at once to distinct banks.
-__host__ __device__ constexpr int fast_rs(int ST) { return ST == 8 ? 8 : (ST | 1); }
-__host__ __device__ constexpr int fast_d_bytes(int NSH, int ST)
-{
-    return ((NSH >= 3 ? 3 : 2) * ST * ST * fast_rs(ST) * 4 + 15) / 16 * 16;
-}
-
-template <bool IS_INT, int S>
-__device__ __forceinline__ typename Acc<IS_INT>::T dot_biased(uint32_t H, const typename Acc<IS_INT>::T *D)
-{
-    using T = typename Acc<IS_INT>::T;
-    T acc = D[S - 1];
-#pragma unroll
-    for (int q = 0; q < S - 1; ++q) {
-        const int f = (int)((H >> (4 * q)) & 15u);
-        if constexpr (IS_INT)
-            acc += f * D[q];
-        else
-            acc = fmaf((float)f, D[q], acc);
-    }
-    return acc;
-}
-
-template <bool IS_INT, int S>
-__device__ __forceinline__ typename Acc<IS_INT>::T dot_diff(uint32_t Ha, uint32_t Hb, const typename Acc<IS_INT>::T *D)
-{
-    using T = typename Acc<IS_INT>::T;
-    T acc = T(0);
-#pragma unroll
-    for (int q = 0; q < S - 1; ++q) {
-        const int f = (int)((Ha >> (4 * q)) & 15u) - (int)((Hb >> (4 * q)) & 15u);
-        if constexpr (IS_INT)
-            acc += f * D[q];
-        else
-            acc = fmaf((float)f, D[q], acc);
-    }
-    return acc;
-}
-
-#define NIB(v) (1u << ((v) << 2))
-
-// po: byte offsets (in g_smem) of the 9 trial-sublattice row bodies; pt: of
-// the partner block (row index 0).  Returns dE; A, B and the partner's
-// row offset and x through references.
-// Shared-memory row index of partner-sublattice slot (sy, sz).  Two-shell
-// models store the 12 slots they can read (the 4x4 window without its
-// corners) compactly; three-shell models store all 16.
 template <int NSH>
-__host__ __device__ __forceinline__ int pslot(int sy, int sz)
+__host__ __device__ __forceinline__ constexpr int pslot(int sy, int sz)
 {
-    if (NSH >= 3) return 9 + sz * 4 + sy;
-    return 9 + (sz == 0 ? sy - 1 : (sz == 1 ? 2 + sy : (sz == 2 ? 6 + sy : 9 + sy)));
+    return NSH >= 3 ? 9 + sz * 4 + sy : 9 + (sz == 0 ? sy - 1 : (sz == 1 ? 2 + sy : (sz == 2 ? 6 + sy : 9 + sy)));
+}
+template <int NSH>
+__host__ __device__ constexpr int fast_nrows()
+{
+    return NSH >= 3 ? 25 : 21;
 }
 
-// po: byte offsets (in g_smem) of the 9 trial-sublattice row bodies; col0:
-// offset of row 0's body.  Returns dE (exactly 0 when a and b hold the same
-// species: the table rows D'(A, A) vanish); A, B and the partner's row
-// offset and x through references.
-template <bool IS_INT, int NSH, int S, int SOFF>
-__device__ __forceinline__ typename Acc<IS_INT>::T fast_dE(const uint32_t *po, uint32_t col0, uint32_t rb, int x,
-                                                           int dir, uint32_t dt, int &A, int &B, uint32_t &brow,
-                                                           int &xb)
+#define LD8(off) ((uint32_t)g_smem[(off)])
+
+__device__ __forceinline__ void mbar_init(uint32_t a, uint32_t count)
 {
-    using T = typename Acc<IS_INT>::T;
-    const int kx = (dir >> 2) & 1, ky = (dir >> 1) & 1, kz = dir & 1;
-    A = (int)(SM8(po[4] + x) & 7u);
-    // partner's row: slot (ky+1, kz+1) = 12 + 4 kz + ky (two shells) or 14 + 4 kz + ky
-    const uint32_t rbp = col0 + (uint32_t)((NSH >= 3 ? 14 : 12) + 4 * kz + ky) * rb;
-    xb = x + SOFF + kx;
-    B = (int)(SM8(rbp + xb) & 7u);
-    brow = rbp;
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(a), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t a, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(a), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t a, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes, uint32_t mbar)
+{
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+                 "l"(src), "r"(bytes), "r"(mbar)
+                 : "memory");
+}
+
+// Bounded wait for a buffer's bulk copies (parity of the phase to complete).
+// Every copy waited for was issued by this warp, so the wait ends unless the
+// hardware fails; past the time limit the status word and the abort flag are
+// set.
+__device__ __forceinline__ bool mbar_wait(const SweepParams &P, uint32_t a, uint32_t parity)
+{
+    if (mbar_try_wait(a, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        if (mbar_try_wait(a, parity)) return true;
+        if ((long long)(global_ns() - t0) > P.timeout_ns) {
+            atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+            atomicExch(P.abort_flag, 1);
+            return false;
+        }
+    }
+}
+
+// One non-blocking look at the 8 neighbouring tiles' progress.
+__device__ __forceinline__ bool deps_ready(const SweepParams &P, const RepDesc &D, int ty, int tz, uint32_t need,
+                                           int lane)
+{
+    bool ok = true;
+    if (lane < 9 && lane != 4) {
+        int nty = ty + (lane % 3) - 1, ntz = tz + (lane / 3) - 1;
+        nty = nty < 0 ? nty + D.NTy : (nty >= D.NTy ? nty - D.NTy : nty);
+        ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
+        ok = ld_acquire_u32(P.flags + D.tile0 + ntz * D.NTy + nty) >= need;
+    }
+    return __all_sync(0xffffffffu, ok);
+}
+
+// Row r of a column: sublattice (relative: 0 own, 1 partner) and offsets.
+template <int NSH>
+__device__ __forceinline__ void fast_row(int r, int soff, int &part, int &dy, int &dz)
+{
+    if (r < 9) {
+        dy = r % 3 - 1;
+        dz = r / 3 - 1;
+        part = 0;
+    } else {
+        const int k = r - 9;
+        int sy, sz;
+        if (NSH >= 3) {
+            sy = k & 3;
+            sz = k >> 2;
+        } else {
+            sz = k < 2 ? 0 : (k < 6 ? 1 : (k < 10 ? 2 : 3));
+            sy = k < 2 ? k + 1 : (k < 6 ? k - 2 : (k < 10 ? k - 6 : k - 9));
+        }
+        dy = sy - 1 + soff;
+        dz = sz - 1 + soff;
+        part = 1;
+    }
+}
+
+// Geometry of a work item (sweep t of the launch, group g, tile, column c).
+struct FastGeo {
+    int r, ty, tz, j, l, y0, z0, dy, dz, sub, soff, ncols, nj;
+    uint32_t gstep, need;
+};
+
+__device__ __forceinline__ FastGeo fast_geo(const SweepParams &P, int t, int g, int tile, int c)
+{
+    FastGeo q;
+    int r = 0;
+    while (r + 1 < P.R && P.rep[r + 1].tile0 <= tile) ++r;
+    const RepDesc &RD = P.rep[r];
+    q.r = r;
+    const int lt = tile - RD.tile0;
+    q.ty = lt % RD.NTy;
+    q.tz = lt / RD.NTy;
+    const int j0 = q.ty * P.TY, j1 = min(j0 + P.TY, RD.NLy);
+    const int l0 = q.tz * P.TZ, l1 = min(l0 + P.TZ, RD.NLz);
+    q.nj = j1 - j0;
+    q.ncols = q.nj * (l1 - l0);
+    q.j = j0 + c % q.nj;
+    q.l = l0 + c / q.nj;
+    q.dy = g & 3;
+    q.dz = (g >> 2) & 3;
+    q.sub = g >> 4;
+    q.soff = q.sub == 0 ? -1 : 0;
+    q.y0 = 4 * q.j + q.dy;
+    q.z0 = 4 * q.l + q.dz;
+    q.gstep = (uint32_t)(t * P.G + g);
+    const int lagv = P.lag[g];
+    q.need = q.gstep + 1 >= (uint32_t)lagv ? q.gstep + 1 - lagv : 0;
+    return q;
+}
+
+// Stages the rows of column geometry q into the buffer at g_smem offset buf.
+// Rows of a multiple of 16 bytes, 16-byte aligned: mode 0, one cp.async.bulk
+// per row, completing on mbarrier `mbar` (absolute shared address); mode 1,
+// 16-byte cp.async per lane in one commit group (the issuing warp waits with
+// cp.async.wait_group).  Otherwise the warp copies 4-byte words and returns
+// with the rows in place.
+template <int NSH>
+__device__ __forceinline__ void fast_stage(const RepDesc &RD, const FastGeo &q, uint32_t smem0, uint32_t buf,
+                                           uint32_t rb, uint32_t mbar, int lane, int mode)
+{
+    constexpr int NROWS = fast_nrows<NSH>();
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz;
+    const int8_t *src = RD.occ;
+    if (lane < NROWS) {
+        int part, dy, dz;
+        fast_row<NSH>(lane, q.soff, part, dy, dz);
+        const int gsub = part ? 1 - q.sub : q.sub;
+        const int gy = wrapc(q.y0 + dy, ny), gz = wrapc(q.z0 + dz, nz);
+        src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
+    }
+    if (RD.vec && mode == 0) {
+        // order this warp's earlier generic accesses of the buffer, and the
+        // rows other warps published (seen through the acquire loads), before
+        // the async-proxy copies
+        __syncwarp();
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_expect_tx(mbar, (uint32_t)(NROWS * nx));
+        __syncwarp();
+        if (lane < NROWS) bulk_g2s(smem0 + buf + (uint32_t)lane * rb + 16, src, (uint32_t)nx, mbar);
+    } else if (RD.vec) {
+        // 16-byte cp.async (L2 only: never a stale L1 line), one commit group
+        const int cpr = nx >> 4;
+        int lr = 0, lc = lane, rstep = 1, cstep = 32;
+        if (cpr < 32) {
+            rstep = 32 / cpr;
+            lr = lane / cpr;
+            lc = lane - lr * cpr;
+            cstep = cpr;
+        }
+        for (int it = 0; it < (NROWS + rstep - 1) / rstep; ++it) {
+            const int rr = lr + it * rstep;
+            const int rsel = rr < NROWS ? rr : 0;
+            const int8_t *s = (const int8_t *)__shfl_sync(0xffffffffu, (unsigned long long)src, rsel);
+            if (lr < rstep && rr < NROWS) {
+                const uint32_t d = smem0 + buf + (uint32_t)rr * rb + 16;
+                for (int c = lc; c < cpr; c += cstep)
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 16 * c), "l"(s + 16 * c)
+                                 : "memory");
+            }
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    } else {
+        const int cpr = nx >> 2;
+        int lr = 0, lc = lane, rstep = 1, cstep = 32;
+        if (cpr < 32) {
+            rstep = 32 / cpr;
+            lr = lane / cpr;
+            lc = lane - lr * cpr;
+            cstep = cpr;
+        }
+        for (int it = 0; it < (NROWS + rstep - 1) / rstep; ++it) {
+            const int rr = lr + it * rstep;
+            const int rsel = rr < NROWS ? rr : 0;
+            const unsigned *s4 = (const unsigned *)__shfl_sync(0xffffffffu, (unsigned long long)src, rsel);
+            if (lr < rstep && rr < NROWS) {
+                unsigned *d4 = (unsigned *)(g_smem + buf + (uint32_t)rr * rb + 16);
+                for (int c = lc; c < cpr; c += cstep) d4[c] = __ldcg(s4 + c);
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// dE_fix of the trial at a = own row (0, 0), x, with ya = row-0 body + x and
+// pa = ya + s_off, partner direction dir; the species a8, b8 (x 8) and b's
+// shared-memory offset through references.
+template <int NSH, int SW, int RB>
+__device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rbr, uint32_t dir, uint32_t lut,
+                                           uint32_t qt, uint32_t &a8, uint32_t &b8, uint32_t &pb)
+{
+    const uint32_t rb = RB ? (uint32_t)RB : rbr;
+    constexpr uint32_t S11 = pslot<NSH>(1, 1), S21 = pslot<NSH>(2, 1), S12 = pslot<NSH>(1, 2), S22 = pslot<NSH>(2, 2);
+    const int4 L = *(const int4 *)(g_smem + lut + dir * 16u);
+    a8 = LD8(ya + 4 * rb);
+    pb = pa + (uint32_t)L.x;
+    b8 = LD8(pb);
+    uint32_t H[NSH][SW];
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int w = 0; w < SW; ++w) H[m][w] = m < 2 ? 0x08080808u : 0x10101010u;
     // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
-    // trial-sublattice neighbours plus a.  A species >= 8 (invalid input)
-    // shifts the 1 out of the word and is ignored.
-    uint32_t H1 = 0x88888888u - NIB(B) + NIB(A);
-    {
-        const uint32_t xa = col0 + x + SOFF;
-        const uint32_t r11 = xa + pslot<NSH>(1, 1) * rb, r21 = xa + pslot<NSH>(2, 1) * rb;
-        const uint32_t r12 = xa + pslot<NSH>(1, 2) * rb, r22 = xa + pslot<NSH>(2, 2) * rb;
-        H1 += NIB(SM8(r11)) + NIB(SM8(r11 + 1)) + NIB(SM8(r21)) + NIB(SM8(r21 + 1)) + NIB(SM8(r12)) +
-              NIB(SM8(r12 + 1)) + NIB(SM8(r22)) + NIB(SM8(r22 + 1));
-        const uint32_t ob = po[0] + (uint32_t)(kz * 3 + ky) * rb + x + kx - 1;
-        H1 -= NIB(SM8(ob)) + NIB(SM8(ob + 1)) + NIB(SM8(ob + rb)) + NIB(SM8(ob + rb + 1)) + NIB(SM8(ob + 3 * rb)) +
-              NIB(SM8(ob + 3 * rb + 1)) + NIB(SM8(ob + 4 * rb)) + NIB(SM8(ob + 4 * rb + 1));
+    // trial-sublattice neighbours plus a
+    hadd<SW>(H[0], a8);
+    hsub<SW>(H[0], b8);
+    hadd<SW>(H[0], LD8(pa + S11 * rb));
+    hadd<SW>(H[0], LD8(pa + S11 * rb + 1));
+    hadd<SW>(H[0], LD8(pa + S21 * rb));
+    hadd<SW>(H[0], LD8(pa + S21 * rb + 1));
+    hadd<SW>(H[0], LD8(pa + S12 * rb));
+    hadd<SW>(H[0], LD8(pa + S12 * rb + 1));
+    hadd<SW>(H[0], LD8(pa + S22 * rb));
+    hadd<SW>(H[0], LD8(pa + S22 * rb + 1));
+    const uint32_t ob = ya + (uint32_t)L.y;
+    hsub<SW>(H[0], LD8(ob));
+    hsub<SW>(H[0], LD8(ob + 1));
+    hsub<SW>(H[0], LD8(ob + rb));
+    hsub<SW>(H[0], LD8(ob + rb + 1));
+    hsub<SW>(H[0], LD8(ob + 3 * rb));
+    hsub<SW>(H[0], LD8(ob + 3 * rb + 1));
+    hsub<SW>(H[0], LD8(ob + 4 * rb));
+    hsub<SW>(H[0], LD8(ob + 4 * rb + 1));
+    // shell 2: a's 6 trial-sublattice neighbours, b's 6 partner-sublattice ones
+    hadd<SW>(H[1], LD8(ya + 4 * rb - 1));
+    hadd<SW>(H[1], LD8(ya + 4 * rb + 1));
+    hadd<SW>(H[1], LD8(ya + 3 * rb));
+    hadd<SW>(H[1], LD8(ya + 5 * rb));
+    hadd<SW>(H[1], LD8(ya + rb));
+    hadd<SW>(H[1], LD8(ya + 7 * rb));
+    hsub<SW>(H[1], LD8(pb - 1));
+    hsub<SW>(H[1], LD8(pb + 1));
+    hsub<SW>(H[1], LD8(pb - rb));
+    hsub<SW>(H[1], LD8(pb + rb));
+    hsub<SW>(H[1], LD8(pb - (uint32_t)L.z));
+    hsub<SW>(H[1], LD8(pb + (uint32_t)L.w));
+    if constexpr (NSH >= 3) {
+        hadd<SW>(H[2], LD8(ya));
+        hadd<SW>(H[2], LD8(ya + 2 * rb));
+        hadd<SW>(H[2], LD8(ya + 6 * rb));
+        hadd<SW>(H[2], LD8(ya + 8 * rb));
+        hadd<SW>(H[2], LD8(ya + 3 * rb - 1));
+        hadd<SW>(H[2], LD8(ya + 3 * rb + 1));
+        hadd<SW>(H[2], LD8(ya + 5 * rb - 1));
+        hadd<SW>(H[2], LD8(ya + 5 * rb + 1));
+        hadd<SW>(H[2], LD8(ya + rb - 1));
+        hadd<SW>(H[2], LD8(ya + rb + 1));
+        hadd<SW>(H[2], LD8(ya + 7 * rb - 1));
+        hadd<SW>(H[2], LD8(ya + 7 * rb + 1));
+        hsub<SW>(H[2], LD8(pb - 5 * rb));
+        hsub<SW>(H[2], LD8(pb - 3 * rb));
+        hsub<SW>(H[2], LD8(pb + 3 * rb));
+        hsub<SW>(H[2], LD8(pb + 5 * rb));
+        hsub<SW>(H[2], LD8(pb - rb - 1));
+        hsub<SW>(H[2], LD8(pb - rb + 1));
+        hsub<SW>(H[2], LD8(pb + rb - 1));
+        hsub<SW>(H[2], LD8(pb + rb + 1));
+        hsub<SW>(H[2], LD8(pb - 4 * rb - 1));
+        hsub<SW>(H[2], LD8(pb - 4 * rb + 1));
+        hsub<SW>(H[2], LD8(pb + 4 * rb - 1));
+        hsub<SW>(H[2], LD8(pb + 4 * rb + 1));
     }
-    constexpr int RS = fast_rs(S), SH = S * S * RS;
-    const T *Dt = (const T *)(g_smem + dt);
-    const T *D1 = Dt + (A * S + B) * RS;
-    T dE = dot_biased<IS_INT, S>(H1, D1);
-    const uint32_t bx = rbp + xb;
-    // partner rows one slot down / up in z (compact layout: 3 or 4 rows apart)
-    const uint32_t zdn = NSH >= 3 ? 4 * rb : 3 * rb + (uint32_t)kz * rb;
-    const uint32_t zup = NSH >= 3 ? 4 * rb : 4 * rb - (uint32_t)kz * rb;
-    if (NSH >= 2) {
-        const uint32_t ax = po[4] + x;
-        uint32_t H2 = 0x88888888u;
-        H2 += NIB(SM8(ax - 1)) + NIB(SM8(ax + 1)) + NIB(SM8(po[3] + x)) + NIB(SM8(po[5] + x)) + NIB(SM8(po[1] + x)) +
-              NIB(SM8(po[7] + x));
-        H2 -= NIB(SM8(bx - 1)) + NIB(SM8(bx + 1)) + NIB(SM8(bx - rb)) + NIB(SM8(bx + rb)) + NIB(SM8(bx - zdn)) +
-              NIB(SM8(bx + zup));
-        dE += dot_biased<IS_INT, S>(H2, D1 + SH);
-    }
-    if (NSH >= 3) {
-        const uint32_t Ha = NIB(SM8(po[0] + x)) + NIB(SM8(po[2] + x)) + NIB(SM8(po[6] + x)) + NIB(SM8(po[8] + x)) +
-                            NIB(SM8(po[3] + x - 1)) + NIB(SM8(po[3] + x + 1)) + NIB(SM8(po[5] + x - 1)) +
-                            NIB(SM8(po[5] + x + 1)) + NIB(SM8(po[1] + x - 1)) + NIB(SM8(po[1] + x + 1)) +
-                            NIB(SM8(po[7] + x - 1)) + NIB(SM8(po[7] + x + 1));
-        const uint32_t Hb = NIB(SM8(bx - 5 * rb)) + NIB(SM8(bx - 3 * rb)) + NIB(SM8(bx + 3 * rb)) +
-                            NIB(SM8(bx + 5 * rb)) + NIB(SM8(bx - rb - 1)) + NIB(SM8(bx - rb + 1)) +
-                            NIB(SM8(bx + rb - 1)) + NIB(SM8(bx + rb + 1)) + NIB(SM8(bx - 4 * rb - 1)) +
-                            NIB(SM8(bx - 4 * rb + 1)) + NIB(SM8(bx + 4 * rb - 1)) + NIB(SM8(bx + 4 * rb + 1));
-        dE += dot_diff<IS_INT, S>(Ha, Hb, D1 + 2 * SH);
-    }
-    return dE;
+    constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
+    const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
+    return dot_fixed<NSH, SW>(H, row);
 }
-#undef NIB
 
-template <bool IS_INT, int NSH, int S, int SOFF, int KU, bool GUARD>
-__device__ __forceinline__ void fast_trials(const SweepParams &P, const uint32_t *po, uint32_t col0, uint32_t rb,
-                                            const uint32_t *wsm, int k0, int nk, int NLx, int nx, int dx, int lane,
-                                            float beta, int2 ti, uint32_t dt, typename Acc<IS_INT>::T &colE,
+// Team synchronisation: the tw warps that share a column meet at named
+// barrier tb (1 + team index in the CTA); one warp needs only __syncwarp.
+// team_and also returns the AND of the threads' predicates.
+__device__ __forceinline__ void team_sync(int tw, int tb)
+{
+    if (tw == 1)
+        __syncwarp();
+    else
+        asm volatile("bar.sync %0, %1;" ::"r"(tb), "r"(tw * 32) : "memory");
+}
+__device__ __forceinline__ bool team_and(int tw, int tb, bool p)
+{
+    if (tw == 1) return __all_sync(0xffffffffu, p);
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred q, d;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "bar.red.and.pred d, %2, %3, q;\n\t"
+        "selp.u32 %0, 1, 0, d;\n\t}"
+        : "=r"(r)
+        : "r"((uint32_t)p), "r"(tb), "r"(tw * 32)
+        : "memory");
+    return r != 0;
+}
+
+// KU trials of mini-step dx per lane: link cells i = ib + is * (k0 + u),
+// u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).
+template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD>
+__device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body, int soff, uint32_t rbr,
+                                            uint32_t wsm, int k0, int nk, int ib, int is, int NLx, int nx, int dx,
+                                            int lane, float cx, int2 ti, uint32_t lut, uint32_t qt, long long &accE,
                                             long long &accN)
 {
-    using T = typename Acc<IS_INT>::T;
-    T dE[KU];
-    int A[KU], B[KU], xb[KU], xs[KU];
-    uint32_t brow[KU];
+    const uint32_t rb = RB ? (uint32_t)RB : rbr;
+    int32_t dE[KU];
+    uint32_t a8[KU], b8[KU], pb[KU], ya[KU];
     bool acc[KU];
 #pragma unroll
     for (int u = 0; u < KU; ++u) {
-        const int k = k0 + u, i = lane + 32 * k;
+        const int k = k0 + u, i = ib + is * k;
         acc[u] = false;
         if (!GUARD || (k < nk && i < NLx)) {
             const int x = 4 * i + dx;
-            xs[u] = x;
-            const uint32_t w = wsm[(k * 4 + dx) * 32 + lane];
-            dE[u] = fast_dE<IS_INT, NSH, S, SOFF>(po, col0, rb, x, (int)(w >> kRBits), dt, A[u], B[u], brow[u], xb[u]);
-            acc[u] = metropolis<IS_INT>(dE[u], w & kRMask, beta, P.tab, ti);
+            ya[u] = body + (uint32_t)x;
+            const uint32_t w = *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
+            dE[u] = fast_dE<NSH, SW, RB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
+            acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
+            // b's store address wraps along x (the load may read a halo copy)
+            const int xb = x + soff + (int)(w >> 31);
+            pb[u] += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
         }
     }
 #pragma unroll
     for (int u = 0; u < KU; ++u) {
         if (acc[u]) {
-            halo_store(po[4], xs[u], nx, (unsigned char)B[u]);
-            halo_store(brow[u], xb[u], nx, (unsigned char)A[u]);
-            colE += dE[u];
+            g_smem[ya[u] + 4 * rb] = (unsigned char)b8[u];
+            g_smem[pb[u]] = (unsigned char)a8[u];
+            accE += dE[u];
             accN += 1;
         }
     }
 }
 
-template <bool IS_INT, int NSH, int S, int SOFF>
-__device__ __forceinline__ void fast_column(const SweepParams &P, const RepDesc &RD, uint32_t col, int y0, int z0,
-                                            uint64_t sweep, float beta, int2 ti, uint32_t dt, int lane,
-                                            typename Acc<IS_INT>::T &accE, double &accEd, long long &accN)
+// The fast kernel.  A team of tw warps (1, 2 or 4) shares one column at a
+// time: the team's first warp ("leader") polls the neighbours' progress,
+// issues the row copies into the team's two buffers and publishes the
+// tile's progress; every warp of the team runs its own link cells (lane +
+// 32 w + 32 tw k) and waits for the copies on the buffer's mbarrier.
+// Shared memory: [table][8 direction offsets][team regions: barriers, two
+// buffers][warp regions: accumulator slots, Philox words].
+template <bool IS_INT, int NSH, int SW, int RB>
+__global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ SweepParams P)
 {
-    using T = typename Acc<IS_INT>::T;
-    constexpr int sub = SOFF == -1 ? 0 : 1;
-    constexpr int rows = NSH >= 3 ? 25 : 21;
-    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
-    const uint32_t rb = (uint32_t)P.rowB;
-    const bool vec = RD.vec != 0;
-    // ---- per-row source (global) and destination (shared) of this column:
-    // lane r computes row r once; the others read it by shuffle ----
-    const int8_t *my_src = RD.occ;
-    uint32_t my_dst = 0;
-    if (lane < rows) {
-        int gsub, dy, dz;
-        if (lane < 9) {
-            dy = lane % 3 - 1;
-            dz = lane / 3 - 1;
-            gsub = sub;
-        } else {
-            const int k = lane - 9;
-            int sy, sz;
-            if (NSH >= 3) {
-                sy = k & 3;
-                sz = k >> 2;
-            } else {
-                sz = k < 2 ? 0 : (k < 6 ? 1 : (k < 10 ? 2 : 3));
-                sy = k < 2 ? k + 1 : (k < 6 ? k - 2 : (k < 10 ? k - 6 : k - 9));
-            }
-            dy = sy - 1 + SOFF;
-            dz = sz - 1 + SOFF;
-            gsub = 1 - sub;
-        }
-        const int gy = wrapc(y0 + dy, ny), gz = wrapc(z0 + dz, nz);
-        my_src = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
-        my_dst = col + (uint32_t)lane * rb + 16;
-    }
-    // ---- stage the rows (L2-only copies: never a stale L1 line) ----
-    {
-        const int cpr = vec ? (nx >> 4) : (nx >> 2);
-        int lr = 0, lc = lane, rstep = 1, cstep = 32;
-        if (cpr < 32) {
-            rstep = 32 / cpr;
-            lr = lane / cpr;
-            lc = lane - lr * cpr;
-            cstep = cpr;
-        }
-        const int iters = (rows + rstep - 1) / rstep;
-        const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
-        for (int it = 0; it < iters; ++it) {
-            const int rr = lr + it * rstep;
-            const int rsel = rr < rows ? rr : 0;
-            const int8_t *src = (const int8_t *)__shfl_sync(0xffffffffu, (unsigned long long)my_src, rsel);
-            const uint32_t dst = __shfl_sync(0xffffffffu, my_dst, rsel);
-            if (lr < rstep && rr < rows) {
-                if (vec) {
-                    for (int c = lc; c < cpr; c += cstep)
-                        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + dst + 16 * c),
-                                     "l"(src + 16 * c)
-                                     : "memory");
-                } else {
-                    const unsigned *s4 = (const unsigned *)src;
-                    unsigned *d4 = (unsigned *)(g_smem + dst);
-                    for (int c = lc; c < cpr; c += 4 * cstep) {
-                        const int c1 = c + cstep, c2 = c + 2 * cstep, c3 = c + 3 * cstep;
-                        const unsigned v0 = __ldcg(s4 + c);
-                        const unsigned v1 = c1 < cpr ? __ldcg(s4 + c1) : 0u;
-                        const unsigned v2 = c2 < cpr ? __ldcg(s4 + c2) : 0u;
-                        const unsigned v3 = c3 < cpr ? __ldcg(s4 + c3) : 0u;
-                        d4[c] = v0;
-                        if (c1 < cpr) d4[c1] = v1;
-                        if (c2 < cpr) d4[c2] = v2;
-                        if (c3 < cpr) d4[c3] = v3;
-                    }
-                }
-            }
-        }
-    }
-    // ---- Philox words of this lane's link cells, kept in shared memory
-    // (computed while the row copies are in flight) ----
-    uint32_t *wsm = (uint32_t *)(g_smem + col + (uint32_t)rows * rb + 16);  // [k][dx][lane]
-    const int nk = (NLx + 31) >> 5;
-    {
-        const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
-        const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-#pragma unroll 1
-        for (int k = 0; k < nk; ++k) {
-            const int i = lane + 32 * k;
-            if (i < NLx) {
-                const U4 w =
-                    philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
-                wsm[(k * 4 + 0) * 32 + lane] = w.x;
-                wsm[(k * 4 + 1) * 32 + lane] = w.y;
-                wsm[(k * 4 + 2) * 32 + lane] = w.z;
-                wsm[(k * 4 + 3) * 32 + lane] = w.w;
-            }
-        }
-    }
-    if (vec) asm volatile("cp.async.wait_all;" ::: "memory");
-    __syncwarp();
-    // periodic halos: 4 bytes before and after each row body
-    if (lane < rows) {
-        *(unsigned *)(g_smem + my_dst - 4) = *(const unsigned *)(g_smem + my_dst + nx - 4);
-        *(unsigned *)(g_smem + my_dst + nx) = *(const unsigned *)(g_smem + my_dst);
-    }
-    __syncwarp();
-    uint32_t po[9];
-#pragma unroll
-    for (int r = 0; r < 9; ++r) po[r] = col + (uint32_t)r * rb + 16;
-    const uint32_t col0 = col + 16;
-    // ---- the four mini-steps of the group ----
-    // accepted dE of this lane's trials in the column (at most nx / 8 of
-    // them), in the kernel's type; widened to FP64 once per column
-    T colE = T(0);
-#pragma unroll 1
-    for (int dx = 0; dx < 4; ++dx) {
-        if (NLx == 32 * nk && (nk & 3) == 0) {
-#pragma unroll 1
-            for (int kk = 0; kk < nk; kk += 4)
-                fast_trials<IS_INT, NSH, S, SOFF, 4, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                            dt, colE, accN);
-        } else if (NLx == 32 * nk) {
-#pragma unroll 1
-            for (int kk = 0; kk < nk; ++kk)
-                fast_trials<IS_INT, NSH, S, SOFF, 1, false>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                            dt, colE, accN);
-        } else {
-#pragma unroll 1
-            for (int kk = 0; kk < nk; ++kk)
-                fast_trials<IS_INT, NSH, S, SOFF, 1, true>(P, po, col0, rb, wsm, kk, nk, NLx, nx, dx, lane, beta, ti,
-                                                           dt, colE, accN);
-        }
-        __syncwarp();
-    }
-    if constexpr (IS_INT)
-        accE += colE;
-    else
-        accEd += (double)colE;
-    // ---- write back trial row (0,0) and partner rows (s_off..s_off+1)^2 ----
-    {
-        const int cpr = vec ? (nx >> 4) : (nx >> 2);
-        int lr = 0, lc = lane, rstep = 1, cstep = 32;
-        if (cpr < 32) {
-            rstep = 32 / cpr;
-            lr = lane / cpr;
-            lc = lane - lr * cpr;
-            cstep = cpr;
-        }
-        if (lr < rstep) {
-            for (int wr = lr; wr < 5; wr += rstep) {
-                int slot, gsub, gy, gz;
-                if (wr == 0) {
-                    slot = 4;
-                    gsub = sub;
-                    gy = y0;
-                    gz = z0;
-                } else {
-                    const int sy = 1 + ((wr - 1) & 1), sz = 1 + ((wr - 1) >> 1);
-                    slot = pslot<NSH>(sy, sz);
-                    gsub = 1 - sub;
-                    gy = wrapc(y0 + sy - 1 + SOFF, ny);
-                    gz = wrapc(z0 + sz - 1 + SOFF, nz);
-                }
-                int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
-                const unsigned char *srcs = g_smem + col + (uint32_t)slot * rb + 16;
-                if (vec) {
-                    for (int c = lc; c < cpr; c += cstep) *((int4 *)dstg + c) = *((const int4 *)srcs + c);
-                } else {
-                    for (int c = lc; c < cpr; c += cstep) *((unsigned *)dstg + c) = *((const unsigned *)srcs + c);
-                }
-            }
-        }
-    }
-    __syncwarp();
-}
-
-template <bool IS_INT, int NSH, int S>
-__global__ void __launch_bounds__(256, 2) k_sweep_fast(const __grid_constant__ SweepParams P)
-{
-    using T = typename Acc<IS_INT>::T;
-    unsigned char *smem = g_smem;
+    constexpr int NROWS = fast_nrows<NSH>();
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int gw = blockIdx.x * nwarp + warp, NW = gridDim.x * nwarp;
-    // compact table: row (m, A, B) of RS words = D'[0..S-2], bias
-    constexpr int RS = fast_rs(S), NDE = (NSH >= 3 ? 3 : 2) * S * S * RS;
-    T *Dt = (T *)smem;
-    for (int i = tid; i < NDE; i += blockDim.x) {
-        const int q = i % RS, row = i / RS, mm = row / (S * S), A = (row / S) % S, B = row % S;
-        const int src = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + (q == S - 1 ? 7 : q);
-        if constexpr (IS_INT)
-            Dt[i] = q < S ? P.D.di[src] : 0;
-        else
-            Dt[i] = q < S ? P.D.df[src] : 0.f;
+    const int tw = P.team, wi = warp % tw, tix = warp / tw, tpb = nwarp / tw;
+    const int gteam = blockIdx.x * tpb + tix, NT = gridDim.x * tpb, NW = gridDim.x * nwarp;
+    const int tb = 1 + tix;
+    const bool leader = wi == 0;
+    const uint32_t rb = RB ? (uint32_t)RB : (uint32_t)P.rowB;
+    const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    // fixed-point table and the per-direction offsets of b and its rows
+    const uint32_t qt = 0u;
+    const int qwords = kQRows * P.qrow;
+    for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+    const uint32_t lut = (uint32_t)qwords * 4u;
+    if (tid < 8) {
+        const int kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
+        int4 e;
+        e.x = pslot<NSH>(ky + 1, kz + 1) * (int)rb + kx;
+        e.y = (3 * kz + ky) * (int)rb + kx - 1;
+        e.z = NSH >= 3 ? 4 * (int)rb : (3 + kz) * (int)rb;
+        e.w = NSH >= 3 ? 4 * (int)rb : (4 - kz) * (int)rb;
+        *(int4 *)(g_smem + lut + (uint32_t)tid * 16u) = e;
     }
-    __syncthreads();
-    unsigned char *wbase = smem + fast_d_bytes(NSH, S) + (size_t)warp * P.warp_bytes;
-    double *slot_e = (double *)wbase;
+    const uint32_t tbase = lut + 128u + (uint32_t)tix * (uint32_t)P.team_bytes;
+    const uint32_t mbar0 = tbase, buf0 = tbase + 16u, bufsz = (uint32_t)NROWS * rb;
+    const int nbuf = P.nbuf;  // 1: no prefetch, the next column reuses the buffer
+    const uint32_t wbase = lut + 128u + (uint32_t)tpb * (uint32_t)P.team_bytes + (uint32_t)warp * (uint32_t)P.warp_bytes;
+    double *slot_e = (double *)(g_smem + wbase);
     long long *slot_n = (long long *)(slot_e + P.tpc);
-    const uint32_t col = (uint32_t)((unsigned char *)(slot_n + P.tpc) - smem);
+    const uint32_t wsm = wbase + (uint32_t)P.tpc * 16u;
+    const int is = 32 * tw, ib = lane + 32 * wi;
+    const int nkw = (P.maxNLx + is - 1) / is;
     for (int i = lane; i < P.tpc; i += 32) {
         slot_e[i] = 0.0;
         slot_n[i] = 0;
     }
-    __syncwarp();
+    if (leader && lane == 0) {
+        mbar_init(smem0 + mbar0, 1);
+        mbar_init(smem0 + mbar0 + 8, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
     bool aborted = false;
-    for (int t = 0; t < P.nsweeps && !aborted; ++t) {
-        const uint64_t sweep = P.sweep0 + (uint64_t)t;
-        for (int g = 0; g < P.G && !aborted; ++g) {
-            const uint32_t gstep = (uint32_t)(t * P.G + g);
-            const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4;
-            const int lagv = P.lag[g];
-            const uint32_t need = gstep + 1 >= (uint32_t)lagv ? gstep + 1 - lagv : 0;
-            int slotk = 0;
-            for (int tile = gw; tile < P.ntiles; tile += NW, ++slotk) {
-                int r = 0;
-                while (r + 1 < P.R && P.rep[r + 1].tile0 <= tile) ++r;
-                const RepDesc &RD = P.rep[r];
-                const int lt = tile - RD.tile0, ty = lt % RD.NTy, tz = lt / RD.NTy;
-                if (!wait_tile_warp(P, RD, ty, tz, need, lane)) {
-                    aborted = true;
-                    break;
-                }
-                float beta = 0.f;
-                int2 ti = make_int2(0, 0);
-                if constexpr (IS_INT)
-                    ti = P.temp.tabinfo[P.beta_stride ? r * P.beta_stride + t : r];
-                else
-                    beta = P.temp.beta[P.beta_stride ? r * P.beta_stride + t : r];
-                T accE = T(0);
-                double accEd = 0.0;
-                long long accN = 0;
-                const int j0 = ty * P.TY, j1 = min(j0 + P.TY, RD.NLy);
-                const int l0 = tz * P.TZ, l1 = min(l0 + P.TZ, RD.NLz);
-                for (int l = l0; l < l1; ++l)
-                    for (int j = j0; j < j1; ++j) {
-                        const int y0 = 4 * j + dy, z0 = 4 * l + dz;
-                        if (sub == 0)
-                            fast_column<IS_INT, NSH, S, -1>(P, RD, col, y0, z0, sweep, beta, ti, 0u, lane, accE,
-                                                            accEd, accN);
-                        else
-                            fast_column<IS_INT, NSH, S, 0>(P, RD, col, y0, z0, sweep, beta, ti, 0u, lane, accE,
-                                                           accEd, accN);
-                    }
-                double e_w;
-                if constexpr (IS_INT)
-                    e_w = (double)warp_sum<long long>((long long)accE);
-                else
-                    e_w = warp_sum<double>(accEd);
-                const long long n_w = warp_sum<long long>(accN);
-                if (lane == 0) {
-                    slot_e[slotk] += e_w;
-                    slot_n[slotk] += n_w;
-                }
-                // every lane's row stores, then one release by lane 0 (the warp
-                // barrier orders the other lanes' stores before it)
-                __syncwarp();
-                if (lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, gstep + 1);
+    // per buffer b: bit b of par = parity of its barrier's next phase; bit b
+    // of inflight (leader) = copies issued and not yet waited for
+    uint32_t par = 0u, inflight = 0u;
+    if (gteam < P.ntiles) {
+        int t = 0, g = 0, tile = gteam, c = 0, nb = 0, slotk = 0;
+        long long accE = 0, accN = 0;
+        FastGeo q = fast_geo(P, t, g, tile, c);
+        bool ok = true;
+        if (leader) {
+            ok = wait_tile_warp(P, P.rep[q.r], q.ty, q.tz, q.need, lane);
+            if (ok) {
+                fast_stage<NSH>(P.rep[q.r], q, smem0, buf0, rb, smem0 + mbar0, lane, P.stage);
+                if (P.rep[q.r].vec && P.stage == 0) inflight = 1u;
             }
         }
+        if (!team_and(tw, tb, ok)) aborted = true;
+        while (!aborted) {
+            const RepDesc &RD = P.rep[q.r];
+            const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
+            // the next item
+            int t2 = t, g2 = g, tile2 = tile, c2 = c + 1, slot2 = slotk;
+            if (c2 >= q.ncols) {
+                c2 = 0;
+                tile2 += NT;
+                ++slot2;
+                if (tile2 >= P.ntiles) {
+                    tile2 = gteam;
+                    slot2 = 0;
+                    if (++g2 == P.G) {
+                        g2 = 0;
+                        ++t2;
+                    }
+                }
+            }
+            const bool has_next = t2 < P.nsweeps;
+            FastGeo q2;
+            if (has_next) q2 = fast_geo(P, t2, g2, tile2, c2);
+            const bool next_vec = has_next && P.rep[q2.r].vec != 0;
+            auto can_prefetch = [&]() -> bool {
+                if (!next_vec || nbuf < 2) return false;
+                if (c2 > 0) return true;
+                if (tile2 == tile) return false;
+                return deps_ready(P, P.rep[q2.r], q2.ty, q2.tz, q2.need, lane);
+            };
+            const int nbn = nbuf == 2 ? nb ^ 1 : nb;
+            const uint32_t bcur = buf0 + (uint32_t)nb * bufsz, bnext = buf0 + (uint32_t)nbn * bufsz;
+            const uint32_t mcur = smem0 + mbar0 + 8u * (uint32_t)nb, mnext = smem0 + mbar0 + 8u * (uint32_t)nbn;
+            bool pre = false;
+            if (leader && can_prefetch()) {
+                fast_stage<NSH>(P.rep[q2.r], q2, smem0, bnext, rb, mnext, lane, P.stage);
+                if (P.stage == 0) inflight |= 1u << nbn;
+                pre = true;
+            }
+            // Philox words of this warp's link cells (while the rows land)
+            const uint64_t sweep = P.sweep0 + (uint64_t)t;
+            {
+                const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0) * nx);
+                const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+                uint32_t *wp = (uint32_t *)(g_smem + wsm);
+#pragma unroll 1
+                for (int k = 0; k < nkw; ++k) {
+                    const int i = ib + is * k;
+                    if (i < NLx) {
+                        const U4 w = philox10(
+                            U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
+                        wp[(k * 4 + 0) * 32 + lane] = w.x;
+                        wp[(k * 4 + 1) * 32 + lane] = w.y;
+                        wp[(k * 4 + 2) * 32 + lane] = w.z;
+                        wp[(k * 4 + 3) * 32 + lane] = w.w;
+                    }
+                }
+            }
+            ok = true;
+            if (RD.vec && P.stage == 0) {
+                ok = mbar_wait(P, mcur, (par >> nb) & 1u);
+                par ^= 1u << nb;
+                if (ok) inflight &= ~(1u << nb);
+            } else if (RD.vec && leader) {
+                // this item's group is the newest unless the next one was just issued
+                if (pre)
+                    asm volatile("cp.async.wait_group 1;" ::: "memory");
+                else
+                    asm volatile("cp.async.wait_group 0;" ::: "memory");
+                __syncwarp();
+            }
+            // periodic halos: 4 bytes before and after each row body
+            if (leader && lane < NROWS) {
+                const uint32_t bd = bcur + (uint32_t)lane * rb + 16u;
+                *(unsigned *)(g_smem + bd - 4) = *(const unsigned *)(g_smem + bd + nx - 4);
+                *(unsigned *)(g_smem + bd + nx) = *(const unsigned *)(g_smem + bd);
+            }
+            if (!team_and(tw, tb, ok)) {
+                aborted = true;
+                break;
+            }
+            float cx = 0.f;
+            int2 ti = make_int2(0, 0);
+            if constexpr (IS_INT)
+                ti = P.temp.tabinfo[P.beta_stride ? q.r * P.beta_stride + t : q.r];
+            else
+                cx = P.temp.beta[P.beta_stride ? q.r * P.beta_stride + t : q.r];
+            const uint32_t body = bcur + 16u;
+            // halo refresh of the 5 rows a mini-step writes: leader lane l < 10
+            // takes row l / 2 (own (0,0), then partner (1,1), (2,1), (1,2),
+            // (2,2)) and side l % 2
+            uint32_t hrow = 0;
+            if (lane < 10) {
+                const int r5 = lane >> 1;
+                const int sl = r5 == 0 ? 4 : pslot<NSH>(1 + ((r5 - 1) & 1), 1 + ((r5 - 1) >> 1));
+                hrow = body + (uint32_t)sl * rb;
+            }
+            for (int dx = 0; dx < 4; ++dx) {
+                if (NLx == is * nkw && (nkw & 3) == 0) {
+#pragma unroll 1
+                    for (int kk = 0; kk < nkw; kk += 4)
+                        fast_trials<IS_INT, NSH, SW, RB, 4, false>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
+                                                                   dx, lane, cx, ti, lut, qt, accE, accN);
+                } else if (NLx == is * nkw && (nkw & 1) == 0) {
+#pragma unroll 1
+                    for (int kk = 0; kk < nkw; kk += 2)
+                        fast_trials<IS_INT, NSH, SW, RB, 2, false>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
+                                                                   dx, lane, cx, ti, lut, qt, accE, accN);
+                } else if (NLx == is * nkw) {
+#pragma unroll 1
+                    for (int kk = 0; kk < nkw; ++kk)
+                        fast_trials<IS_INT, NSH, SW, RB, 1, false>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
+                                                                   dx, lane, cx, ti, lut, qt, accE, accN);
+                } else {
+#pragma unroll 1
+                    for (int kk = 0; kk < nkw; ++kk)
+                        fast_trials<IS_INT, NSH, SW, RB, 1, true>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
+                                                                  dx, lane, cx, ti, lut, qt, accE, accN);
+                }
+                team_sync(tw, tb);
+                if (leader && lane < 10) {
+                    if (lane & 1)
+                        *(unsigned *)(g_smem + hrow + nx) = *(const unsigned *)(g_smem + hrow);
+                    else
+                        *(unsigned *)(g_smem + hrow - 4) = *(const unsigned *)(g_smem + hrow + nx - 4);
+                }
+                team_sync(tw, tb);
+                if (leader && !pre && dx < 3 && can_prefetch()) {
+                    fast_stage<NSH>(P.rep[q2.r], q2, smem0, bnext, rb, mnext, lane, P.stage);
+                    if (P.stage == 0) inflight |= 1u << nbn;
+                    pre = true;
+                }
+            }
+            // ---- write back trial row (0,0) and partner rows (s_off..s_off+1)^2,
+            // the team's threads over (row, chunk) pairs ----
+            {
+                const bool vec = RD.vec != 0;
+                const int cpr = vec ? (nx >> 4) : (nx >> 2);
+                for (int qq = lane + 32 * wi; qq < 5 * cpr; qq += is) {
+                    const int wr = qq / cpr, cc = qq - wr * cpr;
+                    int slot, gsub, gy, gz;
+                    if (wr == 0) {
+                        slot = 4;
+                        gsub = q.sub;
+                        gy = q.y0;
+                        gz = q.z0;
+                    } else {
+                        const int sy = 1 + ((wr - 1) & 1), sz = 1 + ((wr - 1) >> 1);
+                        slot = pslot<NSH>(sy, sz);
+                        gsub = 1 - q.sub;
+                        gy = wrapc(q.y0 + sy - 1 + q.soff, ny);
+                        gz = wrapc(q.z0 + sz - 1 + q.soff, nz);
+                    }
+                    int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
+                    const unsigned char *srcs = g_smem + body + (uint32_t)slot * rb;
+                    if (vec)
+                        *((int4 *)dstg + cc) = *((const int4 *)srcs + cc);
+                    else
+                        *((unsigned *)dstg + cc) = *((const unsigned *)srcs + cc);
+                }
+            }
+            // every thread's row stores, then one release by the leader's lane 0
+            // (the barrier orders the team's stores before it)
+            team_sync(tw, tb);
+            if (c + 1 >= q.ncols) {
+                // the tile's last column: accumulate in fixed order and publish
+                const long long e_w = warp_sum<long long>(accE);
+                const long long n_w = warp_sum<long long>(accN);
+                if (lane == 0) {
+                    slot_e[slotk] += (double)e_w;
+                    slot_n[slotk] += n_w;
+                }
+                accE = 0;
+                accN = 0;
+                if (leader && lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, q.gstep + 1);
+            }
+            if (!has_next) break;
+            ok = true;
+            if (leader && !pre) {
+                if (c2 == 0) ok = wait_tile_warp(P, P.rep[q2.r], q2.ty, q2.tz, q2.need, lane);
+                if (ok) {
+                    fast_stage<NSH>(P.rep[q2.r], q2, smem0, bnext, rb, mnext, lane, P.stage);
+                    if (next_vec && P.stage == 0) inflight |= 1u << nbn;
+                }
+            }
+            if (!team_and(tw, tb, ok)) {
+                aborted = true;
+                break;
+            }
+            t = t2;
+            g = g2;
+            tile = tile2;
+            c = c2;
+            slotk = slot2;
+            q = q2;
+            nb = nbn;
+        }
     }
-    // ---- per-tile partial sums; the last warp to finish reduces them in order ----
-    if (aborted) return;
+    if (aborted) {
+        // let the team's copies in flight land before the CTA ends
+        if (leader) asm volatile("cp.async.wait_all;" ::: "memory");
+        if (leader)
+            for (int b = 0; b < 2; ++b)
+                if (inflight & (1u << b)) mbar_wait(P, smem0 + mbar0 + 8u * (uint32_t)b, (par >> b) & 1u);
+        return;
+    }
+    // ---- per-tile partial sums (one per warp of the team); the last warp to
+    // finish reduces them in order ----
     if (lane == 0) {
         int k = 0;
-        for (int tile = gw; tile < P.ntiles; tile += NW, ++k) {
-            P.part_e[tile] = slot_e[k];
-            P.part_n[tile] = slot_n[k];
+        for (int tl = gteam; tl < P.ntiles; tl += NT, ++k) {
+            P.part_e[(size_t)tl * tw + wi] = slot_e[k];
+            P.part_n[(size_t)tl * tw + wi] = slot_n[k];
         }
     }
     __threadfence();
@@ -901,13 +1124,44 @@ __global__ void __launch_bounds__(256, 2) k_sweep_fast(const __grid_constant__ S
         double se = 0.0;
         long long sn = 0;
         const int nt = RD.NTy * RD.NTz;
-        for (int k = 0; k < nt; ++k) {
-            se += __ldcg(P.part_e + RD.tile0 + k);
-            sn += __ldcg(P.part_n + RD.tile0 + k);
+        for (int k = 0; k < nt * tw; ++k) {
+            se += __ldcg(P.part_e + (size_t)RD.tile0 * tw + k);
+            sn += __ldcg(P.part_n + (size_t)RD.tile0 * tw + k);
         }
-        if (RD.e_acc) *RD.e_acc += se;
+        if (RD.e_acc) *RD.e_acc += se * P.escale;
         if (RD.n_acc) *RD.n_acc += sn;
     }
+}
+
+// Species byte conversion around a fast-path launch: up (s -> 8 s, with a
+// check that 0 <= s < S; a byte outside sets SMC_ERR_ARG in the status word
+// and is taken mod 8) or down (8 s -> s).
+__global__ void k_occ_scale(int8_t *occ, long long n, int up, int S, int *status)
+{
+    const long long nw = n >> 2;
+    uint32_t *w4 = (uint32_t *)occ;
+    const uint32_t lim = (uint32_t)(0x80 - S) * 0x01010101u;
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t v = w4[i];
+        if (up) {
+            bad |= ((v | (v + lim)) & 0x80808080u) != 0u;
+            w4[i] = (v & 0x07070707u) << 3;
+        } else {
+            w4[i] = (v >> 3) & 0x07070707u;
+        }
+    }
+    for (long long i = (nw << 2) + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x) {
+        const int v = occ[i];
+        if (up) {
+            bad |= v < 0 || v >= S;
+            occ[i] = (int8_t)((v & 7) << 3);
+        } else {
+            occ[i] = (int8_t)((v >> 3) & 7);
+        }
+    }
+    if (bad) atomicCAS(status, 0, (int)SMC_ERR_ARG);
 }
 
 // ---------------------------------------------------------------------------
@@ -928,18 +1182,12 @@ struct GView {
     }
 };
 
-template <bool IS_INT>
+template <bool IS_INT, int NSH, int SW>
 __global__ void k_ministep_eval(const __grid_constant__ SweepParams P, int k, float *dE_out, uint8_t *acc_out,
                                 int *swap_a, int *swap_b)
 {
-    using T = typename Acc<IS_INT>::T;
-    __shared__ T Dt[kDEntries];
-    for (int i = threadIdx.x; i < kDEntries; i += blockDim.x) {
-        if constexpr (IS_INT)
-            Dt[i] = P.D.di[i];
-        else
-            Dt[i] = P.D.df[i];
-    }
+    __shared__ __align__(16) uint32_t Qt[kPairQWords];
+    for (int i = threadIdx.x; i < kQRows * P.qrow; i += blockDim.x) Qt[i] = P.qtab[i];
     __syncthreads();
     const RepDesc &RD = P.rep[0];
     const int ntr = RD.NLx * RD.NLy * RD.NLz;
@@ -948,22 +1196,23 @@ __global__ void k_ministep_eval(const __grid_constant__ SweepParams P, int k, fl
     const int dx = k % P.Lx, dy = (k / P.Lx) % P.Ly, dz = (k / (P.Lx * P.Ly)) % P.Lz;
     const int sub = k / (P.Lx * P.Ly * P.Lz);
     const int s_off = sub == 0 ? -1 : 0;
-    const int cx = c % RD.NLx, cy = (c / RD.NLx) % RD.NLy, cz = c / (RD.NLx * RD.NLy);
+    const int cx_ = c % RD.NLx, cy = (c / RD.NLx) % RD.NLy, cz = c / (RD.NLx * RD.NLy);
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz;
-    const int x = cx * P.Lx + dx, y0 = cy * P.Ly + dy, z0 = cz * P.Lz + dz;
+    const int x = cx_ * P.Lx + dx, y0 = cy * P.Ly + dy, z0 = cz * P.Lz + dz;
     const GView gv{(const unsigned char *)RD.occ, nx, ny, nz, sub, y0, z0};
     const uint32_t s = (uint32_t)(((sub * nz + z0) * ny + y0) * nx + x);
     const uint32_t w = site_word(P.seed, RD.rep, P.sweep0, s);
     int A, B, ex, ey, ez;
-    const T dE = trial_dE<IS_INT, GView>(gv, x, nx, s_off, (int)(w >> kRBits), P.nshells, P.S, Dt, A, B, ex, ey, ez);
-    float beta = 0.f;
+    const int32_t dE =
+        trial_dE_hist<NSH, SW, GView>(gv, x, nx, s_off, (int)(w >> kRBits), Qt, P.qrow, A, B, ex, ey, ez);
+    float cxp = 0.f;
     int2 ti = make_int2(0, 0);
     if constexpr (IS_INT)
         ti = P.temp.tabinfo[0];
     else
-        beta = P.temp.beta[0];
-    const bool acc = metropolis<IS_INT>(dE, w & kRMask, beta, P.tab, ti);
-    if (dE_out) dE_out[c] = (float)dE;
+        cxp = P.temp.beta[0];
+    const bool acc = accept_fixed<IS_INT>(dE, w & kRMask, cxp, P.tab, ti);
+    if (dE_out) dE_out[c] = (float)dE * (float)P.escale;
     if (acc_out) acc_out[c] = acc ? 1 : 0;
     const int by = wrapc(y0 + ey, ny), bz = wrapc(z0 + ez, nz), bx = wrapc(x + ex, nx);
     swap_a[c] = (acc && A != B) ? (int)s : -1;
@@ -985,7 +1234,77 @@ __global__ void k_ministep_apply(int8_t *occ, int ntr, const int *swap_a, const 
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
-// Warp count of the warp-per-tile kernel.  Warp w owns tiles w, w + NW, ...
+bool build_pair_table(const smc_model *m, int S, PairTable &t)
+{
+    const bool is_int = m->kind == SMC_PAIR_I32;
+    t.nsh = m->nshells >= 3 ? 3 : 2;
+    t.sw = S <= 5 ? 1 : 2;
+    t.rw = qrow_words(t.nsh, t.sw);
+    const int R = S - 1, nf = 4 * t.sw;
+    auto V = [&](int mm, int p, int q) -> double {
+        return is_int ? (double)m->v_i32[(mm * S + p) * S + q] : (double)m->v_f32[(mm * S + p) * S + q];
+    };
+    if (is_int) {
+        t.sigma = 0;
+    } else {
+        // |dE_fix| <= 2^sigma sum_m 2 (z_m - 1) max|D'_m| with |D'_m| <= 4 max|V_m|;
+        // keep it below 2^30
+        static const int z[3] = {8, 6, 12};
+        double bound = 0.0;
+        for (int mm = 0; mm < m->nshells; ++mm) {
+            double M = 0.0;
+            for (int p = 0; p < S; ++p)
+                for (int q = 0; q < S; ++q) {
+                    const double v = V(mm, p, q);
+                    if (!std::isfinite(v)) return false;
+                    M = std::max(M, std::fabs(v));
+                }
+            bound += 8.0 * (z[mm] - 1) * M;
+        }
+        t.sigma = bound > 0.0 ? (int)std::floor(std::log2(1073741824.0 / bound)) : 40;
+        t.sigma = std::max(-60, std::min(t.sigma, 60));
+    }
+    t.scale = std::ldexp(1.0, -t.sigma);
+    t.rows.assign((size_t)kQRows * t.rw, 0u);
+    for (int A = 0; A < S; ++A)
+        for (int B = 0; B < S; ++B) {
+            uint32_t *row = &t.rows[(size_t)(A * 8 + B) * t.rw];
+            uint32_t kb = 0u;
+            for (int mm = 0; mm < t.nsh; ++mm) {
+                int64_t Q[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+                if (mm < m->nshells && A != B)
+                    for (int q = 0; q < R && q < nf; ++q) {
+                        const double d = (V(mm, B, q) - V(mm, A, q)) - (V(mm, B, R) - V(mm, A, R));
+                        Q[q] = is_int ? (int64_t)d : (int64_t)std::llrint(std::ldexp(d, t.sigma));
+                    }
+                const uint32_t bias = mm < 2 ? 8u : 16u;
+                for (int q = 0; q < nf; ++q) kb -= bias * (uint32_t)Q[q];
+                for (int w = 0; w < t.sw; ++w)
+                    for (int k = 0; k < 4; ++k) {
+                        uint32_t word = 0u;
+                        for (int j = 0; j < 4; ++j) word |= (((uint32_t)Q[4 * w + j] >> (8 * k)) & 0xFFu) << (8 * j);
+                        row[(mm * t.sw + w) * 4 + k] = word;
+                    }
+            }
+            row[t.nsh * t.sw * 4] = kb;
+        }
+    return true;
+}
+
+// Exponent factor of the FP Metropolis test: -log2(e) 2^-sigma / kT.
+static float accept_cx(double scale, double kT)
+{
+    return (float)(-1.4426950408889634 * scale / kT);
+}
+
+static void load_table(SweepParams &P, const PairTable &pt)
+{
+    P.qrow = pt.rw;
+    P.escale = pt.scale;
+    memcpy(P.qtab, pt.rows.data(), pt.rows.size() * 4);
+}
+
+// Warp count of a warp-per-tile kernel.  Warp w owns tiles w, w + NW, ...
 // and CTA b lands on SM b mod num_sms (then b + num_sms, ...), so an SM's
 // time is the sum of its warps' tile counts.  Among all CTA counts that fit
 // at once, take the one with the smallest busiest-SM load (ties: more warps,
@@ -1016,7 +1335,8 @@ namespace {
 
 struct Plan {
     int Lx, Ly, Lz, G;
-    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0, nap_cap = 128, rowB = 0;
+    int threads, CB, TY, TZ, ntiles, grid, tpc, warp_bytes = 0, nap_cap = 128, rowB = 0, maxNLx = 1;
+    int team = 1, team_bytes = 0, nbuf = 2;
     size_t smem;
     const void *kernel = nullptr;
 };
@@ -1030,7 +1350,14 @@ int col_bytes_of(const smc_lattice &l)
 }
 
 template <bool IS_INT>
-smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
+const void *pick_slow(int nsh, int sw)
+{
+    if (nsh >= 3) return sw == 2 ? (const void *)k_sweep_pair<IS_INT, 3, 2> : (const void *)k_sweep_pair<IS_INT, 3, 1>;
+    return sw == 2 ? (const void *)k_sweep_pair<IS_INT, 2, 2> : (const void *)k_sweep_pair<IS_INT, 2, 1>;
+}
+
+template <bool IS_INT>
+smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, const PairTable &pt, Plan &pl)
 {
     const Tuning tu = current_tuning();
     pl.Lx = lc_edge(lats[0].nx);
@@ -1059,14 +1386,9 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
     }
     pl.CB = std::min(pl.CB, pl.TY * pl.TZ);
     const int nwarps = pl.threads / 32;
-    const size_t base = (size_t)kDEntries * 4;
+    const size_t base = (size_t)kQRows * pt.rw * 4;
     auto smem_for = [&](int cb, int tpc) { return base + (size_t)tpc * nwarps * 16 + (size_t)cb * maxcol; };
-    while (pl.CB > 1 && smem_for(pl.CB, 64) > ws->smem_optin) pl.CB /= 2;
-    if (smem_for(pl.CB, 1) > ws->smem_optin) {
-        set_error("lattice rows too long for shared memory (nx = %d)", lats[0].nx);
-        return SMC_ERR_UNSUPPORTED;
-    }
-    auto kern = k_sweep_pair<IS_INT>;
+    const void *kern = pick_slow<IS_INT>(pt.nsh, pt.sw);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
@@ -1103,39 +1425,43 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, Plan &pl)
         }
     }
     pl.smem = smem;
-    pl.kernel = (const void *)k_sweep_pair<IS_INT>;
+    pl.kernel = kern;
     return SMC_OK;
 }
 
-template <bool IS_INT, int NSH>
-const void *pick_fast(int S)
+template <bool IS_INT>
+const void *pick_fast(int nsh, int sw, int rowB, int R)
 {
-    switch (S) {
-    case 2: return (const void *)k_sweep_fast<IS_INT, NSH, 2>;
-    case 5: return (const void *)k_sweep_fast<IS_INT, NSH, 5>;
-    default: return (const void *)k_sweep_fast<IS_INT, NSH, 8>;
+    if (!IS_INT && nsh == 2 && sw == 1 && R == 1) {
+        // compile-time row strides for the benchmark row lengths (128, 256, 512 cells)
+        if (rowB == 160) return (const void *)k_sweep_fast<IS_INT, 2, 1, 160>;
+        if (rowB == 288) return (const void *)k_sweep_fast<IS_INT, 2, 1, 288>;
+        if (rowB == 544) return (const void *)k_sweep_fast<IS_INT, 2, 1, 544>;
     }
+    if (nsh >= 3)
+        return sw == 2 ? (const void *)k_sweep_fast<IS_INT, 3, 2, 0> : (const void *)k_sweep_fast<IS_INT, 3, 1, 0>;
+    return sw == 2 ? (const void *)k_sweep_fast<IS_INT, 2, 2, 0> : (const void *)k_sweep_fast<IS_INT, 2, 1, 0>;
 }
 
 // Plan of the warp-per-tile kernel: tiles of TY x TZ columns, one warp each
-// (a warp owns ceil(ntiles / warps) tiles), shared memory = D table + per warp
-// (accumulator slots + 25 rows).
+// (a warp owns ceil(ntiles / warps) tiles), shared memory = table + offsets
+// + per warp (accumulator slots, barriers, Philox words, two row buffers).
 template <bool IS_INT>
-smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
-                                   int rowB, int same_nx, Plan &pl);
+smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws, const PairTable &pt, int rowB,
+                                   Plan &pl);
 
 // The plan depends only on the shapes, the model's shell and species
 // counts, the tuning and the device, so repeated calls (short chunks of a
 // long run, one call per sample) reuse it instead of searching again.
 template <bool IS_INT>
-smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
-                          int rowB, int same_nx, Plan &pl)
+smc_status make_fast_plan(int R, const smc_lattice *lats, Workspace *ws, const PairTable &pt, int rowB, Plan &pl)
 {
     static std::vector<long long> key_cached;
     static Plan plan_cached;
     const Tuning tu = current_tuning();
-    std::vector<long long> key = {R, nshells, rowB, same_nx, lats[0].nspecies, ws->device, ws->num_sms,
-                                  (long long)ws->smem_optin, tu.tile_y, tu.tile_z, tu.threads, tu.ctas_per_sm};
+    std::vector<long long> key = {R,        pt.nsh,     pt.sw,      rowB,     lats[0].nspecies, ws->device,
+                                  ws->num_sms, (long long)ws->smem_optin, tu.tile_y, tu.tile_z, tu.threads,
+                                  tu.ctas_per_sm, debug_fast_team(), debug_fast_nbuf()};
     for (int r = 0; r < R; ++r) {
         key.push_back(lats[r].nx);
         key.push_back(lats[r].ny);
@@ -1145,7 +1471,7 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
         pl = plan_cached;
         return SMC_OK;
     }
-    const smc_status st = make_fast_plan_uncached<IS_INT>(R, lats, occ, ws, nshells, rowB, same_nx, pl);
+    const smc_status st = make_fast_plan_uncached<IS_INT>(R, lats, ws, pt, rowB, pl);
     if (st == SMC_OK) {
         key_cached = key;
         plan_cached = pl;
@@ -1154,18 +1480,13 @@ smc_status make_fast_plan(int R, const smc_lattice *lats, int8_t *const *occ, Wo
 }
 
 template <bool IS_INT>
-smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const *occ, Workspace *ws, int nshells,
-                                   int rowB, int same_nx, Plan &pl)
+smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws, const PairTable &pt, int rowB,
+                                   Plan &pl)
 {
     const Tuning tu = current_tuning();
     pl.Lx = pl.Ly = pl.Lz = 4;
     pl.G = 32;
-    (void)same_nx;
-    (void)occ;
-    const int S = lats[0].nspecies;
-    const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
-    const int nsh_t = nshells >= 3 ? 3 : 2;
-    pl.kernel = nsh_t == 3 ? pick_fast<IS_INT, 3>(S) : pick_fast<IS_INT, 2>(S);
+    pl.kernel = pick_fast<IS_INT>(pt.nsh, pt.sw, rowB, R);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
@@ -1177,6 +1498,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const
         nkmax = std::max(nkmax, (lats[r].nx / 4 + 31) / 32);
         maxNLx = std::max(maxNLx, lats[r].nx / 4);
     }
+    pl.maxNLx = maxNLx;
     // one column per tile unless tuned: the smallest unit of work keeps the
     // neighbour pipeline fullest
     pl.TY = tu.tile_y > 0 ? tu.tile_y : 1;
@@ -1184,115 +1506,116 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, int8_t *const
     pl.ntiles = 0;
     for (int r = 0; r < R; ++r)
         pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
-    const size_t dbytes = (size_t)fast_d_bytes(nsh_t, ST);
-    // Total warps NW: all resident at once (cooperative launch); preferably a
-    // divisor of the tile count so that every warp owns as many tiles as the
-    // others (an unevenly loaded warp makes its neighbours wait).  Between
-    // CTA sizes giving as many warps, the one whose CTAs spread evenly over
-    // the SMs (at most one per SM, or a multiple of the SM count) wins: a
-    // warp that shares its scheduler with more warps than the others runs
-    // slower and its neighbours wait for it (128^3: 1,024 warps as 128 CTAs
-    // of 8 run a sweep in 199 us, as 256 CTAs of 4 in 226 us).
-    auto search = [&](int rb, Plan &out) -> long long {
-        const size_t rows_bytes = (size_t)(nsh_t >= 3 ? 25 : 21) * rb + 16 + (size_t)512 * nkmax;
-        const int cand[2] = {128, 256};
-        long long best_nw = 0;
-        bool best_even = false;
-        for (int ci = 0; ci < 2; ++ci) {
-            const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // launch bound is 256
-            if (tu.threads && ci > 0) break;
-            const int nwarps = threads / 32;
-            for (int tpc_guess = 1;; tpc_guess *= 2) {
-                const size_t wb = ((size_t)16 * tpc_guess + rows_bytes + 15) / 16 * 16;
-                const size_t smem = dbytes + (size_t)nwarps * wb;
-                if (smem > dyn_max) break;
-                int per_sm = 0;
-                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, threads, smem) != cudaSuccess)
-                    return -1;
-                if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
-                if (per_sm < 1) break;
-                const long long res = (long long)per_sm * ws->num_sms * nwarps;
-                const long long nw = balanced_warps(pl.ntiles, nwarps, per_sm, ws->num_sms);
-                (void)res;
-                const int tpc = (int)((pl.ntiles + nw - 1) / nw);
-                if (tpc <= tpc_guess) {
-                    const long long grid = nw / nwarps;
-                    const bool even = grid <= ws->num_sms || grid % ws->num_sms == 0;
-                    if (nw > best_nw || (nw == best_nw && even && !best_even)) {
-                        best_nw = nw;
-                        best_even = even;
-                        out.threads = threads;
-                        out.grid = (int)(nw / nwarps);
-                        out.tpc = tpc_guess;
-                        out.smem = smem;
-                        out.warp_bytes = (int)wb;
-                        out.rowB = rb;
+    const size_t head = (size_t)kQRows * pt.rw * 4 + 128;
+    const int nrows = pt.nsh >= 3 ? 25 : 21;
+    // A team of tw warps shares a column (two row buffers per team); every
+    // warp keeps its accumulator slots and Philox words.  Total warps: all
+    // resident at once (cooperative launch), teams preferably a divisor of the
+    // tile count so that every team owns as many tiles as the others (an
+    // unevenly loaded team makes its neighbours wait).  The most resident
+    // warps win (latency hiding); then the smaller team (fewer barriers);
+    // then CTAs that spread evenly over the SMs.
+    const int cand[4] = {64, 128, 192, 256};
+    long long best_w = 0;
+    int best_tw = 0, best_nb = 0;
+    pl.threads = 0;
+    bool best_even = false;
+    // Measured on GB300 (512^3 and 128^3, two-shell quinary model): one warp
+    // per column with one buffer runs fastest (16 resident warps hide the
+    // staging latency better than 8 warps with two buffers each, and teams
+    // pay a barrier per mini-step), so those are the defaults; the hooks can
+    // still select the others.
+    const int force_tw = debug_fast_team(), force_nb = debug_fast_nbuf();
+    for (int nbuf = 2; nbuf >= 1; --nbuf) {
+        if (force_nb ? nbuf != force_nb : nbuf != 1) continue;
+        for (int tw = 1; tw <= 4; tw *= 2) {
+            if (force_tw ? tw != force_tw : tw != 1) continue;
+            const int nkw = (maxNLx + 32 * tw - 1) / (32 * tw);
+            const size_t team_bytes = 16 + (size_t)nbuf * nrows * rowB;
+            for (int ci = 0; ci < 4; ++ci) {
+                const int threads = tu.threads ? std::min(tu.threads, 256) : cand[ci];  // launch bound is 256
+                if (tu.threads && ci > 0) break;
+                const int nwarps = threads / 32;
+                if (nwarps % tw) continue;
+                const int tpb = nwarps / tw;
+                for (int tpc_guess = 1;; tpc_guess *= 2) {
+                    const size_t wb = ((size_t)16 * tpc_guess + (size_t)512 * nkw + 15) / 16 * 16;
+                    const size_t smem = head + (size_t)tpb * team_bytes + (size_t)nwarps * wb;
+                    if (smem > dyn_max) break;
+                    int per_sm = 0;
+                    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, threads, smem);
+                    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+                    if (tu.ctas_per_sm > 0) per_sm = std::min(per_sm, tu.ctas_per_sm);
+                    if (per_sm < 1) break;
+                    const long long nt = balanced_warps(pl.ntiles, tpb, per_sm, ws->num_sms);  // teams
+                    const int tpc = (int)((pl.ntiles + nt - 1) / nt);
+                    if (tpc <= tpc_guess) {
+                        const long long grid = nt / tpb, nw = nt * tw;
+                        const bool even = grid <= ws->num_sms || grid % ws->num_sms == 0;
+                        // the most resident warps; then the smaller team (fewer
+                        // barriers); then two buffers; then even CTAs; then
+                        // larger CTAs (at 128^3 and 512^3 CTAs of 8 warps ran
+                        // 5-20 % faster than smaller ones with as many warps)
+                        const bool same = nw == best_w && tw == best_tw && nbuf == best_nb;
+                        const bool better = nw > best_w || (nw == best_w && tw < best_tw) ||
+                                            (nw == best_w && tw == best_tw && nbuf > best_nb) ||
+                                            (same && even && !best_even) ||
+                                            (same && even == best_even && threads > pl.threads);
+                        if (better) {
+                            best_w = nw;
+                            best_tw = tw;
+                            best_nb = nbuf;
+                            best_even = even;
+                            pl.threads = threads;
+                            pl.grid = (int)grid;
+                            pl.tpc = tpc_guess;
+                            pl.smem = smem;
+                            pl.warp_bytes = (int)wb;
+                            pl.team = tw;
+                            pl.team_bytes = (int)team_bytes;
+                            pl.nbuf = nbuf;
+                            pl.rowB = rowB;
+                        }
+                        break;
                     }
-                    break;
                 }
             }
         }
-        return best_nw;
-    };
-    const long long nw = search(rowB, pl);
-    if (nw < 0) return cuda_fail(cudaGetLastError(), "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-    if (nw == 0) {
+    }
+    if (best_w == 0) {
         set_error("fast sweep kernel does not fit on an SM (rows of %d bytes)", rowB);
         return SMC_ERR_UNSUPPORTED;
     }
-    // sleep between progress polls: short for small columns (latency-bound;
-    // at 128^3 a cap of 32 ns measured 1 % faster than 128 ns), longer for
-    // long ones (a tile-group takes tens of microseconds)
+    // sleep between progress polls: short for small columns (latency-bound),
+    // longer for long ones (a tile-group takes tens of microseconds)
     pl.nap_cap = maxNLx >= 64 ? 1024 : 32;
     pl.CB = 1;
     return SMC_OK;
 }
 
-}  // namespace
-
-// Integer acceptance table T[d] = floor(2^29 exp(-d unit / kT)) for d = 0 ..
-// len-1 (T[len] = 0), in FP64 on the host.
-std::vector<uint32_t> int_table(double unit_ev, double kT)
+// Fast path: 4-cell link cells on every axis, rows of at most 1024 cells,
+// 4-byte aligned occupancy.
+bool fast_ok(int R, const smc_lattice *lats, int8_t *const *occ, int &rowB)
 {
-    std::vector<uint32_t> t;
-    for (int64_t d = 0;; ++d) {
-        const double v = floor(536870912.0 * exp(-(double)d * unit_ev / kT));
-        if (v <= 0.0 || d > (1 << 24)) break;
-        t.push_back((uint32_t)v);
-    }
-    return t;
-}
-
-template <bool IS_INT>
-static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,
-                             uint32_t replica0, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
-                             int64_t *n_acc, cudaStream_t stream)
-{
-    smc_status st;
-    Workspace *ws = workspace(&st);
-    if (!ws) return st;
-    // Fast path: 4-cell link cells on every axis, rows of at most 1024 cells,
-    // 4-byte aligned occupancy.
     bool fast = true;
-    int rowB_fast = 0, same_nx = lats[0].nx;
+    rowB = 0;
     for (int r = 0; r < R; ++r) {
         const smc_lattice &l = lats[r];
         fast = fast && lc_edge(l.nx) == 4 && lc_edge(l.ny) == 4 && lc_edge(l.nz) == 4 && l.nx <= 1024 &&
                ((uintptr_t)occ[r] % 4 == 0);
-        rowB_fast = std::max(rowB_fast, ((l.nx + 15) & ~15) + 16);  // body at +16, 4-byte halos
-        if (l.nx != same_nx) same_nx = -1;
+        rowB = std::max(rowB, ((l.nx + 15) & ~15) + 32);  // body at +16, 4-byte halos, 16-byte rows
     }
-    if (current_tuning().threads && current_tuning().threads % 32) fast = false;
-    Plan pl;
-    if (fast) {
-        st = make_fast_plan<IS_INT>(R, lats, occ, ws, m->nshells, rowB_fast, same_nx, pl);
-        if (st != SMC_OK) return st;
-    } else {
-        st = make_plan<IS_INT>(R, lats, ws, pl);
-        if (st != SMC_OK) return st;
-    }
+    const Tuning tu = current_tuning();
+    if (tu.threads && tu.threads % 32) fast = false;
+    return fast;
+}
 
-    static SweepParams P;  // large: keep off the stack (host-only, guarded by the API lock)
+// Shared parameter-block setup of the sweep launches (tiles, replicas,
+// table, schedule lags).
+void fill_params(SweepParams &P, const Plan &pl, bool fast, int R, const smc_lattice *lats, int8_t *const *occ,
+                 uint32_t replica0, double *e_acc, int64_t *n_acc, const smc_model *m, const PairTable &pt,
+                 uint64_t seed)
+{
     memset(&P, 0, sizeof P);
     P.R = R;
     P.G = pl.G;
@@ -1301,13 +1624,20 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     P.Lz = pl.Lz;
     P.TY = pl.TY;
     P.TZ = pl.TZ;
-    P.CB = pl.CB;
+    P.CB = std::min(pl.CB, pl.TY * pl.TZ);
     P.nshells = m->nshells;
     P.S = lats[0].nspecies;
     P.tpc = pl.tpc;
     P.warp_bytes = pl.warp_bytes;
     P.nap_cap = pl.nap_cap;
-    P.rowB = fast ? pl.rowB : rowB_fast;
+    P.rowB = pl.rowB;
+    P.maxNLx = pl.maxNLx;
+    P.team = pl.team;
+    P.team_bytes = pl.team_bytes;
+    P.nbuf = pl.nbuf;
+    // bulk copies for long rows (512^3: 3.36 against 3.56 ms per sweep),
+    // 16-byte cp.async for short ones (128^3: 0.218 against 0.249 ms)
+    P.stage = debug_fast_stage() == 1 ? 0 : (debug_fast_stage() == 2 ? 1 : (pl.maxNLx >= 64 ? 0 : 1));
     for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
     if (fast) {
         // Groups with dy >= 1 conflict with neighbouring columns only two
@@ -1337,52 +1667,62 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
         d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ[r] % 16 == 0);
         tile0 += d.NTy * d.NTz;
     }
-    P.CB = std::min(P.CB, P.TY * P.TZ);
     P.ntiles = tile0;
+    load_table(P, pt);
+}
 
-    // D[m][A][B][q] = V_m(B, q) - V_m(A, q), padded to 8 species.  The fast
-    // kernel reads D'[q] = D[q] - D[ST-1] for q < ST-1 (ST = its species
-    // template: 2, 5 or 8) and, in entry 7 of shells 1 and 2, -8 sum D'.
-    const int S = P.S;
-    if (fast) {
-        const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
-        for (int mm = 0; mm < m->nshells; ++mm)
-            for (int A = 0; A < S; ++A)
-                for (int B = 0; B < S; ++B) {
-                    auto Dv = [&](int q) -> double {
-                        if (q >= S) return 0.0;
-                        if (IS_INT) return (double)m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
-                        return (double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q];
-                    };
-                    const int base = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
-                    double bias = 0.0;
-                    for (int q = 0; q < ST - 1; ++q) {
-                        const double d = Dv(q) - Dv(ST - 1);
-                        if (IS_INT)
-                            P.D.di[base + q] = (int)d;
-                        else
-                            P.D.df[base + q] = (float)d;
-                        bias += d;
-                    }
-                    if (mm < 2) {
-                        if (IS_INT)
-                            P.D.di[base + 7] = (int)(-8.0 * bias);
-                        else
-                            P.D.df[base + 7] = (float)(-8.0 * bias);
-                    }
-                }
+// Species byte conversion around fast-path launches.
+smc_status scale_occ(int R, const smc_lattice *lats, int8_t *const *occ, bool up, int *status, int num_sms,
+                     cudaStream_t stream)
+{
+    for (int r = 0; r < R; ++r) {
+        const long long n = 2LL * lats[r].nx * lats[r].ny * lats[r].nz;
+        const long long nw = (n + 3) / 4;
+        const int grid = (int)std::max<long long>(1, std::min<long long>((nw + 255) / 256, (long long)num_sms * 8));
+        k_occ_scale<<<grid, 256, 0, stream>>>(occ[r], n, up ? 1 : 0, lats[r].nspecies, status);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "k_occ_scale");
     }
-    for (int mm = 0; mm < (fast ? 0 : m->nshells); ++mm)
-        for (int A = 0; A < S; ++A)
-            for (int B = 0; B < S; ++B)
-                for (int q = 0; q < S; ++q) {
-                    const int idx = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q;
-                    if (IS_INT)
-                        P.D.di[idx] = m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
-                    else
-                        P.D.df[idx] = (float)((double)m->v_f32[(mm * S + B) * S + q] -
-                                              (double)m->v_f32[(mm * S + A) * S + q]);
-                }
+    return SMC_OK;
+}
+
+}  // namespace
+
+// Integer acceptance table T[d] = floor(2^29 exp(-d unit / kT)) for d = 0 ..
+// len-1 (T[len] = 0), in FP64 on the host.
+std::vector<uint32_t> int_table(double unit_ev, double kT)
+{
+    std::vector<uint32_t> t;
+    for (int64_t d = 0;; ++d) {
+        const double v = floor(536870912.0 * exp(-(double)d * unit_ev / kT));
+        if (v <= 0.0 || d > (1 << 24)) break;
+        t.push_back((uint32_t)v);
+    }
+    return t;
+}
+
+template <bool IS_INT>
+static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,
+                             uint32_t replica0, uint64_t sweep0, int nsweeps, const double *kT, double *e_acc,
+                             int64_t *n_acc, cudaStream_t stream)
+{
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    PairTable pt;
+    if (!build_pair_table(m, lats[0].nspecies, pt)) {
+        set_error("pair coefficients must be finite");
+        return SMC_ERR_ARG;
+    }
+    int rowB = 0;
+    const bool fast = fast_ok(R, lats, occ, rowB);
+    Plan pl;
+    st = fast ? make_fast_plan<IS_INT>(R, lats, ws, pt, rowB, pl) : make_plan<IS_INT>(R, lats, ws, pt, pl);
+    if (st != SMC_OK) return st;
+    if (!fast) pl.rowB = rowB;
+
+    static SweepParams P;  // large: keep off the stack (host-only, guarded by the API lock)
+    fill_params(P, pl, fast, R, lats, occ, replica0, e_acc, n_acc, m, pt, seed);
 
     // temperature schedule: constant per replica over the call, or per sweep
     bool constant = true;
@@ -1416,10 +1756,11 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
             for (int t = 0; t < nsweeps; ++t) table_of(kT[(size_t)r * nsweeps + t]);
     }
 
-    // workspace: [flags | part_e | part_n | ticket, abort | tables]
-    const size_t nt = (size_t)P.ntiles;
-    const size_t off_flags = 0, off_pe = ((nt * 4 + 15) / 16) * 16, off_pn = off_pe + nt * 8;
-    const size_t off_misc = off_pn + nt * 8, off_tab = off_misc + 16;
+    // workspace: [flags | part_e | part_n | ticket, abort | tables]; the fast
+    // kernel keeps one partial sum per tile and warp of its team
+    const size_t nt = (size_t)P.ntiles, np = nt * (size_t)std::max(1, P.team);
+    const size_t off_flags = 0, off_pe = ((nt * 4 + 15) / 16) * 16, off_pn = off_pe + np * 8;
+    const size_t off_misc = off_pn + np * 8, off_tab = off_misc + 16;
     const size_t need = off_tab + tabs.size() * 4;
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, need, &st);
     if (!scr) return st;
@@ -1435,8 +1776,12 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
         e = cudaMemcpyAsync(scr + off_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance tables)");
     }
-
-    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+    if (fast) {
+        st = scale_occ(R, lats, occ, true, P.status, ws->num_sms, stream);
+        if (st != SMC_OK) return st;
+    }
+    smc_status run = SMC_OK;
+    for (int t0 = 0; t0 < nsweeps && run == SMC_OK; t0 += chunk) {
         const int nc = std::min(chunk, nsweeps - t0);
         P.sweep0 = sweep0 + (uint64_t)t0;
         P.nsweeps = nc;
@@ -1448,15 +1793,23 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
                 if (IS_INT)
                     P.temp.tabinfo[idx] = table_of(kt);
                 else
-                    P.temp.beta[idx] = (float)(1.0 / kt);
+                    P.temp.beta[idx] = accept_cx(pt.scale, kt);
             }
         e = cudaMemsetAsync(scr, 0, off_tab, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
+        if (e != cudaSuccess) {
+            run = cuda_fail(e, "cudaMemsetAsync(sweep scratch)");
+            break;
+        }
         void *args[] = {(void *)&P};
         e = cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(sweep)");
+        if (e != cudaSuccess) run = cuda_fail(e, "cudaLaunchCooperativeKernel(sweep)");
     }
-    return SMC_OK;
+    if (fast) {
+        // the species go back to plain indices even when a launch failed
+        st = scale_occ(R, lats, occ, false, P.status, ws->num_sms, stream);
+        if (run == SMC_OK && st != SMC_OK) run = st;
+    }
+    return run;
 }
 
 smc_status launch_pair_sweep(int R, const smc_lattice *lats, const smc_model *m, int8_t *const *occ, uint64_t seed,
@@ -1483,6 +1836,11 @@ static smc_status trace_impl(const smc_lattice *lat, const smc_model *m, int8_t 
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
+    PairTable pt;
+    if (!build_pair_table(m, lat->nspecies, pt)) {
+        set_error("pair coefficients must be finite");
+        return SMC_ERR_ARG;
+    }
     static SweepParams P;
     memset(&P, 0, sizeof P);
     P.R = 1;
@@ -1502,25 +1860,14 @@ static smc_status trace_impl(const smc_lattice *lat, const smc_model *m, int8_t 
     d.NLy = d.ny / P.Ly;
     d.NLz = d.nz / P.Lz;
     d.rep = replica;
-    const int S = P.S;
-    for (int mm = 0; mm < m->nshells; ++mm)
-        for (int A = 0; A < S; ++A)
-            for (int B = 0; B < S; ++B)
-                for (int q = 0; q < S; ++q) {
-                    const int idx = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q;
-                    if (IS_INT)
-                        P.D.di[idx] = m->v_i32[(mm * S + B) * S + q] - m->v_i32[(mm * S + A) * S + q];
-                    else
-                        P.D.df[idx] = (float)((double)m->v_f32[(mm * S + B) * S + q] -
-                                              (double)m->v_f32[(mm * S + A) * S + q]);
-                }
+    load_table(P, pt);
     const int ntr = d.NLx * d.NLy * d.NLz;
     std::vector<uint32_t> tab;
     if (IS_INT) {
         tab = int_table(m->unit_ev, kT);
         P.temp.tabinfo[0] = make_int2(0, (int)tab.size());
     } else {
-        P.temp.beta[0] = (float)(1.0 / kT);
+        P.temp.beta[0] = accept_cx(pt.scale, kT);
     }
     const size_t off_tab = ((size_t)ntr * 8 + 15) / 16 * 16;
     unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_tab + tab.size() * 4 + 16, &st);
@@ -1533,7 +1880,17 @@ static smc_status trace_impl(const smc_lattice *lat, const smc_model *m, int8_t 
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance table)");
     }
     const int threads = 128, blocks = (ntr + threads - 1) / threads;
-    k_ministep_eval<IS_INT><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+    if (pt.nsh >= 3) {
+        if (pt.sw == 2)
+            k_ministep_eval<IS_INT, 3, 2><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+        else
+            k_ministep_eval<IS_INT, 3, 1><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+    } else {
+        if (pt.sw == 2)
+            k_ministep_eval<IS_INT, 2, 2><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+        else
+            k_ministep_eval<IS_INT, 2, 1><<<blocks, threads, 0, stream>>>(P, k, dE, acc, swap_a, swap_b);
+    }
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "k_ministep_eval");
     k_ministep_apply<<<blocks, threads, 0, stream>>>(occ, ntr, swap_a, swap_b);
@@ -1594,87 +1951,26 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     ws.num_sms = sms;
     ws.smem_optin = (size_t)optin;
 
-    const int R = 1;
-    const smc_lattice *lats = lat;
+    PairTable pt;
+    if (!build_pair_table(m, lat->nspecies, pt)) {
+        set_error("pair coefficients must be finite");
+        return SMC_ERR_ARG;
+    }
     int8_t *occs[1] = {occ};
-    const bool fast = lc_edge(lat->nx) == 4 && lc_edge(lat->ny) == 4 && lc_edge(lat->nz) == 4 && lat->nx <= 1024 &&
-                      ((uintptr_t)occ % 4 == 0);
-    const int rowB_fast = ((lat->nx + 15) & ~15) + 16;
+    int rowB = 0;
+    const bool fast = fast_ok(1, lat, occs, rowB);
     Plan pl;
-    smc_status st = fast ? make_fast_plan<false>(R, lats, occs, &ws, m->nshells, rowB_fast, lat->nx, pl)
-                         : make_plan<false>(R, lats, &ws, pl);
+    smc_status st = fast ? make_fast_plan<false>(1, lat, &ws, pt, rowB, pl) : make_plan<false>(1, lat, &ws, pt, pl);
     if (st != SMC_OK) return st;
-    if (pl.ntiles > kNoAllocMaxTiles) {
+    if (!fast) pl.rowB = rowB;
+    if ((long long)pl.ntiles * std::max(1, pl.team) > kNoAllocMaxTiles) {
         set_error("smc_sweep_noalloc: %d link-cell tiles exceed the scratch limit of %d (use a larger tile_y/tile_z "
                   "tuning or smc_sweep)", pl.ntiles, kNoAllocMaxTiles);
         return SMC_ERR_UNSUPPORTED;
     }
 
     static SweepParams P;
-    memset(&P, 0, sizeof P);
-    P.R = 1;
-    P.G = pl.G;
-    P.Lx = pl.Lx;
-    P.Ly = pl.Ly;
-    P.Lz = pl.Lz;
-    P.TY = pl.TY;
-    P.TZ = pl.TZ;
-    P.CB = std::min(pl.CB, pl.TY * pl.TZ);
-    P.nshells = m->nshells;
-    P.S = lat->nspecies;
-    P.tpc = pl.tpc;
-    P.warp_bytes = pl.warp_bytes;
-    P.nap_cap = pl.nap_cap;
-    P.rowB = fast ? pl.rowB : rowB_fast;
-    for (int g = 0; g < kMaxGroups; ++g) P.lag[g] = 1;
-    if (fast)
-        for (int g = 0; g < pl.G; ++g) P.lag[g] = (g % pl.Ly) == 0 ? 1 : 2;
-    P.skip_tile = (int)debug_skip_tile();
-    P.seed = seed;
-    P.timeout_ns = debug_timeout_ns();
-    RepDesc &d = P.rep[0];
-    d.occ = occ;
-    d.e_acc = e_acc;
-    d.n_acc = (long long *)n_acc;
-    d.nx = lat->nx;
-    d.ny = lat->ny;
-    d.nz = lat->nz;
-    d.NLx = d.nx / pl.Lx;
-    d.NLy = d.ny / pl.Ly;
-    d.NLz = d.nz / pl.Lz;
-    d.NTy = (d.NLy + pl.TY - 1) / pl.TY;
-    d.NTz = (d.NLz + pl.TZ - 1) / pl.TZ;
-    d.tile0 = 0;
-    d.rep = replica;
-    d.vec = (d.nx % 16 == 0) && ((uintptr_t)occ % 16 == 0);
-    P.ntiles = d.NTy * d.NTz;
-    const int S = P.S;
-    if (fast) {
-        const int ST = S == 2 ? 2 : (S == 5 ? 5 : 8);
-        for (int mm = 0; mm < m->nshells; ++mm)
-            for (int A = 0; A < S; ++A)
-                for (int B = 0; B < S; ++B) {
-                    auto Dv = [&](int q) -> double {
-                        if (q >= S) return 0.0;
-                        return (double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q];
-                    };
-                    const int base = ((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies;
-                    double bias = 0.0;
-                    for (int q = 0; q < ST - 1; ++q) {
-                        const double dq = Dv(q) - Dv(ST - 1);
-                        P.D.df[base + q] = (float)dq;
-                        bias += dq;
-                    }
-                    if (mm < 2) P.D.df[base + 7] = (float)(-8.0 * bias);
-                }
-    } else {
-        for (int mm = 0; mm < m->nshells; ++mm)
-            for (int A = 0; A < S; ++A)
-                for (int B = 0; B < S; ++B)
-                    for (int q = 0; q < S; ++q)
-                        P.D.df[((mm * kMaxSpecies + A) * kMaxSpecies + B) * kMaxSpecies + q] =
-                            (float)((double)m->v_f32[(mm * S + B) * S + q] - (double)m->v_f32[(mm * S + A) * S + q]);
-    }
+    fill_params(P, pl, fast, 1, lat, occs, replica, e_acc, n_acc, m, pt, seed);
     bool constant = true;
     for (int t = 1; t < nsweeps; ++t)
         if (kT[t] != kT[0]) constant = false;
@@ -1688,23 +1984,36 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
     P.tab = nullptr;
     e = cudaMemsetAsync(status, 0, sizeof(int32_t), stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(status)");
-    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+    if (fast) {
+        st = scale_occ(1, lat, occs, true, P.status, sms, stream);
+        if (st != SMC_OK) return st;
+    }
+    smc_status run = SMC_OK;
+    for (int t0 = 0; t0 < nsweeps && run == SMC_OK; t0 += chunk) {
         const int nc = std::min(chunk, nsweeps - t0);
         P.sweep0 = sweep0 + (uint64_t)t0;
         P.nsweeps = nc;
         P.beta_stride = constant ? 0 : nc;
-        for (int t = 0; t < (constant ? 1 : nc); ++t) P.temp.beta[t] = (float)(1.0 / kT[t0 + t]);
+        for (int t = 0; t < (constant ? 1 : nc); ++t) P.temp.beta[t] = accept_cx(pt.scale, kT[t0 + t]);
         // the array keeps the last call's contents: zero what must start at
         // zero (ticket, abort word, flags and partial sums of this call's tiles)
         e = cudaMemsetAsync(scr, 0, kNoAllocFlagsOff + (size_t)P.ntiles * 4, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartEOff, 0, (size_t)P.ntiles * 8, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartNOff, 0, (size_t)P.ntiles * 8, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(no-alloc scratch)");
+        const size_t np = (size_t)P.ntiles * (size_t)std::max(1, P.team);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartEOff, 0, np * 8, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr + kNoAllocPartNOff, 0, np * 8, stream);
+        if (e != cudaSuccess) {
+            run = cuda_fail(e, "cudaMemsetAsync(no-alloc scratch)");
+            break;
+        }
         void *args[] = {(void *)&P};
         e = cudaLaunchCooperativeKernel(pl.kernel, dim3(pl.grid), dim3(pl.threads), args, pl.smem, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(no-alloc sweep)");
+        if (e != cudaSuccess) run = cuda_fail(e, "cudaLaunchCooperativeKernel(no-alloc sweep)");
     }
-    return SMC_OK;
+    if (fast) {
+        st = scale_occ(1, lat, occs, false, P.status, sms, stream);
+        if (run == SMC_OK && st != SMC_OK) run = st;
+    }
+    return run;
 }
 
 }  // namespace smc

@@ -3,14 +3,18 @@ anneal workload's model (five species at equal counts, FP32 pair
 coefficients over two shells drawn N(0, 20 meV), the 128^3 job's coefficient
 seed), on a box the oracle finishes in seconds.
 
-Each side runs 8 independent chains (different Philox seeds on the two
+Each side runs 48 independent chains (different Philox seeds on the two
 sides): a linear anneal from 3000 K to 300 K over 150 sweeps, then 100 sweeps
 at 300 K.  Per chain, the final-window means (last 100 sweeps) of the energy
 and of the like-pair Warren-Cowley parameters alpha_m^{pp} of shells 1 and 2
 are taken; the GPU and oracle means over chains must agree within 3 standard
 errors of their difference (the spread across chains, which also holds the
-annealing path's seed-to-seed variation).  The oracle chains run in a pool
-of spawned processes started before the first GPU call."""
+annealing path's seed-to-seed variation: the final energy of one chain
+spreads over about 3.5 eV, so 48 chains per side resolve a shift of about
+2 eV).  The oracle chains run in a pool of spawned processes.  On the same
+seed the GPU chain repeats the oracle's to the last digit unless an FP32 dE
+falls across an acceptance threshold, which is why independent seeds are used
+here: the comparison is of distributions, not of trajectories."""
 import math
 import multiprocessing as mp
 
@@ -24,8 +28,8 @@ pytestmark = pytest.mark.gpu
 
 DIMS, S, NSH = (12, 12, 12), 5, 2
 N_ANNEAL, N_HOLD, WINDOW = 150, 100, 100
-GPU_SEEDS = list(range(1, 9))
-ORACLE_SEEDS = list(range(101, 109))
+GPU_SEEDS = list(range(1, 49))
+ORACLE_SEEDS = list(range(101, 149))
 
 
 def _schedule():
