@@ -320,13 +320,16 @@ smc_status smc_set_tuning(const smc_tuning *t);
  * SMC_DBG_FAST_BUFFERS (1 or 2 row buffers per column) and
  * SMC_DBG_FAST_STAGING (1: one bulk copy per row; 2: 16-byte cp.async) fix
  * those launch choices of the pair sweep on lattices with four-cell link
- * cells on every axis (0 = automatic); results never depend on them. */
+ * cells on every axis (0 = automatic); SMC_DBG_RESIDENT = 1 keeps the pair
+ * sweep from holding a small lattice in shared memory for a whole call
+ * (0 = automatic).  Results never depend on them. */
 enum {
     SMC_DBG_TIMEOUT_MS = 1,
     SMC_DBG_SKIP_PUBLISH = 2,
     SMC_DBG_FAST_TEAM = 3,
     SMC_DBG_FAST_BUFFERS = 4,
-    SMC_DBG_FAST_STAGING = 5
+    SMC_DBG_FAST_STAGING = 5,
+    SMC_DBG_RESIDENT = 6
 };
 smc_status smc_debug_set(int32_t what, int64_t value);
 

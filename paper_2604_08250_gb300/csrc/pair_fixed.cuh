@@ -70,6 +70,20 @@ __device__ __forceinline__ float ex2_approx(float x)
     return r;
 }
 
+// Histogram words of one shell (SW words of four 8-bit fields).
+template <int SW>
+__device__ __forceinline__ void hadd(uint32_t (&h)[SW], uint32_t v8)
+{
+    h[0] += nib8(v8);
+    if constexpr (SW == 2) h[1] += nib8hi(v8);
+}
+template <int SW>
+__device__ __forceinline__ void hsub(uint32_t (&h)[SW], uint32_t v8)
+{
+    h[0] -= nib8(v8);
+    if constexpr (SW == 2) h[1] -= nib8hi(v8);
+}
+
 // dE_fix of the histogram words H[m][w] against table row `row` (smem or
 // global, 16-byte aligned).
 template <int NSH, int SW>
@@ -117,5 +131,12 @@ struct PairTable {
     std::vector<uint32_t> rows;
 };
 bool build_pair_table(const smc_model *m, int S, PairTable &t);
+
+// The resident sweep (sweep_resident.cu): SMC_ERR_UNSUPPORTED, with nothing
+// enqueued, when the lattice does not fit it.
+smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m, const PairTable &pt,
+                                      int8_t *occ, uint64_t seed, uint32_t replica, uint64_t sweep0, int nsweeps,
+                                      const double *kT, double *e_acc, int64_t *n_acc, cudaStream_t stream);
+int debug_resident();
 
 }  // namespace smc

@@ -17,7 +17,7 @@ static std::mutex g_lock;  // the workspace and parameter blocks are shared
 static thread_local Tuning g_tuning;
 static int64_t g_timeout_ns = 2000LL * 1000 * 1000;
 static int64_t g_skip_tile = -1;
-static int g_fast_team = 0, g_fast_nbuf = 0, g_fast_stage = 0;
+static int g_fast_team = 0, g_fast_nbuf = 0, g_fast_stage = 0, g_resident = 0;
 
 void set_error(const char *fmt, ...)
 {
@@ -39,6 +39,7 @@ int64_t debug_skip_tile() { return g_skip_tile; }
 int debug_fast_team() { return g_fast_team; }
 int debug_fast_nbuf() { return g_fast_nbuf; }
 int debug_fast_stage() { return g_fast_stage; }
+int debug_resident() { return g_resident; }
 
 static Workspace g_ws[64];
 
@@ -334,6 +335,14 @@ smc_status smc_debug_set(int32_t what, int64_t value)
             return SMC_ERR_ARG;
         }
         g_fast_stage = (int)value;
+        return SMC_OK;
+    }
+    if (what == SMC_DBG_RESIDENT) {
+        if (value < 0 || value > 1) {
+            set_error("resident must be 0 or 1");
+            return SMC_ERR_ARG;
+        }
+        g_resident = (int)value;
         return SMC_OK;
     }
     set_error("unknown debug key %d", what);

@@ -77,6 +77,12 @@ struct SweepParams {
         float beta[kMaxBeta];        // MLP and qSRO kernels: 1 / kT; pair kernels: cx = -log2(e) 2^-sigma / kT
         int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
     } temp;
+    // resident kernel: block descriptors, exchange lists, exchange copy of the
+    // lattice (species x 8), window of rows per sublattice, block grid
+    const int *rdesc;
+    const uint32_t *rlists;
+    int8_t *exch;
+    int Wy, Wz, NBy, NBz, rcols, rblob;
     uint32_t qtab[kPairQWords];  // pair kernels: fixed-point table rows (pair_fixed.cuh)
     union {
         int di[kMaxShells * kMaxSpecies * kMaxSpecies * kMaxSpecies];

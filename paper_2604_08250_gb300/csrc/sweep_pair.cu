@@ -86,20 +86,6 @@ struct ColView {
     }
 };
 
-// Histogram words of one shell (SW words of four 8-bit fields).
-template <int SW>
-__device__ __forceinline__ void hadd(uint32_t (&h)[SW], uint32_t v8)
-{
-    h[0] += nib8(v8);
-    if constexpr (SW == 2) h[1] += nib8hi(v8);
-}
-template <int SW>
-__device__ __forceinline__ void hsub(uint32_t (&h)[SW], uint32_t v8)
-{
-    h[0] -= nib8(v8);
-    if constexpr (SW == 2) h[1] -= nib8hi(v8);
-}
-
 // dE_fix of swapping the trial site a (own sublattice, x) with its partner
 // in direction `dir` (bits kx, ky, kz -> vector 2k-1 in half units), from raw
 // species read through a view.  Returns the species A, B and the partner's
@@ -1713,6 +1699,12 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     if (!build_pair_table(m, lats[0].nspecies, pt)) {
         set_error("pair coefficients must be finite");
         return SMC_ERR_ARG;
+    }
+    if (R == 1 && debug_resident() == 0) {
+        // a lattice that fits in the SMs' shared memory stays there
+        st = launch_pair_sweep_resident(lats, m, pt, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc,
+                                        stream);
+        if (st != SMC_ERR_UNSUPPORTED) return st;
     }
     int rowB = 0;
     const bool fast = fast_ok(R, lats, occ, rowB);

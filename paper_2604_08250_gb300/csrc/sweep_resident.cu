@@ -1,0 +1,798 @@
+// sweep_resident.cu -- the pair-model sweep with the lattice resident in
+// shared memory, for lattices whose rows fit in the SMs' shared memory
+// (128^3 cells: 4.2 MB of 34 MB).
+//
+// The same schedule and arithmetic as the streaming kernel of sweep_pair.cu
+// (groups of four mini-steps, one column of link cells per warp, the exact
+// fixed-point dE of pair_fixed.cuh), so the trajectories are the same bit for
+// bit.  What changes is where the rows live.  Each CTA owns a rectangular
+// block of columns and keeps in shared memory every row its columns ever
+// touch (a window of 4 b + 7 rows per axis and sublattice), for the whole
+// launch.  Rows that another CTA also touches are kept consistent through an
+// exchange copy of the lattice in global memory (species x 8):
+//
+//   before group g, a CTA fetches the rows its columns read at g whose last
+//   writer before g (in the sequential order of the groups) is another CTA;
+//   after group g, it publishes the rows its columns wrote at g that another
+//   CTA reads, then releases its progress flag.
+//
+// A CTA starts group g once its 8 neighbouring blocks have released group
+// g - lag (lag 2 for groups with dy >= 1, else 1), the rule of the streaming
+// kernel (every fetched row's last writer is then finished and published,
+// and no row a CTA touches at g is touched by a neighbour at g - 1 when the
+// lag is 2).  The lists of rows are built on the host from the groups'
+// row-level read and write sets.
+//
+// Roles in a CTA: warps 0..nc-1 run the trials of one column each; warp nc
+// (the exchange warp) waits for the neighbours' progress, fetches rows with
+// cp.async, fills their periodic x-halos and releases the CTA's progress.
+// The compute warps publish the rows they wrote themselves.  Two named
+// barriers order them: READY (exchange warp arrives, compute warps wait)
+// before every group and DONE (compute warps arrive, exchange warp waits)
+// after it.  When the next group has lag 2 its rows are fetched while the
+// current group still runs: a fetched row is not written by this CTA's
+// current group, and if this group reads it, it reads the same bytes.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <set>
+#include <vector>
+
+#include "pair_fixed.cuh"
+
+namespace smc {
+
+namespace {
+
+constexpr int kResDesc = 12;  // ints per block descriptor
+
+enum : int { kBarReady = 1, kBarDone = 2 };
+
+__device__ __forceinline__ void named_sync(int id, int n)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void named_arrive(int id, int n)
+{
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+
+#define RD8(off) ((uint32_t)g_smem[(off)])
+
+// dE_fix of the trial at a (ya = shared offset of a, own row) with pa = the
+// partner row (y0 + s_off, z0 + s_off) at x + s_off; rows are rb apart in y
+// and RZ apart in z on both sublattices.
+template <int NSH, int SW>
+__device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb, uint32_t RZ, uint32_t dir,
+                                          uint32_t lut, uint32_t &a8, uint32_t &b8, uint32_t &pb)
+{
+    const int2 L = *(const int2 *)(g_smem + lut + dir * 8u);
+    a8 = RD8(ya);
+    pb = pa + (uint32_t)L.x;
+    b8 = RD8(pb);
+    uint32_t H[NSH][SW];
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int w = 0; w < SW; ++w) H[m][w] = m < 2 ? 0x08080808u : 0x10101010u;
+    hadd<SW>(H[0], a8);
+    hsub<SW>(H[0], b8);
+    hadd<SW>(H[0], RD8(pa));
+    hadd<SW>(H[0], RD8(pa + 1));
+    hadd<SW>(H[0], RD8(pa + rb));
+    hadd<SW>(H[0], RD8(pa + rb + 1));
+    hadd<SW>(H[0], RD8(pa + RZ));
+    hadd<SW>(H[0], RD8(pa + RZ + 1));
+    hadd<SW>(H[0], RD8(pa + RZ + rb));
+    hadd<SW>(H[0], RD8(pa + RZ + rb + 1));
+    const uint32_t ob = ya + (uint32_t)L.y;
+    hsub<SW>(H[0], RD8(ob));
+    hsub<SW>(H[0], RD8(ob + 1));
+    hsub<SW>(H[0], RD8(ob + rb));
+    hsub<SW>(H[0], RD8(ob + rb + 1));
+    hsub<SW>(H[0], RD8(ob + RZ));
+    hsub<SW>(H[0], RD8(ob + RZ + 1));
+    hsub<SW>(H[0], RD8(ob + RZ + rb));
+    hsub<SW>(H[0], RD8(ob + RZ + rb + 1));
+    hadd<SW>(H[1], RD8(ya - 1));
+    hadd<SW>(H[1], RD8(ya + 1));
+    hadd<SW>(H[1], RD8(ya - rb));
+    hadd<SW>(H[1], RD8(ya + rb));
+    hadd<SW>(H[1], RD8(ya - RZ));
+    hadd<SW>(H[1], RD8(ya + RZ));
+    hsub<SW>(H[1], RD8(pb - 1));
+    hsub<SW>(H[1], RD8(pb + 1));
+    hsub<SW>(H[1], RD8(pb - rb));
+    hsub<SW>(H[1], RD8(pb + rb));
+    hsub<SW>(H[1], RD8(pb - RZ));
+    hsub<SW>(H[1], RD8(pb + RZ));
+    if constexpr (NSH >= 3) {
+        hadd<SW>(H[2], RD8(ya - rb - RZ));
+        hadd<SW>(H[2], RD8(ya + rb - RZ));
+        hadd<SW>(H[2], RD8(ya - rb + RZ));
+        hadd<SW>(H[2], RD8(ya + rb + RZ));
+        hadd<SW>(H[2], RD8(ya - rb - 1));
+        hadd<SW>(H[2], RD8(ya - rb + 1));
+        hadd<SW>(H[2], RD8(ya + rb - 1));
+        hadd<SW>(H[2], RD8(ya + rb + 1));
+        hadd<SW>(H[2], RD8(ya - RZ - 1));
+        hadd<SW>(H[2], RD8(ya - RZ + 1));
+        hadd<SW>(H[2], RD8(ya + RZ - 1));
+        hadd<SW>(H[2], RD8(ya + RZ + 1));
+        hsub<SW>(H[2], RD8(pb - rb - RZ));
+        hsub<SW>(H[2], RD8(pb + rb - RZ));
+        hsub<SW>(H[2], RD8(pb - rb + RZ));
+        hsub<SW>(H[2], RD8(pb + rb + RZ));
+        hsub<SW>(H[2], RD8(pb - rb - 1));
+        hsub<SW>(H[2], RD8(pb - rb + 1));
+        hsub<SW>(H[2], RD8(pb + rb - 1));
+        hsub<SW>(H[2], RD8(pb + rb + 1));
+        hsub<SW>(H[2], RD8(pb - RZ - 1));
+        hsub<SW>(H[2], RD8(pb - RZ + 1));
+        hsub<SW>(H[2], RD8(pb + RZ - 1));
+        hsub<SW>(H[2], RD8(pb + RZ + 1));
+    }
+    constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
+    return dot_fixed<NSH, SW>(H, (const uint32_t *)(g_smem + (8u * a8 + b8) * half_row));
+}
+
+// Shared-memory body offset of window row (s, y, z) of a block.
+__device__ __forceinline__ uint32_t res_body(const int *d, int s, int y, int z, int ny, int nz, int Wy, int Wz,
+                                             uint32_t rows, uint32_t rb)
+{
+    int yy = y - d[4 + s], zz = z - d[6 + s];
+    yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
+    zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
+    return rows + (uint32_t)((s * Wz + zz) * Wy + yy) * rb + 16u;
+}
+
+// One look at the 8 neighbouring blocks' progress; bounded wait loop around it.
+__device__ bool res_wait(const SweepParams &P, int by, int bz, uint32_t need, int lane)
+{
+    const uint32_t *fp = nullptr;
+    if (lane < 9 && lane != 4) {
+        int nby = by + (lane % 3) - 1, nbz = bz + (lane / 3) - 1;
+        nby = nby < 0 ? nby + P.NBy : (nby >= P.NBy ? nby - P.NBy : nby);
+        nbz = nbz < 0 ? nbz + P.NBz : (nbz >= P.NBz ? nbz - P.NBz : nbz);
+        fp = P.flags + nbz * P.NBy + nby;
+    }
+    const uint64_t t0 = global_ns();
+    for (;;) {
+        const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
+        if (__all_sync(0xffffffffu, ok)) return true;
+        int stop = 0;
+        if (lane == 0) {
+            if (ld_volatile_i32(P.abort_flag)) {
+                stop = 1;
+            } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
+                atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+                atomicExch(P.abort_flag, 1);
+                stop = 1;
+            }
+        }
+        if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        __nanosleep(32);
+    }
+}
+
+// Copies the rows of list entries [e0, e1) (slot << 21 | row) between the
+// exchange copy and shared memory (fetch: global -> shared with 16-byte
+// cp.async; publish: shared -> global), the warp's lanes over (entry, chunk).
+__device__ __forceinline__ void res_fetch(const SweepParams &P, const uint32_t *ent, int n, uint32_t rows_abs,
+                                          uint32_t rb, int nx, int lane)
+{
+    const int cpr = nx >> 4;
+    for (int q = lane; q < n * cpr; q += 32) {
+        const int e = q / cpr, c = q - e * cpr;
+        const uint32_t v = ent[e], slot = v >> 21, row = v & 0x1FFFFFu;
+        const int8_t *src = P.exch + (size_t)row * nx + 16 * c;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(rows_abs + slot * rb + 16u + 16u * c),
+                     "l"(src)
+                     : "memory");
+    }
+}
+__device__ __forceinline__ void res_halos(const uint32_t *ent, int n, uint32_t rows, uint32_t rb, int nx, int lane)
+{
+    for (int q = lane; q < 2 * n; q += 32) {
+        const uint32_t body = rows + (ent[q >> 1] >> 21) * rb + 16u;
+        if (q & 1)
+            *(unsigned *)(g_smem + body + nx) = *(const unsigned *)(g_smem + body);
+        else
+            *(unsigned *)(g_smem + body - 4) = *(const unsigned *)(g_smem + body + nx - 4);
+    }
+}
+
+template <bool IS_INT, int NSH, int SW>
+__global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int nc = nwarp - 1, nbar = nwarp * 32;
+    const int blk = blockIdx.x;
+    const RepDesc &RD = P.rep[0];
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
+    const int Wy = P.Wy, Wz = P.Wz;
+    const uint32_t rb = (uint32_t)P.rowB, RZ = (uint32_t)Wy * rb;
+    const int *d = P.rdesc + blk * kResDesc;
+    const int by = blk % P.NBy, bz = blk / P.NBy;
+    const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    __shared__ int s_abort;
+    // shared memory: [table][8 direction offsets][rows][lists][Philox words per compute warp]
+    const int qwords = kQRows * P.qrow;
+    const uint32_t lut = (uint32_t)qwords * 4u;
+    const uint32_t rows = lut + 64u;
+    const int nslots = 2 * Wy * Wz;
+    const uint32_t lists = rows + (uint32_t)nslots * rb;
+    const int nk = (NLx + 31) >> 5;
+    const uint32_t wsm0 = lists + (uint32_t)P.rblob * 4u;
+    for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+    if (tid < 8) {
+        const int kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
+        int2 e;
+        e.x = ky * (int)rb + kz * (int)RZ + kx;
+        e.y = (ky - 1) * (int)rb + (kz - 1) * (int)RZ + kx - 1;
+        *(int2 *)(g_smem + lut + (uint32_t)tid * 8u) = e;
+    }
+    const uint32_t *gl = P.rlists + d[8];
+    uint32_t *L = (uint32_t *)(g_smem + lists);
+    for (int i = tid; i < d[9]; i += blockDim.x) L[i] = gl[i];
+    if (tid == 0) s_abort = 0;
+    // the window's rows from the exchange copy (species x 8)
+    {
+        const int cpr = nx >> 4;
+        for (int q = tid; q < nslots * cpr; q += blockDim.x) {
+            const int slot = q / cpr, c = q - slot * cpr;
+            const int s = slot / (Wy * Wz), yy = slot % Wy, zz = (slot / Wy) % Wz;
+            int y = d[4 + s] + yy, z = d[6 + s] + zz;
+            y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
+            z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
+            const int8_t *src = P.exch + ((size_t)((s * nz + z) * ny + y)) * nx + 16 * c;
+            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + rows + (uint32_t)slot * rb + 16u +
+                                                                            16u * c),
+                         "l"(src)
+                         : "memory");
+        }
+        asm volatile("cp.async.wait_all;" ::: "memory");
+        __syncthreads();
+        for (int q = tid; q < 2 * nslots; q += blockDim.x) {
+            const uint32_t body = rows + (uint32_t)(q >> 1) * rb + 16u;
+            if (q & 1)
+                *(unsigned *)(g_smem + body + nx) = *(const unsigned *)(g_smem + body);
+            else
+                *(unsigned *)(g_smem + body - 4) = *(const unsigned *)(g_smem + body + nx - 4);
+        }
+        __syncthreads();
+    }
+    const int total = P.nsweeps * 32;
+    // list header: fetch offsets [0..33), publish offsets [33 .. 33 + 32 nc + 1),
+    // then the final rows' offset and count
+    const uint32_t *fo = L, *po = L + 33;
+    const uint32_t fin0 = L[33 + 32 * nc + 1], fin1 = L[33 + 32 * nc + 2];
+
+    if (warp == nc) {
+        // ---------------- exchange warp ----------------
+        named_arrive(kBarReady, nbar);  // group 0: the window was loaded from the exchange copy
+        bool pre = false, aborted = false;
+        for (int gs = 0; gs < total && !aborted; ++gs) {
+            const int nxt = gs + 1, gn = nxt & 31;
+            const uint32_t need = (uint32_t)nxt + 1 - ((gn & 3) ? 2u : 1u);
+            if (nxt < total && (gn & 3)) {
+                // lag 2: the next group's rows can come in while this one runs
+                if (!res_wait(P, by, bz, need, lane)) {
+                    aborted = true;
+                    break;
+                }
+                res_fetch(P, L + fo[gn], (int)(fo[gn + 1] - fo[gn]), smem0 + rows, rb, nx, lane);
+                pre = true;
+            }
+            named_sync(kBarDone, nbar);  // group gs done and its rows published
+            if (lane == 0 && blk != P.skip_tile) {
+                __threadfence();
+                st_release_u32(P.flags + blk, (uint32_t)gs + 1);
+            }
+            if (nxt < total) {
+                if (!pre) {
+                    if (!res_wait(P, by, bz, need, lane)) {
+                        aborted = true;
+                        break;
+                    }
+                    res_fetch(P, L + fo[gn], (int)(fo[gn + 1] - fo[gn]), smem0 + rows, rb, nx, lane);
+                }
+                asm volatile("cp.async.wait_all;" ::: "memory");
+                __syncwarp();
+                res_halos(L + fo[gn], (int)(fo[gn + 1] - fo[gn]), rows, rb, nx, lane);
+                __syncwarp();
+                named_arrive(kBarReady, nbar);
+                pre = false;
+            }
+        }
+        if (aborted) {
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (lane == 0) *(volatile int *)&s_abort = 1;
+            __syncwarp();
+            named_arrive(kBarReady, nbar);  // the compute warps wake up and leave
+            return;
+        }
+    } else {
+        // ---------------- compute warps ----------------
+        const bool active = warp < d[2] * d[3];
+        const int cy = d[0] + warp % max(d[2], 1), cz = d[1] + warp / max(d[2], 1);
+        const uint32_t wsm = wsm0 + (uint32_t)warp * (uint32_t)nk * 512u;
+        long long accE = 0, accN = 0;
+        for (int gs = 0; gs < total; ++gs) {
+            const int t = gs >> 5, g = gs & 31;
+            const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4, soff = sub == 0 ? -1 : 0;
+            const int y0 = 4 * cy + dy, z0 = 4 * cz + dz;
+            const uint64_t sweep = P.sweep0 + (uint64_t)t;
+            if (active) {
+                // Philox words of this column's link cells for this group
+                const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
+                const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+                uint32_t *wp = (uint32_t *)(g_smem + wsm);
+#pragma unroll 1
+                for (int k = 0; k < nk; ++k) {
+                    const int i = lane + 32 * k;
+                    if (i < NLx) {
+                        const U4 w = philox10(
+                            U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
+                        wp[(k * 4 + 0) * 32 + lane] = w.x;
+                        wp[(k * 4 + 1) * 32 + lane] = w.y;
+                        wp[(k * 4 + 2) * 32 + lane] = w.z;
+                        wp[(k * 4 + 3) * 32 + lane] = w.w;
+                    }
+                }
+            }
+            named_sync(kBarReady, nbar);
+            if (*(volatile int *)&s_abort) return;
+            if (active) {
+                float cx = 0.f;
+                int2 ti = make_int2(0, 0);
+                if constexpr (IS_INT)
+                    ti = P.temp.tabinfo[P.beta_stride ? t : 0];
+                else
+                    cx = P.temp.beta[P.beta_stride ? t : 0];
+                const uint32_t ownb = res_body(d, sub, y0, z0, ny, nz, Wy, Wz, rows, rb);
+                const uint32_t parb = res_body(d, 1 - sub, y0 + soff, z0 + soff, ny, nz, Wy, Wz, rows, rb);
+                // the 5 rows a mini-step writes (own row, partner 2 x 2), for the halo refresh
+                uint32_t hrow = ownb;
+                if (lane >= 2 && lane < 10) {
+                    const int k = (lane - 2) >> 1;
+                    hrow = parb + (uint32_t)(k & 1) * rb + (uint32_t)(k >> 1) * RZ;
+                }
+                for (int dx = 0; dx < 4; ++dx) {
+#pragma unroll 1
+                    for (int k = 0; k < nk; ++k) {
+                        const int i = lane + 32 * k;
+                        if (i >= NLx) continue;
+                        const int x = 4 * i + dx;
+                        const uint32_t w =
+                            *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
+                        uint32_t a8, b8, pb;
+                        const uint32_t ya = ownb + (uint32_t)x;
+                        const int32_t dE =
+                            res_dE<NSH, SW>(ya, parb + (uint32_t)(x + soff), rb, RZ, w >> kRBits, lut, a8, b8, pb);
+                        if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
+                            const int xb = x + soff + (int)(w >> 31);
+                            pb += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
+                            g_smem[ya] = (unsigned char)b8;
+                            g_smem[pb] = (unsigned char)a8;
+                            accE += dE;
+                            accN += 1;
+                        }
+                    }
+                    __syncwarp();
+                    if (lane < 10) {
+                        if (lane & 1)
+                            *(unsigned *)(g_smem + hrow + nx) = *(const unsigned *)(g_smem + hrow);
+                        else
+                            *(unsigned *)(g_smem + hrow - 4) = *(const unsigned *)(g_smem + hrow + nx - 4);
+                    }
+                    __syncwarp();
+                }
+                // publish the rows this column wrote that other blocks read
+                const uint32_t *pe = L + po[g * nc + warp];
+                const int np = (int)(po[g * nc + warp + 1] - po[g * nc + warp]);
+                const int cpr = nx >> 4;
+                for (int q = lane; q < np * cpr; q += 32) {
+                    const int e = q / cpr, c = q - e * cpr;
+                    const uint32_t v = pe[e], slot = v >> 21, row = v & 0x1FFFFFu;
+                    *((int4 *)(P.exch + (size_t)row * nx) + c) =
+                        *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
+                }
+            }
+            named_arrive(kBarDone, nbar);
+        }
+        const long long e_w = warp_sum<long long>(accE), n_w = warp_sum<long long>(accN);
+        if (lane == 0) {
+            P.part_e[blk * nc + warp] = (double)e_w;
+            P.part_n[blk * nc + warp] = n_w;
+        }
+    }
+    __syncthreads();
+    // final rows, back to plain species in the caller's array
+    for (int q = tid; q < (int)(fin1 * (uint32_t)(nx >> 4)); q += blockDim.x) {
+        const int cpr = nx >> 4, e = q / cpr, c = q - e * cpr;
+        const uint32_t v = L[fin0 + e], slot = v >> 21, row = v & 0x1FFFFFu;
+        const int4 w = *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
+        int4 o;
+        o.x = (int)(((uint32_t)w.x >> 3) & 0x07070707u);
+        o.y = (int)(((uint32_t)w.y >> 3) & 0x07070707u);
+        o.z = (int)(((uint32_t)w.z >> 3) & 0x07070707u);
+        o.w = (int)(((uint32_t)w.w >> 3) & 0x07070707u);
+        *((int4 *)(RD.occ + (size_t)row * nx) + c) = o;
+    }
+    // per-warp partial sums; the last CTA reduces them in order
+    __shared__ int s_last;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(P.ticket, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last || tid != 0) return;
+    __threadfence();
+    double se = 0.0;
+    long long sn = 0;
+    for (int k = 0; k < (int)gridDim.x * nc; ++k) {
+        se += __ldcg(P.part_e + k);
+        sn += __ldcg(P.part_n + k);
+    }
+    if (RD.e_acc) *RD.e_acc += se * P.escale;
+    if (RD.n_acc) *RD.n_acc += sn;
+}
+
+// ---------------------------------------------------------------------------
+// Host: block shape, windows and exchange lists.
+// ---------------------------------------------------------------------------
+struct ResPlan {
+    int ok = 0, by = 0, bz = 0, NBy = 0, NBz = 0, nblocks = 0, nc = 0, Wy = 0, Wz = 0, rowB = 0, blob = 0;
+    size_t smem = 0;
+    std::vector<int> desc;
+    std::vector<uint32_t> lists;
+    const void *kernel = nullptr;
+};
+
+// Rows (sub, y, z) -> id (sub * nz + z) * ny + y read and written by column
+// (cy, cz) in group g (the same sets as the streaming kernel stages).
+void column_rows(int cy, int cz, int g, int ny, int nz, int nsh, std::vector<int> &R, std::vector<int> &W)
+{
+    const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4, soff = sub == 0 ? -1 : 0;
+    const int y0 = 4 * cy + dy, z0 = 4 * cz + dz;
+    auto id = [&](int s, int y, int z) {
+        y = ((y % ny) + ny) % ny;
+        z = ((z % nz) + nz) % nz;
+        return (s * nz + z) * ny + y;
+    };
+    R.clear();
+    W.clear();
+    for (int b = -1; b <= 1; ++b)
+        for (int a = -1; a <= 1; ++a) R.push_back(id(sub, y0 + a, z0 + b));
+    for (int sz = 0; sz < 4; ++sz)
+        for (int sy = 0; sy < 4; ++sy) {
+            if (nsh < 3 && (sy == 0 || sy == 3) && (sz == 0 || sz == 3)) continue;
+            R.push_back(id(1 - sub, y0 + soff - 1 + sy, z0 + soff - 1 + sz));
+        }
+    W.push_back(id(sub, y0, z0));
+    for (int b = 0; b < 2; ++b)
+        for (int a = 0; a < 2; ++a) W.push_back(id(1 - sub, y0 + soff + a, z0 + soff + b));
+}
+
+template <bool IS_INT>
+const void *pick_resident(int nsh, int sw)
+{
+    if (nsh >= 3)
+        return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 3, 2> : (const void *)k_sweep_resident<IS_INT, 3, 1>;
+    return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 2, 2> : (const void *)k_sweep_resident<IS_INT, 2, 1>;
+}
+
+// Builds the plan for one lattice, or leaves ok = 0 when the lattice does not
+// fit (the streaming kernel then runs).
+template <bool IS_INT>
+smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace *ws, ResPlan &rp)
+{
+    rp = ResPlan();
+    const int nx = lat.nx, ny = lat.ny, nz = lat.nz;
+    const int NLy = ny / 4, NLz = nz / 4, nsh = pt.nsh;
+    const int rowB = nx + 32;
+    const void *kern = pick_resident<IS_INT>(pt.nsh, pt.sw);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
+    // block shapes with at most 8 columns, at most one CTA per SM and at
+    // least 3 blocks per axis; the fewest columns per block (the shortest
+    // group), then the fewest rows held.  A tuned tile shape (tile_y,
+    // tile_z) selects the block shape.
+    const int shapes[][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}, {1, 4}, {4, 1}, {2, 3}, {3, 2}, {2, 4}, {4, 2}, {1, 8}, {8, 1}};
+    const Tuning tu = current_tuning();
+    int best = -1, best_nc = 1 << 30, best_rows = 1 << 30;
+    for (int i = 0; i < (int)(sizeof shapes / sizeof shapes[0]); ++i) {
+        const int by = shapes[i][0], bz = shapes[i][1];
+        if (tu.tile_y > 0 && tu.tile_z > 0 && (by != tu.tile_y || bz != tu.tile_z)) continue;
+        const int NBy = (NLy + by - 1) / by, NBz = (NLz + bz - 1) / bz;
+        if (NBy < 3 || NBz < 3 || NBy * NBz > ws->num_sms) continue;
+        const int Wy = 4 * by + 7, Wz = 4 * bz + 7;
+        if (Wy >= ny || Wz >= nz) continue;
+        const int nrows = 2 * Wy * Wz, nc = by * bz;
+        if (nc < best_nc || (nc == best_nc && nrows < best_rows)) {
+            best = i;
+            best_nc = nc;
+            best_rows = nrows;
+        }
+    }
+    if (best < 0 || nx % 16 != 0) return SMC_OK;
+    const int by = shapes[best][0], bz = shapes[best][1];
+    rp.by = by;
+    rp.bz = bz;
+    rp.NBy = (NLy + by - 1) / by;
+    rp.NBz = (NLz + bz - 1) / bz;
+    rp.nblocks = rp.NBy * rp.NBz;
+    rp.nc = by * bz;
+    rp.Wy = 4 * by + 7;
+    rp.Wz = 4 * bz + 7;
+    rp.rowB = rowB;
+    const int nrows_lat = 2 * ny * nz;
+    auto block_of = [&](int cy, int cz) { return (cz / bz) * rp.NBy + (cy / by); };
+    // per row: writer block at every group (-1 = none), readers' blocks
+    std::vector<int> wblk((size_t)nrows_lat * 32, -1);
+    std::vector<std::vector<int>> rblk(nrows_lat);
+    std::vector<int> R, W;
+    for (int g = 0; g < 32; ++g)
+        for (int cz = 0; cz < NLz; ++cz)
+            for (int cy = 0; cy < NLy; ++cy) {
+                column_rows(cy, cz, g, ny, nz, nsh, R, W);
+                const int b = block_of(cy, cz);
+                for (int r : W) wblk[(size_t)r * 32 + g] = b;
+                for (int r : R) rblk[r].push_back(b);
+            }
+    for (auto &v : rblk) {
+        std::sort(v.begin(), v.end());
+        v.erase(std::unique(v.begin(), v.end()), v.end());
+    }
+    // last writer of row r before group g (cyclic over the sweep)
+    auto last_writer = [&](int r, int g) {
+        for (int h = g - 1; h >= g - 32; --h) {
+            const int b = wblk[(size_t)r * 32 + ((h + 32) & 31)];
+            if (b >= 0) return b;
+        }
+        return -1;
+    };
+    rp.desc.assign((size_t)rp.nblocks * kResDesc, 0);
+    rp.lists.clear();
+    const int nc = rp.nc;
+    for (int blk = 0; blk < rp.nblocks; ++blk) {
+        const int bky = blk % rp.NBy, bkz = blk / rp.NBy;
+        const int cy0 = bky * by, cz0 = bkz * bz;
+        const int ncy = std::min(by, NLy - cy0), ncz = std::min(bz, NLz - cz0);
+        int *dd = &rp.desc[(size_t)blk * kResDesc];
+        dd[0] = cy0;
+        dd[1] = cz0;
+        dd[2] = ncy;
+        dd[3] = ncz;
+        dd[4] = 4 * cy0 - 1;  // sublattice 0 rows y in [4 cy0 - 1, 4 cy0 + 4 by + 5]
+        dd[5] = 4 * cy0 - 2;  // sublattice 1 rows y in [4 cy0 - 2, 4 cy0 + 4 by + 4]
+        dd[6] = 4 * cz0 - 1;
+        dd[7] = 4 * cz0 - 2;
+        auto slot_of = [&](int r) -> int {
+            const int s = r / (ny * nz), z = (r / ny) % nz, y = r % ny;
+            int yy = y - dd[4 + s], zz = z - dd[6 + s];
+            yy = ((yy % ny) + ny) % ny;
+            zz = ((zz % nz) + nz) % nz;
+            if (yy >= rp.Wy || zz >= rp.Wz) return -1;
+            return (s * rp.Wz + zz) * rp.Wy + yy;
+        };
+        std::vector<uint32_t> hdr(33 + 32 * nc + 1 + 2, 0), body;
+        auto entry = [&](int r) -> uint32_t {
+            const int sl = slot_of(r);
+            return ((uint32_t)sl << 21) | (uint32_t)r;
+        };
+        bool fits = true;
+        // fetch lists per group
+        for (int g = 0; g < 32; ++g) {
+            hdr[g] = (uint32_t)(hdr.size() + body.size());
+            std::set<int> fs;
+            for (int k = 0; k < ncy * ncz; ++k) {
+                column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
+                for (int r : R) {
+                    if (slot_of(r) < 0) fits = false;
+                    if (last_writer(r, g) != blk) fs.insert(r);
+                }
+            }
+            for (int r : fs) body.push_back(entry(r));
+        }
+        hdr[32] = (uint32_t)(hdr.size() + body.size());
+        // publish lists per group and compute warp: written rows another block reads
+        for (int g = 0; g < 32; ++g)
+            for (int k = 0; k < nc; ++k) {
+                hdr[33 + g * nc + k] = (uint32_t)(hdr.size() + body.size());
+                if (k >= ncy * ncz) continue;
+                column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
+                for (int r : W) {
+                    bool other = false;
+                    for (int b : rblk[r]) other |= b != blk;
+                    if (other) body.push_back(entry(r));
+                }
+            }
+        hdr[33 + 32 * nc] = (uint32_t)(hdr.size() + body.size());
+        // final rows: those whose last writer in the sweep is this block
+        hdr[33 + 32 * nc + 1] = (uint32_t)(hdr.size() + body.size());
+        uint32_t nfin = 0;
+        for (int r = 0; r < nrows_lat; ++r)
+            if (last_writer(r, 32) == blk) {
+                if (slot_of(r) < 0) fits = false;
+                body.push_back(entry(r));
+                ++nfin;
+            }
+        hdr[33 + 32 * nc + 2] = nfin;
+        if (!fits) return SMC_OK;  // a row outside the window (not expected)
+        dd[8] = (int)rp.lists.size();
+        dd[9] = (int)(hdr.size() + body.size());
+        rp.blob = std::max(rp.blob, dd[9]);
+        rp.lists.insert(rp.lists.end(), hdr.begin(), hdr.end());
+        rp.lists.insert(rp.lists.end(), body.begin(), body.end());
+    }
+    const int nk = (nx / 4 + 31) / 32;
+    const size_t smem = (size_t)kQRows * pt.rw * 4 + 64 + (size_t)2 * rp.Wy * rp.Wz * rowB +
+                        ((size_t)rp.blob * 4 + 15) / 16 * 16 + (size_t)nc * nk * 512;
+    if (smem > dyn_max) return SMC_OK;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + 1) * 32, smem);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+    if (per_sm < 1 || rp.nblocks > per_sm * ws->num_sms) return SMC_OK;
+    rp.smem = smem;
+    rp.kernel = kern;
+    rp.ok = 1;
+    return SMC_OK;
+}
+
+__global__ void k_occ_to_exch(const int8_t *occ, int8_t *exch, long long n, int S, int *status)
+{
+    const long long nw = n >> 2;
+    const uint32_t *s4 = (const uint32_t *)occ;
+    uint32_t *d4 = (uint32_t *)exch;
+    const uint32_t lim = (uint32_t)(0x80 - S) * 0x01010101u;
+    bool bad = false;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nw; i += (long long)gridDim.x * blockDim.x) {
+        const uint32_t v = s4[i];
+        bad |= ((v | (v + lim)) & 0x80808080u) != 0u;
+        d4[i] = (v & 0x07070707u) << 3;
+    }
+    if (bad) atomicCAS(status, 0, (int)SMC_ERR_ARG);
+}
+
+}  // namespace
+
+// The resident sweep, when the lattice fits (single replica, four-cell link
+// cells on every axis, rows of a multiple of 16 bytes).  Returns
+// SMC_ERR_UNSUPPORTED, having enqueued nothing, when it does not apply.
+smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m, const PairTable &pt,
+                                      int8_t *occ, uint64_t seed, uint32_t replica, uint64_t sweep0, int nsweeps,
+                                      const double *kT, double *e_acc, int64_t *n_acc, cudaStream_t stream)
+{
+    if (lc_edge(lat->nx) != 4 || lc_edge(lat->ny) != 4 || lc_edge(lat->nz) != 4 || lat->nx % 16 ||
+        (uintptr_t)occ % 16 || lat->nx > 1024)
+        return SMC_ERR_UNSUPPORTED;
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    const bool is_int = m->kind == SMC_PAIR_I32;
+    static std::vector<long long> key_cached;
+    static ResPlan plan_cached;
+    const Tuning tu = current_tuning();
+    std::vector<long long> key = {lat->nx, lat->ny, lat->nz, pt.nsh, pt.sw, is_int, ws->device, ws->num_sms,
+                                  tu.tile_y, tu.tile_z};
+    if (key != key_cached) {
+        ResPlan rp;
+        st = is_int ? build_res_plan<true>(*lat, pt, ws, rp) : build_res_plan<false>(*lat, pt, ws, rp);
+        if (st != SMC_OK) return st;
+        plan_cached = rp;
+        key_cached = key;
+    }
+    const ResPlan &rp = plan_cached;
+    if (!rp.ok) return SMC_ERR_UNSUPPORTED;
+
+    static SweepParams P;
+    memset(&P, 0, sizeof P);
+    P.R = 1;
+    P.G = 32;
+    P.Lx = P.Ly = P.Lz = 4;
+    P.nshells = m->nshells;
+    P.S = lat->nspecies;
+    P.seed = seed;
+    P.timeout_ns = debug_timeout_ns();
+    P.skip_tile = (int)debug_skip_tile();
+    P.rowB = rp.rowB;
+    P.Wy = rp.Wy;
+    P.Wz = rp.Wz;
+    P.NBy = rp.NBy;
+    P.NBz = rp.NBz;
+    P.rcols = rp.nc;
+    P.rblob = rp.blob;
+    RepDesc &d = P.rep[0];
+    d.occ = occ;
+    d.e_acc = e_acc;
+    d.n_acc = (long long *)n_acc;
+    d.nx = lat->nx;
+    d.ny = lat->ny;
+    d.nz = lat->nz;
+    d.NLx = d.nx / 4;
+    d.NLy = d.ny / 4;
+    d.NLz = d.nz / 4;
+    d.rep = replica;
+    P.qrow = pt.rw;
+    P.escale = pt.scale;
+    memcpy(P.qtab, pt.rows.data(), pt.rows.size() * 4);
+
+    // per-sweep temperatures: one launch per kMaxBeta sweeps
+    bool constant = true;
+    for (int t = 1; t < nsweeps; ++t)
+        if (kT[t] != kT[0]) constant = false;
+    const int cap = is_int ? kMaxBeta / 2 : kMaxBeta;
+    const int chunk = constant ? nsweeps : cap;
+    std::vector<uint32_t> tabs;
+    std::vector<std::pair<double, int2>> tindex;
+    auto table_of = [&](double kt) -> int2 {
+        for (auto &p : tindex)
+            if (p.first == kt) return p.second;
+        std::vector<uint32_t> t = int_table(m->unit_ev, kt);
+        int2 ti = make_int2((int)tabs.size(), (int)t.size());
+        tabs.insert(tabs.end(), t.begin(), t.end());
+        tindex.push_back({kt, ti});
+        return ti;
+    };
+    if (is_int)
+        for (int t = 0; t < nsweeps; ++t) table_of(kT[t]);
+
+    // workspace: [flags | part_e | part_n | ticket, abort | descriptors | lists | tables | exchange copy]
+    const size_t N = 2 * (size_t)lat->nx * lat->ny * lat->nz;
+    const size_t nb = (size_t)rp.nblocks, np = nb * rp.nc;
+    const size_t off_flags = 0, off_pe = ((nb * 4 + 15) / 16) * 16, off_pn = off_pe + np * 8;
+    const size_t off_misc = off_pn + np * 8, off_desc = off_misc + 16;
+    const size_t off_lists = off_desc + ((rp.desc.size() * 4 + 15) / 16) * 16;
+    const size_t off_tab = off_lists + ((rp.lists.size() * 4 + 15) / 16) * 16;
+    const size_t off_exch = off_tab + ((tabs.size() * 4 + 255) / 256) * 256;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_exch + N, &st);
+    if (!scr) return st;
+    P.flags = (uint32_t *)(scr + off_flags);
+    P.part_e = (double *)(scr + off_pe);
+    P.part_n = (long long *)(scr + off_pn);
+    P.ticket = (unsigned *)(scr + off_misc);
+    P.abort_flag = (int *)(scr + off_misc + 4);
+    P.status = ws->status;
+    P.rdesc = (const int *)(scr + off_desc);
+    P.rlists = (const uint32_t *)(scr + off_lists);
+    P.tab = (const uint32_t *)(scr + off_tab);
+    P.exch = (int8_t *)(scr + off_exch);
+    cudaError_t e = cudaMemcpyAsync(scr + off_desc, rp.desc.data(), rp.desc.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(scr + off_lists, rp.lists.data(), rp.lists.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e == cudaSuccess && !tabs.empty())
+        e = cudaMemcpyAsync(scr + off_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(resident plan)");
+    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+        const int nc = std::min(chunk, nsweeps - t0);
+        P.sweep0 = sweep0 + (uint64_t)t0;
+        P.nsweeps = nc;
+        P.beta_stride = constant ? 0 : 1;
+        for (int t = 0; t < (constant ? 1 : nc); ++t) {
+            if (is_int)
+                P.temp.tabinfo[t] = table_of(kT[t0 + t]);
+            else
+                P.temp.beta[t] = (float)(-1.4426950408889634 * pt.scale / kT[t0 + t]);
+        }
+        e = cudaMemsetAsync(scr, 0, off_desc, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(resident scratch)");
+        const long long nw = (long long)(N / 4);
+        const int grid = (int)std::max<long long>(1, std::min<long long>((nw + 255) / 256, (long long)ws->num_sms * 8));
+        k_occ_to_exch<<<grid, 256, 0, stream>>>(occ, P.exch, (long long)N, lat->nspecies, P.status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return cuda_fail(e, "k_occ_to_exch");
+        void *args[] = {(void *)&P};
+        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + 1) * 32), args, rp.smem, stream);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(resident sweep)");
+    }
+    return SMC_OK;
+}
+
+}  // namespace smc

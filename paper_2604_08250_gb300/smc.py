@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(PKG, "libsmc.so")
 
 SMC_OK, SMC_ERR_ARG, SMC_ERR_UNSUPPORTED, SMC_ERR_CUDA, SMC_ERR_TIMEOUT, SMC_ERR_STATE = 0, -1, -2, -3, -4, -5
 PAIR_I32, PAIR_F32, MLP_BF16, PAIR_F32_MLP_BF16, QSRO_F32, MLPNET_BF16 = 0, 1, 2, 3, 4, 5
-DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH, DBG_FAST_TEAM, DBG_FAST_BUFFERS, DBG_FAST_STAGING = 1, 2, 3, 4, 5
+DBG_TIMEOUT_MS, DBG_SKIP_PUBLISH, DBG_FAST_TEAM, DBG_FAST_BUFFERS, DBG_FAST_STAGING, DBG_RESIDENT = 1, 2, 3, 4, 5, 6
 MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 
 # Every symbol declared in include/smc.h.
