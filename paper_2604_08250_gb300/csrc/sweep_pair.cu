@@ -756,16 +756,16 @@ __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rb
 // Team synchronisation: the tw warps that share a column meet at named
 // barrier tb (1 + team index in the CTA); one warp needs only __syncwarp.
 // team_and also returns the AND of the threads' predicates.
+// (bar.sync and bar.red are warp-aligned: the warp reconverges first.)
 __device__ __forceinline__ void team_sync(int tw, int tb)
 {
-    if (tw == 1)
-        __syncwarp();
-    else
-        asm volatile("bar.sync %0, %1;" ::"r"(tb), "r"(tw * 32) : "memory");
+    __syncwarp();
+    if (tw > 1) asm volatile("bar.sync %0, %1;" ::"r"(tb), "r"(tw * 32) : "memory");
 }
 __device__ __forceinline__ bool team_and(int tw, int tb, bool p)
 {
     if (tw == 1) return __all_sync(0xffffffffu, p);
+    __syncwarp();
     uint32_t r;
     asm volatile(
         "{\n\t.reg .pred q, d;\n\t"

@@ -23,15 +23,18 @@
 // lag is 2).  The lists of rows are built on the host from the groups'
 // row-level read and write sets.
 //
-// Roles in a CTA: warps 0..nc-1 run the trials of one column each; warp nc
-// (the exchange warp) waits for the neighbours' progress, fetches rows with
-// cp.async, fills their periodic x-halos and releases the CTA's progress.
-// The compute warps publish the rows they wrote themselves.  Two named
-// barriers order them: READY (exchange warp arrives, compute warps wait)
-// before every group and DONE (compute warps arrive, exchange warp waits)
-// after it.  When the next group has lag 2 its rows are fetched while the
-// current group still runs: a fetched row is not written by this CTA's
-// current group, and if this group reads it, it reads the same bytes.
+// Roles in a CTA: warps 0..nc-1 run the trials of one column each and
+// publish the rows they wrote; warp nc (the exchange warp) prepares the next
+// group while the current one runs -- it waits for the neighbours' progress,
+// fetches rows with cp.async, fills their periodic x-halos and arrives on
+// READY; warp nc + 1 (the release warp) releases the CTA's progress flag once
+// every compute warp has counted the group as done.  A fetch for group g + 1
+// may land while group g runs: a fetched row is not written by this CTA's
+// group g, and if group g reads it, it reads the same bytes.  The exchange
+// warp never runs more than one group ahead (it waits until the compute
+// warps finished g - 1 before it fetches for g + 1), and the READY barriers
+// alternate by group parity so that its arrivals for consecutive groups
+// never meet in one barrier.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -47,14 +50,22 @@ namespace {
 
 constexpr int kResDesc = 12;  // ints per block descriptor
 
-enum : int { kBarReady = 1, kBarDone = 2 };
+// READY barriers, alternating by group parity: the exchange warp may arrive
+// for group g + 1 before every compute warp arrived for group g, never for
+// g + 2 (it waits until the compute warps finished g), so one barrier per
+// parity keeps the arrivals of consecutive groups apart.
+__device__ __forceinline__ int bar_ready(int gs) { return 1 + (gs & 1); }
 
+// bar.sync / bar.arrive are the warp-aligned barrier forms: every lane of
+// the warp must execute them together, so the warp reconverges first.
 __device__ __forceinline__ void named_sync(int id, int n)
 {
+    __syncwarp();
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 __device__ __forceinline__ void named_arrive(int id, int n)
 {
+    __syncwarp();
     asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
@@ -64,12 +75,14 @@ __device__ __forceinline__ void named_arrive(int id, int n)
 // partner row (y0 + s_off, z0 + s_off) at x + s_off; rows are rb apart in y
 // and RZ apart in z on both sublattices.
 template <int NSH, int SW>
-__device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb, uint32_t RZ, uint32_t dir,
-                                          uint32_t lut, uint32_t &a8, uint32_t &b8, uint32_t &pb)
+__device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb, uint32_t RZ, uint32_t w,
+                                          uint32_t &a8, uint32_t &b8, uint32_t &pb)
 {
-    const int2 L = *(const int2 *)(g_smem + lut + dir * 8u);
+    // partner direction = w >> 29 = (kx, ky, kz): b = pa + ky rb + kz RZ + kx,
+    // and b's own-sublattice neighbours start (ky - 1, kz - 1, kx - 1) from a
+    const uint32_t offb = ((w >> 30) & 1u) * rb + ((w >> 29) & 1u) * RZ + (w >> 31);
     a8 = RD8(ya);
-    pb = pa + (uint32_t)L.x;
+    pb = pa + offb;
     b8 = RD8(pb);
     uint32_t H[NSH][SW];
 #pragma unroll
@@ -86,7 +99,7 @@ __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb,
     hadd<SW>(H[0], RD8(pa + RZ + 1));
     hadd<SW>(H[0], RD8(pa + RZ + rb));
     hadd<SW>(H[0], RD8(pa + RZ + rb + 1));
-    const uint32_t ob = ya + (uint32_t)L.y;
+    const uint32_t ob = ya + offb - rb - RZ - 1u;
     hsub<SW>(H[0], RD8(ob));
     hsub<SW>(H[0], RD8(ob + 1));
     hsub<SW>(H[0], RD8(ob + rb));
@@ -137,43 +150,78 @@ __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb,
     return dot_fixed<NSH, SW>(H, (const uint32_t *)(g_smem + (8u * a8 + b8) * half_row));
 }
 
-// Shared-memory body offset of window row (s, y, z) of a block.
-__device__ __forceinline__ uint32_t res_body(const int *d, int s, int y, int z, int ny, int nz, int Wy, int Wz,
+// Shared-memory body offset of window row (s, y, z) of a block whose window
+// on sublattice s starts at (ylo, zlo).
+__device__ __forceinline__ uint32_t res_body(int ylo, int zlo, int s, int y, int z, int ny, int nz, int Wy, int Wz,
                                              uint32_t rows, uint32_t rb)
 {
-    int yy = y - d[4 + s], zz = z - d[6 + s];
+    int yy = y - ylo, zz = z - zlo;
     yy = yy < 0 ? yy + ny : (yy >= ny ? yy - ny : yy);
     zz = zz < 0 ? zz + nz : (zz >= nz ? zz - nz : zz);
     return rows + (uint32_t)((s * Wz + zz) * Wy + yy) * rb + 16u;
 }
 
-// One look at the 8 neighbouring blocks' progress; bounded wait loop around it.
-__device__ bool res_wait(const SweepParams &P, int by, int bz, uint32_t need, int lane)
+// The progress flag of neighbour lane (lanes 0..8 but 4: (dy, dz) = (lane % 3
+// - 1, lane / 3 - 1)); nullptr for the other lanes.
+__device__ __forceinline__ const uint32_t *res_flag(const SweepParams &P, int by, int bz, int lane)
 {
-    const uint32_t *fp = nullptr;
-    if (lane < 9 && lane != 4) {
-        int nby = by + (lane % 3) - 1, nbz = bz + (lane / 3) - 1;
-        nby = nby < 0 ? nby + P.NBy : (nby >= P.NBy ? nby - P.NBy : nby);
-        nbz = nbz < 0 ? nbz + P.NBz : (nbz >= P.NBz ? nbz - P.NBz : nbz);
-        fp = P.flags + nbz * P.NBy + nby;
+    if (lane >= 9 || lane == 4) return nullptr;
+    int nby = by + (lane % 3) - 1, nbz = bz + (lane / 3) - 1;
+    nby = nby < 0 ? nby + P.NBy : (nby >= P.NBy ? nby - P.NBy : nby);
+    nbz = nbz < 0 ? nbz + P.NBz : (nbz >= P.NBz ? nbz - P.NBz : nbz);
+    return P.flags + nbz * P.NBy + nby;
+}
+
+// Gives up a wait: records a timeout (unless another block aborted first)
+// and raises the block's and the launch's abort flags.
+__device__ __forceinline__ void res_give_up(const SweepParams &P, volatile int *s_abort, bool timed_out)
+{
+    if (timed_out) {
+        atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
+        atomicExch(P.abort_flag, 1);
     }
+    *s_abort = 1;
+}
+
+// Bounded wait (whole warp) until the 8 neighbouring blocks' progress flags
+// are >= need; false once the launch or the block aborts or the time runs out.
+__device__ bool res_wait(const SweepParams &P, const uint32_t *fp, uint32_t need, volatile int *s_abort, int lane)
+{
     const uint64_t t0 = global_ns();
     for (;;) {
         const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
         if (__all_sync(0xffffffffu, ok)) return true;
         int stop = 0;
         if (lane == 0) {
-            if (ld_volatile_i32(P.abort_flag)) {
-                stop = 1;
-            } else if ((long long)(global_ns() - t0) > P.timeout_ns) {
-                atomicCAS(P.status, 0, (int)SMC_ERR_TIMEOUT);
-                atomicExch(P.abort_flag, 1);
+            const bool late = (long long)(global_ns() - t0) > P.timeout_ns;
+            if (late || *s_abort || ld_volatile_i32(P.abort_flag)) {
+                res_give_up(P, s_abort, late);
                 stop = 1;
             }
         }
         if (__shfl_sync(0xffffffffu, stop, 0)) return false;
-        __nanosleep(32);
     }
+}
+
+// Bounded wait (whole warp) until the block's count of finished
+// (compute warp, group) pairs is >= need; acquires the compute warps' writes.
+__device__ bool res_wait_count(const SweepParams &P, const volatile unsigned *cnt, unsigned need,
+                               volatile int *s_abort, int lane)
+{
+    const uint64_t t0 = global_ns();
+    int stop = 0;
+    if (lane == 0) {
+        while (*cnt < need) {
+            const bool late = (long long)(global_ns() - t0) > P.timeout_ns;
+            if (late || *s_abort || ld_volatile_i32(P.abort_flag)) {
+                res_give_up(P, s_abort, late);
+                stop = 1;
+                break;
+            }
+        }
+        __threadfence_block();
+    }
+    return __shfl_sync(0xffffffffu, stop, 0) == 0;
 }
 
 // Copies the rows of list entries [e0, e1) (slot << 21 | row) between the
@@ -204,10 +252,10 @@ __device__ __forceinline__ void res_halos(const uint32_t *ent, int n, uint32_t r
 }
 
 template <bool IS_INT, int NSH, int SW>
-__global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
+__global__ void __launch_bounds__(320, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int nc = nwarp - 1, nbar = nwarp * 32;
+    const int nc = nwarp - 2, nbar = (nc + 1) * 32;  // compute warps, then the exchange and release warps
     const int blk = blockIdx.x;
     const RepDesc &RD = P.rep[0];
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
@@ -216,27 +264,25 @@ __global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant
     const int *d = P.rdesc + blk * kResDesc;
     const int by = blk % P.NBy, bz = blk / P.NBy;
     const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
-    __shared__ int s_abort;
-    // shared memory: [table][8 direction offsets][rows][lists][Philox words per compute warp]
+    __shared__ volatile int s_abort;  // a wait gave up: stop
+    __shared__ volatile int s_stop;   // the group at which the compute warps stop (set by the exchange warp)
+    __shared__ unsigned s_cnt;        // (compute warp, group) pairs finished and published
+    // shared memory: [table][rows][lists][Philox words per compute warp]
     const int qwords = kQRows * P.qrow;
-    const uint32_t lut = (uint32_t)qwords * 4u;
-    const uint32_t rows = lut + 64u;
+    const uint32_t rows = (uint32_t)qwords * 4u;
     const int nslots = 2 * Wy * Wz;
     const uint32_t lists = rows + (uint32_t)nslots * rb;
     const int nk = (NLx + 31) >> 5;
     const uint32_t wsm0 = lists + (uint32_t)P.rblob * 4u;
     for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
-    if (tid < 8) {
-        const int kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
-        int2 e;
-        e.x = ky * (int)rb + kz * (int)RZ + kx;
-        e.y = (ky - 1) * (int)rb + (kz - 1) * (int)RZ + kx - 1;
-        *(int2 *)(g_smem + lut + (uint32_t)tid * 8u) = e;
-    }
     const uint32_t *gl = P.rlists + d[8];
     uint32_t *L = (uint32_t *)(g_smem + lists);
     for (int i = tid; i < d[9]; i += blockDim.x) L[i] = gl[i];
-    if (tid == 0) s_abort = 0;
+    if (tid == 0) {
+        s_abort = 0;
+        s_stop = 0x7fffffff;
+        s_cnt = 0u;
+    }
     // the window's rows from the exchange copy (species x 8)
     {
         const int cpr = nx >> 4;
@@ -264,122 +310,133 @@ __global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant
         __syncthreads();
     }
     const int total = P.nsweeps * 32;
-    // list header: fetch offsets [0..33), publish offsets [33 .. 33 + 32 nc + 1),
+    // list header: fetch offsets [0..33), split of each group's fetch list
+    // into early and late rows [33..65), publish offsets [65 .. 65 + 32 nc + 1),
     // then the final rows' offset and count
-    const uint32_t *fo = L, *po = L + 33;
-    const uint32_t fin0 = L[33 + 32 * nc + 1], fin1 = L[33 + 32 * nc + 2];
+    const uint32_t *fo = L, *fm = L + 33, *po = L + 65;
+    const uint32_t fin0 = L[65 + 32 * nc + 1], fin1 = L[65 + 32 * nc + 2];
 
     if (warp == nc) {
         // ---------------- exchange warp ----------------
-        named_arrive(kBarReady, nbar);  // group 0: the window was loaded from the exchange copy
-        bool pre = false, aborted = false;
-        for (int gs = 0; gs < total && !aborted; ++gs) {
+        // Prepares group gs + 1 while the compute warps run group gs: its
+        // early rows once the neighbours finished gs - 1, its late rows once
+        // they finished gs, then the x-halos and READY.
+        named_arrive(bar_ready(0), nbar);  // group 0: the window was loaded from the exchange copy
+        const uint32_t *fp = res_flag(P, by, bz, lane);
+        bool ok = true;
+        int gs = 0;
+        for (; ok && gs + 1 < total; ++gs) {
             const int nxt = gs + 1, gn = nxt & 31;
-            const uint32_t need = (uint32_t)nxt + 1 - ((gn & 3) ? 2u : 1u);
-            if (nxt < total && (gn & 3)) {
-                // lag 2: the next group's rows can come in while this one runs
-                if (!res_wait(P, by, bz, need, lane)) {
-                    aborted = true;
-                    break;
-                }
-                res_fetch(P, L + fo[gn], (int)(fo[gn + 1] - fo[gn]), smem0 + rows, rb, nx, lane);
-                pre = true;
+            // never more than one group ahead: the compute warps finished gs - 1
+            ok = res_wait_count(P, &s_cnt, (unsigned)(gs * nc), &s_abort, lane) &&
+                 res_wait(P, fp, (uint32_t)gs, &s_abort, lane);
+            if (!ok) break;
+            res_fetch(P, L + fo[gn], (int)(fm[gn] - fo[gn]), smem0 + rows, rb, nx, lane);
+            if (fm[gn] < fo[gn + 1]) {
+                // late rows: written by a neighbour in group gs (groups of lag 1)
+                ok = res_wait(P, fp, (uint32_t)nxt, &s_abort, lane);
+                if (!ok) break;
+                res_fetch(P, L + fm[gn], (int)(fo[gn + 1] - fm[gn]), smem0 + rows, rb, nx, lane);
             }
-            named_sync(kBarDone, nbar);  // group gs done and its rows published
-            if (lane == 0 && blk != P.skip_tile) {
-                __threadfence();
-                st_release_u32(P.flags + blk, (uint32_t)gs + 1);
-            }
-            if (nxt < total) {
-                if (!pre) {
-                    if (!res_wait(P, by, bz, need, lane)) {
-                        aborted = true;
-                        break;
-                    }
-                    res_fetch(P, L + fo[gn], (int)(fo[gn + 1] - fo[gn]), smem0 + rows, rb, nx, lane);
-                }
-                asm volatile("cp.async.wait_all;" ::: "memory");
-                __syncwarp();
-                res_halos(L + fo[gn], (int)(fo[gn + 1] - fo[gn]), rows, rb, nx, lane);
-                __syncwarp();
-                named_arrive(kBarReady, nbar);
-                pre = false;
-            }
-        }
-        if (aborted) {
             asm volatile("cp.async.wait_all;" ::: "memory");
-            if (lane == 0) *(volatile int *)&s_abort = 1;
             __syncwarp();
-            named_arrive(kBarReady, nbar);  // the compute warps wake up and leave
-            return;
+            res_halos(L + fo[gn], (int)(fo[gn + 1] - fo[gn]), rows, rb, nx, lane);
+            named_arrive(bar_ready(nxt), nbar);
+        }
+        if (!ok) {
+            // The compute warps run on to READY of group gs + 1 and all stop
+            // there (s_stop is written before that barrier's arrival).  They
+            // pass the READYs already given without waiting, so they finish
+            // group gs - 1 in bounded time; only then is the barrier of
+            // gs + 1's parity free of group gs - 1's arrivals.
+            asm volatile("cp.async.wait_all;" ::: "memory");
+            if (lane == 0) {
+                s_stop = gs + 1;
+                const uint64_t t0 = global_ns();
+                while (*(volatile unsigned *)&s_cnt < (unsigned)(gs * nc) &&
+                       (long long)(global_ns() - t0) < P.timeout_ns) {
+                }
+            }
+            named_arrive(bar_ready(gs + 1), nbar);
+        }
+    } else if (warp == nc + 1) {
+        // ---------------- release warp ----------------
+        // Releases the block's progress flag as soon as every compute warp
+        // finished and published a group; st.release orders the compute
+        // warps' stores to the exchange copy (seen through the count) before it.
+        for (int gs = 0; gs < total; ++gs) {
+            if (!res_wait_count(P, &s_cnt, (unsigned)((gs + 1) * nc), &s_abort, lane)) break;
+            if (lane == 0 && blk != P.skip_tile) st_release_u32(P.flags + blk, (uint32_t)gs + 1);
         }
     } else {
         // ---------------- compute warps ----------------
         const bool active = warp < d[2] * d[3];
         const int cy = d[0] + warp % max(d[2], 1), cz = d[1] + warp / max(d[2], 1);
         const uint32_t wsm = wsm0 + (uint32_t)warp * (uint32_t)nk * 512u;
+        const int ylo0 = d[4], ylo1 = d[5], zlo0 = d[6], zlo1 = d[7];
         long long accE = 0, accN = 0;
         for (int gs = 0; gs < total; ++gs) {
             const int t = gs >> 5, g = gs & 31;
             const int dy = g & 3, dz = (g >> 2) & 3, sub = g >> 4, soff = sub == 0 ? -1 : 0;
             const int y0 = 4 * cy + dy, z0 = 4 * cz + dz;
             const uint64_t sweep = P.sweep0 + (uint64_t)t;
+            U4 w4{0u, 0u, 0u, 0u};
             if (active) {
                 // Philox words of this column's link cells for this group
                 const uint32_t rowsite = (uint32_t)(((sub * nz + z0) * ny + y0) * nx);
                 const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
                 uint32_t *wp = (uint32_t *)(g_smem + wsm);
+                if (nk == 1 && NLx == 32) {
+                    w4 = philox10(U4{(rowsite >> 2) + (uint32_t)lane, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
+                                  k0, k1);
+                } else {
 #pragma unroll 1
-                for (int k = 0; k < nk; ++k) {
-                    const int i = lane + 32 * k;
-                    if (i < NLx) {
-                        const U4 w = philox10(
-                            U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)}, k0, k1);
-                        wp[(k * 4 + 0) * 32 + lane] = w.x;
-                        wp[(k * 4 + 1) * 32 + lane] = w.y;
-                        wp[(k * 4 + 2) * 32 + lane] = w.z;
-                        wp[(k * 4 + 3) * 32 + lane] = w.w;
+                    for (int k = 0; k < nk; ++k) {
+                        const int i = lane + 32 * k;
+                        if (i < NLx) {
+                            const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)i, RD.rep, (uint32_t)sweep,
+                                                     (uint32_t)(sweep >> 32)},
+                                                  k0, k1);
+                            wp[(k * 4 + 0) * 32 + lane] = w.x;
+                            wp[(k * 4 + 1) * 32 + lane] = w.y;
+                            wp[(k * 4 + 2) * 32 + lane] = w.z;
+                            wp[(k * 4 + 3) * 32 + lane] = w.w;
+                        }
                     }
                 }
             }
-            named_sync(kBarReady, nbar);
-            if (*(volatile int *)&s_abort) return;
+            float cx = 0.f;
+            int2 ti = make_int2(0, 0);
+            if constexpr (IS_INT)
+                ti = P.temp.tabinfo[P.beta_stride ? t : 0];
+            else
+                cx = P.temp.beta[P.beta_stride ? t : 0];
+            const uint32_t ownb = res_body(sub ? ylo1 : ylo0, sub ? zlo1 : zlo0, sub, y0, z0, ny, nz, Wy, Wz, rows, rb);
+            const uint32_t parb = res_body(sub ? ylo0 : ylo1, sub ? zlo0 : zlo1, 1 - sub, y0 + soff, z0 + soff, ny, nz,
+                                           Wy, Wz, rows, rb);
+            named_sync(bar_ready(gs), nbar);
+            if (gs >= s_stop) break;
             if (active) {
-                float cx = 0.f;
-                int2 ti = make_int2(0, 0);
-                if constexpr (IS_INT)
-                    ti = P.temp.tabinfo[P.beta_stride ? t : 0];
-                else
-                    cx = P.temp.beta[P.beta_stride ? t : 0];
-                const uint32_t ownb = res_body(d, sub, y0, z0, ny, nz, Wy, Wz, rows, rb);
-                const uint32_t parb = res_body(d, 1 - sub, y0 + soff, z0 + soff, ny, nz, Wy, Wz, rows, rb);
                 // the 5 rows a mini-step writes (own row, partner 2 x 2), for the halo refresh
                 uint32_t hrow = ownb;
                 if (lane >= 2 && lane < 10) {
                     const int k = (lane - 2) >> 1;
                     hrow = parb + (uint32_t)(k & 1) * rb + (uint32_t)(k >> 1) * RZ;
                 }
-                for (int dx = 0; dx < 4; ++dx) {
-#pragma unroll 1
-                    for (int k = 0; k < nk; ++k) {
-                        const int i = lane + 32 * k;
-                        if (i >= NLx) continue;
-                        const int x = 4 * i + dx;
-                        const uint32_t w =
-                            *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
-                        uint32_t a8, b8, pb;
-                        const uint32_t ya = ownb + (uint32_t)x;
-                        const int32_t dE =
-                            res_dE<NSH, SW>(ya, parb + (uint32_t)(x + soff), rb, RZ, w >> kRBits, lut, a8, b8, pb);
-                        if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
-                            const int xb = x + soff + (int)(w >> 31);
-                            pb += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
-                            g_smem[ya] = (unsigned char)b8;
-                            g_smem[pb] = (unsigned char)a8;
-                            accE += dE;
-                            accN += 1;
-                        }
+                auto trial = [&](int x, uint32_t w) {
+                    uint32_t a8, b8, pb;
+                    const uint32_t ya = ownb + (uint32_t)x;
+                    const int32_t dE = res_dE<NSH, SW>(ya, parb + (uint32_t)(x + soff), rb, RZ, w, a8, b8, pb);
+                    if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
+                        const int xb = x + soff + (int)(w >> 31);
+                        pb += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
+                        g_smem[ya] = (unsigned char)b8;
+                        g_smem[pb] = (unsigned char)a8;
+                        accE += dE;
+                        accN += 1;
                     }
+                };
+                auto halo = [&]() {
                     __syncwarp();
                     if (lane < 10) {
                         if (lane & 1)
@@ -388,6 +445,28 @@ __global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant
                             *(unsigned *)(g_smem + hrow - 4) = *(const unsigned *)(g_smem + hrow + nx - 4);
                     }
                     __syncwarp();
+                };
+                if (nk == 1 && NLx == 32) {
+                    // one link cell per lane: its four words stay in registers
+                    trial(4 * lane + 0, w4.x);
+                    halo();
+                    trial(4 * lane + 1, w4.y);
+                    halo();
+                    trial(4 * lane + 2, w4.z);
+                    halo();
+                    trial(4 * lane + 3, w4.w);
+                    halo();
+                } else {
+                    for (int dx = 0; dx < 4; ++dx) {
+#pragma unroll 1
+                        for (int k = 0; k < nk; ++k) {
+                            const int i = lane + 32 * k;
+                            if (i < NLx)
+                                trial(4 * i + dx, *(const uint32_t *)(g_smem + wsm +
+                                                                      (uint32_t)(((k * 4 + dx) * 32 + lane) * 4)));
+                        }
+                        halo();
+                    }
                 }
                 // publish the rows this column wrote that other blocks read
                 const uint32_t *pe = L + po[g * nc + warp];
@@ -400,7 +479,13 @@ __global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant
                         *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
                 }
             }
-            named_arrive(kBarDone, nbar);
+            // count this warp's group as done (release at CTA scope: the
+            // stores above are ordered before the count)
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();
+                atomicAdd(&s_cnt, 1u);
+            }
         }
         const long long e_w = warp_sum<long long>(accE), n_w = warp_sum<long long>(accN);
         if (lane == 0) {
@@ -409,6 +494,7 @@ __global__ void __launch_bounds__(288, 1) k_sweep_resident(const __grid_constant
         }
     }
     __syncthreads();
+    if (s_abort) return;
     // final rows, back to plain species in the caller's array
     for (int q = tid; q < (int)(fin1 * (uint32_t)(nx >> 4)); q += blockDim.x) {
         const int cpr = nx >> 4, e = q / cpr, c = q - e * cpr;
@@ -580,30 +666,39 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
             if (yy >= rp.Wy || zz >= rp.Wz) return -1;
             return (s * rp.Wz + zz) * rp.Wy + yy;
         };
-        std::vector<uint32_t> hdr(33 + 32 * nc + 1 + 2, 0), body;
+        std::vector<uint32_t> hdr(65 + 32 * nc + 1 + 2, 0), body;
         auto entry = [&](int r) -> uint32_t {
             const int sl = slot_of(r);
             return ((uint32_t)sl << 21) | (uint32_t)r;
         };
         bool fits = true;
-        // fetch lists per group
+        // fetch lists per group: rows read at g whose last writer is another
+        // block, those last written two or more groups back first ("early"),
+        // then those written in group g - 1 ("late"; only groups of lag 1)
         for (int g = 0; g < 32; ++g) {
             hdr[g] = (uint32_t)(hdr.size() + body.size());
-            std::set<int> fs;
+            std::set<int> early, late;
             for (int k = 0; k < ncy * ncz; ++k) {
                 column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
                 for (int r : R) {
                     if (slot_of(r) < 0) fits = false;
-                    if (last_writer(r, g) != blk) fs.insert(r);
+                    if (last_writer(r, g) == blk) continue;
+                    if (wblk[(size_t)r * 32 + ((g + 31) & 31)] >= 0)
+                        late.insert(r);
+                    else
+                        early.insert(r);
                 }
             }
-            for (int r : fs) body.push_back(entry(r));
+            if (!late.empty() && (g & 3) != 0) fits = false;  // the lag-2 rule would be broken
+            for (int r : early) body.push_back(entry(r));
+            hdr[33 + g] = (uint32_t)(hdr.size() + body.size());
+            for (int r : late) body.push_back(entry(r));
         }
         hdr[32] = (uint32_t)(hdr.size() + body.size());
         // publish lists per group and compute warp: written rows another block reads
         for (int g = 0; g < 32; ++g)
             for (int k = 0; k < nc; ++k) {
-                hdr[33 + g * nc + k] = (uint32_t)(hdr.size() + body.size());
+                hdr[65 + g * nc + k] = (uint32_t)(hdr.size() + body.size());
                 if (k >= ncy * ncz) continue;
                 column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
                 for (int r : W) {
@@ -612,9 +707,9 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
                     if (other) body.push_back(entry(r));
                 }
             }
-        hdr[33 + 32 * nc] = (uint32_t)(hdr.size() + body.size());
+        hdr[65 + 32 * nc] = (uint32_t)(hdr.size() + body.size());
         // final rows: those whose last writer in the sweep is this block
-        hdr[33 + 32 * nc + 1] = (uint32_t)(hdr.size() + body.size());
+        hdr[65 + 32 * nc + 1] = (uint32_t)(hdr.size() + body.size());
         uint32_t nfin = 0;
         for (int r = 0; r < nrows_lat; ++r)
             if (last_writer(r, 32) == blk) {
@@ -622,7 +717,7 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
                 body.push_back(entry(r));
                 ++nfin;
             }
-        hdr[33 + 32 * nc + 2] = nfin;
+        hdr[65 + 32 * nc + 2] = nfin;
         if (!fits) return SMC_OK;  // a row outside the window (not expected)
         dd[8] = (int)rp.lists.size();
         dd[9] = (int)(hdr.size() + body.size());
@@ -637,7 +732,7 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + 1) * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + 2) * 32, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1 || rp.nblocks > per_sm * ws->num_sms) return SMC_OK;
     rp.smem = smem;
@@ -789,7 +884,7 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "k_occ_to_exch");
         void *args[] = {(void *)&P};
-        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + 1) * 32), args, rp.smem, stream);
+        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + 2) * 32), args, rp.smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(resident sweep)");
     }
     return SMC_OK;

@@ -87,10 +87,13 @@ def _f32_pair(smc, dims, nsweeps, kT, resident, seed=5):
     return occ, float(e_acc.item()), int(n_acc.item())
 
 
-@pytest.mark.parametrize("dims,nsweeps", [((128, 128, 128), 3), ((64, 64, 64), 4), ((32, 48, 40), 5)])
+@pytest.mark.parametrize("dims,nsweeps", [((128, 128, 128), 3), ((64, 64, 64), 4), ((32, 48, 40), 5),
+                                          ((128, 128, 128), 40), ((64, 64, 64), 120)])
 def test_resident_equals_streaming_fp32(smc, dims, nsweeps):
     """The anneal's model on the 128^3 box (2 x 4 blocks of columns) and on
-    smaller boxes: per-sweep temperatures, identical results bit for bit."""
+    smaller boxes: per-sweep temperatures, identical results bit for bit.
+    The long runs give the blocks' progress time to drift apart, so that
+    every ordering of the exchange, release and compute warps occurs."""
     kT = inputs.anneal_kT(1000)[:nsweeps]
     a = _f32_pair(smc, dims, nsweeps, kT, True)
     b = _f32_pair(smc, dims, nsweeps, kT, False)
