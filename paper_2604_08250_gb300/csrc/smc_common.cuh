@@ -103,18 +103,18 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p)
     return v;
 }
 
-// Polling form: a relaxed load (no cache invalidation per poll); once the
-// awaited value is seen, one fence_acq_rel_gpu() makes it an acquire.
-__device__ __forceinline__ uint32_t ld_relaxed_u32(const uint32_t *p)
+// Two 64-bit words with relaxed (single-copy atomic per word) semantics at
+// GPU scope: the tagged exchange of the resident sweep.
+__device__ __forceinline__ ulonglong2 ld_relaxed_v2u64(const unsigned long long *p)
 {
-    uint32_t v;
-    asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    ulonglong2 v;
+    asm volatile("ld.relaxed.gpu.global.v2.u64 {%0, %1}, [%2];" : "=l"(v.x), "=l"(v.y) : "l"(p) : "memory");
     return v;
 }
 
-__device__ __forceinline__ void fence_acq_rel_gpu()
+__device__ __forceinline__ void st_relaxed_v2u64(unsigned long long *p, unsigned long long a, unsigned long long b)
 {
-    asm volatile("fence.acq_rel.gpu;" ::: "memory");
+    asm volatile("st.relaxed.gpu.global.v2.u64 [%0], {%1, %2};" ::"l"(p), "l"(a), "l"(b) : "memory");
 }
 
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v)

@@ -77,11 +77,15 @@ struct SweepParams {
         float beta[kMaxBeta];        // MLP and qSRO kernels: 1 / kT; pair kernels: cx = -log2(e) 2^-sigma / kT
         int2 tabinfo[kMaxBeta / 2];  // (offset, length) into tab
     } temp;
-    // resident kernel: block descriptors, exchange lists, exchange copy of the
-    // lattice (species x 8), window of rows per sublattice, block grid
+    // resident kernel: block descriptors, exchange lists, the lattice at the
+    // start of the launch (species x 8), the published row versions (words of
+    // 4 species bytes | 32-bit tag, two copies by sweep parity), window of
+    // rows per sublattice, block grid
     const int *rdesc;
     const uint32_t *rlists;
     int8_t *exch;
+    unsigned long long *xver;
+    int nver, rxw;  // version slots; exchange warps of the resident kernel
     int Wy, Wz, NBy, NBz, rcols, rblob;
     uint32_t qtab[kPairQWords];  // pair kernels: fixed-point table rows (pair_fixed.cuh)
     union {

@@ -8,32 +8,34 @@
 // bit.  What changes is where the rows live.  Each CTA owns a rectangular
 // block of columns and keeps in shared memory every row its columns ever
 // touch (a window of 4 b + 7 rows per axis and sublattice), for the whole
-// launch.  Rows that another CTA also touches are kept consistent through an
-// exchange copy of the lattice in global memory (species x 8):
+// launch.  Rows that another CTA also touches travel as versions:
 //
-//   before group g, a CTA fetches the rows its columns read at g whose last
-//   writer before g (in the sequential order of the groups) is another CTA;
-//   after group g, it publishes the rows its columns wrote at g that another
-//   CTA reads, then releases its progress flag.
+//   after group g, a CTA publishes each row its columns wrote at g that
+//   another CTA reads before the row's next write: nx / 4 64-bit words of
+//   4 species bytes (x 8) and the tag g + 1 (g counted from the launch);
+//   before group g, it fetches the rows its columns read at g whose last
+//   write is another CTA's and whose version it has not read since, polling
+//   each word until it carries the expected tag.
 //
-// A CTA starts group g once its 8 neighbouring blocks have released group
-// g - lag (lag 2 for groups with dy >= 1, else 1), the rule of the streaming
-// kernel (every fetched row's last writer is then finished and published,
-// and no row a CTA touches at g is touched by a neighbour at g - 1 when the
-// lag is 2).  The lists of rows are built on the host from the groups'
-// row-level read and write sets.
+// A word is single-copy atomic, so a matching tag means matching bytes; no
+// fence or flag sits between a write and its readers, only the data's own
+// latency.  Versions live in two copies (by sweep parity) of one slot per
+// (group of the write, row): the copy a write overwrites was last read 33
+// groups earlier, and the CTA's exchange warps make sure its neighbours have
+// finished that group (their progress flags, released by each CTA's release
+// warp) before READY -- a check that in practice never waits.  The host
+// builds the lists from the groups' row-level read and write sets.
 //
 // Roles in a CTA: warps 0..nc-1 run the trials of one column each and
-// publish the rows they wrote; warp nc (the exchange warp) prepares the next
-// group while the current one runs -- it waits for the neighbours' progress,
-// fetches rows with cp.async, fills their periodic x-halos and arrives on
-// READY; warp nc + 1 (the release warp) releases the CTA's progress flag once
-// every compute warp has counted the group as done.  A fetch for group g + 1
+// publish the rows they wrote; the exchange warps fetch the next group's
+// versions (with their periodic x-halos) while the current group runs and
+// arrive on READY; the release warp releases the CTA's progress flag once
+// every compute warp has counted a group as done.  A fetch for group g + 1
 // may land while group g runs: a fetched row is not written by this CTA's
 // group g, and if group g reads it, it reads the same bytes.  The exchange
-// warp never runs more than one group ahead (it waits until the compute
-// warps finished g - 1 before it fetches for g + 1), and the READY barriers
-// alternate by group parity so that its arrivals for consecutive groups
+// warps never run more than one group ahead (they wait until the compute
+// warps finished g - 1 before they fetch for g + 1), and the READY barriers
+// alternate by group parity so that their arrivals for consecutive groups
 // never meet in one barrier.
 #include <algorithm>
 #include <cmath>
@@ -185,12 +187,17 @@ __device__ __forceinline__ void res_give_up(const SweepParams &P, volatile int *
 
 // Bounded wait (whole warp) until the 8 neighbouring blocks' progress flags
 // are >= need; false once the launch or the block aborts or the time runs out.
-__device__ bool res_wait(const SweepParams &P, const uint32_t *fp, uint32_t need, volatile int *s_abort, int lane)
+// *seen receives the smallest flag read by the successful look.
+__device__ bool res_wait(const SweepParams &P, const uint32_t *fp, uint32_t need, volatile int *s_abort, int lane,
+                         uint32_t *seen)
 {
     const uint64_t t0 = global_ns();
     for (;;) {
-        const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
-        if (__all_sync(0xffffffffu, ok)) return true;
+        const uint32_t v = fp == nullptr ? 0xffffffffu : ld_acquire_u32(fp);
+        if (__all_sync(0xffffffffu, v >= need)) {
+            *seen = __reduce_min_sync(0xffffffffu, v);
+            return true;
+        }
         int stop = 0;
         if (lane == 0) {
             const bool late = (long long)(global_ns() - t0) > P.timeout_ns;
@@ -224,38 +231,98 @@ __device__ bool res_wait_count(const SweepParams &P, const volatile unsigned *cn
     return __shfl_sync(0xffffffffu, stop, 0) == 0;
 }
 
-// Copies the rows of list entries [e0, e1) (slot << 21 | row) between the
-// exchange copy and shared memory (fetch: global -> shared with 16-byte
-// cp.async; publish: shared -> global), the warp's lanes over (entry, chunk).
-__device__ __forceinline__ void res_fetch(const SweepParams &P, const uint32_t *ent, int n, uint32_t rows_abs,
-                                          uint32_t rb, int nx, int lane)
+// Row versions.  Every row a block writes in group g and another block
+// reads before its next write is published as a version: nx / 4 words of
+// (4 species bytes | tag << 32), tag = global group of the write + 1, in
+// copy (global group >> 5) & 1 of its version slot.  A reader knows the
+// tag it needs, so it polls the words themselves: a word with that tag holds
+// that version's bytes (each 64-bit word is single-copy atomic), and no fence
+// or flag stands between the write and the read.
+__device__ __forceinline__ uint32_t ver_word(const SweepParams &P, int gw, uint32_t vid, int nx)
 {
-    const int cpr = nx >> 4;
-    for (int q = lane; q < n * cpr; q += 32) {
-        const int e = q / cpr, c = q - e * cpr;
-        const uint32_t v = ent[e], slot = v >> 21, row = v & 0x1FFFFFu;
-        const int8_t *src = P.exch + (size_t)row * nx + 16 * c;
-        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(rows_abs + slot * rb + 16u + 16u * c),
-                     "l"(src)
-                     : "memory");
-    }
+    return ((uint32_t)((gw >> 5) & 1) * (uint32_t)P.nver + vid) * (uint32_t)(nx >> 2);
 }
-__device__ __forceinline__ void res_halos(const uint32_t *ent, int n, uint32_t rows, uint32_t rb, int nx, int lane)
+
+// Fetches the versions of list entries ent[0, n) ({smem slot | d << 16,
+// version slot}) that group G reads, written in group G - d (entries with
+// G - d < 0 predate the launch and are already in the window).  The nxw
+// exchange warps share the 16-byte chunks (chunk q to warp (q / 32) % nxw),
+// K chunks per lane per round, each chunk polled until both its words carry
+// the tag.  False on timeout or abort.
+template <int K>
+__device__ bool res_fetch_versions(const SweepParams &P, const uint2 *ent, int n, uint32_t rows, uint32_t rb, int nx,
+                                   int G, int xw, int nxw, volatile int *s_abort, int lane)
 {
-    for (int q = lane; q < 2 * n; q += 32) {
-        const uint32_t body = rows + (ent[q >> 1] >> 21) * rb + 16u;
-        if (q & 1)
-            *(unsigned *)(g_smem + body + nx) = *(const unsigned *)(g_smem + body);
-        else
-            *(unsigned *)(g_smem + body - 4) = *(const unsigned *)(g_smem + body + nx - 4);
+    const int cpr = nx >> 3;
+    const int tot = n * cpr, step = 32 * nxw, de = step / cpr, dc = step - de * cpr;
+    const uint64_t t0 = global_ns();
+    for (int base = 0; base < tot; base += step * K) {
+        uint32_t src[K], dst[K], tag[K];  // word offset in P.xver, shared address, tag
+        uint32_t todo = 0u, first = 0u, last = 0u;  // chunks that also fill the right / left x-halo
+        {
+            const int q0 = base + 32 * xw + lane;
+            int e = q0 / cpr, c = q0 - e * cpr;
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                src[k] = 0u;
+                dst[k] = 0u;
+                tag[k] = 0u;
+                if (e < n) {
+                    const uint2 en = ent[e];
+                    const int gw = G - (int)(en.x >> 16);
+                    if (gw >= 0) {
+                        src[k] = ver_word(P, gw, en.y, nx) + 2u * (uint32_t)c;
+                        dst[k] = rows + (en.x & 0xffffu) * rb + 16u + 8u * (uint32_t)c;
+                        tag[k] = (uint32_t)gw + 1u;
+                        todo |= 1u << k;
+                        if (c == 0) first |= 1u << k;
+                        if (c == cpr - 1) last |= 1u << k;
+                    }
+                }
+                e += de;
+                c += dc;
+                if (c >= cpr) {
+                    c -= cpr;
+                    ++e;
+                }
+            }
+        }
+        while (__any_sync(0xffffffffu, todo != 0u)) {
+            ulonglong2 v[K];
+#pragma unroll
+            for (int k = 0; k < K; ++k)
+                if (todo & (1u << k)) v[k] = ld_relaxed_v2u64(P.xver + src[k]);
+#pragma unroll
+            for (int k = 0; k < K; ++k) {
+                if ((todo & (1u << k)) && (uint32_t)(v[k].x >> 32) == tag[k] && (uint32_t)(v[k].y >> 32) == tag[k]) {
+                    *(uint2 *)(g_smem + dst[k]) = make_uint2((uint32_t)v[k].x, (uint32_t)v[k].y);
+                    // periodic x-halos: body[0..4) after the row, body[nx-4..nx) before it
+                    if (first & (1u << k)) *(uint32_t *)(g_smem + dst[k] + nx) = (uint32_t)v[k].x;
+                    if (last & (1u << k)) *(uint32_t *)(g_smem + dst[k] + 4 - nx) = (uint32_t)v[k].y;
+                    todo &= ~(1u << k);
+                }
+            }
+            const bool pending = __any_sync(0xffffffffu, todo != 0u);
+            int stop = 0;
+            if (pending && lane == 0) {
+                const bool late = (long long)(global_ns() - t0) > P.timeout_ns;
+                if (late || *s_abort || ld_volatile_i32(P.abort_flag)) {
+                    res_give_up(P, s_abort, late);
+                    stop = 1;
+                }
+            }
+            if (__shfl_sync(0xffffffffu, stop, 0)) return false;
+        }
     }
+    return true;
 }
 
 template <bool IS_INT, int NSH, int SW>
-__global__ void __launch_bounds__(320, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
+__global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
-    const int nc = nwarp - 2, nbar = (nc + 1) * 32;  // compute warps, then the exchange and release warps
+    // compute warps, then P.rxw exchange warps, then the release warp
+    const int nxw = P.rxw, nc = nwarp - nxw - 1, nbar = (nc + nxw) * 32;
     const int blk = blockIdx.x;
     const RepDesc &RD = P.rep[0];
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
@@ -310,60 +377,63 @@ __global__ void __launch_bounds__(320, 1) k_sweep_resident(const __grid_constant
         __syncthreads();
     }
     const int total = P.nsweeps * 32;
-    // list header: fetch offsets [0..33), split of each group's fetch list
-    // into early and late rows [33..65), publish offsets [65 .. 65 + 32 nc + 1),
-    // then the final rows' offset and count
-    const uint32_t *fo = L, *fm = L + 33, *po = L + 65;
-    const uint32_t fin0 = L[65 + 32 * nc + 1], fin1 = L[65 + 32 * nc + 2];
+    // list header (offsets in words): fetch lists per group [0..33), publish
+    // lists per (group, compute warp) [33 .. 33 + 32 nc + 1), then the final
+    // rows' offset and count; fetch and publish entries are word pairs
+    const uint32_t *fo = L, *po = L + 33;
+    const uint32_t fin0 = L[33 + 32 * nc + 1], fin1 = L[33 + 32 * nc + 2];
 
-    if (warp == nc) {
-        // ---------------- exchange warp ----------------
-        // Prepares group gs + 1 while the compute warps run group gs: its
-        // early rows once the neighbours finished gs - 1, its late rows once
-        // they finished gs, then the x-halos and READY.
-        named_arrive(bar_ready(0), nbar);  // group 0: the window was loaded from the exchange copy
+    if (warp >= nc && warp < nc + nxw) {
+        // ---------------- exchange warps ----------------
+        // Prepare group gs + 1 while the compute warps run group gs: the
+        // versions of the rows it reads that another block wrote (with their
+        // x-halos), shared between the exchange warps, then READY.
+        const int xw = warp - nc;
+        named_arrive(bar_ready(0), nbar);  // group 0: the window was loaded from the lattice copy
         const uint32_t *fp = res_flag(P, by, bz, lane);
+        uint32_t nbmin = 0u;  // a lower bound of the neighbours' progress flags
         bool ok = true;
         int gs = 0;
-        for (; ok && gs + 1 < total; ++gs) {
+        for (; gs + 1 < total; ++gs) {
             const int nxt = gs + 1, gn = nxt & 31;
             // never more than one group ahead: the compute warps finished gs - 1
-            ok = res_wait_count(P, &s_cnt, (unsigned)(gs * nc), &s_abort, lane) &&
-                 res_wait(P, fp, (uint32_t)gs, &s_abort, lane);
+            ok = res_wait_count(P, &s_cnt, (unsigned)(gs * nc), &s_abort, lane);
+            // Group nxt's versions overwrite those of nxt - 64, which readers
+            // fetch up to group nxt - 33: the neighbours must have finished it
+            // (READY of nxt waits for this warp).
+            if (ok && xw == 0 && nxt >= 64 && nbmin < (uint32_t)(nxt - 32))
+                ok = res_wait(P, fp, (uint32_t)(nxt - 32), &s_abort, lane, &nbmin);
+            if (ok)
+                ok = res_fetch_versions<8>(P, (const uint2 *)(L + fo[gn]), (int)(fo[gn + 1] - fo[gn]) >> 1, rows, rb,
+                                           nx, nxt, xw, nxw, &s_abort, lane);
             if (!ok) break;
-            res_fetch(P, L + fo[gn], (int)(fm[gn] - fo[gn]), smem0 + rows, rb, nx, lane);
-            if (fm[gn] < fo[gn + 1]) {
-                // late rows: written by a neighbour in group gs (groups of lag 1)
-                ok = res_wait(P, fp, (uint32_t)nxt, &s_abort, lane);
-                if (!ok) break;
-                res_fetch(P, L + fm[gn], (int)(fo[gn + 1] - fm[gn]), smem0 + rows, rb, nx, lane);
-            }
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            __syncwarp();
-            res_halos(L + fo[gn], (int)(fo[gn + 1] - fo[gn]), rows, rb, nx, lane);
             named_arrive(bar_ready(nxt), nbar);
         }
         if (!ok) {
-            // The compute warps run on to READY of group gs + 1 and all stop
-            // there (s_stop is written before that barrier's arrival).  They
-            // pass the READYs already given without waiting, so they finish
-            // group gs - 1 in bounded time; only then is the barrier of
-            // gs + 1's parity free of group gs - 1's arrivals.
-            asm volatile("cp.async.wait_all;" ::: "memory");
-            if (lane == 0) {
-                s_stop = gs + 1;
+            // The compute warps stop at READY of the smallest group an
+            // exchange warp gave up before (s_stop, lowered before that
+            // barrier's arrival).  If that is gs + 1, they pass the READYs
+            // already given without waiting and finish group gs - 1 in
+            // bounded time; only then is the barrier of gs + 1's parity free
+            // of group gs - 1's arrivals.  If another exchange warp gave up
+            // at an earlier group, the compute warps never reach gs + 1.
+            int arrive = 0;
+            if (lane == 0 && s_stop > gs) {
+                atomicMin((int *)&s_stop, gs + 1);
                 const uint64_t t0 = global_ns();
                 while (*(volatile unsigned *)&s_cnt < (unsigned)(gs * nc) &&
                        (long long)(global_ns() - t0) < P.timeout_ns) {
                 }
+                arrive = 1;
             }
-            named_arrive(bar_ready(gs + 1), nbar);
+            if (__shfl_sync(0xffffffffu, arrive, 0)) named_arrive(bar_ready(gs + 1), nbar);
         }
-    } else if (warp == nc + 1) {
+    } else if (warp == nc + nxw) {
         // ---------------- release warp ----------------
-        // Releases the block's progress flag as soon as every compute warp
-        // finished and published a group; st.release orders the compute
-        // warps' stores to the exchange copy (seen through the count) before it.
+        // Releases the block's progress flag once every compute warp finished
+        // a group: the neighbours' exchange warps wait for it before their
+        // versions overwrite the slots this block may still have to read
+        // (st.release orders this block's reads before the flag).
         for (int gs = 0; gs < total; ++gs) {
             if (!res_wait_count(P, &s_cnt, (unsigned)((gs + 1) * nc), &s_abort, lane)) break;
             if (lane == 0 && blk != P.skip_tile) st_release_u32(P.flags + blk, (uint32_t)gs + 1);
@@ -468,15 +538,19 @@ __global__ void __launch_bounds__(320, 1) k_sweep_resident(const __grid_constant
                         halo();
                     }
                 }
-                // publish the rows this column wrote that other blocks read
-                const uint32_t *pe = L + po[g * nc + warp];
-                const int np = (int)(po[g * nc + warp + 1] - po[g * nc + warp]);
-                const int cpr = nx >> 4;
-                for (int q = lane; q < np * cpr; q += 32) {
-                    const int e = q / cpr, c = q - e * cpr;
-                    const uint32_t v = pe[e], slot = v >> 21, row = v & 0x1FFFFFu;
-                    *((int4 *)(P.exch + (size_t)row * nx) + c) =
-                        *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
+                // publish the versions of the rows this column wrote that other
+                // blocks read ({smem slot, version slot} entries)
+                if (blk != P.skip_tile) {
+                    const uint2 *pe = (const uint2 *)(L + po[g * nc + warp]);
+                    const int np = (int)(po[g * nc + warp + 1] - po[g * nc + warp]) >> 1;
+                    const int cpr = nx >> 3;
+                    const unsigned long long tag = (unsigned long long)(gs + 1) << 32;
+                    for (int q = lane; q < np * cpr; q += 32) {
+                        const int e = q / cpr, c = q - e * cpr;
+                        const uint2 en = pe[e];
+                        const uint2 w = *(const uint2 *)(g_smem + rows + en.x * rb + 16u + 8u * c);
+                        st_relaxed_v2u64(P.xver + ver_word(P, gs, en.y, nx) + 2 * c, tag | w.x, tag | w.y);
+                    }
                 }
             }
             // count this warp's group as done (release at CTA scope: the
@@ -531,6 +605,8 @@ __global__ void __launch_bounds__(320, 1) k_sweep_resident(const __grid_constant
 // ---------------------------------------------------------------------------
 struct ResPlan {
     int ok = 0, by = 0, bz = 0, NBy = 0, NBz = 0, nblocks = 0, nc = 0, Wy = 0, Wz = 0, rowB = 0, blob = 0;
+    int nver = 0;  // version slots (rows written in one group and read by another block)
+    int nxw = 4;   // exchange warps
     size_t smem = 0;
     std::vector<int> desc;
     std::vector<uint32_t> lists;
@@ -560,6 +636,17 @@ void column_rows(int cy, int cz, int g, int ny, int nz, int nsh, std::vector<int
     W.push_back(id(sub, y0, z0));
     for (int b = 0; b < 2; ++b)
         for (int a = 0; a < 2; ++a) W.push_back(id(1 - sub, y0 + soff + a, z0 + soff + b));
+}
+
+// Window slot of row r for a block with descriptor dd, or -1 outside.
+int res_slot_of(const int *dd, int r, int ny, int nz, int Wy, int Wz)
+{
+    const int s = r / (ny * nz), z = (r / ny) % nz, y = r % ny;
+    int yy = y - dd[4 + s], zz = z - dd[6 + s];
+    yy = ((yy % ny) + ny) % ny;
+    zz = ((zz % nz) + nz) % nz;
+    if (yy >= Wy || zz >= Wz) return -1;
+    return (s * Wz + zz) * Wy + yy;
 }
 
 template <bool IS_INT>
@@ -618,33 +705,35 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     rp.rowB = rowB;
     const int nrows_lat = 2 * ny * nz;
     auto block_of = [&](int cy, int cz) { return (cz / bz) * rp.NBy + (cy / by); };
-    // per row: writer block at every group (-1 = none), readers' blocks
+    // per row: writer block at every group (-1 = none)
     std::vector<int> wblk((size_t)nrows_lat * 32, -1);
-    std::vector<std::vector<int>> rblk(nrows_lat);
     std::vector<int> R, W;
     for (int g = 0; g < 32; ++g)
         for (int cz = 0; cz < NLz; ++cz)
             for (int cy = 0; cy < NLy; ++cy) {
                 column_rows(cy, cz, g, ny, nz, nsh, R, W);
-                const int b = block_of(cy, cz);
-                for (int r : W) wblk[(size_t)r * 32 + g] = b;
-                for (int r : R) rblk[r].push_back(b);
+                for (int r : W) wblk[(size_t)r * 32 + g] = block_of(cy, cz);
             }
-    for (auto &v : rblk) {
-        std::sort(v.begin(), v.end());
-        v.erase(std::unique(v.begin(), v.end()), v.end());
-    }
-    // last writer of row r before group g (cyclic over the sweep)
-    auto last_writer = [&](int r, int g) {
-        for (int h = g - 1; h >= g - 32; --h) {
-            const int b = wblk[(size_t)r * 32 + ((h + 32) & 31)];
+    // last write of row r before group g (cyclic over the sweep): writer
+    // block and distance d in groups (1..32), or (-1, 0) if never written
+    auto last_write = [&](int r, int g, int &d) {
+        for (d = 1; d <= 32; ++d) {
+            const int b = wblk[(size_t)r * 32 + ((g - d + 64) & 31)];
             if (b >= 0) return b;
         }
+        d = 0;
         return -1;
     };
     rp.desc.assign((size_t)rp.nblocks * kResDesc, 0);
     rp.lists.clear();
     const int nc = rp.nc;
+    std::vector<int> vslot((size_t)32 * nrows_lat, -1);  // (group of the write, row) -> version slot
+    int nver = 0;
+    struct Blk {
+        std::vector<uint32_t> hdr, body;
+    };
+    std::vector<Blk> blks(rp.nblocks);
+    bool fits = true;
     for (int blk = 0; blk < rp.nblocks; ++blk) {
         const int bky = blk % rp.NBy, bkz = blk / rp.NBy;
         const int cy0 = bky * by, cz0 = bkz * bz;
@@ -658,73 +747,99 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
         dd[5] = 4 * cy0 - 2;  // sublattice 1 rows y in [4 cy0 - 2, 4 cy0 + 4 by + 4]
         dd[6] = 4 * cz0 - 1;
         dd[7] = 4 * cz0 - 2;
-        auto slot_of = [&](int r) -> int {
-            const int s = r / (ny * nz), z = (r / ny) % nz, y = r % ny;
-            int yy = y - dd[4 + s], zz = z - dd[6 + s];
-            yy = ((yy % ny) + ny) % ny;
-            zz = ((zz % nz) + nz) % nz;
-            if (yy >= rp.Wy || zz >= rp.Wz) return -1;
-            return (s * rp.Wz + zz) * rp.Wy + yy;
-        };
-        std::vector<uint32_t> hdr(65 + 32 * nc + 1 + 2, 0), body;
-        auto entry = [&](int r) -> uint32_t {
-            const int sl = slot_of(r);
-            return ((uint32_t)sl << 21) | (uint32_t)r;
-        };
-        bool fits = true;
-        // fetch lists per group: rows read at g whose last writer is another
-        // block, those last written two or more groups back first ("early"),
-        // then those written in group g - 1 ("late"; only groups of lag 1)
+        // rows the block reads in each group
+        std::vector<std::vector<int>> reads(32);
         for (int g = 0; g < 32; ++g) {
-            hdr[g] = (uint32_t)(hdr.size() + body.size());
-            std::set<int> early, late;
             for (int k = 0; k < ncy * ncz; ++k) {
                 column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
-                for (int r : R) {
-                    if (slot_of(r) < 0) fits = false;
-                    if (last_writer(r, g) == blk) continue;
-                    if (wblk[(size_t)r * 32 + ((g + 31) & 31)] >= 0)
-                        late.insert(r);
-                    else
-                        early.insert(r);
-                }
+                reads[g].insert(reads[g].end(), R.begin(), R.end());
             }
-            if (!late.empty() && (g & 3) != 0) fits = false;  // the lag-2 rule would be broken
-            for (int r : early) body.push_back(entry(r));
-            hdr[33 + g] = (uint32_t)(hdr.size() + body.size());
-            for (int r : late) body.push_back(entry(r));
+            std::sort(reads[g].begin(), reads[g].end());
+            reads[g].erase(std::unique(reads[g].begin(), reads[g].end()), reads[g].end());
         }
-        hdr[32] = (uint32_t)(hdr.size() + body.size());
-        // publish lists per group and compute warp: written rows another block reads
+        auto reads_at = [&](int g, int r) {
+            const auto &v = reads[(g + 64) & 31];
+            return std::binary_search(v.begin(), v.end(), r);
+        };
+        Blk &B = blks[blk];
+        B.hdr.assign(33 + 32 * nc + 3, 0);  // an even size: the entry pairs stay 8-byte aligned
+        // fetch lists per group: rows read at g whose last write is another
+        // block's and whose version the block has not read since (the window
+        // keeps it): {smem slot | d << 16, version slot}
+        for (int g = 0; g < 32; ++g) {
+            B.hdr[g] = (uint32_t)(B.hdr.size() + B.body.size());
+            std::vector<std::pair<int, std::pair<uint32_t, uint32_t>>> ents;  // (-d, entry)
+            for (int r : reads[g]) {
+                int d = 0;
+                const int wb = last_write(r, g, d);
+                if (wb < 0 || wb == blk) continue;
+                bool seen = false;
+                for (int h = g - d + 1; h < g && !seen; ++h) seen = reads_at(h, r);
+                if (seen) continue;
+                const int sl = res_slot_of(dd, r, ny, nz, rp.Wy, rp.Wz);
+                if (sl < 0) {
+                    fits = false;
+                    continue;
+                }
+                int &v = vslot[(size_t)((g - d + 64) & 31) * nrows_lat + r];
+                if (v < 0) v = nver++;
+                ents.push_back({-d, {(uint32_t)sl | ((uint32_t)d << 16), (uint32_t)v}});
+            }
+            // oldest versions first: they are ready at once, and the rows
+            // written in the previous group (the ones that may still have to
+            // be waited for) come last, in as few polling rounds as possible
+            std::stable_sort(ents.begin(), ents.end(),
+                             [](const auto &a, const auto &b) { return a.first < b.first; });
+            for (const auto &en : ents) {
+                B.body.push_back(en.second.first);
+                B.body.push_back(en.second.second);
+            }
+        }
+        B.hdr[32] = (uint32_t)(B.hdr.size() + B.body.size());
+    }
+    // publish lists per (group, compute warp): the rows a column writes whose
+    // version another block reads ({smem slot, version slot}); final rows:
+    // those whose last write in the sweep is this block's
+    for (int blk = 0; blk < rp.nblocks && fits; ++blk) {
+        const int *dd = &rp.desc[(size_t)blk * kResDesc];
+        const int cy0 = dd[0], cz0 = dd[1], ncy = dd[2], ncz = dd[3];
+        Blk &B = blks[blk];
         for (int g = 0; g < 32; ++g)
             for (int k = 0; k < nc; ++k) {
-                hdr[65 + g * nc + k] = (uint32_t)(hdr.size() + body.size());
+                B.hdr[33 + g * nc + k] = (uint32_t)(B.hdr.size() + B.body.size());
                 if (k >= ncy * ncz) continue;
                 column_rows(cy0 + k % ncy, cz0 + k / ncy, g, ny, nz, nsh, R, W);
                 for (int r : W) {
-                    bool other = false;
-                    for (int b : rblk[r]) other |= b != blk;
-                    if (other) body.push_back(entry(r));
+                    const int v = vslot[(size_t)g * nrows_lat + r];
+                    if (v < 0) continue;
+                    const int sl = res_slot_of(dd, r, ny, nz, rp.Wy, rp.Wz);
+                    if (sl < 0) fits = false;
+                    B.body.push_back((uint32_t)sl);
+                    B.body.push_back((uint32_t)v);
                 }
             }
-        hdr[65 + 32 * nc] = (uint32_t)(hdr.size() + body.size());
-        // final rows: those whose last writer in the sweep is this block
-        hdr[65 + 32 * nc + 1] = (uint32_t)(hdr.size() + body.size());
+        B.hdr[33 + 32 * nc] = (uint32_t)(B.hdr.size() + B.body.size());
+        B.hdr[33 + 32 * nc + 1] = (uint32_t)(B.hdr.size() + B.body.size());
         uint32_t nfin = 0;
-        for (int r = 0; r < nrows_lat; ++r)
-            if (last_writer(r, 32) == blk) {
-                if (slot_of(r) < 0) fits = false;
-                body.push_back(entry(r));
+        for (int r = 0; r < nrows_lat; ++r) {
+            int d = 0;
+            if (last_write(r, 32, d) == blk) {
+                const int sl = res_slot_of(dd, r, ny, nz, rp.Wy, rp.Wz);
+                if (sl < 0) fits = false;
+                B.body.push_back(((uint32_t)sl << 21) | (uint32_t)r);
                 ++nfin;
             }
-        hdr[65 + 32 * nc + 2] = nfin;
-        if (!fits) return SMC_OK;  // a row outside the window (not expected)
-        dd[8] = (int)rp.lists.size();
-        dd[9] = (int)(hdr.size() + body.size());
-        rp.blob = std::max(rp.blob, dd[9]);
-        rp.lists.insert(rp.lists.end(), hdr.begin(), hdr.end());
-        rp.lists.insert(rp.lists.end(), body.begin(), body.end());
+        }
+        B.hdr[33 + 32 * nc + 2] = nfin;
+        rp.desc[(size_t)blk * kResDesc + 8] = (int)rp.lists.size();
+        rp.desc[(size_t)blk * kResDesc + 9] = (int)(B.hdr.size() + B.body.size());
+        rp.blob = std::max(rp.blob, (int)(B.hdr.size() + B.body.size()));
+        rp.lists.insert(rp.lists.end(), B.hdr.begin(), B.hdr.end());
+        rp.lists.insert(rp.lists.end(), B.body.begin(), B.body.end());
+        if (rp.lists.size() & 1) rp.lists.push_back(0u);  // next block's lists 8-byte aligned
     }
+    if (!fits) return SMC_OK;  // a row outside the window (not expected)
+    rp.nver = std::max(nver, 1);
     const int nk = (nx / 4 + 31) / 32;
     const size_t smem = (size_t)kQRows * pt.rw * 4 + 64 + (size_t)2 * rp.Wy * rp.Wz * rowB +
                         ((size_t)rp.blob * 4 + 15) / 16 * 16 + (size_t)nc * nk * 512;
@@ -732,7 +847,7 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + 2) * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + rp.nxw + 1) * 32, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1 || rp.nblocks > per_sm * ws->num_sms) return SMC_OK;
     rp.smem = smem;
@@ -839,7 +954,7 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
     if (is_int)
         for (int t = 0; t < nsweeps; ++t) table_of(kT[t]);
 
-    // workspace: [flags | part_e | part_n | ticket, abort | descriptors | lists | tables | exchange copy]
+    // workspace: [flags | part_e | part_n | ticket, abort | descriptors | lists | tables | lattice copy | versions]
     const size_t N = 2 * (size_t)lat->nx * lat->ny * lat->nz;
     const size_t nb = (size_t)rp.nblocks, np = nb * rp.nc;
     const size_t off_flags = 0, off_pe = ((nb * 4 + 15) / 16) * 16, off_pn = off_pe + np * 8;
@@ -847,7 +962,9 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
     const size_t off_lists = off_desc + ((rp.desc.size() * 4 + 15) / 16) * 16;
     const size_t off_tab = off_lists + ((rp.lists.size() * 4 + 15) / 16) * 16;
     const size_t off_exch = off_tab + ((tabs.size() * 4 + 255) / 256) * 256;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_exch + N, &st);
+    const size_t off_ver = off_exch + ((N + 255) / 256) * 256;
+    const size_t ver_bytes = (size_t)2 * rp.nver * (size_t)(lat->nx / 4) * 8;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_ver + ver_bytes, &st);
     if (!scr) return st;
     P.flags = (uint32_t *)(scr + off_flags);
     P.part_e = (double *)(scr + off_pe);
@@ -859,6 +976,9 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
     P.rlists = (const uint32_t *)(scr + off_lists);
     P.tab = (const uint32_t *)(scr + off_tab);
     P.exch = (int8_t *)(scr + off_exch);
+    P.xver = (unsigned long long *)(scr + off_ver);
+    P.nver = rp.nver;
+    P.rxw = rp.nxw;
     cudaError_t e = cudaMemcpyAsync(scr + off_desc, rp.desc.data(), rp.desc.size() * 4, cudaMemcpyHostToDevice, stream);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(scr + off_lists, rp.lists.data(), rp.lists.size() * 4, cudaMemcpyHostToDevice, stream);
@@ -876,7 +996,10 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
             else
                 P.temp.beta[t] = (float)(-1.4426950408889634 * pt.scale / kT[t0 + t]);
         }
+        // flags, sums and tags from zero: a tag (group + 1 >= 1) only ever
+        // matches a version written in this launch
         e = cudaMemsetAsync(scr, 0, off_desc, stream);
+        if (e == cudaSuccess) e = cudaMemsetAsync(scr + off_ver, 0, ver_bytes, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(resident scratch)");
         const long long nw = (long long)(N / 4);
         const int grid = (int)std::max<long long>(1, std::min<long long>((nw + 255) / 256, (long long)ws->num_sms * 8));
@@ -884,7 +1007,7 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
         e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_fail(e, "k_occ_to_exch");
         void *args[] = {(void *)&P};
-        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + 2) * 32), args, rp.smem, stream);
+        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + rp.nxw + 1) * 32), args, rp.smem, stream);
         if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(resident sweep)");
     }
     return SMC_OK;
