@@ -245,6 +245,197 @@ __global__ void __launch_bounds__(32 * kCountWarps) k_pair_counts16(const int8_t
     }
 }
 
+// The same counts from bit planes, for rows of nx % 32 == 0 sites.  A word
+// of a row holds 32 consecutive sites; plane k bit i is bit k of the species
+// of site i, so the sites of species p in a word are one three-input logic
+// function of the planes, M_p.  For a vector v (one of the visited half of a
+// shell, as above) and the word's sites i with neighbours i + v,
+//   c_m^{pq} = popc(M_p(i) & M_q(i + v)),
+// where M_q(i + v) comes from the neighbour row's word, funnel-shifted by one
+// site (with the wrap of the row) when v has an x component.  Only the sums
+// n_m^{pq} = c_m^{pq} + c_m^{qp} are needed, and for p != q the two bit sets
+// are disjoint (a site has one species), so each unordered pair costs one
+// popcount: popc((M_p(i) & M_q(i + v)) | (M_q(i) & M_p(i + v))).
+__global__ void k_planes(const int8_t *__restrict__ occ, long long nwords, uint4 *__restrict__ planes)
+{
+    const uint4 *o = reinterpret_cast<const uint4 *>(occ);
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nwords;
+         t += (long long)gridDim.x * blockDim.x) {
+        const uint4 a = __ldg(o + 2 * t), b = __ldg(o + 2 * t + 1);
+        const uint32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+        uint32_t P[3] = {0u, 0u, 0u};
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                // bit k of the four bytes at bits 0, 8, 16, 24; the product
+                // gathers them at bits 24..27 (no two partial products meet)
+                const uint32_t x = (w[j] >> k) & 0x01010101u;
+                P[k] |= ((x * 0x01020408u) >> 24) << (4 * j);
+            }
+        planes[t] = make_uint4(P[0], P[1], P[2], 0u);
+    }
+}
+
+template <int S>
+__device__ __forceinline__ void species_masks(const uint4 &w, uint32_t (&M)[S])
+{
+#pragma unroll
+    for (int p = 0; p < S; ++p)
+        M[p] = ((p & 1) ? w.x : ~w.x) & ((p & 2) ? w.y : ~w.y) & ((p & 4) ? w.z : ~w.z);
+}
+// the word of sites x - 1 (from the previous word's last site) and x + 1
+__device__ __forceinline__ uint4 site_minus1(const uint4 &prev, const uint4 &cur)
+{
+    return make_uint4(__funnelshift_l(prev.x, cur.x, 1), __funnelshift_l(prev.y, cur.y, 1),
+                      __funnelshift_l(prev.z, cur.z, 1), 0u);
+}
+__device__ __forceinline__ uint4 site_plus1(const uint4 &cur, const uint4 &next)
+{
+    return make_uint4(__funnelshift_r(cur.x, next.x, 1), __funnelshift_r(cur.y, next.y, 1),
+                      __funnelshift_r(cur.z, next.z, 1), 0u);
+}
+
+template <int NSH, int S>
+__global__ void __launch_bounds__(256) k_pair_counts_planes(const uint4 *__restrict__ planes, int nw, int ny, int nz,
+                                                            unsigned long long *counts)
+{
+    constexpr int NP = S * (S + 1) / 2;  // pairs p <= q
+    __shared__ unsigned long long bins[NSH * NP];
+    for (int i = threadIdx.x; i < NSH * NP; i += blockDim.x) bins[i] = 0;
+    __syncthreads();
+    uint32_t acc[NSH][NP];  // p < q: n^{pq}; p = q: c^{pp} = n^{pp} / 2
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) acc[m][k] = 0u;
+    const long long total = 2LL * ny * nz * nw;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long row = t / nw;
+        const int w = (int)(t - row * nw);
+        const int sub = (int)(row / ((long long)ny * nz));
+        const int rem = (int)(row - (long long)sub * ny * nz);
+        const int z = rem / ny, y = rem - z * ny;
+        auto PL = [&](int sb, int zz, int yy, int ww) {
+            ww = ww < 0 ? ww + nw : (ww >= nw ? ww - nw : ww);
+            return __ldg(planes + ((size_t)((sb * nz + wrapc(zz, nz)) * ny + wrapc(yy, ny))) * nw + ww);
+        };
+        uint32_t A[S];
+        const uint4 c = PL(sub, z, y, w);
+        species_masks<S>(c, A);
+        auto count = [&](int m, const uint4 &nb) {
+            uint32_t B[S];
+            species_masks<S>(nb, B);
+            int k = 0;
+#pragma unroll
+            for (int p = 0; p < S; ++p) {
+                acc[m][k++] += __popc(A[p] & B[p]);
+#pragma unroll
+                for (int q = p + 1; q < S; ++q) acc[m][k++] += __popc((A[p] & B[q]) | (A[q] & B[p]));
+            }
+        };
+        if (sub == 0) {
+            // shell 1: partners (1, y + dy, z + dz), dy, dz in {-1, 0}, at x - 1 and x
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int dy = (k & 1) - 1, dz = (k >> 1) - 1;
+                const uint4 r = PL(1, z + dz, y + dy, w), rp = PL(1, z + dz, y + dy, w - 1);
+                count(0, r);
+                count(0, site_minus1(rp, r));
+            }
+        }
+        if constexpr (NSH >= 2) {
+            // shell 2: +x, +y, +z
+            const uint4 ry = PL(sub, z, y + 1, w), rz = PL(sub, z + 1, y, w);
+            count(1, site_plus1(c, PL(sub, z, y, w + 1)));
+            count(1, ry);
+            count(1, rz);
+            if constexpr (NSH >= 3) {
+                // shell 3: (+x, +-y), (+x, +-z), (+y, +-z)
+                count(2, site_plus1(ry, PL(sub, z, y + 1, w + 1)));
+                count(2, site_plus1(PL(sub, z, y - 1, w), PL(sub, z, y - 1, w + 1)));
+                count(2, site_plus1(rz, PL(sub, z + 1, y, w + 1)));
+                count(2, site_plus1(PL(sub, z - 1, y, w), PL(sub, z - 1, y, w + 1)));
+                count(2, PL(sub, z + 1, y + 1, w));
+                count(2, PL(sub, z - 1, y + 1, w));
+            }
+        }
+    }
+    // at most 8 visited vectors per shell x 32 sites per word: the 32-bit
+    // counters hold 2^32 / 256 words per thread
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int m = 0; m < NSH; ++m)
+#pragma unroll
+        for (int k = 0; k < NP; ++k) {
+            const unsigned v = __reduce_add_sync(0xffffffffu, acc[m][k]);
+            if (lane == 0 && v) atomicAdd(&bins[m * NP + k], (unsigned long long)v);
+        }
+    __syncthreads();
+    for (int i = threadIdx.x; i < NSH * S * S; i += blockDim.x) {
+        const int m = i / (S * S), p = (i / S) % S, q = i % S;
+        const int a = p < q ? p : q, b = p < q ? q : p;
+        const int k = a * S - a * (a - 1) / 2 + (b - a);  // index of (a, b) among the pairs a <= b
+        const unsigned long long v = bins[m * NP + k];
+        const unsigned long long cnt = p == q ? 2 * v : v;
+        if (cnt) atomicAdd(counts + i, cnt);
+    }
+}
+
+// A grow-only device buffer for the planes (kept apart from the workspace,
+// whose scratch the callers already use for the counts).
+void *planes_buffer(size_t bytes, smc_status *st)
+{
+    static void *buf = nullptr;
+    static size_t cap = 0;
+    static int dev = -1;
+    int d = 0;
+    cudaError_t e = cudaGetDevice(&d);
+    if (e != cudaSuccess) {
+        *st = cuda_fail(e, "cudaGetDevice");
+        return nullptr;
+    }
+    if (buf && (bytes <= cap) && d == dev) return buf;
+    e = cudaDeviceSynchronize();
+    if (e == cudaSuccess && buf) e = cudaFree(buf);
+    buf = nullptr;
+    cap = 0;
+    if (e == cudaSuccess) e = cudaMalloc(&buf, bytes);
+    if (e != cudaSuccess) {
+        buf = nullptr;
+        *st = cuda_fail(e, "cudaMalloc(planes)");
+        return nullptr;
+    }
+    cap = bytes;
+    dev = d;
+    return buf;
+}
+
+template <int NSH, int S>
+void launch_planes_counts(int blocks, const uint4 *planes, int nw, int ny, int nz, unsigned long long *counts,
+                          cudaStream_t stream)
+{
+    k_pair_counts_planes<NSH, S><<<blocks, 256, 0, stream>>>(planes, nw, ny, nz, counts);
+}
+
+// Dispatch on (shells, species) with at most 84 counters per thread; false
+// when the pair is not covered.
+bool planes_counts(int NSH, int S, int blocks, const uint4 *planes, int nw, int ny, int nz,
+                   unsigned long long *counts, cudaStream_t stream)
+{
+#define SMC_PC(n, s)                                                              \
+    if (NSH == n && S == s) {                                                    \
+        launch_planes_counts<n, s>(blocks, planes, nw, ny, nz, counts, stream); \
+        return true;                                                             \
+    }
+    SMC_PC(1, 2) SMC_PC(1, 3) SMC_PC(1, 4) SMC_PC(1, 5) SMC_PC(1, 6) SMC_PC(1, 7) SMC_PC(1, 8)
+    SMC_PC(2, 2) SMC_PC(2, 3) SMC_PC(2, 4) SMC_PC(2, 5) SMC_PC(2, 6) SMC_PC(2, 7) SMC_PC(2, 8)
+    SMC_PC(3, 2) SMC_PC(3, 3) SMC_PC(3, 4) SMC_PC(3, 5) SMC_PC(3, 6) SMC_PC(3, 7)
+#undef SMC_PC
+    return false;
+}
+
 template <int NSH>
 void launch_counts16(int S, int blocks, int threads, const int8_t *occ, int nx, int ny, int nz,
                      unsigned long long *counts, cudaStream_t stream)
@@ -271,6 +462,19 @@ smc_status launch_pair_counts(const smc_lattice *lat, int nshells, const int8_t 
     cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(unsigned long long) * nshells * S * S, stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counts)");
     const long long rows = 2LL * lat->ny * lat->nz;
+    if (lat->nx % 32 == 0 && reinterpret_cast<uintptr_t>(occ) % 16 == 0 && S >= 2 &&
+        S * (S + 1) / 2 * nshells <= 84) {
+        const int nw = lat->nx / 32;
+        const long long nwords = rows * nw;
+        uint4 *planes = (uint4 *)planes_buffer((size_t)nwords * sizeof(uint4), &st);
+        if (!planes) return st;
+        const int grid = (int)std::max(1LL, std::min<long long>((nwords + 255) / 256, (long long)ws->num_sms * 8));
+        k_planes<<<grid, 256, 0, stream>>>(occ, nwords, planes);
+        if (planes_counts(nshells, S, ws->num_sms * 4, planes, nw, lat->ny, lat->nz, counts, stream)) {
+            e = cudaGetLastError();
+            return e == cudaSuccess ? SMC_OK : cuda_fail(e, "k_pair_counts_planes");
+        }
+    }
     const int threads = 256;
     const long long want = (rows + 7) / 8;
     const int blocks = (int)std::max(1LL, std::min<long long>(want, (long long)ws->num_sms * 8));

@@ -227,7 +227,10 @@ def test_counts_sro_energy_grad_match_oracle(smc):
                          ((1100, 4, 2), 8, 3),
                          # rows of a multiple of 16 cells take the 16-byte-load kernel
                          ((32, 8, 12), 5, 2), ((48, 2, 4), 3, 1), ((16, 6, 10), 2, 3), ((528, 4, 2), 4, 3),
-                         ((1024, 2, 2), 7, 2), ((64, 4, 4), 6, 1)):
+                         ((1024, 2, 2), 7, 2), ((64, 4, 4), 6, 1),
+                         # rows of a multiple of 32 cells (at most 84 pair counters) take the bit-plane kernel
+                         ((64, 6, 10), 5, 3), ((96, 4, 6), 6, 2), ((32, 2, 2), 8, 1), ((256, 8, 8), 5, 2),
+                         ((160, 6, 4), 2, 3), ((32, 3, 5), 4, 3), ((64, 4, 6), 8, 2), ((32, 4, 4), 7, 3)):
         N = 2 * dims[0] * dims[1] * dims[2]
         counts = inputs.equiatomic_counts(N, S)
         lat, occ = gpu_state(smc, dims, S, counts, 21)
@@ -247,6 +250,20 @@ def test_counts_sro_energy_grad_match_oracle(smc):
         g = torch.zeros(smc.grad_size(lat, m), dtype=torch.float32, device=dev())
         smc.energy_grad(lat, m, occ, g)
         assert np.array_equal(g.cpu().numpy().astype(np.float64), oracle.energy_grad(olat, om, ref))
+
+
+@pytest.mark.parametrize("dims,S,nsh", [((512, 64, 64), 5, 2), ((128, 128, 128), 5, 3)])
+def test_pair_counts_full_row_lengths(smc, dims, S, nsh):
+    """The bit-plane count kernel on rows of 16 and 4 words (the lengths of
+    the 512^3 and 128^3 lattices), bit-exact against the oracle."""
+    N = 2 * dims[0] * dims[1] * dims[2]
+    counts = inputs.equiatomic_counts(N, S)
+    lat, occ = gpu_state(smc, dims, S, counts, 5)
+    olat = oracle.Lattice(*dims, S)
+    ref = oracle.init_lattice(olat, counts, 5)
+    cnt = torch.zeros((nsh, S, S), dtype=torch.int64, device=dev())
+    smc.sro(lat, nsh, occ, counts=cnt)
+    assert np.array_equal(cnt.cpu().numpy(), oracle.pair_counts(olat, nsh, ref))
 
 
 def test_batched_replicas_equal_single_runs(smc):
