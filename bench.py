@@ -41,7 +41,6 @@ QSRO_SEED, QSRO_SHELLS = 7, 2  # qSRO workload parameters
 # zone sites of a qSRO trial besides a and b (within the model's shells of
 # either), counted from the BCC geometry
 QSRO_ZONE = {1: 14, 2: 20, 3: 38}
-INSTR_PER_TRIAL_512 = 352.9  # thread instructions per trial of k_sweep_fast at 512^3 (ncu)
 MLP_FLOP_PER_SITE_FWD = 2 * (20 * 64 + 64 * 64)  # 10752
 MLP_FLOP_PER_SITE_GRAD = MLP_FLOP_PER_SITE_FWD + 2 * 64 * 64 + 2 * 64 * 64 + 2 * 20 * 64  # 29696
 MLP_FLOP_PER_ATTEMPT = 40 * MLP_FLOP_PER_SITE_FWD  # post-swap energies of the 40-site zone (cached pre-swap)
@@ -257,7 +256,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > 129 MB L2
     stream = torch.cuda.current_stream()
     nsw = prob["nsweeps"]
-    launches_per_step = 1 + 2 + 2  # sweep kernel; counts + energy finish; counts + SRO finish
+    # our kernels per step: lattice copy + resident sweep; bit planes + pair
+    # counts + energy finish; bit planes + pair counts + SRO finish
+    launches_per_step = 2 + 3 + 3
 
     def job(sw_ev=None):
         if sw_ev:
@@ -338,7 +339,7 @@ def main():
         dist.destroy_process_group()
     if rank != 0:
         return
-    traffic = kernel_traffic("k_sweep_fast_bcc128_1000sweeps")
+    traffic = profile_record("k_sweep_resident_bcc128_1000sweeps", "bytes_per_launch")
     line = {
         "metric": METRIC, "value": value, "unit": "attempts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
@@ -350,9 +351,10 @@ def main():
                    "parallelism": f"replicas x{world}"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": pk["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / pk["hbm_gbs"], "traffic": traffic,
-                     "kernel": "k_sweep_fast (one launch = 1000 sweeps)",
+                     "kernel": "k_sweep_resident (one launch = 1000 sweeps)",
                      "bytes_per_attempt": BYTES_PER_ATTEMPT, "peak_source": pk["source"] + " hbm_gbs",
-                     "note": "the 4.2 MB lattice is L2-resident; see extras.hbm_512 for the HBM-resident case"},
+                     "note": "the 4.2 MB lattice stays in shared memory for the launch; see extras.hbm_512 "
+                             "for the HBM-resident case"},
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": "attempts/s", "h2d_bytes_per_step": prob["N"],
                 "d2h_bytes_per_step": prob["N"] + 8 * (1 + 2 * 3 * prob["S"] * prob["S"])},
@@ -470,21 +472,22 @@ def profile_mlp(n: int, nsweeps: int, net: bool = False):
     print(json.dumps({"profile_mlp": [256, n, n], "net": net, "sweeps": nsweeps, "ok": True}))
 
 
-def kernel_traffic(name: str):
-    """DRAM bytes per launch from profiles/traffic.json, or None when the
-    kernel source changed after the counters were taken."""
+def profile_record(name: str, field: str):
+    """A counter figure from profiles/traffic.json (ncu, per launch), or None
+    when a source it names changed after the counters were taken."""
     import hashlib
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(tp):
         return None
     with open(tp) as f:
         d = json.load(f).get(name)
-    if not d:
+    if not d or field not in d:
         return None
-    src = os.path.join(ROOT, d["source"])
-    with open(src, "rb") as f:
-        h = hashlib.sha256(f.read()).hexdigest()
-    return d["bytes_per_launch"] if h == d["source_sha256"] else None
+    for src, sha in d["sources"].items():
+        with open(os.path.join(ROOT, src), "rb") as f:
+            if hashlib.sha256(f.read()).hexdigest() != sha:
+                return None
+    return d[field]
 
 
 def run_extras(smc, torch, dev, pk):
@@ -493,6 +496,14 @@ def run_extras(smc, torch, dev, pk):
     S = 5
     V = inputs.pair_f32_coeffs(inputs.CONFIG2["coeff_seed"], 2, S)
     model = smc.Model(smc.PAIR_F32, 2, V)
+
+    def unlike_fraction(l, o):
+        # fraction of first-shell bonds joining two species: the share of
+        # attempts (partner = a first-shell neighbour) the MLP sweeps evaluate
+        c = torch.zeros((1, S, S), dtype=torch.int64, device=dev)
+        smc.sro(l, 1, o, counts=c)
+        c = c[0].double()
+        return float(1.0 - torch.diagonal(c).sum() / c.sum())
 
     def timed(fn, reps=1):
         fn()
@@ -514,23 +525,26 @@ def run_extras(smc, torch, dev, pk):
     nsw = 4
     ms = timed(lambda: smc.sweep(lat, model, occ, 1, 0, nsw, kT[:nsw]), reps=2)
     att = lat.nsites * nsw / (ms * 1e-3)
-    # integer-issue ceiling beside the HBM one: every SM issues at most 4 warp
-    # instructions (128 lanes) per clock, and one trial costs the measured
-    # instructions per trial (profiles/k_sweep_fast_bcc512.md)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    issue_cap = sms * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / INSTR_PER_TRIAL_512
     out["hbm_512"] = {"cells": [n, n, n], "sweeps_per_launch": nsw, "ms_per_sweep": ms / nsw,
                       "attempts_per_s": att, "achieved_gbs": att * BYTES_PER_ATTEMPT / 1e9,
-                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"],
-                      "alu": {"instructions_per_trial": INSTR_PER_TRIAL_512, "issue_ceiling_attempts_per_s": issue_cap,
-                              "frac_of_issue_ceiling": att / issue_cap,
-                              "source": "ncu smsp__inst_executed.sum x 32 / trials, 512^3 sweep"}}
+                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+    # integer-issue ceiling beside the HBM one: every SM issues at most 4 warp
+    # instructions (128 lanes) per clock, and a trial costs the instructions
+    # ncu counted on this kernel source (None once the source changed)
+    ipt = profile_record("k_sweep_fast_bcc512_4sweeps", "instructions_per_trial")
+    if ipt:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        issue_cap = sms * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / ipt
+        out["hbm_512"]["alu"] = {"instructions_per_trial": ipt, "issue_ceiling_attempts_per_s": issue_cap,
+                                 "frac_of_issue_ceiling": att / issue_cap,
+                                 "source": "profiles/traffic.json: ncu smsp__inst_executed.sum x 32 / trials"}
     # gradient of E (pair part) at the 512^3 configuration vs one plain sweep of it
     g = torch.zeros(smc.grad_size(lat, model), dtype=torch.float32, device=dev)
     gms = timed(lambda: smc.energy_grad(lat, model, occ, g), reps=3)
     out["grad_512"] = {"ms_per_configuration": gms, "ms_per_plain_sweep": ms / nsw,
                        "ratio_to_sweep": gms / (ms / nsw), "params": int(g.numel()),
-                       "achieved_gbs": lat.nsites / (gms * 1e-3) / 1e9}
+                       "bytes_per_site": 1, "achieved_gbs": lat.nsites / (gms * 1e-3) / 1e9,
+                       "frac_of_measured_hbm": lat.nsites / (gms * 1e-3) / 1e9 / pk["hbm_gbs"]}
     del occ
     # batched: 64 uneven replicas on a temperature ladder, one launch
     c3 = inputs.CONFIG3
@@ -553,16 +567,30 @@ def run_extras(smc, torch, dev, pk):
     smc.set_tuning()
     tot = sum(l.nsites for l in lats)
     batt = tot * nb / (bms * 1e-3)
+    del graph
+    for o in occs:
+        del o
+    occs.clear()
+    # the matched plain sweep: one 256^3 lattice (3.4e7 sites, about the
+    # ladder's 3.9e7), same model, one launch of the same number of sweeps at
+    # the ladder's middle temperature
+    n2 = 256
+    lat2 = smc.Lattice(n2, n2, n2, S)
+    occ2 = torch.empty(lat2.nsites, dtype=torch.int8, device=dev)
+    smc.init_lattice(lat2, inputs.equiatomic_counts(lat2.nsites, S), 1, occ2)
+    kTm = float(np.median(kTr))
+    pms = timed(lambda: smc.sweep(lat2, model, occ2, 1, 0, nb, kTm), reps=1)
+    patt = lat2.nsites * nb / (pms * 1e-3)
+    del occ2
     out["batched_64"] = {"replicas": len(lats), "edges_min_max": [int(edges.min()), int(edges.max())],
                          "total_sites": tot, "sweeps": nb, "launch": "one CUDA graph replay (one persistent kernel)",
                          "tuning": {"tile_y": best[0], "tile_z": best[1], "threads": best[2], "ctas_per_sm": best[3]},
                          "tuning_ms_per_sweep": {"x".join(map(str, k)): round(v, 4) for k, v in tune_ms.items()},
                          "attempts_per_s": batt,
-                         "frac_of_measured_hbm": batt * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
-    del graph
-    for o in occs:
-        del o
-    occs.clear()
+                         "frac_of_measured_hbm": batt * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"],
+                         "plain_sweep": {"cells": [n2] * 3, "sites": lat2.nsites, "sweeps": nb, "kT_eV": kTm,
+                                         "attempts_per_s": patt},
+                         "ratio_to_plain_sweep": batt / patt}
     # MLP site energies on the tensor cores: 256^3 Dirichlet quinary at 800 K
     c4 = inputs.CONFIG4
     n4 = c4["cells"][0]
@@ -573,28 +601,37 @@ def run_extras(smc, torch, dev, pk):
     kT4 = inputs.K_B_EV * c4["T"]
     n_acc = torch.zeros(1, dtype=torch.int64, device=dev)
     nsw4 = 2
+    f0 = unlike_fraction(lat4, occ4)
     ms4 = timed(lambda: smc.sweep(lat4, mlp_model, occ4, c4["mc_seed"], 0, nsw4, kT4, n_acc=n_acc), reps=1)
+    fev = 0.5 * (f0 + unlike_fraction(lat4, occ4))
     att4 = lat4.nsites * nsw4 / (ms4 * 1e-3)
     acc_rate = float(n_acc.item()) / (2 * lat4.nsites * nsw4)  # warm-up call + timed call
-    tfl = att4 * MLP_FLOP_PER_ATTEMPT / 1e12
+    tfl = att4 * fev * MLP_FLOP_PER_ATTEMPT / 1e12
     out["mlp_256"] = {"cells": [n4] * 3, "sweeps_per_launch": nsw4, "ms_per_sweep": ms4 / nsw4,
                       "attempts_per_s": att4, "job_s_200_sweeps": ms4 / nsw4 * c4["nsweeps"] / 1e3,
-                      "accept_rate": acc_rate, "achieved_tflops": tfl,
+                      "accept_rate": acc_rate, "evaluated_fraction": fev, "achieved_tflops": tfl,
+                      "achieved_tflops_if_every_attempt": att4 * MLP_FLOP_PER_ATTEMPT / 1e12,
                       "frac_of_measured_bf16_sustained": tfl / pk["bf16_tflops_sustained"],
-                      "flop_per_attempt": MLP_FLOP_PER_ATTEMPT}
+                      "flop_per_evaluated_attempt": MLP_FLOP_PER_ATTEMPT,
+                      "note": "attempts with equal species (dE = 0) are not evaluated; evaluated_fraction is the "
+                              "unlike first-shell bond fraction before and after the timed sweeps"}
     e4 = torch.zeros(1, dtype=torch.float64, device=dev)
     ems = timed(lambda: smc.energy(lat4, mlp_model, occ4, e4), reps=3)
     out["mlp_energy_256"] = {"ms": ems, "achieved_tflops": lat4.nsites * MLP_FLOP_PER_SITE_FWD / (ems * 1e-3) / 1e12}
     # MLPNet at the paper's shape on the same lattice and temperature
     net_model = smc.Model(smc.MLPNET_BF16, net=inputs.mlpnet_weights(c4["mlp_seed"]))
     n_accn = torch.zeros(1, dtype=torch.int64, device=dev)
+    f0 = unlike_fraction(lat4, occ4)
     msn = timed(lambda: smc.sweep(lat4, net_model, occ4, c4["mc_seed"], 0, nsw4, kT4, n_acc=n_accn), reps=1)
+    fevn = 0.5 * (f0 + unlike_fraction(lat4, occ4))
     attn = lat4.nsites * nsw4 / (msn * 1e-3)
-    tfn = attn * NET_FLOP_PER_ATTEMPT / 1e12
+    tfn = attn * fevn * NET_FLOP_PER_ATTEMPT / 1e12
     out["mlpnet_256"] = {"cells": [n4] * 3, "sweeps_per_launch": nsw4, "ms_per_sweep": msn / nsw4,
                          "attempts_per_s": attn, "accept_rate": float(n_accn.item()) / (2 * lat4.nsites * nsw4),
-                         "achieved_tflops": tfn, "frac_of_measured_bf16_sustained": tfn / pk["bf16_tflops_sustained"],
-                         "flop_per_attempt": NET_FLOP_PER_ATTEMPT}
+                         "evaluated_fraction": fevn, "achieved_tflops": tfn,
+                         "achieved_tflops_if_every_attempt": attn * NET_FLOP_PER_ATTEMPT / 1e12,
+                         "frac_of_measured_bf16_sustained": tfn / pk["bf16_tflops_sustained"],
+                         "flop_per_evaluated_attempt": NET_FLOP_PER_ATTEMPT}
     en = torch.zeros(1, dtype=torch.float64, device=dev)
     emsn = timed(lambda: smc.energy(lat4, net_model, occ4, en), reps=3)
     out["mlpnet_energy_256"] = {"ms": emsn,
@@ -661,6 +698,48 @@ def run_extras(smc, torch, dev, pk):
     out["mlp_grad_512"] = {"cells": [n5] * 3, "ms_per_configuration": gms5, "params": int(g5.numel()),
                            "achieved_tflops": tf5, "frac_of_measured_bf16_sustained": tf5 / pk["bf16_tflops_sustained"],
                            "flop_per_site": MLP_FLOP_PER_SITE_GRAD}
+    # Config 5 as a job: at 600 K, equilibration sweeps, then samples of (one
+    # sweep, SRO of shells 1-3, dE/dtheta) and d<alpha>/dtheta from their
+    # covariance.  The job has 20 + 200; a bounded part is timed here (2
+    # equilibration sweeps, 4 samples) and the job's time extrapolated.
+    kT5 = inputs.K_B_EV * c5["T"]
+    n_eq, n_s = 2, 4
+    A5 = torch.zeros((n_s, 3, S, S), dtype=torch.float64, device=dev)
+    G5 = torch.zeros((n_s, g5.numel()), dtype=torch.float64, device=dev)
+    cnt5 = torch.zeros((3, S, S), dtype=torch.int64, device=dev)
+    al5 = torch.zeros((3, S, S), dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(True) for _ in range(2 + 3 * n_s)]
+    ev[0].record(stream)
+    smc.sweep(lat5, m5, occ5, c5["mc_seed"], 0, n_eq, kT5)
+    ev[1].record(stream)
+    for i in range(n_s):
+        ev[2 + 3 * i].record(stream)
+        smc.sweep(lat5, m5, occ5, c5["mc_seed"], n_eq + i, 1, kT5)
+        ev[3 + 3 * i].record(stream)
+        smc.sro(lat5, 3, occ5, counts=cnt5, alpha=al5)
+        smc.energy_grad(lat5, m5, occ5, g5)
+        A5[i].copy_(al5)
+        G5[i].copy_(g5)
+        ev[4 + 3 * i].record(stream)
+    torch.cuda.synchronize()
+    smc.check()
+    sw5 = float(np.mean([ev[2 + 3 * i].elapsed_time(ev[3 + 3 * i]) for i in range(n_s)]))
+    ob5 = float(np.mean([ev[3 + 3 * i].elapsed_time(ev[4 + 3 * i]) for i in range(n_s)]))
+    eq5 = ev[0].elapsed_time(ev[1]) / n_eq
+    dadt = smc.observable_gradient(A5, G5, 1.0 / kT5)
+    out["config5_512"] = {"cells": [n5] * 3, "T_K": c5["T"], "model": "FP32 2-shell pair + BF16 MLP",
+                          "equilibration_sweeps_timed": n_eq, "samples_timed": n_s,
+                          "ms_per_model_sweep": 0.5 * (eq5 + sw5),
+                          "ms_per_configuration": ob5,
+                          "ms_per_sample": sw5 + ob5,
+                          "ratio_configuration_to_model_sweep": ob5 / sw5,
+                          "ratio_configuration_to_plain_pair_sweep": ob5 / (ms / nsw),
+                          "job_s_20_equilibration_200_samples": (20 * eq5 + 200 * (sw5 + ob5)) / 1e3,
+                          "dalpha_dtheta_shape": list(dadt.shape),
+                          "dalpha_dtheta_finite": bool(torch.isfinite(dadt).all()),
+                          "note": "configuration = SRO (pair counts, alpha) + dE/dtheta (pair counts and the MLP "
+                                  "adjoint); d<alpha>/dtheta = -beta cov(alpha, dE/dtheta) over the samples"}
     return out
 
 
