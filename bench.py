@@ -194,6 +194,8 @@ def main():
     ap.add_argument("--profile-sweep", type=int, default=0,
                     help="profiling driver: one sweep launch on an N^3 quinary FP32 lattice, nothing else")
     ap.add_argument("--profile-sweeps", type=int, default=1)
+    ap.add_argument("--profile-counts", type=int, default=0,
+                    help="profiling driver: the pair gradient (bit planes + pair counts) of an N^3 quinary lattice")
     ap.add_argument("--profile-mlp", type=int, default=0,
                     help="run the MLP workload (800 K) on a 256 x n x n box once, for ncu captures")
     ap.add_argument("--profile-mlpnet", type=int, default=0,
@@ -222,6 +224,9 @@ def main():
         return
     if args.profile_sweep:
         profile_sweep(args.profile_sweep, args.profile_sweeps)
+        return
+    if args.profile_counts:
+        profile_counts(args.profile_counts)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -381,6 +386,24 @@ def profile_sweep(n: int, nsweeps: int):
     smc.sweep(lat, model, occ, 1, 0, nsweeps, inputs.anneal_kT(1000)[:nsweeps])
     smc.check()
     print(json.dumps({"profile_sweep": n, "sweeps": nsweeps, "ok": True}))
+
+
+def profile_counts(n: int):
+    """One pair-gradient call (bit planes, pair counts, finish) on the n^3
+    config-2 lattice, for ncu captures (-k regex:k_pair_counts)."""
+    import torch
+    from paper_2604_08250_gb300 import build as _b
+    from paper_2604_08250_gb300 import smc
+    _b.build()
+    S = 5
+    lat = smc.Lattice(n, n, n, S)
+    occ = torch.empty(lat.nsites, dtype=torch.int8, device="cuda")
+    smc.init_lattice(lat, inputs.equiatomic_counts(lat.nsites, S), 1, occ)
+    model = smc.Model(smc.PAIR_F32, 2, inputs.pair_f32_coeffs(inputs.CONFIG2["coeff_seed"], 2, S))
+    g = torch.zeros(smc.grad_size(lat, model), dtype=torch.float32, device="cuda")
+    smc.energy_grad(lat, model, occ, g)
+    smc.check()
+    print(json.dumps({"profile_counts": n, "ok": True}))
 
 
 def qsro_setup(smc, n: int, dev):
