@@ -260,6 +260,36 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
                               uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k,
                               double kT, float *dE, uint8_t *acc, cudaStream_t stream);
 
+/* Mini-step k of sweep `sweep` on one x-slab of the box `lat` (Sec. III-B,
+ * 1D slab decomposition; pair models).  The slab owns cells
+ * x0 <= x < x0 + w of every row; win holds cells [x0 - g, x0 + w + g)
+ * (x modulo nx) as [2][nz][ny][w + 2g] int8 (device, updated in place).
+ * The slab's trials run exactly as in smc_sweep on the whole box -- the same
+ * link cells, the random word of the global site id, the same dE and
+ * decision -- so W slabs that run every mini-step and then exchange the
+ * cells each changed within g of its edges (the ranges of the Python
+ * module slab.py) reproduce smc_sweep bit for bit.
+ *   x0, w    multiples of 4, w >= 4, x0 + w <= nx (nx a multiple of 4, >= 8).
+ *   g        ghost cells per side, 2 <= g <= w (a pair trial reads 2 cells
+ *            past its own along x).
+ *   part     0: every link cell of the slab; 1: the first and last link cell
+ *            of each x-row (the trials that change cells within 3 of the
+ *            slab's edges, the cells the exchange sends); 2: the others
+ *            (reads and writes inside the slab).  Parts 1 and 2 together
+ *            equal part 0 in either order: a mini-step's trials touch
+ *            disjoint cells.  Part 2 reads no ghost cell and writes none of
+ *            the cells the exchange sends, so it may run while the frames of
+ *            its own mini-step travel -- the cells part 1 changed going out,
+ *            the neighbours' changes coming into the ghosts (the overlap of
+ *            Sec. V-C).
+ *   e_acc, n_acc  device, nullable: += accepted dE (eV) and count.
+ * Errors: SMC_ERR_ARG for the ranges above; SMC_ERR_UNSUPPORTED for MLP,
+ * MLPNet and qSRO models. */
+smc_status smc_slab_ministep(const smc_lattice *lat, const smc_model *model, int8_t *win, int32_t x0,
+                             int32_t w, int32_t g, uint64_t seed, uint32_t replica, uint64_t sweep,
+                             int32_t k, double kT, double *e_acc, int64_t *n_acc, int32_t part,
+                             cudaStream_t stream);
+
 /* FCC lattice (the paper's lattice, Sec. IV-C), pair models (SMC_PAIR_I32,
  * SMC_PAIR_F32) and the qSRO model (SMC_QSRO_F32, Eq. quadratic_local_SRO
  * with the FCC shells, z_m = 12, 6, 24; the sweep keeps a cache of

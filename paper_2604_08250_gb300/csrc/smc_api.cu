@@ -516,6 +516,41 @@ smc_status smc_ministep_trace(const smc_lattice *lat, const smc_model *model, in
     return launch_ministep_trace(lat, model, occ, seed, replica, sweep, k, kT, dE, acc, stream);
 }
 
+smc_status smc_slab_ministep(const smc_lattice *lat, const smc_model *model, int8_t *win, int32_t x0, int32_t w,
+                             int32_t g, uint64_t seed, uint32_t replica, uint64_t sweep, int32_t k, double kT,
+                             double *e_acc, int64_t *n_acc, int32_t part, cudaStream_t stream)
+{
+    API_LOCK;
+    smc_status st = check_sweep_args(lat, model, win, 1, &kT, 1, sweep);
+    if (st != SMC_OK) return st;
+    if (model->kind != SMC_PAIR_I32 && model->kind != SMC_PAIR_F32) {
+        set_error("the slab mini-step takes pair models");
+        return SMC_ERR_UNSUPPORTED;
+    }
+    if (lc_edge(lat->nx) != 4) {
+        set_error("slabs need nx >= 8 and a multiple of 4 (got %d)", lat->nx);
+        return SMC_ERR_ARG;
+    }
+    if (x0 < 0 || w < 4 || x0 % 4 != 0 || w % 4 != 0 || x0 + w > lat->nx) {
+        set_error("slab [%d, %d) must be whole link cells inside [0, %d)", x0, x0 + w, lat->nx);
+        return SMC_ERR_ARG;
+    }
+    if (g < 2 || g > w) {
+        set_error("ghost cells g = %d must lie in [2, w = %d]", g, w);
+        return SMC_ERR_ARG;
+    }
+    if (part < 0 || part > 2) {
+        set_error("part must be 0 (all), 1 (edge link cells) or 2 (interior)");
+        return SMC_ERR_ARG;
+    }
+    const int nA = 2 * 4 * lc_edge(lat->ny) * lc_edge(lat->nz);
+    if (k < 0 || k >= nA) {
+        set_error("mini-step %d out of range [0, %d)", k, nA);
+        return SMC_ERR_ARG;
+    }
+    return launch_slab_ministep(lat, model, win, x0, w, g, seed, replica, sweep, k, kT, e_acc, n_acc, part, stream);
+}
+
 // ---- FCC lattice (Sec. IV-C), pair models ----
 
 static bool fcc_lattice_valid(const smc_lattice *lat)

@@ -169,6 +169,9 @@ smc_status launch_pair_sweep_noalloc(const smc_lattice *lat, const smc_model *m,
 smc_status launch_ministep_trace(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                                  uint32_t replica, uint64_t sweep, int k, double kT, float *dE,
                                  uint8_t *acc, cudaStream_t stream);
+smc_status launch_slab_ministep(const smc_lattice *lat, const smc_model *m, int8_t *win, int x0, int w, int g,
+                                uint64_t seed, uint32_t replica, uint64_t sweep, int k, double kT, double *e_acc,
+                                int64_t *n_acc, int part, cudaStream_t stream);
 // Warp count of a warp-per-tile kernel (warp w owns tiles w, w + NW, ...)
 // that gives the busiest SM the fewest tiles (defined in sweep_pair.cu).
 long long balanced_warps(long long ntiles, int nwarps, int per_sm, int num_sms);

@@ -1820,6 +1820,179 @@ smc_status launch_pair_sweep(int R, const smc_lattice *lats, const smc_model *m,
     return sweep_impl<false>(R, lats, m, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc, stream);
 }
 
+// ---------------------------------------------------------------------------
+// One mini-step on one x-slab (Sec. III-B, 1D slab decomposition).  The
+// window holds cells [x0 - g, x0 + w + g) of every row, laid out as the box
+// with x restricted to it: [sub][z][y][w + 2 g].  The trials of the slab's
+// link cells run as in the whole box, each with the random word of its
+// global site id, and apply their swaps in place (the trials of a mini-step
+// touch disjoint cells).  part 1 runs the first and last link cell of every
+// x-row of the slab -- the trials that change cells within g <= 3 of the
+// slab's edges, the cells the ghost exchange sends -- part 2 the others,
+// whose reads and writes stay inside the slab, and part 0 all of them.
+// ---------------------------------------------------------------------------
+struct SlabView {
+    unsigned char *occ;
+    int W, ny, nz, sub, y0, z0;
+    __device__ __forceinline__ unsigned char *O(int dy, int dz) const
+    {
+        return occ + ((size_t)((sub * nz + wrapc(z0 + dz, nz)) * ny + wrapc(y0 + dy, ny))) * W;
+    }
+    __device__ __forceinline__ unsigned char *T(int dy, int dz) const
+    {
+        return occ + ((size_t)(((1 - sub) * nz + wrapc(z0 + dz, nz)) * ny + wrapc(y0 + dy, ny))) * W;
+    }
+};
+
+template <bool IS_INT, int NSH, int SW>
+__global__ void __launch_bounds__(128) k_slab_ministep(const __grid_constant__ SweepParams P, int k, int x0, int w,
+                                                       int g, int part, long long *sums)
+{
+    __shared__ __align__(16) uint32_t Qt[kPairQWords];
+    __shared__ long long s_e[4], s_n[4];
+    for (int i = threadIdx.x; i < kQRows * P.qrow; i += blockDim.x) Qt[i] = P.qtab[i];
+    __syncthreads();
+    const RepDesc &RD = P.rep[0];
+    const int ncx = w / 4;
+    const int ncp = part == 0 ? ncx : (part == 1 ? min(ncx, 2) : max(ncx - 2, 0));
+    const int ntr = ncp * RD.NLy * RD.NLz;
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    long long e = 0, n = 0;
+    if (c < ntr) {
+        const int ci = c % ncp, cy = (c / ncp) % RD.NLy, cz = c / (ncp * RD.NLy);
+        const int cx = part == 2 ? 1 + ci : (part == 1 && ci == 1 ? ncx - 1 : ci);
+        const int dx = k % 4, dy = (k / 4) % P.Ly, dz = (k / (4 * P.Ly)) % P.Lz;
+        const int sub = k / (4 * P.Ly * P.Lz);
+        const int s_off = sub == 0 ? -1 : 0;
+        const int nx = RD.nx, ny = RD.ny, nz = RD.nz, W = w + 2 * g;
+        const int xg = x0 + 4 * cx + dx, xl = xg - x0 + g;
+        const int y0 = cy * P.Ly + dy, z0 = cz * P.Lz + dz;
+        const SlabView sv{(unsigned char *)RD.occ, W, ny, nz, sub, y0, z0};
+        const uint32_t site = (uint32_t)(((sub * nz + z0) * ny + y0) * nx + xg);
+        const uint32_t wd = site_word(P.seed, RD.rep, P.sweep0, site);
+        int A, B, ex, ey, ez;
+        const int32_t dE =
+            trial_dE_hist<NSH, SW, SlabView>(sv, xl, W, s_off, (int)(wd >> kRBits), Qt, P.qrow, A, B, ex, ey, ez);
+        float cxp = 0.f;
+        int2 ti = make_int2(0, 0);
+        if constexpr (IS_INT)
+            ti = P.temp.tabinfo[0];
+        else
+            cxp = P.temp.beta[0];
+        if (accept_fixed<IS_INT>(dE, wd & kRMask, cxp, P.tab, ti)) {
+            if (A != B) {
+                sv.O(0, 0)[xl] = (unsigned char)B;
+                sv.T(ey, ez)[xl + ex] = (unsigned char)A;
+            }
+            e = dE;
+            n = 1;
+        }
+    }
+    e = warp_sum<long long>(e);
+    n = warp_sum<long long>(n);
+    const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_e[wp] = e;
+        s_n[wp] = n;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        long long te = 0, tn = 0;
+        for (int i = 0; i < (int)(blockDim.x >> 5); ++i) {
+            te += s_e[i];
+            tn += s_n[i];
+        }
+        if (te) atomicAdd((unsigned long long *)sums, (unsigned long long)te);
+        if (tn) atomicAdd((unsigned long long *)sums + 1, (unsigned long long)tn);
+    }
+}
+
+// e_acc += sum dE_fix * escale; n_acc += count (one thread).
+__global__ void k_slab_finish(const long long *sums, double escale, double *e_acc, int64_t *n_acc)
+{
+    if (e_acc) *e_acc += (double)sums[0] * escale;
+    if (n_acc) *n_acc += sums[1];
+}
+
+template <bool IS_INT>
+static smc_status slab_impl(const smc_lattice *lat, const smc_model *m, int8_t *win, int x0, int w, int g,
+                            uint64_t seed, uint32_t replica, uint64_t sweep, int k, double kT, double *e_acc,
+                            int64_t *n_acc, int part, cudaStream_t stream)
+{
+    smc_status st;
+    Workspace *ws = workspace(&st);
+    if (!ws) return st;
+    PairTable pt;
+    if (!build_pair_table(m, lat->nspecies, pt)) {
+        set_error("pair coefficients must be finite");
+        return SMC_ERR_ARG;
+    }
+    static SweepParams P;
+    memset(&P, 0, sizeof P);
+    P.R = 1;
+    P.Lx = 4;
+    P.Ly = lc_edge(lat->ny);
+    P.Lz = lc_edge(lat->nz);
+    P.nshells = m->nshells;
+    P.S = lat->nspecies;
+    P.seed = seed;
+    P.sweep0 = sweep;
+    RepDesc &d = P.rep[0];
+    d.occ = win;
+    d.nx = lat->nx;
+    d.ny = lat->ny;
+    d.nz = lat->nz;
+    d.NLx = d.nx / 4;
+    d.NLy = d.ny / P.Ly;
+    d.NLz = d.nz / P.Lz;
+    d.rep = replica;
+    load_table(P, pt);
+    std::vector<uint32_t> tab;
+    if (IS_INT) {
+        tab = int_table(m->unit_ev, kT);
+        P.temp.tabinfo[0] = make_int2(0, (int)tab.size());
+    } else {
+        P.temp.beta[0] = accept_cx(pt.scale, kT);
+    }
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, 16 + tab.size() * 4 + 16, &st);
+    if (!scr) return st;
+    long long *sums = (long long *)scr;
+    P.tab = (const uint32_t *)(scr + 16);
+    cudaError_t e = cudaMemsetAsync(sums, 0, 16, stream);
+    if (e == cudaSuccess && !tab.empty())
+        e = cudaMemcpyAsync(scr + 16, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice, stream);
+    if (e != cudaSuccess) return cuda_fail(e, "slab mini-step setup");
+    const int ncx = w / 4;
+    const int ncp = part == 0 ? ncx : (part == 1 ? std::min(ncx, 2) : std::max(ncx - 2, 0));
+    const int ntr = ncp * d.NLy * d.NLz;
+    const int threads = 128, blocks = std::max(1, (ntr + threads - 1) / threads);
+    if (pt.nsh >= 3) {
+        if (pt.sw == 2)
+            k_slab_ministep<IS_INT, 3, 2><<<blocks, threads, 0, stream>>>(P, k, x0, w, g, part, sums);
+        else
+            k_slab_ministep<IS_INT, 3, 1><<<blocks, threads, 0, stream>>>(P, k, x0, w, g, part, sums);
+    } else {
+        if (pt.sw == 2)
+            k_slab_ministep<IS_INT, 2, 2><<<blocks, threads, 0, stream>>>(P, k, x0, w, g, part, sums);
+        else
+            k_slab_ministep<IS_INT, 2, 1><<<blocks, threads, 0, stream>>>(P, k, x0, w, g, part, sums);
+    }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "k_slab_ministep");
+    k_slab_finish<<<1, 1, 0, stream>>>(sums, pt.scale, e_acc, n_acc);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? SMC_OK : cuda_fail(e, "k_slab_finish");
+}
+
+smc_status launch_slab_ministep(const smc_lattice *lat, const smc_model *m, int8_t *win, int x0, int w, int g,
+                                uint64_t seed, uint32_t replica, uint64_t sweep, int k, double kT, double *e_acc,
+                                int64_t *n_acc, int part, cudaStream_t stream)
+{
+    if (m->kind == SMC_PAIR_I32)
+        return slab_impl<true>(lat, m, win, x0, w, g, seed, replica, sweep, k, kT, e_acc, n_acc, part, stream);
+    return slab_impl<false>(lat, m, win, x0, w, g, seed, replica, sweep, k, kT, e_acc, n_acc, part, stream);
+}
+
 template <bool IS_INT>
 static smc_status trace_impl(const smc_lattice *lat, const smc_model *m, int8_t *occ, uint64_t seed,
                              uint32_t replica, uint64_t sweep, int k, double kT, float *dE, uint8_t *acc,

@@ -236,6 +236,132 @@ class SlabExchange:
             raise SlabExchangeError(f"rank {self.rank}: {what} timed out at sweep {sweep}, mini-step {k}")
 
 
+# ---- device windows (torch tensors) ------------------------------------------
+# The same exchange for windows held as torch tensors [2][nz][ny][w + 2g]:
+# CUDA tensors with the nccl backend (each GPU's own window, payloads sent
+# device to device), CPU tensors with gloo.  A frame is a header tensor of 8
+# int64 (magic, sender, sweep, mini-step, direction, first cell, cell count,
+# 0) and a payload tensor [2][nz][ny][max_cells] (every frame of a plan the
+# same size, so that a frame of another mini-step is received whole and
+# rejected by its header); the header is checked on the host after the
+# receive.  With the trials split into edge and interior link
+# cells (smc_slab_ministep part 1 and 2), `start` after the edge trials and
+# `finish` after the interior ones overlap the transfer with the interior
+# trials (Sec. V-C).
+
+def _cells_index(plan: SlabPlan, rank: int, first: int, ncells: int):
+    """(window positions, payload columns) of every copy of the cells
+    first .. first + ncells - 1 in rank's window."""
+    pos, col = [], []
+    for j in range(ncells):
+        for p in plan.copies(rank, first + j):
+            pos.append(p)
+            col.append(j)
+    return pos, col
+
+
+class TorchSlabExchange:
+    """Ghost exchange of one rank's torch window over a process group."""
+
+    def __init__(self, plan: SlabPlan, rank: int, dist, timeout_s: float = 30.0):
+        if plan.world < 2:
+            raise ValueError("TorchSlabExchange needs world >= 2 (LocalSlabExchange runs slabs in one process)")
+        self.plan, self.rank, self.dist = plan, int(rank), dist
+        self.timeout = datetime.timedelta(seconds=float(timeout_s))
+        self.bytes_sent = 0
+
+    def _header(self, sweep, k, tag, cells, device):
+        import torch
+        P = self.plan
+        return torch.tensor([MAGIC, self.rank, sweep, k, tag, cells[0] % P.nx, P._width(cells), 0],
+                            dtype=torch.int64, device=device)
+
+    def start(self, win, sweep: int, k: int):
+        """Posts, as one batch of point-to-point operations (NCCL runs them
+        as one group), the receives of the neighbours' frames and the sends
+        of this rank's changed edge cells after mini-step k."""
+        import torch
+        P, r = self.plan, self.rank
+        pend = {"sweep": sweep, "k": k, "recv": [], "send": []}
+        ops = []
+        for src, tag in ((P.neighbour(r, 1), LEFTWARD), (P.neighbour(r, -1), RIGHTWARD)):
+            side = 1 if tag == RIGHTWARD else -1
+            cells = P.outgoing(src, k, side)
+            hdr = torch.empty(8, dtype=torch.int64, device=win.device)
+            pay = torch.empty((2, P.nz, P.ny, max(P.max_cells, 1)), dtype=torch.int8, device=win.device)
+            ops += [self.dist.P2POp(self.dist.irecv, hdr, src, tag=2 * tag),
+                    self.dist.P2POp(self.dist.irecv, pay, src, tag=2 * tag + 1)]
+            pend["recv"].append((src, tag, cells, hdr, pay))
+        for side, tag in ((-1, LEFTWARD), (1, RIGHTWARD)):
+            dst, cells = P.neighbour(r, side), P.outgoing(r, k, side)
+            a, b = P.local_index(r, cells[0]), P.local_index(r, cells[1])
+            pay = torch.zeros((2, P.nz, P.ny, max(P.max_cells, 1)), dtype=torch.int8, device=win.device)
+            pay[..., :b - a] = win.reshape(P.local_shape())[..., a:b]
+            hdr = self._header(sweep, k, tag, cells, win.device)
+            ops += [self.dist.P2POp(self.dist.isend, hdr, dst, tag=2 * tag),
+                    self.dist.P2POp(self.dist.isend, pay, dst, tag=2 * tag + 1)]
+            pend["send"].append((dst, hdr, pay))
+            self.bytes_sent += pay.numel() + 64
+        pend["reqs"] = self.dist.batch_isend_irecv(ops)
+        return pend
+
+    def _wait(self, req, what, sweep, k):
+        try:
+            ok = req.wait(self.timeout)
+        except Exception as e:  # gloo and nccl report timeouts and closed peers as RuntimeError
+            raise SlabExchangeError(f"rank {self.rank}: {what} failed at sweep {sweep}, mini-step {k}: {e}") from e
+        if ok is False:
+            raise SlabExchangeError(f"rank {self.rank}: {what} timed out at sweep {sweep}, mini-step {k}")
+
+    def finish(self, win, pend):
+        """Waits for the pending exchange, checks the headers and writes the
+        received cells into every copy in the window."""
+        import torch
+        P, sweep, k = self.plan, pend["sweep"], pend["k"]
+        for req in pend["reqs"]:
+            self._wait(req, "exchange with the neighbours", sweep, k)
+        v = win.reshape(P.local_shape())
+        for src, tag, cells, hdr, pay in pend["recv"]:
+            h = [int(x) for x in hdr.cpu().tolist()]
+            want = [MAGIC, src, sweep, k, tag, cells[0] % P.nx, P._width(cells)]
+            if h[:7] != want:
+                raise SlabExchangeError(f"rank {self.rank}: frame from rank {src}, sweep {sweep}, mini-step {k}: "
+                                        f"header {h[:7]}, expected {want}")
+            pos, col = _cells_index(P, self.rank, cells[0], P._width(cells))
+            if pos:
+                v[..., torch.tensor(pos, device=win.device)] = pay[..., torch.tensor(col, device=win.device)]
+
+    def step(self, win, sweep: int, k: int):
+        self.finish(win, self.start(win, sweep, k))
+
+
+class LocalSlabExchange:
+    """All slabs of a plan in one process (their windows as one list of
+    tensors, e.g. on one GPU): the exchange after a mini-step copies every
+    slab's changed edge cells into its neighbours' windows, device to device.
+    All payloads are taken before any is written."""
+
+    def __init__(self, plan: SlabPlan):
+        self.plan = plan
+
+    def step(self, wins, sweep: int, k: int):
+        import torch
+        P = self.plan
+        moves = []
+        for r in range(P.world):
+            v = wins[r].reshape(P.local_shape())
+            for side in (-1, 1):
+                cells = P.outgoing(r, k, side)
+                a, b = P.local_index(r, cells[0]), P.local_index(r, cells[1])
+                if b > a:
+                    moves.append((P.neighbour(r, side), cells, v[..., a:b].clone()))
+        for dst, cells, pay in moves:
+            pos, col = _cells_index(P, dst, cells[0], P._width(cells))
+            if pos:
+                d = wins[dst].reshape(P.local_shape())
+                d[..., torch.tensor(pos, device=d.device)] = pay[..., torch.tensor(col, device=d.device)]
+
+
 def run_sweeps(exchange: SlabExchange, local: np.ndarray, ministep, sweep0: int, nsweeps: int):
     """nsweeps sweeps of the slab schedule: for every mini-step, the callable
     ministep(local, sweep, k) -> (sum dE, accepted) runs this rank's trials,

@@ -24,7 +24,7 @@ MLP_NPARAM = 64 * 20 + 64 + 64 * 64 + 64 + 64 + 1
 EXPORTS = ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy", "smc_grad_size",
            "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check", "smc_last_error",
            "smc_set_tuning", "smc_debug_set", "smc_fcc_init_lattice", "smc_fcc_sweep", "smc_fcc_ministep_trace",
-           "smc_fcc_energy")
+           "smc_fcc_energy", "smc_slab_ministep")
 
 
 class SMCError(RuntimeError):
@@ -90,6 +90,8 @@ def lib():
         L.smc_fcc_ministep_trace.argtypes = [P(_Lat), P(_Model), vp, C.c_uint64, C.c_uint32, C.c_uint64,
                                              C.c_int32, C.c_double, vp, vp, vp]
         L.smc_fcc_energy.argtypes = [P(_Lat), P(_Model), vp, vp, vp, vp]
+        L.smc_slab_ministep.argtypes = [P(_Lat), P(_Model), vp, C.c_int32, C.c_int32, C.c_int32, C.c_uint64,
+                                        C.c_uint32, C.c_uint64, C.c_int32, C.c_double, vp, vp, C.c_int32, vp]
         L.smc_philox4x32_10.argtypes = [vp, vp, vp, C.c_int64, vp]
         L.smc_check.argtypes = [vp]
         L.smc_set_tuning.argtypes = [P(_Tuning)]
@@ -97,7 +99,7 @@ def lib():
         for name in ("smc_init_lattice", "smc_sweep", "smc_sweep_noalloc", "smc_sweep_batched", "smc_sro", "smc_energy",
                      "smc_energy_grad", "smc_ministep_trace", "smc_philox4x32_10", "smc_check",
                      "smc_set_tuning", "smc_debug_set", "smc_fcc_init_lattice", "smc_fcc_sweep",
-                     "smc_fcc_ministep_trace", "smc_fcc_energy"):
+                     "smc_fcc_ministep_trace", "smc_fcc_energy", "smc_slab_ministep"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -233,6 +235,16 @@ def ministep_trace(lat, model, occ, seed, sweep_index, k, kT, dE=None, acc=None,
     _chk(lib().smc_ministep_trace(C.byref(lat._c), C.byref(model._c), _dptr(occ, torch.int8), C.c_uint64(seed),
                                   C.c_uint32(replica), C.c_uint64(sweep_index), int(k), float(kT),
                                   _dptr(dE, torch.float32), _dptr(acc, torch.uint8), _stream()))
+
+
+def slab_ministep(lat, model, win, x0, w, g, seed, sweep_index, k, kT, part=0, e_acc=None, n_acc=None, replica=0):
+    """Mini-step k on one x-slab: win (device int8 [2][nz][ny][w + 2g]) holds
+    cells [x0 - g, x0 + w + g) of the box lat; part 0 all link cells, 1 the
+    edge link cells, 2 the interior ones (smc_slab_ministep)."""
+    import torch
+    _chk(lib().smc_slab_ministep(C.byref(lat._c), C.byref(model._c), _dptr(win, torch.int8), int(x0), int(w), int(g),
+                                 C.c_uint64(seed), C.c_uint32(replica), C.c_uint64(sweep_index), int(k), float(kT),
+                                 _dptr(e_acc, torch.float64), _dptr(n_acc, torch.int64), int(part), _stream()))
 
 
 def fcc_nsites(lat) -> int:

@@ -99,7 +99,22 @@ def _rank_main(rank, world, port, cfg, q):
                 return inner(local, s, k)
         t0 = time.monotonic()
         try:
-            e, n = slab.run_sweeps(ex, local, step, 0, cfg["nsweeps"])
+            if cfg.get("torch"):
+                # the window as a tensor (CPU, gloo) exchanged by TorchSlabExchange
+                win = torch.from_numpy(local)
+                tex = slab.TorchSlabExchange(plan, rank, dist, timeout_s=cfg["timeout_s"])
+                e, n, steps = 0.0, 0, 0
+                for t in range(cfg["nsweeps"]):
+                    for k in range(plan.nA):
+                        de, dn = step(local, t, k)
+                        e, n = e + de, n + dn
+                        if cfg.get("fault") == "skip" and rank == 1 and (t, k) == cfg["at"]:
+                            continue
+                        tex.step(win, t, k)
+                        steps += 1
+                ex.frames_sent = 2 * steps
+            else:
+                e, n = slab.run_sweeps(ex, local, step, 0, cfg["nsweeps"])
         finally:
             out["elapsed"] = time.monotonic() - t0
         tot = torch.tensor([e, float(n)], dtype=torch.float64)
@@ -229,10 +244,14 @@ def test_one_rank_with_periodic_ghosts_matches_oracle(kind):
 
 # -- gloo ranks -------------------------------------------------------------
 
-@pytest.mark.parametrize("kind,world,nsweeps", [("pair", 2, 3), ("pair", 4, 3), ("mlp", 2, 1)])
-def test_gloo_ranks_match_single_rank_oracle(kind, world, nsweeps):
+@pytest.mark.parametrize("kind,world,nsweeps,tensors", [("pair", 2, 3, False), ("pair", 4, 3, False),
+                                                        ("mlp", 2, 1, False), ("pair", 2, 2, True),
+                                                        ("pair", 4, 2, True)])
+def test_gloo_ranks_match_single_rank_oracle(kind, world, nsweeps, tensors):
+    """Frames of SlabExchange (host arrays), or TorchSlabExchange (windows as
+    tensors, the transport of the nccl path, here on CPU tensors)."""
     seed, dims = 5, (16, 8, 8)
-    cfg = dict(kind=kind, dims=dims, seed=seed, nsweeps=nsweeps, timeout_s=60)
+    cfg = dict(kind=kind, dims=dims, seed=seed, nsweeps=nsweeps, timeout_s=60, torch=tensors)
     res = _run(world, cfg)
     lat, model, occ, kT = _setup(kind, dims, seed)
     e_ref, n_ref = oracle.sweep(lat, model, occ, seed, 0, nsweeps, kT)
@@ -275,6 +294,17 @@ def test_dead_rank_is_detected():
     assert _failed(res[0]), res
     assert "mini-step 3" in res[0]["msg"] or "mini-step 2" in res[0]["msg"]
     assert res[0]["elapsed"] < 5 + 30
+
+
+def test_tensor_exchange_skipped_by_a_rank_raises():
+    """TorchSlabExchange: rank 1 skips its exchange after mini-step 5; rank 0
+    raises SlabExchangeError (receive timeout or a header naming another
+    mini-step), and so does rank 1 at its next exchange."""
+    cfg = dict(kind="pair", dims=(16, 8, 8), seed=2, nsweeps=1, timeout_s=3, fault="skip", at=(0, 5), torch=True)
+    res = _run(2, cfg, wait_s=120)
+    assert 0 in res and _failed(res[0]), res
+    assert "mini-step 5" in res[0]["msg"] or "mini-step 6" in res[0]["msg"], res[0]["msg"]
+    assert 1 in res and _failed(res[1]), res
 
 
 def test_late_rank_times_out_receive():
