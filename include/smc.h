@@ -30,8 +30,15 @@
  * Metropolis (Algorithm 1).  Integer models: accept iff dE <= 0 or
  *   r < floor(2^29 exp(-dE unit_ev / kT)) (table built on the host in FP64).
  *   Floating-point models: accept iff dE <= 0 or (r + 1/2) 2^-29 <
- *   exp(-dE / kT) evaluated in FP32.  A swap of two equal species is an
- *   accepted no-op.
+ *   exp(-dE / kT).  The BCC pair sweeps take dE in exact fixed point,
+ *   dE = dE_fix 2^-sigma (coefficient differences D_m(q) - D_m(S-1) rounded
+ *   once to multiples of 2^-sigma, sigma = floor(log2(2^30 / sum_m 8 (z_m - 1)
+ *   max|V_m|)); within sum |c| 2^-(sigma+1) of the FP64 sum) and test
+ *   2r + 1 < ceil(2^(dE_fix cx + 30)), cx = -log2(e) 2^-sigma / kT in FP32,
+ *   2^x from ex2.approx; the other kernels evaluate exp(-dE / kT) in FP32.
+ *   A swap of two equal species is an accepted no-op.  The BCC pair sweeps
+ *   report a species byte outside [0, S) as SMC_ERR_ARG (smc_check) and use
+ *   it modulo 8.
  * Energies.  Pair: E = sum_i 1/2 sum_m sum_{v in shell m} V_m(s_i, s_{i+v}).
  *   MLP: E = sum_i f(x_i), x_i = [onehot(s_i) | shell-1 counts | shell-2
  *   counts | shell-3 counts] (5 entries each), f = W3 silu(W2 silu(W1 x + b1)
@@ -344,8 +351,9 @@ typedef struct {
 smc_status smc_set_tuning(const smc_tuning *t);
 
 /* Test and tuning hooks.  SMC_DBG_TIMEOUT_MS sets the progress-wait limit
- * (default 2000 ms); SMC_DBG_SKIP_PUBLISH makes the tile with that index never
- * publish its progress so that its neighbours time out (-1 = off).
+ * (default 2000 ms); SMC_DBG_SKIP_PUBLISH makes the tile (streaming sweeps)
+ * or block (the resident pair sweep: its row versions and its progress) with
+ * that index never publish, so that its neighbours time out (-1 = off).
  * SMC_DBG_FAST_TEAM (1, 2 or 4 warps per link-cell column),
  * SMC_DBG_FAST_BUFFERS (1 or 2 row buffers per column) and
  * SMC_DBG_FAST_STAGING (1: one bulk copy per row; 2: 16-byte cp.async) fix
