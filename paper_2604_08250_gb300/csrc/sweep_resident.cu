@@ -665,7 +665,10 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     rp = ResPlan();
     const int nx = lat.nx, ny = lat.ny, nz = lat.nz;
     const int NLy = ny / 4, NLz = nz / 4, nsh = pt.nsh;
-    const int rowB = nx + 32;
+    // row pitch: a multiple of 128 bytes when the windows fit with it, so that
+    // the same x of every row falls in the same bank (the lanes' partner rows
+    // differ per lane; their x do not), else the 16-byte halos only
+    int rowB = (nx + 32 + 127) / 128 * 128;
     const void *kern = pick_resident<IS_INT>(pt.nsh, pt.sw);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -841,8 +844,13 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     if (!fits) return SMC_OK;  // a row outside the window (not expected)
     rp.nver = std::max(nver, 1);
     const int nk = (nx / 4 + 31) / 32;
-    const size_t smem = (size_t)kQRows * pt.rw * 4 + 64 + (size_t)2 * rp.Wy * rp.Wz * rowB +
-                        ((size_t)rp.blob * 4 + 15) / 16 * 16 + (size_t)nc * nk * 512;
+    auto smem_of = [&](int pitch) {
+        return (size_t)kQRows * pt.rw * 4 + 64 + (size_t)2 * rp.Wy * rp.Wz * pitch +
+               ((size_t)rp.blob * 4 + 15) / 16 * 16 + (size_t)nc * nk * 512;
+    };
+    if (smem_of(rowB) > dyn_max) rowB = nx + 32;
+    rp.rowB = rowB;
+    const size_t smem = smem_of(rowB);
     if (smem > dyn_max) return SMC_OK;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
