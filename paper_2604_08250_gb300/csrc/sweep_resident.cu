@@ -30,13 +30,16 @@
 // publish the rows they wrote; the exchange warps fetch the next group's
 // versions (with their periodic x-halos) while the current group runs and
 // arrive on READY; the release warp releases the CTA's progress flag once
-// every compute warp has counted a group as done.  A fetch for group g + 1
-// may land while group g runs: a fetched row is not written by this CTA's
-// group g, and if group g reads it, it reads the same bytes.  The exchange
-// warps never run more than one group ahead (they wait until the compute
-// warps finished g - 1 before they fetch for g + 1), and the READY barriers
-// alternate by group parity so that their arrivals for consecutive groups
-// never meet in one barrier.
+// every compute warp has counted a group as done.  The exchange warps fetch
+// for group g + 2 once the compute warps finished g - 1, so a fetch may land
+// while group g or g + 1 runs.  A fetched row is not written by this CTA in
+// either (its last writer before g + 2 is another CTA), and if one of them
+// reads it, it reads the same bytes: a newer version would be a write by a
+// neighbour at g + 1 of a row this CTA touches at g (excluded by the lag-2
+// rule when g + 1 has dy >= 1, and impossible when it has dy = 0, since the
+// neighbour then waits for this CTA's g) or at g + 1 (same-group
+// disjointness).  The READY barriers cycle through four named barriers so
+// that the exchange warps' arrivals for different groups never meet in one.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -52,11 +55,12 @@ namespace {
 
 constexpr int kResDesc = 12;  // ints per block descriptor
 
-// READY barriers, alternating by group parity: the exchange warp may arrive
-// for group g + 1 before every compute warp arrived for group g, never for
-// g + 2 (it waits until the compute warps finished g), so one barrier per
-// parity keeps the arrivals of consecutive groups apart.
-__device__ __forceinline__ int bar_ready(int gs) { return 1 + (gs & 1); }
+// The exchange warps prepare group g once the compute warps finished group
+// g - kAhead - 1, so while groups g - kAhead .. g - 1 may still wait for
+// their compute warps.  READY barriers cycle through kBars > kAhead named
+// barriers by group, so that arrivals for different groups never meet in one.
+constexpr int kAhead = 2, kBars = 4;
+__device__ __forceinline__ int bar_ready(int gs) { return 1 + (gs & (kBars - 1)); }
 
 // bar.sync / bar.arrive are the warp-aligned barrier forms: every lane of
 // the warp must execute them together, so the warp reconverges first.
@@ -396,8 +400,9 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
         int gs = 0;
         for (; gs + 1 < total; ++gs) {
             const int nxt = gs + 1, gn = nxt & 31;
-            // never more than one group ahead: the compute warps finished gs - 1
-            ok = res_wait_count(P, &s_cnt, (unsigned)(gs * nc), &s_abort, lane);
+            // never more than kAhead groups ahead: the compute warps finished
+            // nxt - kAhead - 1
+            ok = res_wait_count(P, &s_cnt, (unsigned)(max(nxt - kAhead, 0) * nc), &s_abort, lane);
             // Group nxt's versions overwrite those of nxt - 64, which readers
             // fetch up to group nxt - 33: the neighbours must have finished it
             // (READY of nxt waits for this warp).
@@ -413,15 +418,15 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
             // The compute warps stop at READY of the smallest group an
             // exchange warp gave up before (s_stop, lowered before that
             // barrier's arrival).  If that is gs + 1, they pass the READYs
-            // already given without waiting and finish group gs - 1 in
-            // bounded time; only then is the barrier of gs + 1's parity free
-            // of group gs - 1's arrivals.  If another exchange warp gave up
-            // at an earlier group, the compute warps never reach gs + 1.
+            // already given without waiting and finish group gs + 1 - kBars
+            // in bounded time; only then is the barrier of gs + 1 free of
+            // that group's arrivals.  If another exchange warp gave up at an
+            // earlier group, the compute warps never reach gs + 1.
             int arrive = 0;
             if (lane == 0 && s_stop > gs) {
                 atomicMin((int *)&s_stop, gs + 1);
                 const uint64_t t0 = global_ns();
-                while (*(volatile unsigned *)&s_cnt < (unsigned)(gs * nc) &&
+                while (*(volatile unsigned *)&s_cnt < (unsigned)(max(gs + 2 - kBars, 0) * nc) &&
                        (long long)(global_ns() - t0) < P.timeout_ns) {
                 }
                 arrive = 1;
