@@ -242,6 +242,29 @@ def test_one_rank_with_periodic_ghosts_matches_oracle(kind):
     assert e == e_ref if kind == "pair" else abs(e - e_ref) <= 1e-12 * max(1.0, abs(e_ref))
 
 
+@pytest.mark.parametrize("world", [1, 2, 4])
+def test_local_exchange_of_tensor_windows_matches_oracle(world):
+    """LocalSlabExchange (all slabs in one process, windows as tensors; on a
+    GPU the exchange is device-to-device copies), here with CPU tensors and
+    the oracle's slab mini-step: the single-rank oracle's box bit for bit."""
+    lat, model, occ, kT = _setup("pair", (16, 8, 8), 13)
+    ref = occ.copy()
+    e_ref, n_ref = oracle.sweep(lat, model, ref, 13, 0, 2, kT)
+    P = slab.SlabPlan(lat.nx, lat.ny, lat.nz, world, oracle.slab_ghost_cells(model))
+    wins = [torch.from_numpy(P.window_of(occ, r)) for r in range(world)]
+    ex = slab.LocalSlabExchange(P)
+    e, n = 0.0, 0
+    for t in range(2):
+        for k in range(P.nA):
+            for r in range(world):
+                de, dn, _ = oracle.slab_ministep(lat, model, wins[r].numpy(), P.x0(r), P.w, P.ghost, 13, t, k, kT)
+                e, n = e + de, n + dn
+            ex.step(wins, t, k)
+    box = np.concatenate([P.owned(w.numpy()) for w in wins], axis=-1).reshape(-1)
+    assert np.array_equal(box, ref)
+    assert n == n_ref and n > 0 and e == e_ref
+
+
 # -- gloo ranks -------------------------------------------------------------
 
 @pytest.mark.parametrize("kind,world,nsweeps,tensors", [("pair", 2, 3, False), ("pair", 4, 3, False),
