@@ -132,11 +132,12 @@ struct PairTable {
 };
 bool build_pair_table(const smc_model *m, int S, PairTable &t);
 
-// The resident sweep (sweep_resident.cu): SMC_ERR_UNSUPPORTED, with nothing
-// enqueued, when the lattice does not fit it.
-smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m, const PairTable &pt,
-                                      int8_t *occ, uint64_t seed, uint32_t replica, uint64_t sweep0, int nsweeps,
-                                      const double *kT, double *e_acc, int64_t *n_acc, cudaStream_t stream);
+// The resident sweep (sweep_resident.cu) of R replicas: SMC_ERR_UNSUPPORTED,
+// with nothing enqueued, when a replica does not fit it.
+smc_status launch_pair_sweep_resident(int R, const smc_lattice *lats, const smc_model *m, const PairTable &pt,
+                                      int8_t *const *occ, uint64_t seed, uint32_t replica0, uint64_t sweep0,
+                                      int nsweeps, const double *kT, double *e_acc, int64_t *n_acc,
+                                      cudaStream_t stream);
 int debug_resident();
 
 }  // namespace smc

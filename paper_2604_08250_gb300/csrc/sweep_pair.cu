@@ -1700,9 +1700,9 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
         set_error("pair coefficients must be finite");
         return SMC_ERR_ARG;
     }
-    if (R == 1 && debug_resident() == 0) {
-        // a lattice that fits in the SMs' shared memory stays there
-        st = launch_pair_sweep_resident(lats, m, pt, occ[0], seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc,
+    if (debug_resident() == 0) {
+        // lattices that fit in the SMs' shared memory stay there
+        st = launch_pair_sweep_resident(R, lats, m, pt, occ, seed, replica0, sweep0, nsweeps, kT, e_acc, n_acc,
                                         stream);
         if (st != SMC_ERR_UNSUPPORTED) return st;
     }

@@ -53,7 +53,15 @@ namespace smc {
 
 namespace {
 
-constexpr int kResDesc = 12;  // ints per block descriptor
+// Block descriptor (ints): [0..3] first column (cy, cz) and columns per axis,
+// [4..7] window origin y (sublattice 0, 1) and z (0, 1), [8..9] list offset
+// and size, [10] replica (index into P.rep), [11] block index within the
+// replica, [12..13] blocks per axis of the replica, [14] global index of the
+// replica's first block (its progress flags), [15..16] window rows per axis,
+// [17] row pitch, [18] offset of the replica's lattice copy (bytes),
+// [19] offset of its version slots (words), [20] its version slots.
+constexpr int kResDesc = 24;
+constexpr int kResCols = 8;  // compute warps per CTA (columns per block at most)
 
 // The exchange warps prepare group g once the compute warps finished group
 // g - kAhead - 1, so while groups g - kAhead .. g - 1 may still wait for
@@ -169,13 +177,14 @@ __device__ __forceinline__ uint32_t res_body(int ylo, int zlo, int s, int y, int
 
 // The progress flag of neighbour lane (lanes 0..8 but 4: (dy, dz) = (lane % 3
 // - 1, lane / 3 - 1)); nullptr for the other lanes.
-__device__ __forceinline__ const uint32_t *res_flag(const SweepParams &P, int by, int bz, int lane)
+__device__ __forceinline__ const uint32_t *res_flag(const SweepParams &P, const int *d, int lane)
 {
     if (lane >= 9 || lane == 4) return nullptr;
-    int nby = by + (lane % 3) - 1, nbz = bz + (lane / 3) - 1;
-    nby = nby < 0 ? nby + P.NBy : (nby >= P.NBy ? nby - P.NBy : nby);
-    nbz = nbz < 0 ? nbz + P.NBz : (nbz >= P.NBz ? nbz - P.NBz : nbz);
-    return P.flags + nbz * P.NBy + nby;
+    const int NBy = d[12], NBz = d[13];
+    int nby = d[11] % NBy + (lane % 3) - 1, nbz = d[11] / NBy + (lane / 3) - 1;
+    nby = nby < 0 ? nby + NBy : (nby >= NBy ? nby - NBy : nby);
+    nbz = nbz < 0 ? nbz + NBz : (nbz >= NBz ? nbz - NBz : nbz);
+    return P.flags + d[14] + nbz * NBy + nby;
 }
 
 // Gives up a wait: records a timeout (unless another block aborted first)
@@ -236,15 +245,16 @@ __device__ bool res_wait_count(const SweepParams &P, const volatile unsigned *cn
 }
 
 // Row versions.  Every row a block writes in group g and another block
-// reads before its next write is published as a version: nx / 4 words of
-// (4 species bytes | tag << 32), tag = global group of the write + 1, in
+// reads before its next write is published as a version: (nx + 7) / 8
+// 16-byte chunks of two words (4 species bytes | tag << 32) (when nx is
+// 4 mod 8 the last word carries no species), tag = global group of the write + 1, in
 // copy (global group >> 5) & 1 of its version slot.  A reader knows the
 // tag it needs, so it polls the words themselves: a word with that tag holds
 // that version's bytes (each 64-bit word is single-copy atomic), and no fence
 // or flag stands between the write and the read.
-__device__ __forceinline__ uint32_t ver_word(const SweepParams &P, int gw, uint32_t vid, int nx)
+__device__ __forceinline__ uint32_t ver_word(int nver, int gw, uint32_t vid, int nx)
 {
-    return ((uint32_t)((gw >> 5) & 1) * (uint32_t)P.nver + vid) * (uint32_t)(nx >> 2);
+    return ((uint32_t)((gw >> 5) & 1) * (uint32_t)nver + vid) * (uint32_t)(((nx + 7) >> 3) * 2);
 }
 
 // Fetches the versions of list entries ent[0, n) ({smem slot | d << 16,
@@ -254,14 +264,16 @@ __device__ __forceinline__ uint32_t ver_word(const SweepParams &P, int gw, uint3
 // K chunks per lane per round, each chunk polled until both its words carry
 // the tag.  False on timeout or abort.
 template <int K>
-__device__ bool res_fetch_versions(const SweepParams &P, const uint2 *ent, int n, uint32_t rows, uint32_t rb, int nx,
-                                   int G, int xw, int nxw, volatile int *s_abort, int lane)
+__device__ bool res_fetch_versions(const SweepParams &P, const unsigned long long *xver, int nver, const uint2 *ent,
+                                   int n, uint32_t rows, uint32_t rb, int nx, int G, int xw, int nxw,
+                                   volatile int *s_abort, int lane)
 {
-    const int cpr = nx >> 3;
+    const int cpr = (nx + 7) >> 3;  // the last chunk holds 4 species when nx % 8 == 4
+    const bool half = (nx & 7) != 0;
     const int tot = n * cpr, step = 32 * nxw, de = step / cpr, dc = step - de * cpr;
     const uint64_t t0 = global_ns();
     for (int base = 0; base < tot; base += step * K) {
-        uint32_t src[K], dst[K], tag[K];  // word offset in P.xver, shared address, tag
+        uint32_t src[K], dst[K], tag[K];  // word offset in xver, shared address, tag
         uint32_t todo = 0u, first = 0u, last = 0u;  // chunks that also fill the right / left x-halo
         {
             const int q0 = base + 32 * xw + lane;
@@ -275,7 +287,7 @@ __device__ bool res_fetch_versions(const SweepParams &P, const uint2 *ent, int n
                     const uint2 en = ent[e];
                     const int gw = G - (int)(en.x >> 16);
                     if (gw >= 0) {
-                        src[k] = ver_word(P, gw, en.y, nx) + 2u * (uint32_t)c;
+                        src[k] = ver_word(nver, gw, en.y, nx) + 2u * (uint32_t)c;
                         dst[k] = rows + (en.x & 0xffffu) * rb + 16u + 8u * (uint32_t)c;
                         tag[k] = (uint32_t)gw + 1u;
                         todo |= 1u << k;
@@ -295,14 +307,21 @@ __device__ bool res_fetch_versions(const SweepParams &P, const uint2 *ent, int n
             ulonglong2 v[K];
 #pragma unroll
             for (int k = 0; k < K; ++k)
-                if (todo & (1u << k)) v[k] = ld_relaxed_v2u64(P.xver + src[k]);
+                if (todo & (1u << k)) v[k] = ld_relaxed_v2u64(xver + src[k]);
 #pragma unroll
             for (int k = 0; k < K; ++k) {
                 if ((todo & (1u << k)) && (uint32_t)(v[k].x >> 32) == tag[k] && (uint32_t)(v[k].y >> 32) == tag[k]) {
-                    *(uint2 *)(g_smem + dst[k]) = make_uint2((uint32_t)v[k].x, (uint32_t)v[k].y);
+                    const bool lk = (last >> k) & 1u;
+                    if (half && lk) {
+                        *(uint32_t *)(g_smem + dst[k]) = (uint32_t)v[k].x;
+                    } else {
+                        *(uint2 *)(g_smem + dst[k]) = make_uint2((uint32_t)v[k].x, (uint32_t)v[k].y);
+                    }
                     // periodic x-halos: body[0..4) after the row, body[nx-4..nx) before it
                     if (first & (1u << k)) *(uint32_t *)(g_smem + dst[k] + nx) = (uint32_t)v[k].x;
-                    if (last & (1u << k)) *(uint32_t *)(g_smem + dst[k] + 4 - nx) = (uint32_t)v[k].y;
+                    if (lk)
+                        *(uint32_t *)(g_smem + dst[k] + (half ? 0 : 4) - nx) =
+                            half ? (uint32_t)v[k].x : (uint32_t)v[k].y;
                     todo &= ~(1u << k);
                 }
             }
@@ -328,12 +347,15 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
     // compute warps, then P.rxw exchange warps, then the release warp
     const int nxw = P.rxw, nc = nwarp - nxw - 1, nbar = (nc + nxw) * 32;
     const int blk = blockIdx.x;
-    const RepDesc &RD = P.rep[0];
-    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
-    const int Wy = P.Wy, Wz = P.Wz;
-    const uint32_t rb = (uint32_t)P.rowB, RZ = (uint32_t)Wy * rb;
     const int *d = P.rdesc + blk * kResDesc;
-    const int by = blk % P.NBy, bz = blk / P.NBy;
+    const int rep = d[10];
+    const RepDesc &RD = P.rep[rep];
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
+    const int Wy = d[15], Wz = d[16];
+    const uint32_t rb = (uint32_t)d[17], RZ = (uint32_t)Wy * rb;
+    const int8_t *exch = P.exch + (uint32_t)d[18];
+    unsigned long long *xver = P.xver + (uint32_t)d[19];
+    const int nver = d[20];
     const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     __shared__ volatile int s_abort;  // a wait gave up: stop
     __shared__ volatile int s_stop;   // the group at which the compute warps stop (set by the exchange warp)
@@ -356,18 +378,20 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
     }
     // the window's rows from the exchange copy (species x 8)
     {
-        const int cpr = nx >> 4;
+        const bool v16 = (nx & 15) == 0;
+        const int cb = v16 ? 16 : 4, cpr = nx / cb;
         for (int q = tid; q < nslots * cpr; q += blockDim.x) {
             const int slot = q / cpr, c = q - slot * cpr;
             const int s = slot / (Wy * Wz), yy = slot % Wy, zz = (slot / Wy) % Wz;
             int y = d[4 + s] + yy, z = d[6 + s] + zz;
             y = y < 0 ? y + ny : (y >= ny ? y - ny : y);
             z = z < 0 ? z + nz : (z >= nz ? z - nz : z);
-            const int8_t *src = P.exch + ((size_t)((s * nz + z) * ny + y)) * nx + 16 * c;
-            asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem0 + rows + (uint32_t)slot * rb + 16u +
-                                                                            16u * c),
-                         "l"(src)
-                         : "memory");
+            const int8_t *src = exch + ((size_t)((s * nz + z) * ny + y)) * nx + cb * c;
+            const uint32_t dst = smem0 + rows + (uint32_t)slot * rb + 16u + (uint32_t)(cb * c);
+            if (v16)
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src) : "memory");
+            else
+                asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(dst), "l"(src) : "memory");
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         __syncthreads();
@@ -394,7 +418,7 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
         // x-halos), shared between the exchange warps, then READY.
         const int xw = warp - nc;
         named_arrive(bar_ready(0), nbar);  // group 0: the window was loaded from the lattice copy
-        const uint32_t *fp = res_flag(P, by, bz, lane);
+        const uint32_t *fp = res_flag(P, d, lane);
         uint32_t nbmin = 0u;  // a lower bound of the neighbours' progress flags
         bool ok = true;
         int gs = 0;
@@ -409,8 +433,8 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
             if (ok && xw == 0 && nxt >= 64 && nbmin < (uint32_t)(nxt - 32))
                 ok = res_wait(P, fp, (uint32_t)(nxt - 32), &s_abort, lane, &nbmin);
             if (ok)
-                ok = res_fetch_versions<8>(P, (const uint2 *)(L + fo[gn]), (int)(fo[gn + 1] - fo[gn]) >> 1, rows, rb,
-                                           nx, nxt, xw, nxw, &s_abort, lane);
+                ok = res_fetch_versions<8>(P, xver, nver, (const uint2 *)(L + fo[gn]), (int)(fo[gn + 1] - fo[gn]) >> 1,
+                                           rows, rb, nx, nxt, xw, nxw, &s_abort, lane);
             if (!ok) break;
             named_arrive(bar_ready(nxt), nbar);
         }
@@ -483,9 +507,9 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
             float cx = 0.f;
             int2 ti = make_int2(0, 0);
             if constexpr (IS_INT)
-                ti = P.temp.tabinfo[P.beta_stride ? t : 0];
+                ti = P.temp.tabinfo[P.beta_stride ? rep * P.beta_stride + t : rep];
             else
-                cx = P.temp.beta[P.beta_stride ? t : 0];
+                cx = P.temp.beta[P.beta_stride ? rep * P.beta_stride + t : rep];
             const uint32_t ownb = res_body(sub ? ylo1 : ylo0, sub ? zlo1 : zlo0, sub, y0, z0, ny, nz, Wy, Wz, rows, rb);
             const uint32_t parb = res_body(sub ? ylo0 : ylo1, sub ? zlo0 : zlo1, 1 - sub, y0 + soff, z0 + soff, ny, nz,
                                            Wy, Wz, rows, rb);
@@ -548,13 +572,13 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
                 if (blk != P.skip_tile) {
                     const uint2 *pe = (const uint2 *)(L + po[g * nc + warp]);
                     const int np = (int)(po[g * nc + warp + 1] - po[g * nc + warp]) >> 1;
-                    const int cpr = nx >> 3;
+                    const int cpr = (nx + 7) >> 3;  // a last half chunk carries 4 bytes of the halo: not read
                     const unsigned long long tag = (unsigned long long)(gs + 1) << 32;
                     for (int q = lane; q < np * cpr; q += 32) {
                         const int e = q / cpr, c = q - e * cpr;
                         const uint2 en = pe[e];
                         const uint2 w = *(const uint2 *)(g_smem + rows + en.x * rb + 16u + 8u * c);
-                        st_relaxed_v2u64(P.xver + ver_word(P, gs, en.y, nx) + 2 * c, tag | w.x, tag | w.y);
+                        st_relaxed_v2u64(xver + ver_word(nver, gs, en.y, nx) + 2 * c, tag | w.x, tag | w.y);
                     }
                 }
             }
@@ -575,16 +599,25 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
     __syncthreads();
     if (s_abort) return;
     // final rows, back to plain species in the caller's array
-    for (int q = tid; q < (int)(fin1 * (uint32_t)(nx >> 4)); q += blockDim.x) {
-        const int cpr = nx >> 4, e = q / cpr, c = q - e * cpr;
-        const uint32_t v = L[fin0 + e], slot = v >> 21, row = v & 0x1FFFFFu;
-        const int4 w = *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
-        int4 o;
-        o.x = (int)(((uint32_t)w.x >> 3) & 0x07070707u);
-        o.y = (int)(((uint32_t)w.y >> 3) & 0x07070707u);
-        o.z = (int)(((uint32_t)w.z >> 3) & 0x07070707u);
-        o.w = (int)(((uint32_t)w.w >> 3) & 0x07070707u);
-        *((int4 *)(RD.occ + (size_t)row * nx) + c) = o;
+    if ((nx & 15) == 0) {
+        for (int q = tid; q < (int)(fin1 * (uint32_t)(nx >> 4)); q += blockDim.x) {
+            const int cpr = nx >> 4, e = q / cpr, c = q - e * cpr;
+            const uint32_t v = L[fin0 + e], slot = v >> 21, row = v & 0x1FFFFFu;
+            const int4 w = *((const int4 *)(g_smem + rows + slot * rb + 16u) + c);
+            int4 o;
+            o.x = (int)(((uint32_t)w.x >> 3) & 0x07070707u);
+            o.y = (int)(((uint32_t)w.y >> 3) & 0x07070707u);
+            o.z = (int)(((uint32_t)w.z >> 3) & 0x07070707u);
+            o.w = (int)(((uint32_t)w.w >> 3) & 0x07070707u);
+            *((int4 *)(RD.occ + (size_t)row * nx) + c) = o;
+        }
+    } else {
+        for (int q = tid; q < (int)(fin1 * (uint32_t)(nx >> 2)); q += blockDim.x) {
+            const int cpr = nx >> 2, e = q / cpr, c = q - e * cpr;
+            const uint32_t v = L[fin0 + e], slot = v >> 21, row = v & 0x1FFFFFu;
+            const uint32_t w = *((const uint32_t *)(g_smem + rows + slot * rb + 16u) + c);
+            *((uint32_t *)(RD.occ + (size_t)row * nx) + c) = (w >> 3) & 0x07070707u;
+        }
     }
     // per-warp partial sums; the last CTA reduces them in order
     __shared__ int s_last;
@@ -593,16 +626,21 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
         s_last = atomicAdd(P.ticket, 1u) == gridDim.x - 1;
     }
     __syncthreads();
-    if (!s_last || tid != 0) return;
+    if (!s_last || tid >= P.R) return;
+    // thread r: replica r's blocks in order
     __threadfence();
     double se = 0.0;
     long long sn = 0;
-    for (int k = 0; k < (int)gridDim.x * nc; ++k) {
-        se += __ldcg(P.part_e + k);
-        sn += __ldcg(P.part_n + k);
+    for (int b = 0; b < (int)gridDim.x; ++b) {
+        if (__ldcg(P.rdesc + b * kResDesc + 10) != tid) continue;
+        for (int k = b * nc; k < (b + 1) * nc; ++k) {
+            se += __ldcg(P.part_e + k);
+            sn += __ldcg(P.part_n + k);
+        }
     }
-    if (RD.e_acc) *RD.e_acc += se * P.escale;
-    if (RD.n_acc) *RD.n_acc += sn;
+    const RepDesc &RR = P.rep[tid];
+    if (RR.e_acc) *RR.e_acc += se * P.escale;
+    if (RR.n_acc) *RR.n_acc += sn;
 }
 
 // ---------------------------------------------------------------------------
@@ -611,6 +649,7 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
 struct ResPlan {
     int ok = 0, by = 0, bz = 0, NBy = 0, NBz = 0, nblocks = 0, nc = 0, Wy = 0, Wz = 0, rowB = 0, blob = 0;
     int nver = 0;  // version slots (rows written in one group and read by another block)
+    int per_sm = 0;  // CTAs per SM
     int nxw = 4;   // exchange warps
     size_t smem = 0;
     std::vector<int> desc;
@@ -665,7 +704,7 @@ const void *pick_resident(int nsh, int sw)
 // Builds the plan for one lattice, or leaves ok = 0 when the lattice does not
 // fit (the streaming kernel then runs).
 template <bool IS_INT>
-smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace *ws, ResPlan &rp)
+smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace *ws, bool few_blocks, ResPlan &rp)
 {
     rp = ResPlan();
     const int nx = lat.nx, ny = lat.ny, nz = lat.nz;
@@ -681,8 +720,9 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
     // block shapes with at most 8 columns, at most one CTA per SM and at
     // least 3 blocks per axis; the fewest columns per block (the shortest
-    // group), then the fewest rows held.  A tuned tile shape (tile_y,
-    // tile_z) selects the block shape.
+    // group; with few_blocks, for replicas sharing a launch, the most), then
+    // the fewest rows held.  A tuned tile shape (tile_y, tile_z) selects the
+    // block shape.
     const int shapes[][2] = {{1, 1}, {1, 2}, {2, 1}, {2, 2}, {1, 4}, {4, 1}, {2, 3}, {3, 2}, {2, 4}, {4, 2}, {1, 8}, {8, 1}};
     const Tuning tu = current_tuning();
     int best = -1, best_nc = 1 << 30, best_rows = 1 << 30;
@@ -694,13 +734,14 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
         const int Wy = 4 * by + 7, Wz = 4 * bz + 7;
         if (Wy >= ny || Wz >= nz) continue;
         const int nrows = 2 * Wy * Wz, nc = by * bz;
-        if (nc < best_nc || (nc == best_nc && nrows < best_rows)) {
+        const bool better_nc = few_blocks ? (best < 0 || nc > best_nc) : nc < best_nc;
+        if (better_nc || (nc == best_nc && nrows < best_rows)) {
             best = i;
             best_nc = nc;
             best_rows = nrows;
         }
     }
-    if (best < 0 || nx % 16 != 0) return SMC_OK;
+    if (best < 0 || nx % 4 != 0) return SMC_OK;
     const int by = shapes[best][0], bz = shapes[best][1];
     rp.by = by;
     rp.bz = bz;
@@ -734,7 +775,7 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     };
     rp.desc.assign((size_t)rp.nblocks * kResDesc, 0);
     rp.lists.clear();
-    const int nc = rp.nc;
+    const int nc = kResCols;  // compute warps of the kernel (some idle for smaller blocks)
     std::vector<int> vslot((size_t)32 * nrows_lat, -1);  // (group of the write, row) -> version slot
     int nver = 0;
     struct Blk {
@@ -755,6 +796,11 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
         dd[5] = 4 * cy0 - 2;  // sublattice 1 rows y in [4 cy0 - 2, 4 cy0 + 4 by + 4]
         dd[6] = 4 * cz0 - 1;
         dd[7] = 4 * cz0 - 2;
+        dd[11] = blk;
+        dd[12] = rp.NBy;
+        dd[13] = rp.NBz;
+        dd[15] = rp.Wy;
+        dd[16] = rp.Wz;
         // rows the block reads in each group
         std::vector<std::vector<int>> reads(32);
         for (int g = 0; g < 32; ++g) {
@@ -857,12 +903,17 @@ smc_status build_res_plan(const smc_lattice &lat, const PairTable &pt, Workspace
     rp.rowB = rowB;
     const size_t smem = smem_of(rowB);
     if (smem > dyn_max) return SMC_OK;
+    for (int blk = 0; blk < rp.nblocks; ++blk) {
+        rp.desc[(size_t)blk * kResDesc + 17] = rowB;
+        rp.desc[(size_t)blk * kResDesc + 20] = rp.nver;
+    }
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (nc + rp.nxw + 1) * 32, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (kResCols + rp.nxw + 1) * 32, smem);
     if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
     if (per_sm < 1 || rp.nblocks > per_sm * ws->num_sms) return SMC_OK;
+    rp.per_sm = per_sm;
     rp.smem = smem;
     rp.kernel = kern;
     rp.ok = 1;
@@ -886,73 +937,161 @@ __global__ void k_occ_to_exch(const int8_t *occ, int8_t *exch, long long n, int 
 
 }  // namespace
 
-// The resident sweep, when the lattice fits (single replica, four-cell link
-// cells on every axis, rows of a multiple of 16 bytes).  Returns
-// SMC_ERR_UNSUPPORTED, having enqueued nothing, when it does not apply.
-smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m, const PairTable &pt,
-                                      int8_t *occ, uint64_t seed, uint32_t replica, uint64_t sweep0, int nsweeps,
-                                      const double *kT, double *e_acc, int64_t *n_acc, cudaStream_t stream)
+// The resident sweep for R replicas, when every replica fits (four-cell link
+// cells on every axis, rows of a multiple of 16 bytes, windows within shared
+// memory).  Replicas run in waves: one cooperative launch per wave of
+// replicas whose blocks are resident at once (each block waits only for
+// blocks of its own replica).  Returns SMC_ERR_UNSUPPORTED, having enqueued
+// nothing, when one replica does not fit.
+namespace {
+
+struct ResWave {
+    std::vector<int> reps;       // replicas of the wave, in order
+    int nblocks = 0, blob = 0;   // CTAs; largest list blob of a block (words)
+    size_t smem = 0;             // dynamic shared memory per CTA
+    size_t exch_bytes = 0, ver_words = 0;
+    void *dev = nullptr;         // [descriptors | lists], uploaded once
+    size_t lists_off = 0;
+};
+
+struct ResMulti {
+    bool ok = false;
+    const void *kernel = nullptr;
+    std::vector<ResPlan> rp;
+    std::vector<ResWave> waves;
+};
+
+void free_waves(ResMulti &mp)
 {
-    if (lc_edge(lat->nx) != 4 || lc_edge(lat->ny) != 4 || lc_edge(lat->nz) != 4 || lat->nx % 16 ||
-        (uintptr_t)occ % 16 || lat->nx > 1024)
-        return SMC_ERR_UNSUPPORTED;
+    for (auto &w : mp.waves)
+        if (w.dev) cudaFree(w.dev);
+    mp.waves.clear();
+}
+
+template <bool IS_INT>
+smc_status build_res_multi(int R, const smc_lattice *lats, const PairTable &pt, Workspace *ws, ResMulti &mp)
+{
+    mp = ResMulti();
+    for (int r = 0; r < R; ++r) {
+        ResPlan rp;
+        const smc_status st = build_res_plan<IS_INT>(lats[r], pt, ws, R > 1, rp);
+        if (st != SMC_OK) return st;
+        if (!rp.ok) return SMC_OK;
+        mp.kernel = rp.kernel;
+        mp.rp.push_back(std::move(rp));
+    }
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, mp.kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
+    // waves: replicas in order, as many as are resident at once
+    auto smem_with_blob = [&](const ResPlan &rp, int blob) {
+        return rp.smem - ((size_t)rp.blob * 4 + 15) / 16 * 16 + ((size_t)blob * 4 + 15) / 16 * 16;
+    };
+    int r = 0;
+    while (r < R) {
+        ResWave w;
+        int per_sm = 1 << 30;
+        while (r < R && (int)w.reps.size() < kMaxReplicas) {
+            const ResPlan &rp = mp.rp[r];
+            const int ps = std::min(per_sm, rp.per_sm), blob = std::max(w.blob, rp.blob);
+            size_t smem = smem_with_blob(rp, blob);
+            for (int q : w.reps) smem = std::max(smem, smem_with_blob(mp.rp[q], blob));
+            if (!w.reps.empty() && (w.nblocks + rp.nblocks > ps * ws->num_sms || smem > dyn_max)) break;
+            if (smem > dyn_max) return SMC_OK;
+            w.reps.push_back(r);
+            w.nblocks += rp.nblocks;
+            w.blob = blob;
+            w.smem = smem;
+            per_sm = ps;
+            ++r;
+        }
+        // descriptors and lists of the wave's blocks
+        std::vector<int> desc;
+        std::vector<uint32_t> lists;
+        int flag0 = 0;
+        for (int lr = 0; lr < (int)w.reps.size(); ++lr) {
+            const ResPlan &rp = mp.rp[w.reps[lr]];
+            const smc_lattice &l = lats[w.reps[lr]];
+            for (int b = 0; b < rp.nblocks; ++b) {
+                const int *src = &rp.desc[(size_t)b * kResDesc];
+                const size_t at = desc.size();
+                desc.insert(desc.end(), src, src + kResDesc);
+                desc[at + 8] += (int)lists.size();
+                desc[at + 10] = lr;
+                desc[at + 14] = flag0;
+                desc[at + 18] = (int)w.exch_bytes;
+                desc[at + 19] = (int)w.ver_words;
+            }
+            lists.insert(lists.end(), rp.lists.begin(), rp.lists.end());
+            if (lists.size() & 1) lists.push_back(0u);
+            flag0 += rp.nblocks;
+            w.exch_bytes += ((size_t)2 * l.nx * l.ny * l.nz + 255) / 256 * 256;
+            w.ver_words += (size_t)2 * rp.nver * (size_t)(((l.nx + 7) / 8) * 2);
+        }
+        w.lists_off = (desc.size() * 4 + 15) / 16 * 16;
+        e = cudaMalloc(&w.dev, w.lists_off + lists.size() * 4);
+        if (e == cudaSuccess) e = cudaMemcpy(w.dev, desc.data(), desc.size() * 4, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess)
+            e = cudaMemcpy((unsigned char *)w.dev + w.lists_off, lists.data(), lists.size() * 4,
+                           cudaMemcpyHostToDevice);
+        mp.waves.push_back(w);
+        if (e != cudaSuccess) return cuda_fail(e, "resident plan upload");
+    }
+    mp.ok = true;
+    return SMC_OK;
+}
+
+}  // namespace
+
+smc_status launch_pair_sweep_resident(int R, const smc_lattice *lats, const smc_model *m, const PairTable &pt,
+                                      int8_t *const *occ, uint64_t seed, uint32_t replica0, uint64_t sweep0,
+                                      int nsweeps, const double *kT, double *e_acc, int64_t *n_acc,
+                                      cudaStream_t stream)
+{
+    if (R < 1 || R > kMaxReplicas) return SMC_ERR_UNSUPPORTED;
+    for (int r = 0; r < R; ++r) {
+        const smc_lattice &l = lats[r];
+        if (lc_edge(l.nx) != 4 || lc_edge(l.ny) != 4 || lc_edge(l.nz) != 4 || (uintptr_t)occ[r] % 4 ||
+            l.nx > 1024 || l.nspecies != lats[0].nspecies)
+            return SMC_ERR_UNSUPPORTED;
+    }
     smc_status st;
     Workspace *ws = workspace(&st);
     if (!ws) return st;
     const bool is_int = m->kind == SMC_PAIR_I32;
     static std::vector<long long> key_cached;
-    static ResPlan plan_cached;
+    static ResMulti plan_cached;
     const Tuning tu = current_tuning();
-    std::vector<long long> key = {lat->nx, lat->ny, lat->nz, pt.nsh, pt.sw, is_int, ws->device, ws->num_sms,
-                                  tu.tile_y, tu.tile_z};
+    std::vector<long long> key = {R, pt.nsh, pt.sw, is_int, ws->device, ws->num_sms, tu.tile_y, tu.tile_z};
+    for (int r = 0; r < R; ++r) key.insert(key.end(), {lats[r].nx, lats[r].ny, lats[r].nz});
     if (key != key_cached) {
-        ResPlan rp;
-        st = is_int ? build_res_plan<true>(*lat, pt, ws, rp) : build_res_plan<false>(*lat, pt, ws, rp);
-        if (st != SMC_OK) return st;
-        plan_cached = rp;
+        free_waves(plan_cached);
+        key_cached.clear();
+        ResMulti mp;
+        st = is_int ? build_res_multi<true>(R, lats, pt, ws, mp) : build_res_multi<false>(R, lats, pt, ws, mp);
+        plan_cached = std::move(mp);
+        if (st != SMC_OK) {
+            free_waves(plan_cached);
+            plan_cached.ok = false;
+            return st;
+        }
         key_cached = key;
     }
-    const ResPlan &rp = plan_cached;
-    if (!rp.ok) return SMC_ERR_UNSUPPORTED;
+    const ResMulti &mp = plan_cached;
+    if (!mp.ok) return SMC_ERR_UNSUPPORTED;
 
-    static SweepParams P;
-    memset(&P, 0, sizeof P);
-    P.R = 1;
-    P.G = 32;
-    P.Lx = P.Ly = P.Lz = 4;
-    P.nshells = m->nshells;
-    P.S = lat->nspecies;
-    P.seed = seed;
-    P.timeout_ns = debug_timeout_ns();
-    P.skip_tile = (int)debug_skip_tile();
-    P.rowB = rp.rowB;
-    P.Wy = rp.Wy;
-    P.Wz = rp.Wz;
-    P.NBy = rp.NBy;
-    P.NBz = rp.NBz;
-    P.rcols = rp.nc;
-    P.rblob = rp.blob;
-    RepDesc &d = P.rep[0];
-    d.occ = occ;
-    d.e_acc = e_acc;
-    d.n_acc = (long long *)n_acc;
-    d.nx = lat->nx;
-    d.ny = lat->ny;
-    d.nz = lat->nz;
-    d.NLx = d.nx / 4;
-    d.NLy = d.ny / 4;
-    d.NLz = d.nz / 4;
-    d.rep = replica;
-    P.qrow = pt.rw;
-    P.escale = pt.scale;
-    memcpy(P.qtab, pt.rows.data(), pt.rows.size() * 4);
-
-    // per-sweep temperatures: one launch per kMaxBeta sweeps
+    // per-sweep temperatures: one launch per kMaxBeta / (replicas of the wave) sweeps
     bool constant = true;
-    for (int t = 1; t < nsweeps; ++t)
-        if (kT[t] != kT[0]) constant = false;
+    for (int r = 0; r < R && constant; ++r)
+        for (int t = 1; t < nsweeps; ++t)
+            if (kT[(size_t)r * nsweeps + t] != kT[(size_t)r * nsweeps]) {
+                constant = false;
+                break;
+            }
     const int cap = is_int ? kMaxBeta / 2 : kMaxBeta;
-    const int chunk = constant ? nsweeps : cap;
+    for (const auto &w : mp.waves)
+        if (!constant && (int)w.reps.size() > cap) return SMC_ERR_UNSUPPORTED;
     std::vector<uint32_t> tabs;
     std::vector<std::pair<double, int2>> tindex;
     auto table_of = [&](double kt) -> int2 {
@@ -965,63 +1104,109 @@ smc_status launch_pair_sweep_resident(const smc_lattice *lat, const smc_model *m
         return ti;
     };
     if (is_int)
-        for (int t = 0; t < nsweeps; ++t) table_of(kT[t]);
+        for (int r = 0; r < R; ++r)
+            for (int t = 0; t < nsweeps; ++t) table_of(kT[(size_t)r * nsweeps + t]);
 
-    // workspace: [flags | part_e | part_n | ticket, abort | descriptors | lists | tables | lattice copy | versions]
-    const size_t N = 2 * (size_t)lat->nx * lat->ny * lat->nz;
-    const size_t nb = (size_t)rp.nblocks, np = nb * rp.nc;
-    const size_t off_flags = 0, off_pe = ((nb * 4 + 15) / 16) * 16, off_pn = off_pe + np * 8;
-    const size_t off_misc = off_pn + np * 8, off_desc = off_misc + 16;
-    const size_t off_lists = off_desc + ((rp.desc.size() * 4 + 15) / 16) * 16;
-    const size_t off_tab = off_lists + ((rp.lists.size() * 4 + 15) / 16) * 16;
+    // workspace: [flags | part_e | part_n | ticket, abort | tables | lattice copies | versions], sized for
+    // the largest wave
+    size_t nbmax = 0, exmax = 0, vwmax = 0;
+    for (const auto &w : mp.waves) {
+        nbmax = std::max(nbmax, (size_t)w.nblocks);
+        exmax = std::max(exmax, w.exch_bytes);
+        vwmax = std::max(vwmax, w.ver_words);
+    }
+    const size_t np = nbmax * kResCols;
+    const size_t off_flags = 0, off_pe = ((nbmax * 4 + 15) / 16) * 16, off_pn = off_pe + np * 8;
+    const size_t off_misc = off_pn + np * 8, off_tab = off_misc + 16;
     const size_t off_exch = off_tab + ((tabs.size() * 4 + 255) / 256) * 256;
-    const size_t off_ver = off_exch + ((N + 255) / 256) * 256;
-    const size_t ver_bytes = (size_t)2 * rp.nver * (size_t)(lat->nx / 4) * 8;
-    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_ver + ver_bytes, &st);
+    const size_t off_ver = off_exch + exmax;
+    unsigned char *scr = (unsigned char *)workspace_scratch(ws, off_ver + vwmax * 8, &st);
     if (!scr) return st;
-    P.flags = (uint32_t *)(scr + off_flags);
-    P.part_e = (double *)(scr + off_pe);
-    P.part_n = (long long *)(scr + off_pn);
-    P.ticket = (unsigned *)(scr + off_misc);
-    P.abort_flag = (int *)(scr + off_misc + 4);
-    P.status = ws->status;
-    P.rdesc = (const int *)(scr + off_desc);
-    P.rlists = (const uint32_t *)(scr + off_lists);
-    P.tab = (const uint32_t *)(scr + off_tab);
-    P.exch = (int8_t *)(scr + off_exch);
-    P.xver = (unsigned long long *)(scr + off_ver);
-    P.nver = rp.nver;
-    P.rxw = rp.nxw;
-    cudaError_t e = cudaMemcpyAsync(scr + off_desc, rp.desc.data(), rp.desc.size() * 4, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(scr + off_lists, rp.lists.data(), rp.lists.size() * 4, cudaMemcpyHostToDevice, stream);
-    if (e == cudaSuccess && !tabs.empty())
+    cudaError_t e = cudaSuccess;
+    if (!tabs.empty()) {
         e = cudaMemcpyAsync(scr + off_tab, tabs.data(), tabs.size() * 4, cudaMemcpyHostToDevice, stream);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(resident plan)");
-    for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
-        const int nc = std::min(chunk, nsweeps - t0);
-        P.sweep0 = sweep0 + (uint64_t)t0;
-        P.nsweeps = nc;
-        P.beta_stride = constant ? 0 : 1;
-        for (int t = 0; t < (constant ? 1 : nc); ++t) {
-            if (is_int)
-                P.temp.tabinfo[t] = table_of(kT[t0 + t]);
-            else
-                P.temp.beta[t] = (float)(-1.4426950408889634 * pt.scale / kT[t0 + t]);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpyAsync(acceptance tables)");
+    }
+    static SweepParams P;
+    for (const auto &w : mp.waves) {
+        memset(&P, 0, sizeof P);
+        const int Rw = (int)w.reps.size();
+        P.R = Rw;
+        P.G = 32;
+        P.Lx = P.Ly = P.Lz = 4;
+        P.nshells = m->nshells;
+        P.S = lats[0].nspecies;
+        P.seed = seed;
+        P.timeout_ns = debug_timeout_ns();
+        P.skip_tile = (int)debug_skip_tile();
+        P.rblob = w.blob;
+        P.rxw = mp.rp[w.reps[0]].nxw;
+        P.qrow = pt.rw;
+        P.escale = pt.scale;
+        memcpy(P.qtab, pt.rows.data(), pt.rows.size() * 4);
+        P.flags = (uint32_t *)(scr + off_flags);
+        P.part_e = (double *)(scr + off_pe);
+        P.part_n = (long long *)(scr + off_pn);
+        P.ticket = (unsigned *)(scr + off_misc);
+        P.abort_flag = (int *)(scr + off_misc + 4);
+        P.status = ws->status;
+        P.rdesc = (const int *)w.dev;
+        P.rlists = (const uint32_t *)((const unsigned char *)w.dev + w.lists_off);
+        P.tab = (const uint32_t *)(scr + off_tab);
+        P.exch = (int8_t *)(scr + off_exch);
+        P.xver = (unsigned long long *)(scr + off_ver);
+        for (int lr = 0; lr < Rw; ++lr) {
+            const int r = w.reps[lr];
+            RepDesc &d = P.rep[lr];
+            d.occ = occ[r];
+            d.e_acc = e_acc ? e_acc + r : nullptr;
+            d.n_acc = n_acc ? (long long *)n_acc + r : nullptr;
+            d.nx = lats[r].nx;
+            d.ny = lats[r].ny;
+            d.nz = lats[r].nz;
+            d.NLx = d.nx / 4;
+            d.NLy = d.ny / 4;
+            d.NLz = d.nz / 4;
+            d.rep = replica0 + (uint32_t)r;
         }
-        // flags, sums and tags from zero: a tag (group + 1 >= 1) only ever
-        // matches a version written in this launch
-        e = cudaMemsetAsync(scr, 0, off_desc, stream);
-        if (e == cudaSuccess) e = cudaMemsetAsync(scr + off_ver, 0, ver_bytes, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(resident scratch)");
-        const long long nw = (long long)(N / 4);
-        const int grid = (int)std::max<long long>(1, std::min<long long>((nw + 255) / 256, (long long)ws->num_sms * 8));
-        k_occ_to_exch<<<grid, 256, 0, stream>>>(occ, P.exch, (long long)N, lat->nspecies, P.status);
-        e = cudaGetLastError();
-        if (e != cudaSuccess) return cuda_fail(e, "k_occ_to_exch");
-        void *args[] = {(void *)&P};
-        e = cudaLaunchCooperativeKernel(rp.kernel, dim3(rp.nblocks), dim3((rp.nc + rp.nxw + 1) * 32), args, rp.smem, stream);
-        if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(resident sweep)");
+        const int chunk = constant ? nsweeps : std::max(1, cap / Rw);
+        for (int t0 = 0; t0 < nsweeps; t0 += chunk) {
+            const int nc = std::min(chunk, nsweeps - t0);
+            P.sweep0 = sweep0 + (uint64_t)t0;
+            P.nsweeps = nc;
+            P.beta_stride = constant ? 0 : nc;
+            for (int lr = 0; lr < Rw; ++lr)
+                for (int t = 0; t < (constant ? 1 : nc); ++t) {
+                    const double kt = kT[(size_t)w.reps[lr] * nsweeps + t0 + t];
+                    const int idx = constant ? lr : lr * nc + t;
+                    if (is_int)
+                        P.temp.tabinfo[idx] = table_of(kt);
+                    else
+                        P.temp.beta[idx] = (float)(-1.4426950408889634 * pt.scale / kt);
+                }
+            // flags, sums and tags from zero: a tag (group + 1 >= 1) only ever
+            // matches a version written in this launch
+            e = cudaMemsetAsync(scr, 0, off_tab, stream);
+            if (e == cudaSuccess) e = cudaMemsetAsync(scr + off_ver, 0, w.ver_words * 8, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(resident scratch)");
+            size_t xo = 0;
+            for (int lr = 0; lr < Rw; ++lr) {
+                const smc_lattice &l = lats[w.reps[lr]];
+                const size_t N = 2 * (size_t)l.nx * l.ny * l.nz;
+                const long long nw = (long long)(N / 4);
+                const int grid =
+                    (int)std::max<long long>(1, std::min<long long>((nw + 255) / 256, (long long)ws->num_sms * 8));
+                k_occ_to_exch<<<grid, 256, 0, stream>>>(occ[w.reps[lr]], P.exch + xo, (long long)N, l.nspecies,
+                                                        P.status);
+                xo += (N + 255) / 256 * 256;
+            }
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_fail(e, "k_occ_to_exch");
+            void *args[] = {(void *)&P};
+            e = cudaLaunchCooperativeKernel(mp.kernel, dim3(w.nblocks), dim3((kResCols + P.rxw + 1) * 32), args,
+                                            w.smem, stream);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaLaunchCooperativeKernel(resident sweep)");
+        }
     }
     return SMC_OK;
 }

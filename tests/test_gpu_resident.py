@@ -64,6 +64,8 @@ def _run_int(smc, dims, S, nshells, nsweeps, kT, tile=(0, 0), seed=7, vseed=3, c
 
 
 @pytest.mark.parametrize("dims,S,nsh,tile", [((16, 12, 12), 5, 2, (0, 0)), ((32, 16, 16), 3, 3, (0, 0)),
+                                             ((20, 12, 16), 5, 2, (0, 0)), ((36, 16, 12), 4, 3, (0, 0)),
+                                             ((12, 16, 12), 5, 2, (0, 0)),
                                              ((32, 24, 48), 5, 2, (2, 4)), ((16, 24, 12), 8, 2, (2, 1)),
                                              ((48, 12, 36), 2, 3, (1, 3)), ((16, 28, 16), 5, 2, (2, 2))])
 def test_resident_integer_trajectories(smc, dims, S, nsh, tile):
@@ -119,3 +121,55 @@ def test_resident_timeout_is_reported_and_gpu_stays_usable(smc):
         smc.debug_set(smc.DBG_SKIP_PUBLISH, -1)
         smc.debug_set(smc.DBG_TIMEOUT_MS, 2000)
     _run_int(smc, dims, 2, 2, 2, 0.025)
+
+
+def _batched(smc, edges, nsweeps, kT, is_int, resident):
+    S = 5
+    if is_int:
+        model = smc.Model(smc.PAIR_I32, 2, inputs.pair_int_coeffs(3, 2, S), unit_ev=1e-4)
+    else:
+        model = smc.Model(smc.PAIR_F32, 2, inputs.pair_f32_coeffs(inputs.CONFIG2["coeff_seed"], 2, S))
+    lats = [smc.Lattice(e, e + 4 * (i % 2), e, S) for i, e in enumerate(edges)]
+    occs = []
+    for r, lat in enumerate(lats):
+        o = torch.empty(lat.nsites, dtype=torch.int8, device=dev())
+        smc.init_lattice(lat, inputs.equiatomic_counts(lat.nsites, S), 3, o, replica=r)
+        occs.append(o)
+    R = len(lats)
+    e_acc = torch.zeros(R, dtype=torch.float64, device=dev())
+    n_acc = torch.zeros(R, dtype=torch.int64, device=dev())
+    kTr = np.repeat(np.asarray(kT, dtype=np.float64)[:, None], nsweeps, axis=1)
+    smc.debug_set(smc.DBG_RESIDENT, 0 if resident else 1)
+    try:
+        smc.sweep_batched(lats, model, occs, 3, 0, nsweeps, kTr, e_acc=e_acc, n_acc=n_acc)
+        smc.check()
+    finally:
+        smc.debug_set(smc.DBG_RESIDENT, 0)
+    return lats, occs, e_acc, n_acc
+
+
+@pytest.mark.parametrize("edges,is_int", [([16, 20, 24, 32, 16, 28], True), ([32] * 20 + [48] * 4, False),
+                                          ([36, 44, 12, 52], True)])
+def test_resident_replicas_equal_streaming_replicas(smc, edges, is_int):
+    """Replicas of different sizes in waves of one launch each (the second
+    case needs more than one wave): the same occupancies, accepted counts and
+    energy sums as the streaming batched kernel, bit for bit."""
+    kT = np.linspace(0.03, 0.09, len(edges))
+    _, a, ea, na = _batched(smc, edges, 6, kT, is_int, True)
+    _, b, eb, nb = _batched(smc, edges, 6, kT, is_int, False)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+    assert torch.equal(na, nb) and torch.equal(ea, eb)
+
+
+def test_resident_replicas_match_oracle(smc):
+    edges, kT = [16, 20, 24], np.array([0.03, 0.05, 0.07])
+    lats, occs, ea, na = _batched(smc, edges, 3, kT, True, True)
+    S = 5
+    V = inputs.pair_int_coeffs(3, 2, S)
+    for r, lat in enumerate(lats):
+        olat = oracle.Lattice(lat.nx, lat.ny, lat.nz, S)
+        ref = oracle.init_lattice(olat, inputs.equiatomic_counts(lat.nsites, S), 3, replica=r)
+        e, n = oracle.sweep(olat, oracle.Model(oracle.PAIR_I32, 2, V, unit_ev=1e-4), ref, 3, 0, 3, kT[r], replica=r)
+        assert np.array_equal(occs[r].cpu().numpy(), ref)
+        assert int(na[r].item()) == n
