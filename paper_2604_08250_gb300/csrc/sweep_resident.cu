@@ -340,7 +340,10 @@ __device__ bool res_fetch_versions(const SweepParams &P, const unsigned long lon
     return true;
 }
 
-template <bool IS_INT, int NSH, int SW>
+// RB, WY: the row pitch and window rows per y of every block, when known at
+// compile time (0: read from the descriptor), so that the trial's row offsets
+// are immediates.
+template <bool IS_INT, int NSH, int SW, int RB, int WY>
 __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
 {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
@@ -351,8 +354,8 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
     const int rep = d[10];
     const RepDesc &RD = P.rep[rep];
     const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
-    const int Wy = d[15], Wz = d[16];
-    const uint32_t rb = (uint32_t)d[17], RZ = (uint32_t)Wy * rb;
+    const int Wy = WY ? WY : d[15], Wz = d[16];
+    const uint32_t rb = RB ? (uint32_t)RB : (uint32_t)d[17], RZ = (uint32_t)Wy * rb;
     const int8_t *exch = P.exch + (uint32_t)d[18];
     unsigned long long *xver = P.xver + (uint32_t)d[19];
     const int nver = d[20];
@@ -697,8 +700,17 @@ template <bool IS_INT>
 const void *pick_resident(int nsh, int sw)
 {
     if (nsh >= 3)
-        return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 3, 2> : (const void *)k_sweep_resident<IS_INT, 3, 1>;
-    return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 2, 2> : (const void *)k_sweep_resident<IS_INT, 2, 1>;
+        return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 3, 2, 0, 0>
+                       : (const void *)k_sweep_resident<IS_INT, 3, 1, 0, 0>;
+    return sw == 2 ? (const void *)k_sweep_resident<IS_INT, 2, 2, 0, 0> : (const void *)k_sweep_resident<IS_INT, 2, 1, 0, 0>;
+}
+// the specialisation for blocks of 2 x 4 columns on 128-cell rows (pitch 256
+// bytes, 15 window rows per y), when every block of a launch has them
+template <bool IS_INT>
+const void *pick_resident_fixed(int nsh, int sw, int rowB, int Wy)
+{
+    if (nsh == 2 && sw == 1 && rowB == 256 && Wy == 15) return (const void *)k_sweep_resident<IS_INT, 2, 1, 256, 15>;
+    return nullptr;
 }
 
 // Builds the plan for one lattice, or leaves ok = 0 when the lattice does not
@@ -980,8 +992,27 @@ smc_status build_res_multi(int R, const smc_lattice *lats, const PairTable &pt, 
         mp.kernel = rp.kernel;
         mp.rp.push_back(std::move(rp));
     }
+    bool same = true;
+    for (const auto &rp : mp.rp) same = same && rp.rowB == mp.rp[0].rowB && rp.Wy == mp.rp[0].Wy;
+    const void *fixed = same ? pick_resident_fixed<IS_INT>(pt.nsh, pt.sw, mp.rp[0].rowB, mp.rp[0].Wy) : nullptr;
     cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, mp.kernel);
+    cudaError_t e;
+    if (fixed) {
+        e = cudaFuncGetAttributes(&fa, fixed);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+        e = cudaFuncSetAttribute(fixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(ws->smem_optin - fa.sharedSizeBytes));
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed, (kResCols + mp.rp[0].nxw + 1) * 32,
+                                                          mp.rp[0].smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (per_sm >= 1) {
+            mp.kernel = fixed;
+            for (auto &rp : mp.rp) rp.per_sm = std::min(rp.per_sm, per_sm);
+        }
+    }
+    e = cudaFuncGetAttributes(&fa, mp.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
     // waves: replicas in order, as many as are resident at once
