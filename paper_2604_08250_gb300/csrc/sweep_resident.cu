@@ -519,45 +519,37 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
             named_sync(bar_ready(gs), nbar);
             if (gs >= s_stop) break;
             if (active) {
-                // the 5 rows a mini-step writes (own row, partner 2 x 2), for the halo refresh
-                uint32_t hrow = ownb;
-                if (lane >= 2 && lane < 10) {
-                    const int k = (lane - 2) >> 1;
-                    hrow = parb + (uint32_t)(k & 1) * rb + (uint32_t)(k >> 1) * RZ;
-                }
                 auto trial = [&](int x, uint32_t w) {
                     uint32_t a8, b8, pb;
                     const uint32_t ya = ownb + (uint32_t)x;
                     const int32_t dE = res_dE<NSH, SW>(ya, parb + (uint32_t)(x + soff), rb, RZ, w, a8, b8, pb);
                     if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
-                        const int xb = x + soff + (int)(w >> 31);
-                        pb += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
+                        int xb = x + soff + (int)(w >> 31);
+                        const int wrap = xb < 0 ? nx : (xb >= nx ? -nx : 0);
+                        pb += (uint32_t)wrap;
+                        xb += wrap;
+                        // the cell and, within 4 of a row end, its periodic
+                        // x-halo copy (no halo pass between mini-steps)
                         g_smem[ya] = (unsigned char)b8;
+                        if (x < 4) g_smem[ya + nx] = (unsigned char)b8;
+                        if (x >= nx - 4) g_smem[ya - nx] = (unsigned char)b8;
                         g_smem[pb] = (unsigned char)a8;
+                        if (xb < 4) g_smem[pb + nx] = (unsigned char)a8;
+                        if (xb >= nx - 4) g_smem[pb - nx] = (unsigned char)a8;
                         accE += dE;
                         accN += 1;
                     }
                 };
-                auto halo = [&]() {
-                    __syncwarp();
-                    if (lane < 10) {
-                        if (lane & 1)
-                            *(unsigned *)(g_smem + hrow + nx) = *(const unsigned *)(g_smem + hrow);
-                        else
-                            *(unsigned *)(g_smem + hrow - 4) = *(const unsigned *)(g_smem + hrow + nx - 4);
-                    }
-                    __syncwarp();
-                };
                 if (nk == 1 && NLx == 32) {
                     // one link cell per lane: its four words stay in registers
                     trial(4 * lane + 0, w4.x);
-                    halo();
+                    __syncwarp();  // the next mini-step reads what this one wrote
                     trial(4 * lane + 1, w4.y);
-                    halo();
+                    __syncwarp();  // the next mini-step reads what this one wrote
                     trial(4 * lane + 2, w4.z);
-                    halo();
+                    __syncwarp();  // the next mini-step reads what this one wrote
                     trial(4 * lane + 3, w4.w);
-                    halo();
+                    __syncwarp();  // the next mini-step reads what this one wrote
                 } else {
                     for (int dx = 0; dx < 4; ++dx) {
 #pragma unroll 1
@@ -567,7 +559,7 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
                                 trial(4 * i + dx, *(const uint32_t *)(g_smem + wsm +
                                                                       (uint32_t)(((k * 4 + dx) * 32 + lane) * 4)));
                         }
-                        halo();
+                        __syncwarp();  // the next mini-step reads what this one wrote
                     }
                 }
                 // publish the versions of the rows this column wrote that other
