@@ -169,6 +169,11 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  * either, and from those sites' counts, in FP32 (C left out, where it
  * cancels), within 1e-5 eV of FP64.  They need every axis a multiple of 4
  * cells and >= 8.
+ * Pair models on lattices with every axis a multiple of 4 and >= 8 cells
+ * whose rows fit the SMs' shared memory (128^3 and below) keep the lattice
+ * there for the whole call (one cooperative launch per call, row versions
+ * exchanged between CTAs through L2); larger lattices stream their rows from
+ * device memory.  Both give the same trajectory bit for bit.
  * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP or
  * qSRO models on lattices their kernels do not take), SMC_ERR_CUDA. */
 smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
@@ -210,8 +215,10 @@ smc_status smc_sweep_noalloc(const smc_lattice *lat, const smc_model *model, int
 
 /* Independent replicas of possibly different sizes (each its own lattice and
  * occupancy, shared model), advanced together in one persistent launch per
- * chunk of sweeps.  Replica r uses RNG replica index replica0 + r, so it
- * reproduces smc_sweep(..., replica0 + r, ...) bit for bit.
+ * chunk of sweeps (pair models whose replicas all fit shared memory: one
+ * launch per wave of replicas resident at once).  Replica r uses RNG replica
+ * index replica0 + r, so it reproduces smc_sweep(..., replica0 + r, ...) bit
+ * for bit.
  *   lats    host [R];  occ  host [R] array of device pointers.
  *   kT      host [R][nsweeps] (eV).
  *   e_acc, n_acc  device [R], nullable.
