@@ -11,8 +11,8 @@
 // launch.  Rows that another CTA also touches travel as versions:
 //
 //   after group g, a CTA publishes each row its columns wrote at g that
-//   another CTA reads before the row's next write: nx / 4 64-bit words of
-//   4 species bytes (x 8) and the tag g + 1 (g counted from the launch);
+//   another CTA reads before the row's next write: 64-bit words of 4
+//   species bytes (x 8) and the tag g + 1 (g counted from the launch);
 //   before group g, it fetches the rows its columns read at g whose last
 //   write is another CTA's and whose version it has not read since, polling
 //   each word until it carries the expected tag.
@@ -476,6 +476,10 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
         const int cy = d[0] + warp % max(d[2], 1), cz = d[1] + warp / max(d[2], 1);
         const uint32_t wsm = wsm0 + (uint32_t)warp * (uint32_t)nk * 512u;
         const int ylo0 = d[4], ylo1 = d[5], zlo0 = d[6], zlo1 = d[7];
+        // publish chunks: (nx + 7) / 8 per row (a last half chunk carries 4
+        // bytes of the halo, not read); this lane's first chunk and the step
+        const int cpr = (nx + 7) >> 3;
+        const int pub_e0 = lane / cpr, pub_c0 = lane - pub_e0 * cpr, pub_de = 32 / cpr, pub_dc = 32 - pub_de * cpr;
         long long accE = 0, accN = 0;
         for (int gs = 0; gs < total; ++gs) {
             const int t = gs >> 5, g = gs & 31;
@@ -567,13 +571,20 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
                 if (blk != P.skip_tile) {
                     const uint2 *pe = (const uint2 *)(L + po[g * nc + warp]);
                     const int np = (int)(po[g * nc + warp + 1] - po[g * nc + warp]) >> 1;
-                    const int cpr = (nx + 7) >> 3;  // a last half chunk carries 4 bytes of the halo: not read
                     const unsigned long long tag = (unsigned long long)(gs + 1) << 32;
+                    // chunk q = lane + 32 i of entry e = q / cpr, chunk c = q % cpr,
+                    // stepped without divisions
+                    int e = pub_e0, c = pub_c0;
                     for (int q = lane; q < np * cpr; q += 32) {
-                        const int e = q / cpr, c = q - e * cpr;
                         const uint2 en = pe[e];
                         const uint2 w = *(const uint2 *)(g_smem + rows + en.x * rb + 16u + 8u * c);
                         st_relaxed_v2u64(xver + ver_word(nver, gs, en.y, nx) + 2 * c, tag | w.x, tag | w.y);
+                        e += pub_de;
+                        c += pub_dc;
+                        if (c >= cpr) {
+                            c -= cpr;
+                            ++e;
+                        }
                     }
                 }
             }
