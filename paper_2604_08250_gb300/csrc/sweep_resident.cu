@@ -1018,28 +1018,47 @@ smc_status build_res_multi(int R, const smc_lattice *lats, const PairTable &pt, 
     e = cudaFuncGetAttributes(&fa, mp.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
     const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
-    // waves: replicas in order, as many as are resident at once
+    // waves: first-fit decreasing by block count (every wave's blocks
+    // resident at once, at most kMaxReplicas replicas per wave)
     auto smem_with_blob = [&](const ResPlan &rp, int blob) {
         return rp.smem - ((size_t)rp.blob * 4 + 15) / 16 * 16 + ((size_t)blob * 4 + 15) / 16 * 16;
     };
-    int r = 0;
-    while (r < R) {
-        ResWave w;
-        int per_sm = 1 << 30;
-        while (r < R && (int)w.reps.size() < kMaxReplicas) {
-            const ResPlan &rp = mp.rp[r];
-            const int ps = std::min(per_sm, rp.per_sm), blob = std::max(w.blob, rp.blob);
+    std::vector<int> order(R);
+    for (int r = 0; r < R; ++r) order[r] = r;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return mp.rp[a].nblocks > mp.rp[b].nblocks; });
+    std::vector<ResWave> bins;
+    std::vector<int> bin_ps;
+    for (int r : order) {
+        const ResPlan &rp = mp.rp[r];
+        bool placed = false;
+        for (size_t i = 0; i < bins.size() && !placed; ++i) {
+            ResWave &w = bins[i];
+            const int ps = std::min(bin_ps[i], rp.per_sm), blob = std::max(w.blob, rp.blob);
             size_t smem = smem_with_blob(rp, blob);
             for (int q : w.reps) smem = std::max(smem, smem_with_blob(mp.rp[q], blob));
-            if (!w.reps.empty() && (w.nblocks + rp.nblocks > ps * ws->num_sms || smem > dyn_max)) break;
-            if (smem > dyn_max) return SMC_OK;
+            if ((int)w.reps.size() >= kMaxReplicas || w.nblocks + rp.nblocks > ps * ws->num_sms || smem > dyn_max)
+                continue;
             w.reps.push_back(r);
             w.nblocks += rp.nblocks;
             w.blob = blob;
             w.smem = smem;
-            per_sm = ps;
-            ++r;
+            bin_ps[i] = ps;
+            placed = true;
         }
+        if (!placed) {
+            if (smem_with_blob(rp, rp.blob) > dyn_max || rp.nblocks > rp.per_sm * ws->num_sms) return SMC_OK;
+            ResWave w;
+            w.reps.push_back(r);
+            w.nblocks = rp.nblocks;
+            w.blob = rp.blob;
+            w.smem = smem_with_blob(rp, rp.blob);
+            bins.push_back(w);
+            bin_ps.push_back(rp.per_sm);
+        }
+    }
+    for (auto &w : bins) {
+        std::sort(w.reps.begin(), w.reps.end());
         // descriptors and lists of the wave's blocks
         std::vector<int> desc;
         std::vector<uint32_t> lists;
