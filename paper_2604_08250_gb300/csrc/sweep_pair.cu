@@ -670,6 +670,46 @@ __device__ __forceinline__ void fast_stage(const RepDesc &RD, const FastGeo &q, 
     }
 }
 
+// Histogram words of one neighbour (SW words of four 8-bit fields), summed
+// as values so that the counts of a shell form short add trees instead of
+// one chain of dependent adds.
+template <int SW>
+struct HV {
+    uint32_t w[SW];
+};
+template <int SW>
+__device__ __forceinline__ HV<SW> hv(uint32_t v8)
+{
+    HV<SW> h;
+    h.w[0] = nib8(v8);
+    if constexpr (SW == 2) h.w[1] = nib8hi(v8);
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> hconst(uint32_t c)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = c;
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> operator+(const HV<SW> &a, const HV<SW> &b)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] + b.w[w];
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> operator-(const HV<SW> &a, const HV<SW> &b)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] - b.w[w];
+    return h;
+}
+
 // dE_fix of the trial at a = own row (0, 0), x, with ya = row-0 body + x and
 // pa = ya + s_off, partner direction dir; the species a8, b8 (x 8) and b's
 // shared-memory offset through references.
@@ -677,80 +717,56 @@ template <int NSH, int SW, int RB>
 __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rbr, uint32_t dir, uint32_t lut,
                                            uint32_t qt, uint32_t &a8, uint32_t &b8, uint32_t &pb)
 {
+    using H = HV<SW>;
     const uint32_t rb = RB ? (uint32_t)RB : rbr;
     constexpr uint32_t S11 = pslot<NSH>(1, 1), S21 = pslot<NSH>(2, 1), S12 = pslot<NSH>(1, 2), S22 = pslot<NSH>(2, 2);
     const int4 L = *(const int4 *)(g_smem + lut + dir * 16u);
     a8 = LD8(ya + 4 * rb);
     pb = pa + (uint32_t)L.x;
     b8 = LD8(pb);
-    uint32_t H[NSH][SW];
-#pragma unroll
-    for (int m = 0; m < NSH; ++m)
-#pragma unroll
-        for (int w = 0; w < SW; ++w) H[m][w] = m < 2 ? 0x08080808u : 0x10101010u;
-    // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
-    // trial-sublattice neighbours plus a
-    hadd<SW>(H[0], a8);
-    hsub<SW>(H[0], b8);
-    hadd<SW>(H[0], LD8(pa + S11 * rb));
-    hadd<SW>(H[0], LD8(pa + S11 * rb + 1));
-    hadd<SW>(H[0], LD8(pa + S21 * rb));
-    hadd<SW>(H[0], LD8(pa + S21 * rb + 1));
-    hadd<SW>(H[0], LD8(pa + S12 * rb));
-    hadd<SW>(H[0], LD8(pa + S12 * rb + 1));
-    hadd<SW>(H[0], LD8(pa + S22 * rb));
-    hadd<SW>(H[0], LD8(pa + S22 * rb + 1));
     const uint32_t ob = ya + (uint32_t)L.y;
-    hsub<SW>(H[0], LD8(ob));
-    hsub<SW>(H[0], LD8(ob + 1));
-    hsub<SW>(H[0], LD8(ob + rb));
-    hsub<SW>(H[0], LD8(ob + rb + 1));
-    hsub<SW>(H[0], LD8(ob + 3 * rb));
-    hsub<SW>(H[0], LD8(ob + 3 * rb + 1));
-    hsub<SW>(H[0], LD8(ob + 4 * rb));
-    hsub<SW>(H[0], LD8(ob + 4 * rb + 1));
+    // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
+    // trial-sublattice neighbours plus a (biased by 8 per field)
+    const H a0 = hconst<SW>(0x08080808u) + hv<SW>(a8) + hv<SW>(LD8(pa + S11 * rb));
+    const H a1 = hv<SW>(LD8(pa + S11 * rb + 1)) + hv<SW>(LD8(pa + S21 * rb)) + hv<SW>(LD8(pa + S21 * rb + 1));
+    const H a2 = hv<SW>(LD8(pa + S12 * rb)) + hv<SW>(LD8(pa + S12 * rb + 1)) + hv<SW>(LD8(pa + S22 * rb));
+    const H a3 = hv<SW>(LD8(pa + S22 * rb + 1));
+    const H b0 = hv<SW>(b8) + hv<SW>(LD8(ob)) + hv<SW>(LD8(ob + 1));
+    const H b1 = hv<SW>(LD8(ob + rb)) + hv<SW>(LD8(ob + rb + 1)) + hv<SW>(LD8(ob + 3 * rb));
+    const H b2 = hv<SW>(LD8(ob + 3 * rb + 1)) + hv<SW>(LD8(ob + 4 * rb)) + hv<SW>(LD8(ob + 4 * rb + 1));
+    const H h0 = (a0 + a1) + (a2 + a3) - ((b0 + b1) + b2);
     // shell 2: a's 6 trial-sublattice neighbours, b's 6 partner-sublattice ones
-    hadd<SW>(H[1], LD8(ya + 4 * rb - 1));
-    hadd<SW>(H[1], LD8(ya + 4 * rb + 1));
-    hadd<SW>(H[1], LD8(ya + 3 * rb));
-    hadd<SW>(H[1], LD8(ya + 5 * rb));
-    hadd<SW>(H[1], LD8(ya + rb));
-    hadd<SW>(H[1], LD8(ya + 7 * rb));
-    hsub<SW>(H[1], LD8(pb - 1));
-    hsub<SW>(H[1], LD8(pb + 1));
-    hsub<SW>(H[1], LD8(pb - rb));
-    hsub<SW>(H[1], LD8(pb + rb));
-    hsub<SW>(H[1], LD8(pb - (uint32_t)L.z));
-    hsub<SW>(H[1], LD8(pb + (uint32_t)L.w));
+    const H c0 = hconst<SW>(0x08080808u) + hv<SW>(LD8(ya + 4 * rb - 1)) + hv<SW>(LD8(ya + 4 * rb + 1));
+    const H c1 = hv<SW>(LD8(ya + 3 * rb)) + hv<SW>(LD8(ya + 5 * rb)) + hv<SW>(LD8(ya + rb));
+    const H c2 = hv<SW>(LD8(ya + 7 * rb));
+    const H d0 = hv<SW>(LD8(pb - 1)) + hv<SW>(LD8(pb + 1)) + hv<SW>(LD8(pb - rb));
+    const H d1 = hv<SW>(LD8(pb + rb)) + hv<SW>(LD8(pb - (uint32_t)L.z)) + hv<SW>(LD8(pb + (uint32_t)L.w));
+    const H h1 = ((c0 + c1) + c2) - (d0 + d1);
+    uint32_t Hw[NSH][SW];
+#pragma unroll
+    for (int w = 0; w < SW; ++w) {
+        Hw[0][w] = h0.w[w];
+        Hw[1][w] = h1.w[w];
+    }
     if constexpr (NSH >= 3) {
-        hadd<SW>(H[2], LD8(ya));
-        hadd<SW>(H[2], LD8(ya + 2 * rb));
-        hadd<SW>(H[2], LD8(ya + 6 * rb));
-        hadd<SW>(H[2], LD8(ya + 8 * rb));
-        hadd<SW>(H[2], LD8(ya + 3 * rb - 1));
-        hadd<SW>(H[2], LD8(ya + 3 * rb + 1));
-        hadd<SW>(H[2], LD8(ya + 5 * rb - 1));
-        hadd<SW>(H[2], LD8(ya + 5 * rb + 1));
-        hadd<SW>(H[2], LD8(ya + rb - 1));
-        hadd<SW>(H[2], LD8(ya + rb + 1));
-        hadd<SW>(H[2], LD8(ya + 7 * rb - 1));
-        hadd<SW>(H[2], LD8(ya + 7 * rb + 1));
-        hsub<SW>(H[2], LD8(pb - 5 * rb));
-        hsub<SW>(H[2], LD8(pb - 3 * rb));
-        hsub<SW>(H[2], LD8(pb + 3 * rb));
-        hsub<SW>(H[2], LD8(pb + 5 * rb));
-        hsub<SW>(H[2], LD8(pb - rb - 1));
-        hsub<SW>(H[2], LD8(pb - rb + 1));
-        hsub<SW>(H[2], LD8(pb + rb - 1));
-        hsub<SW>(H[2], LD8(pb + rb + 1));
-        hsub<SW>(H[2], LD8(pb - 4 * rb - 1));
-        hsub<SW>(H[2], LD8(pb - 4 * rb + 1));
-        hsub<SW>(H[2], LD8(pb + 4 * rb - 1));
-        hsub<SW>(H[2], LD8(pb + 4 * rb + 1));
+        // shell 3: a's 12 trial-sublattice neighbours, b's 12 partner-sublattice
+        // ones (biased by 16 per field)
+        const H e0 = hconst<SW>(0x10101010u) + hv<SW>(LD8(ya)) + hv<SW>(LD8(ya + 2 * rb));
+        const H e1 = hv<SW>(LD8(ya + 6 * rb)) + hv<SW>(LD8(ya + 8 * rb)) + hv<SW>(LD8(ya + 3 * rb - 1));
+        const H e2 = hv<SW>(LD8(ya + 3 * rb + 1)) + hv<SW>(LD8(ya + 5 * rb - 1)) + hv<SW>(LD8(ya + 5 * rb + 1));
+        const H e3 = hv<SW>(LD8(ya + rb - 1)) + hv<SW>(LD8(ya + rb + 1)) + hv<SW>(LD8(ya + 7 * rb - 1));
+        const H e4 = hv<SW>(LD8(ya + 7 * rb + 1));
+        const H f0 = hv<SW>(LD8(pb - 5 * rb)) + hv<SW>(LD8(pb - 3 * rb)) + hv<SW>(LD8(pb + 3 * rb));
+        const H f1 = hv<SW>(LD8(pb + 5 * rb)) + hv<SW>(LD8(pb - rb - 1)) + hv<SW>(LD8(pb - rb + 1));
+        const H f2 = hv<SW>(LD8(pb + rb - 1)) + hv<SW>(LD8(pb + rb + 1)) + hv<SW>(LD8(pb - 4 * rb - 1));
+        const H f3 = hv<SW>(LD8(pb - 4 * rb + 1)) + hv<SW>(LD8(pb + 4 * rb - 1)) + hv<SW>(LD8(pb + 4 * rb + 1));
+        const H h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
+#pragma unroll
+        for (int w = 0; w < SW; ++w) Hw[2][w] = h2.w[w];
     }
     constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
     const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
-    return dot_fixed<NSH, SW>(H, row);
+    return dot_fixed<NSH, SW>(Hw, row);
 }
 
 // Team synchronisation: the tw warps that share a column meet at named
@@ -779,12 +795,14 @@ __device__ __forceinline__ bool team_and(int tw, int tb, bool p)
 }
 
 // KU trials of mini-step dx per lane: link cells i = ib + is * (k0 + u),
-// u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).
+// u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).  The random
+// words come from the warp's shared-memory words, or from wreg[u] when
+// wreg is given (the words of this mini-step, held in registers).
 template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD>
 __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body, int soff, uint32_t rbr,
                                             uint32_t wsm, int k0, int nk, int ib, int is, int NLx, int nx, int dx,
                                             int lane, float cx, int2 ti, uint32_t lut, uint32_t qt, long long &accE,
-                                            long long &accN)
+                                            long long &accN, const uint32_t *wreg = nullptr)
 {
     const uint32_t rb = RB ? (uint32_t)RB : rbr;
     int32_t dE[KU];
@@ -797,7 +815,8 @@ __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body,
         if (!GUARD || (k < nk && i < NLx)) {
             const int x = 4 * i + dx;
             ya[u] = body + (uint32_t)x;
-            const uint32_t w = *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
+            const uint32_t w =
+                wreg ? wreg[u] : *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
             dE[u] = fast_dE<NSH, SW, RB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
             acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
             // b's store address wraps along x (the load may read a halo copy)
@@ -827,6 +846,13 @@ template <bool IS_INT, int NSH, int SW, int RB>
 __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ SweepParams P)
 {
     constexpr int NROWS = fast_nrows<NSH>();
+    // Rows of RB = nx + 128 bytes (a multiple of 128): every row starts on
+    // the same bank, so the loads of b's rows, which differ from lane to
+    // lane with the partner direction, never conflict.  Each lane then keeps
+    // the random words of its NKW = nx / 128 link cells in registers.
+    constexpr bool WREG = RB != 0 && RB % 128 == 0;
+    constexpr int NKW = WREG ? (RB - 128) / 128 : 1;
+    static_assert(!WREG || (NKW >= 1 && NKW <= 4), "register words: rows of 128 to 512 cells");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int tw = P.team, wi = warp % tw, tix = warp / tw, tpb = nwarp / tw;
     const int gteam = blockIdx.x * tpb + tix, NT = gridDim.x * tpb, NW = gridDim.x * nwarp;
@@ -924,7 +950,21 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             }
             // Philox words of this warp's link cells (while the rows land)
             const uint64_t sweep = P.sweep0 + (uint64_t)t;
-            {
+            uint32_t wr[NKW][4];
+            if constexpr (WREG) {
+                const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0) * nx);
+                const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+#pragma unroll
+                for (int k = 0; k < NKW; ++k) {
+                    const U4 w = philox10(
+                        U4{(rowsite >> 2) + (uint32_t)(ib + is * k), RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
+                        k0, k1);
+                    wr[k][0] = w.x;
+                    wr[k][1] = w.y;
+                    wr[k][2] = w.z;
+                    wr[k][3] = w.w;
+                }
+            } else {
                 const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0) * nx);
                 const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
                 uint32_t *wp = (uint32_t *)(g_smem + wsm);
@@ -981,7 +1021,20 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 hrow = body + (uint32_t)sl * rb;
             }
             for (int dx = 0; dx < 4; ++dx) {
-                if (NLx == is * nkw && (nkw & 3) == 0) {
+                if constexpr (WREG) {
+                    // one trial per link cell of the lane (NLx = 32 NKW), the
+                    // mini-step's word first in each register row
+                    uint32_t wv[NKW];
+#pragma unroll
+                    for (int k = 0; k < NKW; ++k) {
+                        wv[k] = wr[k][0];
+                        wr[k][0] = wr[k][1];
+                        wr[k][1] = wr[k][2];
+                        wr[k][2] = wr[k][3];
+                    }
+                    fast_trials<IS_INT, NSH, SW, RB, NKW, false>(P, body, q.soff, rb, wsm, 0, NKW, ib, is, NLx, nx, dx,
+                                                                 lane, cx, ti, lut, qt, accE, accN, wv);
+                } else if (NLx == is * nkw && (nkw & 3) == 0) {
 #pragma unroll 1
                     for (int kk = 0; kk < nkw; kk += 4)
                         fast_trials<IS_INT, NSH, SW, RB, 4, false>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
@@ -1017,20 +1070,20 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 }
             }
             // ---- write back trial row (0,0) and partner rows (s_off..s_off+1)^2,
-            // the team's threads over (row, chunk) pairs ----
+            // row by row, the team's threads over the row's chunks ----
             {
                 const bool vec = RD.vec != 0;
                 const int cpr = vec ? (nx >> 4) : (nx >> 2);
-                for (int qq = lane + 32 * wi; qq < 5 * cpr; qq += is) {
-                    const int wr = qq / cpr, cc = qq - wr * cpr;
+#pragma unroll 1
+                for (int wrow = 0; wrow < 5; ++wrow) {
                     int slot, gsub, gy, gz;
-                    if (wr == 0) {
+                    if (wrow == 0) {
                         slot = 4;
                         gsub = q.sub;
                         gy = q.y0;
                         gz = q.z0;
                     } else {
-                        const int sy = 1 + ((wr - 1) & 1), sz = 1 + ((wr - 1) >> 1);
+                        const int sy = 1 + ((wrow - 1) & 1), sz = 1 + ((wrow - 1) >> 1);
                         slot = pslot<NSH>(sy, sz);
                         gsub = 1 - q.sub;
                         gy = wrapc(q.y0 + sy - 1 + q.soff, ny);
@@ -1038,10 +1091,12 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                     }
                     int8_t *dstg = RD.occ + ((size_t)((gsub * nz + gz) * ny + gy)) * nx;
                     const unsigned char *srcs = g_smem + body + (uint32_t)slot * rb;
-                    if (vec)
-                        *((int4 *)dstg + cc) = *((const int4 *)srcs + cc);
-                    else
-                        *((unsigned *)dstg + cc) = *((const unsigned *)srcs + cc);
+                    for (int cc = lane + 32 * wi; cc < cpr; cc += is) {
+                        if (vec)
+                            *((int4 *)dstg + cc) = *((const int4 *)srcs + cc);
+                        else
+                            *((unsigned *)dstg + cc) = *((const unsigned *)srcs + cc);
+                    }
                 }
             }
             // every thread's row stores, then one release by the leader's lane 0
@@ -1415,14 +1470,22 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, const PairTa
     return SMC_OK;
 }
 
-template <bool IS_INT>
-const void *pick_fast(int nsh, int sw, int rowB, int R)
+// Rows of 128, 256 or 512 cells of one lattice with a two-shell model of at
+// most 4 + 1 species: rows of nx + 128 bytes (a multiple of 128) and random
+// words in registers (kernels with a compile-time row stride).
+bool fast_wide(int R, const smc_lattice *lats, int nsh, int sw)
 {
-    if (!IS_INT && nsh == 2 && sw == 1 && R == 1) {
-        // compile-time row strides for the benchmark row lengths (128, 256, 512 cells)
-        if (rowB == 160) return (const void *)k_sweep_fast<IS_INT, 2, 1, 160>;
-        if (rowB == 288) return (const void *)k_sweep_fast<IS_INT, 2, 1, 288>;
-        if (rowB == 544) return (const void *)k_sweep_fast<IS_INT, 2, 1, 544>;
+    const int nx = lats[0].nx;
+    return R == 1 && nsh == 2 && sw == 1 && (nx == 128 || nx == 256 || nx == 512);
+}
+
+template <bool IS_INT>
+const void *pick_fast(int nsh, int sw, int rowB, bool wide)
+{
+    if (wide) {
+        if (rowB == 256) return (const void *)k_sweep_fast<IS_INT, 2, 1, 256>;
+        if (rowB == 384) return (const void *)k_sweep_fast<IS_INT, 2, 1, 384>;
+        if (rowB == 640) return (const void *)k_sweep_fast<IS_INT, 2, 1, 640>;
     }
     if (nsh >= 3)
         return sw == 2 ? (const void *)k_sweep_fast<IS_INT, 3, 2, 0> : (const void *)k_sweep_fast<IS_INT, 3, 1, 0>;
@@ -1472,7 +1535,9 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     const Tuning tu = current_tuning();
     pl.Lx = pl.Ly = pl.Lz = 4;
     pl.G = 32;
-    pl.kernel = pick_fast<IS_INT>(pt.nsh, pt.sw, rowB, R);
+    // wide rows (fast_wide: rows of nx + 128 bytes, register words)
+    const bool wide = fast_wide(R, lats, pt.nsh, pt.sw) && rowB == lats[0].nx + 128;
+    pl.kernel = pick_fast<IS_INT>(pt.nsh, pt.sw, rowB, wide);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
@@ -1511,7 +1576,9 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     // staging latency better than 8 warps with two buffers each, and teams
     // pay a barrier per mini-step), so those are the defaults; the hooks can
     // still select the others.
-    const int force_tw = debug_fast_team(), force_nb = debug_fast_nbuf();
+    // register words (wide rows): one warp per column
+    const bool wreg = wide;
+    const int force_tw = wreg ? 1 : debug_fast_team(), force_nb = debug_fast_nbuf();
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
         if (force_nb ? nbuf != force_nb : nbuf != 1) continue;
         for (int tw = 1; tw <= 4; tw *= 2) {
@@ -1525,7 +1592,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
                 if (nwarps % tw) continue;
                 const int tpb = nwarps / tw;
                 for (int tpc_guess = 1;; tpc_guess *= 2) {
-                    const size_t wb = ((size_t)16 * tpc_guess + (size_t)512 * nkw + 15) / 16 * 16;
+                    const size_t wb = ((size_t)16 * tpc_guess + (wreg ? 0 : (size_t)512 * nkw) + 15) / 16 * 16;
                     const size_t smem = head + (size_t)tpb * team_bytes + (size_t)nwarps * wb;
                     if (smem > dyn_max) break;
                     int per_sm = 0;
@@ -1708,6 +1775,7 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     }
     int rowB = 0;
     const bool fast = fast_ok(R, lats, occ, rowB);
+    if (fast && fast_wide(R, lats, pt.nsh, pt.sw)) rowB = lats[0].nx + 128;
     Plan pl;
     st = fast ? make_fast_plan<IS_INT>(R, lats, ws, pt, rowB, pl) : make_plan<IS_INT>(R, lats, ws, pt, pl);
     if (st != SMC_OK) return st;

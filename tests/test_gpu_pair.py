@@ -132,15 +132,23 @@ def test_integer_trajectories_other_shapes(smc, dims, S, nshells):
     _run_int(smc, dims, S, nshells, 6, 0.03, seed=7, vseed=3, chunks=2, sweep0=5)
 
 
+@pytest.mark.parametrize("streaming", [False, True])
 @pytest.mark.parametrize("dims,S,nsw", [((128, 8, 8), 5, 3), ((256, 8, 8), 5, 3), ((512, 8, 8), 5, 3),
                                         ((132, 8, 8), 5, 3), ((128, 16, 16), 5, 3), ((512, 8, 8), 2, 2),
                                         ((260, 8, 12), 3, 2), ((1024, 8, 8), 5, 1)])
-def test_integer_trajectories_full_row_lengths(smc, dims, S, nsw):
-    """The persistent shared-memory sweep on rows as long as the benchmark
-    lattices' (128-1024 cells: every lane owns one to eight link cells of a
-    column, and the tile grid wraps), and on ragged rows (33 and 65 link
-    cells), bit for bit against the oracle after every sweep."""
-    _run_int(smc, dims, S, 2, nsw, 0.03, seed=7, vseed=3, chunks=nsw, sweep0=2)
+def test_integer_trajectories_full_row_lengths(smc, dims, S, nsw, streaming):
+    """The pair sweeps on rows as long as the benchmark lattices' (128-1024
+    cells: every lane owns one to eight link cells of a column, and the tile
+    grid wraps), and on ragged rows (33 and 65 link cells), bit for bit
+    against the oracle after every sweep: the default path (these lattices
+    fit the resident kernel) and the streaming kernel that sweeps lattices
+    too large for shared memory (rows of 128, 256 and 512 cells take its
+    wide-row form: rows of nx + 128 bytes, random words in registers)."""
+    smc.debug_set(smc.DBG_RESIDENT, 1 if streaming else 0)
+    try:
+        _run_int(smc, dims, S, 2, nsw, 0.03, seed=7, vseed=3, chunks=nsw, sweep0=2)
+    finally:
+        smc.debug_set(smc.DBG_RESIDENT, 0)
 
 
 def test_tuning_does_not_change_results(smc):
@@ -199,16 +207,23 @@ def test_f32_lockstep_against_oracle(smc, dims, kT):
     assert worst < 1e-6
 
 
-@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 12, 8), (6, 8, 12), (2, 2, 2), (128, 16, 16), (512, 8, 8)])
-def test_f32_sweep_kernel_equals_trace_kernel(smc, dims):
-    """The persistent sweep (shared-memory windows) and the mini-step trace
-    kernel (global reads) share the dE arithmetic: identical trajectories."""
+@pytest.mark.parametrize("streaming", [False, True])
+@pytest.mark.parametrize("dims", [(8, 8, 8), (16, 12, 8), (6, 8, 12), (2, 2, 2), (128, 16, 16), (512, 8, 8),
+                                  (256, 8, 12)])
+def test_f32_sweep_kernel_equals_trace_kernel(smc, dims, streaming):
+    """The persistent sweeps (the resident kernel, and the streaming kernel
+    with shared-memory windows) and the mini-step trace kernel (global reads)
+    share the dE arithmetic: identical trajectories."""
     V, counts, lat, occ, model, olat, omodel = _f32_setup(smc, dims)
     occ2 = occ.clone()
     kT = [0.05, 0.08]
     e_acc = torch.zeros(1, dtype=torch.float64, device=dev())
     n_acc = torch.zeros(1, dtype=torch.int64, device=dev())
-    smc.sweep(lat, model, occ, 4, 10, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    smc.debug_set(smc.DBG_RESIDENT, 1 if streaming else 0)
+    try:
+        smc.sweep(lat, model, occ, 4, 10, 2, kT, e_acc=e_acc, n_acc=n_acc)
+    finally:
+        smc.debug_set(smc.DBG_RESIDENT, 0)
     nA, _ = oracle.schedule(olat)
     for t in range(2):
         for k in range(nA):
