@@ -710,14 +710,55 @@ __device__ __forceinline__ HV<SW> operator-(const HV<SW> &a, const HV<SW> &b)
     return h;
 }
 
+// Replicated table of the wide-row kernels (two shells, one species word:
+// at most 4 + 1 species): for shell m and row A * 5 + B, eight copies of
+// the row's four plane words side by side (128 bytes), copy j read by the
+// lanes j, j + 8, ... -- the 8 lanes that a 16-byte shared load serves at
+// once then read 8 different bank groups, whatever their rows.  No bias
+// word: the counts are biased by 128 per field and turned into signed bytes
+// (c + 128) ^ 0x80 = c for dp4a with signed first operands.
+constexpr int kRTabRows = 25;
+constexpr int kRTabBytes = 2 * kRTabRows * 128;
+
+__device__ __forceinline__ uint32_t dp4a_su(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t dp4a_ss(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// dE_fix from two shells' count words biased by 128 per field and the
+// replicated table's row for (A, B) (absolute offset `row`, shell 1 at
+// + kRTabRows * 128): sum over shells of dot4(c, Q) with signed c.
+__device__ __forceinline__ int32_t dot_fixed_rtab(uint32_t h0, uint32_t h1, uint32_t row)
+{
+    const uint4 q0 = *(const uint4 *)(g_smem + row);
+    const uint4 q1 = *(const uint4 *)(g_smem + row + kRTabRows * 128);
+    const uint32_t c0 = h0 ^ 0x80808080u, c1 = h1 ^ 0x80808080u;
+    const uint32_t p0 = dp4a_su(c1, q1.x, dp4a_su(c0, q0.x, 0u));
+    const uint32_t p1 = dp4a_su(c1, q1.y, dp4a_su(c0, q0.y, 0u));
+    const uint32_t p2 = dp4a_su(c1, q1.z, dp4a_su(c0, q0.z, 0u));
+    const uint32_t p3 = dp4a_ss(c1, q1.w, dp4a_ss(c0, q0.w, 0u));
+    return (int32_t)(p0 + (p1 << 8) + (p2 << 16) + (p3 << 24));
+}
+
 // dE_fix of the trial at a = own row (0, 0), x, with ya = row-0 body + x and
 // pa = ya + s_off, partner direction dir; the species a8, b8 (x 8) and b's
-// shared-memory offset through references.
-template <int NSH, int SW, int RB>
+// shared-memory offset through references.  XB: the replicated table at qt
+// (qt includes this lane's copy offset), else the plain table at qt.
+template <int NSH, int SW, int RB, bool XB = false>
 __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rbr, uint32_t dir, uint32_t lut,
                                            uint32_t qt, uint32_t &a8, uint32_t &b8, uint32_t &pb)
 {
+    static_assert(!XB || (NSH == 2 && SW == 1), "replicated table: two shells, one species word");
     using H = HV<SW>;
+    constexpr uint32_t B12 = XB ? 0x80808080u : 0x08080808u;
     const uint32_t rb = RB ? (uint32_t)RB : rbr;
     constexpr uint32_t S11 = pslot<NSH>(1, 1), S21 = pslot<NSH>(2, 1), S12 = pslot<NSH>(1, 2), S22 = pslot<NSH>(2, 2);
     const int4 L = *(const int4 *)(g_smem + lut + dir * 16u);
@@ -727,7 +768,7 @@ __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rb
     const uint32_t ob = ya + (uint32_t)L.y;
     // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
     // trial-sublattice neighbours plus a (biased by 8 per field)
-    const H a0 = hconst<SW>(0x08080808u) + hv<SW>(a8) + hv<SW>(LD8(pa + S11 * rb));
+    const H a0 = hconst<SW>(B12) + hv<SW>(a8) + hv<SW>(LD8(pa + S11 * rb));
     const H a1 = hv<SW>(LD8(pa + S11 * rb + 1)) + hv<SW>(LD8(pa + S21 * rb)) + hv<SW>(LD8(pa + S21 * rb + 1));
     const H a2 = hv<SW>(LD8(pa + S12 * rb)) + hv<SW>(LD8(pa + S12 * rb + 1)) + hv<SW>(LD8(pa + S22 * rb));
     const H a3 = hv<SW>(LD8(pa + S22 * rb + 1));
@@ -736,37 +777,41 @@ __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rb
     const H b2 = hv<SW>(LD8(ob + 3 * rb + 1)) + hv<SW>(LD8(ob + 4 * rb)) + hv<SW>(LD8(ob + 4 * rb + 1));
     const H h0 = (a0 + a1) + (a2 + a3) - ((b0 + b1) + b2);
     // shell 2: a's 6 trial-sublattice neighbours, b's 6 partner-sublattice ones
-    const H c0 = hconst<SW>(0x08080808u) + hv<SW>(LD8(ya + 4 * rb - 1)) + hv<SW>(LD8(ya + 4 * rb + 1));
+    const H c0 = hconst<SW>(B12) + hv<SW>(LD8(ya + 4 * rb - 1)) + hv<SW>(LD8(ya + 4 * rb + 1));
     const H c1 = hv<SW>(LD8(ya + 3 * rb)) + hv<SW>(LD8(ya + 5 * rb)) + hv<SW>(LD8(ya + rb));
     const H c2 = hv<SW>(LD8(ya + 7 * rb));
     const H d0 = hv<SW>(LD8(pb - 1)) + hv<SW>(LD8(pb + 1)) + hv<SW>(LD8(pb - rb));
     const H d1 = hv<SW>(LD8(pb + rb)) + hv<SW>(LD8(pb - (uint32_t)L.z)) + hv<SW>(LD8(pb + (uint32_t)L.w));
     const H h1 = ((c0 + c1) + c2) - (d0 + d1);
-    uint32_t Hw[NSH][SW];
+    if constexpr (XB) {
+        return dot_fixed_rtab(h0.w[0], h1.w[0], qt + (a8 * 5u + b8) * 16u);
+    } else {
+        uint32_t Hw[NSH][SW];
 #pragma unroll
-    for (int w = 0; w < SW; ++w) {
-        Hw[0][w] = h0.w[w];
-        Hw[1][w] = h1.w[w];
-    }
-    if constexpr (NSH >= 3) {
-        // shell 3: a's 12 trial-sublattice neighbours, b's 12 partner-sublattice
-        // ones (biased by 16 per field)
-        const H e0 = hconst<SW>(0x10101010u) + hv<SW>(LD8(ya)) + hv<SW>(LD8(ya + 2 * rb));
-        const H e1 = hv<SW>(LD8(ya + 6 * rb)) + hv<SW>(LD8(ya + 8 * rb)) + hv<SW>(LD8(ya + 3 * rb - 1));
-        const H e2 = hv<SW>(LD8(ya + 3 * rb + 1)) + hv<SW>(LD8(ya + 5 * rb - 1)) + hv<SW>(LD8(ya + 5 * rb + 1));
-        const H e3 = hv<SW>(LD8(ya + rb - 1)) + hv<SW>(LD8(ya + rb + 1)) + hv<SW>(LD8(ya + 7 * rb - 1));
-        const H e4 = hv<SW>(LD8(ya + 7 * rb + 1));
-        const H f0 = hv<SW>(LD8(pb - 5 * rb)) + hv<SW>(LD8(pb - 3 * rb)) + hv<SW>(LD8(pb + 3 * rb));
-        const H f1 = hv<SW>(LD8(pb + 5 * rb)) + hv<SW>(LD8(pb - rb - 1)) + hv<SW>(LD8(pb - rb + 1));
-        const H f2 = hv<SW>(LD8(pb + rb - 1)) + hv<SW>(LD8(pb + rb + 1)) + hv<SW>(LD8(pb - 4 * rb - 1));
-        const H f3 = hv<SW>(LD8(pb - 4 * rb + 1)) + hv<SW>(LD8(pb + 4 * rb - 1)) + hv<SW>(LD8(pb + 4 * rb + 1));
-        const H h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
+        for (int w = 0; w < SW; ++w) {
+            Hw[0][w] = h0.w[w];
+            Hw[1][w] = h1.w[w];
+        }
+        if constexpr (NSH >= 3) {
+            // shell 3: a's 12 trial-sublattice neighbours, b's 12
+            // partner-sublattice ones (biased by 16 per field)
+            const H e0 = hconst<SW>(0x10101010u) + hv<SW>(LD8(ya)) + hv<SW>(LD8(ya + 2 * rb));
+            const H e1 = hv<SW>(LD8(ya + 6 * rb)) + hv<SW>(LD8(ya + 8 * rb)) + hv<SW>(LD8(ya + 3 * rb - 1));
+            const H e2 = hv<SW>(LD8(ya + 3 * rb + 1)) + hv<SW>(LD8(ya + 5 * rb - 1)) + hv<SW>(LD8(ya + 5 * rb + 1));
+            const H e3 = hv<SW>(LD8(ya + rb - 1)) + hv<SW>(LD8(ya + rb + 1)) + hv<SW>(LD8(ya + 7 * rb - 1));
+            const H e4 = hv<SW>(LD8(ya + 7 * rb + 1));
+            const H f0 = hv<SW>(LD8(pb - 5 * rb)) + hv<SW>(LD8(pb - 3 * rb)) + hv<SW>(LD8(pb + 3 * rb));
+            const H f1 = hv<SW>(LD8(pb + 5 * rb)) + hv<SW>(LD8(pb - rb - 1)) + hv<SW>(LD8(pb - rb + 1));
+            const H f2 = hv<SW>(LD8(pb + rb - 1)) + hv<SW>(LD8(pb + rb + 1)) + hv<SW>(LD8(pb - 4 * rb - 1));
+            const H f3 = hv<SW>(LD8(pb - 4 * rb + 1)) + hv<SW>(LD8(pb + 4 * rb - 1)) + hv<SW>(LD8(pb + 4 * rb + 1));
+            const H h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
 #pragma unroll
-        for (int w = 0; w < SW; ++w) Hw[2][w] = h2.w[w];
+            for (int w = 0; w < SW; ++w) Hw[2][w] = h2.w[w];
+        }
+        constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
+        const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
+        return dot_fixed<NSH, SW>(Hw, row);
     }
-    constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
-    const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
-    return dot_fixed<NSH, SW>(Hw, row);
 }
 
 // Team synchronisation: the tw warps that share a column meet at named
@@ -798,7 +843,7 @@ __device__ __forceinline__ bool team_and(int tw, int tb, bool p)
 // u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).  The random
 // words come from the warp's shared-memory words, or from wreg[u] when
 // wreg is given (the words of this mini-step, held in registers).
-template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD>
+template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD, bool XB = false>
 __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body, int soff, uint32_t rbr,
                                             uint32_t wsm, int k0, int nk, int ib, int is, int NLx, int nx, int dx,
                                             int lane, float cx, int2 ti, uint32_t lut, uint32_t qt, long long &accE,
@@ -817,7 +862,7 @@ __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body,
             ya[u] = body + (uint32_t)x;
             const uint32_t w =
                 wreg ? wreg[u] : *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
-            dE[u] = fast_dE<NSH, SW, RB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
+            dE[u] = fast_dE<NSH, SW, RB, XB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
             acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
             // b's store address wraps along x (the load may read a halo copy)
             const int xb = x + soff + (int)(w >> 31);
@@ -861,10 +906,22 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     const uint32_t rb = RB ? (uint32_t)RB : (uint32_t)P.rowB;
     const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     // fixed-point table and the per-direction offsets of b and its rows
-    const uint32_t qt = 0u;
-    const int qwords = kQRows * P.qrow;
-    for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
-    const uint32_t lut = (uint32_t)qwords * 4u;
+    uint32_t qt = 0u, lut;
+    if constexpr (WREG) {
+        // replicated table: word i of (shell m, row A * 5 + B, copy j) from
+        // plane word i of shell m in row A * 8 + B of the plain table
+        for (int e = tid; e < 2 * kRTabRows * 8 * 4; e += blockDim.x) {
+            const int i = e & 3, row = (e >> 5) % kRTabRows, m = (e >> 5) / kRTabRows;
+            const int A = row / 5, B = row % 5;
+            ((uint32_t *)g_smem)[e] = P.qtab[(A * 8 + B) * P.qrow + m * 4 + i];
+        }
+        qt = (uint32_t)(lane & 7) * 16u;
+        lut = (uint32_t)kRTabBytes;
+    } else {
+        const int qwords = kQRows * P.qrow;
+        for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+        lut = (uint32_t)qwords * 4u;
+    }
     if (tid < 8) {
         const int kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
         int4 e;
@@ -1032,8 +1089,8 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                         wr[k][1] = wr[k][2];
                         wr[k][2] = wr[k][3];
                     }
-                    fast_trials<IS_INT, NSH, SW, RB, NKW, false>(P, body, q.soff, rb, wsm, 0, NKW, ib, is, NLx, nx, dx,
-                                                                 lane, cx, ti, lut, qt, accE, accN, wv);
+                    fast_trials<IS_INT, NSH, SW, RB, NKW, false, true>(P, body, q.soff, rb, wsm, 0, NKW, ib, is, NLx,
+                                                                       nx, dx, lane, cx, ti, lut, qt, accE, accN, wv);
                 } else if (NLx == is * nkw && (nkw & 3) == 0) {
 #pragma unroll 1
                     for (int kk = 0; kk < nkw; kk += 4)
@@ -1557,7 +1614,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     pl.ntiles = 0;
     for (int r = 0; r < R; ++r)
         pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
-    const size_t head = (size_t)kQRows * pt.rw * 4 + 128;
+    const size_t head = (wide ? (size_t)kRTabBytes : (size_t)kQRows * pt.rw * 4) + 128;
     const int nrows = pt.nsh >= 3 ? 25 : 21;
     // A team of tw warps shares a column (two row buffers per team); every
     // warp keeps its accumulator slots and Philox words.  Total warps: all
