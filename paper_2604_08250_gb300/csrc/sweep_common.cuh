@@ -144,11 +144,12 @@ static __device__ bool wait_tile_warp(const SweepParams &P, const RepDesc &D, in
         ntz = ntz < 0 ? ntz + D.NTz : (ntz >= D.NTz ? ntz - D.NTz : ntz);
         fp = P.flags + D.tile0 + ntz * D.NTy + nty;
     }
-    const uint64_t t0 = global_ns();
+    uint64_t t0 = 0;  // read at the first miss: most waits end at the first look
     unsigned nap = 32;
     for (;;) {
         const bool ok = (fp == nullptr) || ld_acquire_u32(fp) >= need;
         if (__all_sync(0xffffffffu, ok)) return true;
+        if (t0 == 0) t0 = global_ns();
         int stop = 0;
         if (lane == 0) {
             if (ld_volatile_i32(P.abort_flag)) {

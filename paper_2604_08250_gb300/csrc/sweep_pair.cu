@@ -595,6 +595,30 @@ __device__ __forceinline__ FastGeo fast_geo(const SweepParams &P, int t, int g, 
     return q;
 }
 
+// The same for the wide-row kernels: one lattice, one-column tiles, the
+// tile's coordinates (ty, tz) tracked by the caller (no divisions).
+__device__ __forceinline__ FastGeo fast_geo_wide(int t, int g, int ty, int tz)
+{
+    FastGeo q;
+    q.r = 0;
+    q.ty = ty;
+    q.tz = tz;
+    q.nj = 1;
+    q.ncols = 1;
+    q.j = ty;
+    q.l = tz;
+    q.dy = g & 3;
+    q.dz = (g >> 2) & 3;
+    q.sub = g >> 4;
+    q.soff = q.sub == 0 ? -1 : 0;
+    q.y0 = 4 * q.j + q.dy;
+    q.z0 = 4 * q.l + q.dz;
+    q.gstep = (uint32_t)(t * 32 + g);
+    const uint32_t lagv = (g & 3) ? 2u : 1u;  // groups with dy >= 1: lag 2
+    q.need = q.gstep + 1 >= lagv ? q.gstep + 1 - lagv : 0;
+    return q;
+}
+
 // Stages the rows of column geometry q into the buffer at g_smem offset buf.
 // Rows of a multiple of 16 bytes, 16-byte aligned: mode 0, one cp.async.bulk
 // per row, completing on mbarrier `mbar` (absolute shared address); mode 1,
@@ -935,13 +959,14 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     const uint32_t mbar0 = tbase, buf0 = tbase + 16u, bufsz = (uint32_t)NROWS * rb;
     const int nbuf = P.nbuf;  // 1: no prefetch, the next column reuses the buffer
     const uint32_t wbase = lut + 128u + (uint32_t)tpb * (uint32_t)P.team_bytes + (uint32_t)warp * (uint32_t)P.warp_bytes;
-    double *slot_e = (double *)(g_smem + wbase);
-    long long *slot_n = (long long *)(slot_e + P.tpc);
+    // per-tile sums of dE_fix and accepted counts: exact integers
+    long long *slot_e = (long long *)(g_smem + wbase);
+    long long *slot_n = slot_e + P.tpc;
     const uint32_t wsm = wbase + (uint32_t)P.tpc * 16u;
     const int is = 32 * tw, ib = lane + 32 * wi;
     const int nkw = (P.maxNLx + is - 1) / is;
     for (int i = lane; i < P.tpc; i += 32) {
-        slot_e[i] = 0.0;
+        slot_e[i] = 0;
         slot_n[i] = 0;
     }
     if (leader && lane == 0) {
@@ -955,10 +980,16 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     // per buffer b: bit b of par = parity of its barrier's next phase; bit b
     // of inflight (leader) = copies issued and not yet waited for
     uint32_t par = 0u, inflight = 0u;
+    // wide kernels: per-lane sums over the whole launch (exact integers), and
+    // the tile coordinates stepped by NT tiles at a time
+    long long accE = 0, accN = 0;
+    const int NTy0 = P.rep[0].NTy;
+    const int dty = WREG ? NT % NTy0 : 0, dtz = WREG ? NT / NTy0 : 0;
+    const int ty0 = WREG ? gteam % NTy0 : 0, tz0 = WREG ? gteam / NTy0 : 0;
     if (gteam < P.ntiles) {
         int t = 0, g = 0, tile = gteam, c = 0, nb = 0, slotk = 0;
-        long long accE = 0, accN = 0;
-        FastGeo q = fast_geo(P, t, g, tile, c);
+        int cty = ty0, ctz = tz0;
+        FastGeo q = WREG ? fast_geo_wide(t, g, cty, ctz) : fast_geo(P, t, g, tile, c);
         bool ok = true;
         if (leader) {
             ok = wait_tile_warp(P, P.rep[q.r], q.ty, q.tz, q.need, lane);
@@ -973,6 +1004,11 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
             // the next item
             int t2 = t, g2 = g, tile2 = tile, c2 = c + 1, slot2 = slotk;
+            int ty2 = cty + dty, tz2 = ctz + dtz;
+            if (ty2 >= NTy0) {
+                ty2 -= NTy0;
+                ++tz2;
+            }
             if (c2 >= q.ncols) {
                 c2 = 0;
                 tile2 += NT;
@@ -980,6 +1016,8 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 if (tile2 >= P.ntiles) {
                     tile2 = gteam;
                     slot2 = 0;
+                    ty2 = ty0;
+                    tz2 = tz0;
                     if (++g2 == P.G) {
                         g2 = 0;
                         ++t2;
@@ -988,7 +1026,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             }
             const bool has_next = t2 < P.nsweeps;
             FastGeo q2;
-            if (has_next) q2 = fast_geo(P, t2, g2, tile2, c2);
+            if (has_next) q2 = WREG ? fast_geo_wide(t2, g2, ty2, tz2) : fast_geo(P, t2, g2, tile2, c2);
             const bool next_vec = has_next && P.rep[q2.r].vec != 0;
             auto can_prefetch = [&]() -> bool {
                 if (!next_vec || nbuf < 2) return false;
@@ -1159,12 +1197,14 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             // every thread's row stores, then one release by the leader's lane 0
             // (the barrier orders the team's stores before it)
             team_sync(tw, tb);
-            if (c + 1 >= q.ncols) {
+            if (c + 1 >= q.ncols && WREG) {
+                if (leader && lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, q.gstep + 1);
+            } else if (c + 1 >= q.ncols) {
                 // the tile's last column: accumulate in fixed order and publish
                 const long long e_w = warp_sum<long long>(accE);
                 const long long n_w = warp_sum<long long>(accN);
                 if (lane == 0) {
-                    slot_e[slotk] += (double)e_w;
+                    slot_e[slotk] += e_w;
                     slot_n[slotk] += n_w;
                 }
                 accE = 0;
@@ -1191,6 +1231,8 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             slotk = slot2;
             q = q2;
             nb = nbn;
+            cty = ty2;
+            ctz = tz2;
         }
     }
     if (aborted) {
@@ -1201,12 +1243,20 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 if (inflight & (1u << b)) mbar_wait(P, smem0 + mbar0 + 8u * (uint32_t)b, (par >> b) & 1u);
         return;
     }
-    // ---- per-tile partial sums (one per warp of the team); the last warp to
-    // finish reduces them in order ----
-    if (lane == 0) {
+    // ---- per-tile partial sums (one per warp of the team; wide kernels: one
+    // per warp, as int64); the last warp to finish reduces them, all its
+    // lanes at once: the partial sums are integers (dE_fix, counts), so their
+    // int64 sum is exact in any order ----
+    if constexpr (WREG) {
+        const long long e_w = warp_sum<long long>(accE), n_w = warp_sum<long long>(accN);
+        if (lane == 0 && gteam < P.ntiles) {
+            ((long long *)P.part_e)[gteam] = e_w;
+            P.part_n[gteam] = n_w;
+        }
+    } else if (lane == 0) {
         int k = 0;
         for (int tl = gteam; tl < P.ntiles; tl += NT, ++k) {
-            P.part_e[(size_t)tl * tw + wi] = slot_e[k];
+            P.part_e[(size_t)tl * tw + wi] = (double)slot_e[k];
             P.part_n[(size_t)tl * tw + wi] = slot_n[k];
         }
     }
@@ -1217,17 +1267,22 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     last = __shfl_sync(0xffffffffu, last, 0);
     if (!last) return;
     __threadfence();
-    for (int r = lane; r < P.R; r += 32) {
+    for (int r = 0; r < P.R; ++r) {
         const RepDesc &RD = P.rep[r];
-        double se = 0.0;
-        long long sn = 0;
-        const int nt = RD.NTy * RD.NTz;
-        for (int k = 0; k < nt * tw; ++k) {
-            se += __ldcg(P.part_e + (size_t)RD.tile0 * tw + k);
-            sn += __ldcg(P.part_n + (size_t)RD.tile0 * tw + k);
+        const int np = RD.NTy * RD.NTz * tw;
+        const double *pe = P.part_e + (size_t)RD.tile0 * tw;
+        const long long *pn = P.part_n + (size_t)RD.tile0 * tw;
+        long long se = 0, sn = 0;
+        for (int k = lane; k < np; k += 32) {
+            se += WREG ? __ldcg((const long long *)pe + k) : (long long)__ldcg(pe + k);
+            sn += __ldcg(pn + k);
         }
-        if (RD.e_acc) *RD.e_acc += se * P.escale;
-        if (RD.n_acc) *RD.n_acc += sn;
+        se = warp_sum<long long>(se);
+        sn = warp_sum<long long>(sn);
+        if (lane == 0) {
+            if (RD.e_acc) *RD.e_acc += (double)se * P.escale;
+            if (RD.n_acc) *RD.n_acc += sn;
+        }
     }
 }
 
@@ -1528,12 +1583,14 @@ smc_status make_plan(int R, const smc_lattice *lats, Workspace *ws, const PairTa
 }
 
 // Rows of 128, 256 or 512 cells of one lattice with a two-shell model of at
-// most 4 + 1 species: rows of nx + 128 bytes (a multiple of 128) and random
-// words in registers (kernels with a compile-time row stride).
+// most 4 + 1 species, one-column tiles: rows of nx + 128 bytes (a multiple of
+// 128) and random words in registers (kernels with a compile-time row stride).
 bool fast_wide(int R, const smc_lattice *lats, int nsh, int sw)
 {
     const int nx = lats[0].nx;
-    return R == 1 && nsh == 2 && sw == 1 && (nx == 128 || nx == 256 || nx == 512);
+    const Tuning tu = current_tuning();
+    return R == 1 && nsh == 2 && sw == 1 && (nx == 128 || nx == 256 || nx == 512) && tu.tile_y <= 1 &&
+           tu.tile_z <= 1;
 }
 
 template <bool IS_INT>
