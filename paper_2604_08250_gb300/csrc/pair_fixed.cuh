@@ -123,6 +123,55 @@ __device__ __forceinline__ bool accept_fixed(int32_t dE, uint32_t r, float cx, c
     }
 }
 
+// Replicated table (two shells, one species word: at most 4 + 1 species): for shell m and row A * 5 + B, eight copies of
+// the row's four plane words side by side (128 bytes), copy j read by the
+// lanes j, j + 8, ... -- the 8 lanes that a 16-byte shared load serves at
+// once then read 8 different bank groups, whatever their rows.  No bias
+// word: the counts are biased by 128 per field and turned into signed bytes
+// (c + 128) ^ 0x80 = c for dp4a with signed first operands.
+constexpr int kRTabRows = 25;
+constexpr int kRTabBytes = 2 * kRTabRows * 128;
+
+__device__ __forceinline__ uint32_t dp4a_su(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ uint32_t dp4a_ss(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("dp4a.s32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+// dE_fix from two shells' count words biased by 128 per field and the
+// replicated table's row for (A, B) (absolute offset `row`, shell 1 at
+// + kRTabRows * 128): sum over shells of dot4(c, Q) with signed c.
+__device__ __forceinline__ int32_t dot_fixed_rtab(uint32_t h0, uint32_t h1, uint32_t row)
+{
+    const uint4 q0 = *(const uint4 *)(g_smem + row);
+    const uint4 q1 = *(const uint4 *)(g_smem + row + kRTabRows * 128);
+    const uint32_t c0 = h0 ^ 0x80808080u, c1 = h1 ^ 0x80808080u;
+    const uint32_t p0 = dp4a_su(c1, q1.x, dp4a_su(c0, q0.x, 0u));
+    const uint32_t p1 = dp4a_su(c1, q1.y, dp4a_su(c0, q0.y, 0u));
+    const uint32_t p2 = dp4a_su(c1, q1.z, dp4a_su(c0, q0.z, 0u));
+    const uint32_t p3 = dp4a_ss(c1, q1.w, dp4a_ss(c0, q0.w, 0u));
+    return (int32_t)(p0 + (p1 << 8) + (p2 << 16) + (p3 << 24));
+}
+
+// Writes the replicated table at shared offset 0: word i of (shell m, row
+// A * 5 + B, copy j) is plane word i of shell m in row A * 8 + B of the
+// plain table (qrow words per row).
+__device__ __forceinline__ void fill_rtab(const uint32_t *qtab, int qrow, int tid, int nthr)
+{
+    for (int e = tid; e < 2 * kRTabRows * 8 * 4; e += nthr) {
+        const int i = e & 3, row = (e >> 5) % kRTabRows, m = (e >> 5) / kRTabRows;
+        const int A = row / 5, B = row % 5;
+        ((uint32_t *)g_smem)[e] = qtab[(A * 8 + B) * qrow + m * 4 + i];
+    }
+}
+
 // Host: fixed-point table of a pair model (rows A * 8 + B, A, B < 8; rows of
 // species >= S are zero).  Returns false if a coefficient is not finite.
 struct PairTable {

@@ -87,11 +87,14 @@ __device__ __forceinline__ void named_arrive(int id, int n)
 
 // dE_fix of the trial at a (ya = shared offset of a, own row) with pa = the
 // partner row (y0 + s_off, z0 + s_off) at x + s_off; rows are rb apart in y
-// and RZ apart in z on both sublattices.
-template <int NSH, int SW>
+// and RZ apart in z on both sublattices.  XB: the replicated table at shared
+// offset 0 (qt = this lane's copy offset), counts biased by 128 per field;
+// else the plain table.
+template <int NSH, int SW, bool XB = false>
 __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb, uint32_t RZ, uint32_t w,
-                                          uint32_t &a8, uint32_t &b8, uint32_t &pb)
+                                          uint32_t qt, uint32_t &a8, uint32_t &b8, uint32_t &pb)
 {
+    static_assert(!XB || (NSH == 2 && SW == 1), "replicated table: two shells, one species word");
     // partner direction = w >> 29 = (kx, ky, kz): b = pa + ky rb + kz RZ + kx,
     // and b's own-sublattice neighbours start (ky - 1, kz - 1, kx - 1) from a
     const uint32_t offb = ((w >> 30) & 1u) * rb + ((w >> 29) & 1u) * RZ + (w >> 31);
@@ -102,7 +105,7 @@ __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb,
 #pragma unroll
     for (int m = 0; m < NSH; ++m)
 #pragma unroll
-        for (int w = 0; w < SW; ++w) H[m][w] = m < 2 ? 0x08080808u : 0x10101010u;
+        for (int w = 0; w < SW; ++w) H[m][w] = XB ? 0x80808080u : (m < 2 ? 0x08080808u : 0x10101010u);
     hadd<SW>(H[0], a8);
     hsub<SW>(H[0], b8);
     hadd<SW>(H[0], RD8(pa));
@@ -160,8 +163,12 @@ __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb,
         hsub<SW>(H[2], RD8(pb + RZ - 1));
         hsub<SW>(H[2], RD8(pb + RZ + 1));
     }
-    constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
-    return dot_fixed<NSH, SW>(H, (const uint32_t *)(g_smem + (8u * a8 + b8) * half_row));
+    if constexpr (XB) {
+        return dot_fixed_rtab(H[0][0], H[1][0], qt + (a8 * 5u + b8) * 16u);
+    } else {
+        constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
+        return dot_fixed<NSH, SW>(H, (const uint32_t *)(g_smem + (8u * a8 + b8) * half_row));
+    }
 }
 
 // Shared-memory body offset of window row (s, y, z) of a block whose window
@@ -342,10 +349,12 @@ __device__ bool res_fetch_versions(const SweepParams &P, const unsigned long lon
 
 // RB, WY: the row pitch and window rows per y of every block, when known at
 // compile time (0: read from the descriptor), so that the trial's row offsets
-// are immediates.
+// are immediates.  Those kernels (two shells, one species word) also take
+// the replicated pair table (res_xb_table).
 template <bool IS_INT, int NSH, int SW, int RB, int WY>
 __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant__ SweepParams P)
 {
+    constexpr bool XB = RB != 0 && WY != 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     // compute warps, then P.rxw exchange warps, then the release warp
     const int nxw = P.rxw, nc = nwarp - nxw - 1, nbar = (nc + nxw) * 32;
@@ -365,12 +374,16 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
     __shared__ unsigned s_cnt;        // (compute warp, group) pairs finished and published
     // shared memory: [table][rows][lists][Philox words per compute warp]
     const int qwords = kQRows * P.qrow;
-    const uint32_t rows = (uint32_t)qwords * 4u;
+    const uint32_t rows = XB ? (uint32_t)kRTabBytes : (uint32_t)qwords * 4u;
     const int nslots = 2 * Wy * Wz;
     const uint32_t lists = rows + (uint32_t)nslots * rb;
     const int nk = (NLx + 31) >> 5;
     const uint32_t wsm0 = lists + (uint32_t)P.rblob * 4u;
-    for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+    if constexpr (XB)
+        fill_rtab(P.qtab, P.qrow, tid, blockDim.x);
+    else
+        for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+    const uint32_t qt = (uint32_t)(lane & 7) * 16u;
     const uint32_t *gl = P.rlists + d[8];
     uint32_t *L = (uint32_t *)(g_smem + lists);
     for (int i = tid; i < d[9]; i += blockDim.x) L[i] = gl[i];
@@ -526,7 +539,8 @@ __global__ void __launch_bounds__(416, 1) k_sweep_resident(const __grid_constant
                 auto trial = [&](int x, uint32_t w) {
                     uint32_t a8, b8, pb;
                     const uint32_t ya = ownb + (uint32_t)x;
-                    const int32_t dE = res_dE<NSH, SW>(ya, parb + (uint32_t)(x + soff), rb, RZ, w, a8, b8, pb);
+                    const int32_t dE =
+                        res_dE<NSH, SW, XB>(ya, parb + (uint32_t)(x + soff), rb, RZ, w, qt, a8, b8, pb);
                     if (accept_fixed<IS_INT>(dE, w & kRMask, cx, P.tab, ti)) {
                         int xb = x + soff + (int)(w >> 31);
                         const int wrap = xb < 0 ? nx : (xb >= nx ? -nx : 0);
@@ -1001,18 +1015,34 @@ smc_status build_res_multi(int R, const smc_lattice *lats, const PairTable &pt, 
     cudaFuncAttributes fa;
     cudaError_t e;
     if (fixed) {
+        // the compile-time-pitch kernel keeps the replicated table (larger
+        // than the plain one): taken when every block still fits as before
+        const size_t plain = (size_t)kQRows * pt.rw * 4;
+        const size_t extra = (size_t)kRTabBytes > plain ? (size_t)kRTabBytes - plain : 0;
         e = cudaFuncGetAttributes(&fa, fixed);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
-        e = cudaFuncSetAttribute(fixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(ws->smem_optin - fa.sharedSizeBytes));
+        const size_t fdyn = ws->smem_optin - fa.sharedSizeBytes;
+        e = cudaFuncSetAttribute(fixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fdyn);
         if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+        // (largest CTA: any block with the largest list blob of a wave)
+        auto pad = [](int blob) { return ((size_t)blob * 4 + 15) / 16 * 16; };
+        size_t base = 0;
+        int maxblob = 0, need_sm = 0;
+        for (const auto &rp : mp.rp) {
+            base = std::max(base, rp.smem + extra - pad(rp.blob));
+            maxblob = std::max(maxblob, rp.blob);
+            need_sm = std::max(need_sm, rp.per_sm);
+        }
+        const size_t smax = base + pad(maxblob);
         int per_sm = 0;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed, (kResCols + mp.rp[0].nxw + 1) * 32,
-                                                          mp.rp[0].smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fixed, (kResCols + mp.rp[0].nxw + 1) * 32, smax);
         if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
-        if (per_sm >= 1) {
+        if (smax <= fdyn && per_sm >= need_sm) {
             mp.kernel = fixed;
-            for (auto &rp : mp.rp) rp.per_sm = std::min(rp.per_sm, per_sm);
+            for (auto &rp : mp.rp) {
+                rp.smem += extra;
+                rp.per_sm = std::min(rp.per_sm, per_sm);
+            }
         }
     }
     e = cudaFuncGetAttributes(&fa, mp.kernel);
