@@ -84,6 +84,46 @@ __device__ __forceinline__ void hsub(uint32_t (&h)[SW], uint32_t v8)
     if constexpr (SW == 2) h[1] -= nib8hi(v8);
 }
 
+// Histogram words of one neighbour (SW words of four 8-bit fields), summed
+// as values so that the counts of a shell form short add trees instead of
+// one chain of dependent adds.
+template <int SW>
+struct HV {
+    uint32_t w[SW];
+};
+template <int SW>
+__device__ __forceinline__ HV<SW> hv(uint32_t v8)
+{
+    HV<SW> h;
+    h.w[0] = nib8(v8);
+    if constexpr (SW == 2) h.w[1] = nib8hi(v8);
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> hconst(uint32_t c)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = c;
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> operator+(const HV<SW> &a, const HV<SW> &b)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] + b.w[w];
+    return h;
+}
+template <int SW>
+__device__ __forceinline__ HV<SW> operator-(const HV<SW> &a, const HV<SW> &b)
+{
+    HV<SW> h;
+#pragma unroll
+    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] - b.w[w];
+    return h;
+}
+
 // dE_fix of the histogram words H[m][w] against table row `row` (smem or
 // global, 16-byte aligned).
 template <int NSH, int SW>

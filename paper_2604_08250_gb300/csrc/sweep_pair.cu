@@ -694,46 +694,6 @@ __device__ __forceinline__ void fast_stage(const RepDesc &RD, const FastGeo &q, 
     }
 }
 
-// Histogram words of one neighbour (SW words of four 8-bit fields), summed
-// as values so that the counts of a shell form short add trees instead of
-// one chain of dependent adds.
-template <int SW>
-struct HV {
-    uint32_t w[SW];
-};
-template <int SW>
-__device__ __forceinline__ HV<SW> hv(uint32_t v8)
-{
-    HV<SW> h;
-    h.w[0] = nib8(v8);
-    if constexpr (SW == 2) h.w[1] = nib8hi(v8);
-    return h;
-}
-template <int SW>
-__device__ __forceinline__ HV<SW> hconst(uint32_t c)
-{
-    HV<SW> h;
-#pragma unroll
-    for (int w = 0; w < SW; ++w) h.w[w] = c;
-    return h;
-}
-template <int SW>
-__device__ __forceinline__ HV<SW> operator+(const HV<SW> &a, const HV<SW> &b)
-{
-    HV<SW> h;
-#pragma unroll
-    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] + b.w[w];
-    return h;
-}
-template <int SW>
-__device__ __forceinline__ HV<SW> operator-(const HV<SW> &a, const HV<SW> &b)
-{
-    HV<SW> h;
-#pragma unroll
-    for (int w = 0; w < SW; ++w) h.w[w] = a.w[w] - b.w[w];
-    return h;
-}
-
 // dE_fix of the trial at a = own row (0, 0), x, with ya = row-0 body + x and
 // pa = ya + s_off, partner direction dir; the species a8, b8 (x 8) and b's
 // shared-memory offset through references.  XB: the replicated table at qt

@@ -101,67 +101,47 @@ __device__ __forceinline__ int32_t res_dE(uint32_t ya, uint32_t pa, uint32_t rb,
     a8 = RD8(ya);
     pb = pa + offb;
     b8 = RD8(pb);
+    using HW = HV<SW>;
+    constexpr uint32_t B12 = XB ? 0x80808080u : 0x08080808u;
+    const uint32_t ob = ya + offb - rb - RZ - 1u;
+    // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
+    // trial-sublattice neighbours plus a (short add trees)
+    const HW a0 = hconst<SW>(B12) + hv<SW>(a8) + hv<SW>(RD8(pa));
+    const HW a1 = hv<SW>(RD8(pa + 1)) + hv<SW>(RD8(pa + rb)) + hv<SW>(RD8(pa + rb + 1));
+    const HW a2 = hv<SW>(RD8(pa + RZ)) + hv<SW>(RD8(pa + RZ + 1)) + hv<SW>(RD8(pa + RZ + rb));
+    const HW a3 = hv<SW>(RD8(pa + RZ + rb + 1));
+    const HW b0 = hv<SW>(b8) + hv<SW>(RD8(ob)) + hv<SW>(RD8(ob + 1));
+    const HW b1 = hv<SW>(RD8(ob + rb)) + hv<SW>(RD8(ob + rb + 1)) + hv<SW>(RD8(ob + RZ));
+    const HW b2 = hv<SW>(RD8(ob + RZ + 1)) + hv<SW>(RD8(ob + RZ + rb)) + hv<SW>(RD8(ob + RZ + rb + 1));
+    const HW h0 = (a0 + a1) + (a2 + a3) - ((b0 + b1) + b2);
+    // shell 2: a's 6 trial-sublattice neighbours, b's 6 partner-sublattice ones
+    const HW c0 = hconst<SW>(B12) + hv<SW>(RD8(ya - 1)) + hv<SW>(RD8(ya + 1));
+    const HW c1 = hv<SW>(RD8(ya - rb)) + hv<SW>(RD8(ya + rb)) + hv<SW>(RD8(ya - RZ));
+    const HW c2 = hv<SW>(RD8(ya + RZ));
+    const HW d0 = hv<SW>(RD8(pb - 1)) + hv<SW>(RD8(pb + 1)) + hv<SW>(RD8(pb - rb));
+    const HW d1 = hv<SW>(RD8(pb + rb)) + hv<SW>(RD8(pb - RZ)) + hv<SW>(RD8(pb + RZ));
+    const HW h1 = ((c0 + c1) + c2) - (d0 + d1);
     uint32_t H[NSH][SW];
 #pragma unroll
-    for (int m = 0; m < NSH; ++m)
-#pragma unroll
-        for (int w = 0; w < SW; ++w) H[m][w] = XB ? 0x80808080u : (m < 2 ? 0x08080808u : 0x10101010u);
-    hadd<SW>(H[0], a8);
-    hsub<SW>(H[0], b8);
-    hadd<SW>(H[0], RD8(pa));
-    hadd<SW>(H[0], RD8(pa + 1));
-    hadd<SW>(H[0], RD8(pa + rb));
-    hadd<SW>(H[0], RD8(pa + rb + 1));
-    hadd<SW>(H[0], RD8(pa + RZ));
-    hadd<SW>(H[0], RD8(pa + RZ + 1));
-    hadd<SW>(H[0], RD8(pa + RZ + rb));
-    hadd<SW>(H[0], RD8(pa + RZ + rb + 1));
-    const uint32_t ob = ya + offb - rb - RZ - 1u;
-    hsub<SW>(H[0], RD8(ob));
-    hsub<SW>(H[0], RD8(ob + 1));
-    hsub<SW>(H[0], RD8(ob + rb));
-    hsub<SW>(H[0], RD8(ob + rb + 1));
-    hsub<SW>(H[0], RD8(ob + RZ));
-    hsub<SW>(H[0], RD8(ob + RZ + 1));
-    hsub<SW>(H[0], RD8(ob + RZ + rb));
-    hsub<SW>(H[0], RD8(ob + RZ + rb + 1));
-    hadd<SW>(H[1], RD8(ya - 1));
-    hadd<SW>(H[1], RD8(ya + 1));
-    hadd<SW>(H[1], RD8(ya - rb));
-    hadd<SW>(H[1], RD8(ya + rb));
-    hadd<SW>(H[1], RD8(ya - RZ));
-    hadd<SW>(H[1], RD8(ya + RZ));
-    hsub<SW>(H[1], RD8(pb - 1));
-    hsub<SW>(H[1], RD8(pb + 1));
-    hsub<SW>(H[1], RD8(pb - rb));
-    hsub<SW>(H[1], RD8(pb + rb));
-    hsub<SW>(H[1], RD8(pb - RZ));
-    hsub<SW>(H[1], RD8(pb + RZ));
+    for (int w = 0; w < SW; ++w) {
+        H[0][w] = h0.w[w];
+        H[1][w] = h1.w[w];
+    }
     if constexpr (NSH >= 3) {
-        hadd<SW>(H[2], RD8(ya - rb - RZ));
-        hadd<SW>(H[2], RD8(ya + rb - RZ));
-        hadd<SW>(H[2], RD8(ya - rb + RZ));
-        hadd<SW>(H[2], RD8(ya + rb + RZ));
-        hadd<SW>(H[2], RD8(ya - rb - 1));
-        hadd<SW>(H[2], RD8(ya - rb + 1));
-        hadd<SW>(H[2], RD8(ya + rb - 1));
-        hadd<SW>(H[2], RD8(ya + rb + 1));
-        hadd<SW>(H[2], RD8(ya - RZ - 1));
-        hadd<SW>(H[2], RD8(ya - RZ + 1));
-        hadd<SW>(H[2], RD8(ya + RZ - 1));
-        hadd<SW>(H[2], RD8(ya + RZ + 1));
-        hsub<SW>(H[2], RD8(pb - rb - RZ));
-        hsub<SW>(H[2], RD8(pb + rb - RZ));
-        hsub<SW>(H[2], RD8(pb - rb + RZ));
-        hsub<SW>(H[2], RD8(pb + rb + RZ));
-        hsub<SW>(H[2], RD8(pb - rb - 1));
-        hsub<SW>(H[2], RD8(pb - rb + 1));
-        hsub<SW>(H[2], RD8(pb + rb - 1));
-        hsub<SW>(H[2], RD8(pb + rb + 1));
-        hsub<SW>(H[2], RD8(pb - RZ - 1));
-        hsub<SW>(H[2], RD8(pb - RZ + 1));
-        hsub<SW>(H[2], RD8(pb + RZ - 1));
-        hsub<SW>(H[2], RD8(pb + RZ + 1));
+        // shell 3: a's 12 trial-sublattice neighbours, b's 12
+        // partner-sublattice ones (biased by 16 per field)
+        const HW e0 = hconst<SW>(0x10101010u) + hv<SW>(RD8(ya - rb - RZ)) + hv<SW>(RD8(ya + rb - RZ));
+        const HW e1 = hv<SW>(RD8(ya - rb + RZ)) + hv<SW>(RD8(ya + rb + RZ)) + hv<SW>(RD8(ya - rb - 1));
+        const HW e2 = hv<SW>(RD8(ya - rb + 1)) + hv<SW>(RD8(ya + rb - 1)) + hv<SW>(RD8(ya + rb + 1));
+        const HW e3 = hv<SW>(RD8(ya - RZ - 1)) + hv<SW>(RD8(ya - RZ + 1)) + hv<SW>(RD8(ya + RZ - 1));
+        const HW e4 = hv<SW>(RD8(ya + RZ + 1));
+        const HW f0 = hv<SW>(RD8(pb - rb - RZ)) + hv<SW>(RD8(pb + rb - RZ)) + hv<SW>(RD8(pb - rb + RZ));
+        const HW f1 = hv<SW>(RD8(pb + rb + RZ)) + hv<SW>(RD8(pb - rb - 1)) + hv<SW>(RD8(pb - rb + 1));
+        const HW f2 = hv<SW>(RD8(pb + rb - 1)) + hv<SW>(RD8(pb + rb + 1)) + hv<SW>(RD8(pb - RZ - 1));
+        const HW f3 = hv<SW>(RD8(pb - RZ + 1)) + hv<SW>(RD8(pb + RZ - 1)) + hv<SW>(RD8(pb + RZ + 1));
+        const HW h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
+#pragma unroll
+        for (int w = 0; w < SW; ++w) H[2][w] = h2.w[w];
     }
     if constexpr (XB) {
         return dot_fixed_rtab(H[0][0], H[1][0], qt + (a8 * 5u + b8) * 16u);
