@@ -28,6 +28,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <type_traits>
 #include <vector>
 
 #include "pair_fixed.cuh"
@@ -1202,6 +1203,351 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     }
 }
 
+// ---------------------------------------------------------------------------
+// Paired-group streaming sweep (rows of 128, 256 or 512 cells, one lattice,
+// two shells, at most 4 + 1 species).  The groups of a column come in pairs
+// (dy, dy + 1) with dy = 0 or 2: group dy + 1 reads no row that a
+// neighbouring column writes in group dy, nor the other way round (the
+// lag-2 rule of groups with dy >= 1), so once the 8 neighbouring columns
+// have finished the previous pair, one warp stages the union of the pair's
+// rows (28 rows instead of 2 x 21), runs both groups' 4 mini-steps in it,
+// writes back the union of the rows they change (8 instead of 2 x 5) and
+// publishes the pair.  Rows in shared memory (relative to the pair's first
+// group, y0 = 4 cy + dy, z0 = 4 cz + dz):
+//   slots 0..11:  own sublattice, (y0 - 1 + oy, z0 - 1 + oz) at 4 oz + oy,
+//                 oy < 4, oz < 3;
+//   slots 12..27: partner sublattice, (y0 + s_off - 1 + sy, z0 + s_off - 1
+//                 + sz) for sy in 1..3 (sz = 0, 3) or 0..4 (sz = 1, 2), at
+//                 pslot2(sy, sz).
+// Group h (0 or 1) of the pair sees its own rows shifted by h in y.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int pslot2(int sy, int sz)
+{
+    return sz == 0 ? 11 + sy : (sz == 1 ? 15 + sy : (sz == 2 ? 20 + sy : 24 + sy));
+}
+constexpr int kPairRows = 28;
+
+// dE_fix of the trial at a (ya = slot-0 body + x, pa = ya + s_off) of group
+// H of the pair, direction dir; a8, b8 and b's offset through references.
+template <int RB, int H>
+__device__ __forceinline__ int32_t pair2_dE(uint32_t ya, uint32_t pa, uint32_t dir, uint32_t lut, uint32_t qt,
+                                            uint32_t &a8, uint32_t &b8, uint32_t &pb)
+{
+    using HW = HV<1>;
+    constexpr uint32_t rb = (uint32_t)RB;
+    constexpr uint32_t A0 = 5 + H;  // own (0, 0)
+    constexpr uint32_t S11 = pslot2(1 + H, 1), S21 = pslot2(2 + H, 1), S12 = pslot2(1 + H, 2),
+                       S22 = pslot2(2 + H, 2);
+    const int4 L = *(const int4 *)(g_smem + lut + (uint32_t)H * 128u + dir * 16u);
+    a8 = LD8(ya + A0 * rb);
+    pb = pa + (uint32_t)L.x;
+    b8 = LD8(pb);
+    const uint32_t ob = ya + (uint32_t)L.y;
+    // shell 1: a's 8 partner-sublattice neighbours minus b, minus b's 8
+    // trial-sublattice neighbours plus a (counts biased by 128 per field)
+    const HW a0 = hconst<1>(0x80808080u) + hv<1>(a8) + hv<1>(LD8(pa + S11 * rb));
+    const HW a1 = hv<1>(LD8(pa + S11 * rb + 1)) + hv<1>(LD8(pa + S21 * rb)) + hv<1>(LD8(pa + S21 * rb + 1));
+    const HW a2 = hv<1>(LD8(pa + S12 * rb)) + hv<1>(LD8(pa + S12 * rb + 1)) + hv<1>(LD8(pa + S22 * rb));
+    const HW a3 = hv<1>(LD8(pa + S22 * rb + 1));
+    const HW b0 = hv<1>(b8) + hv<1>(LD8(ob)) + hv<1>(LD8(ob + 1));
+    const HW b1 = hv<1>(LD8(ob + rb)) + hv<1>(LD8(ob + rb + 1)) + hv<1>(LD8(ob + 4 * rb));
+    const HW b2 = hv<1>(LD8(ob + 4 * rb + 1)) + hv<1>(LD8(ob + 5 * rb)) + hv<1>(LD8(ob + 5 * rb + 1));
+    const HW h0 = (a0 + a1) + (a2 + a3) - ((b0 + b1) + b2);
+    // shell 2: a's 6 trial-sublattice neighbours, b's 6 partner-sublattice ones
+    const HW c0 = hconst<1>(0x80808080u) + hv<1>(LD8(ya + A0 * rb - 1)) + hv<1>(LD8(ya + A0 * rb + 1));
+    const HW c1 = hv<1>(LD8(ya + (A0 - 1) * rb)) + hv<1>(LD8(ya + (A0 + 1) * rb)) + hv<1>(LD8(ya + (A0 - 4) * rb));
+    const HW c2 = hv<1>(LD8(ya + (A0 + 4) * rb));
+    const HW d0 = hv<1>(LD8(pb - 1)) + hv<1>(LD8(pb + 1)) + hv<1>(LD8(pb - rb));
+    const HW d1 = hv<1>(LD8(pb + rb)) + hv<1>(LD8(pb - (uint32_t)L.z)) + hv<1>(LD8(pb + (uint32_t)L.w));
+    const HW h1 = ((c0 + c1) + c2) - (d0 + d1);
+    return dot_fixed_rtab(h0.w[0], h1.w[0], qt + (a8 * 5u + b8) * 16u);
+}
+
+// The trials of mini-step dx of group H for this lane's NKW link cells
+// i = lane + 32 k, with the random words wv[k].
+template <bool IS_INT, int RB, int NKW, int H>
+__device__ __forceinline__ void pair2_trials(const SweepParams &P, uint32_t body, int soff, int nx, int dx, int lane,
+                                             float cx, int2 ti, uint32_t lut, uint32_t qt, const uint32_t (&wv)[NKW],
+                                             long long &accE, long long &accN)
+{
+    constexpr uint32_t A0 = 5 + H;
+    int32_t dE[NKW];
+    uint32_t a8[NKW], b8[NKW], pb[NKW], ya[NKW];
+    bool acc[NKW];
+#pragma unroll
+    for (int u = 0; u < NKW; ++u) {
+        const int x = 4 * (lane + 32 * u) + dx;
+        ya[u] = body + (uint32_t)x;
+        const uint32_t w = wv[u];
+        dE[u] = pair2_dE<RB, H>(ya[u], ya[u] + soff, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
+        acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
+        // b's store address wraps along x (the load may read a halo copy)
+        const int xb = x + soff + (int)(w >> 31);
+        pb[u] += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
+    }
+#pragma unroll
+    for (int u = 0; u < NKW; ++u) {
+        if (acc[u]) {
+            g_smem[ya[u] + A0 * (uint32_t)RB] = (unsigned char)b8[u];
+            g_smem[pb[u]] = (unsigned char)a8[u];
+            accE += dE[u];
+            accN += 1;
+        }
+    }
+}
+
+// Global row of slot `slot` of the pair at (sub, y0, z0, s_off).
+__device__ __forceinline__ const int8_t *pair2_row(const RepDesc &RD, int slot, int sub, int y0, int z0, int soff)
+{
+    int s, y, z;
+    if (slot < 12) {
+        s = sub;
+        y = y0 - 1 + (slot & 3);
+        z = z0 - 1 + (slot >> 2);
+    } else {
+        const int k = slot - 12;
+        const int sz = k < 3 ? 0 : (k < 8 ? 1 : (k < 13 ? 2 : 3));
+        const int sy = k - (sz == 0 ? -1 : (sz == 1 ? 3 : (sz == 2 ? 8 : 12)));
+        s = 1 - sub;
+        y = y0 + soff - 1 + sy;
+        z = z0 + soff - 1 + sz;
+    }
+    return RD.occ + ((size_t)((s * RD.nz + wrapc(z, RD.nz)) * RD.ny + wrapc(y, RD.ny))) * RD.nx;
+}
+
+// Stages the pair's 28 rows into the warp's buffer (bulk copies completing on
+// the buffer's mbarrier).
+__device__ __forceinline__ void pair2_stage(const RepDesc &RD, int sub, int y0, int z0, int soff, uint32_t dst,
+                                            uint32_t rb, uint32_t mbar, int lane)
+{
+    const int8_t *src = lane < kPairRows ? pair2_row(RD, lane, sub, y0, z0, soff) : RD.occ;
+    // order this warp's earlier accesses of the buffer, and the rows other
+    // warps published (seen through the acquire loads), before the copies
+    __syncwarp();
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+    __syncwarp();
+    if (lane == 0) mbar_expect_tx(mbar, (uint32_t)(kPairRows * RD.nx));
+    __syncwarp();
+    if (lane < kPairRows) bulk_g2s(dst + (uint32_t)lane * rb + 16u, src, (uint32_t)RD.nx, mbar);
+}
+
+// Pair item geometry: sweep t, pair index pp (0..15), tile (ty, tz).
+struct Pair2Geo {
+    int sub, soff, y0, z0;
+    uint32_t gstep, need;  // the pair's first group; neighbours' progress needed
+};
+__device__ __forceinline__ Pair2Geo pair2_geo(int t, int pp, int ty, int tz)
+{
+    Pair2Geo q;
+    const int g = 2 * pp;
+    q.sub = g >> 4;
+    q.soff = q.sub == 0 ? -1 : 0;
+    q.y0 = 4 * ty + (g & 3);
+    q.z0 = 4 * tz + ((g >> 2) & 3);
+    q.gstep = (uint32_t)(t * 32 + g);
+    q.need = q.gstep;  // the neighbours finished group gstep - 1 (their previous pair)
+    return q;
+}
+
+// One warp per column-pair item, the tiles of one column each, gteam + k NT.
+// Shared memory: [replicated table][LUT: 2 groups x 8 directions][per warp:
+// mbarrier (16 bytes), 28 rows of RB bytes].
+template <bool IS_INT, int NKW>
+__global__ void __launch_bounds__(512, 1) k_sweep_pairs(const __grid_constant__ SweepParams P)
+{
+    constexpr int RB = 128 * NKW + 128;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
+    const int gteam = blockIdx.x * nwarp + warp, NT = gridDim.x * nwarp, NW = NT;
+    const uint32_t rb = (uint32_t)RB;
+    const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
+    fill_rtab(P.qtab, P.qrow, tid, blockDim.x);
+    const uint32_t qt = (uint32_t)(lane & 7) * 16u, lut = (uint32_t)kRTabBytes;
+    if (tid < 16) {
+        const int H = tid >> 3, kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
+        int4 e;
+        e.x = pslot2(ky + 1 + H, kz + 1) * RB + kx;  // b: partner row (ky + 1 + H, kz + 1), x + s_off + kx
+        e.y = (kz * 4 + H + ky) * RB + kx - 1;       // b's own 2 x 2 rows from (H + ky, kz), x + kx - 1
+        e.z = (4 + kz) * RB;                         // b's partner row z - 1
+        e.w = (5 - kz) * RB;                         // b's partner row z + 1
+        *(int4 *)(g_smem + lut + (uint32_t)tid * 16u) = e;
+    }
+    const uint32_t wbase = lut + 256u + (uint32_t)warp * (uint32_t)P.warp_bytes;
+    const uint32_t mbar = smem0 + wbase, buf = wbase + 16u;
+    if (lane == 0) {
+        mbar_init(mbar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    const RepDesc &RD = P.rep[0];
+    const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NTy = RD.NTy;
+    const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
+    bool aborted = false, inflight = false;
+    uint32_t par = 0u;
+    long long accE = 0, accN = 0;
+    if (gteam < P.ntiles) {
+        const int dty = NT % NTy, dtz = NT / NTy, ty0 = gteam % NTy, tz0 = gteam / NTy;
+        int t = 0, pp = 0, tile = gteam, ty = ty0, tz = tz0;
+        Pair2Geo q = pair2_geo(t, pp, ty, tz);
+        bool ok = wait_tile_warp(P, RD, ty, tz, q.need, lane);
+        if (ok) {
+            pair2_stage(RD, q.sub, q.y0, q.z0, q.soff, smem0 + buf, rb, mbar, lane);
+            inflight = true;
+        }
+        if (!__all_sync(0xffffffffu, ok)) aborted = true;
+        while (!aborted) {
+            // the next item
+            int t2 = t, pp2 = pp, tile2 = tile + NT, ty2 = ty + dty, tz2 = tz + dtz;
+            if (ty2 >= NTy) {
+                ty2 -= NTy;
+                ++tz2;
+            }
+            if (tile2 >= P.ntiles) {
+                tile2 = gteam;
+                ty2 = ty0;
+                tz2 = tz0;
+                if (++pp2 == 16) {
+                    pp2 = 0;
+                    ++t2;
+                }
+            }
+            const bool has_next = t2 < P.nsweeps;
+            const uint64_t sweep = P.sweep0 + (uint64_t)t;
+            float cx = 0.f;
+            int2 ti = make_int2(0, 0);
+            if constexpr (IS_INT)
+                ti = P.temp.tabinfo[P.beta_stride ? t : 0];
+            else
+                cx = P.temp.beta[P.beta_stride ? t : 0];
+            const uint32_t body = buf + 16u;
+            // Philox words of the pair's first group (while the rows land)
+            uint32_t wr[NKW][4];
+            auto philox_group = [&](int h) {
+                const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0 + h) * nx);
+#pragma unroll
+                for (int k = 0; k < NKW; ++k) {
+                    const U4 w = philox10(U4{(rowsite >> 2) + (uint32_t)(lane + 32 * k), RD.rep, (uint32_t)sweep,
+                                             (uint32_t)(sweep >> 32)},
+                                          k0, k1);
+                    wr[k][0] = w.x;
+                    wr[k][1] = w.y;
+                    wr[k][2] = w.z;
+                    wr[k][3] = w.w;
+                }
+            };
+            philox_group(0);
+            ok = mbar_wait(P, mbar, par);
+            par ^= 1u;
+            if (ok) inflight = false;
+            if (!__all_sync(0xffffffffu, ok)) {
+                aborted = true;
+                break;
+            }
+            // periodic halos: 4 bytes before and after each row body
+            if (lane < kPairRows) {
+                const uint32_t bd = body + (uint32_t)lane * rb;
+                *(unsigned *)(g_smem + bd - 4) = *(const unsigned *)(g_smem + bd + nx - 4);
+                *(unsigned *)(g_smem + bd + nx) = *(const unsigned *)(g_smem + bd);
+            }
+            __syncwarp();
+            // the two groups; after each mini-step the halos of the 5 rows it
+            // may change (lane l < 10: row l / 2, side l % 2)
+            auto run_group = [&](auto Hc) {
+                constexpr int H = decltype(Hc)::value;
+                uint32_t hrow = 0;
+                if (lane < 10) {
+                    const int r5 = lane >> 1;
+                    const int sl = r5 == 0 ? 5 + H : pslot2(1 + H + ((r5 - 1) & 1), 1 + ((r5 - 1) >> 1));
+                    hrow = body + (uint32_t)sl * rb;
+                }
+#pragma unroll 1
+                for (int dx = 0; dx < 4; ++dx) {
+                    uint32_t wv[NKW];
+#pragma unroll
+                    for (int k = 0; k < NKW; ++k) {
+                        wv[k] = wr[k][0];
+                        wr[k][0] = wr[k][1];
+                        wr[k][1] = wr[k][2];
+                        wr[k][2] = wr[k][3];
+                    }
+                    pair2_trials<IS_INT, RB, NKW, H>(P, body, q.soff, nx, dx, lane, cx, ti, lut, qt, wv, accE, accN);
+                    __syncwarp();
+                    if (lane < 10) {
+                        if (lane & 1)
+                            *(unsigned *)(g_smem + hrow + nx) = *(const unsigned *)(g_smem + hrow);
+                        else
+                            *(unsigned *)(g_smem + hrow - 4) = *(const unsigned *)(g_smem + hrow + nx - 4);
+                    }
+                    __syncwarp();
+                }
+            };
+            run_group(std::integral_constant<int, 0>());
+            philox_group(1);
+            run_group(std::integral_constant<int, 1>());
+            // write back the rows the pair changed: own (0, 0) of both groups
+            // (slots 5, 6) and partner slots 16-18 and 21-23
+#pragma unroll 1
+            for (int wrow = 0; wrow < 8; ++wrow) {
+                const int slot = wrow < 2 ? 5 + wrow : (wrow < 5 ? 14 + wrow : 16 + wrow);
+                int8_t *dstg = (int8_t *)pair2_row(RD, slot, q.sub, q.y0, q.z0, q.soff);
+                const int4 *srcs = (const int4 *)(g_smem + body + (uint32_t)slot * rb);
+                for (int cc = lane; cc < (nx >> 4); cc += 32) *((int4 *)dstg + cc) = srcs[cc];
+            }
+            // the rows' stores, then the release (the pair's second group)
+            __syncwarp();
+            if (lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, q.gstep + 2);
+            if (!has_next) break;
+            const Pair2Geo q2 = pair2_geo(t2, pp2, ty2, tz2);
+            ok = wait_tile_warp(P, RD, ty2, tz2, q2.need, lane);
+            if (ok) {
+                pair2_stage(RD, q2.sub, q2.y0, q2.z0, q2.soff, smem0 + buf, rb, mbar, lane);
+                inflight = true;
+            }
+            if (!__all_sync(0xffffffffu, ok)) {
+                aborted = true;
+                break;
+            }
+            t = t2;
+            pp = pp2;
+            tile = tile2;
+            ty = ty2;
+            tz = tz2;
+            q = q2;
+        }
+    }
+    if (aborted) {
+        // let the copies in flight land before the CTA ends
+        if (inflight) mbar_wait(P, mbar, par);
+        return;
+    }
+    // per-warp sums (exact integers); the last warp reduces them
+    const long long e_w = warp_sum<long long>(accE), n_w = warp_sum<long long>(accN);
+    if (lane == 0 && gteam < P.ntiles) {
+        ((long long *)P.part_e)[gteam] = e_w;
+        P.part_n[gteam] = n_w;
+    }
+    __threadfence();
+    __syncwarp();
+    unsigned last = 0;
+    if (lane == 0) last = (atomicAdd(P.ticket, 1u) == (unsigned)NW - 1) ? 1u : 0u;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    if (!last) return;
+    __threadfence();
+    const int np = P.ntiles;
+    long long se = 0, sn = 0;
+    for (int k = lane; k < np; k += 32) {
+        se += __ldcg((const long long *)P.part_e + k);
+        sn += __ldcg(P.part_n + k);
+    }
+    se = warp_sum<long long>(se);
+    sn = warp_sum<long long>(sn);
+    if (lane == 0) {
+        if (RD.e_acc) *RD.e_acc += (double)se * P.escale;
+        if (RD.n_acc) *RD.n_acc += sn;
+    }
+}
+
 // Species byte conversion around a fast-path launch: up (s -> 8 s, with a
 // check that 0 <= s < S; a byte outside sets SMC_ERR_ARG in the status word
 // and is taken mod 8) or down (8 s -> s).
@@ -1676,6 +2022,63 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     return SMC_OK;
 }
 
+// Plan of the paired-group kernel (fast_wide lattices): one CTA per SM with
+// as many warps as shared memory and registers allow (at most 16), CTAs
+// spread so that the busiest SM has the fewest tiles.
+template <bool IS_INT>
+smc_status make_pairs_plan(const smc_lattice &lat, Workspace *ws, Plan &pl)
+{
+    static long long key_cached[5] = {-1, -1, -1, -1, -1};
+    static Plan plan_cached;
+    const long long key[5] = {lat.nx, lat.ny, lat.nz, ws->device, (long long)ws->smem_optin};
+    if (std::equal(key, key + 5, key_cached)) {
+        pl = plan_cached;
+        return SMC_OK;
+    }
+    const int nkw = lat.nx / 128;
+    pl.kernel = nkw == 1 ? (const void *)k_sweep_pairs<IS_INT, 1>
+                         : (nkw == 2 ? (const void *)k_sweep_pairs<IS_INT, 2> : (const void *)k_sweep_pairs<IS_INT, 4>);
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
+    const size_t dyn_max = ws->smem_optin - fa.sharedSizeBytes;
+    e = cudaFuncSetAttribute(pl.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn_max);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+    pl.Lx = pl.Ly = pl.Lz = 4;
+    pl.G = 32;
+    pl.TY = pl.TZ = 1;
+    pl.CB = 1;
+    pl.ntiles = (lat.ny / 4) * (lat.nz / 4);
+    pl.maxNLx = lat.nx / 4;
+    pl.rowB = lat.nx + 128;
+    pl.team = 1;
+    pl.nbuf = 1;
+    pl.team_bytes = 0;
+    pl.tpc = 1;
+    pl.nap_cap = 1024;
+    pl.warp_bytes = 16 + kPairRows * pl.rowB;
+    const size_t head = (size_t)kRTabBytes + 256;
+    int wpc = 0;
+    for (int w = 16; w >= 1 && !wpc; --w) {
+        const size_t smem = head + (size_t)w * pl.warp_bytes;
+        if (smem > dyn_max) continue;
+        int per_sm = 0;
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.kernel, 32 * w, smem);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaOccupancyMaxActiveBlocksPerMultiprocessor");
+        if (per_sm >= 1) wpc = w;
+    }
+    if (!wpc) {
+        set_error("paired sweep kernel does not fit on an SM (rows of %d bytes)", pl.rowB);
+        return SMC_ERR_UNSUPPORTED;
+    }
+    pl.threads = 32 * wpc;
+    pl.smem = head + (size_t)wpc * pl.warp_bytes;
+    pl.grid = (int)(balanced_warps(pl.ntiles, wpc, 1, ws->num_sms) / wpc);
+    std::copy(key, key + 5, key_cached);
+    plan_cached = pl;
+    return SMC_OK;
+}
+
 // Fast path: 4-cell link cells on every axis, rows of at most 1024 cells,
 // 4-byte aligned occupancy.
 bool fast_ok(int R, const smc_lattice *lats, int8_t *const *occ, int &rowB)
@@ -1805,9 +2208,13 @@ static smc_status sweep_impl(int R, const smc_lattice *lats, const smc_model *m,
     }
     int rowB = 0;
     const bool fast = fast_ok(R, lats, occ, rowB);
-    if (fast && fast_wide(R, lats, pt.nsh, pt.sw)) rowB = lats[0].nx + 128;
+    // (paired kernel: bulk row copies, so 16-byte aligned rows)
+    const bool wide = fast && fast_wide(R, lats, pt.nsh, pt.sw) && (uintptr_t)occ[0] % 16 == 0;
     Plan pl;
-    st = fast ? make_fast_plan<IS_INT>(R, lats, ws, pt, rowB, pl) : make_plan<IS_INT>(R, lats, ws, pt, pl);
+    if (wide)
+        st = make_pairs_plan<IS_INT>(lats[0], ws, pl);
+    else
+        st = fast ? make_fast_plan<IS_INT>(R, lats, ws, pt, rowB, pl) : make_plan<IS_INT>(R, lats, ws, pt, pl);
     if (st != SMC_OK) return st;
     if (!fast) pl.rowB = rowB;
 
