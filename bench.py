@@ -545,16 +545,19 @@ def run_extras(smc, torch, dev, pk):
     occ = torch.empty(lat.nsites, dtype=torch.int8, device=dev)
     smc.init_lattice(lat, inputs.equiatomic_counts(lat.nsites, S), 1, occ)
     kT = inputs.anneal_kT(1000)
-    nsw = 4
+    nsw = 20
     ms = timed(lambda: smc.sweep(lat, model, occ, 1, 0, nsw, kT[:nsw]), reps=2)
     att = lat.nsites * nsw / (ms * 1e-3)
     out["hbm_512"] = {"cells": [n, n, n], "sweeps_per_launch": nsw, "ms_per_sweep": ms / nsw,
                       "attempts_per_s": att, "achieved_gbs": att * BYTES_PER_ATTEMPT / 1e9,
-                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"]}
+                      "frac_of_measured_hbm": att * BYTES_PER_ATTEMPT / 1e9 / pk["hbm_gbs"],
+                      "kernel": "k_sweep_pairs (groups in pairs; the call includes the species scaling "
+                                "passes around the launch)",
+                      "dram_bytes_per_attempt": profile_record("k_sweep_pairs_bcc512_4sweeps", "bytes_per_attempt")}
     # integer-issue ceiling beside the HBM one: every SM issues at most 4 warp
     # instructions (128 lanes) per clock, and a trial costs the instructions
     # ncu counted on this kernel source (None once the source changed)
-    ipt = profile_record("k_sweep_fast_bcc512_4sweeps", "instructions_per_trial")
+    ipt = profile_record("k_sweep_pairs_bcc512_4sweeps", "instructions_per_trial")
     if ipt:
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         issue_cap = sms * 128 * pk.get("sm_max_mhz", 2070.0) * 1e6 / ipt

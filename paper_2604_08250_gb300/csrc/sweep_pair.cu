@@ -596,30 +596,6 @@ __device__ __forceinline__ FastGeo fast_geo(const SweepParams &P, int t, int g, 
     return q;
 }
 
-// The same for the wide-row kernels: one lattice, one-column tiles, the
-// tile's coordinates (ty, tz) tracked by the caller (no divisions).
-__device__ __forceinline__ FastGeo fast_geo_wide(int t, int g, int ty, int tz)
-{
-    FastGeo q;
-    q.r = 0;
-    q.ty = ty;
-    q.tz = tz;
-    q.nj = 1;
-    q.ncols = 1;
-    q.j = ty;
-    q.l = tz;
-    q.dy = g & 3;
-    q.dz = (g >> 2) & 3;
-    q.sub = g >> 4;
-    q.soff = q.sub == 0 ? -1 : 0;
-    q.y0 = 4 * q.j + q.dy;
-    q.z0 = 4 * q.l + q.dz;
-    q.gstep = (uint32_t)(t * 32 + g);
-    const uint32_t lagv = (g & 3) ? 2u : 1u;  // groups with dy >= 1: lag 2
-    q.need = q.gstep + 1 >= lagv ? q.gstep + 1 - lagv : 0;
-    return q;
-}
-
 // Stages the rows of column geometry q into the buffer at g_smem offset buf.
 // Rows of a multiple of 16 bytes, 16-byte aligned: mode 0, one cp.async.bulk
 // per row, completing on mbarrier `mbar` (absolute shared address); mode 1,
@@ -697,15 +673,13 @@ __device__ __forceinline__ void fast_stage(const RepDesc &RD, const FastGeo &q, 
 
 // dE_fix of the trial at a = own row (0, 0), x, with ya = row-0 body + x and
 // pa = ya + s_off, partner direction dir; the species a8, b8 (x 8) and b's
-// shared-memory offset through references.  XB: the replicated table at qt
-// (qt includes this lane's copy offset), else the plain table at qt.
-template <int NSH, int SW, int RB, bool XB = false>
+// shared-memory offset through references.
+template <int NSH, int SW, int RB>
 __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rbr, uint32_t dir, uint32_t lut,
                                            uint32_t qt, uint32_t &a8, uint32_t &b8, uint32_t &pb)
 {
-    static_assert(!XB || (NSH == 2 && SW == 1), "replicated table: two shells, one species word");
     using H = HV<SW>;
-    constexpr uint32_t B12 = XB ? 0x80808080u : 0x08080808u;
+    constexpr uint32_t B12 = 0x08080808u;
     const uint32_t rb = RB ? (uint32_t)RB : rbr;
     constexpr uint32_t S11 = pslot<NSH>(1, 1), S21 = pslot<NSH>(2, 1), S12 = pslot<NSH>(1, 2), S22 = pslot<NSH>(2, 2);
     const int4 L = *(const int4 *)(g_smem + lut + dir * 16u);
@@ -730,35 +704,31 @@ __device__ __forceinline__ int32_t fast_dE(uint32_t ya, uint32_t pa, uint32_t rb
     const H d0 = hv<SW>(LD8(pb - 1)) + hv<SW>(LD8(pb + 1)) + hv<SW>(LD8(pb - rb));
     const H d1 = hv<SW>(LD8(pb + rb)) + hv<SW>(LD8(pb - (uint32_t)L.z)) + hv<SW>(LD8(pb + (uint32_t)L.w));
     const H h1 = ((c0 + c1) + c2) - (d0 + d1);
-    if constexpr (XB) {
-        return dot_fixed_rtab(h0.w[0], h1.w[0], qt + (a8 * 5u + b8) * 16u);
-    } else {
-        uint32_t Hw[NSH][SW];
+    uint32_t Hw[NSH][SW];
 #pragma unroll
-        for (int w = 0; w < SW; ++w) {
-            Hw[0][w] = h0.w[w];
-            Hw[1][w] = h1.w[w];
-        }
-        if constexpr (NSH >= 3) {
-            // shell 3: a's 12 trial-sublattice neighbours, b's 12
-            // partner-sublattice ones (biased by 16 per field)
-            const H e0 = hconst<SW>(0x10101010u) + hv<SW>(LD8(ya)) + hv<SW>(LD8(ya + 2 * rb));
-            const H e1 = hv<SW>(LD8(ya + 6 * rb)) + hv<SW>(LD8(ya + 8 * rb)) + hv<SW>(LD8(ya + 3 * rb - 1));
-            const H e2 = hv<SW>(LD8(ya + 3 * rb + 1)) + hv<SW>(LD8(ya + 5 * rb - 1)) + hv<SW>(LD8(ya + 5 * rb + 1));
-            const H e3 = hv<SW>(LD8(ya + rb - 1)) + hv<SW>(LD8(ya + rb + 1)) + hv<SW>(LD8(ya + 7 * rb - 1));
-            const H e4 = hv<SW>(LD8(ya + 7 * rb + 1));
-            const H f0 = hv<SW>(LD8(pb - 5 * rb)) + hv<SW>(LD8(pb - 3 * rb)) + hv<SW>(LD8(pb + 3 * rb));
-            const H f1 = hv<SW>(LD8(pb + 5 * rb)) + hv<SW>(LD8(pb - rb - 1)) + hv<SW>(LD8(pb - rb + 1));
-            const H f2 = hv<SW>(LD8(pb + rb - 1)) + hv<SW>(LD8(pb + rb + 1)) + hv<SW>(LD8(pb - 4 * rb - 1));
-            const H f3 = hv<SW>(LD8(pb - 4 * rb + 1)) + hv<SW>(LD8(pb + 4 * rb - 1)) + hv<SW>(LD8(pb + 4 * rb + 1));
-            const H h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
-#pragma unroll
-            for (int w = 0; w < SW; ++w) Hw[2][w] = h2.w[w];
-        }
-        constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
-        const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
-        return dot_fixed<NSH, SW>(Hw, row);
+    for (int w = 0; w < SW; ++w) {
+        Hw[0][w] = h0.w[w];
+        Hw[1][w] = h1.w[w];
     }
+    if constexpr (NSH >= 3) {
+        // shell 3: a's 12 trial-sublattice neighbours, b's 12
+        // partner-sublattice ones (biased by 16 per field)
+        const H e0 = hconst<SW>(0x10101010u) + hv<SW>(LD8(ya)) + hv<SW>(LD8(ya + 2 * rb));
+        const H e1 = hv<SW>(LD8(ya + 6 * rb)) + hv<SW>(LD8(ya + 8 * rb)) + hv<SW>(LD8(ya + 3 * rb - 1));
+        const H e2 = hv<SW>(LD8(ya + 3 * rb + 1)) + hv<SW>(LD8(ya + 5 * rb - 1)) + hv<SW>(LD8(ya + 5 * rb + 1));
+        const H e3 = hv<SW>(LD8(ya + rb - 1)) + hv<SW>(LD8(ya + rb + 1)) + hv<SW>(LD8(ya + 7 * rb - 1));
+        const H e4 = hv<SW>(LD8(ya + 7 * rb + 1));
+        const H f0 = hv<SW>(LD8(pb - 5 * rb)) + hv<SW>(LD8(pb - 3 * rb)) + hv<SW>(LD8(pb + 3 * rb));
+        const H f1 = hv<SW>(LD8(pb + 5 * rb)) + hv<SW>(LD8(pb - rb - 1)) + hv<SW>(LD8(pb - rb + 1));
+        const H f2 = hv<SW>(LD8(pb + rb - 1)) + hv<SW>(LD8(pb + rb + 1)) + hv<SW>(LD8(pb - 4 * rb - 1));
+        const H f3 = hv<SW>(LD8(pb - 4 * rb + 1)) + hv<SW>(LD8(pb + 4 * rb - 1)) + hv<SW>(LD8(pb + 4 * rb + 1));
+        const H h2 = ((e0 + e1) + (e2 + e3) + e4) - ((f0 + f1) + (f2 + f3));
+#pragma unroll
+        for (int w = 0; w < SW; ++w) Hw[2][w] = h2.w[w];
+    }
+    constexpr uint32_t half_row = (uint32_t)qrow_words(NSH, SW) / 2;  // (A * 8 + B) rows = (8 a8 + b8) / 8
+    const uint32_t *row = (const uint32_t *)(g_smem + qt + (8u * a8 + b8) * half_row);
+    return dot_fixed<NSH, SW>(Hw, row);
 }
 
 // Team synchronisation: the tw warps that share a column meet at named
@@ -787,14 +757,12 @@ __device__ __forceinline__ bool team_and(int tw, int tb, bool p)
 }
 
 // KU trials of mini-step dx per lane: link cells i = ib + is * (k0 + u),
-// u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).  The random
-// words come from the warp's shared-memory words, or from wreg[u] when
-// wreg is given (the words of this mini-step, held in registers).
-template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD, bool XB = false>
+// u < KU (ib = lane + 32 * warp-in-team, is = 32 * team size).
+template <bool IS_INT, int NSH, int SW, int RB, int KU, bool GUARD>
 __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body, int soff, uint32_t rbr,
                                             uint32_t wsm, int k0, int nk, int ib, int is, int NLx, int nx, int dx,
                                             int lane, float cx, int2 ti, uint32_t lut, uint32_t qt, long long &accE,
-                                            long long &accN, const uint32_t *wreg = nullptr)
+                                            long long &accN)
 {
     const uint32_t rb = RB ? (uint32_t)RB : rbr;
     int32_t dE[KU];
@@ -807,9 +775,8 @@ __device__ __forceinline__ void fast_trials(const SweepParams &P, uint32_t body,
         if (!GUARD || (k < nk && i < NLx)) {
             const int x = 4 * i + dx;
             ya[u] = body + (uint32_t)x;
-            const uint32_t w =
-                wreg ? wreg[u] : *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
-            dE[u] = fast_dE<NSH, SW, RB, XB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
+            const uint32_t w = *(const uint32_t *)(g_smem + wsm + (uint32_t)(((k * 4 + dx) * 32 + lane) * 4));
+            dE[u] = fast_dE<NSH, SW, RB>(ya[u], ya[u] + soff, rbr, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
             acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
             // b's store address wraps along x (the load may read a halo copy)
             const int xb = x + soff + (int)(w >> 31);
@@ -838,13 +805,6 @@ template <bool IS_INT, int NSH, int SW, int RB>
 __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ SweepParams P)
 {
     constexpr int NROWS = fast_nrows<NSH>();
-    // Rows of RB = nx + 128 bytes (a multiple of 128): every row starts on
-    // the same bank, so the loads of b's rows, which differ from lane to
-    // lane with the partner direction, never conflict.  Each lane then keeps
-    // the random words of its NKW = nx / 128 link cells in registers.
-    constexpr bool WREG = RB != 0 && RB % 128 == 0;
-    constexpr int NKW = WREG ? (RB - 128) / 128 : 1;
-    static_assert(!WREG || (NKW >= 1 && NKW <= 4), "register words: rows of 128 to 512 cells");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     const int tw = P.team, wi = warp % tw, tix = warp / tw, tpb = nwarp / tw;
     const int gteam = blockIdx.x * tpb + tix, NT = gridDim.x * tpb, NW = gridDim.x * nwarp;
@@ -853,16 +813,10 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     const uint32_t rb = RB ? (uint32_t)RB : (uint32_t)P.rowB;
     const uint32_t smem0 = (uint32_t)__cvta_generic_to_shared(g_smem);
     // fixed-point table and the per-direction offsets of b and its rows
-    uint32_t qt = 0u, lut;
-    if constexpr (WREG) {
-        fill_rtab(P.qtab, P.qrow, tid, blockDim.x);
-        qt = (uint32_t)(lane & 7) * 16u;
-        lut = (uint32_t)kRTabBytes;
-    } else {
-        const int qwords = kQRows * P.qrow;
-        for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
-        lut = (uint32_t)qwords * 4u;
-    }
+    const uint32_t qt = 0u;
+    const int qwords = kQRows * P.qrow;
+    for (int i = tid; i < qwords; i += blockDim.x) ((uint32_t *)g_smem)[i] = P.qtab[i];
+    const uint32_t lut = (uint32_t)qwords * 4u;
     if (tid < 8) {
         const int kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
         int4 e;
@@ -897,16 +851,10 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
     // per buffer b: bit b of par = parity of its barrier's next phase; bit b
     // of inflight (leader) = copies issued and not yet waited for
     uint32_t par = 0u, inflight = 0u;
-    // wide kernels: per-lane sums over the whole launch (exact integers), and
-    // the tile coordinates stepped by NT tiles at a time
-    long long accE = 0, accN = 0;
-    const int NTy0 = P.rep[0].NTy;
-    const int dty = WREG ? NT % NTy0 : 0, dtz = WREG ? NT / NTy0 : 0;
-    const int ty0 = WREG ? gteam % NTy0 : 0, tz0 = WREG ? gteam / NTy0 : 0;
     if (gteam < P.ntiles) {
         int t = 0, g = 0, tile = gteam, c = 0, nb = 0, slotk = 0;
-        int cty = ty0, ctz = tz0;
-        FastGeo q = WREG ? fast_geo_wide(t, g, cty, ctz) : fast_geo(P, t, g, tile, c);
+        long long accE = 0, accN = 0;
+        FastGeo q = fast_geo(P, t, g, tile, c);
         bool ok = true;
         if (leader) {
             ok = wait_tile_warp(P, P.rep[q.r], q.ty, q.tz, q.need, lane);
@@ -921,11 +869,6 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             const int nx = RD.nx, ny = RD.ny, nz = RD.nz, NLx = RD.NLx;
             // the next item
             int t2 = t, g2 = g, tile2 = tile, c2 = c + 1, slot2 = slotk;
-            int ty2 = cty + dty, tz2 = ctz + dtz;
-            if (ty2 >= NTy0) {
-                ty2 -= NTy0;
-                ++tz2;
-            }
             if (c2 >= q.ncols) {
                 c2 = 0;
                 tile2 += NT;
@@ -933,8 +876,6 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 if (tile2 >= P.ntiles) {
                     tile2 = gteam;
                     slot2 = 0;
-                    ty2 = ty0;
-                    tz2 = tz0;
                     if (++g2 == P.G) {
                         g2 = 0;
                         ++t2;
@@ -943,7 +884,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             }
             const bool has_next = t2 < P.nsweeps;
             FastGeo q2;
-            if (has_next) q2 = WREG ? fast_geo_wide(t2, g2, ty2, tz2) : fast_geo(P, t2, g2, tile2, c2);
+            if (has_next) q2 = fast_geo(P, t2, g2, tile2, c2);
             const bool next_vec = has_next && P.rep[q2.r].vec != 0;
             auto can_prefetch = [&]() -> bool {
                 if (!next_vec || nbuf < 2) return false;
@@ -962,21 +903,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             }
             // Philox words of this warp's link cells (while the rows land)
             const uint64_t sweep = P.sweep0 + (uint64_t)t;
-            uint32_t wr[NKW][4];
-            if constexpr (WREG) {
-                const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0) * nx);
-                const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
-#pragma unroll
-                for (int k = 0; k < NKW; ++k) {
-                    const U4 w = philox10(
-                        U4{(rowsite >> 2) + (uint32_t)(ib + is * k), RD.rep, (uint32_t)sweep, (uint32_t)(sweep >> 32)},
-                        k0, k1);
-                    wr[k][0] = w.x;
-                    wr[k][1] = w.y;
-                    wr[k][2] = w.z;
-                    wr[k][3] = w.w;
-                }
-            } else {
+            {
                 const uint32_t rowsite = (uint32_t)(((q.sub * nz + q.z0) * ny + q.y0) * nx);
                 const uint32_t k0 = (uint32_t)P.seed, k1 = (uint32_t)(P.seed >> 32);
                 uint32_t *wp = (uint32_t *)(g_smem + wsm);
@@ -1033,20 +960,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 hrow = body + (uint32_t)sl * rb;
             }
             for (int dx = 0; dx < 4; ++dx) {
-                if constexpr (WREG) {
-                    // one trial per link cell of the lane (NLx = 32 NKW), the
-                    // mini-step's word first in each register row
-                    uint32_t wv[NKW];
-#pragma unroll
-                    for (int k = 0; k < NKW; ++k) {
-                        wv[k] = wr[k][0];
-                        wr[k][0] = wr[k][1];
-                        wr[k][1] = wr[k][2];
-                        wr[k][2] = wr[k][3];
-                    }
-                    fast_trials<IS_INT, NSH, SW, RB, NKW, false, true>(P, body, q.soff, rb, wsm, 0, NKW, ib, is, NLx,
-                                                                       nx, dx, lane, cx, ti, lut, qt, accE, accN, wv);
-                } else if (NLx == is * nkw && (nkw & 3) == 0) {
+                if (NLx == is * nkw && (nkw & 3) == 0) {
 #pragma unroll 1
                     for (int kk = 0; kk < nkw; kk += 4)
                         fast_trials<IS_INT, NSH, SW, RB, 4, false>(P, body, q.soff, rb, wsm, kk, nkw, ib, is, NLx, nx,
@@ -1114,9 +1028,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             // every thread's row stores, then one release by the leader's lane 0
             // (the barrier orders the team's stores before it)
             team_sync(tw, tb);
-            if (c + 1 >= q.ncols && WREG) {
-                if (leader && lane == 0 && tile != P.skip_tile) st_release_u32(P.flags + tile, q.gstep + 1);
-            } else if (c + 1 >= q.ncols) {
+            if (c + 1 >= q.ncols) {
                 // the tile's last column: accumulate in fixed order and publish
                 const long long e_w = warp_sum<long long>(accE);
                 const long long n_w = warp_sum<long long>(accN);
@@ -1148,8 +1060,6 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
             slotk = slot2;
             q = q2;
             nb = nbn;
-            cty = ty2;
-            ctz = tz2;
         }
     }
     if (aborted) {
@@ -1160,17 +1070,10 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
                 if (inflight & (1u << b)) mbar_wait(P, smem0 + mbar0 + 8u * (uint32_t)b, (par >> b) & 1u);
         return;
     }
-    // ---- per-tile partial sums (one per warp of the team; wide kernels: one
-    // per warp, as int64); the last warp to finish reduces them, all its
-    // lanes at once: the partial sums are integers (dE_fix, counts), so their
-    // int64 sum is exact in any order ----
-    if constexpr (WREG) {
-        const long long e_w = warp_sum<long long>(accE), n_w = warp_sum<long long>(accN);
-        if (lane == 0 && gteam < P.ntiles) {
-            ((long long *)P.part_e)[gteam] = e_w;
-            P.part_n[gteam] = n_w;
-        }
-    } else if (lane == 0) {
+    // ---- per-tile partial sums (one per warp of the team); the last warp to
+    // finish reduces them, all its lanes at once: the partial sums are
+    // integers (dE_fix, counts), so their int64 sum is exact in any order ----
+    if (lane == 0) {
         int k = 0;
         for (int tl = gteam; tl < P.ntiles; tl += NT, ++k) {
             P.part_e[(size_t)tl * tw + wi] = (double)slot_e[k];
@@ -1191,7 +1094,7 @@ __global__ void __launch_bounds__(256) k_sweep_fast(const __grid_constant__ Swee
         const long long *pn = P.part_n + (size_t)RD.tile0 * tw;
         long long se = 0, sn = 0;
         for (int k = lane; k < np; k += 32) {
-            se += WREG ? __ldcg((const long long *)pe + k) : (long long)__ldcg(pe + k);
+            se += (long long)__ldcg(pe + k);
             sn += __ldcg(pn + k);
         }
         se = warp_sum<long long>(se);
@@ -1856,13 +1759,8 @@ bool fast_wide(int R, const smc_lattice *lats, int nsh, int sw)
 }
 
 template <bool IS_INT>
-const void *pick_fast(int nsh, int sw, int rowB, bool wide)
+const void *pick_fast(int nsh, int sw)
 {
-    if (wide) {
-        if (rowB == 256) return (const void *)k_sweep_fast<IS_INT, 2, 1, 256>;
-        if (rowB == 384) return (const void *)k_sweep_fast<IS_INT, 2, 1, 384>;
-        if (rowB == 640) return (const void *)k_sweep_fast<IS_INT, 2, 1, 640>;
-    }
     if (nsh >= 3)
         return sw == 2 ? (const void *)k_sweep_fast<IS_INT, 3, 2, 0> : (const void *)k_sweep_fast<IS_INT, 3, 1, 0>;
     return sw == 2 ? (const void *)k_sweep_fast<IS_INT, 2, 2, 0> : (const void *)k_sweep_fast<IS_INT, 2, 1, 0>;
@@ -1911,9 +1809,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     const Tuning tu = current_tuning();
     pl.Lx = pl.Ly = pl.Lz = 4;
     pl.G = 32;
-    // wide rows (fast_wide: rows of nx + 128 bytes, register words)
-    const bool wide = fast_wide(R, lats, pt.nsh, pt.sw) && rowB == lats[0].nx + 128;
-    pl.kernel = pick_fast<IS_INT>(pt.nsh, pt.sw, rowB, wide);
+    pl.kernel = pick_fast<IS_INT>(pt.nsh, pt.sw);
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, pl.kernel);
     if (e != cudaSuccess) return cuda_fail(e, "cudaFuncGetAttributes");
@@ -1933,7 +1829,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     pl.ntiles = 0;
     for (int r = 0; r < R; ++r)
         pl.ntiles += ((lats[r].ny / 4 + pl.TY - 1) / pl.TY) * ((lats[r].nz / 4 + pl.TZ - 1) / pl.TZ);
-    const size_t head = (wide ? (size_t)kRTabBytes : (size_t)kQRows * pt.rw * 4) + 128;
+    const size_t head = (size_t)kQRows * pt.rw * 4 + 128;
     const int nrows = pt.nsh >= 3 ? 25 : 21;
     // A team of tw warps shares a column (two row buffers per team); every
     // warp keeps its accumulator slots and Philox words.  Total warps: all
@@ -1952,9 +1848,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
     // staging latency better than 8 warps with two buffers each, and teams
     // pay a barrier per mini-step), so those are the defaults; the hooks can
     // still select the others.
-    // register words (wide rows): one warp per column
-    const bool wreg = wide;
-    const int force_tw = wreg ? 1 : debug_fast_team(), force_nb = debug_fast_nbuf();
+    const int force_tw = debug_fast_team(), force_nb = debug_fast_nbuf();
     for (int nbuf = 2; nbuf >= 1; --nbuf) {
         if (force_nb ? nbuf != force_nb : nbuf != 1) continue;
         for (int tw = 1; tw <= 4; tw *= 2) {
@@ -1968,7 +1862,7 @@ smc_status make_fast_plan_uncached(int R, const smc_lattice *lats, Workspace *ws
                 if (nwarps % tw) continue;
                 const int tpb = nwarps / tw;
                 for (int tpc_guess = 1;; tpc_guess *= 2) {
-                    const size_t wb = ((size_t)16 * tpc_guess + (wreg ? 0 : (size_t)512 * nkw) + 15) / 16 * 16;
+                    const size_t wb = ((size_t)16 * tpc_guess + (size_t)512 * nkw + 15) / 16 * 16;
                     const size_t smem = head + (size_t)tpb * team_bytes + (size_t)nwarps * wb;
                     if (smem > dyn_max) break;
                     int per_sm = 0;
