@@ -1141,7 +1141,12 @@ __device__ __forceinline__ int32_t pair2_dE(uint32_t ya, uint32_t pa, uint32_t d
     constexpr uint32_t A0 = 5 + H;  // own (0, 0)
     constexpr uint32_t S11 = pslot2(1 + H, 1), S21 = pslot2(2 + H, 1), S12 = pslot2(1 + H, 2),
                        S22 = pslot2(2 + H, 2);
-    const int4 L = *(const int4 *)(g_smem + lut + (uint32_t)H * 128u + dir * 16u);
+    // b's partner row and x (L.x), b's own 2 x 2 rows (L.y): one 8-byte load
+    // (16 lanes of 8 directions per phase); b's partner rows z -/+ 1 are
+    // (4 + kz) and (5 - kz) rows away
+    const int2 L = *(const int2 *)(g_smem + lut + (uint32_t)H * 64u + dir * 8u);
+    const uint32_t kz = dir & 1u;
+    const uint32_t Lz = (4u + kz) * rb, Lw = (5u - kz) * rb;
     a8 = LD8(ya + A0 * rb);
     pb = pa + (uint32_t)L.x;
     b8 = LD8(pb);
@@ -1161,18 +1166,22 @@ __device__ __forceinline__ int32_t pair2_dE(uint32_t ya, uint32_t pa, uint32_t d
     const HW c1 = hv<1>(LD8(ya + (A0 - 1) * rb)) + hv<1>(LD8(ya + (A0 + 1) * rb)) + hv<1>(LD8(ya + (A0 - 4) * rb));
     const HW c2 = hv<1>(LD8(ya + (A0 + 4) * rb));
     const HW d0 = hv<1>(LD8(pb - 1)) + hv<1>(LD8(pb + 1)) + hv<1>(LD8(pb - rb));
-    const HW d1 = hv<1>(LD8(pb + rb)) + hv<1>(LD8(pb - (uint32_t)L.z)) + hv<1>(LD8(pb + (uint32_t)L.w));
+    const HW d1 = hv<1>(LD8(pb + rb)) + hv<1>(LD8(pb - Lz)) + hv<1>(LD8(pb + Lw));
     const HW h1 = ((c0 + c1) + c2) - (d0 + d1);
     return dot_fixed_rtab(h0.w[0], h1.w[0], qt + (a8 * 5u + b8) * 16u);
 }
 
 // The trials of mini-step dx of group H for this lane's NKW link cells
-// i = lane + 32 k, with the random words wv[k].
+// i = lane + 32 k, with the random words wv[k].  b's store address wraps
+// along x only for the row's first cell (lane 0, k = 0, dx = 0, s_off = -1,
+// kx = 0: x = -1) and its last (lane 31, k = NKW - 1, dx = 3, s_off = 0,
+// kx = 1: x = nx); its loads may read the halo copies.
 template <bool IS_INT, int RB, int NKW, int H>
 __device__ __forceinline__ void pair2_trials(const SweepParams &P, uint32_t body, int soff, int nx, int dx, int lane,
                                              float cx, int2 ti, uint32_t lut, uint32_t qt, const uint32_t (&wv)[NKW],
-                                             long long &accE, long long &accN)
+                                             long long &accE, uint32_t &accN)
 {
+    const bool lo_edge = lane == 0 && dx == 0 && soff < 0, hi_edge = lane == 31 && dx == 3 && soff == 0;
     constexpr uint32_t A0 = 5 + H;
     int32_t dE[NKW];
     uint32_t a8[NKW], b8[NKW], pb[NKW], ya[NKW];
@@ -1184,9 +1193,9 @@ __device__ __forceinline__ void pair2_trials(const SweepParams &P, uint32_t body
         const uint32_t w = wv[u];
         dE[u] = pair2_dE<RB, H>(ya[u], ya[u] + soff, w >> kRBits, lut, qt, a8[u], b8[u], pb[u]);
         acc[u] = accept_fixed<IS_INT>(dE[u], w & kRMask, cx, P.tab, ti);
-        // b's store address wraps along x (the load may read a halo copy)
-        const int xb = x + soff + (int)(w >> 31);
-        pb[u] += xb < 0 ? (uint32_t)nx : (xb >= nx ? (uint32_t)(-nx) : 0u);
+        const bool kx = (w >> 31) != 0;
+        if (u == 0 && lo_edge && !kx) pb[u] += (uint32_t)nx;
+        if (u == NKW - 1 && hi_edge && kx) pb[u] -= (uint32_t)nx;
     }
 #pragma unroll
     for (int u = 0; u < NKW; ++u) {
@@ -1194,7 +1203,7 @@ __device__ __forceinline__ void pair2_trials(const SweepParams &P, uint32_t body
             g_smem[ya[u] + A0 * (uint32_t)RB] = (unsigned char)b8[u];
             g_smem[pb[u]] = (unsigned char)a8[u];
             accE += dE[u];
-            accN += 1;
+            accN += 1u;
         }
     }
 }
@@ -1268,12 +1277,10 @@ __global__ void __launch_bounds__(512, 1) k_sweep_pairs(const __grid_constant__ 
     const uint32_t qt = (uint32_t)(lane & 7) * 16u, lut = (uint32_t)kRTabBytes;
     if (tid < 16) {
         const int H = tid >> 3, kx = (tid >> 2) & 1, ky = (tid >> 1) & 1, kz = tid & 1;
-        int4 e;
+        int2 e;
         e.x = pslot2(ky + 1 + H, kz + 1) * RB + kx;  // b: partner row (ky + 1 + H, kz + 1), x + s_off + kx
         e.y = (kz * 4 + H + ky) * RB + kx - 1;       // b's own 2 x 2 rows from (H + ky, kz), x + kx - 1
-        e.z = (4 + kz) * RB;                         // b's partner row z - 1
-        e.w = (5 - kz) * RB;                         // b's partner row z + 1
-        *(int4 *)(g_smem + lut + (uint32_t)tid * 16u) = e;
+        *(int2 *)(g_smem + lut + (uint32_t)tid * 8u) = e;
     }
     const uint32_t wbase = lut + 256u + (uint32_t)warp * (uint32_t)P.warp_bytes;
     const uint32_t mbar = smem0 + wbase, buf = wbase + 16u;
@@ -1356,6 +1363,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_pairs(const __grid_constant__ 
             __syncwarp();
             // the two groups; after each mini-step the halos of the 5 rows it
             // may change (lane l < 10: row l / 2, side l % 2)
+            uint32_t accN32 = 0;  // this pair's accepted trials (at most 8 NKW per lane)
             auto run_group = [&](auto Hc) {
                 constexpr int H = decltype(Hc)::value;
                 uint32_t hrow = 0;
@@ -1374,7 +1382,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_pairs(const __grid_constant__ 
                         wr[k][1] = wr[k][2];
                         wr[k][2] = wr[k][3];
                     }
-                    pair2_trials<IS_INT, RB, NKW, H>(P, body, q.soff, nx, dx, lane, cx, ti, lut, qt, wv, accE, accN);
+                    pair2_trials<IS_INT, RB, NKW, H>(P, body, q.soff, nx, dx, lane, cx, ti, lut, qt, wv, accE, accN32);
                     __syncwarp();
                     if (lane < 10) {
                         if (lane & 1)
@@ -1388,6 +1396,7 @@ __global__ void __launch_bounds__(512, 1) k_sweep_pairs(const __grid_constant__ 
             run_group(std::integral_constant<int, 0>());
             philox_group(1);
             run_group(std::integral_constant<int, 1>());
+            accN += accN32;
             // write back the rows the pair changed: own (0, 0) of both groups
             // (slots 5, 6) and partner slots 16-18 and 21-23
 #pragma unroll 1
