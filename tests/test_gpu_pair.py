@@ -305,15 +305,21 @@ def test_batched_replicas_equal_single_runs(smc):
         assert int(n1.item()) == int(n_acc[r].item())
 
 
-def test_timeout_is_reported_and_gpu_stays_usable(smc):
-    dims, S = (16, 16, 16), 2
+@pytest.mark.parametrize("dims,streaming", [((16, 16, 16), False), ((16, 16, 16), True), ((128, 8, 8), True)])
+def test_timeout_is_reported_and_gpu_stays_usable(smc, dims, streaming):
+    """A tile that never publishes its progress: the waits of its neighbours
+    give up after the time limit, the call reports SMC_ERR_TIMEOUT, and the
+    next call runs normally -- the default path, the single-group streaming
+    kernel and the paired one (rows of 128 cells)."""
+    S = 2
     V = int_model(S, 2, 1)
-    counts = inputs.equiatomic_counts(2 * 16 ** 3, S)
+    counts = inputs.equiatomic_counts(2 * dims[0] * dims[1] * dims[2], S)
     lat, occ = gpu_state(smc, dims, S, counts, 1)
     model = smc.Model(smc.PAIR_I32, 2, V, unit_ev=1e-4)
     smc.set_tuning(1, 1, 32, 0)
     smc.debug_set(smc.DBG_TIMEOUT_MS, 200)
     smc.debug_set(smc.DBG_SKIP_PUBLISH, 3)
+    smc.debug_set(smc.DBG_RESIDENT, 1 if streaming else 0)
     try:
         smc.sweep(lat, model, occ, 1, 0, 2, 0.025)
         with pytest.raises(smc.SMCError) as ei:
@@ -322,6 +328,7 @@ def test_timeout_is_reported_and_gpu_stays_usable(smc):
     finally:
         smc.debug_set(smc.DBG_SKIP_PUBLISH, -1)
         smc.debug_set(smc.DBG_TIMEOUT_MS, 2000)
+        smc.debug_set(smc.DBG_RESIDENT, 0)
         smc.set_tuning()
     # the context is intact: a normal run still matches the oracle
     _run_int(smc, (8, 8, 8), 2, 2, 3, 0.025)
