@@ -173,7 +173,9 @@ smc_status smc_init_lattice(const smc_lattice *lat, const int64_t *counts, uint6
  * whose rows fit the SMs' shared memory (128^3 and below) keep the lattice
  * there for the whole call (one cooperative launch per call, row versions
  * exchanged between CTAs through L2); larger lattices stream their rows from
- * device memory.  Both give the same trajectory bit for bit.
+ * device memory (rows of 128, 256 or 512 cells with a two-shell model of at
+ * most 5 species and a 16-byte aligned occ: two groups of mini-steps per
+ * staging of a column's rows).  All give the same trajectory bit for bit.
  * Errors: SMC_ERR_ARG (dimensions, model, kT), SMC_ERR_UNSUPPORTED (MLP or
  * qSRO models on lattices their kernels do not take), SMC_ERR_CUDA. */
 smc_status smc_sweep(const smc_lattice *lat, const smc_model *model, int8_t *occ, uint64_t seed,
